@@ -1,0 +1,521 @@
+"""Seeded synthetic tracker events: the shared input generator.
+
+The paper's workloads (simulated ttbar events with pile-up in the CMS Phase-1 and
+Phase-2 trackers, Sec. 2.3) are not available, so events are simulated here with
+the shapes the method sees: tracks from the origin through barrel cylinders and
+endcap disks in a uniform solenoid field, one Gaussian-smeared 3D hit per crossed
+layer, multiple-scattering kicks and mean energy loss at each crossing, uniform
+noise hits, and seeds made of the true hits on the first three crossed layers.
+
+This module is test and benchmark input only.  It contains no step of the Kalman
+filter: tracks are moved with the circle-centre description of a helix
+(circle-circle intersection for cylinders), which is a different formulation
+from the path-length form with Newton iteration that the filter uses, and all
+random numbers are drawn here.  Both the CUDA path and the FP64 oracle consume
+its arrays; it imports neither of them.
+
+Units: cm, GeV, tesla, radians.  Packed 3x3 covariance order: xx, yx, yy, zx, zy, zz.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BARREL = 0
+DISK = 1
+
+C_LIGHT = 0.00299792458      # curvature [1/cm] = C_LIGHT * B[T] / pT[GeV]
+M_PION = 0.13957039          # GeV
+M_ELECTRON = 0.51099895e-3   # GeV
+# Silicon (PDG atomic and nuclear properties)
+SI_K = 0.307075              # MeV cm^2 / mol
+SI_Z_OVER_A = 0.49848
+SI_RHO = 2.329               # g / cm^3
+SI_X0 = 9.37                 # cm
+SI_I = 173.0e-9              # GeV
+INCIDENCE_CAP = 10.0
+
+
+# --------------------------------------------------------------------------- geometry
+
+@dataclass
+class Geometry:
+    """Layers (Sec. 3.1: an r-z bounding box that aggregates hits) and layer plans."""
+    kind: np.ndarray          # int32 [L]: BARREL or DISK
+    pos: np.ndarray           # float64 [L]: R (barrel) or z (disk)
+    lo: np.ndarray            # barrel zmin / disk rmin
+    hi: np.ndarray            # barrel zmax / disk rmax
+    x_over_x0: np.ndarray     # thickness at normal incidence [X0]
+    sig: np.ndarray           # float64 [L,3]: hit sigma along (r-hat, phi-hat, z-hat)
+    n_eta: np.ndarray         # int32 [L] eta bins of the hit index
+    n_phi: np.ndarray         # int32 [L] phi bins of the hit index
+    eta_lo: np.ndarray        # float64 [L] eta range covered by the bins
+    eta_hi: np.ndarray
+    plans: list               # list of lists of layer indices, one per tracking region
+    bz: float = 3.8
+    barrel_eta_max: float = 1.0   # |eta_seed| below this -> region 0, else 1 (+z) / 2 (-z)
+
+    @property
+    def n_layers(self) -> int:
+        return int(self.kind.shape[0])
+
+    def plan_arrays(self):
+        """Concatenated plans and their offsets (int32), the form the C interfaces take."""
+        off = np.zeros(len(self.plans) + 1, np.int32)
+        for i, pl in enumerate(self.plans):
+            off[i + 1] = off[i] + len(pl)
+        flat = np.concatenate([np.asarray(p, np.int32) for p in self.plans]).astype(np.int32)
+        return flat, off
+
+    @property
+    def max_plan(self) -> int:
+        return max(len(p) for p in self.plans)
+
+
+def _layer_table(rows, plans, bz=3.8, barrel_eta_max=1.0) -> Geometry:
+    kind = np.array([r[0] for r in rows], np.int32)
+    pos = np.array([r[1] for r in rows], np.float64)
+    lo = np.array([r[2] for r in rows], np.float64)
+    hi = np.array([r[3] for r in rows], np.float64)
+    xx0 = np.array([r[4] for r in rows], np.float64)
+    sig = np.array([r[5] for r in rows], np.float64)
+    n_eta = np.array([r[6] for r in rows], np.int32)
+    n_phi = np.array([r[7] for r in rows], np.int32)
+    eta_lo = np.empty(len(rows))
+    eta_hi = np.empty(len(rows))
+    for i in range(len(rows)):
+        if kind[i] == BARREL:
+            eta_lo[i] = np.arcsinh(lo[i] / pos[i])
+            eta_hi[i] = np.arcsinh(hi[i] / pos[i])
+        else:
+            a = np.arcsinh(pos[i] / hi[i])
+            b = np.arcsinh(pos[i] / lo[i])
+            eta_lo[i], eta_hi[i] = (a, b) if pos[i] > 0 else (-b, -a)
+    return Geometry(kind, pos, lo, hi, xx0, sig, n_eta, n_phi, eta_lo, eta_hi,
+                    [list(p) for p in plans], bz, barrel_eta_max)
+
+
+SIG_BARREL = (30e-4, 30e-4, 100e-4)   # (r, r-phi, z): 30 um r-phi, 100 um z, 30 um along the normal
+SIG_DISK = (100e-4, 30e-4, 30e-4)     # (r, r-phi, z): z is the disk normal
+
+
+def barrel_radii(n=10, r0=4.0, r1=100.0):
+    return [r0 + (r1 - r0) * i / (n - 1) for i in range(n)]
+
+
+def disk_z(n=12, z0=125.0, z1=275.0):
+    return [z0 + (z1 - z0) * j / (n - 1) for j in range(n)]
+
+
+def _eta_bins(width, lo, hi):
+    return max(8, int(np.ceil((hi - lo) / width)))
+
+
+def geometry_barrel(n_layers=10, zmax=120.0, x_over_x0=0.02, n_eta=32, n_phi=128,
+                    bz=3.8) -> Geometry:
+    """Phase-1-like barrel: cylinders at r = 4..100 cm, |z| <= zmax; one region."""
+    rows = [(BARREL, r, -zmax, zmax, x_over_x0, SIG_BARREL, n_eta, n_phi)
+            for r in barrel_radii(n_layers)]
+    return _layer_table(rows, [list(range(n_layers))], bz=bz, barrel_eta_max=1e9)
+
+
+def geometry_phase2(x_over_x0=0.02, eta_bin=0.05, n_phi=256, sides=(+1, -1), bz=3.8,
+                    barrel_eta_max=1.0) -> Geometry:
+    """Phase-2-like tracker: 10 cylinders plus 12 disks per side covering |eta| < 3.
+
+    Regions (layer plans): 0 barrel = cylinders; 1 endcap+ = cylinders then +z disks;
+    2 endcap- = cylinders then -z disks.  With sides=(+1,) it is the 22-layer
+    (10 barrel + 12 disk) single-endcap tracker with one plan.
+    """
+    zmax = 120.0
+    rows = []
+    for r in barrel_radii():
+        e = np.arcsinh(zmax / r)
+        rows.append((BARREL, r, -zmax, zmax, x_over_x0, SIG_BARREL,
+                     _eta_bins(eta_bin, -e, e), n_phi))
+    disk_first = {}
+    for side in sides:
+        disk_first[side] = len(rows)
+        for zd in disk_z():
+            rmin = zd / np.sinh(3.0)
+            e0, e1 = np.arcsinh(zd / 100.0), np.arcsinh(zd / rmin)
+            rows.append((DISK, side * zd, rmin, 100.0, x_over_x0, SIG_DISK,
+                         _eta_bins(eta_bin, e0, e1), n_phi))
+    cyl = list(range(10))
+    if len(sides) == 1:
+        plans = [cyl + list(range(disk_first[sides[0]], disk_first[sides[0]] + 12))]
+        return _layer_table(rows, plans, bz=bz, barrel_eta_max=-1.0)
+    plans = [cyl,
+             cyl + list(range(disk_first[+1], disk_first[+1] + 12)),
+             cyl + list(range(disk_first[-1], disk_first[-1] + 12))]
+    return _layer_table(rows, plans, bz=bz, barrel_eta_max=barrel_eta_max)
+
+
+# --------------------------------------------------------------------------- params
+
+def default_params(**kw) -> dict:
+    """Search parameters (Sec. 3.2 IterationParams / IterationLayerConfig), one set for all layers."""
+    p = dict(chi2_cut=30.0, max_cands=6, max_holes=3, win_nsigma=3.5,
+             deta_min=0.002, deta_max=0.1, dphi_min=0.002, dphi_max=0.1,
+             score_hit=4.0, score_hole=8.0, material=1)
+    p.update(kw)
+    return p
+
+
+# --------------------------------------------------------------------------- physics of the simulated detector
+
+def _bethe_bloch_loss(p, t):
+    """Mean energy lost [GeV] by a pion of momentum p crossing t radiation lengths of silicon."""
+    m = M_PION
+    e = np.sqrt(p * p + m * m)
+    bg2 = (p / m) ** 2
+    b2 = bg2 / (1.0 + bg2)
+    gam = e / m
+    me = M_ELECTRON
+    tmax = 2.0 * me * bg2 / (1.0 + 2.0 * gam * me / m + (me / m) ** 2)
+    dedx = SI_K * SI_Z_OVER_A / b2 * (0.5 * np.log(2.0 * me * bg2 * tmax / (SI_I * SI_I)) - b2)
+    return dedx * SI_RHO * (t * SI_X0) * 1e-3
+
+
+def _highland(p, t):
+    beta = p / np.sqrt(p * p + M_PION * M_PION)
+    return 0.0136 / (beta * p) * np.sqrt(t) * (1.0 + 0.038 * np.log(t / (beta * beta)))
+
+
+def _local_cov6(phi, sig):
+    """3x3 covariance (packed) of a hit whose local axes are (r-hat, phi-hat, z-hat) at azimuth phi."""
+    c, s = np.cos(phi), np.sin(phi)
+    sr2, sp2, sz2 = (np.asarray(sig[..., 0]) ** 2, np.asarray(sig[..., 1]) ** 2,
+                     np.asarray(sig[..., 2]) ** 2)
+    out = np.zeros(np.broadcast(phi, sr2).shape + (6,))
+    out[..., 0] = sr2 * c * c + sp2 * s * s
+    out[..., 1] = (sr2 - sp2) * c * s
+    out[..., 2] = sr2 * s * s + sp2 * c * c
+    out[..., 5] = sz2
+    return out
+
+
+def _smear(x, y, z, sig, rng):
+    phi = np.arctan2(y, x)
+    g = rng.standard_normal((3,) + np.shape(x))
+    dr, dp, dz = g[0] * sig[..., 0], g[1] * sig[..., 1], g[2] * sig[..., 2]
+    c, s = np.cos(phi), np.sin(phi)
+    return x + dr * c - dp * s, y + dr * s + dp * c, z + dz
+
+
+class _Tracks:
+    """Vectorised truth state: position, transverse direction phi, polar angle, |p|, charge."""
+
+    def __init__(self, q, pt, eta, phi, x=None, y=None, z=None):
+        n = q.shape[0]
+        self.q = q.astype(np.float64)
+        self.theta = 2.0 * np.arctan(np.exp(-eta))
+        self.p = pt / np.sin(self.theta)
+        self.phi = phi.astype(np.float64)
+        self.x = np.zeros(n) if x is None else x
+        self.y = np.zeros(n) if y is None else y
+        self.z = np.zeros(n) if z is None else z
+
+    def omega(self, bz, idx):
+        pt = self.p[idx] * np.sin(self.theta[idx])
+        return -self.q[idx] * C_LIGHT * bz / pt
+
+
+def _cylinder_crossing(x, y, phi, om, R):
+    """First positive transverse path to radius R along circles given by centre (returns nan if none)."""
+    n = x.shape[0]
+    s_out = np.full(n, np.nan)
+    straight = np.abs(om) < 1e-15
+    if np.any(straight):
+        i = straight
+        b = x[i] * np.cos(phi[i]) + y[i] * np.sin(phi[i])
+        d2 = R * R - (x[i] * np.sin(phi[i]) - y[i] * np.cos(phi[i])) ** 2
+        s = -b + np.sqrt(np.maximum(d2, 0.0))
+        s_out[i] = np.where((d2 >= 0) & (s > 0), s, np.nan)
+    i = ~straight
+    if np.any(i):
+        w = om[i]
+        cx = x[i] - np.sin(phi[i]) / w
+        cy = y[i] + np.cos(phi[i]) / w
+        rho = 1.0 / np.abs(w)
+        d = np.hypot(cx, cy)
+        ok = (d > 0) & (np.abs(d - rho) <= R) & (R <= d + rho)
+        dd = np.where(d > 0, d, 1.0)
+        a = (rho * rho - R * R + dd * dd) / (2.0 * dd)
+        h = np.sqrt(np.maximum(rho * rho - a * a, 0.0))
+        ex, ey = -cx / dd, -cy / dd
+        best = np.full(w.shape, np.inf)
+        for sgn in (+1.0, -1.0):
+            px = cx + a * ex - sgn * h * ey
+            py = cy + a * ey + sgn * h * ex
+            psi = np.arctan2(w * (px - cx), -w * (py - cy))
+            turn = np.mod((psi - phi[i]) * np.sign(w), 2.0 * np.pi)
+            s = turn * rho
+            s = np.where(s > 1e-9, s, np.inf)
+            best = np.minimum(best, s)
+        best = np.where(ok & np.isfinite(best), best, np.nan)
+        s_out[i] = best
+    return s_out
+
+
+def _move(x, y, z, phi, theta, om, s):
+    """Position and direction after transverse path s (circle-centre form)."""
+    straight = np.abs(om) < 1e-15
+    w = np.where(straight, 1.0, om)
+    cx = x - np.sin(phi) / w
+    cy = y + np.cos(phi) / w
+    psi = phi + om * s
+    xn = np.where(straight, x + s * np.cos(phi), cx + np.sin(psi) / w)
+    yn = np.where(straight, y + s * np.sin(phi), cy - np.cos(psi) / w)
+    zn = z + s / np.tan(theta)
+    return xn, yn, zn, psi
+
+
+# --------------------------------------------------------------------------- events
+
+@dataclass
+class Event:
+    """One event's hits grouped by layer, truth, and seeds (event-local hit indices)."""
+    hit_xyz: np.ndarray        # float32 [H,3]
+    hit_cov: np.ndarray        # float32 [H,6]
+    layer_off: np.ndarray      # int64 [L+1]
+    hit_track: np.ndarray      # int32 [H], -1 for noise
+    track_q: np.ndarray
+    track_pt: np.ndarray
+    track_eta: np.ndarray
+    track_phi: np.ndarray
+    track_hits: np.ndarray     # int32 [T, maxh] local hit indices in crossing order, -1 padded
+    track_layers: np.ndarray   # int32 [T, maxh]
+    track_truth: np.ndarray    # float64 [T, maxh, 6] state (x,y,z,q/pT,phi,theta) leaving each hit's layer
+    seed_hits: np.ndarray      # int32 [S,3]
+    seed_track: np.ndarray     # int32 [S]
+
+    @property
+    def n_hits(self):
+        return int(self.hit_xyz.shape[0])
+
+
+def _traversal(geom: Geometry, side: int):
+    cyl = sorted([i for i in range(geom.n_layers) if geom.kind[i] == BARREL], key=lambda i: geom.pos[i])
+    dsk = sorted([i for i in range(geom.n_layers) if geom.kind[i] == DISK and np.sign(geom.pos[i]) == side],
+                 key=lambda i: abs(geom.pos[i]))
+    return cyl + dsk
+
+
+def sample_pt_loguniform(rng, n, lo, hi):
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), n))
+
+
+def sample_pt_phase2(rng, n, frac_low=0.7):
+    """70% log-uniform in [0.5, 2] GeV, the rest log-uniform in [2, 50] GeV."""
+    low = rng.random(n) < frac_low
+    return np.where(low, sample_pt_loguniform(rng, n, 0.5, 2.0), sample_pt_loguniform(rng, n, 2.0, 50.0))
+
+
+def simulate_event(geom: Geometry, n_tracks: int, seed: int = 0, event: int = 0, *,
+                   pt_sampler=None, eta_max=1.0, eta_min=None, noise_per_layer=None,
+                   noise_total=None, material=True, smear=True, min_hits_seed=3) -> Event:
+    """Simulate one event.  Random streams depend only on (seed, event)."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, event])))
+    L = geom.n_layers
+    q = rng.choice(np.array([-1.0, 1.0]), n_tracks)
+    pt = (pt_sampler(rng, n_tracks) if pt_sampler is not None
+          else sample_pt_loguniform(rng, n_tracks, 0.5, 10.0))
+    lo_eta = -eta_max if eta_min is None else eta_min
+    eta = rng.uniform(lo_eta, eta_max, n_tracks)
+    phi0 = rng.uniform(-np.pi, np.pi, n_tracks)
+    trk = _Tracks(q, pt, eta, phi0)
+    plus = _traversal(geom, +1)
+    minus = _traversal(geom, -1)
+    nstep = max(len(plus), len(minus))
+    side_plus = trk.theta < 0.5 * np.pi
+
+    maxh = nstep
+    t_layers = np.full((n_tracks, maxh), -1, np.int32)
+    t_truth = np.zeros((n_tracks, maxh, 6))
+    t_xyz = np.zeros((n_tracks, maxh, 3))
+    nh = np.zeros(n_tracks, np.int32)
+    alive = np.ones(n_tracks, bool)
+
+    for j in range(nstep):
+        for side_mask, trav in ((side_plus, plus), (~side_plus, minus)):
+            if j >= len(trav):
+                continue
+            lay = trav[j]
+            idx = np.nonzero(side_mask & alive)[0]
+            if idx.size == 0:
+                continue
+            om = trk.omega(geom.bz, idx)
+            x, y, z, ph, th = trk.x[idx], trk.y[idx], trk.z[idx], trk.phi[idx], trk.theta[idx]
+            if geom.kind[lay] == BARREL:
+                s = _cylinder_crossing(x, y, ph, om, geom.pos[lay])
+            else:
+                s = (geom.pos[lay] - z) * np.tan(th)
+                s = np.where(s > 0, s, np.nan)
+            ok = np.isfinite(s)
+            s = np.where(ok, s, 0.0)
+            xn, yn, zn, psi = _move(x, y, z, ph, th, om, s)
+            if geom.kind[lay] == BARREL:
+                ok &= (zn >= geom.lo[lay]) & (zn <= geom.hi[lay])
+            else:
+                rn = np.hypot(xn, yn)
+                ok &= (rn >= geom.lo[lay]) & (rn <= geom.hi[lay])
+            sel = idx[ok]
+            if sel.size == 0:
+                continue
+            xn, yn, zn, psi = xn[ok], yn[ok], zn[ok], psi[ok]
+            th = th[ok]
+            k = nh[sel]
+            t_layers[sel, k] = lay
+            t_xyz[sel, k] = np.stack([xn, yn, zn], -1)
+            # material: Highland kick at fixed |p|, then mean energy loss
+            p = trk.p[sel]
+            if material and geom.x_over_x0[lay] > 0:
+                ux, uy, uz = np.sin(th) * np.cos(psi), np.sin(th) * np.sin(psi), np.cos(th)
+                if geom.kind[lay] == BARREL:
+                    rr = np.hypot(xn, yn)
+                    cosi = np.abs((xn * ux + yn * uy) / rr)
+                else:
+                    cosi = np.abs(uz)
+                t = geom.x_over_x0[lay] * np.minimum(1.0 / np.maximum(cosi, 1e-300), INCIDENCE_CAP)
+                th0 = _highland(p, t)
+                g = rng.standard_normal((2, sel.size))
+                th_new = th + th0 * g[0]
+                psi = psi + th0 * g[1] / np.sin(th)
+                th = np.clip(th_new, 1e-6, np.pi - 1e-6)
+                e = np.sqrt(p * p + M_PION ** 2) - _bethe_bloch_loss(p, t)
+                p = np.sqrt(np.maximum(e * e - M_PION ** 2, 1e-12))
+            psi = np.mod(psi + np.pi, 2.0 * np.pi) - np.pi
+            trk.x[sel], trk.y[sel], trk.z[sel] = xn, yn, zn
+            trk.phi[sel], trk.theta[sel], trk.p[sel] = psi, th, p
+            t_truth[sel, k] = np.stack([xn, yn, zn, trk.q[sel] / (p * np.sin(th)), psi, th], -1)
+            nh[sel] += 1
+
+    # assemble hits per layer: signal + noise, shuffled within the layer
+    if noise_total is not None:
+        area = np.where(geom.kind == BARREL, 2 * np.pi * np.abs(geom.pos) * (geom.hi - geom.lo),
+                        np.pi * (geom.hi ** 2 - geom.lo ** 2))
+        n_noise = np.floor(noise_total * area / area.sum()).astype(np.int64)
+        n_noise[: int(noise_total - n_noise.sum())] += 1
+    else:
+        n_noise = np.full(L, 0 if noise_per_layer is None else int(noise_per_layer), np.int64)
+
+    xyz_parts, cov_parts, trk_parts = [], [], []
+    local_of = np.full((n_tracks, maxh), -1, np.int64)
+    layer_off = np.zeros(L + 1, np.int64)
+    for lay in range(L):
+        ti, ki = np.nonzero(t_layers == lay)
+        sx, sy, sz = t_xyz[ti, ki, 0], t_xyz[ti, ki, 1], t_xyz[ti, ki, 2]
+        nn = int(n_noise[lay])
+        u = rng.random((2, nn))
+        nphi = -np.pi + 2 * np.pi * u[0]
+        if geom.kind[lay] == BARREL:
+            r = np.full(nn, geom.pos[lay])
+            nz = geom.lo[lay] + (geom.hi[lay] - geom.lo[lay]) * u[1]
+        else:
+            r = np.sqrt(geom.lo[lay] ** 2 + (geom.hi[lay] ** 2 - geom.lo[lay] ** 2) * u[1])
+            nz = np.full(nn, geom.pos[lay])
+        ax = np.concatenate([sx, r * np.cos(nphi)])
+        ay = np.concatenate([sy, r * np.sin(nphi)])
+        az = np.concatenate([sz, nz])
+        owner = np.concatenate([ti, np.full(nn, -1)]).astype(np.int32)
+        sig = np.broadcast_to(geom.sig[lay], (ax.size, 3))
+        if smear:
+            ax, ay, az = _smear(ax, ay, az, sig, rng)
+        perm = rng.permutation(ax.size)
+        ax, ay, az, owner = ax[perm], ay[perm], az[perm], owner[perm]
+        inv = np.empty_like(perm)
+        inv[perm] = np.arange(perm.size)
+        base = layer_off[lay]
+        local_of[ti, ki] = base + inv[: ti.size]
+        cov = _local_cov6(np.arctan2(ay, ax), np.broadcast_to(geom.sig[lay], (ax.size, 3)))
+        xyz_parts.append(np.stack([ax, ay, az], -1))
+        cov_parts.append(cov)
+        trk_parts.append(owner)
+        layer_off[lay + 1] = base + ax.size
+
+    hit_xyz = np.concatenate(xyz_parts).astype(np.float32) if xyz_parts else np.zeros((0, 3), np.float32)
+    hit_cov = np.concatenate(cov_parts).astype(np.float32) if cov_parts else np.zeros((0, 6), np.float32)
+    hit_track = np.concatenate(trk_parts).astype(np.int32) if trk_parts else np.zeros(0, np.int32)
+    track_hits = np.where(t_layers >= 0, local_of, -1).astype(np.int32)
+    has_seed = nh >= min_hits_seed
+    seed_track = np.nonzero(has_seed)[0].astype(np.int32)
+    seed_hits = track_hits[seed_track, :3].astype(np.int32)
+    return Event(hit_xyz, hit_cov, layer_off, hit_track, q, pt, eta, phi0,
+                 track_hits, t_layers, t_truth, seed_hits, seed_track)
+
+
+@dataclass
+class Batch:
+    """Several events concatenated: global hit index = hit_off[e*L] + event-local index."""
+    n_events: int
+    n_layers: int
+    hit_xyz: np.ndarray
+    hit_cov: np.ndarray
+    hit_off: np.ndarray        # int64 [E*L+1]
+    hit_track: np.ndarray
+    seed_hits: np.ndarray      # int32 [S,3] global hit indices
+    seed_event: np.ndarray     # int32 [S]
+    seed_track: np.ndarray     # int32 [S] event-local track index
+    events: list = field(default_factory=list)
+
+
+def concat_events(events, n_layers) -> Batch:
+    offs = [0]
+    for ev in events:
+        offs.append(offs[-1] + ev.n_hits)
+    hit_off = np.concatenate([[0]] + [offs[e] + ev.layer_off[1:] for e, ev in enumerate(events)]).astype(np.int64)
+    seeds = [ev.seed_hits + offs[e] for e, ev in enumerate(events)]
+    return Batch(len(events), n_layers,
+                 np.concatenate([ev.hit_xyz for ev in events]),
+                 np.concatenate([ev.hit_cov for ev in events]),
+                 hit_off,
+                 np.concatenate([ev.hit_track for ev in events]),
+                 np.concatenate(seeds).astype(np.int32) if seeds else np.zeros((0, 3), np.int32),
+                 np.concatenate([np.full(ev.seed_hits.shape[0], e, np.int32) for e, ev in enumerate(events)]),
+                 np.concatenate([ev.seed_track for ev in events]).astype(np.int32),
+                 list(events))
+
+
+def fit_workload(ev: Event, seed: int = 0, *, sig_pos=0.005, sig_z=0.01, rel_k=0.05,
+                 sig_ang=0.002, min_hits=1, event_offset=0):
+    """Tracks with their true hit assignment and a starting state drawn around the truth at the origin.
+
+    Returns (layers [T,maxh] int32 (-1 end), hits [T,maxh] int32 global indices, p0 [T,6], c0 [T,21],
+    truth_last [T,6], n_hits [T]).  p0 ~ N(truth at vertex, C0) so that a consistent fit has unit pulls.
+    """
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 7919])))
+    nh = (ev.track_layers >= 0).sum(1)
+    sel = np.nonzero(nh >= min_hits)[0]
+    T = sel.size
+    theta = 2.0 * np.arctan(np.exp(-ev.track_eta[sel]))
+    k = ev.track_q[sel] / ev.track_pt[sel]
+    truth0 = np.stack([np.zeros(T), np.zeros(T), np.zeros(T), k, ev.track_phi[sel], theta], -1)
+    sig = np.stack([np.full(T, sig_pos), np.full(T, sig_pos), np.full(T, sig_z),
+                    rel_k * np.abs(k), np.full(T, sig_ang), np.full(T, sig_ang)], -1)
+    p0 = truth0 + sig * rng.standard_normal((T, 6))
+    c0 = np.zeros((T, 21))
+    for i in range(6):
+        c0[:, i * (i + 1) // 2 + i] = sig[:, i] ** 2
+    layers = ev.track_layers[sel].copy()
+    hits = np.where(ev.track_hits[sel] >= 0, ev.track_hits[sel] + event_offset, -1).astype(np.int32)
+    last = nh[sel] - 1
+    truth_last = ev.track_truth[sel, last]
+    return layers, hits, p0, c0, truth_last, nh[sel].astype(np.int32), sel
+
+
+def workload_small_barrel(seed=0):
+    """1,000 tracks through 10 barrel cylinders, pT log-uniform 0.5-10 GeV, |eta| < 1,
+    2% X0 per layer, 200 uniform noise hits per layer."""
+    g = geometry_barrel()
+    ev = simulate_event(g, 1000, seed, 0, eta_max=1.0, noise_per_layer=200)
+    return g, ev
+
+
+def workload_phase2(n_events=64, n_tracks=20000, seed=0, noise_total=50000):
+    """Phase-2-like events: 10 cylinders + 2x12 disks, |eta| < 3, pT 0.5-50 GeV (70% below 2)."""
+    g = geometry_phase2()
+    evs = [simulate_event(g, n_tracks, seed, e, pt_sampler=sample_pt_phase2, eta_max=3.0,
+                          noise_total=noise_total) for e in range(n_events)]
+    return g, evs

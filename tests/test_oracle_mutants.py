@@ -1,0 +1,49 @@
+"""Plant plausible mistakes in copies of the oracle (a dropped term, a wrong sign, a wrong
+index, a transposed operand) and check that the pin suite fails on every one of them."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "mkoracle.c")
+PINS = ["tests/test_oracle_propagation.py", "tests/test_oracle_kalman.py", "tests/test_oracle_search.py"]
+
+MUTANTS = {
+    "jacobian_sign": ("A[0 * 6 + 4] = -dy;", "A[0 * 6 + 4] = dy;"),
+    "jacobian_dk": ("A[4 * 6 + 3] = -cB * s;", "A[4 * 6 + 3] = cB * s;"),
+    "transport_transposed": ("acc += T[i][l] * J[j * 6 + l];", "acc += T[i][l] * J[l * 6 + j];"),
+    "ms_dropped_kk": ("C[ix(3, 3)] += k * k * cot * cot * th02;", ";"),
+    "ms_ktheta_sign": ("C[ix(5, 3)] += -k * cot * th02;", "C[ix(5, 3)] += k * cot * th02;"),
+    "ms_phi_sin": ("C[ix(4, 4)] += th02 / (st * st);", "C[ix(4, 4)] += th02;"),
+    "highland_log": ("log(t / (beta * beta))", "log(t * beta * beta)"),
+    "eloss_sign": ("double e2 = e - direction * orc_eloss(pm, t);", "double e2 = e + direction * orc_eloss(pm, t);"),
+    "update_sign": ("pout[i] = p[i] + K[i][0] * r[0]", "pout[i] = p[i] - K[i][0] * r[0]"),
+    "chi2_index": ("double y2 = (r[2] - Lc[3] * y0 - Lc[4] * y1) / Lc[5];",
+                   "double y2 = (r[2] - Lc[4] * y0 - Lc[3] * y1) / Lc[5];"),
+    "helix_cot": ("out[2] = p[2] + s * cos(p[5]) / sin(p[5]);", "out[2] = p[2] + s * sin(p[5]) / cos(p[5]);"),
+    "seed_charge": ("k = -om / cB;", "k = om / cB;"),
+    "window_index": ("ve += ge[i] * M[i][j] * ge[j];", "ve += ge[i] * M[i][i] * ge[j];"),
+    "miss_penalty_sign": ("ch.score = cd->score - P->score_hole;", "ch.score = cd->score + P->score_hole;"),
+    "child_order": ("if (x->score != y->score) return x->score > y->score ? -1 : 1;",
+                    "if (x->score != y->score) return x->score < y->score ? -1 : 1;"),
+    "bin_guard": ("int e0 = eta_bin(L, w[0] - w[2] - eps), e1 = eta_bin(L, w[0] + w[2] + eps);",
+                  "int e0 = eta_bin(L, w[0]), e1 = eta_bin(L, w[0]);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not found exactly once"
+    mut = tmp_path / "mut.c"
+    mut.write_text(src.replace(old, new))
+    so = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-I", os.path.join(ROOT, "oracle"), "-o", str(so), str(mut), "-lm"])
+    env = dict(os.environ, MKORACLE_LIB=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
