@@ -1,0 +1,335 @@
+"""Benchmark: Kalman propagate + chi2 + update steps/s on one GB300 (or N replicas).
+
+Workload: Phase-2-like events, 64 per batch, 20,000 tracks and 50,000 noise hits each, 10 barrel
+cylinders + 2x12 endcap disks, best-N = 6.  One step = one pass of the whole hot path over the
+batch: bin every layer's hits, seed, combinatorial forward search, and the Kalman fit of every
+track over its known hits.  Kalman steps = candidate-layer steps of the search + track-layer
+steps of the fit (crossed layers), counted by the kernels themselves.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Inputs are seeded and synthetic (see paper_2312_11728_gb300/synth.py).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Kalman propagate+χ²+update steps/s on 1 GB300; % of FP32/HBM roofline"
+UNIT = "Kalman steps/s"
+N_EVENTS, N_TRACKS, N_NOISE = 64, 20000, 50000
+WORKLOAD = "phase2_like_64ev_20k_tracks_50k_noise_bestN6"
+
+# Algorithmic FP32 operations per unit of work (FMA = 2), counted from the kernel source
+# (csrc/kalman.cuh); multi-function-unit work (sqrt, rsqrt, division, sincos, log, atan2) is
+# not counted.  Derivation in the design doc.
+FLOPS = dict(step=730, newton=22, tested=6, chi2=46, update=770)
+
+
+def build_flops(c):
+    """c: build counters [steps, chi2 evaluations, updates, hits tested, Newton iterations]."""
+    return (FLOPS["step"] * c[0] + FLOPS["chi2"] * c[1] + FLOPS["update"] * c[2] + FLOPS["tested"] * c[3]
+            + FLOPS["newton"] * c[4])
+
+
+def fit_flops(c):
+    return FLOPS["step"] * c[0] + (FLOPS["chi2"] + FLOPS["update"]) * c[2] + FLOPS["newton"] * c[4]
+
+
+def _gen_event(args):
+    e, seed = args
+    from paper_2312_11728_gb300 import synth as S
+    g = S.geometry_phase2()
+    return S.simulate_event(g, N_TRACKS, seed, e, pt_sampler=S.sample_pt_phase2, eta_max=3.0, noise_total=N_NOISE)
+
+
+def make_batch(seed, n_events=N_EVENTS):
+    """Events generated in a spawn pool (before any CUDA call in this process)."""
+    from paper_2312_11728_gb300 import synth as S
+    g = S.geometry_phase2()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        evs = pool.map(_gen_event, [(e, seed) for e in range(n_events)])
+    return g, S.concat_events(evs, g.n_layers)
+
+
+def scan_launches(n):
+    """Kernels one device-wide exclusive scan of n ints launches (mirrors csrc/k_hits.cu)."""
+    nb = (n + 2047) // 2048
+    return 1 if nb <= 1 else 3 + scan_launches(nb)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                out, _ = self.p.communicate()
+            self.rows = [r.split(", ") for r in out.strip().splitlines() if r.count(",") >= 8]
+
+    def summary(self):
+        rows = getattr(self, "rows", [])
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.strip() == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+def cpu_baseline(g, batch, fit, params, n_events_sample=2):
+    """The FP64 oracle, as it stands, on a bounded sample: every seed and track of the first events."""
+    import oracle
+    from oracle import parity as PR
+    orc = oracle.Oracle(g, params)
+    sel = np.nonzero(batch.seed_event < n_events_sample)[0]
+    t0 = time.perf_counter()
+    o = PR.oracle_build(orc, batch, sel)
+    tsel = np.nonzero(fit.event < n_events_sample)[0]
+    r = orc.fit_batch(fit.layers[tsel], fit.hits[tsel], batch.hit_xyz.astype(np.float64),
+                      batch.hit_cov.astype(np.float64), fit.p0[tsel].astype(np.float64),
+                      fit.c0[tsel].astype(np.float64))
+    dt = time.perf_counter() - t0
+    steps = int(o["counters"][0] + r["counters"][0])
+    return {"value": steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n_events_sample} of {batch.n_events} events: {len(sel)} seeds built + {len(tsel)} tracks "
+                      f"fitted ({steps} Kalman steps, {dt:.1f} s, FP64, single thread)"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    from paper_2312_11728_gb300 import pipeline, synth as S
+    g, batch = make_batch(0, n_events=2)
+    fit = pipeline.fit_inputs(batch)
+    params = S.default_params()
+    import oracle
+    from oracle import parity as PR
+    orc = oracle.Oracle(g, params)
+    rng = np.random.default_rng(0)
+    per_step = 1500
+    times, steps = [], []
+    for it in range(args.warmup + args.steps):
+        sel = np.sort(rng.choice(batch.seed_hits.shape[0], per_step, replace=False))
+        tsel = np.sort(rng.choice(fit.layers.shape[0], per_step, replace=False))
+        t0 = time.perf_counter()
+        o = PR.oracle_build(orc, batch, sel)
+        r = orc.fit_batch(fit.layers[tsel], fit.hits[tsel], batch.hit_xyz.astype(np.float64),
+                          batch.hit_cov.astype(np.float64), fit.p0[tsel].astype(np.float64),
+                          fit.c0[tsel].astype(np.float64))
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+            steps.append(int(o["counters"][0] + r["counters"][0]))
+    value = sum(steps) / sum(times)
+    sample = f"per step {per_step} random seeds built + {per_step} tracks fitted from the same workload"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    from paper_2312_11728_gb300 import pipeline, synth as S
+    g, batch = make_batch(seed=rank)          # before the first CUDA call (spawn pool)
+    fit = pipeline.fit_inputs(batch, seed=rank)
+    params = S.default_params()
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2312_11728_gb300 import mkgb
+
+    stream = torch.cuda.current_stream()
+    ctx = pipeline.make_context(g, params, device=local, stream=stream)
+    db = pipeline.DeviceBatch(batch, fit, g.max_plan, f"cuda:{local}")
+    n_seeds = batch.seed_hits.shape[0]
+    n_tracks = fit.layers.shape[0]
+
+    def step(ev=None):
+        ctx.load_hits(db.n_events, db.seg_off, db.xyz, db.cov)
+        if ev: ev[0].record(stream)
+        ctx.seed(db.seeds)
+        if ev: ev[1].record(stream)
+        ctx.build(db.out)
+        if ev: ev[2].record(stream)
+        f = db.fit
+        ctx.fit(f["layers"], f["hits"], f["p0"], f["c0"], f["p"], f["c"], f["chi2"], f["status"])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    bc = ctx.counters(0)
+    fc = ctx.counters(1)
+    kalman_steps = int(bc[0] + fc[0])
+
+    ev_step = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            e = ev_step[k]
+            e[3].record(stream)
+            step(e)
+            e[4].record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    total_ms = sum(e[3].elapsed_time(e[4]) for e in ev_step)
+    build_ms = [e[1].elapsed_time(e[2]) for e in ev_step]
+    stage = {"bin_hits": np.mean([e[3].elapsed_time(e[0]) for e in ev_step]),
+             "seed": np.mean([e[0].elapsed_time(e[1]) for e in ev_step]),
+             "build": np.mean(build_ms),
+             "fit": np.mean([e[2].elapsed_time(e[4]) for e in ev_step])}
+    t = torch.tensor([total_ms / 1e3], device=f"cuda:{local}", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    wall = float(t.item())
+    value = kalman_steps * args.steps * world / wall
+
+    # ---- end to end through the C ABI with host (pinned) buffers, copies inside the timed region
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h = dict(xyz=pin(batch.hit_xyz), cov=pin(batch.hit_cov), seeds=pin(batch.seed_hits), layers=pin(fit.layers),
+             hits=pin(fit.hits), p0=pin(fit.p0), c0=pin(fit.c0))
+    ho = {k: torch.from_numpy(v).pin_memory() for k, v in mkgb.alloc_tracks(n_seeds, g.max_plan).items()}
+    hf = dict(p=torch.zeros((n_tracks, 6), dtype=torch.float32).pin_memory(),
+              c=torch.zeros((n_tracks, 21), dtype=torch.float32).pin_memory(),
+              chi2=torch.zeros(n_tracks, dtype=torch.float32).pin_memory(),
+              status=torch.zeros(n_tracks, dtype=torch.int32).pin_memory())
+    h2d = sum(v.numel() * v.element_size() for v in h.values())
+    d2h = sum(v.numel() * v.element_size() for v in ho.values()) + sum(v.numel() * v.element_size() for v in hf.values())
+
+    def e2e_step():
+        ctx.load_hits(db.n_events, db.seg_off, h["xyz"], h["cov"])
+        ctx.seed(h["seeds"])
+        ctx.build(ho)
+        ctx.fit(h["layers"], h["hits"], h["p0"], h["c0"], hf["p"], hf["c"], hf["chi2"], hf["status"])
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_e2e = max(1, min(args.steps, 5))
+    e0.record(stream)
+    for _ in range(n_e2e):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    te = torch.tensor([e0.elapsed_time(e1) / 1e3], device=f"cuda:{local}", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = kalman_steps * n_e2e * world / float(te.item())
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    hbm, sm_max, src = peaks()
+    n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = n_sms * 128 * 2 * sm_max * 1e6 / 1e12        # TFLOP/s at the maximum SM clock
+    achieved = build_flops(bc) / (np.mean(build_ms) / 1e3) / 1e12
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "k_build_traffic.json")
+    if os.path.exists(tr_path):
+        traffic = json.load(open(tr_path)).get("bytes_per_launch")
+    bins_total = batch.n_events * int((g.n_eta.astype(np.int64) * g.n_phi).sum())
+    keys_total = batch.n_events * 32 * 64
+    launches_per_step = (2 + scan_launches(bins_total)) + (2 + scan_launches(keys_total)) + 1 + 1
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "events": batch.n_events, "tracks_per_event": N_TRACKS,
+                   "noise_hits_per_event": N_NOISE, "layers": g.n_layers, "best_n": params["max_cands"],
+                   "seeds": int(n_seeds), "fit_tracks": int(n_tracks), "hits": int(batch.hit_xyz.shape[0]),
+                   "kalman_steps_per_step": kalman_steps, "build_steps": int(bc[0]), "fit_steps": int(fc[0]),
+                   "l2": f"inputs larger than L2: {batch.hit_xyz.shape[0] * 92 / 1e9:.2f} GB of hit data resident",
+                   "parallelism": f"replicas{world}"},
+        "stages_ms": {k: round(float(v), 4) for k, v in stage.items()},
+        "roofline": {"bound": "alu", "kernel": "k_build", "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
+                     "peak_note": f"FP32: {n_sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz ({src} max clock)",
+                     "flops_per_launch": build_flops(bc)},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "clocks": clocks,
+        "counters": {"build": [int(x) for x in bc], "fit": [int(x) for x in fc]},
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(g, batch, fit, params)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

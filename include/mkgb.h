@@ -1,0 +1,166 @@
+/* mkgb — batched Kalman track building and fitting on one GB300 (sm_103a).
+ *
+ * C ABI of libmkgb.so.  The calls follow the paper's statement of the problem
+ * (arXiv:2312.11728): a detector geometry with material, set up once (Sec. 3.1);
+ * hits aggregated per layer (Sec. 3.1); seeds with parameters at their outermost
+ * hit (Sec. 2.2); iteration parameters (Sec. 3.2, IterationParams and
+ * IterationLayerConfig); a combinatorial forward search returning the
+ * best-scoring candidate per seed (Sec. 2.2, forward search); and a plain Kalman
+ * fit over a known hit assignment (Sec. 4, final fit).
+ *
+ * Conventions
+ *  - Units: cm, GeV, tesla, radians.  Track state p = (x, y, z, q/pT, phi, theta),
+ *    phi in (-pi, pi], theta in (0, pi).  Covariances are packed lower triangles:
+ *    index(i, j) = i(i+1)/2 + j for i >= j (21 floats for the state, 6 for a hit
+ *    in the order xx, yx, yy, zx, zy, zz).
+ *  - Every call returns MKGB_OK (0) or a negative code; mkgb_last_error() gives
+ *    the message.  No call keeps a pointer it was given after it returns.
+ *  - The caller owns every array it passes.  `on_device` = 1: array arguments
+ *    are device pointers (e.g. torch CUDA tensors) and the call is asynchronous
+ *    on the context's stream; 0: host pointers, copied in and out, and the call
+ *    returns after its outputs are written.
+ *  - All state lives in the context (the paper's rule of no non-constant global
+ *    state, Sec. 3): contexts are independent; one context is not thread-safe.
+ */
+#ifndef MKGB_H
+#define MKGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MKGB_OK 0
+#define MKGB_EINVAL (-1)   /* bad argument or size */
+#define MKGB_ENOMEM (-2)   /* device allocation failed */
+#define MKGB_ECUDA (-3)    /* a CUDA call failed */
+#define MKGB_ESTATE (-5)   /* call out of order (no geometry, no hits, no seeds) */
+
+#define MKGB_BARREL 0
+#define MKGB_DISK 1
+
+#define MKGB_MAX_LAYERS 64
+#define MKGB_MAX_REGIONS 8
+#define MKGB_MAX_PLAN 48       /* layers in one layer plan */
+#define MKGB_MAX_CANDS 8       /* candidates kept per seed */
+
+/* hit codes per plan step in mkgb_tracks.hits */
+#define MKGB_HIT_MISS (-1)     /* layer crossed, no hit taken (a hole) */
+#define MKGB_HIT_SKIP (-2)     /* layer not crossed */
+#define MKGB_HIT_STOP (-3)     /* candidate had reached the hole limit */
+#define MKGB_HIT_PRE (-4)      /* plan step before the search (seed layers) or after the plan */
+
+typedef struct mkgb_ctx mkgb_ctx;
+
+/* A layer: an r-z bounding box in cylindrical space that aggregates hits (Sec. 3.1). */
+typedef struct {
+    int32_t kind;          /* MKGB_BARREL: cylinder of radius pos; MKGB_DISK: plane z = pos */
+    float pos;             /* radius or z [cm] */
+    float lo, hi;          /* barrel: z extent; disk: r extent [cm] */
+    float x_over_x0;       /* thickness at normal incidence in radiation lengths (Sec. 3.1 material) */
+    float sig_local[3];    /* hit resolution along (r-hat, phi-hat, z-hat) [cm], used for the window */
+    int32_t n_eta_bins;    /* eta-phi index of the layer's hits (Sec. 2.2: eta-phi sorting for coherency) */
+    int32_t n_phi_bins;
+    float eta_lo, eta_hi;  /* eta range covered by the bins (hits outside go to the edge bins) */
+} mkgb_layer;
+
+/* Search parameters (Sec. 3.2: maximum missed layers, chi2 cut, hit-search parameters). */
+typedef struct {
+    float chi2_cut;        /* accept a hit if its predicted chi2 < chi2_cut */
+    int32_t max_cands;     /* N: candidates kept per seed, 1..MKGB_MAX_CANDS */
+    int32_t max_holes;     /* missed layers allowed per candidate */
+    float win_nsigma;      /* window half-width = n_sigma * sigma(eta or phi) ... */
+    float deta_min, deta_max, dphi_min, dphi_max;   /* ... clamped to [min, max] */
+    float score_hit;       /* candidate score = score_hit * n_found - score_hole * n_holes - sum chi2 */
+    float score_hole;
+    float barrel_eta_max;  /* region choice with >1 plan: |eta_seed| < this -> plan 0, else 1 (eta>0) / 2 */
+    int32_t material;      /* 1: multiple scattering and energy loss at every crossed layer */
+} mkgb_params;
+
+/* Output of mkgb_build: caller-allocated arrays (device or host per on_device). */
+typedef struct {
+    float* params;         /* n_seeds x 6: best candidate's state at its last layer */
+    float* cov;            /* n_seeds x 21 */
+    float* chi2;           /* n_seeds: sum of chi2 of the hits added by the search */
+    float* score;          /* n_seeds: -inf if the seed failed */
+    int32_t* nfound;       /* n_seeds: hits including the 3 seed hits */
+    int32_t* nholes;       /* n_seeds */
+    int32_t* hits;         /* n_seeds x max_plan: global hit index or MKGB_HIT_* per plan step */
+    int32_t max_plan;      /* row stride of hits, >= the longest plan */
+} mkgb_tracks;
+
+/* Creates a context on `device` that launches on `stream` (a cudaStream_t; NULL = a stream
+ * the context creates).  Errors: MKGB_EINVAL (out == NULL), MKGB_ECUDA. */
+int mkgb_create(mkgb_ctx** out, int device, void* stream);
+void mkgb_destroy(mkgb_ctx* ctx);
+/* Message of the last failing call on this context (static text for a NULL context). */
+const char* mkgb_last_error(const mkgb_ctx* ctx);
+/* Version string of the library build. */
+const char* mkgb_version(void);
+
+/* Detector geometry and layer plans (Sec. 3.1: layers, layer plans per tracking region,
+ * material).  `plan` holds n_regions plans back to back, plan_off[r]..plan_off[r+1].
+ * Host arrays.  Errors: MKGB_EINVAL on sizes beyond the MKGB_MAX_* limits, bad kinds,
+ * plan entries out of range or empty extents. */
+int mkgb_load_geometry(mkgb_ctx* ctx, const mkgb_layer* layers, int n_layers,
+                       const int32_t* plan, const int32_t* plan_off, int n_regions, float bz_tesla);
+
+/* Iteration parameters (Sec. 3.2).  Host struct.  Errors: MKGB_EINVAL if max_cands is outside
+ * 1..MKGB_MAX_CANDS, max_holes < 0 or a window bound is negative. */
+int mkgb_set_params(mkgb_ctx* ctx, const mkgb_params* params);
+
+/* Hits of n_events events, grouped by (event, layer): segment e*n_layers + l holds hits
+ * seg_off[e*n_layers + l] .. seg_off[e*n_layers + l + 1] - 1 (host array, n_events*n_layers+1
+ * entries, non-decreasing, seg_off[0] = 0).  xyz: n x 3, cov6: n x 6 (n = seg_off[last]).
+ * The library builds each segment's eta-phi bin index (counting sort).  Hit indices used by
+ * mkgb_seed, mkgb_build and mkgb_fit are positions in these arrays.
+ * Errors: MKGB_ESTATE without geometry, MKGB_EINVAL on bad offsets, MKGB_ENOMEM. */
+int mkgb_load_hits(mkgb_ctx* ctx, int n_events, const int64_t* seg_off,
+                   const float* xyz, const float* cov6, int on_device);
+
+/* Seeds (Sec. 2.2): n_seeds x 3 hit indices on three consecutive crossed layers of one event,
+ * innermost first.  Computes each seed's state at its third hit (circle estimate + 3-hit
+ * Kalman fit), its region and first search step, and orders seeds by (event, eta, phi) for
+ * hit-access coherency.  Optional outputs (NULL to skip): state n x 6, cov n x 21, info n x 3
+ * (region, first plan step, status 0 = ok).  Errors: MKGB_ESTATE without hits, MKGB_EINVAL. */
+int mkgb_seed(mkgb_ctx* ctx, int n_seeds, const int32_t* seed_hits, int on_device,
+              float* state_out, float* cov_out, int32_t* info_out);
+
+/* Combinatorial forward search (Sec. 2.2) for the seeds of the last mkgb_seed call: along the
+ * seed's layer plan, every candidate is propagated, hits in its eta-phi window get a chi2, the
+ * N best children per seed are kept and updated; the best candidate is returned with its hit
+ * list.  Errors: MKGB_ESTATE without seeds or params, MKGB_EINVAL on a short max_plan. */
+int mkgb_build(mkgb_ctx* ctx, const mkgb_tracks* out, int on_device);
+
+/* Kalman fit over a known assignment (Sec. 4): n tracks, each from p0/c0 through up to
+ * max_steps layers (layers[i*max_steps + j], -1 ends the list) taking hits[i*max_steps + j]
+ * (-1: propagate only).  Outputs: p_out n x 6, c_out n x 21, chi2_out (sum of predicted chi2),
+ * status_out (0 ok, 1 a listed layer was not crossed, 2 particle stopped, 3 update failed,
+ * 4 hit index outside the loaded hits;
+ * NULL to skip).  Errors: MKGB_ESTATE without geometry/params, MKGB_EINVAL. */
+int mkgb_fit(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const int32_t* hits,
+             const float* p0, const float* c0, float* p_out, float* c_out, float* chi2_out,
+             int32_t* status_out, int on_device);
+
+/* Single propagation step (Sec. 3.1 propagation; a4-a7): n states to the given layers.
+ * crossed_out: 1 crossed, 0 not crossed (state copied through), -1 stopped. */
+int mkgb_propagate(mkgb_ctx* ctx, int n, const int32_t* layers, const float* p_in,
+                   const float* c_in, float* p_out, float* c_out, int32_t* crossed_out, int on_device);
+
+/* Single chi2 + Kalman update (a9, a11): n predicted states with one hit each (xyz n x 3,
+ * cov6 n x 6).  ok_out: 1 ok, 0 update rejected (S not positive definite or theta left (0, pi)). */
+int mkgb_update(mkgb_ctx* ctx, int n, const float* p_in, const float* c_in, const float* hit_xyz,
+                const float* hit_cov, float* p_out, float* c_out, float* chi2_out, int32_t* ok_out,
+                int on_device);
+
+/* Work counters of the last mkgb_build (kind 0) or mkgb_fit (kind 1), after the call's stream
+ * work has finished: [0] candidate-layer (build) or track-layer (fit) steps on crossed layers,
+ * [1] chi2 evaluations of hits inside windows, [2] Kalman updates, [3] hits tested against a
+ * window, [4] Newton iterations of the barrel crossing.  Synchronises the stream. */
+int mkgb_counters(mkgb_ctx* ctx, int kind, int64_t out[5]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

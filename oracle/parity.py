@@ -1,0 +1,115 @@
+"""Comparison of the CUDA path's outputs with the oracle's (test infrastructure).
+
+Tolerances (stated by the method's target): parameters |dp_i| <= 1e-4 * max(|p_i|, f_i) with
+floors f = (1, 1, 1, 0.01, 1, 1) (phi compared modulo 2 pi); covariance
+|dC_ij| <= 1e-3 * sqrt(C_ii C_jj); chi2 |d chi2| <= 1e-3 * max(1, chi2); selected hit indices
+bit-exact up to the first near-tie step the oracle flags for that seed.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import Oracle, hit_layers
+
+P_FLOOR = np.array([1.0, 1.0, 1.0, 0.01, 1.0, 1.0])
+TRI = np.tril_indices(6)
+
+
+def param_close(pg, po, rel=1e-4):
+    d = np.abs(np.asarray(pg, np.float64) - po)
+    d[..., 4] = np.abs(np.angle(np.exp(1j * (np.asarray(pg, np.float64)[..., 4] - po[..., 4]))))
+    tol = rel * np.maximum(np.abs(po), P_FLOOR)
+    return d <= tol, d / tol
+
+
+def cov_close(cg, co, rel=1e-3):
+    cg = np.asarray(cg, np.float64)
+    diag_idx = [i * (i + 1) // 2 + i for i in range(6)]
+    dg = np.abs(co[..., diag_idx])
+    scale = np.sqrt(dg[..., TRI[0]] * dg[..., TRI[1]])
+    d = np.abs(cg - co)
+    return d <= rel * scale + 1e-30, d / (rel * scale + 1e-30)
+
+
+def chi2_close(xg, xo, rel=1e-3):
+    d = np.abs(np.asarray(xg, np.float64) - xo)
+    tol = rel * np.maximum(1.0, np.abs(xo))
+    return d <= tol, d / tol
+
+
+def oracle_build(orc: Oracle, batch, seed_index=None, binned=True):
+    """Oracle forward search for the given seeds of a batch (all seeds by default), event by event."""
+    S = batch.seed_hits.shape[0]
+    idx = np.arange(S) if seed_index is None else np.asarray(seed_index)
+    L = batch.n_layers
+    xyz = batch.hit_xyz.astype(np.float64)
+    cov = batch.hit_cov.astype(np.float64)
+    mp = max(len(p) for p in orc.geom.plans)
+    res = None
+    for e in np.unique(batch.seed_event[idx]):
+        sel = idx[batch.seed_event[idx] == e]
+        lo = batch.hit_off[e * L:(e + 1) * L + 1]
+        sh = batch.seed_hits[sel]
+        r = orc.build_event(lo, xyz, cov, sh, hit_layers(lo, sh), binned=binned)
+        if res is None:
+            res = {k: (np.zeros((len(idx),) + v.shape[1:], v.dtype) if k != "counters" else np.zeros(4, np.int64))
+                   for k, v in r.items()}
+            pos = {s: i for i, s in enumerate(idx)}
+        rows = [pos[s] for s in sel]
+        for k, v in r.items():
+            if k == "counters":
+                res[k] += v
+            else:
+                res[k][rows] = v
+    res["seed_index"] = idx
+    res["max_plan"] = mp
+    return res
+
+
+def compare_build(gpu: dict, orc: dict):
+    """Per-seed comparison of build outputs.  gpu: numpy arrays over all seeds; orc: oracle_build
+    result for orc['seed_index'].  Returns a report dict; callers assert on it."""
+    idx = orc["seed_index"]
+    mp = orc["max_plan"]
+    gh = np.asarray(gpu["hits"])[idx, :mp]
+    oh = orc["hits"][:, :mp]
+    tie = orc["tie_step"]
+    n = len(idx)
+    hit_ok = np.ones(n, bool)
+    full = np.zeros(n, bool)
+    for i in range(n):
+        if tie[i] < 0:
+            hit_ok[i] = np.array_equal(gh[i], oh[i])
+            full[i] = True
+        else:
+            hit_ok[i] = np.array_equal(gh[i, :tie[i]], oh[i, :tie[i]])
+    ok_score = np.isfinite(orc["score"])
+    cmp = full & ok_score
+    pg = np.asarray(gpu["params"])[idx]
+    cg = np.asarray(gpu["cov"])[idx]
+    p_ok, p_ratio = param_close(pg[cmp], orc["params"][cmp])
+    c_ok, c_ratio = cov_close(cg[cmp], orc["cov"][cmp])
+    x_ok, x_ratio = chi2_close(np.asarray(gpu["chi2"])[idx][cmp], orc["chi2"][cmp])
+    same_int = (np.asarray(gpu["nfound"])[idx][cmp] == orc["nfound"][cmp]) & \
+               (np.asarray(gpu["nholes"])[idx][cmp] == orc["nholes"][cmp])
+    fail_gpu = ~np.isfinite(np.asarray(gpu["score"])[idx])
+    return dict(n=n, n_tie=int((tie >= 0).sum()), hit_mismatch=np.nonzero(~hit_ok)[0],
+                n_full=int(cmp.sum()), param_bad=int((~p_ok).any(1).sum()), cov_bad=int((~c_ok).any(1).sum()),
+                chi2_bad=int((~x_ok).sum()), count_bad=int((~same_int).sum()),
+                failed_mismatch=int((fail_gpu != ~ok_score).sum()),
+                worst_param=float(p_ratio.max()) if p_ratio.size else 0.0,
+                worst_cov=float(c_ratio.max()) if c_ratio.size else 0.0,
+                worst_chi2=float(x_ratio.max()) if x_ratio.size else 0.0)
+
+
+def compare_fit(gpu: dict, orc: dict, mask=None):
+    st_ok = np.asarray(gpu["status"]) == orc["status"]
+    m = (orc["status"] == 0) & st_ok if mask is None else mask & (orc["status"] == 0) & st_ok
+    p_ok, p_ratio = param_close(np.asarray(gpu["p"])[m], orc["p"][m])
+    c_ok, c_ratio = cov_close(np.asarray(gpu["c"])[m], orc["c"][m])
+    x_ok, x_ratio = chi2_close(np.asarray(gpu["chi2"])[m], orc["chi2"][m])
+    return dict(n=int(m.sum()), status_bad=int((~st_ok).sum()), param_bad=int((~p_ok).any(1).sum()),
+                cov_bad=int((~c_ok).any(1).sum()), chi2_bad=int((~x_ok).sum()),
+                worst_param=float(p_ratio.max()) if p_ratio.size else 0.0,
+                worst_cov=float(c_ratio.max()) if c_ratio.size else 0.0,
+                worst_chi2=float(x_ratio.max()) if x_ratio.size else 0.0)

@@ -1,0 +1,533 @@
+// C ABI of libmkgb.so: context, device buffers, host staging and kernel launches.
+// Declarations and argument contracts: include/mkgb.h.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace mk;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+cudaError_t ensure(DevBuf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.p && b.bytes >= bytes) return cudaSuccess;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e == cudaSuccess) b.bytes = bytes;
+    return e;
+}
+
+void release(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int d) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DevGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+enum Stage { S_A, S_B, S_C, S_D, S_E, S_F, S_G, S_H, S_I, S_COUNT };
+
+}  // namespace
+
+struct mkgb_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int n_sms = 0;
+    std::string err;
+    bool has_geom = false, has_params = false, has_hits = false, has_seeds = false;
+    DevGeom geom_h;
+    DevBuf geom_d;
+    int max_plan_len = 0;
+    DevParams params;
+    int n_events = 0, n_layers = 0;
+    int64_t n_hits = 0;
+    std::vector<int64_t> seg_off_h;
+    DevBuf seg_off, in_xyz, in_cov, pay, ep_tmp, bin_of_hit, hit_seg, bins, hb_ep, hb_pay, cursor, scan_tmp;
+    int n_seeds = 0;
+    DevBuf seed_hits, seed_state, seed_info, seed_key, key_counts, key_cursor, seed_order, seed_scan_tmp;
+    DevBuf counters_build, counters_fit, queue;
+    DevBuf stage[S_COUNT];
+};
+
+namespace {
+
+int fail(mkgb_ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? MKGB_ENOMEM : MKGB_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                       \
+    } while (0)
+
+HitStore hit_store(const mkgb_ctx* c) {
+    HitStore H;
+    H.seg_off = (const int64_t*)c->seg_off.p;
+    H.n_events = c->n_events;
+    H.n_layers = c->n_layers;
+    H.n_hits = c->n_hits;
+    H.pay = (const float4*)c->pay.p;
+    H.hb_ep = (const float2*)c->hb_ep.p;
+    H.hb_pay = (const float4*)c->hb_pay.p;
+    H.bin_start = (const int*)c->bins.p;
+    H.hit_seg = (const int*)c->hit_seg.p;
+    return H;
+}
+
+// Device view of an input array: the pointer itself (on_device) or a staged copy.
+cudaError_t stage_in(mkgb_ctx* c, Stage s, const void* src, size_t bytes, bool on_device, const void** out) {
+    if (on_device || src == nullptr) {
+        *out = src;
+        return cudaSuccess;
+    }
+    cudaError_t e = ensure(c->stage[s], bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(c->stage[s].p, src, bytes, cudaMemcpyHostToDevice, c->stream);
+    *out = c->stage[s].p;
+    return e;
+}
+
+cudaError_t stage_out(mkgb_ctx* c, Stage s, void* dst, size_t bytes, bool on_device, void** out) {
+    if (on_device || dst == nullptr) {
+        *out = dst;
+        return cudaSuccess;
+    }
+    cudaError_t e = ensure(c->stage[s], bytes);
+    *out = c->stage[s].p;
+    return e;
+}
+
+cudaError_t copy_back(mkgb_ctx* c, void* dst, const void* dev, size_t bytes, bool on_device) {
+    if (on_device || dst == nullptr || bytes == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst, dev, bytes, cudaMemcpyDeviceToHost, c->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mkgb_version(void) { return "mkgb 0.1 sm_103a"; }
+
+const char* mkgb_last_error(const mkgb_ctx* ctx) {
+    if (!ctx) return "null context";
+    return ctx->err.c_str();
+}
+
+int mkgb_create(mkgb_ctx** out, int device, void* stream) {
+    mkgb_ctx* ctx = nullptr;
+    if (!out) return MKGB_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return MKGB_ECUDA;
+    ctx = new mkgb_ctx();
+    ctx->device = device;
+    DevGuard guard(device);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete ctx;
+        return MKGB_ECUDA;
+    }
+    ctx->n_sms = prop.multiProcessorCount;
+    if (stream) {
+        ctx->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return MKGB_ECUDA;
+        }
+        ctx->own_stream = true;
+    }
+    if (ensure(ctx->counters_build, 8 * kNumCounters) != cudaSuccess ||
+        ensure(ctx->counters_fit, 8 * kNumCounters) != cudaSuccess || ensure(ctx->queue, 16) != cudaSuccess ||
+        ensure(ctx->geom_d, sizeof(DevGeom)) != cudaSuccess) {
+        mkgb_destroy(ctx);
+        return MKGB_ENOMEM;
+    }
+    cudaMemsetAsync(ctx->counters_build.p, 0, 8 * kNumCounters, ctx->stream);
+    cudaMemsetAsync(ctx->counters_fit.p, 0, 8 * kNumCounters, ctx->stream);
+    *out = ctx;
+    return MKGB_OK;
+}
+
+void mkgb_destroy(mkgb_ctx* ctx) {
+    if (!ctx) return;
+    {
+        DevGuard guard(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+        DevBuf* all[] = {&ctx->geom_d, &ctx->seg_off, &ctx->in_xyz, &ctx->in_cov, &ctx->pay, &ctx->ep_tmp,
+                         &ctx->bin_of_hit, &ctx->hit_seg, &ctx->bins, &ctx->hb_ep, &ctx->hb_pay, &ctx->cursor,
+                         &ctx->scan_tmp, &ctx->seed_hits, &ctx->seed_state, &ctx->seed_info, &ctx->seed_key,
+                         &ctx->key_counts, &ctx->key_cursor, &ctx->seed_order, &ctx->seed_scan_tmp,
+                         &ctx->counters_build, &ctx->counters_fit, &ctx->queue};
+        for (DevBuf* b : all) release(*b);
+        for (auto& b : ctx->stage) release(b);
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    }
+    delete ctx;
+}
+
+int mkgb_load_geometry(mkgb_ctx* ctx, const mkgb_layer* layers, int n_layers, const int32_t* plan,
+                       const int32_t* plan_off, int n_regions, float bz_tesla) {
+    if (!ctx) return MKGB_EINVAL;
+    if (!layers || !plan || !plan_off) return fail(ctx, MKGB_EINVAL, "null geometry array");
+    if (n_layers < 1 || n_layers > MKGB_MAX_LAYERS) return fail(ctx, MKGB_EINVAL, "n_layers %d outside 1..%d", n_layers, MKGB_MAX_LAYERS);
+    if (n_regions < 1 || n_regions > MKGB_MAX_REGIONS) return fail(ctx, MKGB_EINVAL, "n_regions %d outside 1..%d", n_regions, MKGB_MAX_REGIONS);
+    if (!(bz_tesla != 0.0f) || !(bz_tesla == bz_tesla)) return fail(ctx, MKGB_EINVAL, "bz must be non-zero");
+    DevGeom g;
+    memset(&g, 0, sizeof(g));
+    g.n_layers = n_layers;
+    g.n_regions = n_regions;
+    g.bz = bz_tesla;
+    g.cB = kCLight * bz_tesla;
+    int64_t bins = 0;
+    for (int l = 0; l < n_layers; ++l) {
+        const mkgb_layer& s = layers[l];
+        DevLayer& d = g.layers[l];
+        if (s.kind != MKGB_BARREL && s.kind != MKGB_DISK) return fail(ctx, MKGB_EINVAL, "layer %d: bad kind %d", l, s.kind);
+        if (!(s.hi > s.lo)) return fail(ctx, MKGB_EINVAL, "layer %d: empty extent", l);
+        if (s.kind == MKGB_BARREL && !(s.pos > 0.0f)) return fail(ctx, MKGB_EINVAL, "layer %d: radius must be > 0", l);
+        if (s.kind == MKGB_DISK && !(s.lo > 0.0f)) return fail(ctx, MKGB_EINVAL, "layer %d: disk rmin must be > 0", l);
+        if (s.n_eta_bins < 1 || s.n_phi_bins < 1 || s.n_eta_bins > 4096 || s.n_phi_bins > 4096)
+            return fail(ctx, MKGB_EINVAL, "layer %d: bin counts outside 1..4096", l);
+        if (!(s.eta_hi > s.eta_lo)) return fail(ctx, MKGB_EINVAL, "layer %d: empty eta range", l);
+        if (!(s.x_over_x0 >= 0.0f)) return fail(ctx, MKGB_EINVAL, "layer %d: negative material", l);
+        d.kind = s.kind;
+        d.pos = s.pos;
+        d.lo = s.lo;
+        d.hi = s.hi;
+        d.xx0 = s.x_over_x0;
+        for (int j = 0; j < 3; ++j) d.sig[j] = s.sig_local[j];
+        d.n_eta = s.n_eta_bins;
+        d.n_phi = s.n_phi_bins;
+        d.eta_lo = s.eta_lo;
+        d.eta_scale = (float)s.n_eta_bins / (s.eta_hi - s.eta_lo);
+        d.bin_base = (int)bins;
+        bins += (int64_t)s.n_eta_bins * s.n_phi_bins;
+    }
+    if (bins > (1 << 26)) return fail(ctx, MKGB_EINVAL, "too many bins per event (%lld)", (long long)bins);
+    g.bins_per_event = (int)bins;
+    if (plan_off[0] != 0) return fail(ctx, MKGB_EINVAL, "plan_off[0] must be 0");
+    int maxp = 0;
+    for (int r = 0; r < n_regions; ++r) {
+        const int len = plan_off[r + 1] - plan_off[r];
+        if (len < 1 || len > MKGB_MAX_PLAN) return fail(ctx, MKGB_EINVAL, "plan %d length %d outside 1..%d", r, len, MKGB_MAX_PLAN);
+        maxp = len > maxp ? len : maxp;
+    }
+    const int total = plan_off[n_regions];
+    if (total > MKGB_MAX_REGIONS * MKGB_MAX_PLAN) return fail(ctx, MKGB_EINVAL, "plans too long");
+    for (int r = 0; r <= n_regions; ++r) g.plan_off[r] = plan_off[r];
+    for (int q = 0; q < total; ++q) {
+        if (plan[q] < 0 || plan[q] >= n_layers) return fail(ctx, MKGB_EINVAL, "plan entry %d = %d out of range", q, plan[q]);
+        g.plan[q] = plan[q];
+    }
+    g.max_plan = maxp;
+    DevGuard guard(ctx->device);
+    ctx->geom_h = g;
+    CK(cudaMemcpyAsync(ctx->geom_d.p, &ctx->geom_h, sizeof(DevGeom), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->max_plan_len = maxp;
+    ctx->n_layers = n_layers;
+    ctx->has_geom = true;
+    ctx->has_hits = false;
+    ctx->has_seeds = false;
+    return MKGB_OK;
+}
+
+int mkgb_set_params(mkgb_ctx* ctx, const mkgb_params* p) {
+    if (!ctx) return MKGB_EINVAL;
+    if (!p) return fail(ctx, MKGB_EINVAL, "null params");
+    if (p->max_cands < 1 || p->max_cands > MKGB_MAX_CANDS) return fail(ctx, MKGB_EINVAL, "max_cands %d outside 1..%d", p->max_cands, MKGB_MAX_CANDS);
+    if (p->max_holes < 0) return fail(ctx, MKGB_EINVAL, "max_holes < 0");
+    if (!(p->deta_min >= 0.0f && p->dphi_min >= 0.0f && p->deta_max >= p->deta_min && p->dphi_max >= p->dphi_min))
+        return fail(ctx, MKGB_EINVAL, "bad window bounds");
+    if (!(p->dphi_max < 1.5f)) return fail(ctx, MKGB_EINVAL, "dphi_max must be < 1.5 rad");
+    if (!(p->win_nsigma >= 0.0f) || !(p->chi2_cut > 0.0f)) return fail(ctx, MKGB_EINVAL, "bad n_sigma or chi2_cut");
+    DevParams& d = ctx->params;
+    d.chi2_cut = p->chi2_cut;
+    d.max_cands = p->max_cands;
+    d.max_holes = p->max_holes;
+    d.material = p->material ? 1 : 0;
+    d.nsig = p->win_nsigma;
+    d.deta_min = p->deta_min;
+    d.deta_max = p->deta_max;
+    d.dphi_min = p->dphi_min;
+    d.dphi_max = p->dphi_max;
+    d.score_hit = p->score_hit;
+    d.score_hole = p->score_hole;
+    d.barrel_eta_max = p->barrel_eta_max;
+    ctx->has_params = true;
+    return MKGB_OK;
+}
+
+int mkgb_load_hits(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz, const float* cov6,
+                   int on_device) {
+    if (!ctx) return MKGB_EINVAL;
+    if (!ctx->has_geom) return fail(ctx, MKGB_ESTATE, "load_hits before load_geometry");
+    if (n_events < 1 || !seg_off) return fail(ctx, MKGB_EINVAL, "need n_events >= 1 and seg_off");
+    const int L = ctx->n_layers;
+    const int64_t nseg = (int64_t)n_events * L;
+    if (seg_off[0] != 0) return fail(ctx, MKGB_EINVAL, "seg_off[0] must be 0");
+    for (int64_t s = 0; s < nseg; ++s)
+        if (seg_off[s + 1] < seg_off[s]) return fail(ctx, MKGB_EINVAL, "seg_off decreases at %lld", (long long)s);
+    const int64_t n = seg_off[nseg];
+    if (n > ((int64_t)1 << 28) - 8) return fail(ctx, MKGB_EINVAL, "too many hits (%lld)", (long long)n);
+    if (n > 0 && (!xyz || !cov6)) return fail(ctx, MKGB_EINVAL, "null hit arrays");
+    const int64_t nbins = (int64_t)n_events * ctx->geom_h.bins_per_event;
+    if (nbins > ((int64_t)1 << 31) - 2) return fail(ctx, MKGB_EINVAL, "too many bins (%lld)", (long long)nbins);
+    DevGuard guard(ctx->device);
+    cudaStream_t st = ctx->stream;
+    CK(cudaStreamSynchronize(st));   // seg_off_h may still feed an earlier async copy
+    ctx->seg_off_h.assign(seg_off, seg_off + nseg + 1);
+    CK(ensure(ctx->seg_off, 8 * (nseg + 1)));
+    CK(cudaMemcpyAsync(ctx->seg_off.p, ctx->seg_off_h.data(), 8 * (nseg + 1), cudaMemcpyHostToDevice, st));
+    const float* dx = xyz;
+    const float* dc = cov6;
+    if (!on_device && n > 0) {
+        CK(ensure(ctx->in_xyz, 12 * n));
+        CK(ensure(ctx->in_cov, 24 * n));
+        CK(cudaMemcpyAsync(ctx->in_xyz.p, xyz, 12 * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ctx->in_cov.p, cov6, 24 * n, cudaMemcpyHostToDevice, st));
+        dx = (const float*)ctx->in_xyz.p;
+        dc = (const float*)ctx->in_cov.p;
+    }
+    CK(ensure(ctx->pay, 48 * n));
+    CK(ensure(ctx->ep_tmp, 8 * n));
+    CK(ensure(ctx->bin_of_hit, 4 * n));
+    CK(ensure(ctx->hit_seg, 4 * n));
+    CK(ensure(ctx->hb_ep, 8 * n));
+    CK(ensure(ctx->hb_pay, 48 * n));
+    CK(ensure(ctx->bins, 4 * (nbins + 1)));
+    CK(ensure(ctx->cursor, 4 * (nbins + 1)));
+    CK(ensure(ctx->scan_tmp, 4 * scan_tmp_ints(nbins + 1)));
+    CK(cudaMemsetAsync(ctx->bins.p, 0, 4 * (nbins + 1), st));
+    CK(launch_hit_prep(st, (const DevGeom*)ctx->geom_d.p, L, (const int64_t*)ctx->seg_off.p, (int)nseg, n, dx, dc,
+                       ctx->geom_h.bins_per_event, (float4*)ctx->pay.p, (float2*)ctx->ep_tmp.p,
+                       (int*)ctx->bin_of_hit.p, (int*)ctx->hit_seg.p, (int*)ctx->bins.p));
+    CK(exclusive_scan(st, (const int*)ctx->bins.p, (int*)ctx->bins.p, nbins, (int*)ctx->scan_tmp.p));
+    CK(cudaMemcpyAsync(ctx->cursor.p, ctx->bins.p, 4 * nbins, cudaMemcpyDeviceToDevice, st));
+    CK(launch_hit_scatter(st, n, (const float4*)ctx->pay.p, (const float2*)ctx->ep_tmp.p,
+                          (const int*)ctx->bin_of_hit.p, (int*)ctx->cursor.p, (float2*)ctx->hb_ep.p,
+                          (float4*)ctx->hb_pay.p));
+    if (!on_device) CK(cudaStreamSynchronize(st));
+    ctx->n_events = n_events;
+    ctx->n_hits = n;
+    ctx->has_hits = true;
+    ctx->has_seeds = false;
+    return MKGB_OK;
+}
+
+int mkgb_seed(mkgb_ctx* ctx, int n_seeds, const int32_t* seed_hits, int on_device, float* state_out,
+              float* cov_out, int32_t* info_out) {
+    if (!ctx) return MKGB_EINVAL;
+    if (!ctx->has_hits) return fail(ctx, MKGB_ESTATE, "seed before load_hits");
+    if (!ctx->has_params) return fail(ctx, MKGB_ESTATE, "seed before set_params");
+    if (n_seeds < 0 || (n_seeds > 0 && !seed_hits)) return fail(ctx, MKGB_EINVAL, "bad seeds");
+    if (n_seeds > 0 && ctx->n_hits == 0) return fail(ctx, MKGB_EINVAL, "seeds given but no hits loaded");
+    if ((state_out == nullptr) != (cov_out == nullptr)) return fail(ctx, MKGB_EINVAL, "state_out and cov_out go together");
+    DevGuard guard(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const int n = n_seeds;
+    const int64_t nkeys = (int64_t)ctx->n_events * kSeedEtaCells * kSeedPhiCells;
+    const void* sh = nullptr;
+    CK(stage_in(ctx, S_A, seed_hits, 12 * (size_t)n, on_device, &sh));
+    CK(ensure(ctx->seed_state, 4 * (size_t)kSeedStateStride * n));
+    CK(ensure(ctx->seed_info, 16 * (size_t)n));
+    CK(ensure(ctx->seed_key, 4 * (size_t)n));
+    CK(ensure(ctx->seed_order, 4 * (size_t)n));
+    CK(ensure(ctx->key_counts, 4 * (nkeys + 1)));
+    CK(ensure(ctx->key_cursor, 4 * (nkeys + 1)));
+    CK(ensure(ctx->seed_scan_tmp, 4 * scan_tmp_ints(nkeys + 1)));
+    void *s6 = nullptr, *c21 = nullptr, *i3 = nullptr;
+    CK(stage_out(ctx, S_B, state_out, 24 * (size_t)n, on_device, &s6));
+    CK(stage_out(ctx, S_C, cov_out, 84 * (size_t)n, on_device, &c21));
+    CK(stage_out(ctx, S_D, info_out, 12 * (size_t)n, on_device, &i3));
+    CK(cudaMemsetAsync(ctx->key_counts.p, 0, 4 * (nkeys + 1), st));
+    CK(launch_seed(st, (const DevGeom*)ctx->geom_d.p, ctx->params, hit_store(ctx), n, (const int*)sh,
+                   (float*)ctx->seed_state.p, (int4*)ctx->seed_info.p, (int*)ctx->seed_key.p,
+                   (int*)ctx->key_counts.p, (float*)s6, (float*)c21, (int*)i3));
+    CK(exclusive_scan(st, (const int*)ctx->key_counts.p, (int*)ctx->key_counts.p, nkeys, (int*)ctx->seed_scan_tmp.p));
+    CK(cudaMemcpyAsync(ctx->key_cursor.p, ctx->key_counts.p, 4 * nkeys, cudaMemcpyDeviceToDevice, st));
+    CK(launch_seed_scatter(st, n, (const int*)ctx->seed_key.p, (int*)ctx->key_cursor.p, (int*)ctx->seed_order.p));
+    CK(copy_back(ctx, state_out, s6, 24 * (size_t)n, on_device));
+    CK(copy_back(ctx, cov_out, c21, 84 * (size_t)n, on_device));
+    CK(copy_back(ctx, info_out, i3, 12 * (size_t)n, on_device));
+    if (!on_device) CK(cudaStreamSynchronize(st));
+    ctx->n_seeds = n;
+    ctx->has_seeds = true;
+    return MKGB_OK;
+}
+
+int mkgb_build(mkgb_ctx* ctx, const mkgb_tracks* out, int on_device) {
+    if (!ctx) return MKGB_EINVAL;
+    if (!ctx->has_seeds) return fail(ctx, MKGB_ESTATE, "build before seed");
+    if (!out || !out->params || !out->cov || !out->chi2 || !out->score || !out->nfound || !out->nholes || !out->hits)
+        return fail(ctx, MKGB_EINVAL, "null output array");
+    if (out->max_plan < ctx->max_plan_len) return fail(ctx, MKGB_EINVAL, "max_plan %d < longest plan %d", out->max_plan, ctx->max_plan_len);
+    DevGuard guard(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const size_t n = (size_t)ctx->n_seeds;
+    BuildOutDev d;
+    void* p;
+    CK(stage_out(ctx, S_A, out->params, 24 * n, on_device, &p)); d.params = (float*)p;
+    CK(stage_out(ctx, S_B, out->cov, 84 * n, on_device, &p)); d.cov = (float*)p;
+    CK(stage_out(ctx, S_C, out->chi2, 4 * n, on_device, &p)); d.chi2 = (float*)p;
+    CK(stage_out(ctx, S_D, out->score, 4 * n, on_device, &p)); d.score = (float*)p;
+    CK(stage_out(ctx, S_E, out->nfound, 4 * n, on_device, &p)); d.nfound = (int*)p;
+    CK(stage_out(ctx, S_F, out->nholes, 4 * n, on_device, &p)); d.nholes = (int*)p;
+    CK(stage_out(ctx, S_G, out->hits, 4 * n * out->max_plan, on_device, &p)); d.hits = (int*)p;
+    d.max_plan = out->max_plan;
+    SeedStore S{ctx->n_seeds, (const float*)ctx->seed_state.p, (const int4*)ctx->seed_info.p,
+                (const int*)ctx->seed_order.p};
+    CK(cudaMemsetAsync(ctx->queue.p, 0, 16, st));
+    CK(cudaMemsetAsync(ctx->counters_build.p, 0, 8 * kNumCounters, st));
+    CK(launch_build(st, (const DevGeom*)ctx->geom_d.p, ctx->max_plan_len, ctx->params, hit_store(ctx), S, d,
+                    (int*)ctx->queue.p, (unsigned long long*)ctx->counters_build.p, ctx->n_sms));
+    CK(copy_back(ctx, out->params, d.params, 24 * n, on_device));
+    CK(copy_back(ctx, out->cov, d.cov, 84 * n, on_device));
+    CK(copy_back(ctx, out->chi2, d.chi2, 4 * n, on_device));
+    CK(copy_back(ctx, out->score, d.score, 4 * n, on_device));
+    CK(copy_back(ctx, out->nfound, d.nfound, 4 * n, on_device));
+    CK(copy_back(ctx, out->nholes, d.nholes, 4 * n, on_device));
+    CK(copy_back(ctx, out->hits, d.hits, 4 * n * out->max_plan, on_device));
+    if (!on_device) CK(cudaStreamSynchronize(st));
+    return MKGB_OK;
+}
+
+int mkgb_fit(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const int32_t* hits, const float* p0,
+             const float* c0, float* p_out, float* c_out, float* chi2_out, int32_t* status_out, int on_device) {
+    if (!ctx) return MKGB_EINVAL;
+    if (!ctx->has_geom || !ctx->has_params) return fail(ctx, MKGB_ESTATE, "fit before geometry/params");
+    if (n < 0 || max_steps < 0) return fail(ctx, MKGB_EINVAL, "negative size");
+    if (n > 0 && (!layers || !hits || !p0 || !c0 || !p_out || !c_out || !chi2_out))
+        return fail(ctx, MKGB_EINVAL, "null fit array");
+    bool any_hit = false;
+    if (!on_device)
+        for (size_t q = 0; q < (size_t)n * max_steps && !any_hit; ++q) any_hit = hits[q] >= 0;
+    if ((on_device || any_hit) && !ctx->has_hits) return fail(ctx, MKGB_ESTATE, "fit with hits before load_hits");
+    if (!on_device)
+        for (size_t q = 0; q < (size_t)n * max_steps; ++q)
+            if (hits[q] >= ctx->n_hits) return fail(ctx, MKGB_EINVAL, "hit index %d out of range", hits[q]);
+    DevGuard guard(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const size_t N = (size_t)n, M = (size_t)max_steps;
+    const void *dl, *dh, *dp0, *dc0;
+    CK(stage_in(ctx, S_A, layers, 4 * N * M, on_device, &dl));
+    CK(stage_in(ctx, S_B, hits, 4 * N * M, on_device, &dh));
+    CK(stage_in(ctx, S_C, p0, 24 * N, on_device, &dp0));
+    CK(stage_in(ctx, S_D, c0, 84 * N, on_device, &dc0));
+    void *po, *co, *xo, *so;
+    CK(stage_out(ctx, S_E, p_out, 24 * N, on_device, &po));
+    CK(stage_out(ctx, S_F, c_out, 84 * N, on_device, &co));
+    CK(stage_out(ctx, S_G, chi2_out, 4 * N, on_device, &xo));
+    CK(stage_out(ctx, S_H, status_out, 4 * N, on_device, &so));
+    CK(cudaMemsetAsync(ctx->counters_fit.p, 0, 8 * kNumCounters, st));
+    CK(launch_fit(st, (const DevGeom*)ctx->geom_d.p, ctx->params, (const float4*)ctx->pay.p, ctx->has_hits ? ctx->n_hits : 0,
+                  n, max_steps,
+                  (const int*)dl, (const int*)dh, (const float*)dp0, (const float*)dc0, (float*)po, (float*)co,
+                  (float*)xo, (int*)so, (unsigned long long*)ctx->counters_fit.p));
+    CK(copy_back(ctx, p_out, po, 24 * N, on_device));
+    CK(copy_back(ctx, c_out, co, 84 * N, on_device));
+    CK(copy_back(ctx, chi2_out, xo, 4 * N, on_device));
+    CK(copy_back(ctx, status_out, so, 4 * N, on_device));
+    if (!on_device) CK(cudaStreamSynchronize(st));
+    return MKGB_OK;
+}
+
+int mkgb_propagate(mkgb_ctx* ctx, int n, const int32_t* layers, const float* p_in, const float* c_in, float* p_out,
+                   float* c_out, int32_t* crossed_out, int on_device) {
+    if (!ctx) return MKGB_EINVAL;
+    if (!ctx->has_geom || !ctx->has_params) return fail(ctx, MKGB_ESTATE, "propagate before geometry/params");
+    if (n < 0 || (n > 0 && (!layers || !p_in || !c_in || !p_out || !c_out || !crossed_out)))
+        return fail(ctx, MKGB_EINVAL, "bad propagate arguments");
+    DevGuard guard(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const size_t N = (size_t)n;
+    const void *dl, *dp, *dc;
+    CK(stage_in(ctx, S_A, layers, 4 * N, on_device, &dl));
+    CK(stage_in(ctx, S_B, p_in, 24 * N, on_device, &dp));
+    CK(stage_in(ctx, S_C, c_in, 84 * N, on_device, &dc));
+    void *po, *co, *xo;
+    CK(stage_out(ctx, S_D, p_out, 24 * N, on_device, &po));
+    CK(stage_out(ctx, S_E, c_out, 84 * N, on_device, &co));
+    CK(stage_out(ctx, S_F, crossed_out, 4 * N, on_device, &xo));
+    CK(launch_step_propagate(st, (const DevGeom*)ctx->geom_d.p, ctx->params, n, (const int*)dl, (const float*)dp,
+                             (const float*)dc, (float*)po, (float*)co, (int*)xo));
+    CK(copy_back(ctx, p_out, po, 24 * N, on_device));
+    CK(copy_back(ctx, c_out, co, 84 * N, on_device));
+    CK(copy_back(ctx, crossed_out, xo, 4 * N, on_device));
+    if (!on_device) CK(cudaStreamSynchronize(st));
+    return MKGB_OK;
+}
+
+int mkgb_update(mkgb_ctx* ctx, int n, const float* p_in, const float* c_in, const float* hit_xyz,
+                const float* hit_cov, float* p_out, float* c_out, float* chi2_out, int32_t* ok_out, int on_device) {
+    if (!ctx) return MKGB_EINVAL;
+    if (n < 0 || (n > 0 && (!p_in || !c_in || !hit_xyz || !hit_cov || !p_out || !c_out || !chi2_out || !ok_out)))
+        return fail(ctx, MKGB_EINVAL, "bad update arguments");
+    DevGuard guard(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const size_t N = (size_t)n;
+    const void *dp, *dc, *dx, *dv;
+    CK(stage_in(ctx, S_A, p_in, 24 * N, on_device, &dp));
+    CK(stage_in(ctx, S_B, c_in, 84 * N, on_device, &dc));
+    CK(stage_in(ctx, S_C, hit_xyz, 12 * N, on_device, &dx));
+    CK(stage_in(ctx, S_D, hit_cov, 24 * N, on_device, &dv));
+    void *po, *co, *xo, *ko;
+    CK(stage_out(ctx, S_E, p_out, 24 * N, on_device, &po));
+    CK(stage_out(ctx, S_F, c_out, 84 * N, on_device, &co));
+    CK(stage_out(ctx, S_G, chi2_out, 4 * N, on_device, &xo));
+    CK(stage_out(ctx, S_H, ok_out, 4 * N, on_device, &ko));
+    CK(launch_step_update(st, n, (const float*)dp, (const float*)dc, (const float*)dx, (const float*)dv, (float*)po,
+                          (float*)co, (float*)xo, (int*)ko));
+    CK(copy_back(ctx, p_out, po, 24 * N, on_device));
+    CK(copy_back(ctx, c_out, co, 84 * N, on_device));
+    CK(copy_back(ctx, chi2_out, xo, 4 * N, on_device));
+    CK(copy_back(ctx, ok_out, ko, 4 * N, on_device));
+    if (!on_device) CK(cudaStreamSynchronize(st));
+    return MKGB_OK;
+}
+
+int mkgb_counters(mkgb_ctx* ctx, int kind, int64_t out[5]) {
+    if (!ctx) return MKGB_EINVAL;
+    if (!out || (kind != 0 && kind != 1)) return fail(ctx, MKGB_EINVAL, "bad counters request");
+    DevGuard guard(ctx->device);
+    unsigned long long h[kNumCounters];
+    CK(cudaMemcpyAsync(h, kind == 0 ? ctx->counters_build.p : ctx->counters_fit.p, sizeof(h), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < kNumCounters; ++i) out[i] = (int64_t)h[i];
+    return MKGB_OK;
+}
+
+}  // extern "C"

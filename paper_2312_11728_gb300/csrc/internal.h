@@ -1,0 +1,81 @@
+// Internal interfaces between the C-ABI layer (api.cu) and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kalman.cuh"
+
+namespace mk {
+
+// Child kinds of a candidate at one layer (a10).
+enum : int { K_NONE = 0, K_HIT = 1, K_MISS = 2, K_SKIP = 3, K_STOP = 4, K_CARRY = 5 };
+
+constexpr int kSeedStateStride = 32;   // xh,yh,zh,xl,yl,zl,k,phi,th,c[21],pad,pad
+constexpr int kSeedEtaCells = 32;      // coarse eta-phi cells for the seed order (a3)
+constexpr int kSeedPhiCells = 64;
+
+// Hits after mkgb_load_hits: original order (payload) and the binned copy (a2).
+struct HitStore {
+    const int64_t* seg_off;    // E*L + 1 (device)
+    int n_events, n_layers;
+    int64_t n_hits;
+    const float4* pay;         // 3 float4 per hit, original order: (x,y,z,id) (v0..v3) (v4,v5,-,-)
+    const float2* hb_ep;       // binned order: (eta, phi)
+    const float4* hb_pay;      // binned order payload
+    const int* bin_start;      // E*bins_per_event + 1 offsets into the binned arrays
+    const int* hit_seg;        // per hit: segment e*L + l
+};
+
+struct SeedStore {
+    int n;
+    const float* state;        // n x kSeedStateStride
+    const int4* info;          // n: (region, first plan step, event, status)
+    const int* order;          // n: seeds sorted by (event, eta cell, phi cell)
+};
+
+struct BuildOutDev {
+    float* params;
+    float* cov;
+    float* chi2;
+    float* score;
+    int* nfound;
+    int* nholes;
+    int* hits;
+    int max_plan;
+};
+
+// counters (64-bit): [0] steps, [1] chi2 evaluations, [2] updates, [3] hits tested, [4] Newton iterations
+constexpr int kNumCounters = 5;
+
+// ---- k_hits.cu
+cudaError_t launch_hit_prep(cudaStream_t st, const DevGeom* g, int n_layers, const int64_t* seg_off, int n_seg,
+                            int64_t n_hits, const float* xyz, const float* cov, int bins_per_event,
+                            float4* pay, float2* ep_tmp, int* bin_of_hit, int* hit_seg, int* counts);
+cudaError_t launch_hit_scatter(cudaStream_t st, int64_t n_hits, const float4* pay, const float2* ep_tmp,
+                               const int* bin_of_hit, int* cursor, float2* hb_ep, float4* hb_pay);
+// Exclusive scan of n ints (out[n] gets the total); tmp must hold scan_tmp_ints(n) ints.
+size_t scan_tmp_ints(int64_t n);
+cudaError_t exclusive_scan(cudaStream_t st, const int* in, int* out, int64_t n, int* tmp);
+cudaError_t launch_seed_scatter(cudaStream_t st, int n, const int* key_of, int* cursor, int* order);
+
+// ---- k_seed.cu
+cudaError_t launch_seed(cudaStream_t st, const DevGeom* g, DevParams P, HitStore H, int n, const int* seed_hits,
+                        float* state, int4* info, int* key_of, int* key_counts, float* state6, float* cov21,
+                        int* info3);
+
+// ---- k_build.cu
+cudaError_t launch_build(cudaStream_t st, const DevGeom* g, int max_plan_len, DevParams P, HitStore H, SeedStore S,
+                         BuildOutDev out, int* queue, unsigned long long* counters, int n_sms);
+
+// ---- k_fit.cu
+cudaError_t launch_fit(cudaStream_t st, const DevGeom* g, DevParams P, const float4* pay, int64_t n_hits, int n,
+                       int max_steps,
+                       const int* layers, const int* hits, const float* p0, const float* c0, float* p_out,
+                       float* c_out, float* chi2_out, int* status_out, unsigned long long* counters);
+cudaError_t launch_step_propagate(cudaStream_t st, const DevGeom* g, DevParams P, int n, const int* layers,
+                                  const float* p_in, const float* c_in, float* p_out, float* c_out, int* crossed);
+cudaError_t launch_step_update(cudaStream_t st, int n, const float* p_in, const float* c_in, const float* hxyz,
+                               const float* hcov, float* p_out, float* c_out, float* chi2, int* ok);
+
+}  // namespace mk

@@ -1,0 +1,152 @@
+// Kalman fit over a known hit assignment (a12) and single-step kernels.
+//
+// Sec. 4: with faster building, the final fit becomes a comparably expensive step.  One
+// track per lane, the state stays in registers across all its layers; per step the lane
+// reads one 48-byte hit payload.  FP32-bound (a few hundred FMA per 52 bytes read).
+#include "internal.h"
+
+namespace mk {
+
+namespace {
+
+constexpr int kThreads = 128;
+
+__device__ __forceinline__ void load_geom(const DevGeom* __restrict__ gp, DevGeom& g) {
+    const int4* src = reinterpret_cast<const int4*>(gp);
+    int4* dst = reinterpret_cast<int4*>(&g);
+    for (int i = threadIdx.x; i < (int)(sizeof(DevGeom) / 16); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) k_fit(const DevGeom* __restrict__ gp, DevParams P,
+                                                  const float4* __restrict__ pay, int64_t n_hits, int n, int max_steps,
+                                                  const int* __restrict__ layers, const int* __restrict__ hits,
+                                                  const float* __restrict__ p0, const float* __restrict__ c0,
+                                                  float* __restrict__ p_out, float* __restrict__ c_out,
+                                                  float* __restrict__ chi2_out, int* __restrict__ status_out,
+                                                  unsigned long long* counters) {
+    __shared__ DevGeom g;
+    load_geom(gp, g);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long c_steps = 0, c_upd = 0;
+    int c_newton = 0;
+    if (i < n) {
+        State t;
+        load_state6(p0 + 6 * (int64_t)i, c0 + 21 * (int64_t)i, t);
+        float sum = 0.0f;
+        int status = 0;
+        const int* lrow = layers + (int64_t)i * max_steps;
+        const int* hrow = hits + (int64_t)i * max_steps;
+        for (int j = 0; j < max_steps; ++j) {
+            const int l = __ldg(lrow + j);
+            if (l < 0 || l >= g.n_layers) break;
+            const int r = propagate(g.layers[l], g.cB, P.material, t, c_newton);
+            if (r != 1) {
+                status = r == 0 ? 1 : 2;
+                break;
+            }
+            ++c_steps;
+            const int h = __ldg(hrow + j);
+            if (h >= n_hits) {
+                status = 4;   // hit index outside the loaded hits
+                break;
+            }
+            if (h >= 0) {
+                float m[3], v[6], x2;
+                load_hit(pay, h, m, v, nullptr);
+                if (!chi2_hit(t, m[0], m[1], m[2], v, x2) || !kalman_update(t, m[0], m[1], m[2], v)) {
+                    status = 3;
+                    break;
+                }
+                sum += x2;
+                ++c_upd;
+            }
+        }
+        store_state6(t, p_out + 6 * (int64_t)i, c_out + 21 * (int64_t)i);
+        chi2_out[i] = sum;
+        if (status_out) status_out[i] = status;
+    }
+    if (counters) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            c_steps += __shfl_xor_sync(0xffffffffu, c_steps, off);
+            c_upd += __shfl_xor_sync(0xffffffffu, c_upd, off);
+            c_newton += __shfl_xor_sync(0xffffffffu, c_newton, off);
+        }
+        if ((threadIdx.x & 31) == 0 && c_steps) {
+            atomicAdd(counters + 0, c_steps);
+            atomicAdd(counters + 1, c_upd);
+            atomicAdd(counters + 2, c_upd);
+            atomicAdd(counters + 4, (unsigned long long)c_newton);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_step_propagate(const DevGeom* __restrict__ gp, DevParams P, int n,
+                                                             const int* __restrict__ layers,
+                                                             const float* __restrict__ p_in,
+                                                             const float* __restrict__ c_in, float* p_out,
+                                                             float* c_out, int* crossed) {
+    __shared__ DevGeom g;
+    load_geom(gp, g);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    State t;
+    load_state6(p_in + 6 * (int64_t)i, c_in + 21 * (int64_t)i, t);
+    const int l = layers[i];
+    int it = 0;
+    int r = 0;
+    if (l >= 0 && l < g.n_layers) r = propagate(g.layers[l], g.cB, P.material, t, it);
+    store_state6(t, p_out + 6 * (int64_t)i, c_out + 21 * (int64_t)i);
+    crossed[i] = r;
+}
+
+__global__ void __launch_bounds__(kThreads) k_step_update(int n, const float* __restrict__ p_in,
+                                                          const float* __restrict__ c_in,
+                                                          const float* __restrict__ hxyz,
+                                                          const float* __restrict__ hcov, float* p_out,
+                                                          float* c_out, float* chi2, int* ok) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    State t;
+    load_state6(p_in + 6 * (int64_t)i, c_in + 21 * (int64_t)i, t);
+    float v[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) v[j] = hcov[6 * (int64_t)i + j];
+    const float mx = hxyz[3 * (int64_t)i], my = hxyz[3 * (int64_t)i + 1], mz = hxyz[3 * (int64_t)i + 2];
+    float x2 = 0.0f;
+    const bool good = chi2_hit(t, mx, my, mz, v, x2) && kalman_update(t, mx, my, mz, v);
+    store_state6(t, p_out + 6 * (int64_t)i, c_out + 21 * (int64_t)i);
+    chi2[i] = x2;
+    ok[i] = good ? 1 : 0;
+}
+
+}  // namespace
+
+cudaError_t launch_fit(cudaStream_t st, const DevGeom* g, DevParams P, const float4* pay, int64_t n_hits, int n,
+                       int max_steps,
+                       const int* layers, const int* hits, const float* p0, const float* c0, float* p_out,
+                       float* c_out, float* chi2_out, int* status_out, unsigned long long* counters) {
+    if (n == 0) return cudaSuccess;
+    k_fit<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p0, c0, p_out,
+                                                             c_out, chi2_out, status_out, counters);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_propagate(cudaStream_t st, const DevGeom* g, DevParams P, int n, const int* layers,
+                                  const float* p_in, const float* c_in, float* p_out, float* c_out, int* crossed) {
+    if (n == 0) return cudaSuccess;
+    k_step_propagate<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(g, P, n, layers, p_in, c_in, p_out, c_out,
+                                                                        crossed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_update(cudaStream_t st, int n, const float* p_in, const float* c_in, const float* hxyz,
+                               const float* hcov, float* p_out, float* c_out, float* chi2, int* ok) {
+    if (n == 0) return cudaSuccess;
+    k_step_update<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(n, p_in, c_in, hxyz, hcov, p_out, c_out, chi2,
+                                                                     ok);
+    return cudaGetLastError();
+}
+
+}  // namespace mk

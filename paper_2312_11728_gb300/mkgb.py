@@ -1,0 +1,231 @@
+"""Python binding of libmkgb.so (include/mkgb.h): argument marshalling only.
+
+Every step of the build and the fit runs in the library's CUDA kernels.  Arrays may be
+torch CUDA tensors (passed as device pointers, calls asynchronous on the context's
+stream) or numpy arrays (host pointers; the library copies them and returns after its
+outputs are written).  Loading fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmkgb.so")
+
+BARREL, DISK = 0, 1
+MAX_CANDS = 8
+HIT_MISS, HIT_SKIP, HIT_STOP, HIT_PRE = -1, -2, -3, -4
+ERRORS = {-1: "MKGB_EINVAL", -2: "MKGB_ENOMEM", -3: "MKGB_ECUDA", -5: "MKGB_ESTATE"}
+
+
+class Layer(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pos", C.c_float), ("lo", C.c_float), ("hi", C.c_float),
+                ("x_over_x0", C.c_float), ("sig_local", C.c_float * 3), ("n_eta_bins", C.c_int32),
+                ("n_phi_bins", C.c_int32), ("eta_lo", C.c_float), ("eta_hi", C.c_float)]
+
+
+class Params(C.Structure):
+    _fields_ = [("chi2_cut", C.c_float), ("max_cands", C.c_int32), ("max_holes", C.c_int32),
+                ("win_nsigma", C.c_float), ("deta_min", C.c_float), ("deta_max", C.c_float),
+                ("dphi_min", C.c_float), ("dphi_max", C.c_float), ("score_hit", C.c_float),
+                ("score_hole", C.c_float), ("barrel_eta_max", C.c_float), ("material", C.c_int32)]
+
+
+class Tracks(C.Structure):
+    _fields_ = [("params", C.c_void_p), ("cov", C.c_void_p), ("chi2", C.c_void_p), ("score", C.c_void_p),
+                ("nfound", C.c_void_p), ("nholes", C.c_void_p), ("hits", C.c_void_p), ("max_plan", C.c_int32)]
+
+
+EXPORTS = ["mkgb_create", "mkgb_destroy", "mkgb_last_error", "mkgb_version", "mkgb_load_geometry",
+           "mkgb_set_params", "mkgb_load_hits", "mkgb_seed", "mkgb_build", "mkgb_fit", "mkgb_propagate",
+           "mkgb_update", "mkgb_counters"]
+
+_lib = None
+
+
+class MkgbError(RuntimeError):
+    pass
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libmkgb.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise MkgbError(f"{path} not built: run `python -m paper_2312_11728_gb300.build` "
+                        "(or __graft_entry__.build()); there is no CPU fallback")
+    lib = C.CDLL(path)
+    vp, i32, f32 = C.c_void_p, C.c_int, C.c_float
+    lib.mkgb_create.argtypes = [C.POINTER(vp), i32, vp]
+    lib.mkgb_destroy.argtypes = [vp]
+    lib.mkgb_destroy.restype = None
+    lib.mkgb_last_error.argtypes = [vp]
+    lib.mkgb_last_error.restype = C.c_char_p
+    lib.mkgb_version.restype = C.c_char_p
+    lib.mkgb_load_geometry.argtypes = [vp, C.POINTER(Layer), i32, vp, vp, i32, f32]
+    lib.mkgb_set_params.argtypes = [vp, C.POINTER(Params)]
+    lib.mkgb_load_hits.argtypes = [vp, i32, vp, vp, vp, i32]
+    lib.mkgb_seed.argtypes = [vp, i32, vp, i32, vp, vp, vp]
+    lib.mkgb_build.argtypes = [vp, C.POINTER(Tracks), i32]
+    lib.mkgb_fit.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32]
+    lib.mkgb_propagate.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, i32]
+    lib.mkgb_update.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32]
+    lib.mkgb_counters.argtypes = [vp, i32, vp]
+    _lib = lib
+    return lib
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, dtype):
+    """(pointer, on_device) of an array argument; None -> (None, None)."""
+    if a is None:
+        return None, None
+    if _is_torch(a):
+        import torch
+        want = {np.float32: torch.float32, np.int32: torch.int32, np.int64: torch.int64}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise MkgbError(f"tensor must be contiguous {want}, got {a.dtype}")
+        return C.c_void_p(a.data_ptr()), a.is_cuda
+    if not (isinstance(a, np.ndarray) and a.dtype == dtype and a.flags.c_contiguous):
+        raise MkgbError(f"array must be a C-contiguous numpy {np.dtype(dtype).name} array")
+    return C.c_void_p(a.ctypes.data), False
+
+
+def _same(*flags):
+    fl = {f for f in flags if f is not None}
+    if len(fl) > 1:
+        raise MkgbError("mix of device tensors and host arrays in one call")
+    return int(fl.pop()) if fl else 0
+
+
+class Context:
+    """One mkgb context on a CUDA device, launching on a given stream (default: torch's current)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.lib = load_library()
+        h = C.c_void_p()
+        s = None
+        if stream is not None:
+            s = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        else:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    s = C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+            except ImportError:
+                pass
+        rc = self.lib.mkgb_create(C.byref(h), int(device), s)
+        if rc != 0:
+            raise MkgbError(f"mkgb_create failed ({ERRORS.get(rc, rc)})")
+        self.h = h
+        self.device = device
+        self.max_plan = 0
+        self.n_seeds = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mkgb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != 0:
+            msg = self.lib.mkgb_last_error(self.h).decode()
+            raise MkgbError(f"{what} failed ({ERRORS.get(rc, rc)}): {msg}")
+
+    # ---- setup
+    def load_geometry(self, geom):
+        L = geom.n_layers
+        arr = (Layer * L)()
+        for i in range(L):
+            arr[i] = Layer(int(geom.kind[i]), float(geom.pos[i]), float(geom.lo[i]), float(geom.hi[i]),
+                           float(geom.x_over_x0[i]), (C.c_float * 3)(*[float(v) for v in geom.sig[i]]),
+                           int(geom.n_eta[i]), int(geom.n_phi[i]), float(geom.eta_lo[i]), float(geom.eta_hi[i]))
+        plan, off = geom.plan_arrays()
+        self._check(self.lib.mkgb_load_geometry(self.h, arr, L, plan.ctypes.data, off.ctypes.data, len(geom.plans),
+                                                float(geom.bz)), "mkgb_load_geometry")
+        self.max_plan = geom.max_plan
+        self.barrel_eta_max = float(geom.barrel_eta_max)
+
+    def set_params(self, params: dict):
+        p = Params(float(params["chi2_cut"]), int(params["max_cands"]), int(params["max_holes"]),
+                   float(params["win_nsigma"]), float(params["deta_min"]), float(params["deta_max"]),
+                   float(params["dphi_min"]), float(params["dphi_max"]), float(params["score_hit"]),
+                   float(params["score_hole"]), float(params.get("barrel_eta_max", self.barrel_eta_max)),
+                   int(params["material"]))
+        self._check(self.lib.mkgb_set_params(self.h, C.byref(p)), "mkgb_set_params")
+
+    # ---- data
+    def load_hits(self, n_events, seg_off, xyz, cov):
+        so = np.ascontiguousarray(seg_off, np.int64)
+        px, dx = _ptr(xyz, np.float32)
+        pc, dc = _ptr(cov, np.float32)
+        self._check(self.lib.mkgb_load_hits(self.h, int(n_events), so.ctypes.data, px, pc, _same(dx, dc)),
+                    "mkgb_load_hits")
+
+    def seed(self, seed_hits, state=None, cov=None, info=None):
+        n = int(seed_hits.shape[0])
+        ps, d0 = _ptr(seed_hits, np.int32)
+        p1, d1 = _ptr(state, np.float32)
+        p2, d2 = _ptr(cov, np.float32)
+        p3, d3 = _ptr(info, np.int32)
+        self._check(self.lib.mkgb_seed(self.h, n, ps, _same(d0, d1, d2, d3), p1, p2, p3), "mkgb_seed")
+        self.n_seeds = n
+
+    def build(self, out: dict):
+        """out: dict of arrays params (n,6) cov (n,21) chi2 score nfound nholes hits (n, max_plan)."""
+        f, i = np.float32, np.int32
+        ptrs = [_ptr(out[k], t) for k, t in (("params", f), ("cov", f), ("chi2", f), ("score", f),
+                                              ("nfound", i), ("nholes", i), ("hits", i))]
+        t = Tracks(*[p for p, _ in ptrs], int(out["hits"].shape[1]))
+        self._check(self.lib.mkgb_build(self.h, C.byref(t), _same(*[d for _, d in ptrs])), "mkgb_build")
+        return out
+
+    def fit(self, layers, hits, p0, c0, p_out, c_out, chi2_out, status_out=None):
+        n, m = layers.shape
+        args = [_ptr(layers, np.int32), _ptr(hits, np.int32), _ptr(p0, np.float32), _ptr(c0, np.float32),
+                _ptr(p_out, np.float32), _ptr(c_out, np.float32), _ptr(chi2_out, np.float32),
+                _ptr(status_out, np.int32)]
+        self._check(self.lib.mkgb_fit(self.h, int(n), int(m), *[p for p, _ in args], _same(*[d for _, d in args])),
+                    "mkgb_fit")
+
+    def propagate(self, layers, p_in, c_in, p_out, c_out, crossed):
+        args = [_ptr(layers, np.int32), _ptr(p_in, np.float32), _ptr(c_in, np.float32), _ptr(p_out, np.float32),
+                _ptr(c_out, np.float32), _ptr(crossed, np.int32)]
+        self._check(self.lib.mkgb_propagate(self.h, int(layers.shape[0]), *[p for p, _ in args],
+                                            _same(*[d for _, d in args])), "mkgb_propagate")
+
+    def update(self, p_in, c_in, hxyz, hcov, p_out, c_out, chi2, ok):
+        args = [_ptr(p_in, np.float32), _ptr(c_in, np.float32), _ptr(hxyz, np.float32), _ptr(hcov, np.float32),
+                _ptr(p_out, np.float32), _ptr(c_out, np.float32), _ptr(chi2, np.float32), _ptr(ok, np.int32)]
+        self._check(self.lib.mkgb_update(self.h, int(p_in.shape[0]), *[p for p, _ in args],
+                                         _same(*[d for _, d in args])), "mkgb_update")
+
+    def counters(self, kind: int = 0):
+        out = np.zeros(5, np.int64)
+        self._check(self.lib.mkgb_counters(self.h, int(kind), out.ctypes.data), "mkgb_counters")
+        return out
+
+
+def alloc_tracks(n, max_plan, device=None):
+    """Output arrays of Context.build: numpy (device None) or torch CUDA tensors."""
+    shapes = dict(params=((n, 6), np.float32), cov=((n, 21), np.float32), chi2=((n,), np.float32),
+                  score=((n,), np.float32), nfound=((n,), np.int32), nholes=((n,), np.int32),
+                  hits=((n, max_plan), np.int32))
+    if device is None:
+        return {k: np.zeros(s, t) for k, (s, t) in shapes.items()}
+    import torch
+    tt = {np.float32: torch.float32, np.int32: torch.int32}
+    return {k: torch.zeros(s, dtype=tt[t], device=device) for k, (s, t) in shapes.items()}

@@ -1,0 +1,267 @@
+"""CUDA path vs the FP64 oracle, element by element on the same seeded inputs, through the C ABI.
+
+Tolerances: parameters 1e-4 relative (floors 1 cm / 1 rad and 0.01 c/GeV for q/pT), covariance
+1e-3 * sqrt(C_ii C_jj), chi2 1e-3 * max(1, chi2); selected hit indices bit-exact up to the first
+near-tie step the oracle flags (see oracle/parity.py)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import parity as PR
+from paper_2312_11728_gb300 import build as B
+from paper_2312_11728_gb300 import mkgb, pipeline, synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="session")
+def lib():
+    B.build()
+    return mkgb.load_library()
+
+
+def _ctx(geom, params):
+    return pipeline.make_context(geom, params)
+
+
+def _sym_rand_cov(rng, n, scales):
+    A = rng.standard_normal((n, 6, 6)) * np.asarray(scales)[None, :, None]
+    M = A @ A.transpose(0, 2, 1) / 6.0
+    return M[:, np.tril_indices(6)[0], np.tril_indices(6)[1]]
+
+
+# ------------------------------------------------------------------ single steps
+
+def test_step_propagation_matches_oracle(lib):
+    g = S.geometry_phase2()
+    params = S.default_params()
+    ctx = _ctx(g, params)
+    orc = oracle.Oracle(g, params)
+    rng = np.random.default_rng(1)
+    n = 4000
+    r = rng.uniform(0, 30, n)
+    a = rng.uniform(-np.pi, np.pi, n)
+    pt = np.exp(rng.uniform(np.log(0.5), np.log(50), n))
+    th = rng.uniform(0.1, np.pi - 0.1, n)
+    p = np.stack([r * np.cos(a), r * np.sin(a), rng.uniform(-40, 40, n), rng.choice([-1, 1], n) / pt,
+                  rng.uniform(-np.pi, np.pi, n), th], -1).astype(np.float32)
+    c = _sym_rand_cov(rng, n, [0.01, 0.01, 0.02, 0.05, 0.002, 0.002]).astype(np.float32)
+    layers = rng.integers(3, g.n_layers, n).astype(np.int32)
+    po, co, cr = np.zeros((n, 6), np.float32), np.zeros((n, 21), np.float32), np.zeros(n, np.int32)
+    ctx.propagate(layers, p, c, po, co, cr)
+    n_cmp = 0
+    for i in range(n):
+        pi, ci = p[i].astype(np.float64), c[i].astype(np.float64)
+        ok, s, margin = orc.path(int(layers[i]), pi)
+        rc, pp, cc, _ = orc.propagate(int(layers[i]), pi, ci)
+        if margin < 1e-4:
+            continue
+        assert cr[i] == rc, (i, cr[i], rc)
+        if rc == 1:
+            pok, _ = PR.param_close(po[i], pp)
+            cok, _ = PR.cov_close(co[i], cc)
+            assert pok.all(), (i, po[i], pp)
+            assert cok.all(), (i, co[i], cc)
+            n_cmp += 1
+    assert n_cmp > 800
+
+
+def test_step_update_matches_oracle(lib):
+    g = S.geometry_barrel()
+    params = S.default_params()
+    ctx = _ctx(g, params)
+    orc = oracle.Oracle(g, params)
+    rng = np.random.default_rng(2)
+    n = 3000
+    p = np.stack([rng.uniform(-100, 100, n), rng.uniform(-100, 100, n), rng.uniform(-250, 250, n),
+                  rng.uniform(-2, 2, n), rng.uniform(-np.pi, np.pi, n), rng.uniform(0.2, 2.9, n)], -1)
+    c = _sym_rand_cov(rng, n, [0.005, 0.005, 0.01, 0.02, 0.001, 0.001])
+    V = _sym_rand_cov(rng, n, [0.003, 0.003, 0.01, 0, 0, 0])[:, :6]
+    m = p[:, :3] + rng.standard_normal((n, 3)) * 0.004
+    p, c, V, m = p.astype(np.float32), c.astype(np.float32), V.astype(np.float32), m.astype(np.float32)
+    po, co, x2, ok = np.zeros((n, 6), np.float32), np.zeros((n, 21), np.float32), np.zeros(n, np.float32), np.zeros(n, np.int32)
+    ctx.update(p, c, m, V, po, co, x2, ok)
+    for i in range(n):
+        okr, pp, cc, xr = orc.update(p[i].astype(np.float64), c[i].astype(np.float64),
+                                     m[i].astype(np.float64), V[i].astype(np.float64))
+        assert ok[i] == int(okr)
+        if okr:
+            assert PR.chi2_close(x2[i], xr)[0], (i, x2[i], xr)
+            assert PR.param_close(po[i], pp)[0].all(), (i, po[i], pp)
+            assert PR.cov_close(co[i], cc)[0].all(), (i, co[i], cc)
+
+
+# ------------------------------------------------------------------ seeds, fit, build
+
+@pytest.fixture(scope="module")
+def small_barrel():
+    g, ev = S.workload_small_barrel()
+    batch = S.concat_events([ev], g.n_layers)
+    params = S.default_params()
+    return g, batch, params
+
+
+@pytest.fixture(scope="module")
+def phase2_small():
+    g = S.geometry_phase2()
+    evs = [S.simulate_event(g, 1501, 0, e, pt_sampler=S.sample_pt_phase2, eta_max=3.0, noise_total=4000)
+           for e in range(3)]
+    batch = S.concat_events(evs, g.n_layers)
+    return g, batch, S.default_params()
+
+
+@pytest.mark.parametrize("which", ["small_barrel", "phase2_small"])
+def test_seed_states_match_oracle(lib, which, request):
+    g, batch, params = request.getfixturevalue(which)
+    ctx = _ctx(g, params)
+    res = pipeline.run_host(ctx, batch, g.max_plan)
+    orc = oracle.Oracle(g, params)
+    lo = batch.hit_off
+    sl = np.concatenate([oracle.hit_layers(lo[e * g.n_layers:(e + 1) * g.n_layers + 1],
+                                           batch.seed_hits[batch.seed_event == e]) for e in range(batch.n_events)])
+    r = orc.seed_batch(batch.seed_hits, sl, batch.hit_xyz.astype(np.float64), batch.hit_cov.astype(np.float64))
+    info = res["seed_info"]
+    assert np.array_equal(info[:, 0], r["region"])
+    assert np.array_equal(info[:, 1], r["start"])
+    assert np.array_equal(info[:, 2], r["status"])
+    ok = r["status"] == 0
+    pok, prat = PR.param_close(res["seed_state"][ok], r["p"][ok])
+    cok, crat = PR.cov_close(res["seed_cov"][ok], r["c"][ok])
+    assert pok.all(), prat.max()
+    assert cok.all(), crat.max()
+
+
+@pytest.mark.parametrize("which", ["small_barrel", "phase2_small"])
+def test_fit_over_known_assignment_matches_oracle(lib, which, request):
+    g, batch, params = request.getfixturevalue(which)
+    ctx = _ctx(g, params)
+    fi = pipeline.fit_inputs(batch)
+    res = pipeline.run_host(ctx, batch, g.max_plan, fi)
+    orc = oracle.Oracle(g, params)
+    r = orc.fit_batch(fi.layers, fi.hits, batch.hit_xyz.astype(np.float64), batch.hit_cov.astype(np.float64),
+                      fi.p0.astype(np.float64), fi.c0.astype(np.float64))
+    rep = PR.compare_fit(res["fit"], r)
+    assert rep["status_bad"] == 0, rep
+    assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0, rep
+    assert rep["n"] > 0.95 * fi.layers.shape[0]
+    c = res["fit"]["counters"]
+    assert c[0] == r["counters"][0] and c[2] == r["counters"][2]
+
+
+@pytest.mark.parametrize("which", ["small_barrel", "phase2_small"])
+def test_build_matches_oracle(lib, which, request):
+    g, batch, params = request.getfixturevalue(which)
+    ctx = _ctx(g, params)
+    res = pipeline.run_host(ctx, batch, g.max_plan)
+    orc = oracle.Oracle(g, params)
+    o = PR.oracle_build(orc, batch)
+    rep = PR.compare_build(res["build"], o)
+    assert len(rep["hit_mismatch"]) == 0, rep
+    assert rep["failed_mismatch"] == 0, rep
+    assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0 and rep["count_bad"] == 0, rep
+    assert rep["n_tie"] < 0.03 * rep["n"], rep
+    # work counters agree up to the near-tie seeds
+    gc, oc = res["build_counters"], o["counters"]
+    for k in range(3):
+        assert abs(gc[k] - oc[k]) <= 0.02 * oc[k] + 10, (k, gc, oc)
+
+
+def test_device_and_host_paths_agree_and_are_deterministic(lib, phase2_small):
+    import torch
+    g, batch, params = phase2_small
+    ctx = _ctx(g, params)
+    fi = pipeline.fit_inputs(batch)
+    host = pipeline.run_host(ctx, batch, g.max_plan, fi)
+    db = pipeline.DeviceBatch(batch, fi, g.max_plan, "cuda")
+    outs = []
+    for _ in range(2):
+        pipeline.run_step(ctx, db)
+        torch.cuda.synchronize()
+        outs.append({k: v.cpu().numpy().copy() for k, v in db.out.items()})
+    for k in outs[0]:
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+        assert np.array_equal(outs[0][k], host["build"][k]), k
+    assert np.array_equal(db.fit["p"].cpu().numpy(), host["fit"]["p"])
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_edge_cases_empty_single_and_ragged(lib):
+    g = S.geometry_barrel()
+    params = S.default_params()
+    ctx = _ctx(g, params)
+    ev = S.simulate_event(g, 5, 4, 0, eta_max=1.0, noise_per_layer=0)
+    batch = S.concat_events([ev], g.n_layers)
+    # zero seeds
+    ctx.load_hits(1, batch.hit_off, batch.hit_xyz, batch.hit_cov)
+    ctx.seed(np.zeros((0, 3), np.int32))
+    out = ctx.build(mkgb.alloc_tracks(0, g.max_plan))
+    assert out["hits"].shape == (0, g.max_plan)
+    # one seed, and an invalid one (index out of range -> status 1, score -inf)
+    sh = np.concatenate([batch.seed_hits[:1], np.array([[0, 1, 10 ** 6]], np.int32)])
+    info = np.zeros((2, 3), np.int32)
+    ctx.seed(sh, np.zeros((2, 6), np.float32), np.zeros((2, 21), np.float32), info)
+    out = ctx.build(mkgb.alloc_tracks(2, g.max_plan))
+    assert info[0, 2] == 0 and info[1, 2] == 1
+    assert np.isfinite(out["score"][0]) and out["score"][1] == -np.inf
+    assert np.all(out["hits"][1] == mkgb.HIT_PRE)
+    # empty layers: an event with hits on only the first three layers
+    keep = batch.hit_off[3]
+    off = np.concatenate([batch.hit_off[:4], np.full(g.n_layers - 3, keep)]).astype(np.int64)
+    ctx.load_hits(1, off, batch.hit_xyz[:keep], batch.hit_cov[:keep])
+    ctx.seed(batch.seed_hits)
+    out = ctx.build(mkgb.alloc_tracks(batch.seed_hits.shape[0], g.max_plan))
+    assert np.all(out["hits"][:, 3:] < 0)
+    # bad arguments are errors, not faults
+    with pytest.raises(mkgb.MkgbError):
+        ctx.build(mkgb.alloc_tracks(batch.seed_hits.shape[0], 3))
+    with pytest.raises(mkgb.MkgbError):
+        ctx.set_params(dict(params, max_cands=9))
+    with pytest.raises(mkgb.MkgbError):
+        ctx.load_hits(1, np.array([0, 5, 3] + [3] * (g.n_layers - 2), np.int64), batch.hit_xyz, batch.hit_cov)
+
+
+@pytest.mark.parametrize("n_cands", [1, 8])
+def test_candidate_limits_match_oracle(lib, small_barrel, n_cands):
+    g, batch, params = small_barrel
+    params = dict(params, max_cands=n_cands)
+    ctx = _ctx(g, params)
+    res = pipeline.run_host(ctx, batch, g.max_plan)
+    o = PR.oracle_build(oracle.Oracle(g, params), batch)
+    rep = PR.compare_build(res["build"], o)
+    assert len(rep["hit_mismatch"]) == 0 and rep["param_bad"] == 0 and rep["chi2_bad"] == 0, rep
+
+
+# ------------------------------------------------------------------ full-size workload, sampled
+
+@pytest.fixture(scope="module")
+def phase2_full():
+    g, evs = S.workload_phase2()
+    return g, S.concat_events(evs, g.n_layers), S.default_params()
+
+
+def test_full_size_phase2_sampled_against_oracle(lib, phase2_full):
+    """64 events x 20,000 tracks, in the launch configuration the benchmark times; the oracle
+    recomputes a random sample of seeds (searches are independent per seed)."""
+    import torch
+    g, batch, params = phase2_full
+    ctx = _ctx(g, params)
+    fi = pipeline.fit_inputs(batch)
+    db = pipeline.DeviceBatch(batch, fi, g.max_plan, "cuda")
+    pipeline.run_step(ctx, db)
+    torch.cuda.synchronize()
+    gpu = {k: v.cpu().numpy() for k, v in db.out.items()}
+    rng = np.random.default_rng(7)
+    sample = np.sort(rng.choice(batch.seed_hits.shape[0], 400, replace=False))
+    orc = oracle.Oracle(g, params)
+    o = PR.oracle_build(orc, batch, sample)
+    rep = PR.compare_build(gpu, o)
+    assert len(rep["hit_mismatch"]) == 0, rep
+    assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0, rep
+    tsample = np.sort(rng.choice(fi.layers.shape[0], 2000, replace=False))
+    r = orc.fit_batch(fi.layers[tsample], fi.hits[tsample], batch.hit_xyz.astype(np.float64),
+                      batch.hit_cov.astype(np.float64), fi.p0[tsample].astype(np.float64),
+                      fi.c0[tsample].astype(np.float64))
+    gf = {k: db.fit[k].cpu().numpy()[tsample] for k in ("p", "c", "chi2", "status")}
+    rep = PR.compare_fit(gf, r)
+    assert rep["status_bad"] == 0 and rep["param_bad"] == 0 and rep["chi2_bad"] == 0, rep
