@@ -98,6 +98,21 @@ int orc_path(const orc_geom* g, int layer, const double p[6], double* s_out, dou
         if (fabs(ct) < 1e-15) { *edge_margin = margin; return 0; }
         s = (L->pos - p[2]) * st / ct;
         if (!(s > 0)) { *edge_margin = margin; return 0; }
+        /* loopers are followed on the outgoing part of their current turn only: the disk must
+           be reached before the next point of largest radius, moving outward in r */
+        if (fabs(om) >= 1e-14) {
+            double sf = sin(p[4]), cf = cos(p[4]);
+            double cx = p[0] - sf / om, cy = p[1] + cf / om, d = hypot(cx, cy);
+            double sg = om > 0 ? 1.0 : -1.0;
+            double turn = fmod((atan2(sg * cx / d, -sg * cy / d) - p[4]) * sg, TWO_PI);
+            if (turn < 0) turn += TWO_PI;
+            double s_far = turn / fabs(om);
+            double q[6];
+            orc_helix(g->bz, p, s, q);
+            double vr = (q[0] * cos(q[4]) + q[1] * sin(q[4])) / fmax(hypot(q[0], q[1]), 1e-300);
+            margin = fmin(fabs(s - s_far) / s_far, fabs(vr));
+            if (s > s_far || vr < 0) { *edge_margin = margin; return 0; }
+        }
     } else {
         double R = L->pos, x = p[0], y = p[1], cf = cos(p[4]), sf = sin(p[4]);
         if (x * x + y * y >= R * R) { *edge_margin = margin; return 0; }

@@ -23,9 +23,14 @@ def param_close(pg, po, rel=1e-4):
 
 
 def cov_close(cg, co, rel=1e-3):
+    """|dC_ij| <= rel * sqrt(d_i d_j).  d_i = C_ii, floored at 1e-12 of the largest variance of
+    its block (position or not): a state on a disk has exactly zero z variance, where the
+    oracle holds FP64 rounding noise of ~1e-16 of the position variances."""
     cg = np.asarray(cg, np.float64)
     diag_idx = [i * (i + 1) // 2 + i for i in range(6)]
     dg = np.abs(co[..., diag_idx])
+    pos_max = dg[..., :3].max(axis=-1, keepdims=True)
+    dg = np.concatenate([np.maximum(dg[..., :3], 1e-12 * pos_max), dg[..., 3:]], axis=-1)
     scale = np.sqrt(dg[..., TRI[0]] * dg[..., TRI[1]])
     d = np.abs(cg - co)
     return d <= rel * scale + 1e-30, d / (rel * scale + 1e-30)

@@ -110,12 +110,13 @@ __global__ void __launch_bounds__(kThreads) k_build(BuildArgs a) {
             int nh_kind = K_NONE;
             float nh_score = -kBig;
             bool crossed = false;
+            Pred q;
             if (gact && alive) {
                 if (stopped) {
                     nh_kind = K_CARRY;
                     nh_score = score;
                 } else {
-                    const int r = propagate(L, g.cB, P.material, t, c_newton);
+                    const int r = propagate(L, g.cB, P.material, t, q, c_newton);
                     if (r < 0) {
                         alive = false;
                     } else if (r == 0) {
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(kThreads) k_build(BuildArgs a) {
                 lq[j] = 0;
             }
             if (crossed) {
-                const Window w = window(L, P, t);
+                const Window w = window(L, P, q);
                 const float eps = 1e-5f;
                 const float fe0 = (w.eta - w.deta - eps - L.eta_lo) * L.eta_scale;
                 const float fe1 = (w.eta + w.deta + eps - L.eta_lo) * L.eta_scale;
@@ -171,17 +172,17 @@ __global__ void __launch_bounds__(kThreads) k_build(BuildArgs a) {
                         if (nb <= 0) continue;
                         const int q0 = __ldg(a.H.bin_start + rowb + b0);
                         const int q1 = __ldg(a.H.bin_start + rowb + b0 + nb);
-                        for (int q = q0; q < q1; ++q) {
+                        for (int hq = q0; hq < q1; ++hq) {
                             ++c_tested;
-                            const float2 ep = __ldg(a.H.hb_ep + q);
+                            const float2 ep = __ldg(a.H.hb_ep + hq);
                             if (fabsf(ep.x - w.eta) <= w.deta && fabsf(wrap_pi(ep.y - w.phi)) <= w.dphi) {
                                 ++c_chi2;
                                 float m[3], v[6];
                                 int id;
-                                load_hit(a.H.hb_pay, q, m, v, &id);
+                                load_hit(a.H.hb_pay, hq, m, v, &id);
                                 float x2;
-                                if (chi2_hit(t, m[0], m[1], m[2], v, x2) && x2 < P.chi2_cut) {
-                                    int qq = q;
+                                if (chi2_hit(L.kind, q, m[0], m[1], m[2], v, x2) && x2 < P.chi2_cut) {
+                                    int qq = hq;
 #pragma unroll
                                     for (int j = 0; j < kGroup; ++j) {
                                         const bool better = x2 < lx[j] || (x2 == lx[j] && id < lid[j]);
@@ -257,20 +258,24 @@ __global__ void __launch_bounds__(kThreads) k_build(BuildArgs a) {
             }
 
             // ---- 4. pull the parent's state and update (a11); 5. trail
-            const int psrc = gbase + (my_parent >= 0 ? my_parent : slot);
-            State np;
-            np.xh = shfl_f(t.xh, psrc); np.yh = shfl_f(t.yh, psrc); np.zh = shfl_f(t.zh, psrc);
-            np.xl = shfl_f(t.xl, psrc); np.yl = shfl_f(t.yl, psrc); np.zl = shfl_f(t.zl, psrc);
-            np.k = shfl_f(t.k, psrc); np.phi = shfl_f(t.phi, psrc); np.th = shfl_f(t.th, psrc);
+            // Payload of a lane: its predicted state (surface frame) if it crossed, else its state.
+            float R[30];
+            R[0] = crossed ? q.xh : t.xh; R[1] = crossed ? q.yh : t.yh; R[2] = crossed ? q.zh : t.zh;
+            R[3] = crossed ? q.xl : t.xl; R[4] = crossed ? q.yl : t.yl; R[5] = crossed ? q.zl : t.zl;
+            R[6] = crossed ? q.k : t.k; R[7] = crossed ? q.phi : t.phi; R[8] = crossed ? q.th : t.th;
 #pragma unroll
-            for (int q = 0; q < 21; ++q) np.c[q] = shfl_f(t.c[q], psrc);
+            for (int i = 0; i < 15; ++i) R[9 + i] = crossed ? q.c[i] : t.c[i];
+#pragma unroll
+            for (int i = 15; i < 21; ++i) R[9 + i] = t.c[i];
+            const int psrc = gbase + (my_parent >= 0 ? my_parent : slot);
+#pragma unroll
+            for (int i = 0; i < 30; ++i) R[i] = shfl_f(R[i], psrc);
             const float p_chi2 = shfl_f(chi2s, psrc);
             const int p_nfound = shfl_i(nfound, psrc);
             const int p_nholes = shfl_i(nholes, psrc);
             const int p_stopped = shfl_i((int)stopped, psrc);
             if (gact) {
                 if (my_kind != K_NONE) {
-                    t = np;
                     chi2s = p_chi2;
                     nfound = p_nfound;
                     nholes = p_nholes;
@@ -278,24 +283,38 @@ __global__ void __launch_bounds__(kThreads) k_build(BuildArgs a) {
                     score = my_score;
                     alive = true;
                     int code = MKGB_HIT_STOP;
-                    if (my_kind == K_HIT) {
-                        float m[3], v[6];
-                        load_hit(a.H.hb_pay, my_q, m, v, nullptr);
-                        if (kalman_update(t, m[0], m[1], m[2], v)) {
-                            chi2s += my_x2;
-                            ++nfound;
-                            ++c_upd;
-                            code = my_id;
+                    if (my_kind == K_SKIP || my_kind == K_CARRY) {
+                        t.xh = R[0]; t.yh = R[1]; t.zh = R[2]; t.xl = R[3]; t.yl = R[4]; t.zl = R[5];
+                        t.k = R[6]; t.phi = R[7]; t.th = R[8];
+#pragma unroll
+                        for (int i = 0; i < 21; ++i) t.c[i] = R[9 + i];
+                        if (my_kind == K_SKIP) code = MKGB_HIT_SKIP;
+                    } else {
+                        Pred pq;
+                        pq.xh = R[0]; pq.yh = R[1]; pq.zh = R[2]; pq.xl = R[3]; pq.yl = R[4]; pq.zl = R[5];
+                        pq.k = R[6]; pq.phi = R[7]; pq.th = R[8];
+#pragma unroll
+                        for (int i = 0; i < 15; ++i) pq.c[i] = R[9 + i];
+                        if (my_kind == K_HIT) {
+                            float m[3], v[6];
+                            load_hit(a.H.hb_pay, my_q, m, v, nullptr);
+                            if (kalman_update(L.kind, pq, m[0], m[1], m[2], v, t)) {
+                                chi2s += my_x2;
+                                ++nfound;
+                                ++c_upd;
+                                code = my_id;
+                            } else {
+                                alive = false;
+                            }
                         } else {
-                            alive = false;
+                            pred_to_state(L.kind, pq, t);
+                            if (my_kind == K_MISS) {
+                                ++nholes;
+                                code = MKGB_HIT_MISS;
+                            } else {   // K_STOP
+                                stopped = true;
+                            }
                         }
-                    } else if (my_kind == K_MISS) {
-                        ++nholes;
-                        code = MKGB_HIT_MISS;
-                    } else if (my_kind == K_STOP) {
-                        stopped = true;
-                    } else if (my_kind == K_SKIP) {
-                        code = MKGB_HIT_SKIP;
                     }
                     trail[tau * kGroup + slot] = ((code + 4) << 3) | my_parent;
                 } else {

@@ -40,7 +40,9 @@ __global__ void __launch_bounds__(kThreads) k_fit(const DevGeom* __restrict__ gp
         for (int j = 0; j < max_steps; ++j) {
             const int l = __ldg(lrow + j);
             if (l < 0 || l >= g.n_layers) break;
-            const int r = propagate(g.layers[l], g.cB, P.material, t, c_newton);
+            const DevLayer& L = g.layers[l];
+            Pred q;
+            const int r = propagate(L, g.cB, P.material, t, q, c_newton);
             if (r != 1) {
                 status = r == 0 ? 1 : 2;
                 break;
@@ -49,17 +51,20 @@ __global__ void __launch_bounds__(kThreads) k_fit(const DevGeom* __restrict__ gp
             const int h = __ldg(hrow + j);
             if (h >= n_hits) {
                 status = 4;   // hit index outside the loaded hits
+                pred_to_state(L.kind, q, t);
                 break;
             }
             if (h >= 0) {
                 float m[3], v[6], x2;
                 load_hit(pay, h, m, v, nullptr);
-                if (!chi2_hit(t, m[0], m[1], m[2], v, x2) || !kalman_update(t, m[0], m[1], m[2], v)) {
+                if (!chi2_hit(L.kind, q, m[0], m[1], m[2], v, x2) || !kalman_update(L.kind, q, m[0], m[1], m[2], v, t)) {
                     status = 3;
                     break;
                 }
                 sum += x2;
                 ++c_upd;
+            } else {
+                pred_to_state(L.kind, q, t);
             }
         }
         store_state6(t, p_out + 6 * (int64_t)i, c_out + 21 * (int64_t)i);
@@ -96,7 +101,11 @@ __global__ void __launch_bounds__(kThreads) k_step_propagate(const DevGeom* __re
     const int l = layers[i];
     int it = 0;
     int r = 0;
-    if (l >= 0 && l < g.n_layers) r = propagate(g.layers[l], g.cB, P.material, t, it);
+    if (l >= 0 && l < g.n_layers) {
+        Pred q;
+        r = propagate(g.layers[l], g.cB, P.material, t, q, it);
+        if (r == 1) pred_to_state(g.layers[l].kind, q, t);
+    }
     store_state6(t, p_out + 6 * (int64_t)i, c_out + 21 * (int64_t)i);
     crossed[i] = r;
 }
@@ -115,7 +124,19 @@ __global__ void __launch_bounds__(kThreads) k_step_update(int n, const float* __
     for (int j = 0; j < 6; ++j) v[j] = hcov[6 * (int64_t)i + j];
     const float mx = hxyz[3 * (int64_t)i], my = hxyz[3 * (int64_t)i + 1], mz = hxyz[3 * (int64_t)i + 2];
     float x2 = 0.0f;
-    const bool good = chi2_hit(t, mx, my, mz, v, x2) && kalman_update(t, mx, my, mz, v);
+    // a state given in the global frame is updated without a surface constraint
+    float S[6], Lc[6], inv[3];
+    bool good = true;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) S[j] = t.c[j] + v[j];
+    if (chol3(S, Lc, inv)) {
+        const float r0 = mx - t.xh, r1 = my - t.yh, r2 = mz - t.zh;
+        const float y0 = r0 * inv[0], y1 = (r1 - Lc[1] * y0) * inv[1], y2 = (r2 - Lc[3] * y0 - Lc[4] * y1) * inv[2];
+        x2 = y0 * y0 + y1 * y1 + y2 * y2;
+    } else {
+        good = false;
+    }
+    good = good && state_update(t, mx, my, mz, v);
     store_state6(t, p_out + 6 * (int64_t)i, c_out + 21 * (int64_t)i);
     chi2[i] = x2;
     ok[i] = good ? 1 : 0;

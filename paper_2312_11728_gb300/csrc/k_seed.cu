@@ -80,11 +80,12 @@ __global__ void __launch_bounds__(kThreads) k_seed(const DevGeom* __restrict__ g
     t.c[ix(0, 0)] = 0.01f; t.c[ix(1, 1)] = 0.01f; t.c[ix(2, 2)] = 0.01f;
     t.c[ix(3, 3)] = sk * sk; t.c[ix(4, 4)] = 0.0025f; t.c[ix(5, 5)] = 0.0025f;
     int newton = 0;
-    ok = ok && kalman_update(t, m[0][0], m[0][1], m[0][2], v[0]);
+    ok = ok && state_update(t, m[0][0], m[0][1], m[0][2], v[0]);
 #pragma unroll
     for (int j = 1; j < 3; ++j) {
-        ok = ok && propagate(g.layers[lay[j]], g.cB, P.material, t, newton) == 1;
-        ok = ok && kalman_update(t, m[j][0], m[j][1], m[j][2], v[j]);
+        Pred q;
+        ok = ok && propagate(g.layers[lay[j]], g.cB, P.material, t, q, newton) == 1;
+        ok = ok && kalman_update(g.layers[lay[j]].kind, q, m[j][0], m[j][1], m[j][2], v[j], t);
     }
     // region and first search step
     const float eta = -logf(tanf(0.5f * t.th));

@@ -73,13 +73,18 @@ class Geometry:
         return max(len(p) for p in self.plans)
 
 
+def _f32(v):
+    """Values the C interface carries as float32, so that every consumer sees the same geometry."""
+    return np.asarray(v, np.float32).astype(np.float64)
+
+
 def _layer_table(rows, plans, bz=3.8, barrel_eta_max=1.0) -> Geometry:
     kind = np.array([r[0] for r in rows], np.int32)
-    pos = np.array([r[1] for r in rows], np.float64)
-    lo = np.array([r[2] for r in rows], np.float64)
-    hi = np.array([r[3] for r in rows], np.float64)
-    xx0 = np.array([r[4] for r in rows], np.float64)
-    sig = np.array([r[5] for r in rows], np.float64)
+    pos = _f32([r[1] for r in rows])
+    lo = _f32([r[2] for r in rows])
+    hi = _f32([r[3] for r in rows])
+    xx0 = _f32([r[4] for r in rows])
+    sig = _f32([r[5] for r in rows])
     n_eta = np.array([r[6] for r in rows], np.int32)
     n_phi = np.array([r[7] for r in rows], np.int32)
     eta_lo = np.empty(len(rows))
@@ -91,9 +96,9 @@ def _layer_table(rows, plans, bz=3.8, barrel_eta_max=1.0) -> Geometry:
         else:
             a = np.arcsinh(pos[i] / hi[i])
             b = np.arcsinh(pos[i] / lo[i])
-            eta_lo[i], eta_hi[i] = (a, b) if pos[i] > 0 else (-b, -a)
-    return Geometry(kind, pos, lo, hi, xx0, sig, n_eta, n_phi, eta_lo, eta_hi,
-                    [list(p) for p in plans], bz, barrel_eta_max)
+            eta_lo[i], eta_hi[i] = min(a, b), max(a, b)
+    return Geometry(kind, pos, lo, hi, xx0, sig, n_eta, n_phi, _f32(eta_lo), _f32(eta_hi),
+                    [list(p) for p in plans], float(_f32(bz)), float(_f32(barrel_eta_max)))
 
 
 SIG_BARREL = (30e-4, 30e-4, 100e-4)   # (r, r-phi, z): 30 um r-phi, 100 um z, 30 um along the normal
@@ -259,6 +264,18 @@ def _cylinder_crossing(x, y, phi, om, R):
     return s_out
 
 
+def _path_to_apex(x, y, phi, om):
+    """Transverse path to the track circle's point farthest from the z axis (inf if straight)."""
+    straight = np.abs(om) < 1e-15
+    w = np.where(straight, 1.0, om)
+    cx = x - np.sin(phi) / w
+    cy = y + np.cos(phi) / w
+    sg = np.sign(w)
+    psi_far = np.arctan2(sg * cx, -sg * cy)
+    turn = np.mod((psi_far - phi) * sg, 2.0 * np.pi)
+    return np.where(straight, np.inf, turn / np.abs(w))
+
+
 def _move(x, y, z, phi, theta, om, s):
     """Position and direction after transverse path s (circle-centre form)."""
     straight = np.abs(om) < 1e-15
@@ -352,7 +369,11 @@ def simulate_event(geom: Geometry, n_tracks: int, seed: int = 0, event: int = 0,
                 s = _cylinder_crossing(x, y, ph, om, geom.pos[lay])
             else:
                 s = (geom.pos[lay] - z) * np.tan(th)
-                s = np.where(s > 0, s, np.nan)
+                # a curling track is followed only up to its point of largest radius: a disk it
+                # would reach later ends the track
+                past = np.isfinite(s) & (s > 0) & (s > _path_to_apex(x, y, ph, om))
+                alive[idx[past]] = False
+                s = np.where((s > 0) & ~past, s, np.nan)
             ok = np.isfinite(s)
             s = np.where(ok, s, 0.0)
             xn, yn, zn, psi = _move(x, y, z, ph, th, om, s)

@@ -7,7 +7,7 @@ import pytest
 import oracle
 from paper_2312_11728_gb300 import synth as S
 
-BZ = 3.8
+BZ = float(S.geometry_phase2().bz)
 CB = 0.00299792458 * BZ
 
 
