@@ -318,7 +318,7 @@ def main():
         "roofline": {"bound": "alu", "kernel": "k_build", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                      "peak_note": f"FP32: {n_sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz ({src} max clock)",
-                     "flops_per_launch": build_flops(bc)},
+                     "flops_per_launch": int(build_flops(bc))},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches_per_step * args.steps),
         "clocks": clocks,
@@ -326,7 +326,7 @@ def main():
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, batch, fit, params)
-    print(json.dumps(line), flush=True)
+    print(json.dumps(line, default=lambda o: o.item() if hasattr(o, "item") else str(o)), flush=True)
     if dist:
         dist.destroy_process_group()
 

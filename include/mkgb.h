@@ -76,7 +76,12 @@ typedef struct {
     float score_hole;
     float barrel_eta_max;  /* region choice with >1 plan: |eta_seed| < this -> plan 0, else 1 (eta>0) / 2 */
     int32_t material;      /* 1: multiple scattering and energy loss at every crossed layer */
+    int32_t precision;     /* MKGB_FP32: Kalman steps of the search and the fit in FP32 (seed fits in FP64);
+                              MKGB_FP64: every step in FP64 (the plain comparison path) */
 } mkgb_params;
+
+#define MKGB_FP32 0
+#define MKGB_FP64 2
 
 /* Output of mkgb_build: caller-allocated arrays (device or host per on_device). */
 typedef struct {

@@ -104,7 +104,9 @@ def compare_build(gpu: dict, orc: dict):
                 failed_mismatch=int((fail_gpu != ~ok_score).sum()),
                 worst_param=float(p_ratio.max()) if p_ratio.size else 0.0,
                 worst_cov=float(c_ratio.max()) if c_ratio.size else 0.0,
-                worst_chi2=float(x_ratio.max()) if x_ratio.size else 0.0)
+                worst_chi2=float(x_ratio.max()) if x_ratio.size else 0.0,
+                bad_seeds=idx[cmp][(~p_ok).any(1) | (~c_ok).any(1) | ~x_ok][:20],
+                worst_cov_elem=int(np.argmax(c_ratio.max(0))) if c_ratio.size else -1)
 
 
 def compare_fit(gpu: dict, orc: dict, mask=None):
@@ -117,4 +119,6 @@ def compare_fit(gpu: dict, orc: dict, mask=None):
                 cov_bad=int((~c_ok).any(1).sum()), chi2_bad=int((~x_ok).sum()),
                 worst_param=float(p_ratio.max()) if p_ratio.size else 0.0,
                 worst_cov=float(c_ratio.max()) if c_ratio.size else 0.0,
-                worst_chi2=float(x_ratio.max()) if x_ratio.size else 0.0)
+                worst_chi2=float(x_ratio.max()) if x_ratio.size else 0.0,
+                bad_tracks=np.nonzero(m)[0][(~p_ok).any(1) | (~c_ok).any(1) | ~x_ok][:20],
+                worst_cov_elem=int(np.argmax(c_ratio.max(0))) if c_ratio.size else -1)

@@ -286,6 +286,8 @@ int mkgb_set_params(mkgb_ctx* ctx, const mkgb_params* p) {
     d.score_hit = p->score_hit;
     d.score_hole = p->score_hole;
     d.barrel_eta_max = p->barrel_eta_max;
+    if (p->precision != MKGB_FP32 && p->precision != MKGB_FP64) return fail(ctx, MKGB_EINVAL, "bad precision %d", p->precision);
+    d.precision = p->precision;
     ctx->has_params = true;
     return MKGB_OK;
 }

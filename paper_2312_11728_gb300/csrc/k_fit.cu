@@ -18,6 +18,7 @@ __device__ __forceinline__ void load_geom(const DevGeom* __restrict__ gp, DevGeo
     __syncthreads();
 }
 
+template <class F>
 __global__ void __launch_bounds__(kThreads) k_fit(const DevGeom* __restrict__ gp, DevParams P,
                                                   const float4* __restrict__ pay, int64_t n_hits, int n, int max_steps,
                                                   const int* __restrict__ layers, const int* __restrict__ hits,
@@ -31,9 +32,9 @@ __global__ void __launch_bounds__(kThreads) k_fit(const DevGeom* __restrict__ gp
     unsigned long long c_steps = 0, c_upd = 0;
     int c_newton = 0;
     if (i < n) {
-        State t;
+        StateT<F> t;
         load_state6(p0 + 6 * (int64_t)i, c0 + 21 * (int64_t)i, t);
-        float sum = 0.0f;
+        F sum = F(0);
         int status = 0;
         const int* lrow = layers + (int64_t)i * max_steps;
         const int* hrow = hits + (int64_t)i * max_steps;
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(kThreads) k_fit(const DevGeom* __restrict__ gp
             const int l = __ldg(lrow + j);
             if (l < 0 || l >= g.n_layers) break;
             const DevLayer& L = g.layers[l];
-            Pred q;
+            PredT<F> q;
             const int r = propagate(L, g.cB, P.material, t, q, c_newton);
             if (r != 1) {
                 status = r == 0 ? 1 : 2;
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(kThreads) k_fit(const DevGeom* __restrict__ gp
                 break;
             }
             if (h >= 0) {
-                float m[3], v[6], x2;
+                F m[3], v[6], x2;
                 load_hit(pay, h, m, v, nullptr);
                 if (!chi2_hit(L.kind, q, m[0], m[1], m[2], v, x2) || !kalman_update(L.kind, q, m[0], m[1], m[2], v, t)) {
                     status = 3;
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(kThreads) k_fit(const DevGeom* __restrict__ gp
             }
         }
         store_state6(t, p_out + 6 * (int64_t)i, c_out + 21 * (int64_t)i);
-        chi2_out[i] = sum;
+        chi2_out[i] = float(sum);
         if (status_out) status_out[i] = status;
     }
     if (counters) {
@@ -149,8 +150,13 @@ cudaError_t launch_fit(cudaStream_t st, const DevGeom* g, DevParams P, const flo
                        const int* layers, const int* hits, const float* p0, const float* c0, float* p_out,
                        float* c_out, float* chi2_out, int* status_out, unsigned long long* counters) {
     if (n == 0) return cudaSuccess;
-    k_fit<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p0, c0, p_out,
-                                                             c_out, chi2_out, status_out, counters);
+    const int blocks = (n + kThreads - 1) / kThreads;
+    if (P.precision == MKGB_FP64)
+        k_fit<double><<<blocks, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p0, c0, p_out, c_out,
+                                                   chi2_out, status_out, counters);
+    else
+        k_fit<float><<<blocks, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p0, c0, p_out, c_out,
+                                                  chi2_out, status_out, counters);
     return cudaGetLastError();
 }
 

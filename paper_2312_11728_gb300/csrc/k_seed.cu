@@ -8,7 +8,14 @@
 // Kalman fit through hits 1, 2, 3 (propagation with material between them) gives the
 // state at hit 3.  The seed's region (layer plan) follows from its eta, and the search
 // starts at the plan step after hit 3's layer.
-#include "internal.h"
+//
+// Precision: the seed fit runs in FP64 (the same code instantiated for double).  Its diffuse
+// prior makes every update badly conditioned (the innovation covariance S has a condition
+// number of ~1e6 at the median seed): the posterior variance along a precisely measured
+// direction is a small difference of numbers that FP32 rounding has already perturbed.  It is
+// done once per seed, against ~60 FP32 Kalman steps per seed in the search.  A second kernel
+// computes the (event, eta, phi) ordering keys.
+#include "seed.cuh"
 
 namespace mk {
 
@@ -16,105 +23,59 @@ namespace {
 
 constexpr int kThreads = 128;
 
-__global__ void __launch_bounds__(kThreads) k_seed(const DevGeom* __restrict__ gp, DevParams P, HitStore H, int n,
-                                                   const int* __restrict__ seed_hits, float* __restrict__ state,
-                                                   int4* __restrict__ info, int* __restrict__ key_of,
-                                                   int* __restrict__ key_counts, float* state6, float* cov21,
-                                                   int* info3) {
-    __shared__ DevGeom g;
-    {
-        const int4* src = reinterpret_cast<const int4*>(gp);
-        int4* dst = reinterpret_cast<int4*>(&g);
-        for (int i = threadIdx.x; i < (int)(sizeof(DevGeom) / 16); i += blockDim.x) dst[i] = src[i];
-    }
+__device__ __forceinline__ void load_geom(const DevGeom* __restrict__ gp, DevGeom& g) {
+    const int4* src = reinterpret_cast<const int4*>(gp);
+    int4* dst = reinterpret_cast<int4*>(&g);
+    for (int i = threadIdx.x; i < (int)(sizeof(DevGeom) / 16); i += blockDim.x) dst[i] = src[i];
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int id[3], lay[3], ev[3];
-    float m[3][3], v[3][6];
-    bool ok = true;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        id[j] = seed_hits[3 * i + j];
-        if (id[j] < 0 || id[j] >= H.n_hits) {
-            ok = false;
-            id[j] = 0;
-        }
-        const int seg = H.hit_seg[id[j]];
-        ev[j] = seg / H.n_layers;
-        lay[j] = seg - ev[j] * H.n_layers;
-        load_hit(H.pay, id[j], m[j], v[j], nullptr);
-    }
-    ok = ok && ev[0] == ev[1] && ev[1] == ev[2];
+}
 
-    // circle through the three transverse points, relative to hit 1
-    const float ax = m[1][0] - m[0][0], ay = m[1][1] - m[0][1];
-    const float bx = m[2][0] - m[0][0], by = m[2][1] - m[0][1];
-    const float cross = ax * by - ay * bx;
-    const float chord2 = bx * bx + by * by;
-    float k, phi1, arc;
-    if (fabsf(cross) < 1e-7f * chord2) {
-        k = 0.0f;
-        phi1 = atan2f(by, bx);
-        arc = sqrtf(chord2);
-    } else {
-        const float a2 = ax * ax + ay * ay;
-        const float inv2c = 0.5f / cross;
-        const float ux = (by * a2 - ay * chord2) * inv2c;
-        const float uy = (ax * chord2 - bx * a2) * inv2c;
-        const float rho = sqrtf(ux * ux + uy * uy);
-        const float sg = cross > 0.0f ? 1.0f : -1.0f;
-        k = -(sg / rho) / g.cB;
-        phi1 = atan2f(-sg * ux, sg * uy);
-        const float v1x = -ux, v1y = -uy, v3x = bx - ux, v3y = by - uy;
-        arc = fabsf(atan2f(v1x * v3y - v1y * v3x, v1x * v3x + v1y * v3y)) * rho;
-    }
-    const float cot = (m[2][2] - m[0][2]) / arc;
-    State t;
-    t.xh = m[0][0]; t.yh = m[0][1]; t.zh = m[0][2];
-    t.xl = 0.0f; t.yl = 0.0f; t.zl = 0.0f;
-    t.k = k; t.phi = phi1; t.th = atan2f(1.0f, cot);
-#pragma unroll
-    for (int q = 0; q < 21; ++q) t.c[q] = 0.0f;
-    const float sk = 0.5f * fabsf(k) + 0.05f;
-    t.c[ix(0, 0)] = 0.01f; t.c[ix(1, 1)] = 0.01f; t.c[ix(2, 2)] = 0.01f;
-    t.c[ix(3, 3)] = sk * sk; t.c[ix(4, 4)] = 0.0025f; t.c[ix(5, 5)] = 0.0025f;
-    int newton = 0;
-    ok = ok && state_update(t, m[0][0], m[0][1], m[0][2], v[0]);
-#pragma unroll
-    for (int j = 1; j < 3; ++j) {
-        Pred q;
-        ok = ok && propagate(g.layers[lay[j]], g.cB, P.material, t, q, newton) == 1;
-        ok = ok && kalman_update(g.layers[lay[j]].kind, q, m[j][0], m[j][1], m[j][2], v[j], t);
-    }
-    // region and first search step
-    const float eta = -logf(tanf(0.5f * t.th));
-    int region = 0;
-    if (g.n_regions > 1 && !(fabsf(eta) < P.barrel_eta_max)) region = eta > 0.0f ? 1 : 2;
-    if (region >= g.n_regions) region = 0;
-    int start = -1;
-    for (int q = g.plan_off[region]; q < g.plan_off[region + 1]; ++q)
-        if (g.plan[q] == lay[2]) start = q - g.plan_off[region] + 1;
-    const int status = (ok && start >= 0) ? 0 : 1;
-
+__device__ __forceinline__ void write_seed(const State& t, int i, int region, int start, int event, float* state,
+                                           int4* info, float* state6, float* cov21, int* info3) {
     float* o = state + (int64_t)i * kSeedStateStride;
     o[0] = t.xh; o[1] = t.yh; o[2] = t.zh; o[3] = t.xl; o[4] = t.yl; o[5] = t.zl;
     o[6] = t.k; o[7] = t.phi; o[8] = t.th;
 #pragma unroll
     for (int q = 0; q < 21; ++q) o[9 + q] = t.c[q];
-    info[i] = make_int4(region, start, ev[0], status);
+    const int status = region >= 0 ? 0 : 1;
+    info[i] = make_int4(region, start, event, status);
     if (state6) store_state6(t, state6 + 6 * (int64_t)i, cov21 + 21 * (int64_t)i);
     if (info3) {
         info3[3 * i] = region;
         info3[3 * i + 1] = start;
         info3[3 * i + 2] = status;
     }
-    // (event, eta cell, phi cell) key for the hit-coherent processing order
+}
+
+__global__ void __launch_bounds__(kThreads) k_seed(const DevGeom* __restrict__ gp, DevParams P, HitStore H, int n,
+                                                   const int* __restrict__ seed_hits, float* __restrict__ state,
+                                                   int4* __restrict__ info, float* state6, float* cov21, int* info3) {
+    __shared__ DevGeom g;
+    load_geom(gp, g);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    StateT<double> td;
+    int lay[3], event, region, start;
+    const bool ok = seed_fit<double>(g, P, H, seed_hits, i, td, lay, event);
+    State t;
+    narrow_state(td, t);
+    seed_region(g, P, t.th, lay[2], ok, region, start);
+    write_seed(t, i, region, start, event, state, info, state6, cov21, info3);
+}
+
+// (event, eta cell, phi cell) key of every seed and its histogram, for the hit-coherent order
+__global__ void __launch_bounds__(kThreads) k_seed_key(int n, const float* __restrict__ state,
+                                                       const int4* __restrict__ info, int* __restrict__ key_of,
+                                                       int* __restrict__ key_counts) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float* o = state + (int64_t)i * kSeedStateStride;
+    const float eta = -logf(tanf(0.5f * o[8]));
     int ce = (int)floorf((eta + 4.0f) * (kSeedEtaCells / 8.0f));
     ce = ce < 0 ? 0 : (ce >= kSeedEtaCells ? kSeedEtaCells - 1 : ce);
-    int cp = (int)floorf((t.phi + kPi) * (kSeedPhiCells / kTwoPi));
+    int cp = (int)floorf((o[7] + kPi) * (kSeedPhiCells / kTwoPi));
     cp = cp < 0 ? 0 : (cp >= kSeedPhiCells ? kSeedPhiCells - 1 : cp);
-    const int key = (ev[0] * kSeedEtaCells + ce) * kSeedPhiCells + cp;
+    const int key = (info[i].z * kSeedEtaCells + ce) * kSeedPhiCells + cp;
     key_of[i] = key;
     atomicAdd(key_counts + key, 1);
 }
@@ -125,8 +86,9 @@ cudaError_t launch_seed(cudaStream_t st, const DevGeom* g, DevParams P, HitStore
                         float* state, int4* info, int* key_of, int* key_counts, float* state6, float* cov21,
                         int* info3) {
     if (n == 0) return cudaSuccess;
-    k_seed<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(g, P, H, n, seed_hits, state, info, key_of,
-                                                              key_counts, state6, cov21, info3);
+    const int blocks = (n + kThreads - 1) / kThreads;
+    k_seed<<<blocks, kThreads, 0, st>>>(g, P, H, n, seed_hits, state, info, state6, cov21, info3);
+    k_seed_key<<<blocks, kThreads, 0, st>>>(n, state, info, key_of, key_counts);
     return cudaGetLastError();
 }
 

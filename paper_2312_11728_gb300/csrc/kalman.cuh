@@ -1,4 +1,4 @@
-// Device-side Kalman step for one track candidate per CUDA lane (sm_103a, FP32).
+// Device-side Kalman step for one track candidate per CUDA lane (sm_103a).
 //
 // Propagation to a barrel cylinder or endcap disk in a uniform solenoid field with its
 // 6x6 Jacobian, covariance transport J C J^T, multiple scattering and mean energy loss
@@ -6,11 +6,17 @@
 // (a11).  The paper (Sec. 3.1) names propagation, hit selection and the Kalman filter
 // calculations as the per-layer work; the formulas are the textbook ones it cites.
 //
-// Precision: all arithmetic is FP32 except the track position, which is carried as an
-// unevaluated sum hi + lo of two floats.  Positions reach |z| = 275 cm where one FP32 ulp
-// is 15 nm, comparable to the 1e-3 chi2 tolerance on 30 um hits; the compensated sum keeps
-// the predicted residual m - x' exact to ~1e-12 relative, and the crossing equation is
-// written relative to the current position so its terms stay small.
+// Every function is a template on the scalar type F: float is the bulk path, double the
+// seed fit (whose diffuse prior makes it ill-conditioned) and the plain all-FP64 path.
+//
+// FP32 precision measures:
+//  - the track position is an unevaluated sum hi + lo of two floats: positions reach
+//    |z| = 275 cm where one FP32 ulp is 15 nm, comparable to the 1e-3 chi2 tolerance on
+//    30 um hits; the crossing equation is written relative to the current position, the
+//    crossing point is polished onto the cylinder with an exactly evaluated gap, and the
+//    helix step uses the chord form with an unrounded mid-angle;
+//  - the predicted covariance is kept in surface coordinates (exactly zero along the
+//    surface normal) and the chi2 and the update run in the local measurement frame.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -22,16 +28,21 @@
 namespace mk {
 
 constexpr float kCLight = 0.00299792458f;   // curvature [1/cm] per (T / GeV)
-constexpr float kMPion = 0.13957039f;        // GeV
-constexpr float kMElec = 0.51099895e-3f;     // GeV
-constexpr float kSiK = 0.307075f;            // MeV cm^2/mol
-constexpr float kSiZA = 0.49848f;
-constexpr float kSiRho = 2.329f;             // g/cm^3
-constexpr float kSiX0 = 9.37f;               // cm
-constexpr float kSiI = 173.0e-9f;            // GeV
-constexpr float kIncCap = 10.0f;
 constexpr float kPi = 3.14159265358979f;
 constexpr float kTwoPi = 6.28318530717959f;
+
+template <class F> struct Phys {
+    static constexpr F mpi = F(0.13957039);       // pion mass, GeV
+    static constexpr F me = F(0.51099895e-3);     // electron mass, GeV
+    static constexpr F K = F(0.307075);           // MeV cm^2/mol
+    static constexpr F ZA = F(0.49848);           // silicon Z/A
+    static constexpr F rho = F(2.329);            // g/cm^3
+    static constexpr F X0 = F(9.37);              // cm
+    static constexpr F I = F(173.0e-9);           // GeV
+    static constexpr F inc_cap = F(10.0);
+    static constexpr F pi = F(3.14159265358979323846);
+    static constexpr F two_pi = F(6.28318530717959647692);
+};
 
 struct DevLayer {
     int kind;
@@ -56,126 +67,138 @@ struct DevParams {
     int max_cands, max_holes, material;
     float nsig, deta_min, deta_max, dphi_min, dphi_max;
     float score_hit, score_hole, barrel_eta_max;
+    int precision;      // MKGB_FP32: FP32 Kalman steps (FP64 seed fit); MKGB_FP64: every step in FP64
 };
 
-// Packed lower-triangle index of a symmetric 6x6 (i, j in 0..5).
+// Packed lower-triangle index of a symmetric matrix (i, j >= 0).
 __host__ __device__ constexpr int ix(int i, int j) { return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i; }
 
-struct State {
-    float xh, yh, zh;   // position, high part
-    float xl, yl, zl;   // position, low part (|lo| <= ulp(hi)/2)
-    float k, phi, th;   // q/pT, direction phi, polar angle
-    float c[21];        // covariance of (x, y, z, k, phi, theta), packed
+template <class F> struct StateT {
+    F xh, yh, zh;   // position, high part
+    F xl, yl, zl;   // position, low part (|lo| <= ulp(hi)/2)
+    F k, phi, th;   // q/pT, direction phi, polar angle
+    F c[21];        // covariance of (x, y, z, k, phi, theta), packed
 };
 
-// ----------------------------------------------------------------- compensated sums
+// Predicted state at a layer surface; covariance of (u1, u2, k, phi, theta) where (u1, u2)
+// are surface coordinates:  barrel: u1 along e1 = (-y, x, 0)/r, u2 along z, normal
+// n = (x, y, 0)/r;  disk: u1 = x, u2 = y, normal z.
+template <class F> struct PredT {
+    F xh, yh, zh, xl, yl, zl, k, phi, th;
+    F c[15];
+};
 
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = __fadd_rn(a, b);
-    float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+using State = StateT<float>;
+using Pred = PredT<float>;
+
+// ----------------------------------------------------------------- scalar helpers
+
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ void sin_cos(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sin_cos(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
+
+template <class F> __device__ __forceinline__ void two_sum(F a, F b, F& s, F& e) {
+    s = add_rn(a, b);
+    const F bb = sub_rn(s, a);
+    e = add_rn(sub_rn(a, sub_rn(s, bb)), sub_rn(b, bb));
 }
 
 // (hi, lo) += d, renormalised.
-__device__ __forceinline__ void add_ff(float& hi, float& lo, float d) {
-    float s, e;
+template <class F> __device__ __forceinline__ void add_ff(F& hi, F& lo, F d) {
+    F s, e;
     two_sum(hi, d, s, e);
-    e = __fadd_rn(e, lo);
-    hi = __fadd_rn(s, e);
-    lo = __fsub_rn(e, __fsub_rn(hi, s));
+    e = add_rn(e, lo);
+    hi = add_rn(s, e);
+    lo = sub_rn(e, sub_rn(hi, s));
 }
 
 // R^2 - (x^2 + y^2) for x = xh + xl, y = yh + yl, with the squares split exactly by FMA.
-__device__ __forceinline__ float r2_gap(float R, float xh, float xl, float yh, float yl) {
-    float pR = __fmul_rn(R, R), eR = __fmaf_rn(R, R, -pR);
-    float p1 = __fmul_rn(xh, xh), e1 = __fmaf_rn(xh, xh, -p1);
-    float p2 = __fmul_rn(yh, yh), e2 = __fmaf_rn(yh, yh, -p2);
-    float s1, t1, s2, t2;
+template <class F> __device__ __forceinline__ F r2_gap(F R, F xh, F xl, F yh, F yl) {
+    const F pR = mul_rn(R, R), eR = fma_rn(R, R, -pR);
+    const F p1 = mul_rn(xh, xh), e1 = fma_rn(xh, xh, -p1);
+    const F p2 = mul_rn(yh, yh), e2 = fma_rn(yh, yh, -p2);
+    F s1, t1, s2, t2;
     two_sum(pR, -p1, s1, t1);
     two_sum(s1, -p2, s2, t2);
-    float tail = __fadd_rn(__fadd_rn(t1, t2), __fsub_rn(__fsub_rn(eR, e1), e2));
-    tail = __fsub_rn(tail, 2.0f * (xh * xl + yh * yl));
-    return __fadd_rn(s2, tail);
+    F tail = add_rn(add_rn(t1, t2), sub_rn(sub_rn(eR, e1), e2));
+    tail = sub_rn(tail, F(2) * (xh * xl + yh * yl));
+    return add_rn(s2, tail);
 }
 
-__device__ __forceinline__ float wrap_pi(float a) {
+template <class F> __device__ __forceinline__ F wrap_pi(F a) {
     // into (-pi, pi]
-    a = a - kTwoPi * rintf(a * (1.0f / kTwoPi));
-    if (a <= -kPi) a += kTwoPi;
-    if (a > kPi) a -= kTwoPi;
+    a = a - Phys<F>::two_pi * rint(a * (F(1) / Phys<F>::two_pi));
+    if (a <= -Phys<F>::pi) a += Phys<F>::two_pi;
+    if (a > Phys<F>::pi) a -= Phys<F>::two_pi;
     return a;
 }
 
 // sin(a)/a and (1 - cos a)/a.
-__device__ __forceinline__ void s1c1(float a, float& S1, float& C1) {
-    if (fabsf(a) < 1e-4f) {
-        S1 = 1.0f - a * a * (1.0f / 6.0f);
-        C1 = a * (0.5f - a * a * (1.0f / 24.0f));
+template <class F> __device__ __forceinline__ void s1c1(F a, F& S1, F& C1) {
+    if (fabs(a) < F(1e-4)) {
+        S1 = F(1) - a * a * (F(1) / F(6));
+        C1 = a * (F(0.5) - a * a * (F(1) / F(24)));
     } else {
-        float sh, ch;
-        sincosf(0.5f * a, &sh, &ch);
-        float inv = 1.0f / a;
-        S1 = 2.0f * sh * ch * inv;
-        C1 = 2.0f * sh * sh * inv;
+        F sh, ch;
+        sin_cos(F(0.5) * a, &sh, &ch);
+        const F inv = F(1) / a;
+        S1 = F(2) * sh * ch * inv;
+        C1 = F(2) * sh * sh * inv;
     }
 }
 
 // sin(a/2) / (a/2)
-__device__ __forceinline__ float sinc_half(float a) {
-    const float h = 0.5f * a;
-    if (fabsf(h) < 0.05f) {
-        const float h2 = h * h;
-        return 1.0f + h2 * (-1.0f / 6.0f + h2 * (1.0f / 120.0f - h2 * (1.0f / 5040.0f)));
+template <class F> __device__ __forceinline__ F sinc_half(F a) {
+    const F h = F(0.5) * a;
+    if (fabs(h) < F(0.05)) {
+        const F h2 = h * h;
+        return F(1) + h2 * (F(-1) / F(6) + h2 * (F(1) / F(120) + h2 * (F(-1) / F(5040) + h2 * (F(1) / F(362880)))));
     }
-    return sinf(h) / h;
+    return sin(h) / h;
 }
 
-// Derivatives of S1 and C1 with respect to a (power series below |a| = 0.3).
-__device__ __forceinline__ void s1c1_deriv(float a, float S1, float C1, float& dS1, float& dC1) {
-    if (fabsf(a) < 0.3f) {
-        float a2 = a * a;
-        dS1 = a * (-1.0f / 3.0f + a2 * (1.0f / 30.0f + a2 * (-1.0f / 840.0f + a2 * (1.0f / 45360.0f - a2 * (1.0f / 3991680.0f)))));
-        dC1 = 0.5f + a2 * (-1.0f / 8.0f + a2 * (1.0f / 144.0f + a2 * (-1.0f / 5760.0f + a2 * (1.0f / 403200.0f))));
+// Derivatives of S1 and C1 with respect to a (power series for small |a|).
+template <class F> __device__ __forceinline__ void s1c1_deriv(F a, F S1, F C1, F& dS1, F& dC1) {
+    const F lim = sizeof(F) == 4 ? F(0.3) : F(0.05);
+    if (fabs(a) < lim) {
+        const F a2 = a * a;
+        dS1 = a * (F(-1) / F(3) + a2 * (F(1) / F(30) + a2 * (F(-1) / F(840) + a2 * (F(1) / F(45360) - a2 * (F(1) / F(3991680))))));
+        dC1 = F(0.5) + a2 * (F(-1) / F(8) + a2 * (F(1) / F(144) + a2 * (F(-1) / F(5760) + a2 * (F(1) / F(403200)))));
     } else {
-        float inv = 1.0f / a;
-        float sa = S1 * a, ca = 1.0f - C1 * a;   // sin(a), cos(a)
+        const F inv = F(1) / a;
+        const F sa = S1 * a, ca = F(1) - C1 * a;   // sin(a), cos(a)
         dS1 = (ca - S1) * inv;
         dC1 = (sa - C1) * inv;
     }
 }
 
-// ----------------------------------------------------------------- predicted state in the surface frame
-//
-// At a layer surface the predicted position has no spread along the surface normal (the
-// crossing is constrained to the surface).  With a large spread along the surface (a grazing
-// crossing of a curling track) a global FP32 covariance carries rounding of ~1e-7 of that
-// spread in the normal direction, comparable to the hit's own normal variance.  The
-// predicted covariance is therefore kept in surface coordinates (u1, u2, k, phi, theta),
-// 15 packed floats whose normal row is exactly zero, and the chi2 and the update are
-// evaluated in the local measurement frame (n, e1, e2):
-//   barrel: n = (x, y, 0)/r, e1 = (-y, x, 0)/r, e2 = z-hat;   disk: n = z-hat, e1 = x-hat, e2 = y-hat.
+// ----------------------------------------------------------------- surface frame
 
-struct Pred {
-    float xh, yh, zh, xl, yl, zl, k, phi, th;
-    float c[15];   // covariance of (u1, u2, k, phi, theta), packed like ix()
-};
-
-struct Frame {
-    float c, s;    // barrel: n = (c, s, 0); unused for disks
+template <class F> struct FrameT {
+    F c, s;    // barrel: n = (c, s, 0); unused for disks
     int disk;
 };
 
-__device__ __forceinline__ Frame frame_of(int kind, float x, float y) {
-    Frame f;
+template <class F> __device__ __forceinline__ FrameT<F> frame_of(int kind, F x, F y) {
+    FrameT<F> f;
     f.disk = kind == MKGB_DISK;
-    const float ir = rsqrtf(x * x + y * y);
+    const F ir = rsq(x * x + y * y);
     f.c = x * ir;
     f.s = y * ir;
     return f;
 }
 
 // global 3-vector -> local (n, e1, e2) components
-__device__ __forceinline__ void to_local3(const Frame& f, const float g[3], float l[3]) {
+template <class F> __device__ __forceinline__ void to_local3(const FrameT<F>& f, const F g[3], F l[3]) {
     if (f.disk) {
         l[0] = g[2]; l[1] = g[0]; l[2] = g[1];
     } else {
@@ -186,23 +209,23 @@ __device__ __forceinline__ void to_local3(const Frame& f, const float g[3], floa
 }
 
 // surface displacement (d1 along e1, d2 along e2) -> global
-__device__ __forceinline__ void surface_to_global(const Frame& f, float d1, float d2, float g[3]) {
+template <class F> __device__ __forceinline__ void surface_to_global(const FrameT<F>& f, F d1, F d2, F g[3]) {
     if (f.disk) {
-        g[0] = d1; g[1] = d2; g[2] = 0.0f;
+        g[0] = d1; g[1] = d2; g[2] = F(0);
     } else {
         g[0] = -f.s * d1; g[1] = f.c * d1; g[2] = d2;
     }
 }
 
 // packed 3x3 symmetric (xx, yx, yy, zx, zy, zz) global -> local frame
-__device__ __forceinline__ void to_local_sym3(const Frame& f, const float v[6], float w[6]) {
+template <class F> __device__ __forceinline__ void to_local_sym3(const FrameT<F>& f, const F v[6], F w[6]) {
     if (f.disk) {   // (n, e1, e2) = (z, x, y)
         w[0] = v[5]; w[1] = v[3]; w[2] = v[0]; w[3] = v[4]; w[4] = v[1]; w[5] = v[2];
     } else {
-        const float c = f.c, s = f.s, cc = c * c, ss = s * s, cs = c * s;
-        w[0] = cc * v[0] + 2.0f * cs * v[1] + ss * v[2];              // nn
+        const F c = f.c, s = f.s, cc = c * c, ss = s * s, cs = c * s;
+        w[0] = cc * v[0] + F(2) * cs * v[1] + ss * v[2];              // nn
         w[1] = cs * (v[2] - v[0]) + (cc - ss) * v[1];                 // e1 n
-        w[2] = ss * v[0] - 2.0f * cs * v[1] + cc * v[2];              // e1 e1
+        w[2] = ss * v[0] - F(2) * cs * v[1] + cc * v[2];              // e1 e1
         w[3] = c * v[3] + s * v[4];                                   // e2 n
         w[4] = -s * v[3] + c * v[4];                                  // e2 e1
         w[5] = v[5];                                                  // e2 e2
@@ -210,22 +233,20 @@ __device__ __forceinline__ void to_local_sym3(const Frame& f, const float v[6], 
 }
 
 // Surface-frame covariance (15) -> global state covariance (21).
-__device__ __forceinline__ void embed_cov(const Frame& f, const float q[15], float c[21]) {
-    // columns of E (3x2): e1, e2
-    float E[3][2];
+template <class F> __device__ __forceinline__ void embed_cov(const FrameT<F>& f, const F q[15], F c[21]) {
+    F E[3][2];
     if (f.disk) {
-        E[0][0] = 1.0f; E[0][1] = 0.0f; E[1][0] = 0.0f; E[1][1] = 1.0f; E[2][0] = 0.0f; E[2][1] = 0.0f;
+        E[0][0] = F(1); E[0][1] = F(0); E[1][0] = F(0); E[1][1] = F(1); E[2][0] = F(0); E[2][1] = F(0);
     } else {
-        E[0][0] = -f.s; E[0][1] = 0.0f; E[1][0] = f.c; E[1][1] = 0.0f; E[2][0] = 0.0f; E[2][1] = 1.0f;
+        E[0][0] = -f.s; E[0][1] = F(0); E[1][0] = f.c; E[1][1] = F(0); E[2][0] = F(0); E[2][1] = F(1);
     }
-    const float cuu[2][2] = {{q[0], q[1]}, {q[1], q[2]}};
+    const F cuu[2][2] = {{q[0], q[1]}, {q[1], q[2]}};
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        const float m0 = E[i][0] * cuu[0][0] + E[i][1] * cuu[1][0];
-        const float m1 = E[i][0] * cuu[0][1] + E[i][1] * cuu[1][1];
+        const F m0 = E[i][0] * cuu[0][0] + E[i][1] * cuu[1][0];
+        const F m1 = E[i][0] * cuu[0][1] + E[i][1] * cuu[1][1];
 #pragma unroll
         for (int j = 0; j <= i; ++j) c[ix(i, j)] = m0 * E[j][0] + m1 * E[j][1];
-        // position x (k, phi, theta): local indices 2, 3, 4
 #pragma unroll
         for (int o = 0; o < 3; ++o) c[ix(3 + o, i)] = E[i][0] * q[ix(2 + o, 0)] + E[i][1] * q[ix(2 + o, 1)];
     }
@@ -235,7 +256,7 @@ __device__ __forceinline__ void embed_cov(const Frame& f, const float q[15], flo
         for (int b = 0; b <= a; ++b) c[ix(3 + a, 3 + b)] = q[ix(2 + a, 2 + b)];
 }
 
-__device__ __forceinline__ void pred_to_state(int kind, const Pred& q, State& t) {
+template <class F> __device__ __forceinline__ void pred_to_state(int kind, const PredT<F>& q, StateT<F>& t) {
     t.xh = q.xh; t.yh = q.yh; t.zh = q.zh; t.xl = q.xl; t.yl = q.yl; t.zl = q.zl;
     t.k = q.k; t.phi = q.phi; t.th = q.th;
     embed_cov(frame_of(kind, q.xh, q.yh), q.c, t.c);
@@ -243,45 +264,44 @@ __device__ __forceinline__ void pred_to_state(int kind, const Pred& q, State& t)
 
 // ----------------------------------------------------------------- propagation (a4-a7)
 
-__device__ __forceinline__ float R_of(const DevLayer& L) { return L.pos; }
-
 // Material of layer L at the predicted state: Highland Q on (k, phi, theta) and mean energy loss
 // scaling k and its row/column.  Returns false if the particle stops.
-__device__ __forceinline__ bool apply_material(const DevLayer& L, Pred& q, float st, float ct, float sfp,
-                                               float cfp) {
-    float cosi;
+template <class F>
+__device__ __forceinline__ bool apply_material(const DevLayer& L, PredT<F>& q, F st, F ct, F sfp, F cfp) {
+    using P = Phys<F>;
+    F cosi;
     if (L.kind == MKGB_BARREL) {
-        const float ir = rsqrtf(q.xh * q.xh + q.yh * q.yh);
-        cosi = fabsf((q.xh * cfp + q.yh * sfp) * st * ir);
+        const F ir = rsq(q.xh * q.xh + q.yh * q.yh);
+        cosi = fabs((q.xh * cfp + q.yh * sfp) * st * ir);
     } else {
-        cosi = fabsf(ct);
+        cosi = fabs(ct);
     }
-    const float fac = (cosi * kIncCap > 1.0f) ? 1.0f / cosi : kIncCap;
-    const float tt = L.xx0 * fac;
-    const float k = q.k;
-    if (!(tt > 0.0f) || k == 0.0f) return true;
-    const float pm = 1.0f / (fabsf(k) * st);
-    const float e2 = pm * pm + kMPion * kMPion;
-    const float beta2 = pm * pm / e2;
-    const float beta = sqrtf(beta2);
-    const float th0 = 0.0136f / (beta * pm) * sqrtf(tt) * (1.0f + 0.038f * logf(tt / beta2));
-    const float th02 = th0 * th0;
-    const float kc = k * (ct / st);
+    const F fac = (cosi * P::inc_cap > F(1)) ? F(1) / cosi : P::inc_cap;
+    const F tt = F(L.xx0) * fac;
+    const F k = q.k;
+    if (!(tt > F(0)) || k == F(0)) return true;
+    const F pm = F(1) / (fabs(k) * st);
+    const F e2 = pm * pm + P::mpi * P::mpi;
+    const F beta2 = pm * pm / e2;
+    const F beta = sqrt(beta2);
+    const F th0 = F(0.0136) / (beta * pm) * sqrt(tt) * (F(1) + F(0.038) * log(tt / beta2));
+    const F th02 = th0 * th0;
+    const F kc = k * (ct / st);
     q.c[ix(3, 3)] += th02 / (st * st);
     q.c[ix(4, 4)] += th02;
     q.c[ix(2, 2)] += kc * kc * th02;
     q.c[ix(4, 2)] -= kc * th02;
     // PDG Bethe-Bloch mean energy loss in silicon (no density effect)
-    const float e = sqrtf(e2);
-    const float bg2 = pm * pm * (1.0f / (kMPion * kMPion));
-    const float gam = e * (1.0f / kMPion);
-    const float rme = kMElec / kMPion;
-    const float tmax = 2.0f * kMElec * bg2 / (1.0f + 2.0f * gam * rme + rme * rme);
-    const float dedx = kSiK * kSiZA / beta2 * (0.5f * logf(2.0f * kMElec * bg2 * tmax / (kSiI * kSiI)) - beta2);
-    const float de = dedx * kSiRho * (tt * kSiX0) * 1e-3f;
-    const float en = e - de;
-    if (!(en > kMPion)) return false;
-    const float a = pm / sqrtf((en - kMPion) * (en + kMPion));
+    const F e = sqrt(e2);
+    const F bg2 = pm * pm * (F(1) / (P::mpi * P::mpi));
+    const F gam = e * (F(1) / P::mpi);
+    const F rme = P::me / P::mpi;
+    const F tmax = F(2) * P::me * bg2 / (F(1) + F(2) * gam * rme + rme * rme);
+    const F dedx = P::K * P::ZA / beta2 * (F(0.5) * log(F(2) * P::me * bg2 * tmax / (P::I * P::I)) - beta2);
+    const F de = dedx * P::rho * (tt * P::X0) * F(1e-3);
+    const F en = e - de;
+    if (!(en > P::mpi)) return false;
+    const F a = pm / sqrt((en - P::mpi) * (en + P::mpi));
     q.k = k * a;
     q.c[ix(2, 0)] *= a; q.c[ix(2, 1)] *= a; q.c[ix(3, 2)] *= a; q.c[ix(4, 2)] *= a;
     q.c[ix(2, 2)] *= a * a;
@@ -290,169 +310,172 @@ __device__ __forceinline__ bool apply_material(const DevLayer& L, Pred& q, float
 
 // Propagates t to layer L.  Returns 1 (crossed; q holds the predicted state with material),
 // 0 (not crossed) or -1 (particle stopped in the material).  newton_it counts iterations.
-__device__ __forceinline__ int propagate(const DevLayer& L, float cB, int material, const State& t, Pred& q,
+template <class F>
+__device__ __forceinline__ int propagate(const DevLayer& L, float cBf, int material, const StateT<F>& t, PredT<F>& q,
                                          int& newton_it) {
-    float sf, cf, st, ct;
-    sincosf(t.phi, &sf, &cf);
-    sincosf(t.th, &st, &ct);
-    const float om = -cB * t.k;
-    const float ux = t.xh + t.xl, uy = t.yh + t.yl;
-    float s, S1, C1, dx, dy;
+    using P = Phys<F>;
+    const F cB = F(cBf);
+    F sf, cf, st, ct;
+    sin_cos(t.phi, &sf, &cf);
+    sin_cos(t.th, &st, &ct);
+    const F om = -cB * t.k;
+    const F ux = t.xh + t.xl, uy = t.yh + t.yl;
+    const F Rl = F(L.pos), zd = F(L.pos);
+    F s, S1, C1, dx, dy;
     if (L.kind == MKGB_BARREL) {
-        const float R = L.pos;
-        const float c0 = r2_gap(R, t.xh, t.xl, t.yh, t.yl);   // R^2 - |u|^2
-        if (!(c0 > 0.0f)) return 0;
-        const float b = ux * cf + uy * sf;
-        const float sq = sqrtf(b * b + c0);
-        const float s0 = (b > 0.0f) ? c0 / (b + sq) : sq - b;
-        float lo = 0.0f, hi = 3.0e38f;
-        if (fabsf(om) > 1e-12f) {
-            const float inv = 1.0f / om;
-            const float cx = ux - sf * inv, cy = uy + cf * inv;
-            const float rho = fabsf(inv);
-            const float reach = sqrtf(cx * cx + cy * cy) + rho - R;
-            if (reach < 0.0f) return 0;
-            const float sg = om > 0.0f ? 1.0f : -1.0f;
-            float turn = (atan2f(sg * cx, -sg * cy) - t.phi) * sg;
-            turn -= kTwoPi * floorf(turn * (1.0f / kTwoPi));
+        const F c0 = r2_gap(Rl, t.xh, t.xl, t.yh, t.yl);   // R^2 - |u|^2
+        if (!(c0 > F(0))) return 0;
+        const F b = ux * cf + uy * sf;
+        const F sq = sqrt(b * b + c0);
+        const F s0 = (b > F(0)) ? c0 / (b + sq) : sq - b;
+        F lo = F(0), hi = F(3.0e38);
+        if (fabs(om) > F(1e-12)) {
+            const F inv = F(1) / om;
+            const F cx = ux - sf * inv, cy = uy + cf * inv;
+            const F rho = fabs(inv);
+            const F reach = sqrt(cx * cx + cy * cy) + rho - Rl;
+            if (reach < F(0)) return 0;
+            const F sg = om > F(0) ? F(1) : F(-1);
+            F turn = (atan2(sg * cx, -sg * cy) - t.phi) * sg;
+            turn -= P::two_pi * floor(turn * (F(1) / P::two_pi));
             hi = turn * rho;
         }
-        s = (s0 > lo && s0 < hi) ? s0 : 0.5f * (lo + hi);
-        for (int it = 0; it < 40; ++it) {
+        s = (s0 > lo && s0 < hi) ? s0 : F(0.5) * (lo + hi);
+        const F tol = sizeof(F) == 4 ? F(1e-6) : F(1e-13);
+        for (int it = 0; it < 60; ++it) {
             ++newton_it;
             s1c1(om * s, S1, C1);
             dx = s * (cf * S1 - sf * C1);
             dy = s * (sf * S1 + cf * C1);
             // g(s) = |u + d|^2 - R^2 = 2 u.d + |d|^2 - c0 (terms of size |u||d|, not R^2)
-            const float g = 2.0f * (ux * dx + uy * dy) + (dx * dx + dy * dy) - c0;
-            if (g == 0.0f) break;
-            if (g < 0.0f) lo = s; else hi = s;
-            float spn, cpn;
-            sincosf(t.phi + om * s, &spn, &cpn);
-            const float dg = 2.0f * ((ux + dx) * cpn + (uy + dy) * spn);
-            float sn = (dg > 0.0f) ? s - g / dg : 0.5f * (lo + hi);
-            if (!(sn >= lo && sn <= hi)) sn = 0.5f * (lo + hi);
-            const float ds = sn - s;
+            const F g = F(2) * (ux * dx + uy * dy) + (dx * dx + dy * dy) - c0;
+            if (g == F(0)) break;
+            if (g < F(0)) lo = s; else hi = s;
+            F spn, cpn;
+            sin_cos(t.phi + om * s, &spn, &cpn);
+            const F dg = F(2) * ((ux + dx) * cpn + (uy + dy) * spn);
+            F sn = (dg > F(0)) ? s - g / dg : F(0.5) * (lo + hi);
+            if (!(sn >= lo && sn <= hi)) sn = F(0.5) * (lo + hi);
+            const F ds = sn - s;
             s = sn;
-            if (fabsf(ds) <= 1e-6f * s) break;
+            if (fabs(ds) <= tol * s) break;
         }
     } else {
-        if (fabsf(ct) < 1e-7f) return 0;
-        const float dzp = __fsub_rn(__fsub_rn(L.pos, t.zh), t.zl);
+        if (fabs(ct) < F(1e-7)) return 0;
+        const F dzp = sub_rn(sub_rn(zd, t.zh), t.zl);
         s = dzp * st / ct;
-        if (!(s > 0.0f)) return 0;
+        if (!(s > F(0))) return 0;
         // loopers are followed on the outgoing part of their current turn only: the disk must be
         // reached before the next point of largest radius (and moving outward, checked below)
-        if (fabsf(om) > 1e-12f) {
-            const float inv = 1.0f / om;
-            const float cx = ux - sf * inv, cy = uy + cf * inv;
-            const float sg = om > 0.0f ? 1.0f : -1.0f;
-            float turn = (atan2f(sg * cx, -sg * cy) - t.phi) * sg;
-            turn -= kTwoPi * floorf(turn * (1.0f / kTwoPi));
-            if (s > turn * fabsf(inv)) return 0;
+        if (fabs(om) > F(1e-12)) {
+            const F inv = F(1) / om;
+            const F cx = ux - sf * inv, cy = uy + cf * inv;
+            const F sg = om > F(0) ? F(1) : F(-1);
+            F turn = (atan2(sg * cx, -sg * cy) - t.phi) * sg;
+            turn -= P::two_pi * floor(turn * (F(1) / P::two_pi));
+            if (s > turn * fabs(inv)) return 0;
         }
     }
-    const float a = om * s;
+    const F a = om * s;
     s1c1(a, S1, C1);
     {
         // chord form: d = s sinc(a/2) (cos psi, sin psi) with psi = phi + a/2 kept as an unrounded
         // sum; sin and cos of psi get the first-order correction for its low part
-        float psh, psl;
-        two_sum(t.phi, 0.5f * a, psh, psl);
-        float sp, cp;
-        sincosf(psh, &sp, &cp);
-        const float chord = s * sinc_half(a);
-        const float cpc = fmaf(-sp, psl, cp), spc = fmaf(cp, psl, sp);
-        dx = chord * cpc;
-        dy = chord * spc;
+        F psh, psl;
+        two_sum(t.phi, F(0.5) * a, psh, psl);
+        F sp, cp;
+        sin_cos(psh, &sp, &cp);
+        const F chord = s * sinc_half(a);
+        dx = chord * fma(-sp, psl, cp);
+        dy = chord * fma(cp, psl, sp);
     }
-    const float cot = ct / st;
-    const float dz = (L.kind == MKGB_BARREL) ? s * cot : __fsub_rn(__fsub_rn(L.pos, t.zh), t.zl);
-    float xh = t.xh, xl = t.xl, yh = t.yh, yl = t.yl, zh = t.zh, zl = t.zl;
+    const F cot = ct / st;
+    const F dz = (L.kind == MKGB_BARREL) ? s * cot : sub_rn(sub_rn(zd, t.zh), t.zl);
+    F xh = t.xh, xl = t.xl, yh = t.yh, yl = t.yl, zh = t.zh, zl = t.zl;
     add_ff(xh, xl, dx);
     add_ff(yh, yl, dy);
     add_ff(zh, zl, dz);
     if (L.kind == MKGB_BARREL) {
-        // polish: the FP32 Newton residual carries ~1e-7 |u||d| of rounding, i.e. the point sits
-        // up to a few 1e-6 cm off the cylinder along the normal (where the hit error is 30 um);
-        // the gap R^2 - r'^2 of the compensated position is exact to ~1e-10, so one more step
+        // polish: the Newton residual carries ~eps |u||d| of rounding, i.e. the point sits up to
+        // a few 1e-6 cm (FP32) off the cylinder along the normal, where the hit error is 30 um;
+        // the gap R^2 - r'^2 of the compensated position is exact to ~eps^2, so one more step
         // along the track puts the predicted point on the surface
-        float spn, cpn;
-        sincosf(t.phi + a, &spn, &cpn);
-        const float gap = r2_gap(R_of(L), xh, xl, yh, yl);
-        const float dsp = gap / (2.0f * (xh * cpn + yh * spn));
+        F spn, cpn;
+        sin_cos(t.phi + a, &spn, &cpn);
+        const F gap = r2_gap(Rl, xh, xl, yh, yl);
+        const F dsp = gap / (F(2) * (xh * cpn + yh * spn));
         add_ff(xh, xl, dsp * cpn);
         add_ff(yh, yl, dsp * spn);
         add_ff(zh, zl, dsp * cot);
-        if (!(zh >= L.lo && zh <= L.hi)) return 0;
+        if (!(zh >= F(L.lo) && zh <= F(L.hi))) return 0;
     } else {
-        const float r = sqrtf(xh * xh + yh * yh);
-        if (!(r >= L.lo && r <= L.hi)) return 0;
+        const F r = sqrt(xh * xh + yh * yh);
+        if (!(r >= F(L.lo) && r <= F(L.hi))) return 0;
     }
-    const float phin = t.phi + a;
-    float sfp, cfp;
-    sincosf(phin, &sfp, &cfp);
-    if (L.kind == MKGB_DISK && xh * cfp + yh * sfp < 0.0f) return 0;   // moving inward: past the apex
+    const F phin = t.phi + a;
+    F sfp, cfp;
+    sin_cos(phin, &sfp, &cfp);
+    if (L.kind == MKGB_DISK && xh * cfp + yh * sfp < F(0)) return 0;   // moving inward: past the apex
 
     // ---- Jacobian rows x, y, z, phi: J = A + (df/ds)(ds/dp); rows k, theta are identity
-    float dS1, dC1;
+    F dS1, dC1;
     s1c1_deriv(a, S1, C1, dS1, dC1);
-    const float A03 = -cB * s * s * (cf * dS1 - sf * dC1);
-    const float A13 = -cB * s * s * (sf * dS1 + cf * dC1);
-    const float A04 = -dy, A14 = dx;
-    const float A25 = -s / (st * st);
-    const float A43 = -cB * s;
-    const Frame fr = frame_of(L.kind, xh, yh);
-    float ds[6];
+    const F A03 = -cB * s * s * (cf * dS1 - sf * dC1);
+    const F A13 = -cB * s * s * (sf * dS1 + cf * dC1);
+    const F A04 = -dy, A14 = dx;
+    const F A25 = -s / (st * st);
+    const F A43 = -cB * s;
+    const FrameT<F> fr = frame_of(L.kind, xh, yh);
+    F ds[6];
     if (L.kind == MKGB_BARREL) {
-        const float ig = -1.0f / (xh * cfp + yh * sfp);
-        ds[0] = xh * ig; ds[1] = yh * ig; ds[2] = 0.0f;
+        const F ig = F(-1) / (xh * cfp + yh * sfp);
+        ds[0] = xh * ig; ds[1] = yh * ig; ds[2] = F(0);
         ds[3] = (xh * A03 + yh * A13) * ig;
         ds[4] = (xh * A04 + yh * A14) * ig;
-        ds[5] = 0.0f;
+        ds[5] = F(0);
     } else {
-        const float ig = -1.0f / cot;
-        ds[0] = 0.0f; ds[1] = 0.0f; ds[2] = ig;
-        ds[3] = 0.0f; ds[4] = 0.0f; ds[5] = A25 * ig;
+        const F ig = F(-1) / cot;
+        ds[0] = F(0); ds[1] = F(0); ds[2] = ig;
+        ds[3] = F(0); ds[4] = F(0); ds[5] = A25 * ig;
     }
     // surface rows: barrel u1 = -s x + c y (along e1), u2 = z; disk u1 = x, u2 = y.  The row
     // along the normal vanishes by the surface constraint and is not formed.
-    const float f1 = fr.disk ? cfp : (-fr.s * cfp + fr.c * sfp);
-    const float f2 = fr.disk ? sfp : cot;
-    const float fs[3] = {f1, f2, om};   // df/ds along u1, u2, phi
-    float J[3][6];
+    const F f1 = fr.disk ? cfp : (-fr.s * cfp + fr.c * sfp);
+    const F f2 = fr.disk ? sfp : cot;
+    const F fs[3] = {f1, f2, om};   // df/ds along u1, u2, phi
+    F J[3][6];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int j = 0; j < 6; ++j) J[r][j] = fs[r] * ds[j];
     if (fr.disk) {
-        J[0][0] += 1.0f; J[0][3] += A03; J[0][4] += A04;
-        J[1][1] += 1.0f; J[1][3] += A13; J[1][4] += A14;
+        J[0][0] += F(1); J[0][3] += A03; J[0][4] += A04;
+        J[1][1] += F(1); J[1][3] += A13; J[1][4] += A14;
     } else {
         J[0][0] -= fr.s; J[0][1] += fr.c; J[0][3] += -fr.s * A03 + fr.c * A13; J[0][4] += -fr.s * A04 + fr.c * A14;
-        J[1][2] += 1.0f; J[1][5] += A25;
+        J[1][2] += F(1); J[1][5] += A25;
     }
-    J[2][3] += A43; J[2][4] += 1.0f;
+    J[2][3] += A43; J[2][4] += F(1);
 
     // ---- transport into the surface frame: rows (u1, u2, phi) dense, (k, theta) identity
     constexpr int D[3] = {0, 1, 3};   // local indices of the dense rows
-    float T[3][6];
+    F T[3][6];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
-            float acc = 0.0f;
+            F acc = F(0);
 #pragma unroll
-            for (int l = 0; l < 6; ++l) acc = fmaf(J[r][l], t.c[ix(l, j)], acc);
+            for (int l = 0; l < 6; ++l) acc = fma(J[r][l], t.c[ix(l, j)], acc);
             T[r][j] = acc;
         }
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
 #pragma unroll
         for (int p = 0; p <= r; ++p) {
-            float acc = 0.0f;
+            F acc = F(0);
 #pragma unroll
-            for (int l = 0; l < 6; ++l) acc = fmaf(T[r][l], J[p][l], acc);
+            for (int l = 0; l < 6; ++l) acc = fma(T[r][l], J[p][l], acc);
             q.c[ix(D[r], D[p])] = acc;
         }
         q.c[ix(D[r], 2)] = T[r][3];
@@ -507,95 +530,95 @@ __device__ __forceinline__ Window window(const DevLayer& L, const DevParams& P, 
 // ----------------------------------------------------------------- chi2 (a9) and update (a11)
 
 // Cholesky of a packed 3x3; inv[] gets 1/L_ii.  Returns false if not positive definite.
-__device__ __forceinline__ bool chol3(const float S[6], float L[6], float inv[3]) {
-    if (!(S[0] > 0.0f)) return false;
-    inv[0] = rsqrtf(S[0]);
-    const float l10 = S[1] * inv[0], l20 = S[3] * inv[0];
-    const float d1 = S[2] - l10 * l10;
-    if (!(d1 > 0.0f)) return false;
-    inv[1] = rsqrtf(d1);
-    const float l21 = (S[4] - l20 * l10) * inv[1];
-    const float d2 = S[5] - l20 * l20 - l21 * l21;
-    if (!(d2 > 0.0f)) return false;
-    inv[2] = rsqrtf(d2);
+template <class F> __device__ __forceinline__ bool chol3(const F S[6], F L[6], F inv[3]) {
+    if (!(S[0] > F(0))) return false;
+    inv[0] = rsq(S[0]);
+    const F l10 = S[1] * inv[0], l20 = S[3] * inv[0];
+    const F d1 = S[2] - l10 * l10;
+    if (!(d1 > F(0))) return false;
+    inv[1] = rsq(d1);
+    const F l21 = (S[4] - l20 * l10) * inv[1];
+    const F d2 = S[5] - l20 * l20 - l21 * l21;
+    if (!(d2 > F(0))) return false;
+    inv[2] = rsq(d2);
     L[0] = S[0] * inv[0]; L[1] = l10; L[2] = d1 * inv[1]; L[3] = l20; L[4] = l21; L[5] = d2 * inv[2];
     return true;
 }
 
 // Residual m - x' (compensated position) and hit covariance in the local frame; S = V + C_surface.
-__device__ __forceinline__ void local_meas(const Frame& f, const Pred& q, float mx, float my, float mz,
-                                           const float v[6], float rl[3], float vl[6], float S[6]) {
-    const float r[3] = {__fsub_rn(__fsub_rn(mx, q.xh), q.xl), __fsub_rn(__fsub_rn(my, q.yh), q.yl),
-                        __fsub_rn(__fsub_rn(mz, q.zh), q.zl)};
+template <class F>
+__device__ __forceinline__ void local_meas(const FrameT<F>& f, const PredT<F>& q, F mx, F my, F mz, const F v[6],
+                                           F rl[3], F vl[6], F S[6]) {
+    const F r[3] = {sub_rn(sub_rn(mx, q.xh), q.xl), sub_rn(sub_rn(my, q.yh), q.yl), sub_rn(sub_rn(mz, q.zh), q.zl)};
     to_local3(f, r, rl);
     to_local_sym3(f, v, vl);
     S[0] = vl[0]; S[1] = vl[1]; S[3] = vl[3];
     S[2] = vl[2] + q.c[0]; S[4] = vl[4] + q.c[1]; S[5] = vl[5] + q.c[2];
 }
 
-__device__ __forceinline__ bool chi2_hit(int kind, const Pred& q, float mx, float my, float mz, const float v[6],
-                                         float& chi2) {
-    const Frame f = frame_of(kind, q.xh, q.yh);
-    float rl[3], vl[6], S[6], L[6], inv[3];
+template <class F>
+__device__ __forceinline__ bool chi2_hit(int kind, const PredT<F>& q, F mx, F my, F mz, const F v[6], F& chi2) {
+    const FrameT<F> f = frame_of(kind, q.xh, q.yh);
+    F rl[3], vl[6], S[6], L[6], inv[3];
     local_meas(f, q, mx, my, mz, v, rl, vl, S);
     if (!chol3(S, L, inv)) return false;
-    const float y0 = rl[0] * inv[0];
-    const float y1 = (rl[1] - L[1] * y0) * inv[1];
-    const float y2 = (rl[2] - L[3] * y0 - L[4] * y1) * inv[2];
+    const F y0 = rl[0] * inv[0];
+    const F y1 = (rl[1] - L[1] * y0) * inv[1];
+    const F y2 = (rl[2] - L[3] * y0 - L[4] * y1) * inv[2];
     chi2 = y0 * y0 + y1 * y1 + y2 * y2;
     return true;
 }
 
 // Kalman update of a predicted state with one hit, Joseph form in the surface frame:
 // K = C H^T S^-1 (H picks u1, u2 into measurement rows e1, e2; the normal row is zero),
-// C+ = (I - K H) C (I - K H)^T + K V K^T; the result is returned as a global-frame State.
+// C+ = (I - K H) C (I - K H)^T + K V K^T; the result is returned as a global-frame state.
 // Returns false if S is not positive definite or theta leaves (0, pi).
-__device__ __forceinline__ bool kalman_update(int kind, const Pred& q, float mx, float my, float mz,
-                                              const float v[6], State& out) {
-    const Frame f = frame_of(kind, q.xh, q.yh);
-    float rl[3], vl[6], S[6], L[6], inv[3];
+template <class F>
+__device__ __forceinline__ bool kalman_update(int kind, const PredT<F>& q, F mx, F my, F mz, const F v[6],
+                                              StateT<F>& out) {
+    const FrameT<F> f = frame_of(kind, q.xh, q.yh);
+    F rl[3], vl[6], S[6], L[6], inv[3];
     local_meas(f, q, mx, my, mz, v, rl, vl, S);
     if (!chol3(S, L, inv)) return false;
     // W = S^-1 = L^-T L^-1
-    const float i00 = inv[0], i11 = inv[1], i22 = inv[2];
-    const float i10 = -L[1] * i00 * i11;
-    const float i21 = -L[4] * i11 * i22;
-    const float i20 = -(L[3] * i00 + L[4] * i10) * i22;
-    const float W[3][3] = {{i00 * i00 + i10 * i10 + i20 * i20, i10 * i11 + i20 * i21, i20 * i22},
-                           {i10 * i11 + i20 * i21, i11 * i11 + i21 * i21, i21 * i22},
-                           {i20 * i22, i21 * i22, i22 * i22}};
-    float K[5][3];
+    const F i00 = inv[0], i11 = inv[1], i22 = inv[2];
+    const F i10 = -L[1] * i00 * i11;
+    const F i21 = -L[4] * i11 * i22;
+    const F i20 = -(L[3] * i00 + L[4] * i10) * i22;
+    const F W[3][3] = {{i00 * i00 + i10 * i10 + i20 * i20, i10 * i11 + i20 * i21, i20 * i22},
+                       {i10 * i11 + i20 * i21, i11 * i11 + i21 * i21, i21 * i22},
+                       {i20 * i22, i21 * i22, i22 * i22}};
+    F K[5][3];
 #pragma unroll
     for (int i = 0; i < 5; ++i)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) K[i][a] = fmaf(q.c[ix(i, 0)], W[1][a], q.c[ix(i, 1)] * W[2][a]);
-    float dp[5];
+        for (int a = 0; a < 3; ++a) K[i][a] = fma(q.c[ix(i, 0)], W[1][a], q.c[ix(i, 1)] * W[2][a]);
+    F dp[5];
 #pragma unroll
-    for (int i = 0; i < 5; ++i) dp[i] = fmaf(K[i][0], rl[0], fmaf(K[i][1], rl[1], K[i][2] * rl[2]));
+    for (int i = 0; i < 5; ++i) dp[i] = fma(K[i][0], rl[0], fma(K[i][1], rl[1], K[i][2] * rl[2]));
     // T = (I - K H) C : row i minus K_i1 * row u1 minus K_i2 * row u2
-    float T[5][5];
+    F T[5][5];
 #pragma unroll
     for (int i = 0; i < 5; ++i)
 #pragma unroll
-        for (int j = 0; j < 5; ++j)
-            T[i][j] = fmaf(-K[i][1], q.c[ix(0, j)], fmaf(-K[i][2], q.c[ix(1, j)], q.c[ix(i, j)]));
-    const float V[3][3] = {{vl[0], vl[1], vl[3]}, {vl[1], vl[2], vl[4]}, {vl[3], vl[4], vl[5]}};
-    float KV[5][3];
+        for (int j = 0; j < 5; ++j) T[i][j] = fma(-K[i][1], q.c[ix(0, j)], fma(-K[i][2], q.c[ix(1, j)], q.c[ix(i, j)]));
+    const F V[3][3] = {{vl[0], vl[1], vl[3]}, {vl[1], vl[2], vl[4]}, {vl[3], vl[4], vl[5]}};
+    F KV[5][3];
 #pragma unroll
     for (int i = 0; i < 5; ++i)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) KV[i][a] = fmaf(K[i][0], V[0][a], fmaf(K[i][1], V[1][a], K[i][2] * V[2][a]));
-    float cn[15];
+        for (int a = 0; a < 3; ++a) KV[i][a] = fma(K[i][0], V[0][a], fma(K[i][1], V[1][a], K[i][2] * V[2][a]));
+    F cn[15];
 #pragma unroll
     for (int i = 0; i < 5; ++i)
 #pragma unroll
         for (int j = 0; j <= i; ++j) {
-            float acc = fmaf(-T[i][0], K[j][1], fmaf(-T[i][1], K[j][2], T[i][j]));
+            F acc = fma(-T[i][0], K[j][1], fma(-T[i][1], K[j][2], T[i][j]));
 #pragma unroll
-            for (int a = 0; a < 3; ++a) acc = fmaf(KV[i][a], K[j][a], acc);
+            for (int a = 0; a < 3; ++a) acc = fma(KV[i][a], K[j][a], acc);
             cn[ix(i, j)] = acc;
         }
-    float dg[3];
+    F dg[3];
     surface_to_global(f, dp[0], dp[1], dg);
     out.xh = q.xh; out.xl = q.xl; out.yh = q.yh; out.yl = q.yl; out.zh = q.zh; out.zl = q.zl;
     add_ff(out.xh, out.xl, dg[0]);
@@ -605,61 +628,60 @@ __device__ __forceinline__ bool kalman_update(int kind, const Pred& q, float mx,
     out.phi = wrap_pi(q.phi + dp[3]);
     out.th = q.th + dp[4];
     embed_cov(f, cn, out.c);
-    return out.th > 0.0f && out.th < kPi;
+    return out.th > F(0) && out.th < Phys<F>::pi;
 }
 
 // Kalman update of a global-frame state that is not constrained to a surface (the first hit of
 // a seed, whose starting covariance is a diagonal prior): Joseph form in global coordinates.
-__device__ __forceinline__ bool state_update(State& t, float mx, float my, float mz, const float v[6]) {
-    float S[6], L[6], inv[3];
+template <class F> __device__ __forceinline__ bool state_update(StateT<F>& t, F mx, F my, F mz, const F v[6]) {
+    F S[6], L[6], inv[3];
 #pragma unroll
     for (int i = 0; i < 6; ++i) S[i] = t.c[i] + v[i];
     if (!chol3(S, L, inv)) return false;
-    const float r[3] = {__fsub_rn(__fsub_rn(mx, t.xh), t.xl), __fsub_rn(__fsub_rn(my, t.yh), t.yl),
-                        __fsub_rn(__fsub_rn(mz, t.zh), t.zl)};
-    const float i00 = inv[0], i11 = inv[1], i22 = inv[2];
-    const float i10 = -L[1] * i00 * i11;
-    const float i21 = -L[4] * i11 * i22;
-    const float i20 = -(L[3] * i00 + L[4] * i10) * i22;
-    const float W[3][3] = {{i00 * i00 + i10 * i10 + i20 * i20, i10 * i11 + i20 * i21, i20 * i22},
-                           {i10 * i11 + i20 * i21, i11 * i11 + i21 * i21, i21 * i22},
-                           {i20 * i22, i21 * i22, i22 * i22}};
-    float K[6][3];
+    const F r[3] = {sub_rn(sub_rn(mx, t.xh), t.xl), sub_rn(sub_rn(my, t.yh), t.yl), sub_rn(sub_rn(mz, t.zh), t.zl)};
+    const F i00 = inv[0], i11 = inv[1], i22 = inv[2];
+    const F i10 = -L[1] * i00 * i11;
+    const F i21 = -L[4] * i11 * i22;
+    const F i20 = -(L[3] * i00 + L[4] * i10) * i22;
+    const F W[3][3] = {{i00 * i00 + i10 * i10 + i20 * i20, i10 * i11 + i20 * i21, i20 * i22},
+                       {i10 * i11 + i20 * i21, i11 * i11 + i21 * i21, i21 * i22},
+                       {i20 * i22, i21 * i22, i22 * i22}};
+    F K[6][3];
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            float acc = 0.0f;
+            F acc = F(0);
 #pragma unroll
-            for (int b = 0; b < 3; ++b) acc = fmaf(t.c[ix(i, b)], W[b][a], acc);
+            for (int b = 0; b < 3; ++b) acc = fma(t.c[ix(i, b)], W[b][a], acc);
             K[i][a] = acc;
         }
-    float dp[6];
+    F dp[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) dp[i] = fmaf(K[i][0], r[0], fmaf(K[i][1], r[1], K[i][2] * r[2]));
-    float T[6][6];
+    for (int i = 0; i < 6; ++i) dp[i] = fma(K[i][0], r[0], fma(K[i][1], r[1], K[i][2] * r[2]));
+    F T[6][6];
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
-            float acc = t.c[ix(i, j)];
+            F acc = t.c[ix(i, j)];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) acc = fmaf(-K[i][a], t.c[ix(a, j)], acc);
+            for (int a = 0; a < 3; ++a) acc = fma(-K[i][a], t.c[ix(a, j)], acc);
             T[i][j] = acc;
         }
-    const float V[3][3] = {{v[0], v[1], v[3]}, {v[1], v[2], v[4]}, {v[3], v[4], v[5]}};
-    float KV[6][3];
+    const F V[3][3] = {{v[0], v[1], v[3]}, {v[1], v[2], v[4]}, {v[3], v[4], v[5]}};
+    F KV[6][3];
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) KV[i][a] = fmaf(K[i][0], V[0][a], fmaf(K[i][1], V[1][a], K[i][2] * V[2][a]));
+        for (int a = 0; a < 3; ++a) KV[i][a] = fma(K[i][0], V[0][a], fma(K[i][1], V[1][a], K[i][2] * V[2][a]));
 #pragma unroll
     for (int i = 0; i < 6; ++i)
 #pragma unroll
         for (int j = 0; j <= i; ++j) {
-            float acc = T[i][j];
+            F acc = T[i][j];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) acc = fmaf(KV[i][a] - T[i][a], K[j][a], acc);
+            for (int a = 0; a < 3; ++a) acc = fma(KV[i][a] - T[i][a], K[j][a], acc);
             t.c[ix(i, j)] = acc;
         }
     add_ff(t.xh, t.xl, dp[0]);
@@ -668,33 +690,44 @@ __device__ __forceinline__ bool state_update(State& t, float mx, float my, float
     t.k += dp[3];
     t.phi = wrap_pi(t.phi + dp[4]);
     t.th += dp[5];
-    return t.th > 0.0f && t.th < kPi;
+    return t.th > F(0) && t.th < Phys<F>::pi;
 }
 
-// ----------------------------------------------------------------- state I/O
+// ----------------------------------------------------------------- state I/O and conversion
 
-__device__ __forceinline__ void load_state6(const float* p, const float* c, State& t) {
-    t.xh = p[0]; t.yh = p[1]; t.zh = p[2];
-    t.xl = 0.0f; t.yl = 0.0f; t.zl = 0.0f;
-    t.k = p[3]; t.phi = p[4]; t.th = p[5];
+template <class F, class G> __device__ __forceinline__ void load_state6(const G* p, const G* c, StateT<F>& t) {
+    t.xh = F(p[0]); t.yh = F(p[1]); t.zh = F(p[2]);
+    t.xl = F(0); t.yl = F(0); t.zl = F(0);
+    t.k = F(p[3]); t.phi = F(p[4]); t.th = F(p[5]);
 #pragma unroll
-    for (int i = 0; i < 21; ++i) t.c[i] = c[i];
+    for (int i = 0; i < 21; ++i) t.c[i] = F(c[i]);
 }
 
-__device__ __forceinline__ void store_state6(const State& t, float* p, float* c) {
-    p[0] = t.xh + t.xl; p[1] = t.yh + t.yl; p[2] = t.zh + t.zl;
-    p[3] = t.k; p[4] = t.phi; p[5] = t.th;
+template <class F> __device__ __forceinline__ void store_state6(const StateT<F>& t, float* p, float* c) {
+    p[0] = float(t.xh + t.xl); p[1] = float(t.yh + t.yl); p[2] = float(t.zh + t.zl);
+    p[3] = float(t.k); p[4] = float(t.phi); p[5] = float(t.th);
 #pragma unroll
-    for (int i = 0; i < 21; ++i) c[i] = t.c[i];
+    for (int i = 0; i < 21; ++i) c[i] = float(t.c[i]);
+}
+
+// double state -> float state: positions split into hi + lo
+__device__ __forceinline__ void narrow_state(const StateT<double>& d, State& t) {
+    const double x = d.xh + d.xl, y = d.yh + d.yl, z = d.zh + d.zl;
+    t.xh = float(x); t.xl = float(x - double(t.xh));
+    t.yh = float(y); t.yl = float(y - double(t.yh));
+    t.zh = float(z); t.zl = float(z - double(t.zh));
+    t.k = float(d.k); t.phi = float(d.phi); t.th = float(d.th);
+#pragma unroll
+    for (int i = 0; i < 21; ++i) t.c[i] = float(d.c[i]);
 }
 
 // Hit payload: 3 x float4 = (x, y, z, id) (v0, v1, v2, v3) (v4, v5, -, -)
-__device__ __forceinline__ void load_hit(const float4* __restrict__ pay, long long q, float m[3], float v[6],
-                                         int* id) {
+template <class F>
+__device__ __forceinline__ void load_hit(const float4* __restrict__ pay, long long q, F m[3], F v[6], int* id) {
     const float4 a = __ldg(pay + 3 * q), b = __ldg(pay + 3 * q + 1), c = __ldg(pay + 3 * q + 2);
-    m[0] = a.x; m[1] = a.y; m[2] = a.z;
+    m[0] = F(a.x); m[1] = F(a.y); m[2] = F(a.z);
     if (id) *id = __float_as_int(a.w);
-    v[0] = b.x; v[1] = b.y; v[2] = b.z; v[3] = b.w; v[4] = c.x; v[5] = c.y;
+    v[0] = F(b.x); v[1] = F(b.y); v[2] = F(b.z); v[3] = F(b.w); v[4] = F(c.x); v[5] = F(c.y);
 }
 
 }  // namespace mk

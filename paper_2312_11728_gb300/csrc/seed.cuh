@@ -1,0 +1,87 @@
+// Seed fit device functions (a1), shared by the seed kernels.
+#pragma once
+
+#include "internal.h"
+
+namespace mk {
+
+// Seed fit of seed i in precision F.  Returns ok.
+template <class F>
+__device__ __forceinline__ bool seed_fit(const DevGeom& g, const DevParams& P, const HitStore& H, const int* __restrict__ seed_hits,
+                         int i, StateT<F>& t, int lay[3], int& event) {
+    int id[3], ev[3];
+    F m[3][3], v[3][6];
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        id[j] = seed_hits[3 * i + j];
+        if (id[j] < 0 || id[j] >= H.n_hits) {
+            ok = false;
+            id[j] = 0;
+        }
+        const int seg = H.hit_seg[id[j]];
+        ev[j] = seg / H.n_layers;
+        lay[j] = seg - ev[j] * H.n_layers;
+        load_hit(H.pay, id[j], m[j], v[j], nullptr);
+    }
+    event = ev[0];
+    ok = ok && ev[0] == ev[1] && ev[1] == ev[2];
+    // circle through the three transverse points, relative to hit 1
+    const F ax = m[1][0] - m[0][0], ay = m[1][1] - m[0][1];
+    const F bx = m[2][0] - m[0][0], by = m[2][1] - m[0][1];
+    const F cross = ax * by - ay * bx;
+    const F chord2 = bx * bx + by * by;
+    F k, phi1, arc;
+    if (fabs(cross) < F(1e-7) * chord2) {
+        k = F(0);
+        phi1 = atan2(by, bx);
+        arc = sqrt(chord2);
+    } else {
+        const F a2 = ax * ax + ay * ay;
+        const F inv2c = F(0.5) / cross;
+        const F ux = (by * a2 - ay * chord2) * inv2c;
+        const F uy = (ax * chord2 - bx * a2) * inv2c;
+        const F rho = sqrt(ux * ux + uy * uy);
+        const F sg = cross > F(0) ? F(1) : F(-1);
+        k = -(sg / rho) / F(g.cB);
+        phi1 = atan2(-sg * ux, sg * uy);
+        const F v1x = -ux, v1y = -uy, v3x = bx - ux, v3y = by - uy;
+        arc = fabs(atan2(v1x * v3y - v1y * v3x, v1x * v3x + v1y * v3y)) * rho;
+    }
+    const F cot = (m[2][2] - m[0][2]) / arc;
+    t.xh = m[0][0]; t.yh = m[0][1]; t.zh = m[0][2];
+    t.xl = F(0); t.yl = F(0); t.zl = F(0);
+    t.k = k; t.phi = phi1; t.th = atan2(F(1), cot);
+#pragma unroll
+    for (int q = 0; q < 21; ++q) t.c[q] = F(0);
+    const F sk = F(0.5) * fabs(k) + F(0.05);
+    t.c[ix(0, 0)] = F(0.01); t.c[ix(1, 1)] = F(0.01); t.c[ix(2, 2)] = F(0.01);
+    t.c[ix(3, 3)] = sk * sk; t.c[ix(4, 4)] = F(0.0025); t.c[ix(5, 5)] = F(0.0025);
+    int newton = 0;
+    ok = ok && state_update(t, m[0][0], m[0][1], m[0][2], v[0]);
+#pragma unroll
+    for (int j = 1; j < 3; ++j) {
+        PredT<F> q;
+        const DevLayer& L = g.layers[lay[j]];
+        ok = ok && propagate(L, g.cB, P.material, t, q, newton) == 1;
+        ok = ok && kalman_update(L.kind, q, m[j][0], m[j][1], m[j][2], v[j], t);
+    }
+    return ok;
+}
+
+__device__ __forceinline__ void seed_region(const DevGeom& g, const DevParams& P, float th, int lay3, bool ok,
+                                            int& region, int& start) {
+    const float eta = -logf(tanf(0.5f * th));
+    region = 0;
+    if (g.n_regions > 1 && !(fabsf(eta) < P.barrel_eta_max)) region = eta > 0.0f ? 1 : 2;
+    if (region >= g.n_regions) region = 0;
+    start = -1;
+    for (int q = g.plan_off[region]; q < g.plan_off[region + 1]; ++q)
+        if (g.plan[q] == lay3) start = q - g.plan_off[region] + 1;
+    if (!ok || start < 0) {
+        region = -1;
+        start = -1;
+    }
+}
+
+}  // namespace mk

@@ -16,6 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmkgb.so")
 
 BARREL, DISK = 0, 1
+FP32, FP64 = 0, 2
 MAX_CANDS = 8
 HIT_MISS, HIT_SKIP, HIT_STOP, HIT_PRE = -1, -2, -3, -4
 ERRORS = {-1: "MKGB_EINVAL", -2: "MKGB_ENOMEM", -3: "MKGB_ECUDA", -5: "MKGB_ESTATE"}
@@ -31,7 +32,8 @@ class Params(C.Structure):
     _fields_ = [("chi2_cut", C.c_float), ("max_cands", C.c_int32), ("max_holes", C.c_int32),
                 ("win_nsigma", C.c_float), ("deta_min", C.c_float), ("deta_max", C.c_float),
                 ("dphi_min", C.c_float), ("dphi_max", C.c_float), ("score_hit", C.c_float),
-                ("score_hole", C.c_float), ("barrel_eta_max", C.c_float), ("material", C.c_int32)]
+                ("score_hole", C.c_float), ("barrel_eta_max", C.c_float), ("material", C.c_int32),
+                ("precision", C.c_int32)]
 
 
 class Tracks(C.Structure):
@@ -83,8 +85,12 @@ def _is_torch(a):
     return type(a).__module__.startswith("torch")
 
 
-def _ptr(a, dtype):
-    """(pointer, on_device) of an array argument; None -> (None, None)."""
+_keep = []   # host copies made for the call in progress
+
+
+def _ptr(a, dtype, out=False):
+    """(pointer, on_device) of an array argument; None -> (None, None).  Host inputs of another
+    dtype or layout are copied; outputs must already be contiguous arrays of the right dtype."""
     if a is None:
         return None, None
     if _is_torch(a):
@@ -94,7 +100,10 @@ def _ptr(a, dtype):
             raise MkgbError(f"tensor must be contiguous {want}, got {a.dtype}")
         return C.c_void_p(a.data_ptr()), a.is_cuda
     if not (isinstance(a, np.ndarray) and a.dtype == dtype and a.flags.c_contiguous):
-        raise MkgbError(f"array must be a C-contiguous numpy {np.dtype(dtype).name} array")
+        if out:
+            raise MkgbError(f"output must be a C-contiguous numpy {np.dtype(dtype).name} array")
+        a = np.ascontiguousarray(a, dtype)
+        _keep.append(a)
     return C.c_void_p(a.ctypes.data), False
 
 
@@ -141,6 +150,7 @@ class Context:
             pass
 
     def _check(self, rc, what):
+        _keep.clear()
         if rc != 0:
             msg = self.lib.mkgb_last_error(self.h).decode()
             raise MkgbError(f"{what} failed ({ERRORS.get(rc, rc)}): {msg}")
@@ -164,7 +174,7 @@ class Context:
                    float(params["win_nsigma"]), float(params["deta_min"]), float(params["deta_max"]),
                    float(params["dphi_min"]), float(params["dphi_max"]), float(params["score_hit"]),
                    float(params["score_hole"]), float(params.get("barrel_eta_max", self.barrel_eta_max)),
-                   int(params["material"]))
+                   int(params["material"]), int(params.get("precision", 0)))
         self._check(self.lib.mkgb_set_params(self.h, C.byref(p)), "mkgb_set_params")
 
     # ---- data
@@ -178,16 +188,16 @@ class Context:
     def seed(self, seed_hits, state=None, cov=None, info=None):
         n = int(seed_hits.shape[0])
         ps, d0 = _ptr(seed_hits, np.int32)
-        p1, d1 = _ptr(state, np.float32)
-        p2, d2 = _ptr(cov, np.float32)
-        p3, d3 = _ptr(info, np.int32)
+        p1, d1 = _ptr(state, np.float32, out=True)
+        p2, d2 = _ptr(cov, np.float32, out=True)
+        p3, d3 = _ptr(info, np.int32, out=True)
         self._check(self.lib.mkgb_seed(self.h, n, ps, _same(d0, d1, d2, d3), p1, p2, p3), "mkgb_seed")
         self.n_seeds = n
 
     def build(self, out: dict):
         """out: dict of arrays params (n,6) cov (n,21) chi2 score nfound nholes hits (n, max_plan)."""
         f, i = np.float32, np.int32
-        ptrs = [_ptr(out[k], t) for k, t in (("params", f), ("cov", f), ("chi2", f), ("score", f),
+        ptrs = [_ptr(out[k], t, out=True) for k, t in (("params", f), ("cov", f), ("chi2", f), ("score", f),
                                               ("nfound", i), ("nholes", i), ("hits", i))]
         t = Tracks(*[p for p, _ in ptrs], int(out["hits"].shape[1]))
         self._check(self.lib.mkgb_build(self.h, C.byref(t), _same(*[d for _, d in ptrs])), "mkgb_build")
@@ -196,20 +206,21 @@ class Context:
     def fit(self, layers, hits, p0, c0, p_out, c_out, chi2_out, status_out=None):
         n, m = layers.shape
         args = [_ptr(layers, np.int32), _ptr(hits, np.int32), _ptr(p0, np.float32), _ptr(c0, np.float32),
-                _ptr(p_out, np.float32), _ptr(c_out, np.float32), _ptr(chi2_out, np.float32),
-                _ptr(status_out, np.int32)]
+                _ptr(p_out, np.float32, True), _ptr(c_out, np.float32, True), _ptr(chi2_out, np.float32, True),
+                _ptr(status_out, np.int32, True)]
         self._check(self.lib.mkgb_fit(self.h, int(n), int(m), *[p for p, _ in args], _same(*[d for _, d in args])),
                     "mkgb_fit")
 
     def propagate(self, layers, p_in, c_in, p_out, c_out, crossed):
-        args = [_ptr(layers, np.int32), _ptr(p_in, np.float32), _ptr(c_in, np.float32), _ptr(p_out, np.float32),
-                _ptr(c_out, np.float32), _ptr(crossed, np.int32)]
+        args = [_ptr(layers, np.int32), _ptr(p_in, np.float32), _ptr(c_in, np.float32), _ptr(p_out, np.float32, True),
+                _ptr(c_out, np.float32, True), _ptr(crossed, np.int32, True)]
         self._check(self.lib.mkgb_propagate(self.h, int(layers.shape[0]), *[p for p, _ in args],
                                             _same(*[d for _, d in args])), "mkgb_propagate")
 
     def update(self, p_in, c_in, hxyz, hcov, p_out, c_out, chi2, ok):
         args = [_ptr(p_in, np.float32), _ptr(c_in, np.float32), _ptr(hxyz, np.float32), _ptr(hcov, np.float32),
-                _ptr(p_out, np.float32), _ptr(c_out, np.float32), _ptr(chi2, np.float32), _ptr(ok, np.int32)]
+                _ptr(p_out, np.float32, True), _ptr(c_out, np.float32, True), _ptr(chi2, np.float32, True),
+                _ptr(ok, np.int32, True)]
         self._check(self.lib.mkgb_update(self.h, int(p_in.shape[0]), *[p for p, _ in args],
                                          _same(*[d for _, d in args])), "mkgb_update")
 

@@ -67,4 +67,4 @@ def test_binding_refuses_mixed_host_and_device_arrays():
     with pytest.raises(mkgb.MkgbError):
         mkgb._same(True, False)
     with pytest.raises(mkgb.MkgbError):
-        mkgb._ptr(np.zeros(3, np.float64), np.float32)
+        mkgb._ptr(np.zeros(3, np.float64), np.float32, out=True)

@@ -14,6 +14,18 @@ from paper_2312_11728_gb300 import mkgb, pipeline, synth as S
 pytestmark = pytest.mark.gpu
 
 
+def _report(name, rep):
+    """Writes a comparison report to $MKGB_REPORT_DIR (if set) for offline diagnosis."""
+    import json
+    import os
+    d = os.environ.get("MKGB_REPORT_DIR")
+    if d:
+        os.makedirs(d, exist_ok=True)
+        with open(os.path.join(d, f"{name}.json"), "w") as f:
+            json.dump(rep, f, default=lambda o: o.tolist() if hasattr(o, "tolist") else str(o), indent=1)
+    return rep
+
+
 @pytest.fixture(scope="session")
 def lib():
     B.build()
@@ -121,6 +133,12 @@ def test_seed_states_match_oracle(lib, which, request):
                                            batch.seed_hits[batch.seed_event == e]) for e in range(batch.n_events)])
     r = orc.seed_batch(batch.seed_hits, sl, batch.hit_xyz.astype(np.float64), batch.hit_cov.astype(np.float64))
     info = res["seed_info"]
+    _report(f"seed_{which}", dict(region_mismatch=np.nonzero(info[:, 0] != r["region"])[0],
+                                 status_mismatch=np.nonzero(info[:, 2] != r["status"])[0],
+                                 worst_param=float(PR.param_close(res["seed_state"][r["status"] == 0],
+                                                                  r["p"][r["status"] == 0])[1].max()),
+                                 worst_cov=float(PR.cov_close(res["seed_cov"][r["status"] == 0],
+                                                              r["c"][r["status"] == 0])[1].max())))
     assert np.array_equal(info[:, 0], r["region"])
     assert np.array_equal(info[:, 1], r["start"])
     assert np.array_equal(info[:, 2], r["status"])
@@ -140,7 +158,7 @@ def test_fit_over_known_assignment_matches_oracle(lib, which, request):
     orc = oracle.Oracle(g, params)
     r = orc.fit_batch(fi.layers, fi.hits, batch.hit_xyz.astype(np.float64), batch.hit_cov.astype(np.float64),
                       fi.p0.astype(np.float64), fi.c0.astype(np.float64))
-    rep = PR.compare_fit(res["fit"], r)
+    rep = _report(f"fit_{which}", PR.compare_fit(res["fit"], r))
     assert rep["status_bad"] == 0, rep
     assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0, rep
     assert rep["n"] > 0.95 * fi.layers.shape[0]
@@ -155,7 +173,7 @@ def test_build_matches_oracle(lib, which, request):
     res = pipeline.run_host(ctx, batch, g.max_plan)
     orc = oracle.Oracle(g, params)
     o = PR.oracle_build(orc, batch)
-    rep = PR.compare_build(res["build"], o)
+    rep = _report(f"build_{which}", PR.compare_build(res["build"], o))
     assert len(rep["hit_mismatch"]) == 0, rep
     assert rep["failed_mismatch"] == 0, rep
     assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0 and rep["count_bad"] == 0, rep
@@ -255,7 +273,7 @@ def test_full_size_phase2_sampled_against_oracle(lib, phase2_full):
     sample = np.sort(rng.choice(batch.seed_hits.shape[0], 400, replace=False))
     orc = oracle.Oracle(g, params)
     o = PR.oracle_build(orc, batch, sample)
-    rep = PR.compare_build(gpu, o)
+    rep = _report("build_full_size", PR.compare_build(gpu, o))
     assert len(rep["hit_mismatch"]) == 0, rep
     assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0, rep
     tsample = np.sort(rng.choice(fi.layers.shape[0], 2000, replace=False))
@@ -263,5 +281,5 @@ def test_full_size_phase2_sampled_against_oracle(lib, phase2_full):
                       batch.hit_cov.astype(np.float64), fi.p0[tsample].astype(np.float64),
                       fi.c0[tsample].astype(np.float64))
     gf = {k: db.fit[k].cpu().numpy()[tsample] for k in ("p", "c", "chi2", "status")}
-    rep = PR.compare_fit(gf, r)
+    rep = _report("fit_full_size", PR.compare_fit(gf, r))
     assert rep["status_bad"] == 0 and rep["param_bad"] == 0 and rep["chi2_bad"] == 0, rep
