@@ -78,6 +78,8 @@ typedef struct {
     int32_t material;      /* 1: multiple scattering and energy loss at every crossed layer */
     int32_t precision;     /* MKGB_FP32: Kalman steps of the search and the fit in FP32 (seed fits in FP64);
                               MKGB_FP64: every step in FP64 (the plain comparison path) */
+    float kappa_fp64;      /* fit: a track with an update whose innovation covariance S has a condition
+                              estimate above this is refit in FP64; 0 = never */
 } mkgb_params;
 
 #define MKGB_FP32 0
@@ -142,7 +144,7 @@ int mkgb_build(mkgb_ctx* ctx, const mkgb_tracks* out, int on_device);
  * max_steps layers (layers[i*max_steps + j], -1 ends the list) taking hits[i*max_steps + j]
  * (-1: propagate only).  Outputs: p_out n x 6, c_out n x 21, chi2_out (sum of predicted chi2),
  * status_out (0 ok, 1 a listed layer was not crossed, 2 particle stopped, 3 update failed,
- * 4 hit index outside the loaded hits;
+ * 4 hit index outside the loaded hits; tracks above params.kappa_fp64 are refit in FP64;
  * NULL to skip).  Errors: MKGB_ESTATE without geometry/params, MKGB_EINVAL. */
 int mkgb_fit(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const int32_t* hits,
              const float* p0, const float* c0, float* p_out, float* c_out, float* chi2_out,

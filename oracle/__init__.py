@@ -56,7 +56,8 @@ class Params(C.Structure):
 
 class Tie(C.Structure):
     _fields_ = [("chi2_rel", C.c_double), ("win_abs", C.c_double), ("win_rel", C.c_double),
-                ("score_abs", C.c_double), ("score_rel", C.c_double), ("edge_rel", C.c_double)]
+                ("score_abs", C.c_double), ("score_rel", C.c_double), ("edge_rel", C.c_double),
+                ("kappa", C.c_double)]
 
 
 class BuildOut(C.Structure):
@@ -115,7 +116,8 @@ class Oracle:
         self.g = Geom(float(geom.bz), float(geom.barrel_eta_max), L, len(geom.plans),
                       self._layers, _p(self._plan, C.c_int), _p(self._plan_off, C.c_int))
         self.set_params(params or {})
-        t = dict(chi2_rel=1e-3, win_abs=1e-5, win_rel=1e-4, score_abs=2e-3, score_rel=1e-4, edge_rel=1e-5)
+        t = dict(chi2_rel=1e-3, win_abs=1e-5, win_rel=1e-4, score_abs=2e-3, score_rel=1e-4, edge_rel=1e-5,
+                 kappa=1e6)
         t.update(tie or {})
         self.tie = Tie(**t)
         self.lib = lib()

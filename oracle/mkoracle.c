@@ -679,6 +679,22 @@ static int cmp_ll(const void* a, const void* b) {
 
 static double gap_tol(const orc_tie* T, double s) { return fmax(T->score_abs, T->score_rel * fabs(s)); }
 
+/* Frobenius condition number ||S||_F ||S^-1||_F of the innovation covariance S = C_pos + V. */
+static double cond_frob(const double C[21], const double V[6]) {
+    double S[6], Lc[6], Si[3][3];
+    for (int i = 0; i < 6; ++i) S[i] = C[i] + V[i];
+    if (!chol3(S, Lc)) return INFINITY;
+    inv3_from_chol(Lc, Si);
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double sij = S[ix(i, j)];
+            a += sij * sij;
+            b += Si[i][j] * Si[i][j];
+        }
+    return sqrt(a * b);
+}
+
 int orc_build_event(const orc_geom* g, const orc_params* P, const orc_tie* T,
                     const long long* layer_off, const double* xyz, const double* cov,
                     int n_seeds, const int* seed_hits, const int* seed_layers,
@@ -824,6 +840,21 @@ int orc_build_event(const orc_geom* g, const orc_params* P, const orc_tie* T,
             for (int a = 0; a < amb.n; ++a) {
                 double thr = kids.n >= N ? kids.v[N - 1].score : -INFINITY;
                 if (amb.v[a].score >= thr - gap_tol(T, amb.v[a].score)) tie = 1;
+            }
+            if (tie && out->tie_step[si] < 0) out->tie_step[si] = t;
+
+            /* precision limit: an update (or, for a non-hit child, a prediction measured with the
+               layer's resolution) whose innovation covariance is too ill-conditioned for FP32 */
+            for (int q = 0; q < nkeep && !tie; ++q) {
+                child_t* k = &kids.v[q];
+                if (k->kind == K_SKIP || k->kind == K_CARRY) continue;
+                double Vc[6];
+                if (k->kind == K_HIT) {
+                    memcpy(Vc, &cov[6 * k->gid], sizeof(Vc));
+                } else {
+                    local_cov(L, atan2(pp[k->parent][1], pp[k->parent][0]), Vc);
+                }
+                if (cond_frob(CC[k->parent], Vc) > T->kappa) tie = 1;
             }
             if (tie && out->tie_step[si] < 0) out->tie_step[si] = t;
 

@@ -64,6 +64,8 @@ typedef struct {
     double score_abs;     /* score gap < max(score_abs, score_rel * |score|) */
     double score_rel;
     double edge_rel;      /* crossing point within edge_rel * |edge| of a layer boundary */
+    double kappa;         /* a kept child whose innovation covariance S = C_pos + V has a Frobenius
+                             condition number above this (FP32 cannot resolve its update) */
 } orc_tie;
 
 typedef struct {

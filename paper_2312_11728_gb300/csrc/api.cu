@@ -67,7 +67,7 @@ struct mkgb_ctx {
     DevBuf seg_off, in_xyz, in_cov, pay, ep_tmp, bin_of_hit, hit_seg, bins, hb_ep, hb_pay, cursor, scan_tmp;
     int n_seeds = 0;
     DevBuf seed_hits, seed_state, seed_info, seed_key, key_counts, key_cursor, seed_order, seed_scan_tmp;
-    DevBuf counters_build, counters_fit, queue;
+    DevBuf counters_build, counters_fit, queue, rescue_list, rescue_count;
     DevBuf stage[S_COUNT];
 };
 
@@ -189,7 +189,8 @@ void mkgb_destroy(mkgb_ctx* ctx) {
                          &ctx->bin_of_hit, &ctx->hit_seg, &ctx->bins, &ctx->hb_ep, &ctx->hb_pay, &ctx->cursor,
                          &ctx->scan_tmp, &ctx->seed_hits, &ctx->seed_state, &ctx->seed_info, &ctx->seed_key,
                          &ctx->key_counts, &ctx->key_cursor, &ctx->seed_order, &ctx->seed_scan_tmp,
-                         &ctx->counters_build, &ctx->counters_fit, &ctx->queue};
+                         &ctx->counters_build, &ctx->counters_fit, &ctx->queue, &ctx->rescue_list,
+                         &ctx->rescue_count};
         for (DevBuf* b : all) release(*b);
         for (auto& b : ctx->stage) release(b);
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -288,6 +289,8 @@ int mkgb_set_params(mkgb_ctx* ctx, const mkgb_params* p) {
     d.barrel_eta_max = p->barrel_eta_max;
     if (p->precision != MKGB_FP32 && p->precision != MKGB_FP64) return fail(ctx, MKGB_EINVAL, "bad precision %d", p->precision);
     d.precision = p->precision;
+    if (!(p->kappa_fp64 >= 0.0f)) return fail(ctx, MKGB_EINVAL, "kappa_fp64 must be >= 0");
+    d.kappa_fp64 = p->kappa_fp64;
     ctx->has_params = true;
     return MKGB_OK;
 }
@@ -454,10 +457,14 @@ int mkgb_fit(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const i
     CK(stage_out(ctx, S_G, chi2_out, 4 * N, on_device, &xo));
     CK(stage_out(ctx, S_H, status_out, 4 * N, on_device, &so));
     CK(cudaMemsetAsync(ctx->counters_fit.p, 0, 8 * kNumCounters, st));
-    CK(launch_fit(st, (const DevGeom*)ctx->geom_d.p, ctx->params, (const float4*)ctx->pay.p, ctx->has_hits ? ctx->n_hits : 0,
-                  n, max_steps,
-                  (const int*)dl, (const int*)dh, (const float*)dp0, (const float*)dc0, (float*)po, (float*)co,
-                  (float*)xo, (int*)so, (unsigned long long*)ctx->counters_fit.p));
+    CK(ensure(ctx->rescue_list, 4 * (N > 0 ? N : 1)));
+    CK(ensure(ctx->rescue_count, 16));
+    CK(cudaMemsetAsync(ctx->rescue_count.p, 0, 16, st));
+    CK(launch_fit(st, (const DevGeom*)ctx->geom_d.p, ctx->params, (const float4*)ctx->pay.p,
+                  ctx->has_hits ? ctx->n_hits : 0, n, max_steps, (const int*)dl, (const int*)dh, (const float*)dp0,
+                  (const float*)dc0, (float*)po, (float*)co, (float*)xo, (int*)so,
+                  (unsigned long long*)ctx->counters_fit.p, (int*)ctx->rescue_list.p, (int*)ctx->rescue_count.p,
+                  ctx->n_sms));
     CK(copy_back(ctx, p_out, po, 24 * N, on_device));
     CK(copy_back(ctx, c_out, co, 84 * N, on_device));
     CK(copy_back(ctx, chi2_out, xo, 4 * N, on_device));

@@ -3,6 +3,12 @@
 // Sec. 4: with faster building, the final fit becomes a comparably expensive step.  One
 // track per lane, the state stays in registers across all its layers; per step the lane
 // reads one 48-byte hit payload.  FP32-bound (a few hundred FMA per 52 bytes read).
+//
+// Mixed precision: the FP32 pass estimates the condition number of every innovation
+// covariance S from its Cholesky factor.  An update with kappa(S) near 1/eps_FP32 (a grazing
+// crossing whose along-track spread dwarfs the hit error) leaves FP32 rounding in the
+// posterior, so tracks above a threshold are appended to a list and a second kernel refits
+// them entirely in FP64 (the same code for double).  About 0.5% of tracks at kappa > 1e5.
 #include "internal.h"
 
 namespace mk {
@@ -18,61 +24,113 @@ __device__ __forceinline__ void load_geom(const DevGeom* __restrict__ gp, DevGeo
     __syncthreads();
 }
 
+// One track in precision F; returns its status and the largest kappa(S) of its updates.
 template <class F>
+__device__ __forceinline__ int fit_track(const DevGeom& g, const DevParams& P, const float4* __restrict__ pay,
+                                         int64_t n_hits, int max_steps, const int* __restrict__ lrow,
+                                         const int* __restrict__ hrow, const float* p0, const float* c0,
+                                         StateT<F>& t, F& sum, float& kmax, unsigned long long& c_steps,
+                                         unsigned long long& c_upd, int& c_newton) {
+    load_state6(p0, c0, t);
+    sum = F(0);
+    kmax = 0.0f;
+    for (int j = 0; j < max_steps; ++j) {
+        const int l = __ldg(lrow + j);
+        if (l < 0 || l >= g.n_layers) break;
+        const DevLayer& L = g.layers[l];
+        PredT<F> q;
+        const int r = propagate(L, g.cB, P.material, t, q, c_newton);
+        if (r != 1) return r == 0 ? 1 : 2;
+        ++c_steps;
+        const int h = __ldg(hrow + j);
+        if (h >= n_hits) {
+            pred_to_state(L.kind, q, t);
+            return 4;   // hit index outside the loaded hits
+        }
+        if (h >= 0) {
+            F m[3], v[6], x2;
+            float kap = 0.0f;
+            load_hit(pay, h, m, v, nullptr);
+            if (!chi2_hit(L.kind, q, m[0], m[1], m[2], v, x2) ||
+                !kalman_update(L.kind, q, m[0], m[1], m[2], v, t, &kap))
+                return 3;
+            kmax = fmaxf(kmax, kap);
+            sum += x2;
+            ++c_upd;
+        } else {
+            pred_to_state(L.kind, q, t);
+        }
+    }
+    return 0;
+}
+
 __global__ void __launch_bounds__(kThreads) k_fit(const DevGeom* __restrict__ gp, DevParams P,
                                                   const float4* __restrict__ pay, int64_t n_hits, int n, int max_steps,
                                                   const int* __restrict__ layers, const int* __restrict__ hits,
                                                   const float* __restrict__ p0, const float* __restrict__ c0,
                                                   float* __restrict__ p_out, float* __restrict__ c_out,
                                                   float* __restrict__ chi2_out, int* __restrict__ status_out,
-                                                  unsigned long long* counters) {
+                                                  unsigned long long* counters, int* rescue_list,
+                                                  int* rescue_count) {
     __shared__ DevGeom g;
     load_geom(gp, g);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long c_steps = 0, c_upd = 0;
     int c_newton = 0;
     if (i < n) {
-        StateT<F> t;
-        load_state6(p0 + 6 * (int64_t)i, c0 + 21 * (int64_t)i, t);
-        F sum = F(0);
-        int status = 0;
-        const int* lrow = layers + (int64_t)i * max_steps;
-        const int* hrow = hits + (int64_t)i * max_steps;
-        for (int j = 0; j < max_steps; ++j) {
-            const int l = __ldg(lrow + j);
-            if (l < 0 || l >= g.n_layers) break;
-            const DevLayer& L = g.layers[l];
-            PredT<F> q;
-            const int r = propagate(L, g.cB, P.material, t, q, c_newton);
-            if (r != 1) {
-                status = r == 0 ? 1 : 2;
-                break;
-            }
-            ++c_steps;
-            const int h = __ldg(hrow + j);
-            if (h >= n_hits) {
-                status = 4;   // hit index outside the loaded hits
-                pred_to_state(L.kind, q, t);
-                break;
-            }
-            if (h >= 0) {
-                F m[3], v[6], x2;
-                load_hit(pay, h, m, v, nullptr);
-                if (!chi2_hit(L.kind, q, m[0], m[1], m[2], v, x2) || !kalman_update(L.kind, q, m[0], m[1], m[2], v, t)) {
-                    status = 3;
-                    break;
-                }
-                sum += x2;
-                ++c_upd;
-            } else {
-                pred_to_state(L.kind, q, t);
-            }
+        State t;
+        float sum, kmax;
+        const int status = fit_track<float>(g, P, pay, n_hits, max_steps, layers + (int64_t)i * max_steps,
+                                            hits + (int64_t)i * max_steps, p0 + 6 * (int64_t)i, c0 + 21 * (int64_t)i,
+                                            t, sum, kmax, c_steps, c_upd, c_newton);
+        store_state6(t, p_out + 6 * (int64_t)i, c_out + 21 * (int64_t)i);
+        chi2_out[i] = sum;
+        if (status_out) status_out[i] = status;
+        if (rescue_list && P.kappa_fp64 > 0.0f && kmax > P.kappa_fp64) rescue_list[atomicAdd(rescue_count, 1)] = i;
+    }
+    if (counters) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            c_steps += __shfl_xor_sync(0xffffffffu, c_steps, off);
+            c_upd += __shfl_xor_sync(0xffffffffu, c_upd, off);
+            c_newton += __shfl_xor_sync(0xffffffffu, c_newton, off);
         }
+        if ((threadIdx.x & 31) == 0 && c_steps) {
+            atomicAdd(counters + 0, c_steps);
+            atomicAdd(counters + 1, c_upd);
+            atomicAdd(counters + 2, c_upd);
+            atomicAdd(counters + 4, (unsigned long long)c_newton);
+        }
+    }
+}
+
+// FP64 refit of the listed tracks (kappa rescue) or of all tracks (all-FP64 path, list == null).
+__global__ void __launch_bounds__(kThreads) k_fit64(const DevGeom* __restrict__ gp, DevParams P,
+                                                    const float4* __restrict__ pay, int64_t n_hits, int n,
+                                                    int max_steps, const int* __restrict__ layers,
+                                                    const int* __restrict__ hits, const float* __restrict__ p0,
+                                                    const float* __restrict__ c0, float* __restrict__ p_out,
+                                                    float* __restrict__ c_out, float* __restrict__ chi2_out,
+                                                    int* __restrict__ status_out, unsigned long long* counters,
+                                                    const int* __restrict__ list, const int* __restrict__ count) {
+    __shared__ DevGeom g;
+    load_geom(gp, g);
+    const int cnt = list ? *count : n;
+    unsigned long long c_steps = 0, c_upd = 0;
+    int c_newton = 0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < cnt; r += gridDim.x * blockDim.x) {
+        const int i = list ? list[r] : r;
+        StateT<double> t;
+        double sum;
+        float kmax;
+        const int status = fit_track<double>(g, P, pay, n_hits, max_steps, layers + (int64_t)i * max_steps,
+                                             hits + (int64_t)i * max_steps, p0 + 6 * (int64_t)i, c0 + 21 * (int64_t)i,
+                                             t, sum, kmax, c_steps, c_upd, c_newton);
         store_state6(t, p_out + 6 * (int64_t)i, c_out + 21 * (int64_t)i);
         chi2_out[i] = float(sum);
         if (status_out) status_out[i] = status;
     }
-    if (counters) {
+    if (counters && !list) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             c_steps += __shfl_xor_sync(0xffffffffu, c_steps, off);
@@ -146,17 +204,23 @@ __global__ void __launch_bounds__(kThreads) k_step_update(int n, const float* __
 }  // namespace
 
 cudaError_t launch_fit(cudaStream_t st, const DevGeom* g, DevParams P, const float4* pay, int64_t n_hits, int n,
-                       int max_steps,
-                       const int* layers, const int* hits, const float* p0, const float* c0, float* p_out,
-                       float* c_out, float* chi2_out, int* status_out, unsigned long long* counters) {
+                       int max_steps, const int* layers, const int* hits, const float* p0, const float* c0,
+                       float* p_out, float* c_out, float* chi2_out, int* status_out, unsigned long long* counters,
+                       int* rescue_list, int* rescue_count, int n_sms) {
     if (n == 0) return cudaSuccess;
     const int blocks = (n + kThreads - 1) / kThreads;
-    if (P.precision == MKGB_FP64)
-        k_fit<double><<<blocks, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p0, c0, p_out, c_out,
-                                                   chi2_out, status_out, counters);
-    else
-        k_fit<float><<<blocks, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p0, c0, p_out, c_out,
-                                                  chi2_out, status_out, counters);
+    if (P.precision == MKGB_FP64) {
+        k_fit64<<<blocks, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p0, c0, p_out, c_out,
+                                            chi2_out, status_out, counters, nullptr, nullptr);
+        return cudaGetLastError();
+    }
+    k_fit<<<blocks, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p0, c0, p_out, c_out, chi2_out,
+                                      status_out, counters, rescue_list, rescue_count);
+    if (P.kappa_fp64 > 0.0f && rescue_list) {
+        const int rb = blocks < 2 * n_sms ? blocks : 2 * n_sms;
+        k_fit64<<<rb, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p0, c0, p_out, c_out,
+                                        chi2_out, status_out, counters, rescue_list, rescue_count);
+    }
     return cudaGetLastError();
 }
 

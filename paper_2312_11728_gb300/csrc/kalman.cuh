@@ -68,6 +68,7 @@ struct DevParams {
     float nsig, deta_min, deta_max, dphi_min, dphi_max;
     float score_hit, score_hole, barrel_eta_max;
     int precision;      // MKGB_FP32: FP32 Kalman steps (FP64 seed fit); MKGB_FP64: every step in FP64
+    float kappa_fp64;   // fit: tracks with an update whose S condition estimate exceeds this are refit in FP64
 };
 
 // Packed lower-triangle index of a symmetric matrix (i, j >= 0).
@@ -81,8 +82,7 @@ template <class F> struct StateT {
 };
 
 // Predicted state at a layer surface; covariance of (u1, u2, k, phi, theta) where (u1, u2)
-// are surface coordinates:  barrel: u1 along e1 = (-y, x, 0)/r, u2 along z, normal
-// n = (x, y, 0)/r;  disk: u1 = x, u2 = y, normal z.
+// are coordinates along the surface frame axes e1, e2 (see frame_of).
 template <class F> struct PredT {
     F xh, yh, zh, xl, yl, zl, k, phi, th;
     F c[15];
@@ -182,73 +182,94 @@ template <class F> __device__ __forceinline__ void s1c1_deriv(F a, F S1, F C1, F
 }
 
 // ----------------------------------------------------------------- surface frame
+//
+// Orthonormal frame of a predicted state on its surface: n the surface normal, e1 the
+// direction of the track projected onto the surface, e2 = n x e1 (in the surface).  Aligning
+// e1 with the track keeps the large along-track spread of a grazing crossing in the u1
+// variance alone: the u2 row of the Jacobian has no path-length term, so no covariance entry
+// is a difference of large FP32 numbers.  Barrel n = (x, y, 0)/r, disk n = z-hat.
 
 template <class F> struct FrameT {
-    F c, s;    // barrel: n = (c, s, 0); unused for disks
-    int disk;
+    F n[3], e1[3], e2[3];
 };
 
-template <class F> __device__ __forceinline__ FrameT<F> frame_of(int kind, F x, F y) {
+template <class F> __device__ __forceinline__ FrameT<F> frame_of(int kind, F x, F y, F sphi, F cphi, F st, F ct) {
     FrameT<F> f;
-    f.disk = kind == MKGB_DISK;
-    const F ir = rsq(x * x + y * y);
-    f.c = x * ir;
-    f.s = y * ir;
+    if (kind == MKGB_DISK) {
+        f.n[0] = F(0); f.n[1] = F(0); f.n[2] = F(1);
+        f.e1[0] = cphi; f.e1[1] = sphi; f.e1[2] = F(0);
+        f.e2[0] = -sphi; f.e2[1] = cphi; f.e2[2] = F(0);
+    } else {
+        const F ir = rsq(x * x + y * y);
+        const F c = x * ir, s = y * ir;
+        // projection of the direction onto (t-hat = (-s, c, 0), z-hat)
+        F a = st * (c * sphi - s * cphi), b = ct;
+        const F nrm2 = a * a + b * b;
+        if (nrm2 > F(1e-12)) {
+            const F inv = rsq(nrm2);
+            a *= inv;
+            b *= inv;
+        } else {
+            a = F(1);
+            b = F(0);
+        }
+        f.n[0] = c; f.n[1] = s; f.n[2] = F(0);
+        f.e1[0] = -a * s; f.e1[1] = a * c; f.e1[2] = b;
+        f.e2[0] = b * s; f.e2[1] = -b * c; f.e2[2] = a;
+    }
     return f;
+}
+
+template <class F> __device__ __forceinline__ FrameT<F> frame_of(int kind, const PredT<F>& q) {
+    F sp, cp, st, ct;
+    sin_cos(q.phi, &sp, &cp);
+    sin_cos(q.th, &st, &ct);
+    return frame_of(kind, q.xh, q.yh, sp, cp, st, ct);
+}
+
+template <class F> __device__ __forceinline__ F dot3(const F a[3], const F b[3]) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
 }
 
 // global 3-vector -> local (n, e1, e2) components
 template <class F> __device__ __forceinline__ void to_local3(const FrameT<F>& f, const F g[3], F l[3]) {
-    if (f.disk) {
-        l[0] = g[2]; l[1] = g[0]; l[2] = g[1];
-    } else {
-        l[0] = f.c * g[0] + f.s * g[1];
-        l[1] = -f.s * g[0] + f.c * g[1];
-        l[2] = g[2];
-    }
+    l[0] = dot3(f.n, g);
+    l[1] = dot3(f.e1, g);
+    l[2] = dot3(f.e2, g);
 }
 
 // surface displacement (d1 along e1, d2 along e2) -> global
 template <class F> __device__ __forceinline__ void surface_to_global(const FrameT<F>& f, F d1, F d2, F g[3]) {
-    if (f.disk) {
-        g[0] = d1; g[1] = d2; g[2] = F(0);
-    } else {
-        g[0] = -f.s * d1; g[1] = f.c * d1; g[2] = d2;
-    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) g[i] = d1 * f.e1[i] + d2 * f.e2[i];
 }
 
-// packed 3x3 symmetric (xx, yx, yy, zx, zy, zz) global -> local frame
+// packed 3x3 symmetric (xx, yx, yy, zx, zy, zz) global -> local frame (n, e1, e2)
 template <class F> __device__ __forceinline__ void to_local_sym3(const FrameT<F>& f, const F v[6], F w[6]) {
-    if (f.disk) {   // (n, e1, e2) = (z, x, y)
-        w[0] = v[5]; w[1] = v[3]; w[2] = v[0]; w[3] = v[4]; w[4] = v[1]; w[5] = v[2];
-    } else {
-        const F c = f.c, s = f.s, cc = c * c, ss = s * s, cs = c * s;
-        w[0] = cc * v[0] + F(2) * cs * v[1] + ss * v[2];              // nn
-        w[1] = cs * (v[2] - v[0]) + (cc - ss) * v[1];                 // e1 n
-        w[2] = ss * v[0] - F(2) * cs * v[1] + cc * v[2];              // e1 e1
-        w[3] = c * v[3] + s * v[4];                                   // e2 n
-        w[4] = -s * v[3] + c * v[4];                                  // e2 e1
-        w[5] = v[5];                                                  // e2 e2
-    }
+    const F M[3][3] = {{v[0], v[1], v[3]}, {v[1], v[2], v[4]}, {v[3], v[4], v[5]}};
+    const F* R[3] = {f.n, f.e1, f.e2};
+    F MR[3][3];   // M R[b]
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) MR[b][i] = M[i][0] * R[b][0] + M[i][1] * R[b][1] + M[i][2] * R[b][2];
+#pragma unroll
+    for (int a2 = 0; a2 < 3; ++a2)
+#pragma unroll
+        for (int b = 0; b <= a2; ++b) w[ix(a2, b)] = dot3(R[a2], MR[b]);
 }
 
 // Surface-frame covariance (15) -> global state covariance (21).
 template <class F> __device__ __forceinline__ void embed_cov(const FrameT<F>& f, const F q[15], F c[21]) {
-    F E[3][2];
-    if (f.disk) {
-        E[0][0] = F(1); E[0][1] = F(0); E[1][0] = F(0); E[1][1] = F(1); E[2][0] = F(0); E[2][1] = F(0);
-    } else {
-        E[0][0] = -f.s; E[0][1] = F(0); E[1][0] = f.c; E[1][1] = F(0); E[2][0] = F(0); E[2][1] = F(1);
-    }
     const F cuu[2][2] = {{q[0], q[1]}, {q[1], q[2]}};
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        const F m0 = E[i][0] * cuu[0][0] + E[i][1] * cuu[1][0];
-        const F m1 = E[i][0] * cuu[0][1] + E[i][1] * cuu[1][1];
+        const F m0 = f.e1[i] * cuu[0][0] + f.e2[i] * cuu[1][0];
+        const F m1 = f.e1[i] * cuu[0][1] + f.e2[i] * cuu[1][1];
 #pragma unroll
-        for (int j = 0; j <= i; ++j) c[ix(i, j)] = m0 * E[j][0] + m1 * E[j][1];
+        for (int j = 0; j <= i; ++j) c[ix(i, j)] = m0 * f.e1[j] + m1 * f.e2[j];
 #pragma unroll
-        for (int o = 0; o < 3; ++o) c[ix(3 + o, i)] = E[i][0] * q[ix(2 + o, 0)] + E[i][1] * q[ix(2 + o, 1)];
+        for (int o = 0; o < 3; ++o) c[ix(3 + o, i)] = f.e1[i] * q[ix(2 + o, 0)] + f.e2[i] * q[ix(2 + o, 1)];
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -259,7 +280,7 @@ template <class F> __device__ __forceinline__ void embed_cov(const FrameT<F>& f,
 template <class F> __device__ __forceinline__ void pred_to_state(int kind, const PredT<F>& q, StateT<F>& t) {
     t.xh = q.xh; t.yh = q.yh; t.zh = q.zh; t.xl = q.xl; t.yl = q.yl; t.zl = q.zl;
     t.k = q.k; t.phi = q.phi; t.th = q.th;
-    embed_cov(frame_of(kind, q.xh, q.yh), q.c, t.c);
+    embed_cov(frame_of(kind, q), q.c, t.c);
 }
 
 // ----------------------------------------------------------------- propagation (a4-a7)
@@ -425,7 +446,6 @@ __device__ __forceinline__ int propagate(const DevLayer& L, float cBf, int mater
     const F A04 = -dy, A14 = dx;
     const F A25 = -s / (st * st);
     const F A43 = -cB * s;
-    const FrameT<F> fr = frame_of(L.kind, xh, yh);
     F ds[6];
     if (L.kind == MKGB_BARREL) {
         const F ig = F(-1) / (xh * cfp + yh * sfp);
@@ -438,22 +458,23 @@ __device__ __forceinline__ int propagate(const DevLayer& L, float cBf, int mater
         ds[0] = F(0); ds[1] = F(0); ds[2] = ig;
         ds[3] = F(0); ds[4] = F(0); ds[5] = A25 * ig;
     }
-    // surface rows: barrel u1 = -s x + c y (along e1), u2 = z; disk u1 = x, u2 = y.  The row
-    // along the normal vanishes by the surface constraint and is not formed.
-    const F f1 = fr.disk ? cfp : (-fr.s * cfp + fr.c * sfp);
-    const F f2 = fr.disk ? sfp : cot;
-    const F fs[3] = {f1, f2, om};   // df/ds along u1, u2, phi
+    // Rows of the fixed-s Jacobian for x, y, z (identity + A terms), projected on e1 and e2.
+    // df/ds along the position is the track direction / sin(theta), whose surface projection
+    // lies along e1: the path-length term enters u1 only (e2 . df/ds = 0 by construction).
+    const FrameT<F> fr = frame_of(L.kind, xh, yh, sfp, cfp, st, ct);
+    const F Apos[3][6] = {{F(1), F(0), F(0), A03, A04, F(0)},
+                          {F(0), F(1), F(0), A13, A14, F(0)},
+                          {F(0), F(0), F(1), F(0), F(0), A25}};
+    const F fpos[3] = {cfp, sfp, cot};
+    const F f1 = dot3(fr.e1, fpos);
     F J[3][6];
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int j = 0; j < 6; ++j) J[r][j] = fs[r] * ds[j];
-    if (fr.disk) {
-        J[0][0] += F(1); J[0][3] += A03; J[0][4] += A04;
-        J[1][1] += F(1); J[1][3] += A13; J[1][4] += A14;
-    } else {
-        J[0][0] -= fr.s; J[0][1] += fr.c; J[0][3] += -fr.s * A03 + fr.c * A13; J[0][4] += -fr.s * A04 + fr.c * A14;
-        J[1][2] += F(1); J[1][5] += A25;
+    for (int j = 0; j < 6; ++j) {
+        const F a1 = fr.e1[0] * Apos[0][j] + fr.e1[1] * Apos[1][j] + fr.e1[2] * Apos[2][j];
+        const F a2 = fr.e2[0] * Apos[0][j] + fr.e2[1] * Apos[1][j] + fr.e2[2] * Apos[2][j];
+        J[0][j] = fma(f1, ds[j], a1);
+        J[1][j] = a2;
+        J[2][j] = om * ds[j];
     }
     J[2][3] += A43; J[2][4] += F(1);
 
@@ -512,14 +533,11 @@ __device__ __forceinline__ Window window(const DevLayer& L, const DevParams& P, 
     float ve = ge_r * ge_r * sr2 + ge_z * ge_z * sz2;
     float vp = gp_p * gp_p * sp2;
     // surface part: gradient components along e1, e2
-    float ge1, ge2, gp1, gp2;
-    if (L.kind == MKGB_DISK) {         // e1 = x-hat, e2 = y-hat
-        ge1 = ge_r * c; ge2 = ge_r * sn;
-        gp1 = -gp_p * sn; gp2 = gp_p * c;
-    } else {                           // e1 = phi-hat, e2 = z-hat
-        ge1 = 0.0f; ge2 = ge_z;
-        gp1 = gp_p; gp2 = 0.0f;
-    }
+    const FrameT<float> fr = frame_of(L.kind, q);
+    const float geg[3] = {ge_r * c, ge_r * sn, ge_z};       // eta gradient, global
+    const float gpg[3] = {-gp_p * sn, gp_p * c, 0.0f};     // phi gradient, global
+    const float ge1 = dot3(fr.e1, geg), ge2 = dot3(fr.e2, geg);
+    const float gp1 = dot3(fr.e1, gpg), gp2 = dot3(fr.e2, gpg);
     ve += ge1 * ge1 * q.c[0] + 2.0f * ge1 * ge2 * q.c[1] + ge2 * ge2 * q.c[2];
     vp += gp1 * gp1 * q.c[0] + 2.0f * gp1 * gp2 * q.c[1] + gp2 * gp2 * q.c[2];
     w.deta = fminf(fmaxf(P.nsig * sqrtf(fmaxf(ve, 0.0f)), P.deta_min), P.deta_max);
@@ -558,7 +576,7 @@ __device__ __forceinline__ void local_meas(const FrameT<F>& f, const PredT<F>& q
 
 template <class F>
 __device__ __forceinline__ bool chi2_hit(int kind, const PredT<F>& q, F mx, F my, F mz, const F v[6], F& chi2) {
-    const FrameT<F> f = frame_of(kind, q.xh, q.yh);
+    const FrameT<F> f = frame_of(kind, q);
     F rl[3], vl[6], S[6], L[6], inv[3];
     local_meas(f, q, mx, my, mz, v, rl, vl, S);
     if (!chol3(S, L, inv)) return false;
@@ -573,13 +591,19 @@ __device__ __forceinline__ bool chi2_hit(int kind, const PredT<F>& q, F mx, F my
 // K = C H^T S^-1 (H picks u1, u2 into measurement rows e1, e2; the normal row is zero),
 // C+ = (I - K H) C (I - K H)^T + K V K^T; the result is returned as a global-frame state.
 // Returns false if S is not positive definite or theta leaves (0, pi).
+// kappa (optional) gets (max L_ii / min L_ii)^2 of the Cholesky factor of S, an estimate of its
+// condition number.
 template <class F>
 __device__ __forceinline__ bool kalman_update(int kind, const PredT<F>& q, F mx, F my, F mz, const F v[6],
-                                              StateT<F>& out) {
-    const FrameT<F> f = frame_of(kind, q.xh, q.yh);
+                                              StateT<F>& out, float* kappa = nullptr) {
+    const FrameT<F> f = frame_of(kind, q);
     F rl[3], vl[6], S[6], L[6], inv[3];
     local_meas(f, q, mx, my, mz, v, rl, vl, S);
     if (!chol3(S, L, inv)) return false;
+    if (kappa) {
+        const F lmax = fmax(fmax(L[0], L[2]), L[5]), lmin = fmin(fmin(L[0], L[2]), L[5]);
+        *kappa = float((lmax / lmin) * (lmax / lmin));
+    }
     // W = S^-1 = L^-T L^-1
     const F i00 = inv[0], i11 = inv[1], i22 = inv[2];
     const F i10 = -L[1] * i00 * i11;

@@ -33,7 +33,7 @@ class Params(C.Structure):
                 ("win_nsigma", C.c_float), ("deta_min", C.c_float), ("deta_max", C.c_float),
                 ("dphi_min", C.c_float), ("dphi_max", C.c_float), ("score_hit", C.c_float),
                 ("score_hole", C.c_float), ("barrel_eta_max", C.c_float), ("material", C.c_int32),
-                ("precision", C.c_int32)]
+                ("precision", C.c_int32), ("kappa_fp64", C.c_float)]
 
 
 class Tracks(C.Structure):
@@ -174,7 +174,8 @@ class Context:
                    float(params["win_nsigma"]), float(params["deta_min"]), float(params["deta_max"]),
                    float(params["dphi_min"]), float(params["dphi_max"]), float(params["score_hit"]),
                    float(params["score_hole"]), float(params.get("barrel_eta_max", self.barrel_eta_max)),
-                   int(params["material"]), int(params.get("precision", 0)))
+                   int(params["material"]), int(params.get("precision", 0)),
+                   float(params.get("kappa_fp64", 0.0)))
         self._check(self.lib.mkgb_set_params(self.h, C.byref(p)), "mkgb_set_params")
 
     # ---- data
