@@ -117,7 +117,7 @@ class Oracle:
                       self._layers, _p(self._plan, C.c_int), _p(self._plan_off, C.c_int))
         self.set_params(params or {})
         t = dict(chi2_rel=1e-3, win_abs=1e-5, win_rel=1e-4, score_abs=2e-3, score_rel=1e-4, edge_rel=1e-5,
-                 kappa=1e6)
+                 kappa=2.0 ** 24)
         t.update(tie or {})
         self.tie = Tie(**t)
         self.lib = lib()

@@ -385,8 +385,12 @@ int orc_chi2(const double p[6], const double C[21], const double m[3], const dou
 }
 
 /* Kalman update: K = C H^T S^-1, p+ = p + K r, and either C+ = C - K S K^T (standard)
- * or C+ = (I - K H) C (I - K H)^T + K V K^T (Joseph).  phi is wrapped to (-pi, pi];
- * returns 0 if S is not positive definite or theta leaves (0, pi). */
+ * or C+ = (I - K H) C (I - K H)^T + K V K^T (Joseph).  Both are the same posterior; the
+ * oracle's searches, seeds and fits use the Joseph form, whose result is first-order
+ * insensitive to errors in K: when S is ill-conditioned (a grazing crossing with a prior
+ * spread of ~10 cm against 30 um hits, condition ~1e7) the standard form loses ~1e-2 of the
+ * posterior even in FP64.  phi is wrapped to (-pi, pi]; returns 0 if S is not positive
+ * definite or theta leaves (0, pi). */
 int orc_update(const double p[6], const double C[21], const double m[3], const double V[6],
                int joseph, double pout[6], double Cout[21], double* chi2) {
     double S[6], Lc[6], Si[3][3];
@@ -491,10 +495,10 @@ int orc_seed(const orc_geom* g, int material, const double h[9], const double V[
     Cq[ix(0, 0)] = 0.01; Cq[ix(1, 1)] = 0.01; Cq[ix(2, 2)] = 0.01;
     Cq[ix(3, 3)] = sk * sk; Cq[ix(4, 4)] = 0.0025; Cq[ix(5, 5)] = 0.0025;
     double pu[6], Cu[21], pp[6], Cp[21], s;
-    if (!orc_update(q, Cq, &h[0], &V[0], 0, pu, Cu, NULL)) return 0;
+    if (!orc_update(q, Cq, &h[0], &V[0], 1, pu, Cu, NULL)) return 0;
     for (int j = 1; j < 3; ++j) {
         if (orc_propagate(g, layers[j], pu, Cu, material, pp, Cp, &s) != 1) return 0;
-        if (!orc_update(pp, Cp, &h[3 * j], &V[6 * j], 0, pu, Cu, NULL)) return 0;
+        if (!orc_update(pp, Cp, &h[3 * j], &V[6 * j], 1, pu, Cu, NULL)) return 0;
     }
     memcpy(p, pu, sizeof(pu));
     memcpy(C, Cu, sizeof(Cu));
@@ -547,7 +551,7 @@ void orc_fit_batch(const orc_geom* g, int material, int n, int max_steps, const 
             int h = hits[(long long)i * max_steps + j];
             if (h >= 0) {
                 double x2;
-                if (!orc_update(pp, Cp, &xyz[3 * (long long)h], &cov[6 * (long long)h], 0, q, Cq, &x2)) {
+                if (!orc_update(pp, Cp, &xyz[3 * (long long)h], &cov[6 * (long long)h], 1, q, Cq, &x2)) {
                     st = 3;
                     break;
                 }
@@ -871,7 +875,7 @@ int orc_build_event(const orc_geom* g, const orc_params* P, const orc_tie* T,
                 nc->stopped = par->stopped;
                 if (k->kind == K_HIT) {
                     double x2;
-                    if (!orc_update(pp[k->parent], CC[k->parent], &xyz[3 * k->gid], &cov[6 * k->gid], 0,
+                    if (!orc_update(pp[k->parent], CC[k->parent], &xyz[3 * k->gid], &cov[6 * k->gid], 1,
                                     nc->p, nc->C, &x2))
                         continue;
                     ctr[2]++;

@@ -65,7 +65,8 @@ typedef struct {
     double score_rel;
     double edge_rel;      /* crossing point within edge_rel * |edge| of a layer boundary */
     double kappa;         /* a kept child whose innovation covariance S = C_pos + V has a Frobenius
-                             condition number above this (FP32 cannot resolve its update) */
+                             condition number above this (default 2^24 = 1/eps of FP32, where an FP32
+                             update cannot resolve the posterior) */
 } orc_tie;
 
 typedef struct {

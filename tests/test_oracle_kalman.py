@@ -179,3 +179,33 @@ def test_covariances_are_psd_with_the_surface_normal_as_null_direction(smeared_f
         n = np.array([p[0], p[1], 0.0]) / np.hypot(p[0], p[1])
         assert n @ M[:3, :3] @ n < 1e-6 * np.trace(M[:3, :3])
         assert np.all(np.linalg.eigvalsh(M[:3, :3] + np.diag([9e-6, 9e-6, 1e-4])) > 0)
+
+
+def test_update_is_accurate_when_the_innovation_covariance_is_ill_conditioned(orc):
+    """A prior spread of 10 cm along one surface direction against a 30 um hit gives cond(S) ~ 1e7.
+    The oracle's update must match a 50-digit evaluation of the same posterior."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    rng = np.random.default_rng(21)
+    for _ in range(5):
+        u = rng.standard_normal(3); u[2] = 0.3 * u[2]; u /= np.linalg.norm(u)
+        sig = np.array([100.0, 0.05, 1e-2, 1e-3, 3e-3, 1e-3])
+        A = rng.standard_normal((6, 6)) * 0.3 + np.eye(6)
+        C = A @ np.diag(sig ** 2) @ A.T
+        C[:3, :3] += 150.0 * np.outer(u, u)
+        V = np.diag([9e-6, 9e-6, 1e-4])
+        p = np.array([60.0, 80.0, 100.0, -1.5, -2.5, 1.0])
+        m = p[:3] + 0.003
+        ok, po, co, x2 = orc.update(p, C[np.tril_indices(6)], m, V[np.tril_indices(3)], joseph=True)
+        assert ok
+        Cm, Vm = mp.matrix(C.tolist()), mp.matrix(V.tolist())
+        H = mp.matrix(np.hstack([np.eye(3), np.zeros((3, 3))]).tolist())
+        S = H * Cm * H.T + Vm
+        K = Cm * H.T * mp.inverse(S)
+        Cx = Cm - K * S * K.T
+        ref = np.array([[float(Cx[i, j]) for j in range(6)] for i in range(6)])
+        got = sym(co)
+        scale = np.sqrt(np.outer(np.diag(ref), np.diag(ref)))
+        assert np.all(np.abs(got - ref) <= 1e-7 * scale + 1e-20)
+        kk = np.linalg.cond(S.tolist() and np.array([[float(S[i, j]) for j in range(3)] for i in range(3)]))
+        assert kk > 1e6
