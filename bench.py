@@ -33,7 +33,7 @@ WORKLOAD = "phase2_like_64ev_20k_tracks_50k_noise_bestN6"
 # Algorithmic FP32 operations per unit of work (FMA = 2), counted from the kernel source
 # (csrc/kalman.cuh); multi-function-unit work (sqrt, rsqrt, division, sincos, log, atan2) is
 # not counted.  Derivation in the design doc.
-FLOPS = dict(step=730, newton=22, tested=6, chi2=46, update=770)
+FLOPS = dict(step=560, newton=30, tested=6, chi2=160, update=700)
 
 
 def build_flops(c):
@@ -204,7 +204,8 @@ def main():
     __graft_entry__.build()
     from paper_2312_11728_gb300 import mkgb
 
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(stream)
     ctx = pipeline.make_context(g, params, device=local, stream=stream)
     db = pipeline.DeviceBatch(batch, fit, g.max_plan, f"cuda:{local}")
     n_seeds = batch.seed_hits.shape[0]

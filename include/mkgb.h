@@ -97,8 +97,9 @@ typedef struct {
     int32_t max_plan;      /* row stride of hits, >= the longest plan */
 } mkgb_tracks;
 
-/* Creates a context on `device` that launches on `stream` (a cudaStream_t; NULL = a stream
- * the context creates).  Errors: MKGB_EINVAL (out == NULL), MKGB_ECUDA. */
+/* Creates a context on `device` that launches on `stream` (a cudaStream_t, including
+ * cudaStreamLegacy or cudaStreamPerThread; NULL = a non-blocking stream the context creates).
+ * Errors: MKGB_EINVAL (out == NULL), MKGB_ECUDA. */
 int mkgb_create(mkgb_ctx** out, int device, void* stream);
 void mkgb_destroy(mkgb_ctx* ctx);
 /* Message of the last failing call on this context (static text for a NULL context). */

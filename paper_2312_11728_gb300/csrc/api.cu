@@ -2,6 +2,7 @@
 // Declarations and argument contracts: include/mkgb.h.
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -312,10 +313,16 @@ int mkgb_load_hits(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const fl
     if (nbins > ((int64_t)1 << 31) - 2) return fail(ctx, MKGB_EINVAL, "too many bins (%lld)", (long long)nbins);
     DevGuard guard(ctx->device);
     cudaStream_t st = ctx->stream;
-    CK(cudaStreamSynchronize(st));   // seg_off_h may still feed an earlier async copy
-    ctx->seg_off_h.assign(seg_off, seg_off + nseg + 1);
-    CK(ensure(ctx->seg_off, 8 * (nseg + 1)));
-    CK(cudaMemcpyAsync(ctx->seg_off.p, ctx->seg_off_h.data(), 8 * (nseg + 1), cudaMemcpyHostToDevice, st));
+    // The offsets are copied only when they change (a repeated batch costs no host round trip).
+    // A copy from pageable memory returns once the source has been staged, so the host vector
+    // may be rewritten after the call.
+    const bool same = ctx->seg_off_h.size() == (size_t)(nseg + 1) && ctx->seg_off.p &&
+                      std::equal(seg_off, seg_off + nseg + 1, ctx->seg_off_h.begin());
+    if (!same) {
+        ctx->seg_off_h.assign(seg_off, seg_off + nseg + 1);
+        CK(ensure(ctx->seg_off, 8 * (nseg + 1)));
+        CK(cudaMemcpyAsync(ctx->seg_off.p, ctx->seg_off_h.data(), 8 * (nseg + 1), cudaMemcpyHostToDevice, st));
+    }
     const float* dx = xyz;
     const float* dc = cov6;
     if (!on_device && n > 0) {

@@ -121,15 +121,18 @@ class Context:
         self.lib = load_library()
         h = C.c_void_p()
         s = None
-        if stream is not None:
-            s = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
-        else:
+        if stream is None:
             try:
                 import torch
                 if torch.cuda.is_available():
-                    s = C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+                    stream = torch.cuda.current_stream(device)
             except ImportError:
                 pass
+        if stream is not None:
+            handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+            # torch's default stream has handle 0, which the library reads as "create a stream":
+            # pass cudaStreamLegacy (1) so both launch on the same stream
+            s = C.c_void_p(handle if handle else 1)
         rc = self.lib.mkgb_create(C.byref(h), int(device), s)
         if rc != 0:
             raise MkgbError(f"mkgb_create failed ({ERRORS.get(rc, rc)})")
