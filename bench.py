@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Kalman propagate+χ²+update steps/s on 1 GB300; % of FP32/HBM roofline"
 UNIT = "Kalman steps/s"
 N_EVENTS, N_TRACKS, N_NOISE = 64, 20000, 50000
-WORKLOAD = "phase2_like_64ev_20k_tracks_50k_noise_bestN6"
+WORKLOAD = "phase2_like_{events}ev_20k_tracks_50k_noise_bestN6"
 
 # Algorithmic FP32 operations per unit of work (FMA = 2), counted from the kernel source
 # (csrc/kalman.cuh); multi-function-unit work (sqrt, rsqrt, division, sincos, log, atan2) is
@@ -168,10 +168,53 @@ def run_reference(args, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": sample},
+            "config": {"workload": WORKLOAD.format(events=N_EVENTS), "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def measure_e2e(args, ctx, db, batch, fit, g, stream, kalman_steps, world, local, dist):
+    """The same pass through the C ABI with host (pinned) buffers: every step copies its inputs in
+    and its results out inside the timed region."""
+    import torch
+    from paper_2312_11728_gb300 import mkgb
+    n_seeds = batch.seed_hits.shape[0]
+    n_tracks = fit.layers.shape[0]
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h = dict(xyz=pin(batch.hit_xyz), cov=pin(batch.hit_cov), seeds=pin(batch.seed_hits), layers=pin(fit.layers),
+             hits=pin(fit.hits), p0=pin(fit.p0), c0=pin(fit.c0))
+    ho = {k: torch.from_numpy(v).pin_memory() for k, v in mkgb.alloc_tracks(n_seeds, g.max_plan).items()}
+    hf = dict(p=torch.zeros((n_tracks, 6), dtype=torch.float32).pin_memory(),
+              c=torch.zeros((n_tracks, 21), dtype=torch.float32).pin_memory(),
+              chi2=torch.zeros(n_tracks, dtype=torch.float32).pin_memory(),
+              status=torch.zeros(n_tracks, dtype=torch.int32).pin_memory())
+    h2d = sum(v.numel() * v.element_size() for v in h.values())
+    d2h = sum(v.numel() * v.element_size() for v in ho.values()) + sum(v.numel() * v.element_size() for v in hf.values())
+
+    def e2e_step():
+        ctx.load_hits(db.n_events, db.seg_off, h["xyz"], h["cov"])
+        ctx.seed(h["seeds"])
+        ctx.build(ho)
+        ctx.fit(h["layers"], h["hits"], h["p0"], h["c0"], hf["p"], hf["c"], hf["chi2"], hf["status"])
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_e2e = max(1, min(args.steps, 5))
+    e0.record(stream)
+    for _ in range(n_e2e):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    te = torch.tensor([e0.elapsed_time(e1) / 1e3], device=f"cuda:{local}", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    return {"value": kalman_steps * n_e2e * world / float(te.item()), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h)}
 
 
 def main():
@@ -181,6 +224,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--events", type=int, default=N_EVENTS, help="events per batch (profiling of small cases)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -190,7 +235,7 @@ def main():
         return
 
     from paper_2312_11728_gb300 import pipeline, synth as S
-    g, batch = make_batch(seed=rank)          # before the first CUDA call (spawn pool)
+    g, batch = make_batch(seed=rank, n_events=args.events)   # before the first CUDA call (spawn pool)
     fit = pipeline.fit_inputs(batch, seed=rank)
     params = S.default_params()
 
@@ -254,39 +299,9 @@ def main():
     value = kalman_steps * args.steps * world / wall
 
     # ---- end to end through the C ABI with host (pinned) buffers, copies inside the timed region
-    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-    h = dict(xyz=pin(batch.hit_xyz), cov=pin(batch.hit_cov), seeds=pin(batch.seed_hits), layers=pin(fit.layers),
-             hits=pin(fit.hits), p0=pin(fit.p0), c0=pin(fit.c0))
-    ho = {k: torch.from_numpy(v).pin_memory() for k, v in mkgb.alloc_tracks(n_seeds, g.max_plan).items()}
-    hf = dict(p=torch.zeros((n_tracks, 6), dtype=torch.float32).pin_memory(),
-              c=torch.zeros((n_tracks, 21), dtype=torch.float32).pin_memory(),
-              chi2=torch.zeros(n_tracks, dtype=torch.float32).pin_memory(),
-              status=torch.zeros(n_tracks, dtype=torch.int32).pin_memory())
-    h2d = sum(v.numel() * v.element_size() for v in h.values())
-    d2h = sum(v.numel() * v.element_size() for v in ho.values()) + sum(v.numel() * v.element_size() for v in hf.values())
-
-    def e2e_step():
-        ctx.load_hits(db.n_events, db.seg_off, h["xyz"], h["cov"])
-        ctx.seed(h["seeds"])
-        ctx.build(ho)
-        ctx.fit(h["layers"], h["hits"], h["p0"], h["c0"], hf["p"], hf["c"], hf["chi2"], hf["status"])
-
-    for _ in range(max(1, args.warmup)):
-        e2e_step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    n_e2e = max(1, min(args.steps, 5))
-    e0.record(stream)
-    for _ in range(n_e2e):
-        e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    te = torch.tensor([e0.elapsed_time(e1) / 1e3], device=f"cuda:{local}", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = kalman_steps * n_e2e * world / float(te.item())
+    e2e = None
+    if not args.no_e2e:
+        e2e = measure_e2e(args, ctx, db, batch, fit, g, stream, kalman_steps, world, local, dist)
 
     if rank != 0:
         if dist:
@@ -309,7 +324,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "events": batch.n_events, "tracks_per_event": N_TRACKS,
+        "config": {"workload": WORKLOAD.format(events=batch.n_events), "events": batch.n_events, "tracks_per_event": N_TRACKS,
                    "noise_hits_per_event": N_NOISE, "layers": g.n_layers, "best_n": params["max_cands"],
                    "seeds": int(n_seeds), "fit_tracks": int(n_tracks), "hits": int(batch.hit_xyz.shape[0]),
                    "kalman_steps_per_step": kalman_steps, "build_steps": int(bc[0]), "fit_steps": int(fc[0]),
@@ -320,7 +335,7 @@ def main():
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                      "peak_note": f"FP32: {n_sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz ({src} max clock)",
                      "flops_per_launch": int(build_flops(bc))},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "e2e": e2e,
         "gpu_launches": int(launches_per_step * args.steps),
         "clocks": clocks,
         "counters": {"build": [int(x) for x in bc], "fit": [int(x) for x in fc]},

@@ -8,7 +8,8 @@
 // covariance S from its Cholesky factor.  An update with kappa(S) near 1/eps_FP32 (a grazing
 // crossing whose along-track spread dwarfs the hit error) leaves FP32 rounding in the
 // posterior, so tracks above a threshold are appended to a list and a second kernel refits
-// them entirely in FP64 (the same code for double).  About 0.5% of tracks at kappa > 1e5.
+// them entirely in FP64 (the same code for double).  The default threshold is 2^24, where the
+// innovation covariance's condition reaches 1/eps of FP32.
 #include "internal.h"
 
 namespace mk {
