@@ -111,12 +111,13 @@ __global__ void __launch_bounds__(kThreads) k_build(BuildArgs a) {
             float nh_score = -kBig;
             bool crossed = false;
             Pred q;
+            float dir[4];
             if (gact && alive) {
                 if (stopped) {
                     nh_kind = K_CARRY;
                     nh_score = score;
                 } else {
-                    const int r = propagate(L, g.cB, P.material, t, q, c_newton);
+                    const int r = propagate(L, g.cB, P.material, t, q, c_newton, dir);
                     if (r < 0) {
                         alive = false;
                     } else if (r == 0) {
@@ -146,7 +147,8 @@ __global__ void __launch_bounds__(kThreads) k_build(BuildArgs a) {
                 lq[j] = 0;
             }
             if (crossed) {
-                const Window w = window(L, P, q);
+                const FrameT<float> fr = frame_of(L.kind, q.xh, q.yh, dir[0], dir[1], dir[2], dir[3]);
+                const Window w = window(L, P, q, fr);
                 const float eps = 1e-5f;
                 const float fe0 = (w.eta - w.deta - eps - L.eta_lo) * L.eta_scale;
                 const float fe1 = (w.eta + w.deta + eps - L.eta_lo) * L.eta_scale;
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(kThreads) k_build(BuildArgs a) {
                                 int id;
                                 load_hit(a.H.hb_pay, hq, m, v, &id);
                                 float x2;
-                                if (chi2_hit(L.kind, q, m[0], m[1], m[2], v, x2) && x2 < P.chi2_cut) {
+                                if (chi2_hit(fr, q, m[0], m[1], m[2], v, x2) && x2 < P.chi2_cut) {
                                     int qq = hq;
 #pragma unroll
                                     for (int j = 0; j < kGroup; ++j) {

@@ -20,6 +20,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include "trig.cuh"
 #include <math.h>
 #include <stdint.h>
 
@@ -101,9 +103,15 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
-__device__ __forceinline__ void sin_cos(float x, float* s, float* c) { sincosf(x, s, c); }
+// FP32: reduction by pi/2 and Taylor series (trig.cuh), no large-argument path
+__device__ __forceinline__ void sin_cos(float x, float* s, float* c) { sin_cos_cw(x, s, c); }
 __device__ __forceinline__ void sin_cos(double x, double* s, double* c) { sincos(x, s, c); }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+// Logarithm inside the material terms (Highland's log correction, Bethe-Bloch's log term): an
+// absolute error of ~1e-6 there moves theta0 and dE/dx by ~1e-7 relative, so FP32 takes the
+// hardware logarithm (__logf, at most 3 ulp off outside [0.5, 2]).
+__device__ __forceinline__ float log_mat(float x) { return __logf(x); }
+__device__ __forceinline__ double log_mat(double x) { return log(x); }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 
 template <class F> __device__ __forceinline__ void two_sum(F a, F b, F& s, F& e) {
@@ -154,16 +162,6 @@ template <class F> __device__ __forceinline__ void s1c1(F a, F& S1, F& C1) {
         S1 = F(2) * sh * ch * inv;
         C1 = F(2) * sh * sh * inv;
     }
-}
-
-// sin(a/2) / (a/2)
-template <class F> __device__ __forceinline__ F sinc_half(F a) {
-    const F h = F(0.5) * a;
-    if (fabs(h) < F(0.05)) {
-        const F h2 = h * h;
-        return F(1) + h2 * (F(-1) / F(6) + h2 * (F(1) / F(120) + h2 * (F(-1) / F(5040) + h2 * (F(1) / F(362880)))));
-    }
-    return sin(h) / h;
 }
 
 // Derivatives of S1 and C1 with respect to a (power series for small |a|).
@@ -305,7 +303,7 @@ __device__ __forceinline__ bool apply_material(const DevLayer& L, PredT<F>& q, F
     const F e2 = pm * pm + P::mpi * P::mpi;
     const F beta2 = pm * pm / e2;
     const F beta = sqrt(beta2);
-    const F th0 = F(0.0136) / (beta * pm) * sqrt(tt) * (F(1) + F(0.038) * log(tt / beta2));
+    const F th0 = F(0.0136) / (beta * pm) * sqrt(tt) * (F(1) + F(0.038) * log_mat(tt / beta2));
     const F th02 = th0 * th0;
     const F kc = k * (ct / st);
     q.c[ix(3, 3)] += th02 / (st * st);
@@ -318,7 +316,7 @@ __device__ __forceinline__ bool apply_material(const DevLayer& L, PredT<F>& q, F
     const F gam = e * (F(1) / P::mpi);
     const F rme = P::me / P::mpi;
     const F tmax = F(2) * P::me * bg2 / (F(1) + F(2) * gam * rme + rme * rme);
-    const F dedx = P::K * P::ZA / beta2 * (F(0.5) * log(F(2) * P::me * bg2 * tmax / (P::I * P::I)) - beta2);
+    const F dedx = P::K * P::ZA / beta2 * (F(0.5) * log_mat(F(2) * P::me * bg2 * tmax / (P::I * P::I)) - beta2);
     const F de = dedx * P::rho * (tt * P::X0) * F(1e-3);
     const F en = e - de;
     if (!(en > P::mpi)) return false;
@@ -331,9 +329,10 @@ __device__ __forceinline__ bool apply_material(const DevLayer& L, PredT<F>& q, F
 
 // Propagates t to layer L.  Returns 1 (crossed; q holds the predicted state with material),
 // 0 (not crossed) or -1 (particle stopped in the material).  newton_it counts iterations.
+// dir (optional) gets sin(phi'), cos(phi'), sin(theta), cos(theta) at the crossing.
 template <class F>
 __device__ __forceinline__ int propagate(const DevLayer& L, float cBf, int material, const StateT<F>& t, PredT<F>& q,
-                                         int& newton_it) {
+                                         int& newton_it, F* dir = nullptr) {
     using P = Phys<F>;
     const F cB = F(cBf);
     F sf, cf, st, ct;
@@ -365,15 +364,25 @@ __device__ __forceinline__ int propagate(const DevLayer& L, float cBf, int mater
         const F tol = sizeof(F) == 4 ? F(1e-6) : F(1e-13);
         for (int it = 0; it < 60; ++it) {
             ++newton_it;
-            s1c1(om * s, S1, C1);
+            const F a = om * s;
+            // one sine/cosine of the half angle per iterate: S1, C1 and the direction at s follow
+            F sh, ch;
+            sin_cos(F(0.5) * a, &sh, &ch);
+            const F sa = F(2) * sh * ch, oc = F(2) * sh * sh;   // sin(a), 1 - cos(a)
+            if (fabs(a) < F(1e-4)) {
+                S1 = F(1) - a * a * (F(1) / F(6));
+                C1 = a * (F(0.5) - a * a * (F(1) / F(24)));
+            } else {
+                S1 = sa / a;
+                C1 = oc / a;
+            }
             dx = s * (cf * S1 - sf * C1);
             dy = s * (sf * S1 + cf * C1);
             // g(s) = |u + d|^2 - R^2 = 2 u.d + |d|^2 - c0 (terms of size |u||d|, not R^2)
             const F g = F(2) * (ux * dx + uy * dy) + (dx * dx + dy * dy) - c0;
             if (g == F(0)) break;
             if (g < F(0)) lo = s; else hi = s;
-            F spn, cpn;
-            sin_cos(t.phi + om * s, &spn, &cpn);
+            const F cpn = cf * (F(1) - oc) - sf * sa, spn = sf * (F(1) - oc) + cf * sa;   // direction at s
             const F dg = F(2) * ((ux + dx) * cpn + (uy + dy) * spn);
             F sn = (dg > F(0)) ? s - g / dg : F(0.5) * (lo + hi);
             if (!(sn >= lo && sn <= hi)) sn = F(0.5) * (lo + hi);
@@ -398,17 +407,31 @@ __device__ __forceinline__ int propagate(const DevLayer& L, float cBf, int mater
         }
     }
     const F a = om * s;
-    s1c1(a, S1, C1);
+    F sh, ch;
+    sin_cos(F(0.5) * a, &sh, &ch);
+    const F sa = F(2) * sh * ch, ca = fma(F(-2) * sh, sh, F(1));   // sin(a), cos(a)
+    if (fabs(a) < F(1e-4)) {
+        S1 = F(1) - a * a * (F(1) / F(6));
+        C1 = a * (F(0.5) - a * a * (F(1) / F(24)));
+    } else {
+        S1 = sa / a;
+        C1 = F(2) * sh * sh / a;
+    }
     {
-        // chord form: d = s sinc(a/2) (cos psi, sin psi) with psi = phi + a/2 kept as an unrounded
-        // sum; sin and cos of psi get the first-order correction for its low part
-        F psh, psl;
-        two_sum(t.phi, F(0.5) * a, psh, psl);
-        F sp, cp;
-        sin_cos(psh, &sp, &cp);
-        const F chord = s * sinc_half(a);
-        dx = chord * fma(-sp, psl, cp);
-        dy = chord * fma(cp, psl, sp);
+        // chord form: d = s sinc(a/2) (cos psi, sin psi) with psi = phi + a/2; sin and cos of psi
+        // by the angle-addition formulas, so psi is never rounded
+        const F sp = fma(sf, ch, cf * sh), cp = fma(cf, ch, -sf * sh);
+        const F h = F(0.5) * a;
+        F sinc;
+        if (fabs(h) < F(0.05)) {
+            const F h2 = h * h;
+            sinc = F(1) + h2 * (F(-1) / F(6) + h2 * (F(1) / F(120) + h2 * (F(-1) / F(5040) + h2 * (F(1) / F(362880)))));
+        } else {
+            sinc = sh / h;
+        }
+        const F chord = s * sinc;
+        dx = chord * cp;
+        dy = chord * sp;
     }
     const F cot = ct / st;
     const F dz = (L.kind == MKGB_BARREL) ? s * cot : sub_rn(sub_rn(zd, t.zh), t.zl);
@@ -416,26 +439,22 @@ __device__ __forceinline__ int propagate(const DevLayer& L, float cBf, int mater
     add_ff(xh, xl, dx);
     add_ff(yh, yl, dy);
     add_ff(zh, zl, dz);
+    const F sfp = fma(sf, ca, cf * sa), cfp = fma(cf, ca, -sf * sa);   // direction at the crossing
     if (L.kind == MKGB_BARREL) {
-        // polish: the Newton residual carries ~eps |u||d| of rounding, i.e. the point sits up to
-        // a few 1e-6 cm (FP32) off the cylinder along the normal, where the hit error is 30 um;
-        // the gap R^2 - r'^2 of the compensated position is exact to ~eps^2, so one more step
-        // along the track puts the predicted point on the surface
-        F spn, cpn;
-        sin_cos(t.phi + a, &spn, &cpn);
+        // polish: the Newton iterate carries ~1e-6 relative error (FP32 tolerance), i.e.
+        // the point may sit ~1e-5 cm off the cylinder along the normal, where the hit error is
+        // 30 um; the gap R^2 - r'^2 of the compensated position is exact to ~eps^2, so one
+        // more Newton step along the track puts the predicted point on the surface
         const F gap = r2_gap(Rl, xh, xl, yh, yl);
-        const F dsp = gap / (F(2) * (xh * cpn + yh * spn));
-        add_ff(xh, xl, dsp * cpn);
-        add_ff(yh, yl, dsp * spn);
+        const F dsp = gap / (F(2) * (xh * cfp + yh * sfp));
+        add_ff(xh, xl, dsp * cfp);
+        add_ff(yh, yl, dsp * sfp);
         add_ff(zh, zl, dsp * cot);
         if (!(zh >= F(L.lo) && zh <= F(L.hi))) return 0;
     } else {
         const F r = sqrt(xh * xh + yh * yh);
         if (!(r >= F(L.lo) && r <= F(L.hi))) return 0;
     }
-    const F phin = t.phi + a;
-    F sfp, cfp;
-    sin_cos(phin, &sfp, &cfp);
     if (L.kind == MKGB_DISK && xh * cfp + yh * sfp < F(0)) return 0;   // moving inward: past the apex
 
     // ---- Jacobian rows x, y, z, phi: J = A + (df/ds)(ds/dp); rows k, theta are identity
@@ -507,8 +526,11 @@ __device__ __forceinline__ int propagate(const DevLayer& L, float cBf, int mater
     q.c[ix(4, 4)] = t.c[ix(5, 5)];
     q.xh = xh; q.xl = xl; q.yh = yh; q.yl = yl; q.zh = zh; q.zl = zl;
     q.k = t.k;
-    q.phi = wrap_pi(phin);
+    q.phi = wrap_pi(t.phi + a);
     q.th = t.th;
+    if (dir) {
+        dir[0] = sfp; dir[1] = cfp; dir[2] = st; dir[3] = ct;
+    }
     if (material && !apply_material(L, q, st, ct, sfp, cfp)) return -1;
     return 1;
 }
@@ -519,7 +541,8 @@ struct Window {
     float eta, phi, deta, dphi;
 };
 
-__device__ __forceinline__ Window window(const DevLayer& L, const DevParams& P, const Pred& q) {
+__device__ __forceinline__ Window window(const DevLayer& L, const DevParams& P, const Pred& q,
+                                         const FrameT<float>& fr) {
     const float x = q.xh, y = q.yh, z = q.zh;
     const float rt2 = x * x + y * y, rt = sqrtf(rt2), r3 = sqrtf(rt2 + z * z);
     Window w;
@@ -533,7 +556,6 @@ __device__ __forceinline__ Window window(const DevLayer& L, const DevParams& P, 
     float ve = ge_r * ge_r * sr2 + ge_z * ge_z * sz2;
     float vp = gp_p * gp_p * sp2;
     // surface part: gradient components along e1, e2
-    const FrameT<float> fr = frame_of(L.kind, q);
     const float geg[3] = {ge_r * c, ge_r * sn, ge_z};       // eta gradient, global
     const float gpg[3] = {-gp_p * sn, gp_p * c, 0.0f};     // phi gradient, global
     const float ge1 = dot3(fr.e1, geg), ge2 = dot3(fr.e2, geg);
@@ -575,8 +597,8 @@ __device__ __forceinline__ void local_meas(const FrameT<F>& f, const PredT<F>& q
 }
 
 template <class F>
-__device__ __forceinline__ bool chi2_hit(int kind, const PredT<F>& q, F mx, F my, F mz, const F v[6], F& chi2) {
-    const FrameT<F> f = frame_of(kind, q);
+__device__ __forceinline__ bool chi2_hit(const FrameT<F>& f, const PredT<F>& q, F mx, F my, F mz, const F v[6],
+                                         F& chi2) {
     F rl[3], vl[6], S[6], L[6], inv[3];
     local_meas(f, q, mx, my, mz, v, rl, vl, S);
     if (!chol3(S, L, inv)) return false;
@@ -585,6 +607,11 @@ __device__ __forceinline__ bool chi2_hit(int kind, const PredT<F>& q, F mx, F my
     const F y2 = (rl[2] - L[3] * y0 - L[4] * y1) * inv[2];
     chi2 = y0 * y0 + y1 * y1 + y2 * y2;
     return true;
+}
+
+template <class F>
+__device__ __forceinline__ bool chi2_hit(int kind, const PredT<F>& q, F mx, F my, F mz, const F v[6], F& chi2) {
+    return chi2_hit(frame_of(kind, q), q, mx, my, mz, v, chi2);
 }
 
 // Kalman update of a predicted state with one hit, Joseph form in the surface frame:
