@@ -151,6 +151,33 @@ int mkgb_fit(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const i
              const float* p0, const float* c0, float* p_out, float* c_out, float* chi2_out,
              int32_t* status_out, int on_device);
 
+/* Kalman fit over a known assignment that allocates nothing.  The paper has no counterpart:
+ * this is a library service, not a step of the method.  Same arguments, outputs and
+ * arithmetic as mkgb_fit with on_device = 1 (every array a device pointer on the context's
+ * device; status_out may be NULL), but the call makes no device allocation or free: its
+ * scratch (work counters, the FP64 refit counter and the refit list) is a fixed file-scope
+ * device array of about 256 KB per device, sized for at most 65536 tracks per call.  It is
+ * meant for callers that must not allocate while they run: cudaMalloc and cudaFree can
+ * synchronise the whole device and can fail while a caching allocator (PyTorch's, a serving
+ * pool) holds the free memory, so a stream-ordered loop that fits batch after batch keeps its
+ * memory footprint fixed by calling this entry point instead.
+ * Setup: the first call on a device looks up the scratch address (cudaGetSymbolAddress) and
+ * keeps it for the process; make that first call before any stream capture begins.
+ * Zero state: the work counters and the refit counter must be zero when a fit starts; the call
+ * clears them itself (cudaMemsetAsync on the context's stream) before its kernels, and the
+ * refit list needs no initial value.
+ * Concurrency: all calls on one device share the one scratch array, so two calls whose work
+ * overlaps in time (other streams, other contexts, other host threads) race on it and give
+ * wrong results; order them on one stream or synchronise between them.
+ * The call is asynchronous with respect to the host (outputs are ready when the context's
+ * stream reaches them); mkgb_counters does not report it.
+ * Errors: MKGB_EINVAL for n > 65536 (the message names the limit; split the batch or use
+ * mkgb_fit), a negative size or a NULL array; MKGB_ESTATE without geometry, params or hits;
+ * MKGB_ECUDA if the scratch lookup or a launch fails. */
+int mkgb_fit_static(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const int32_t* hits,
+                    const float* p0, const float* c0, float* p_out, float* c_out, float* chi2_out,
+                    int32_t* status_out);
+
 /* Single propagation step (Sec. 3.1 propagation; a4-a7): n states to the given layers.
  * crossed_out: 1 crossed, 0 not crossed (state copied through), -1 stopped. */
 int mkgb_propagate(mkgb_ctx* ctx, int n, const int32_t* layers, const float* p_in,

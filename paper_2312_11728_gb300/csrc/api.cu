@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -477,6 +478,57 @@ int mkgb_fit(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const i
     CK(copy_back(ctx, chi2_out, xo, 4 * N, on_device));
     CK(copy_back(ctx, status_out, so, 4 * N, on_device));
     if (!on_device) CK(cudaStreamSynchronize(st));
+    return MKGB_OK;
+}
+
+namespace {
+
+// Per-device address of the static fit scratch, looked up on the first mkgb_fit_static call on
+// that device and kept for the life of the process.
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_base[kMaxDevices] = {};
+
+cudaError_t static_scratch(int device, void** out) {
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_base[device]) {
+        void* p = nullptr;
+        const cudaError_t e = fit_static_scratch_address(&p);
+        if (e != cudaSuccess) return e;
+        g_static_base[device] = p;
+    }
+    *out = g_static_base[device];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+int mkgb_fit_static(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const int32_t* hits,
+                    const float* p0, const float* c0, float* p_out, float* c_out, float* chi2_out,
+                    int32_t* status_out) {
+    if (!ctx) return MKGB_EINVAL;
+    if (!ctx->has_geom || !ctx->has_params) return fail(ctx, MKGB_ESTATE, "fit before geometry/params");
+    if (!ctx->has_hits) return fail(ctx, MKGB_ESTATE, "fit with device hit indices before load_hits");
+    if (n < 0 || max_steps < 0) return fail(ctx, MKGB_EINVAL, "negative size");
+    if (n > kFitStaticMaxTracks)
+        return fail(ctx, MKGB_EINVAL, "mkgb_fit_static: %d tracks exceed its static scratch limit of %d; "
+                    "split the batch or call mkgb_fit", n, kFitStaticMaxTracks);
+    if (n > 0 && (!layers || !hits || !p0 || !c0 || !p_out || !c_out || !chi2_out))
+        return fail(ctx, MKGB_EINVAL, "null fit array");
+    DevGuard guard(ctx->device);
+    void* base = nullptr;
+    CK(static_scratch(ctx->device, &base));
+    if (n == 0) return MKGB_OK;
+    unsigned char* b = static_cast<unsigned char*>(base);
+    cudaStream_t st = ctx->stream;
+    // the work counters and the refit counter start at zero on every call
+    CK(cudaMemsetAsync(b, 0, kFitStaticZeroBytes, st));
+    CK(launch_fit(st, (const DevGeom*)ctx->geom_d.p, ctx->params, (const float4*)ctx->pay.p, ctx->n_hits, n,
+                  max_steps, layers, hits, p0, c0, p_out, c_out, chi2_out, status_out,
+                  reinterpret_cast<unsigned long long*>(b + kFitStaticCountersOff),
+                  reinterpret_cast<int*>(b + kFitStaticListOff), reinterpret_cast<int*>(b + kFitStaticRescueCountOff),
+                  ctx->n_sms));
     return MKGB_OK;
 }
 

@@ -69,6 +69,17 @@ cudaError_t launch_build(cudaStream_t st, const DevGeom* g, int max_plan_len, De
                          BuildOutDev out, int* queue, unsigned long long* counters, int n_sms);
 
 // ---- k_fit.cu
+// Static scratch of mkgb_fit_static: [0, 64) work counters (kNumCounters x u64), [64, 80) the
+// FP64 refit counter, [256, 256 + 4 * kFitStaticMaxTracks) the refit list.  The counters and the
+// refit counter must be zero when a fit starts; the list needs no initial value.
+constexpr int kFitStaticMaxTracks = 1 << 16;
+constexpr size_t kFitStaticCountersOff = 0, kFitStaticRescueCountOff = 64, kFitStaticListOff = 256;
+constexpr size_t kFitStaticZeroBytes = 128;
+constexpr size_t kFitStaticScratchBytes = kFitStaticListOff + 4 * (size_t)kFitStaticMaxTracks;
+static_assert(8 * kNumCounters <= (int)kFitStaticRescueCountOff, "counters overlap the refit counter");
+// Device address of that scratch on the current device (cudaGetSymbolAddress).
+cudaError_t fit_static_scratch_address(void** base);
+
 cudaError_t launch_fit(cudaStream_t st, const DevGeom* g, DevParams P, const float4* pay, int64_t n_hits, int n,
                        int max_steps, const int* layers, const int* hits, const float* p0, const float* c0,
                        float* p_out, float* c_out, float* chi2_out, int* status_out, unsigned long long* counters,

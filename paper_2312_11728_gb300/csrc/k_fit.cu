@@ -225,6 +225,15 @@ cudaError_t launch_fit(cudaStream_t st, const DevGeom* g, DevParams P, const flo
     return cudaGetLastError();
 }
 
+// Scratch of mkgb_fit_static, the fit entry point that allocates nothing: a file-scope device
+// array holding the work counters, the FP64 refit counter and the refit list for at most
+// kFitStaticMaxTracks tracks (layout in internal.h).  Its address is looked up, not allocated.
+static __device__ __align__(256) unsigned char g_fit_static_scratch[kFitStaticScratchBytes];
+
+cudaError_t fit_static_scratch_address(void** base) {
+    return cudaGetSymbolAddress(base, g_fit_static_scratch);
+}
+
 cudaError_t launch_step_propagate(cudaStream_t st, const DevGeom* g, DevParams P, int n, const int* layers,
                                   const float* p_in, const float* c_in, float* p_out, float* c_out, int* crossed) {
     if (n == 0) return cudaSuccess;

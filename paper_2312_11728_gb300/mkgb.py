@@ -42,8 +42,8 @@ class Tracks(C.Structure):
 
 
 EXPORTS = ["mkgb_create", "mkgb_destroy", "mkgb_last_error", "mkgb_version", "mkgb_load_geometry",
-           "mkgb_set_params", "mkgb_load_hits", "mkgb_seed", "mkgb_build", "mkgb_fit", "mkgb_propagate",
-           "mkgb_update", "mkgb_counters"]
+           "mkgb_set_params", "mkgb_load_hits", "mkgb_seed", "mkgb_build", "mkgb_fit", "mkgb_fit_static",
+           "mkgb_propagate", "mkgb_update", "mkgb_counters"]
 
 _lib = None
 
@@ -74,6 +74,7 @@ def load_library(path: str = LIB_PATH):
     lib.mkgb_seed.argtypes = [vp, i32, vp, i32, vp, vp, vp]
     lib.mkgb_build.argtypes = [vp, C.POINTER(Tracks), i32]
     lib.mkgb_fit.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32]
+    lib.mkgb_fit_static.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.mkgb_propagate.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, i32]
     lib.mkgb_update.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32]
     lib.mkgb_counters.argtypes = [vp, i32, vp]
@@ -214,6 +215,17 @@ class Context:
                 _ptr(status_out, np.int32, True)]
         self._check(self.lib.mkgb_fit(self.h, int(n), int(m), *[p for p, _ in args], _same(*[d for _, d in args])),
                     "mkgb_fit")
+
+    def fit_static(self, layers, hits, p0, c0, p_out, c_out, chi2_out, status_out=None):
+        """mkgb_fit_static: the fit without device allocations (device tensors only, at most
+        65536 tracks; calls on one device must not overlap in time)."""
+        n, m = layers.shape
+        args = [_ptr(layers, np.int32), _ptr(hits, np.int32), _ptr(p0, np.float32), _ptr(c0, np.float32),
+                _ptr(p_out, np.float32, True), _ptr(c_out, np.float32, True), _ptr(chi2_out, np.float32, True),
+                _ptr(status_out, np.int32, True)]
+        if _same(*[d for _, d in args]) != 1:
+            raise MkgbError("mkgb_fit_static takes CUDA tensors only")
+        self._check(self.lib.mkgb_fit_static(self.h, int(n), int(m), *[p for p, _ in args]), "mkgb_fit_static")
 
     def propagate(self, layers, p_in, c_in, p_out, c_out, crossed):
         args = [_ptr(layers, np.int32), _ptr(p_in, np.float32), _ptr(c_in, np.float32), _ptr(p_out, np.float32, True),
