@@ -69,7 +69,7 @@ struct mkgb_ctx {
     DevBuf seg_off, in_xyz, in_cov, pay, ep_tmp, bin_of_hit, hit_seg, bins, hb_ep, hb_pay, cursor, scan_tmp;
     int n_seeds = 0;
     DevBuf seed_hits, seed_state, seed_info, seed_key, key_counts, key_cursor, seed_order, seed_scan_tmp;
-    DevBuf counters_build, counters_fit, queue, rescue_list, rescue_count;
+    DevBuf counters_build, counters_fit, queue, rescue_list, rescue_count, build_work;
     DevBuf stage[S_COUNT];
 };
 
@@ -192,7 +192,7 @@ void mkgb_destroy(mkgb_ctx* ctx) {
                          &ctx->scan_tmp, &ctx->seed_hits, &ctx->seed_state, &ctx->seed_info, &ctx->seed_key,
                          &ctx->key_counts, &ctx->key_cursor, &ctx->seed_order, &ctx->seed_scan_tmp,
                          &ctx->counters_build, &ctx->counters_fit, &ctx->queue, &ctx->rescue_list,
-                         &ctx->rescue_count};
+                         &ctx->rescue_count, &ctx->build_work};
         for (DevBuf* b : all) release(*b);
         for (auto& b : ctx->stage) release(b);
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -422,10 +422,11 @@ int mkgb_build(mkgb_ctx* ctx, const mkgb_tracks* out, int on_device) {
     d.max_plan = out->max_plan;
     SeedStore S{ctx->n_seeds, (const float*)ctx->seed_state.p, (const int4*)ctx->seed_info.p,
                 (const int*)ctx->seed_order.p};
-    CK(cudaMemsetAsync(ctx->queue.p, 0, 16, st));
+    CK(ensure(ctx->build_work, build_work_bytes(ctx->n_seeds, ctx->max_plan_len)));
+    const BuildWork w = carve_build_work(ctx->build_work.p, ctx->n_seeds, ctx->max_plan_len);
     CK(cudaMemsetAsync(ctx->counters_build.p, 0, 8 * kNumCounters, st));
-    CK(launch_build(st, (const DevGeom*)ctx->geom_d.p, ctx->max_plan_len, ctx->params, hit_store(ctx), S, d,
-                    (int*)ctx->queue.p, (unsigned long long*)ctx->counters_build.p, ctx->n_sms));
+    CK(launch_build(st, (const DevGeom*)ctx->geom_d.p, ctx->max_plan_len, ctx->params, hit_store(ctx), S, d, w,
+                    (unsigned long long*)ctx->counters_build.p, ctx->n_sms));
     CK(copy_back(ctx, out->params, d.params, 24 * n, on_device));
     CK(copy_back(ctx, out->cov, d.cov, 84 * n, on_device));
     CK(copy_back(ctx, out->chi2, d.chi2, 4 * n, on_device));

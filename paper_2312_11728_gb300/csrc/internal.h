@@ -45,6 +45,20 @@ struct BuildOutDev {
     int max_plan;
 };
 
+// Work buffers of the search (k_build.cu): per seed 8 candidate slots, double-buffered.
+struct BuildWork {
+    float4* st[2];    // slot states, 8 float4 each
+    int4* meta[2];    // slot (score, chi2 sum, nfound | nholes << 8 | stopped << 16, alive)
+    float4* pr;       // slot predictions at the round's layer, 6 float4 each
+    int4* ls;         // slot children: (n hits, non-hit kind, non-hit score, -) + 4 x (chi2, hit, chi2, hit)
+    int* live[2];     // work list of live candidate slots per round
+    int* seeds[2];    // work list of seeds with a live candidate per round
+    int4* sinfo;      // per ordered seed: (plan position of its first step, first step, steps, event)
+    int* fin;         // per ordered seed: buffer holding its final slots, -1 none
+    int* trail;       // per ordered seed: longest plan x 8 ints ((code + 4) << 3 | parent slot)
+    int* counts;      // [live0, live1, seeds0, seeds1]
+};
+
 // counters (64-bit): [0] steps, [1] chi2 evaluations, [2] updates, [3] hits tested, [4] Newton iterations
 constexpr int kNumCounters = 5;
 
@@ -65,8 +79,10 @@ cudaError_t launch_seed(cudaStream_t st, const DevGeom* g, DevParams P, HitStore
                         int* info3);
 
 // ---- k_build.cu
+size_t build_work_bytes(int n_seeds, int max_plan_len);
+BuildWork carve_build_work(void* base, int n_seeds, int max_plan_len);
 cudaError_t launch_build(cudaStream_t st, const DevGeom* g, int max_plan_len, DevParams P, HitStore H, SeedStore S,
-                         BuildOutDev out, int* queue, unsigned long long* counters, int n_sms);
+                         BuildOutDev out, BuildWork w, unsigned long long* counters, int n_sms);
 
 // ---- k_fit.cu
 // Static scratch of mkgb_fit_static: [0, 64) work counters (kNumCounters x u64), [64, 80) the

@@ -1,33 +1,33 @@
-// Combinatorial forward search (Sec. 2.2), one persistent fused kernel.
+// Combinatorial forward search (Sec. 2.2) as layer-synchronous rounds of two kernels.
 //
-// Work unit: a group of 8 lanes owns one seed and holds its (at most 8) candidates, one
-// per lane, in registers for the whole layer plan; a warp serves 4 seeds at a time and
-// takes the next 4 from a global atomic work counter, in the (event, eta, phi) order of
-// the seeds so that neighbouring warps read neighbouring hit bins.  Per plan step:
-//   1. each live candidate propagates to the step's layer with Jacobian, transport and
-//      material (a4-a7);
-//   2. it scans the eta-phi bins overlapping its window, tests each hit against the
-//      window and computes the 3D chi2 of the hits inside (a8-a9), keeping its best
-//      hit children in a sorted register list;
-//   3. the group merges its lanes' children into the N best of the seed with 64-bit
-//      (score, parent slot) keys reduced by warp shuffles (a10);
-//   4. lane r takes the r-th child: pulls the parent's predicted state by shuffles and
-//      applies the Joseph update with the child's hit (a11);
-//   5. (parent slot, hit) of every kept child goes to a shared-memory trail, walked back
-//      at the end for the best candidate's hit list (a13).
-// No global state is read or written between layers: per seed, the only HBM traffic is
-// the hit bins it scans, the seed state in and the result out.  There are no waits on
-// other warps or CTAs; every loop is bounded by the plan length, the window's bin range
-// or a fixed Newton iteration limit.
+// All seeds of all events advance together, one step of their layer plan per round (the
+// paper's search processes every candidate of a layer before the next, Sec. 3.1).  A seed owns
+// 8 candidate slots; per round:
+//   k_find    one thread per live candidate, taken from a compacted work list: propagation with
+//             Jacobian, transport and material (a4-a7), the eta-phi window (a8) and the chi2 of
+//             each hit inside it (a9).  Writes the predicted state (surface frame) and the
+//             candidate's children: its best hits (chi2 asc, hit id asc) and its non-hit child;
+//   k_select  eight lanes per seed (lane = parent slot): merges the children of the seed's
+//             candidates into the N best with 64-bit (score, parent slot) keys reduced by warp
+//             shuffles (a10); lane r takes the r-th child, applies the Joseph update with its hit
+//             from the parent's prediction (a11), writes slot r of the next round's buffers and
+//             (parent slot, hit) to the trail, and appends the child to the next work lists.
+// k_start fills round 0 from the seed states; k_finish picks each seed's best candidate and walks
+// the trail back for its hit list (a13).
+//
+// Slot records are array-of-structures in HBM: a state is 32 floats (xh, yh, zh, xl, yl, zl, k,
+// phi, theta, 21 covariance terms, 2 spare), a prediction 24 floats, a child list 20 ints, the
+// slot's (score, chi2 sum, counts, alive) one int4.  Work lists are filled with warp-aggregated
+// atomics, so the threads of a warp read neighbouring slots.  No kernel waits on another block;
+// every loop is bounded by a list length, a window's bin range or the Newton iteration limit.
 #include "internal.h"
 
 namespace mk {
 
 namespace {
 
-constexpr int kGroup = 8;                  // lanes per seed (>= MKGB_MAX_CANDS)
-constexpr int kWarps = 4;                  // warps per CTA
-constexpr int kThreads = kWarps * 32;
+constexpr int kGroup = 8;   // slots (lanes) per seed, >= MKGB_MAX_CANDS
+constexpr int kThreads = 128;
 constexpr float kBig = 3.0e38f;
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -40,164 +40,255 @@ __device__ __forceinline__ unsigned long long order_key(float score, int slot) {
 __device__ __forceinline__ float shfl_f(float v, int src) { return __shfl_sync(kFull, v, src); }
 __device__ __forceinline__ int shfl_i(int v, int src) { return __shfl_sync(kFull, v, src); }
 
+// ---- slot records
+
+__device__ __forceinline__ void load_state_rec(const float4* __restrict__ r, State& t) {
+    float f[32];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const float4 v = r[i];
+        f[4 * i] = v.x; f[4 * i + 1] = v.y; f[4 * i + 2] = v.z; f[4 * i + 3] = v.w;
+    }
+    t.xh = f[0]; t.yh = f[1]; t.zh = f[2]; t.xl = f[3]; t.yl = f[4]; t.zl = f[5];
+    t.k = f[6]; t.phi = f[7]; t.th = f[8];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) t.c[i] = f[9 + i];
+}
+
+__device__ __forceinline__ void store_state_rec(float4* __restrict__ r, const State& t) {
+    float f[32];
+    f[0] = t.xh; f[1] = t.yh; f[2] = t.zh; f[3] = t.xl; f[4] = t.yl; f[5] = t.zl;
+    f[6] = t.k; f[7] = t.phi; f[8] = t.th;
+#pragma unroll
+    for (int i = 0; i < 21; ++i) f[9 + i] = t.c[i];
+    f[30] = 0.0f; f[31] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) r[i] = make_float4(f[4 * i], f[4 * i + 1], f[4 * i + 2], f[4 * i + 3]);
+}
+
+__device__ __forceinline__ void load_pred_rec(const float4* __restrict__ r, Pred& q) {
+    float f[24];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const float4 v = r[i];
+        f[4 * i] = v.x; f[4 * i + 1] = v.y; f[4 * i + 2] = v.z; f[4 * i + 3] = v.w;
+    }
+    q.xh = f[0]; q.yh = f[1]; q.zh = f[2]; q.xl = f[3]; q.yl = f[4]; q.zl = f[5];
+    q.k = f[6]; q.phi = f[7]; q.th = f[8];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) q.c[i] = f[9 + i];
+}
+
+__device__ __forceinline__ void store_pred_rec(float4* __restrict__ r, const Pred& q) {
+    float f[24];
+    f[0] = q.xh; f[1] = q.yh; f[2] = q.zh; f[3] = q.xl; f[4] = q.yl; f[5] = q.zl;
+    f[6] = q.k; f[7] = q.phi; f[8] = q.th;
+#pragma unroll
+    for (int i = 0; i < 15; ++i) f[9 + i] = q.c[i];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) r[i] = make_float4(f[4 * i], f[4 * i + 1], f[4 * i + 2], f[4 * i + 3]);
+}
+
+// slot meta: (score, chi2 sum, nfound | nholes << 8 | stopped << 16, alive)
+__device__ __forceinline__ int4 pack_meta(float score, float chi2s, int nfound, int nholes, bool stopped, bool alive) {
+    return make_int4(__float_as_int(score), __float_as_int(chi2s), nfound | (nholes << 8) | ((int)stopped << 16),
+                     (int)alive);
+}
+
+// Appends v to list (count at *cnt) for the lanes with pred set: one atomic per warp.
+__device__ __forceinline__ void warp_append(bool pred, int v, int* list, int* cnt) {
+    const unsigned m = __ballot_sync(kFull, pred);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(cnt, __popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (pred) list[base + __popc(m & ((1u << lane) - 1u))] = v;
+}
+
+__device__ __forceinline__ void load_geom_smem(const DevGeom* __restrict__ gp, DevGeom& g) {
+    const int4* src = reinterpret_cast<const int4*>(gp);
+    int4* dst = reinterpret_cast<int4*>(&g);
+    for (int i = threadIdx.x; i < (int)(sizeof(DevGeom) / 16); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+}
+
+__device__ __forceinline__ void add_counters(unsigned long long* counters, unsigned long long c0,
+                                             unsigned long long c1, unsigned long long c2, unsigned long long c3,
+                                             unsigned long long c4) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        c0 += __shfl_xor_sync(kFull, c0, off);
+        c1 += __shfl_xor_sync(kFull, c1, off);
+        c2 += __shfl_xor_sync(kFull, c2, off);
+        c3 += __shfl_xor_sync(kFull, c3, off);
+        c4 += __shfl_xor_sync(kFull, c4, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (c0) atomicAdd(counters + 0, c0);
+        if (c1) atomicAdd(counters + 1, c1);
+        if (c2) atomicAdd(counters + 2, c2);
+        if (c3) atomicAdd(counters + 3, c3);
+        if (c4) atomicAdd(counters + 4, c4);
+    }
+}
+
 struct BuildArgs {
     const DevGeom* geom;
     DevParams P;
     HitStore H;
     SeedStore S;
     BuildOutDev out;
-    int* queue;
+    BuildWork w;
     unsigned long long* counters;
-    int max_steps;   // longest plan (trail rows)
+    int max_steps;   // trail rows per seed (longest plan)
 };
 
-__global__ void __launch_bounds__(kThreads) k_build(BuildArgs a) {
-    __shared__ DevGeom g;
-    extern __shared__ int trail_smem[];
-    {
-        const int4* src = reinterpret_cast<const int4*>(a.geom);
-        int4* dst = reinterpret_cast<int4*>(&g);
-        for (int i = threadIdx.x; i < (int)(sizeof(DevGeom) / 16); i += blockDim.x) dst[i] = src[i];
+// ---- round 0: slot 0 of every seed with work takes the seed state
+__global__ void __launch_bounds__(kThreads) k_start(BuildArgs a) {
+    const DevGeom* __restrict__ g = a.geom;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;   // seed position in the (event, eta, phi) order
+    bool work = false;
+    if (i < a.S.n) {
+        const int seed = a.S.order[i];
+        const int4 inf = a.S.info[seed];
+        int pos = 0, start = 0, nsteps = 0, event = 0;
+        if (inf.w == 0) {
+            const int pb = g->plan_off[inf.x];
+            start = inf.y;
+            pos = pb + start;
+            nsteps = g->plan_off[inf.x + 1] - pos;
+            if (nsteps < 0) nsteps = 0;
+            event = inf.z;
+        }
+        a.w.sinfo[i] = make_int4(pos, start, nsteps, event);
+        a.w.fin[i] = -1;
+        work = nsteps > 0;
+        const int4 dead = make_int4(0, 0, 0, 0);
+#pragma unroll
+        for (int c = 1; c < kGroup; ++c) a.w.meta[0][i * kGroup + c] = dead;
+        if (work) {
+            const float4* src = reinterpret_cast<const float4*>(a.S.state + (int64_t)seed * kSeedStateStride);
+            float4* dst = a.w.st[0] + (int64_t)i * kGroup * 8;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) dst[q] = src[q];
+            a.w.meta[0][i * kGroup] = pack_meta(0.0f, 0.0f, 3, 0, false, true);
+        } else {
+            a.w.meta[0][i * kGroup] = dead;
+        }
     }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int grp = lane >> 3, slot = lane & 7, gbase = grp << 3;
-    int* trail = trail_smem + (warp * 4 + grp) * a.max_steps * kGroup;
+    warp_append(work, i * kGroup, a.w.live[0], a.w.counts + 0);
+    warp_append(work, i, a.w.seeds[0], a.w.counts + 2);
+}
+
+// ---- a4-a9 for every live candidate of round tau
+__global__ void __launch_bounds__(kThreads) k_find(BuildArgs a, int tau) {
+    __shared__ DevGeom g;
+    load_geom_smem(a.geom, g);
+    const int cur = tau & 1, nxt = cur ^ 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {   // next round's lists are filled by k_select
+        a.w.counts[nxt] = 0;
+        a.w.counts[2 + nxt] = 0;
+    }
     const DevParams& P = a.P;
-    unsigned long long c_steps = 0, c_chi2 = 0, c_upd = 0, c_tested = 0;
-    int c_newton = 0;
-
-    for (;;) {
-        __syncwarp();
-        int base = 0;
-        if (lane == 0) base = atomicAdd(a.queue, 4);
-        base = shfl_i(base, 0);
-        if (base >= a.S.n) break;
-        const int sidx = base + grp;
-        int seed = -1, plan_base = 0, start = 0, event = 0, nsteps = 0;
-        if (sidx < a.S.n) {
-            seed = a.S.order[sidx];
-            const int4 inf = a.S.info[seed];
-            if (inf.w == 0) {
-                plan_base = g.plan_off[inf.x];
-                start = inf.y;
-                event = inf.z;
-                nsteps = g.plan_off[inf.x + 1] - plan_base - start;
-                if (nsteps < 0) nsteps = 0;
-            }
-        }
-        const int nsteps_w = __reduce_max_sync(kFull, nsteps);
-
+    const int n = a.w.counts[cur];
+    const int* __restrict__ list = a.w.live[cur];
+    unsigned long long c_steps = 0, c_chi2 = 0, c_tested = 0, c_newton = 0;
+    const int stride = gridDim.x * blockDim.x;
+    // every lane of a warp runs the same number of iterations (warp_append inside k_select
+    // needs converged warps; here it keeps the loop uniform)
+    for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const int idx = base + (threadIdx.x & 31);
+        if (idx >= n) continue;
+        const int sl = list[idx];
+        const int i = sl / kGroup;
+        const int4 si = a.w.sinfo[i];
+        const int layer = g.plan[si.x + tau];
+        const DevLayer& L = g.layers[layer];
         State t;
-        float score = 0.0f, chi2s = 0.0f;
-        int nfound = 3, nholes = 0;
-        bool stopped = false;
-        bool alive = seed >= 0 && nsteps > 0 && slot == 0;
-        {
-            const float* o = a.S.state + (int64_t)(seed >= 0 ? seed : 0) * kSeedStateStride;
-            t.xh = o[0]; t.yh = o[1]; t.zh = o[2]; t.xl = o[3]; t.yl = o[4]; t.zl = o[5];
-            t.k = o[6]; t.phi = o[7]; t.th = o[8];
+        load_state_rec(a.w.st[cur] + (int64_t)sl * 8, t);
+        const int4 mt = a.w.meta[cur][sl];
+        const float score = __int_as_float(mt.x);
+        const int nholes = (mt.z >> 8) & 0xff;
+
+        Pred q;
+        float dir[4];
+        int newton = 0;
+        const int r = propagate(L, g.cB, P.material, t, q, newton, dir);
+        c_newton += newton;
+        int nh_kind = K_NONE, n_h = 0;
+        float nh_score = 0.0f;
+        float lx[kGroup];
+        int lid[kGroup], lq[kGroup];
 #pragma unroll
-            for (int q = 0; q < 21; ++q) t.c[q] = o[9 + q];
+        for (int j = 0; j < kGroup; ++j) {
+            lx[j] = kBig;
+            lid[j] = 0x7fffffff;
+            lq[j] = 0;
         }
-
-        for (int tau = 0; tau < nsteps_w; ++tau) {
-            const bool gact = tau < nsteps;
-            const int layer = gact ? g.plan[plan_base + start + tau] : 0;
-            const DevLayer& L = g.layers[layer];
-
-            // ---- 1. propagation (a4-a7)
-            int nh_kind = K_NONE;
-            float nh_score = -kBig;
-            bool crossed = false;
-            Pred q;
-            float dir[4];
-            if (gact && alive) {
-                if (stopped) {
-                    nh_kind = K_CARRY;
-                    nh_score = score;
-                } else {
-                    const int r = propagate(L, g.cB, P.material, t, q, c_newton, dir);
-                    if (r < 0) {
-                        alive = false;
-                    } else if (r == 0) {
-                        nh_kind = K_SKIP;
-                        nh_score = score;
-                    } else {
-                        crossed = true;
-                        ++c_steps;
-                        if (nholes < P.max_holes) {
-                            nh_kind = K_MISS;
-                            nh_score = score - P.score_hole;
-                        } else {
-                            nh_kind = K_STOP;
-                            nh_score = score;
-                        }
-                    }
-                }
+        if (r == 0) {
+            nh_kind = K_SKIP;
+            nh_score = score;
+        } else if (r > 0) {
+            ++c_steps;
+            if (nholes < P.max_holes) {
+                nh_kind = K_MISS;
+                nh_score = score - P.score_hole;
+            } else {
+                nh_kind = K_STOP;
+                nh_score = score;
             }
-
-            // ---- 2. window and chi2 of the hits inside (a8-a9); sorted list (chi2 asc, id asc)
-            float lx[kGroup];
-            int lid[kGroup], lq[kGroup];
-#pragma unroll
-            for (int j = 0; j < kGroup; ++j) {
-                lx[j] = kBig;
-                lid[j] = 0x7fffffff;
-                lq[j] = 0;
+            const FrameT<float> fr = frame_of(L.kind, q.xh, q.yh, dir[0], dir[1], dir[2], dir[3]);
+            const Window w = window(L, P, q, fr);
+            const float eps = 1e-5f;
+            const float fe0 = (w.eta - w.deta - eps - L.eta_lo) * L.eta_scale;
+            const float fe1 = (w.eta + w.deta + eps - L.eta_lo) * L.eta_scale;
+            const int e0 = fe0 >= 0.0f ? (int)fminf(floorf(fe0), (float)(L.n_eta - 1)) : 0;
+            const int e1 = fe1 >= 0.0f ? (int)fminf(floorf(fe1), (float)(L.n_eta - 1)) : 0;
+            const float pscale = L.n_phi * (1.0f / kTwoPi);
+            const int f0 = (int)floorf((w.phi - w.dphi - eps + kPi) * pscale);
+            const int f1 = (int)floorf((w.phi + w.dphi + eps + kPi) * pscale);
+            int nf = f1 - f0 + 1;
+            int fa = f0 % L.n_phi;
+            if (fa < 0) fa += L.n_phi;
+            if (nf >= L.n_phi) {
+                nf = L.n_phi;
+                fa = 0;
             }
-            if (crossed) {
-                const FrameT<float> fr = frame_of(L.kind, q.xh, q.yh, dir[0], dir[1], dir[2], dir[3]);
-                const Window w = window(L, P, q, fr);
-                const float eps = 1e-5f;
-                const float fe0 = (w.eta - w.deta - eps - L.eta_lo) * L.eta_scale;
-                const float fe1 = (w.eta + w.deta + eps - L.eta_lo) * L.eta_scale;
-                const int e0 = fe0 >= 0.0f ? (int)fminf(floorf(fe0), (float)(L.n_eta - 1)) : 0;
-                const int e1 = fe1 >= 0.0f ? (int)fminf(floorf(fe1), (float)(L.n_eta - 1)) : 0;
-                const float pscale = L.n_phi * (1.0f / kTwoPi);
-                const int f0 = (int)floorf((w.phi - w.dphi - eps + kPi) * pscale);
-                const int f1 = (int)floorf((w.phi + w.dphi + eps + kPi) * pscale);
-                int nf = f1 - f0 + 1;
-                int fa = f0 % L.n_phi;
-                if (fa < 0) fa += L.n_phi;
-                if (nf >= L.n_phi) {
-                    nf = L.n_phi;
-                    fa = 0;
-                }
-                const int run1 = min(nf, L.n_phi - fa), run2 = nf - run1;
-                const int64_t bb = (int64_t)event * g.bins_per_event + L.bin_base;
-                for (int ie = e0; ie <= e1; ++ie) {
-                    const int64_t rowb = bb + (int64_t)ie * L.n_phi;
-                    for (int run = 0; run < 2; ++run) {
-                        const int b0 = run == 0 ? fa : 0;
-                        const int nb = run == 0 ? run1 : run2;
-                        if (nb <= 0) continue;
-                        const int q0 = __ldg(a.H.bin_start + rowb + b0);
-                        const int q1 = __ldg(a.H.bin_start + rowb + b0 + nb);
-                        for (int hq = q0; hq < q1; ++hq) {
-                            ++c_tested;
-                            const float2 ep = __ldg(a.H.hb_ep + hq);
-                            if (fabsf(ep.x - w.eta) <= w.deta && fabsf(wrap_pi(ep.y - w.phi)) <= w.dphi) {
-                                ++c_chi2;
-                                float m[3], v[6];
-                                int id;
-                                load_hit(a.H.hb_pay, hq, m, v, &id);
-                                float x2;
-                                if (chi2_hit(fr, q, m[0], m[1], m[2], v, x2) && x2 < P.chi2_cut) {
-                                    int qq = hq;
+            const int run1 = min(nf, L.n_phi - fa), run2 = nf - run1;
+            const int64_t bb = (int64_t)si.w * g.bins_per_event + L.bin_base;
+            for (int ie = e0; ie <= e1; ++ie) {
+                const int64_t rowb = bb + (int64_t)ie * L.n_phi;
+                for (int run = 0; run < 2; ++run) {
+                    const int b0 = run == 0 ? fa : 0;
+                    const int nb = run == 0 ? run1 : run2;
+                    if (nb <= 0) continue;
+                    const int q0 = __ldg(a.H.bin_start + rowb + b0);
+                    const int q1 = __ldg(a.H.bin_start + rowb + b0 + nb);
+                    for (int hq = q0; hq < q1; ++hq) {
+                        ++c_tested;
+                        const float2 ep = __ldg(a.H.hb_ep + hq);
+                        if (fabsf(ep.x - w.eta) <= w.deta && fabsf(wrap_pi(ep.y - w.phi)) <= w.dphi) {
+                            ++c_chi2;
+                            float m[3], v[6];
+                            int id;
+                            load_hit(a.H.hb_pay, hq, m, v, &id);
+                            float x2;
+                            if (chi2_hit(fr, q, m[0], m[1], m[2], v, x2) && x2 < P.chi2_cut) {
+                                int qq = hq;
 #pragma unroll
-                                    for (int j = 0; j < kGroup; ++j) {
-                                        const bool better = x2 < lx[j] || (x2 == lx[j] && id < lid[j]);
-                                        const float tx = lx[j];
-                                        const int ti = lid[j], tq = lq[j];
-                                        if (better) {
-                                            lx[j] = x2;
-                                            lid[j] = id;
-                                            lq[j] = qq;
-                                            x2 = tx;
-                                            id = ti;
-                                            qq = tq;
-                                        }
+                                for (int j = 0; j < kGroup; ++j) {
+                                    const bool better = x2 < lx[j] || (x2 == lx[j] && id < lid[j]);
+                                    const float tx = lx[j];
+                                    const int ti = lid[j], tq = lq[j];
+                                    if (better) {
+                                        lx[j] = x2;
+                                        lid[j] = id;
+                                        lq[j] = qq;
+                                        x2 = tx;
+                                        id = ti;
+                                        qq = tq;
                                     }
                                 }
                             }
@@ -205,198 +296,301 @@ __global__ void __launch_bounds__(kThreads) k_build(BuildArgs a) {
                     }
                 }
             }
+#pragma unroll
+            for (int j = 0; j < kGroup; ++j) n_h += lx[j] < kBig ? 1 : 0;
+            store_pred_rec(a.w.pr + (int64_t)sl * 6, q);
+        }
+        int4* lrec = a.w.ls + (int64_t)sl * 5;
+        lrec[0] = make_int4(n_h, nh_kind, __float_as_int(nh_score), 0);
+#pragma unroll
+        for (int j = 0; j < kGroup; j += 2)
+            if (j < n_h)
+                lrec[1 + j / 2] = make_int4(__float_as_int(lx[j]), lq[j], __float_as_int(lx[j + 1]), lq[j + 1]);
+    }
+    add_counters(a.counters, c_steps, c_chi2, 0ull, c_tested, c_newton);
+}
 
-            // ---- 3. the N best children of the seed (a10)
-            bool nh_avail = nh_kind != K_NONE;
-            int my_parent = -1, my_kind = K_NONE, my_id = -1, my_q = 0;
-            float my_x2 = 0.0f, my_score = 0.0f;
-            for (int r = 0; r < P.max_cands; ++r) {
-                const bool has_hit = lx[0] < kBig;
-                const float hit_score = score + P.score_hit - lx[0];
-                int hk = K_NONE;
-                float hs = 0.0f;
-                if (has_hit && (!nh_avail || hit_score >= nh_score)) {
-                    hk = K_HIT;
-                    hs = hit_score;
-                } else if (nh_avail) {
-                    hk = nh_kind;
-                    hs = nh_score;
-                }
-                unsigned long long best = hk != K_NONE ? order_key(hs, slot) : 0ull;
+// ---- a10-a11 for every seed with a live candidate in round tau
+__global__ void __launch_bounds__(kThreads) k_select(BuildArgs a, int tau) {
+    __shared__ DevGeom g;
+    load_geom_smem(a.geom, g);
+    const int cur = tau & 1, nxt = cur ^ 1;
+    const DevParams& P = a.P;
+    const int lane = threadIdx.x & 31;
+    const int slot = lane & 7, gbase = lane & ~7;
+    const int n = a.w.counts[2 + cur];
+    const int* __restrict__ list = a.w.seeds[cur];
+    unsigned long long c_upd = 0;
+    const int groups_per_block = kThreads / kGroup;
+    const int gstride = gridDim.x * groups_per_block;
+    // loop bound uniform over the warp: the first group index of the warp
+    const int g0 = blockIdx.x * groups_per_block + (threadIdx.x >> 5) * 4;
+    for (int wg = g0; wg < n; wg += gstride) {
+        const int gi = wg + (lane >> 3);
+        const bool gact = gi < n;
+        const int i = gact ? list[gi] : 0;
+        const int4 si = gact ? a.w.sinfo[i] : make_int4(0, 0, 0, 0);
+        const int sl = i * kGroup + slot;
+        const int4 mt = gact ? a.w.meta[cur][sl] : make_int4(0, 0, 0, 0);
+        const float score = __int_as_float(mt.x);
+        const bool alive = mt.w != 0;
+        const bool stopped = ((mt.z >> 16) & 1) != 0;
+
+        int nh_kind = K_NONE;
+        float nh_score = -kBig;
+        float lx[kGroup];
+        int lq[kGroup];
 #pragma unroll
-                for (int off = 1; off < kGroup; off <<= 1) {
-                    const unsigned long long o = __shfl_xor_sync(kFull, best, off);
-                    best = o > best ? o : best;
-                }
-                const bool valid = best != 0ull;
-                const int wslot = kGroup - 1 - (int)(best & 7ull);
-                const int src = gbase + wslot;
-                const int w_kind = shfl_i(hk, src);
-                const int w_id = shfl_i(lid[0], src);
-                const int w_q = shfl_i(lq[0], src);
-                const float w_x2 = shfl_f(lx[0], src);
-                const float w_score = shfl_f(hs, src);
-                if (valid && slot == r) {
-                    my_parent = wslot;
-                    my_kind = w_kind;
-                    my_id = w_id;
-                    my_q = w_q;
-                    my_x2 = w_x2;
-                    my_score = w_score;
-                }
-                if (valid && slot == wslot) {
-                    if (hk == K_HIT) {
+        for (int j = 0; j < kGroup; ++j) {
+            lx[j] = kBig;
+            lq[j] = 0;
+        }
+        if (alive) {
+            if (stopped) {
+                nh_kind = K_CARRY;
+                nh_score = score;
+            } else {
+                const int4* lrec = a.w.ls + (int64_t)sl * 5;
+                const int4 h = lrec[0];
+                nh_kind = h.y;
+                nh_score = __int_as_float(h.z);
 #pragma unroll
-                        for (int j = 0; j < kGroup - 1; ++j) {
-                            lx[j] = lx[j + 1];
-                            lid[j] = lid[j + 1];
-                            lq[j] = lq[j + 1];
+                for (int j = 0; j < kGroup; j += 2)
+                    if (j < h.x) {
+                        const int4 e = lrec[1 + j / 2];
+                        lx[j] = __int_as_float(e.x);
+                        lq[j] = e.y;
+                        if (j + 1 < h.x) {
+                            lx[j + 1] = __int_as_float(e.z);
+                            lq[j + 1] = e.w;
                         }
-                        lx[kGroup - 1] = kBig;
-                    } else {
-                        nh_avail = false;
                     }
-                }
             }
+        }
 
-            // ---- 4. pull the parent's state and update (a11); 5. trail
-            // Payload of a lane: its predicted state (surface frame) if it crossed, else its state.
-            float R[30];
-            R[0] = crossed ? q.xh : t.xh; R[1] = crossed ? q.yh : t.yh; R[2] = crossed ? q.zh : t.zh;
-            R[3] = crossed ? q.xl : t.xl; R[4] = crossed ? q.yl : t.yl; R[5] = crossed ? q.zl : t.zl;
-            R[6] = crossed ? q.k : t.k; R[7] = crossed ? q.phi : t.phi; R[8] = crossed ? q.th : t.th;
+        // ---- the N best children of the seed (a10)
+        bool nh_avail = nh_kind != K_NONE;
+        int my_parent = -1, my_kind = K_NONE, my_q = 0;
+        float my_x2 = 0.0f, my_score = 0.0f;
+        for (int r = 0; r < P.max_cands; ++r) {
+            const bool has_hit = lx[0] < kBig;
+            const float hit_score = score + P.score_hit - lx[0];
+            int hk = K_NONE;
+            float hs = 0.0f;
+            if (has_hit && (!nh_avail || hit_score >= nh_score)) {
+                hk = K_HIT;
+                hs = hit_score;
+            } else if (nh_avail) {
+                hk = nh_kind;
+                hs = nh_score;
+            }
+            unsigned long long best = hk != K_NONE ? order_key(hs, slot) : 0ull;
 #pragma unroll
-            for (int i = 0; i < 15; ++i) R[9 + i] = crossed ? q.c[i] : t.c[i];
+            for (int off = 1; off < kGroup; off <<= 1) {
+                const unsigned long long o = __shfl_xor_sync(kFull, best, off);
+                best = o > best ? o : best;
+            }
+            const bool valid = best != 0ull;
+            const int wslot = kGroup - 1 - (int)(best & 7ull);
+            const int src = gbase + wslot;
+            const int w_kind = shfl_i(hk, src);
+            const int w_q = shfl_i(lq[0], src);
+            const float w_x2 = shfl_f(lx[0], src);
+            const float w_score = shfl_f(hs, src);
+            if (valid && slot == r) {
+                my_parent = wslot;
+                my_kind = w_kind;
+                my_q = w_q;
+                my_x2 = w_x2;
+                my_score = w_score;
+            }
+            if (valid && slot == wslot) {
+                if (hk == K_HIT) {
 #pragma unroll
-            for (int i = 15; i < 21; ++i) R[9 + i] = t.c[i];
-            const int psrc = gbase + (my_parent >= 0 ? my_parent : slot);
-#pragma unroll
-            for (int i = 0; i < 30; ++i) R[i] = shfl_f(R[i], psrc);
-            const float p_chi2 = shfl_f(chi2s, psrc);
-            const int p_nfound = shfl_i(nfound, psrc);
-            const int p_nholes = shfl_i(nholes, psrc);
-            const int p_stopped = shfl_i((int)stopped, psrc);
-            if (gact) {
-                if (my_kind != K_NONE) {
-                    chi2s = p_chi2;
-                    nfound = p_nfound;
-                    nholes = p_nholes;
-                    stopped = p_stopped != 0;
-                    score = my_score;
-                    alive = true;
-                    int code = MKGB_HIT_STOP;
-                    if (my_kind == K_SKIP || my_kind == K_CARRY) {
-                        t.xh = R[0]; t.yh = R[1]; t.zh = R[2]; t.xl = R[3]; t.yl = R[4]; t.zl = R[5];
-                        t.k = R[6]; t.phi = R[7]; t.th = R[8];
-#pragma unroll
-                        for (int i = 0; i < 21; ++i) t.c[i] = R[9 + i];
-                        if (my_kind == K_SKIP) code = MKGB_HIT_SKIP;
-                    } else {
-                        Pred pq;
-                        pq.xh = R[0]; pq.yh = R[1]; pq.zh = R[2]; pq.xl = R[3]; pq.yl = R[4]; pq.zl = R[5];
-                        pq.k = R[6]; pq.phi = R[7]; pq.th = R[8];
-#pragma unroll
-                        for (int i = 0; i < 15; ++i) pq.c[i] = R[9 + i];
-                        if (my_kind == K_HIT) {
-                            float m[3], v[6];
-                            load_hit(a.H.hb_pay, my_q, m, v, nullptr);
-                            if (kalman_update(L.kind, pq, m[0], m[1], m[2], v, t)) {
-                                chi2s += my_x2;
-                                ++nfound;
-                                ++c_upd;
-                                code = my_id;
-                            } else {
-                                alive = false;
-                            }
-                        } else {
-                            pred_to_state(L.kind, pq, t);
-                            if (my_kind == K_MISS) {
-                                ++nholes;
-                                code = MKGB_HIT_MISS;
-                            } else {   // K_STOP
-                                stopped = true;
-                            }
-                        }
+                    for (int j = 0; j < kGroup - 1; ++j) {
+                        lx[j] = lx[j + 1];
+                        lq[j] = lq[j + 1];
                     }
-                    trail[tau * kGroup + slot] = ((code + 4) << 3) | my_parent;
+                    lx[kGroup - 1] = kBig;
                 } else {
-                    alive = false;
+                    nh_avail = false;
                 }
             }
         }
 
-        // ---- best candidate and its hit list (a13)
-        __syncwarp();
-        const unsigned am = __ballot_sync(kFull, alive);
-        const unsigned gm = (am >> gbase) & 0xffu;
-        const int best_slot = gm ? __ffs(gm) - 1 : -1;
-        if (seed >= 0) {
-            int* hrow = a.out.hits + (int64_t)seed * a.out.max_plan;
-            if (slot == 0) {
-                for (int q = 0; q < a.out.max_plan; ++q) hrow[q] = MKGB_HIT_PRE;
-            }
-            __syncwarp(0xffu << gbase);
-            if (slot == (best_slot >= 0 ? best_slot : 0)) {
-                float* po = a.out.params + 6 * (int64_t)seed;
-                float* co = a.out.cov + 21 * (int64_t)seed;
-                if (best_slot >= 0) {
-                    store_state6(t, po, co);
-                    a.out.chi2[seed] = chi2s;
-                    a.out.score[seed] = score;
-                    a.out.nfound[seed] = nfound;
-                    a.out.nholes[seed] = nholes;
-                    int s_ = best_slot;
-                    for (int tau = nsteps - 1; tau >= 0; --tau) {
-                        const int v = trail[tau * kGroup + s_];
-                        hrow[start + tau] = (v >> 3) - 4;
-                        s_ = v & 7;
+        // ---- the child's state (a11), meta, trail and next-round lists
+        const int psrc = gbase + (my_parent >= 0 ? my_parent : slot);
+        const int4 pm = make_int4(shfl_i(mt.x, psrc), shfl_i(mt.y, psrc), shfl_i(mt.z, psrc), shfl_i(mt.w, psrc));
+        bool c_alive = false, c_stopped = false;
+        float chi2s = __int_as_float(pm.y);
+        int nfound = pm.z & 0xff, nholes = (pm.z >> 8) & 0xff;
+        int code = MKGB_HIT_STOP;
+        const int csl = i * kGroup + slot;
+        if (gact && my_kind != K_NONE) {
+            const int psl = i * kGroup + my_parent;
+            c_alive = true;
+            c_stopped = ((pm.z >> 16) & 1) != 0;
+            if (my_kind == K_SKIP || my_kind == K_CARRY) {
+                const float4* src = a.w.st[cur] + (int64_t)psl * 8;
+                float4* dst = a.w.st[nxt] + (int64_t)csl * 8;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) dst[q] = src[q];
+                if (my_kind == K_SKIP) code = MKGB_HIT_SKIP;
+            } else {
+                const DevLayer& L = g.layers[g.plan[si.x + tau]];
+                Pred pq;
+                load_pred_rec(a.w.pr + (int64_t)psl * 6, pq);
+                State t;
+                if (my_kind == K_HIT) {
+                    float m[3], v[6];
+                    int id;
+                    load_hit(a.H.hb_pay, my_q, m, v, &id);
+                    if (kalman_update(L.kind, pq, m[0], m[1], m[2], v, t)) {
+                        chi2s += my_x2;
+                        ++nfound;
+                        ++c_upd;
+                        code = id;
+                    } else {
+                        c_alive = false;
                     }
                 } else {
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) po[q] = 0.0f;
-#pragma unroll
-                    for (int q = 0; q < 21; ++q) co[q] = 0.0f;
-                    a.out.chi2[seed] = 0.0f;
-                    a.out.score[seed] = -INFINITY;
-                    a.out.nfound[seed] = 0;
-                    a.out.nholes[seed] = 0;
+                    pred_to_state(L.kind, pq, t);
+                    if (my_kind == K_MISS) {
+                        ++nholes;
+                        code = MKGB_HIT_MISS;
+                    } else {   // K_STOP
+                        c_stopped = true;
+                    }
                 }
+                store_state_rec(a.w.st[nxt] + (int64_t)csl * 8, t);
             }
+            a.w.trail[((int64_t)i * a.max_steps + tau) * kGroup + slot] = ((code + 4) << 3) | my_parent;
         }
+        if (gact) a.w.meta[nxt][csl] = pack_meta(my_score, chi2s, nfound, nholes, c_stopped, c_alive);
+        const bool more = gact && tau + 1 < si.z;
+        warp_append(more && c_alive && !c_stopped, csl, a.w.live[nxt], a.w.counts + nxt);
+        const unsigned am = __ballot_sync(kFull, c_alive);
+        const bool any = ((am >> gbase) & 0xffu) != 0u;
+        warp_append(more && any && slot == 0, i, a.w.seeds[nxt], a.w.counts + 2 + nxt);
+        if (gact && slot == 0 && (!more || !any)) a.w.fin[i] = nxt;
     }
-    // ---- counters
+    add_counters(a.counters, 0ull, 0ull, c_upd, 0ull, 0ull);
+}
+
+// ---- best candidate per seed and its hit list (a13); 8 lanes per seed
+__global__ void __launch_bounds__(kThreads) k_finish(BuildArgs a) {
+    const int lane = threadIdx.x & 31, slot = lane & 7, gbase = lane & ~7;
+    const int gi = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const bool gact = gi < a.S.n;
+    const int i = gact ? gi : 0;
+    const int fin = gact ? a.w.fin[i] : -1;
+    int4 mt = make_int4(0, 0, 0, 0);
+    if (fin >= 0) mt = a.w.meta[fin][i * kGroup + slot];
+    const unsigned am = __ballot_sync(kFull, mt.w != 0);
+    const unsigned gm = (am >> gbase) & 0xffu;
+    if (!gact) return;
+    const int best = gm ? __ffs(gm) - 1 : -1;
+    const int seed = a.S.order[i];
+    int* hrow = a.out.hits + (int64_t)seed * a.out.max_plan;
+    for (int q = slot; q < a.out.max_plan; q += kGroup) hrow[q] = MKGB_HIT_PRE;
+    __syncwarp(0xffu << gbase);
+    if (slot != (best >= 0 ? best : 0)) return;
+    float* po = a.out.params + 6 * (int64_t)seed;
+    float* co = a.out.cov + 21 * (int64_t)seed;
+    if (best >= 0) {
+        State t;
+        load_state_rec(a.w.st[fin] + (int64_t)(i * kGroup + best) * 8, t);
+        store_state6(t, po, co);
+        a.out.chi2[seed] = __int_as_float(mt.y);
+        a.out.score[seed] = __int_as_float(mt.x);
+        a.out.nfound[seed] = mt.z & 0xff;
+        a.out.nholes[seed] = (mt.z >> 8) & 0xff;
+        const int4 si = a.w.sinfo[i];
+        int s_ = best;
+        for (int tau = si.z - 1; tau >= 0; --tau) {
+            const int v = a.w.trail[((int64_t)i * a.max_steps + tau) * kGroup + s_];
+            hrow[si.y + tau] = (v >> 3) - 4;
+            s_ = v & 7;
+        }
+    } else {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        c_steps += __shfl_xor_sync(kFull, c_steps, off);
-        c_chi2 += __shfl_xor_sync(kFull, c_chi2, off);
-        c_upd += __shfl_xor_sync(kFull, c_upd, off);
-        c_tested += __shfl_xor_sync(kFull, c_tested, off);
-        c_newton += __shfl_xor_sync(kFull, c_newton, off);
+        for (int q = 0; q < 6; ++q) po[q] = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 21; ++q) co[q] = 0.0f;
+        a.out.chi2[seed] = 0.0f;
+        a.out.score[seed] = -INFINITY;
+        a.out.nfound[seed] = 0;
+        a.out.nholes[seed] = 0;
     }
-    if (lane == 0) {
-        atomicAdd(a.counters + 0, c_steps);
-        atomicAdd(a.counters + 1, c_chi2);
-        atomicAdd(a.counters + 2, c_upd);
-        atomicAdd(a.counters + 3, c_tested);
-        atomicAdd(a.counters + 4, (unsigned long long)c_newton);
-    }
+}
+
+int resident_grid(const void* kernel, int n_sms, size_t smem) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return n_sms * per_sm;
 }
 
 }  // namespace
 
+namespace {
+
+// Carves the work buffers out of one allocation (256-byte aligned pieces); with base == nullptr
+// only the total size is computed.
+size_t layout_build_work(char* base, int n_seeds, int max_plan_len, BuildWork* w) {
+    const size_t ns = (size_t)n_seeds, slots = ns * kGroup;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char* r = base ? base + off : nullptr;
+        off += (bytes + 255) & ~(size_t)255;
+        return r;
+    };
+    BuildWork t;
+    t.st[0] = reinterpret_cast<float4*>(take(slots * 128));
+    t.st[1] = reinterpret_cast<float4*>(take(slots * 128));
+    t.meta[0] = reinterpret_cast<int4*>(take(slots * 16));
+    t.meta[1] = reinterpret_cast<int4*>(take(slots * 16));
+    t.pr = reinterpret_cast<float4*>(take(slots * 96));
+    t.ls = reinterpret_cast<int4*>(take(slots * 80));
+    t.live[0] = reinterpret_cast<int*>(take(slots * 4));
+    t.live[1] = reinterpret_cast<int*>(take(slots * 4));
+    t.seeds[0] = reinterpret_cast<int*>(take(ns * 4));
+    t.seeds[1] = reinterpret_cast<int*>(take(ns * 4));
+    t.sinfo = reinterpret_cast<int4*>(take(ns * 16));
+    t.fin = reinterpret_cast<int*>(take(ns * 4));
+    t.trail = reinterpret_cast<int*>(take(ns * (size_t)max_plan_len * kGroup * 4));
+    t.counts = reinterpret_cast<int*>(take(16));
+    if (w) *w = t;
+    return off;
+}
+
+}  // namespace
+
+size_t build_work_bytes(int n_seeds, int max_plan_len) {
+    return layout_build_work(nullptr, n_seeds, max_plan_len, nullptr);
+}
+
+BuildWork carve_build_work(void* base, int n_seeds, int max_plan_len) {
+    BuildWork w;
+    layout_build_work(static_cast<char*>(base), n_seeds, max_plan_len, &w);
+    return w;
+}
+
 cudaError_t launch_build(cudaStream_t st, const DevGeom* g, int max_plan_len, DevParams P, HitStore H, SeedStore S,
-                         BuildOutDev out, int* queue, unsigned long long* counters, int n_sms) {
+                         BuildOutDev out, BuildWork w, unsigned long long* counters, int n_sms) {
     if (S.n == 0) return cudaSuccess;
-    BuildArgs a{g, P, H, S, out, queue, counters, max_plan_len};
-    const size_t smem = (size_t)kWarps * 4 * max_plan_len * kGroup * sizeof(int);
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build, kThreads, smem);
+    BuildArgs a{g, P, H, S, out, w, counters, max_plan_len};
+    cudaError_t e = cudaMemsetAsync(w.counts, 0, 16, st);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    const int64_t want = ((int64_t)S.n + 4 * kWarps - 1) / (4 * kWarps);
-    int64_t grid = (int64_t)n_sms * per_sm;
-    if (grid > want) grid = want;
-    k_build<<<(unsigned)grid, kThreads, smem, st>>>(a);
+    const int nb = (S.n + kThreads - 1) / kThreads;
+    k_start<<<nb, kThreads, 0, st>>>(a);
+    const int grid_find = resident_grid((const void*)k_find, n_sms, 0);
+    const int grid_sel = resident_grid((const void*)k_select, n_sms, 0);
+    for (int tau = 0; tau < max_plan_len; ++tau) {
+        k_find<<<grid_find, kThreads, 0, st>>>(a, tau);
+        k_select<<<grid_sel, kThreads, 0, st>>>(a, tau);
+    }
+    k_finish<<<(S.n * kGroup + kThreads - 1) / kThreads, kThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
