@@ -138,7 +138,8 @@ int mkgb_seed(mkgb_ctx* ctx, int n_seeds, const int32_t* seed_hits, int on_devic
 /* Combinatorial forward search (Sec. 2.2) for the seeds of the last mkgb_seed call: along the
  * seed's layer plan, every candidate is propagated, hits in its eta-phi window get a chi2, the
  * N best children per seed are kept and updated; the best candidate is returned with its hit
- * list.  Errors: MKGB_ESTATE without seeds or params, MKGB_EINVAL on a short max_plan. */
+ * list.  Errors: MKGB_ESTATE without seeds or params, MKGB_EINVAL on a short max_plan or with
+ * 2^28 - 8 or more hits loaded (the hit trail packs hit indices in 28 bits). */
 int mkgb_build(mkgb_ctx* ctx, const mkgb_tracks* out, int on_device);
 
 /* Kalman fit over a known assignment (Sec. 4): n tracks, each from p0/c0 through up to

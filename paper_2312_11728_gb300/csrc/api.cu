@@ -407,6 +407,9 @@ int mkgb_build(mkgb_ctx* ctx, const mkgb_tracks* out, int on_device) {
     if (!out || !out->params || !out->cov || !out->chi2 || !out->score || !out->nfound || !out->nholes || !out->hits)
         return fail(ctx, MKGB_EINVAL, "null output array");
     if (out->max_plan < ctx->max_plan_len) return fail(ctx, MKGB_EINVAL, "max_plan %d < longest plan %d", out->max_plan, ctx->max_plan_len);
+    if (ctx->n_hits >= ((int64_t)1 << 28) - 8)
+        return fail(ctx, MKGB_EINVAL, "%lld hits loaded: the search takes fewer than 2^28 - 8",
+                    (long long)ctx->n_hits);
     DevGuard guard(ctx->device);
     cudaStream_t st = ctx->stream;
     const size_t n = (size_t)ctx->n_seeds;

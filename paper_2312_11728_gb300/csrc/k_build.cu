@@ -185,7 +185,12 @@ __global__ void __launch_bounds__(kThreads) k_start(BuildArgs a) {
 // ---- a4-a9 for every live candidate of round tau
 __global__ void __launch_bounds__(kThreads) k_find(BuildArgs a, int tau) {
     __shared__ DevGeom g;
+    // per-thread sorted list of hit children (chi2 asc, id asc), one column per thread
+    __shared__ float s_x2[kGroup][kThreads];
+    __shared__ int s_id[kGroup][kThreads];
+    __shared__ int s_hq[kGroup][kThreads];
     load_geom_smem(a.geom, g);
+    const int tx = threadIdx.x;
     const int cur = tau & 1, nxt = cur ^ 1;
     if (blockIdx.x == 0 && threadIdx.x == 0) {   // next round's lists are filled by k_select
         a.w.counts[nxt] = 0;
@@ -219,14 +224,6 @@ __global__ void __launch_bounds__(kThreads) k_find(BuildArgs a, int tau) {
         c_newton += newton;
         int nh_kind = K_NONE, n_h = 0;
         float nh_score = 0.0f;
-        float lx[kGroup];
-        int lid[kGroup], lq[kGroup];
-#pragma unroll
-        for (int j = 0; j < kGroup; ++j) {
-            lx[j] = kBig;
-            lid[j] = 0x7fffffff;
-            lq[j] = 0;
-        }
         if (r == 0) {
             nh_kind = K_SKIP;
             nh_score = score;
@@ -276,42 +273,42 @@ __global__ void __launch_bounds__(kThreads) k_find(BuildArgs a, int tau) {
                             load_hit(a.H.hb_pay, hq, m, v, &id);
                             float x2;
                             if (chi2_hit(fr, q, m[0], m[1], m[2], v, x2) && x2 < P.chi2_cut) {
-                                int qq = hq;
-#pragma unroll
-                                for (int j = 0; j < kGroup; ++j) {
-                                    const bool better = x2 < lx[j] || (x2 == lx[j] && id < lid[j]);
-                                    const float tx = lx[j];
-                                    const int ti = lid[j], tq = lq[j];
-                                    if (better) {
-                                        lx[j] = x2;
-                                        lid[j] = id;
-                                        lq[j] = qq;
-                                        x2 = tx;
-                                        id = ti;
-                                        qq = tq;
+                                // insert into the sorted list (kept to its first kGroup entries)
+                                int j = n_h < kGroup ? n_h : kGroup - 1;
+                                const bool fits = n_h < kGroup ||
+                                                  x2 < s_x2[j][tx] || (x2 == s_x2[j][tx] && id < s_id[j][tx]);
+                                if (fits) {
+                                    while (j > 0 && (x2 < s_x2[j - 1][tx] ||
+                                                     (x2 == s_x2[j - 1][tx] && id < s_id[j - 1][tx]))) {
+                                        s_x2[j][tx] = s_x2[j - 1][tx];
+                                        s_id[j][tx] = s_id[j - 1][tx];
+                                        s_hq[j][tx] = s_hq[j - 1][tx];
+                                        --j;
                                     }
+                                    s_x2[j][tx] = x2;
+                                    s_id[j][tx] = id;
+                                    s_hq[j][tx] = hq;
+                                    if (n_h < kGroup) ++n_h;
                                 }
                             }
                         }
                     }
                 }
             }
-#pragma unroll
-            for (int j = 0; j < kGroup; ++j) n_h += lx[j] < kBig ? 1 : 0;
             store_pred_rec(a.w.pr + (int64_t)sl * 6, q);
         }
         int4* lrec = a.w.ls + (int64_t)sl * 5;
         lrec[0] = make_int4(n_h, nh_kind, __float_as_int(nh_score), 0);
-#pragma unroll
-        for (int j = 0; j < kGroup; j += 2)
-            if (j < n_h)
-                lrec[1 + j / 2] = make_int4(__float_as_int(lx[j]), lq[j], __float_as_int(lx[j + 1]), lq[j + 1]);
+        for (int j = 0; j < n_h; j += 2)
+            lrec[1 + j / 2] = make_int4(__float_as_int(s_x2[j][tx]), s_hq[j][tx],
+                                        __float_as_int(j + 1 < n_h ? s_x2[j + 1][tx] : kBig),
+                                        j + 1 < n_h ? s_hq[j + 1][tx] : 0);
     }
     add_counters(a.counters, c_steps, c_chi2, 0ull, c_tested, c_newton);
 }
 
 // ---- a10-a11 for every seed with a live candidate in round tau
-__global__ void __launch_bounds__(kThreads) k_select(BuildArgs a, int tau) {
+__global__ void __launch_bounds__(kThreads, 5) k_select(BuildArgs a, int tau) {
     __shared__ DevGeom g;
     load_geom_smem(a.geom, g);
     const int cur = tau & 1, nxt = cur ^ 1;
@@ -351,20 +348,22 @@ __global__ void __launch_bounds__(kThreads) k_select(BuildArgs a, int tau) {
                 nh_score = score;
             } else {
                 const int4* lrec = a.w.ls + (int64_t)sl * 5;
-                const int4 h = lrec[0];
-                nh_kind = h.y;
-                nh_score = __int_as_float(h.z);
+                int4 e[5];
 #pragma unroll
-                for (int j = 0; j < kGroup; j += 2)
-                    if (j < h.x) {
-                        const int4 e = lrec[1 + j / 2];
-                        lx[j] = __int_as_float(e.x);
-                        lq[j] = e.y;
-                        if (j + 1 < h.x) {
-                            lx[j + 1] = __int_as_float(e.z);
-                            lq[j + 1] = e.w;
-                        }
+                for (int q = 0; q < 5; ++q) e[q] = lrec[q];   // all at once; entries past the count unused
+                nh_kind = e[0].y;
+                nh_score = __int_as_float(e[0].z);
+#pragma unroll
+                for (int j = 0; j < kGroup; j += 2) {
+                    if (j < e[0].x) {
+                        lx[j] = __int_as_float(e[1 + j / 2].x);
+                        lq[j] = e[1 + j / 2].y;
                     }
+                    if (j + 1 < e[0].x) {
+                        lx[j + 1] = __int_as_float(e[1 + j / 2].z);
+                        lq[j + 1] = e[1 + j / 2].w;
+                    }
+                }
             }
         }
 
