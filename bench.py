@@ -30,20 +30,37 @@ UNIT = "Kalman steps/s"
 N_EVENTS, N_TRACKS, N_NOISE = 64, 20000, 50000
 WORKLOAD = "phase2_like_{events}ev_20k_tracks_50k_noise_bestN6"
 
-# Algorithmic FP32 operations per unit of work (FMA = 2), counted from the kernel source
-# (csrc/kalman.cuh); multi-function-unit work (sqrt, rsqrt, division, sincos, log, atan2) is
-# not counted.  Derivation in the design doc.
-FLOPS = dict(step=560, newton=30, tested=6, chi2=160, update=700)
+# FP32 operations per unit of work (FMA = 2), counted by ncu's per-thread instruction counters
+# (FFMA/FFMA2/FADD/FADD2/FMUL/FMUL2 with true predicates) on the search and fit kernels for the
+# 8-event version of this workload, divided by the work counters of the same run:
+#   find: per crossed candidate-layer step, k_find's propagation with Jacobian, transport and
+#         material, window and chi2 of the window's hits (a4-a9);
+#   update: per Kalman update of the search, k_select's merge of the children and the Joseph
+#         update (a10-a11);
+#   fit: per track-layer step of k_fit (a4-a9, a11 on one hit).
+# Multi-function-unit work (sqrt, rsqrt, division seeds, sincos, log, atan2) is not counted.
+FLOPS = dict(find=1443.1, update=706.1, fit=1788.8)
+# the search and fit kernel sources the counts (and the DRAM traffic in profiles/) belong to
+KERNEL_SOURCES = ("paper_2312_11728_gb300/csrc/k_build.cu", "paper_2312_11728_gb300/csrc/kalman.cuh",
+                  "paper_2312_11728_gb300/csrc/trig.cuh", "paper_2312_11728_gb300/csrc/internal.h")
 
 
 def build_flops(c):
     """c: build counters [steps, chi2 evaluations, updates, hits tested, Newton iterations]."""
-    return (FLOPS["step"] * c[0] + FLOPS["chi2"] * c[1] + FLOPS["update"] * c[2] + FLOPS["tested"] * c[3]
-            + FLOPS["newton"] * c[4])
+    return FLOPS["find"] * c[0] + FLOPS["update"] * c[2]
 
 
 def fit_flops(c):
-    return FLOPS["step"] * c[0] + (FLOPS["chi2"] + FLOPS["update"]) * c[2] + FLOPS["newton"] * c[4]
+    return FLOPS["fit"] * c[0]
+
+
+def kernel_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def _gen_event(args):
@@ -312,13 +329,20 @@ def main():
     n_sms = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_peak = n_sms * 128 * 2 * sm_max * 1e6 / 1e12        # TFLOP/s at the maximum SM clock
     achieved = build_flops(bc) / (np.mean(build_ms) / 1e3) / 1e12
+    # DRAM bytes of the search kernels per crossed candidate-layer step, from an ncu capture of
+    # the same sources (null if the kernels changed since)
     traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "k_build_traffic.json")
+    tr_path = os.path.join(ROOT, "profiles", "search_traffic.json")
     if os.path.exists(tr_path):
-        traffic = json.load(open(tr_path)).get("bytes_per_launch")
+        tr = json.load(open(tr_path))
+        if tr.get("sources_sha256_16") == kernel_sources_hash():
+            traffic = tr["dram_bytes_per_crossed_step"] * int(bc[0])
     bins_total = batch.n_events * int((g.n_eta.astype(np.int64) * g.n_phi).sum())
     keys_total = batch.n_events * 32 * 64
-    launches_per_step = (2 + scan_launches(bins_total)) + (2 + scan_launches(keys_total)) + 1 + 1
+    # hits: prep, scatter, scans; seeds: fit, key, scans, scatter; search: start, (find, select)
+    # per plan step of the longest plan, finish; fit: FP32 fit and FP64 refit
+    launches_per_step = ((2 + scan_launches(bins_total)) + (2 + scan_launches(keys_total)) + 2 + 2 * g.max_plan
+                         + 1 + (1 if params["kappa_fp64"] > 0 else 0))
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -331,10 +355,12 @@ def main():
                    "l2": f"inputs larger than L2: {batch.hit_xyz.shape[0] * 92 / 1e9:.2f} GB of hit data resident",
                    "parallelism": f"replicas{world}"},
         "stages_ms": {k: round(float(v), 4) for k, v in stage.items()},
-        "roofline": {"bound": "alu", "kernel": "k_build", "achieved": achieved, "peak": fp32_peak,
+        "roofline": {"bound": "alu", "kernel": "search (k_start, k_find + k_select per plan step, k_finish)",
+                     "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                      "peak_note": f"FP32: {n_sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz ({src} max clock)",
-                     "flops_per_launch": int(build_flops(bc))},
+                     "flops_per_launch": int(build_flops(bc)),
+                     "launch": "one mkgb_build call per step, timed with CUDA events on its stream"},
         "e2e": e2e,
         "gpu_launches": int(launches_per_step * args.steps),
         "clocks": clocks,

@@ -283,33 +283,31 @@ template <class F> __device__ __forceinline__ void pred_to_state(int kind, const
 
 // ----------------------------------------------------------------- propagation (a4-a7)
 
-// Material of layer L at the predicted state: Highland Q on (k, phi, theta) and mean energy loss
-// scaling k and its row/column.  Returns false if the particle stops.
+// Material of layer L at the predicted state (Sec. 3.1 material; a7): the Highland variance
+// th02 of the scattering angle, kc = k cot(theta), and the factor a = p / p' of the mean energy
+// loss.  Returns 1 (material applied), 0 (no material: zero thickness or k = 0) or -1 (the
+// particle stops).  Computed in the trajectory precision F.
 template <class F>
-__device__ __forceinline__ bool apply_material(const DevLayer& L, PredT<F>& q, F st, F ct, F sfp, F cfp) {
+__device__ __forceinline__ int material_terms(const DevLayer& L, F xh, F yh, F k, F st, F ct, F sfp, F cfp,
+                                              F& th02, F& kc, F& a) {
     using P = Phys<F>;
     F cosi;
     if (L.kind == MKGB_BARREL) {
-        const F ir = rsq(q.xh * q.xh + q.yh * q.yh);
-        cosi = fabs((q.xh * cfp + q.yh * sfp) * st * ir);
+        const F ir = rsq(xh * xh + yh * yh);
+        cosi = fabs((xh * cfp + yh * sfp) * st * ir);
     } else {
         cosi = fabs(ct);
     }
     const F fac = (cosi * P::inc_cap > F(1)) ? F(1) / cosi : P::inc_cap;
     const F tt = F(L.xx0) * fac;
-    const F k = q.k;
-    if (!(tt > F(0)) || k == F(0)) return true;
+    if (!(tt > F(0)) || k == F(0)) return 0;
     const F pm = F(1) / (fabs(k) * st);
     const F e2 = pm * pm + P::mpi * P::mpi;
     const F beta2 = pm * pm / e2;
     const F beta = sqrt(beta2);
     const F th0 = F(0.0136) / (beta * pm) * sqrt(tt) * (F(1) + F(0.038) * log_mat(tt / beta2));
-    const F th02 = th0 * th0;
-    const F kc = k * (ct / st);
-    q.c[ix(3, 3)] += th02 / (st * st);
-    q.c[ix(4, 4)] += th02;
-    q.c[ix(2, 2)] += kc * kc * th02;
-    q.c[ix(4, 2)] -= kc * th02;
+    th02 = th0 * th0;
+    kc = k * (ct / st);
     // PDG Bethe-Bloch mean energy loss in silicon (no density effect)
     const F e = sqrt(e2);
     const F bg2 = pm * pm * (F(1) / (P::mpi * P::mpi));
@@ -319,20 +317,34 @@ __device__ __forceinline__ bool apply_material(const DevLayer& L, PredT<F>& q, F
     const F dedx = P::K * P::ZA / beta2 * (F(0.5) * log_mat(F(2) * P::me * bg2 * tmax / (P::I * P::I)) - beta2);
     const F de = dedx * P::rho * (tt * P::X0) * F(1e-3);
     const F en = e - de;
-    if (!(en > P::mpi)) return false;
-    const F a = pm / sqrt((en - P::mpi) * (en + P::mpi));
-    q.k = k * a;
-    q.c[ix(2, 0)] *= a; q.c[ix(2, 1)] *= a; q.c[ix(3, 2)] *= a; q.c[ix(4, 2)] *= a;
-    q.c[ix(2, 2)] *= a * a;
-    return true;
+    if (!(en > P::mpi)) return -1;
+    a = pm / sqrt((en - P::mpi) * (en + P::mpi));
+    return 1;
+}
+
+// Adds the Highland Q to the (k, phi, theta) block of the surface-frame covariance qc and scales
+// row/column k by a (material_terms' outputs; the terms are formed in F, added in G).
+template <class F, class G>
+__device__ __forceinline__ void material_cov(G qc[15], F th02, F kc, F st, F a) {
+    qc[ix(3, 3)] += G(th02 / (st * st));
+    qc[ix(4, 4)] += G(th02);
+    qc[ix(2, 2)] += G(kc * kc * th02);
+    qc[ix(4, 2)] -= G(kc * th02);
+    const G ag = G(a);
+    qc[ix(2, 0)] *= ag; qc[ix(2, 1)] *= ag; qc[ix(3, 2)] *= ag; qc[ix(4, 2)] *= ag;
+    qc[ix(2, 2)] *= G(a * a);
 }
 
 // Propagates t to layer L.  Returns 1 (crossed; q holds the predicted state with material),
 // 0 (not crossed) or -1 (particle stopped in the material).  newton_it counts iterations.
 // dir (optional) gets sin(phi'), cos(phi'), sin(theta), cos(theta) at the crossing.
-template <class F>
-__device__ __forceinline__ int propagate(const DevLayer& L, float cBf, int material, const StateT<F>& t, PredT<F>& q,
-                                         int& newton_it, F* dir = nullptr) {
+// The trajectory, its Jacobian and the material terms are computed in F; the covariance cin (21,
+// global frame) is transported into qc (15, surface frame) in G (G = F for the plain step; the
+// seed fit takes F = float, G = double).  q.c is not touched.
+template <class F, class G>
+__device__ __forceinline__ int propagate_core(const DevLayer& L, float cBf, int material, const StateT<F>& t,
+                                              const G cin[21], PredT<F>& q, G qc[15], int& newton_it,
+                                              F* dir = nullptr) {
     using P = Phys<F>;
     const F cB = F(cBf);
     F sf, cf, st, ct;
@@ -499,31 +511,31 @@ __device__ __forceinline__ int propagate(const DevLayer& L, float cBf, int mater
 
     // ---- transport into the surface frame: rows (u1, u2, phi) dense, (k, theta) identity
     constexpr int D[3] = {0, 1, 3};   // local indices of the dense rows
-    F T[3][6];
+    G T[3][6];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
-            F acc = F(0);
+            G acc = G(0);
 #pragma unroll
-            for (int l = 0; l < 6; ++l) acc = fma(J[r][l], t.c[ix(l, j)], acc);
+            for (int l = 0; l < 6; ++l) acc = fma(G(J[r][l]), cin[ix(l, j)], acc);
             T[r][j] = acc;
         }
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
 #pragma unroll
         for (int p = 0; p <= r; ++p) {
-            F acc = F(0);
+            G acc = G(0);
 #pragma unroll
-            for (int l = 0; l < 6; ++l) acc = fma(T[r][l], J[p][l], acc);
-            q.c[ix(D[r], D[p])] = acc;
+            for (int l = 0; l < 6; ++l) acc = fma(T[r][l], G(J[p][l]), acc);
+            qc[ix(D[r], D[p])] = acc;
         }
-        q.c[ix(D[r], 2)] = T[r][3];
-        q.c[ix(4, D[r])] = T[r][5];
+        qc[ix(D[r], 2)] = T[r][3];
+        qc[ix(4, D[r])] = T[r][5];
     }
-    q.c[ix(2, 2)] = t.c[ix(3, 3)];
-    q.c[ix(4, 2)] = t.c[ix(5, 3)];
-    q.c[ix(4, 4)] = t.c[ix(5, 5)];
+    qc[ix(2, 2)] = cin[ix(3, 3)];
+    qc[ix(4, 2)] = cin[ix(5, 3)];
+    qc[ix(4, 4)] = cin[ix(5, 5)];
     q.xh = xh; q.xl = xl; q.yh = yh; q.yl = yl; q.zh = zh; q.zl = zl;
     q.k = t.k;
     q.phi = wrap_pi(t.phi + a);
@@ -531,8 +543,22 @@ __device__ __forceinline__ int propagate(const DevLayer& L, float cBf, int mater
     if (dir) {
         dir[0] = sfp; dir[1] = cfp; dir[2] = st; dir[3] = ct;
     }
-    if (material && !apply_material(L, q, st, ct, sfp, cfp)) return -1;
+    if (material) {
+        F th02, kc, ea;
+        const int mr = material_terms(L, q.xh, q.yh, q.k, st, ct, sfp, cfp, th02, kc, ea);
+        if (mr < 0) return -1;
+        if (mr > 0) {
+            material_cov(qc, th02, kc, st, ea);
+            q.k = q.k * ea;
+        }
+    }
     return 1;
+}
+
+template <class F>
+__device__ __forceinline__ int propagate(const DevLayer& L, float cBf, int material, const StateT<F>& t, PredT<F>& q,
+                                         int& newton_it, F* dir = nullptr) {
+    return propagate_core<F, F>(L, cBf, material, t, t.c, q, q.c, newton_it, dir);
 }
 
 // ----------------------------------------------------------------- window (a8)

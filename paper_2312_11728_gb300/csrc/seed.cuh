@@ -5,12 +5,13 @@
 
 namespace mk {
 
-// Seed fit of seed i in precision F.  Returns ok.
+// Hits of seed i and the prior of its fit (a1): the circle through the three transverse points
+// gives |curvature|, the charge (turning sign) and phi at hit 1; dz over the arc length gives
+// cot(theta); the covariance is diagonal and diffuse.  Returns ok (valid hits of one event).
 template <class F>
-__device__ __forceinline__ bool seed_fit(const DevGeom& g, const DevParams& P, const HitStore& H, const int* __restrict__ seed_hits,
-                         int i, StateT<F>& t, int lay[3], int& event) {
+__device__ __forceinline__ bool seed_prior(const DevGeom& g, const HitStore& H, const int* __restrict__ seed_hits,
+                                           int i, F m[3][3], F v[3][6], int lay[3], int& event, StateT<F>& t) {
     int id[3], ev[3];
-    F m[3][3], v[3][6];
     bool ok = true;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -57,6 +58,17 @@ __device__ __forceinline__ bool seed_fit(const DevGeom& g, const DevParams& P, c
     const F sk = F(0.5) * fabs(k) + F(0.05);
     t.c[ix(0, 0)] = F(0.01); t.c[ix(1, 1)] = F(0.01); t.c[ix(2, 2)] = F(0.01);
     t.c[ix(3, 3)] = sk * sk; t.c[ix(4, 4)] = F(0.0025); t.c[ix(5, 5)] = F(0.0025);
+    return ok;
+}
+
+// Seed fit of seed i entirely in precision F (the all-FP64 path takes F = double): update with
+// hit 1, then propagate to and update with hits 2 and 3.  Returns ok.
+template <class F>
+__device__ __forceinline__ bool seed_fit(const DevGeom& g, const DevParams& P, const HitStore& H,
+                                         const int* __restrict__ seed_hits, int i, StateT<F>& t, int lay[3],
+                                         int& event) {
+    F m[3][3], v[3][6];
+    bool ok = seed_prior(g, H, seed_hits, i, m, v, lay, event, t);
     int newton = 0;
     ok = ok && state_update(t, m[0][0], m[0][1], m[0][2], v[0]);
 #pragma unroll
