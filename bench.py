@@ -227,11 +227,9 @@ def measure_e2e(args, ctx, db, batch, fit, g, stream, kalman_steps, world, local
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    te = torch.tensor([e0.elapsed_time(e1) / 1e3], device=f"cuda:{local}", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    return {"value": kalman_steps * n_e2e * world / float(te.item()), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h)}
+    from paper_2312_11728_gb300 import pipeline
+    value, _, _ = pipeline.replica_throughput(e0.elapsed_time(e1) / 1e3, kalman_steps * n_e2e, dist, f"cuda:{local}")
+    return {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
 
 def main():
@@ -309,11 +307,7 @@ def main():
              "seed": np.mean([e[0].elapsed_time(e[1]) for e in ev_step]),
              "build": np.mean(build_ms),
              "fit": np.mean([e[2].elapsed_time(e[4]) for e in ev_step])}
-    t = torch.tensor([total_ms / 1e3], device=f"cuda:{local}", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    wall = float(t.item())
-    value = kalman_steps * args.steps * world / wall
+    value, wall, _ = pipeline.replica_throughput(total_ms / 1e3, kalman_steps * args.steps, dist, f"cuda:{local}")
 
     # ---- end to end through the C ABI with host (pinned) buffers, copies inside the timed region
     e2e = None

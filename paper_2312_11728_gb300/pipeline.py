@@ -106,3 +106,17 @@ def make_context(geom, params: dict, device: int = 0, stream=None) -> mkgb.Conte
     ctx.load_geometry(geom)
     ctx.set_params(dict(params, barrel_eta_max=params.get("barrel_eta_max", geom.barrel_eta_max)))
     return ctx
+
+
+def replica_throughput(seconds: float, units: int, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas (one process per GPU, each on its own
+    events): the units of all ranks / the slowest rank's time.  Returns (value, max seconds,
+    total units).  dist: torch.distributed (initialised) or None for one process."""
+    import torch
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    wall, total = float(t.item()), float(u.item())
+    return total / wall, wall, total

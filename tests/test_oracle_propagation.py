@@ -280,16 +280,30 @@ def test_multiple_scattering_q_matches_monte_carlo_kicks(orc):
         assert np.linalg.matrix_rank(ref, tol=1e-12 * np.abs(ref).max()) == 2
 
 
+def _golden(name):
+    import os
+    out = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if line:
+                k, v = line.split("=")
+                out[k.strip()] = float(v)
+    return out
+
+
 def test_bethe_bloch_minimum_matches_pdg_silicon(orc):
-    """PDG tabulates the minimum ionisation of silicon as 1.664 MeV cm^2/g at beta*gamma ~ 3.5
-    (with the density effect; without it the minimum is a little higher)."""
+    """The PDG tabulates the minimum ionisation of silicon (tests/golden/pdg_silicon.txt) at
+    beta*gamma ~ 3.5, with the density effect; without it the minimum is a little higher.  The
+    oracle's loss per unit thickness is converted with the tabulated density and X0."""
+    si = _golden("pdg_silicon.txt")
     m_pi = 0.13957039
     bg = np.exp(np.linspace(np.log(0.5), np.log(100), 400))
     t = 0.01
-    dedx = np.array([orc.eloss(b * m_pi, t) for b in bg]) * 1e3 / (2.329 * t * 9.37)
+    dedx = np.array([orc.eloss(b * m_pi, t) for b in bg]) * 1e3 / (si["density_g_cm3"] * t * si["radiation_length_cm"])
     i = np.argmin(dedx)
     assert 2.5 < bg[i] < 4.5
-    assert 1.0 < dedx[i] / 1.664 < 1.04
+    assert 1.0 < dedx[i] / si["min_ionization_mev_cm2_g"] < 1.04
     # energy loss grows at low momentum as 1/beta^2
     assert dedx[0] > 3.0 * dedx[i]
 
