@@ -76,7 +76,7 @@ def make_batch(seed, n_events=N_EVENTS):
     g = S.geometry_phase2()
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
         evs = pool.map(_gen_event, [(e, seed) for e in range(n_events)])
-    return g, S.concat_events(evs, g.n_layers)
+    return g, S.concat_events(evs, g.n_layers), evs
 
 
 def scan_launches(n):
@@ -159,7 +159,7 @@ def run_reference(args, rank):
     if rank != 0:
         return
     from paper_2312_11728_gb300 import pipeline, synth as S
-    g, batch = make_batch(0, n_events=2)
+    g, batch, _ = make_batch(0, n_events=2)
     fit = pipeline.fit_inputs(batch)
     params = S.default_params()
     import oracle
@@ -232,6 +232,35 @@ def measure_e2e(args, ctx, db, batch, fit, g, stream, kalman_steps, world, local
     return {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
 
+def measure_fp64_plain(args, g, params, evs, stream, local, rank, dist):
+    """The plain comparison path: every Kalman step (seed, search, fit) in FP64, one event per
+    call sequence (no batching across events), on the same events; 1 warm-up + 1 timed pass."""
+    import torch
+    from paper_2312_11728_gb300 import pipeline, synth as S
+    p64 = dict(params, precision=2)
+    ctx = pipeline.make_context(g, p64, device=local, stream=stream)
+    dbs = []
+    for ev in evs:
+        b = S.concat_events([ev], g.n_layers)
+        dbs.append(pipeline.DeviceBatch(b, pipeline.fit_inputs(b, seed=rank), g.max_plan, f"cuda:{local}"))
+    steps = 0
+    for db in dbs:                        # warm-up pass, counting the Kalman steps
+        pipeline.run_step(ctx, db)
+        steps += int(ctx.counters(0)[0] + ctx.counters(1)[0])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for db in dbs:
+        pipeline.run_step(ctx, db)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    value, wall, _ = pipeline.replica_throughput(e0.elapsed_time(e1) / 1e3, steps, dist, f"cuda:{local}")
+    return {"value": value, "unit": UNIT, "ms_per_step": wall * 1e3, "kalman_steps": steps,
+            "mode": "seed, search and fit all in FP64; events one at a time; same events as the FP32 line"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -241,6 +270,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--events", type=int, default=N_EVENTS, help="events per batch (profiling of small cases)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison path")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -250,7 +280,7 @@ def main():
         return
 
     from paper_2312_11728_gb300 import pipeline, synth as S
-    g, batch = make_batch(seed=rank, n_events=args.events)   # before the first CUDA call (spawn pool)
+    g, batch, evs = make_batch(seed=rank, n_events=args.events)   # before the first CUDA call (spawn pool)
     fit = pipeline.fit_inputs(batch, seed=rank)
     params = S.default_params()
 
@@ -309,6 +339,12 @@ def main():
              "fit": np.mean([e[2].elapsed_time(e[4]) for e in ev_step])}
     value, wall, _ = pipeline.replica_throughput(total_ms / 1e3, kalman_steps * args.steps, dist, f"cuda:{local}")
 
+    # ---- the plain all-FP64 path on the same events (the comparison factor)
+    fp64 = None
+    if not args.no_fp64:
+        fp64 = measure_fp64_plain(args, g, params, evs, stream, local, rank, dist)
+        fp64["factor"] = value / fp64["value"]
+
     # ---- end to end through the C ABI with host (pinned) buffers, copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -356,6 +392,7 @@ def main():
                      "flops_per_launch": int(build_flops(bc)),
                      "launch": "one mkgb_build call per step, timed with CUDA events on its stream"},
         "e2e": e2e,
+        "fp64_plain": fp64,
         "gpu_launches": int(launches_per_step * args.steps),
         "clocks": clocks,
         "counters": {"build": [int(x) for x in bc], "fit": [int(x) for x in fc]},

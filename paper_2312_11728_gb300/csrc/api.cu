@@ -58,7 +58,7 @@ struct mkgb_ctx {
     bool own_stream = false;
     int n_sms = 0;
     std::string err;
-    bool has_geom = false, has_params = false, has_hits = false, has_seeds = false;
+    bool has_geom = false, has_params = false, has_hits = false, has_seeds = false, seeds_fp64 = false;
     DevGeom geom_h;
     DevBuf geom_d;
     int max_plan_len = 0;
@@ -68,7 +68,7 @@ struct mkgb_ctx {
     std::vector<int64_t> seg_off_h;
     DevBuf seg_off, in_xyz, in_cov, pay, ep_tmp, bin_of_hit, hit_seg, bins, hb_ep, hb_pay, cursor, scan_tmp;
     int n_seeds = 0;
-    DevBuf seed_hits, seed_state, seed_info, seed_key, key_counts, key_cursor, seed_order, seed_scan_tmp;
+    DevBuf seed_hits, seed_state, seed_state64, seed_info, seed_key, key_counts, key_cursor, seed_order, seed_scan_tmp;
     DevBuf counters_build, counters_fit, queue, rescue_list, rescue_count, build_work;
     DevBuf stage[S_COUNT];
 };
@@ -189,7 +189,7 @@ void mkgb_destroy(mkgb_ctx* ctx) {
         cudaStreamSynchronize(ctx->stream);
         DevBuf* all[] = {&ctx->geom_d, &ctx->seg_off, &ctx->in_xyz, &ctx->in_cov, &ctx->pay, &ctx->ep_tmp,
                          &ctx->bin_of_hit, &ctx->hit_seg, &ctx->bins, &ctx->hb_ep, &ctx->hb_pay, &ctx->cursor,
-                         &ctx->scan_tmp, &ctx->seed_hits, &ctx->seed_state, &ctx->seed_info, &ctx->seed_key,
+                         &ctx->scan_tmp, &ctx->seed_hits, &ctx->seed_state, &ctx->seed_state64, &ctx->seed_info, &ctx->seed_key,
                          &ctx->key_counts, &ctx->key_cursor, &ctx->seed_order, &ctx->seed_scan_tmp,
                          &ctx->counters_build, &ctx->counters_fit, &ctx->queue, &ctx->rescue_list,
                          &ctx->rescue_count, &ctx->build_work};
@@ -375,6 +375,8 @@ int mkgb_seed(mkgb_ctx* ctx, int n_seeds, const int32_t* seed_hits, int on_devic
     const void* sh = nullptr;
     CK(stage_in(ctx, S_A, seed_hits, 12 * (size_t)n, on_device, &sh));
     CK(ensure(ctx->seed_state, 4 * (size_t)kSeedStateStride * n));
+    const bool fp64 = ctx->params.precision == MKGB_FP64;
+    if (fp64) CK(ensure(ctx->seed_state64, 8 * (size_t)kSeedStateStride * n));
     CK(ensure(ctx->seed_info, 16 * (size_t)n));
     CK(ensure(ctx->seed_key, 4 * (size_t)n));
     CK(ensure(ctx->seed_order, 4 * (size_t)n));
@@ -387,7 +389,8 @@ int mkgb_seed(mkgb_ctx* ctx, int n_seeds, const int32_t* seed_hits, int on_devic
     CK(stage_out(ctx, S_D, info_out, 12 * (size_t)n, on_device, &i3));
     CK(cudaMemsetAsync(ctx->key_counts.p, 0, 4 * (nkeys + 1), st));
     CK(launch_seed(st, (const DevGeom*)ctx->geom_d.p, ctx->params, hit_store(ctx), n, (const int*)sh,
-                   (float*)ctx->seed_state.p, (int4*)ctx->seed_info.p, (int*)ctx->seed_key.p,
+                   (float*)ctx->seed_state.p, fp64 ? (double*)ctx->seed_state64.p : nullptr,
+                   (int4*)ctx->seed_info.p, (int*)ctx->seed_key.p,
                    (int*)ctx->key_counts.p, (float*)s6, (float*)c21, (int*)i3));
     CK(exclusive_scan(st, (const int*)ctx->key_counts.p, (int*)ctx->key_counts.p, nkeys, (int*)ctx->seed_scan_tmp.p));
     CK(cudaMemcpyAsync(ctx->key_cursor.p, ctx->key_counts.p, 4 * nkeys, cudaMemcpyDeviceToDevice, st));
@@ -398,6 +401,7 @@ int mkgb_seed(mkgb_ctx* ctx, int n_seeds, const int32_t* seed_hits, int on_devic
     if (!on_device) CK(cudaStreamSynchronize(st));
     ctx->n_seeds = n;
     ctx->has_seeds = true;
+    ctx->seeds_fp64 = fp64;
     return MKGB_OK;
 }
 
@@ -423,10 +427,14 @@ int mkgb_build(mkgb_ctx* ctx, const mkgb_tracks* out, int on_device) {
     CK(stage_out(ctx, S_F, out->nholes, 4 * n, on_device, &p)); d.nholes = (int*)p;
     CK(stage_out(ctx, S_G, out->hits, 4 * n * out->max_plan, on_device, &p)); d.hits = (int*)p;
     d.max_plan = out->max_plan;
-    SeedStore S{ctx->n_seeds, (const float*)ctx->seed_state.p, (const int4*)ctx->seed_info.p,
+    SeedStore S{ctx->n_seeds, (const float*)ctx->seed_state.p, (const double*)ctx->seed_state64.p,
+                (const int4*)ctx->seed_info.p,
                 (const int*)ctx->seed_order.p};
-    CK(ensure(ctx->build_work, build_work_bytes(ctx->n_seeds, ctx->max_plan_len)));
-    const BuildWork w = carve_build_work(ctx->build_work.p, ctx->n_seeds, ctx->max_plan_len);
+    const int prec = ctx->params.precision;
+    if (prec == MKGB_FP64 && !ctx->seeds_fp64)
+        return fail(ctx, MKGB_ESTATE, "FP64 search needs seeds made under the FP64 precision");
+    CK(ensure(ctx->build_work, build_work_bytes(ctx->n_seeds, ctx->max_plan_len, prec)));
+    const BuildWork w = carve_build_work(ctx->build_work.p, ctx->n_seeds, ctx->max_plan_len, prec);
     CK(cudaMemsetAsync(ctx->counters_build.p, 0, 8 * kNumCounters, st));
     CK(launch_build(st, (const DevGeom*)ctx->geom_d.p, ctx->max_plan_len, ctx->params, hit_store(ctx), S, d, w,
                     (unsigned long long*)ctx->counters_build.p, ctx->n_sms));

@@ -30,6 +30,7 @@ struct HitStore {
 struct SeedStore {
     int n;
     const float* state;        // n x kSeedStateStride
+    const double* state64;     // n x kSeedStateStride, FP64 states (precision MKGB_FP64 only)
     const int4* info;          // n: (region, first plan step, event, status)
     const int* order;          // n: seeds sorted by (event, eta cell, phi cell)
 };
@@ -47,9 +48,9 @@ struct BuildOutDev {
 
 // Work buffers of the search (k_build.cu): per seed 8 candidate slots, double-buffered.
 struct BuildWork {
-    float4* st[2];    // slot states, 8 float4 each
+    unsigned char* st[2];   // slot states, 32 words (FP32 or FP64 per the precision)
     int4* meta[2];    // slot (score, chi2 sum, nfound | nholes << 8 | stopped << 16, alive)
-    float4* pr;       // slot predictions at the round's layer, 6 float4 each
+    unsigned char* pr;      // slot predictions at the round's layer, 24 words
     int4* ls;         // slot children: (n hits, non-hit kind, non-hit score, -) + 4 x (chi2, hit, chi2, hit)
     int* live[2];     // work list of live candidate slots per round
     int* seeds[2];    // work list of seeds with a live candidate per round
@@ -75,12 +76,12 @@ cudaError_t launch_seed_scatter(cudaStream_t st, int n, const int* key_of, int* 
 
 // ---- k_seed.cu
 cudaError_t launch_seed(cudaStream_t st, const DevGeom* g, DevParams P, HitStore H, int n, const int* seed_hits,
-                        float* state, int4* info, int* key_of, int* key_counts, float* state6, float* cov21,
-                        int* info3);
+                        float* state, double* state64, int4* info, int* key_of, int* key_counts, float* state6,
+                        float* cov21, int* info3);
 
 // ---- k_build.cu
-size_t build_work_bytes(int n_seeds, int max_plan_len);
-BuildWork carve_build_work(void* base, int n_seeds, int max_plan_len);
+size_t build_work_bytes(int n_seeds, int max_plan_len, int precision);
+BuildWork carve_build_work(void* base, int n_seeds, int max_plan_len, int precision);
 cudaError_t launch_build(cudaStream_t st, const DevGeom* g, int max_plan_len, DevParams P, HitStore H, SeedStore S,
                          BuildOutDev out, BuildWork w, unsigned long long* counters, int n_sms);
 

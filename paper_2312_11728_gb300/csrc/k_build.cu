@@ -40,53 +40,78 @@ __device__ __forceinline__ unsigned long long order_key(float score, int slot) {
 __device__ __forceinline__ float shfl_f(float v, int src) { return __shfl_sync(kFull, v, src); }
 __device__ __forceinline__ int shfl_i(int v, int src) { return __shfl_sync(kFull, v, src); }
 
-// ---- slot records
+// ---- slot records: a state is 32 words (xh, yh, zh, xl, yl, zl, k, phi, theta, 21 covariance
+// terms, 2 spare), a prediction 24 words; words are F, moved as 16-byte vectors
 
-__device__ __forceinline__ void load_state_rec(const float4* __restrict__ r, State& t) {
-    float f[32];
+__device__ __forceinline__ void unpack16(const float4& v, float* f) { f[0] = v.x; f[1] = v.y; f[2] = v.z; f[3] = v.w; }
+__device__ __forceinline__ void unpack16(const double2& v, double* f) { f[0] = v.x; f[1] = v.y; }
+__device__ __forceinline__ float4 pack16(const float* f) { return make_float4(f[0], f[1], f[2], f[3]); }
+__device__ __forceinline__ double2 pack16(const double* f) { return make_double2(f[0], f[1]); }
+template <class F> struct Vec16;
+template <> struct Vec16<float> { using T = float4; };
+template <> struct Vec16<double> { using T = double2; };
+
+template <class F, int N> __device__ __forceinline__ void load_words(const unsigned char* __restrict__ p, F* f) {
+    using V = typename Vec16<F>::T;
+    constexpr int per = 16 / sizeof(F);
+    const V* v = reinterpret_cast<const V*>(p);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const float4 v = r[i];
-        f[4 * i] = v.x; f[4 * i + 1] = v.y; f[4 * i + 2] = v.z; f[4 * i + 3] = v.w;
-    }
+    for (int i = 0; i < N / per; ++i) unpack16(v[i], f + per * i);
+}
+
+template <class F, int N> __device__ __forceinline__ void store_words(unsigned char* __restrict__ p, const F* f) {
+    using V = typename Vec16<F>::T;
+    constexpr int per = 16 / sizeof(F);
+    V* v = reinterpret_cast<V*>(p);
+#pragma unroll
+    for (int i = 0; i < N / per; ++i) v[i] = pack16(f + per * i);
+}
+
+template <class F> constexpr size_t state_bytes() { return 32 * sizeof(F); }
+template <class F> constexpr size_t pred_bytes() { return 24 * sizeof(F); }
+
+template <class F> __device__ __forceinline__ void load_state_rec(const unsigned char* r, StateT<F>& t) {
+    F f[32];
+    load_words<F, 32>(r, f);
     t.xh = f[0]; t.yh = f[1]; t.zh = f[2]; t.xl = f[3]; t.yl = f[4]; t.zl = f[5];
     t.k = f[6]; t.phi = f[7]; t.th = f[8];
 #pragma unroll
     for (int i = 0; i < 21; ++i) t.c[i] = f[9 + i];
 }
 
-__device__ __forceinline__ void store_state_rec(float4* __restrict__ r, const State& t) {
-    float f[32];
+template <class F> __device__ __forceinline__ void store_state_rec(unsigned char* r, const StateT<F>& t) {
+    F f[32];
     f[0] = t.xh; f[1] = t.yh; f[2] = t.zh; f[3] = t.xl; f[4] = t.yl; f[5] = t.zl;
     f[6] = t.k; f[7] = t.phi; f[8] = t.th;
 #pragma unroll
     for (int i = 0; i < 21; ++i) f[9 + i] = t.c[i];
-    f[30] = 0.0f; f[31] = 0.0f;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) r[i] = make_float4(f[4 * i], f[4 * i + 1], f[4 * i + 2], f[4 * i + 3]);
+    f[30] = F(0); f[31] = F(0);
+    store_words<F, 32>(r, f);
 }
 
-__device__ __forceinline__ void load_pred_rec(const float4* __restrict__ r, Pred& q) {
-    float f[24];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        const float4 v = r[i];
-        f[4 * i] = v.x; f[4 * i + 1] = v.y; f[4 * i + 2] = v.z; f[4 * i + 3] = v.w;
-    }
+template <class F> __device__ __forceinline__ void load_pred_rec(const unsigned char* r, PredT<F>& q) {
+    F f[24];
+    load_words<F, 24>(r, f);
     q.xh = f[0]; q.yh = f[1]; q.zh = f[2]; q.xl = f[3]; q.yl = f[4]; q.zl = f[5];
     q.k = f[6]; q.phi = f[7]; q.th = f[8];
 #pragma unroll
     for (int i = 0; i < 15; ++i) q.c[i] = f[9 + i];
 }
 
-__device__ __forceinline__ void store_pred_rec(float4* __restrict__ r, const Pred& q) {
-    float f[24];
+template <class F> __device__ __forceinline__ void store_pred_rec(unsigned char* r, const PredT<F>& q) {
+    F f[24];
     f[0] = q.xh; f[1] = q.yh; f[2] = q.zh; f[3] = q.xl; f[4] = q.yl; f[5] = q.zl;
     f[6] = q.k; f[7] = q.phi; f[8] = q.th;
 #pragma unroll
     for (int i = 0; i < 15; ++i) f[9 + i] = q.c[i];
+    store_words<F, 24>(r, f);
+}
+
+template <class F> __device__ __forceinline__ void copy_state_rec(const unsigned char* src, unsigned char* dst) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
-    for (int i = 0; i < 6; ++i) r[i] = make_float4(f[4 * i], f[4 * i + 1], f[4 * i + 2], f[4 * i + 3]);
+    for (int q = 0; q < (int)(state_bytes<F>() / 16); ++q) d4[q] = s4[q];
 }
 
 // slot meta: (score, chi2 sum, nfound | nholes << 8 | stopped << 16, alive)
@@ -146,6 +171,7 @@ struct BuildArgs {
 };
 
 // ---- round 0: slot 0 of every seed with work takes the seed state
+template <class F>
 __global__ void __launch_bounds__(kThreads) k_start(BuildArgs a) {
     const DevGeom* __restrict__ g = a.geom;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;   // seed position in the (event, eta, phi) order
@@ -169,10 +195,10 @@ __global__ void __launch_bounds__(kThreads) k_start(BuildArgs a) {
 #pragma unroll
         for (int c = 1; c < kGroup; ++c) a.w.meta[0][i * kGroup + c] = dead;
         if (work) {
-            const float4* src = reinterpret_cast<const float4*>(a.S.state + (int64_t)seed * kSeedStateStride);
-            float4* dst = a.w.st[0] + (int64_t)i * kGroup * 8;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) dst[q] = src[q];
+            const unsigned char* src = sizeof(F) == 4
+                ? reinterpret_cast<const unsigned char*>(a.S.state + (int64_t)seed * kSeedStateStride)
+                : reinterpret_cast<const unsigned char*>(a.S.state64 + (int64_t)seed * kSeedStateStride);
+            copy_state_rec<F>(src, a.w.st[0] + (int64_t)i * kGroup * state_bytes<F>());
             a.w.meta[0][i * kGroup] = pack_meta(0.0f, 0.0f, 3, 0, false, true);
         } else {
             a.w.meta[0][i * kGroup] = dead;
@@ -183,6 +209,7 @@ __global__ void __launch_bounds__(kThreads) k_start(BuildArgs a) {
 }
 
 // ---- a4-a9 for every live candidate of round tau
+template <class F>
 __global__ void __launch_bounds__(kThreads) k_find(BuildArgs a, int tau) {
     __shared__ DevGeom g;
     // per-thread sorted list of hit children (chi2 asc, id asc), one column per thread
@@ -211,14 +238,14 @@ __global__ void __launch_bounds__(kThreads) k_find(BuildArgs a, int tau) {
         const int4 si = a.w.sinfo[i];
         const int layer = g.plan[si.x + tau];
         const DevLayer& L = g.layers[layer];
-        State t;
-        load_state_rec(a.w.st[cur] + (int64_t)sl * 8, t);
+        StateT<F> t;
+        load_state_rec(a.w.st[cur] + (int64_t)sl * state_bytes<F>(), t);
         const int4 mt = a.w.meta[cur][sl];
         const float score = __int_as_float(mt.x);
         const int nholes = (mt.z >> 8) & 0xff;
 
-        Pred q;
-        float dir[4];
+        PredT<F> q;
+        F dir[4];
         int newton = 0;
         const int r = propagate(L, g.cB, P.material, t, q, newton, dir);
         c_newton += newton;
@@ -236,8 +263,8 @@ __global__ void __launch_bounds__(kThreads) k_find(BuildArgs a, int tau) {
                 nh_kind = K_STOP;
                 nh_score = score;
             }
-            const FrameT<float> fr = frame_of(L.kind, q.xh, q.yh, dir[0], dir[1], dir[2], dir[3]);
-            const Window w = window(L, P, q, fr);
+            const FrameT<F> fr = frame_of(L.kind, q.xh, q.yh, dir[0], dir[1], dir[2], dir[3]);
+            const WindowT<F> w = window(L, P, q, fr);
             const float eps = 1e-5f;
             const float fe0 = (w.eta - w.deta - eps - L.eta_lo) * L.eta_scale;
             const float fe1 = (w.eta + w.deta + eps - L.eta_lo) * L.eta_scale;
@@ -266,13 +293,14 @@ __global__ void __launch_bounds__(kThreads) k_find(BuildArgs a, int tau) {
                     for (int hq = q0; hq < q1; ++hq) {
                         ++c_tested;
                         const float2 ep = __ldg(a.H.hb_ep + hq);
-                        if (fabsf(ep.x - w.eta) <= w.deta && fabsf(wrap_pi(ep.y - w.phi)) <= w.dphi) {
+                        if (fabs(F(ep.x) - w.eta) <= w.deta && fabs(wrap_pi(F(ep.y) - w.phi)) <= w.dphi) {
                             ++c_chi2;
-                            float m[3], v[6];
+                            F m[3], v[6];
                             int id;
                             load_hit(a.H.hb_pay, hq, m, v, &id);
-                            float x2;
-                            if (chi2_hit(fr, q, m[0], m[1], m[2], v, x2) && x2 < P.chi2_cut) {
+                            F x2f;
+                            if (chi2_hit(fr, q, m[0], m[1], m[2], v, x2f) && x2f < F(P.chi2_cut)) {
+                                const float x2 = float(x2f);   // scores and child order in FP32
                                 // insert into the sorted list (kept to its first kGroup entries)
                                 int j = n_h < kGroup ? n_h : kGroup - 1;
                                 const bool fits = n_h < kGroup ||
@@ -295,7 +323,7 @@ __global__ void __launch_bounds__(kThreads) k_find(BuildArgs a, int tau) {
                     }
                 }
             }
-            store_pred_rec(a.w.pr + (int64_t)sl * 6, q);
+            store_pred_rec(a.w.pr + (int64_t)sl * pred_bytes<F>(), q);
         }
         int4* lrec = a.w.ls + (int64_t)sl * 5;
         lrec[0] = make_int4(n_h, nh_kind, __float_as_int(nh_score), 0);
@@ -308,6 +336,7 @@ __global__ void __launch_bounds__(kThreads) k_find(BuildArgs a, int tau) {
 }
 
 // ---- a10-a11 for every seed with a live candidate in round tau
+template <class F>
 __global__ void __launch_bounds__(kThreads, 5) k_select(BuildArgs a, int tau) {
     __shared__ DevGeom g;
     load_geom_smem(a.geom, g);
@@ -430,18 +459,16 @@ __global__ void __launch_bounds__(kThreads, 5) k_select(BuildArgs a, int tau) {
             c_alive = true;
             c_stopped = ((pm.z >> 16) & 1) != 0;
             if (my_kind == K_SKIP || my_kind == K_CARRY) {
-                const float4* src = a.w.st[cur] + (int64_t)psl * 8;
-                float4* dst = a.w.st[nxt] + (int64_t)csl * 8;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) dst[q] = src[q];
+                copy_state_rec<F>(a.w.st[cur] + (int64_t)psl * state_bytes<F>(),
+                                  a.w.st[nxt] + (int64_t)csl * state_bytes<F>());
                 if (my_kind == K_SKIP) code = MKGB_HIT_SKIP;
             } else {
                 const DevLayer& L = g.layers[g.plan[si.x + tau]];
-                Pred pq;
-                load_pred_rec(a.w.pr + (int64_t)psl * 6, pq);
-                State t;
+                PredT<F> pq;
+                load_pred_rec(a.w.pr + (int64_t)psl * pred_bytes<F>(), pq);
+                StateT<F> t;
                 if (my_kind == K_HIT) {
-                    float m[3], v[6];
+                    F m[3], v[6];
                     int id;
                     load_hit(a.H.hb_pay, my_q, m, v, &id);
                     if (kalman_update(L.kind, pq, m[0], m[1], m[2], v, t)) {
@@ -461,7 +488,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_select(BuildArgs a, int tau) {
                         c_stopped = true;
                     }
                 }
-                store_state_rec(a.w.st[nxt] + (int64_t)csl * 8, t);
+                store_state_rec(a.w.st[nxt] + (int64_t)csl * state_bytes<F>(), t);
             }
             a.w.trail[((int64_t)i * a.max_steps + tau) * kGroup + slot] = ((code + 4) << 3) | my_parent;
         }
@@ -477,6 +504,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_select(BuildArgs a, int tau) {
 }
 
 // ---- best candidate per seed and its hit list (a13); 8 lanes per seed
+template <class F>
 __global__ void __launch_bounds__(kThreads) k_finish(BuildArgs a) {
     const int lane = threadIdx.x & 31, slot = lane & 7, gbase = lane & ~7;
     const int gi = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
@@ -497,8 +525,8 @@ __global__ void __launch_bounds__(kThreads) k_finish(BuildArgs a) {
     float* po = a.out.params + 6 * (int64_t)seed;
     float* co = a.out.cov + 21 * (int64_t)seed;
     if (best >= 0) {
-        State t;
-        load_state_rec(a.w.st[fin] + (int64_t)(i * kGroup + best) * 8, t);
+        StateT<F> t;
+        load_state_rec(a.w.st[fin] + (int64_t)(i * kGroup + best) * state_bytes<F>(), t);
         store_state6(t, po, co);
         a.out.chi2[seed] = __int_as_float(mt.y);
         a.out.score[seed] = __int_as_float(mt.x);
@@ -536,8 +564,8 @@ namespace {
 
 // Carves the work buffers out of one allocation (256-byte aligned pieces); with base == nullptr
 // only the total size is computed.
-size_t layout_build_work(char* base, int n_seeds, int max_plan_len, BuildWork* w) {
-    const size_t ns = (size_t)n_seeds, slots = ns * kGroup;
+size_t layout_build_work(char* base, int n_seeds, int max_plan_len, int word_bytes, BuildWork* w) {
+    const size_t ns = (size_t)n_seeds, slots = ns * kGroup, wb = (size_t)word_bytes;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         char* r = base ? base + off : nullptr;
@@ -545,11 +573,11 @@ size_t layout_build_work(char* base, int n_seeds, int max_plan_len, BuildWork* w
         return r;
     };
     BuildWork t;
-    t.st[0] = reinterpret_cast<float4*>(take(slots * 128));
-    t.st[1] = reinterpret_cast<float4*>(take(slots * 128));
+    t.st[0] = reinterpret_cast<unsigned char*>(take(slots * 32 * wb));
+    t.st[1] = reinterpret_cast<unsigned char*>(take(slots * 32 * wb));
     t.meta[0] = reinterpret_cast<int4*>(take(slots * 16));
     t.meta[1] = reinterpret_cast<int4*>(take(slots * 16));
-    t.pr = reinterpret_cast<float4*>(take(slots * 96));
+    t.pr = reinterpret_cast<unsigned char*>(take(slots * 24 * wb));
     t.ls = reinterpret_cast<int4*>(take(slots * 80));
     t.live[0] = reinterpret_cast<int*>(take(slots * 4));
     t.live[1] = reinterpret_cast<int*>(take(slots * 4));
@@ -563,15 +591,29 @@ size_t layout_build_work(char* base, int n_seeds, int max_plan_len, BuildWork* w
     return off;
 }
 
-}  // namespace
-
-size_t build_work_bytes(int n_seeds, int max_plan_len) {
-    return layout_build_work(nullptr, n_seeds, max_plan_len, nullptr);
+template <class F>
+cudaError_t launch_rounds(cudaStream_t st, const BuildArgs& a, int n, int max_plan_len, int n_sms) {
+    const int nb = (n + kThreads - 1) / kThreads;
+    k_start<F><<<nb, kThreads, 0, st>>>(a);
+    const int grid_find = resident_grid((const void*)k_find<F>, n_sms, 0);
+    const int grid_sel = resident_grid((const void*)k_select<F>, n_sms, 0);
+    for (int tau = 0; tau < max_plan_len; ++tau) {
+        k_find<F><<<grid_find, kThreads, 0, st>>>(a, tau);
+        k_select<F><<<grid_sel, kThreads, 0, st>>>(a, tau);
+    }
+    k_finish<F><<<(n * kGroup + kThreads - 1) / kThreads, kThreads, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
-BuildWork carve_build_work(void* base, int n_seeds, int max_plan_len) {
+}  // namespace
+
+size_t build_work_bytes(int n_seeds, int max_plan_len, int precision) {
+    return layout_build_work(nullptr, n_seeds, max_plan_len, precision == MKGB_FP64 ? 8 : 4, nullptr);
+}
+
+BuildWork carve_build_work(void* base, int n_seeds, int max_plan_len, int precision) {
     BuildWork w;
-    layout_build_work(static_cast<char*>(base), n_seeds, max_plan_len, &w);
+    layout_build_work(static_cast<char*>(base), n_seeds, max_plan_len, precision == MKGB_FP64 ? 8 : 4, &w);
     return w;
 }
 
@@ -581,16 +623,9 @@ cudaError_t launch_build(cudaStream_t st, const DevGeom* g, int max_plan_len, De
     BuildArgs a{g, P, H, S, out, w, counters, max_plan_len};
     cudaError_t e = cudaMemsetAsync(w.counts, 0, 16, st);
     if (e != cudaSuccess) return e;
-    const int nb = (S.n + kThreads - 1) / kThreads;
-    k_start<<<nb, kThreads, 0, st>>>(a);
-    const int grid_find = resident_grid((const void*)k_find, n_sms, 0);
-    const int grid_sel = resident_grid((const void*)k_select, n_sms, 0);
-    for (int tau = 0; tau < max_plan_len; ++tau) {
-        k_find<<<grid_find, kThreads, 0, st>>>(a, tau);
-        k_select<<<grid_sel, kThreads, 0, st>>>(a, tau);
-    }
-    k_finish<<<(S.n * kGroup + kThreads - 1) / kThreads, kThreads, 0, st>>>(a);
-    return cudaGetLastError();
+    // MKGB_FP64: the plain all-FP64 comparison path (same rounds, every Kalman step in FP64)
+    return P.precision == MKGB_FP64 ? launch_rounds<double>(st, a, S.n, max_plan_len, n_sms)
+                                    : launch_rounds<float>(st, a, S.n, max_plan_len, n_sms);
 }
 
 }  // namespace mk

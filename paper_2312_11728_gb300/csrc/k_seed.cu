@@ -49,7 +49,8 @@ __device__ __forceinline__ void write_seed(const State& t, int i, int region, in
 
 __global__ void __launch_bounds__(kThreads) k_seed(const DevGeom* __restrict__ gp, DevParams P, HitStore H, int n,
                                                    const int* __restrict__ seed_hits, float* __restrict__ state,
-                                                   int4* __restrict__ info, float* state6, float* cov21, int* info3) {
+                                                   double* __restrict__ state64, int4* __restrict__ info,
+                                                   float* state6, float* cov21, int* info3) {
     __shared__ DevGeom g;
     load_geom(gp, g);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -61,6 +62,14 @@ __global__ void __launch_bounds__(kThreads) k_seed(const DevGeom* __restrict__ g
     narrow_state(td, t);
     seed_region(g, P, t.th, lay[2], ok, region, start);
     write_seed(t, i, region, start, event, state, info, state6, cov21, info3);
+    if (state64) {   // the FP64 state for the all-FP64 search
+        double* o = state64 + (int64_t)i * kSeedStateStride;
+        o[0] = td.xh; o[1] = td.yh; o[2] = td.zh; o[3] = td.xl; o[4] = td.yl; o[5] = td.zl;
+        o[6] = td.k; o[7] = td.phi; o[8] = td.th;
+#pragma unroll
+        for (int q = 0; q < 21; ++q) o[9 + q] = td.c[q];
+        o[30] = 0.0; o[31] = 0.0;
+    }
 }
 
 // (event, eta cell, phi cell) key of every seed and its histogram, for the hit-coherent order
@@ -83,11 +92,11 @@ __global__ void __launch_bounds__(kThreads) k_seed_key(int n, const float* __res
 }  // namespace
 
 cudaError_t launch_seed(cudaStream_t st, const DevGeom* g, DevParams P, HitStore H, int n, const int* seed_hits,
-                        float* state, int4* info, int* key_of, int* key_counts, float* state6, float* cov21,
-                        int* info3) {
+                        float* state, double* state64, int4* info, int* key_of, int* key_counts, float* state6,
+                        float* cov21, int* info3) {
     if (n == 0) return cudaSuccess;
     const int blocks = (n + kThreads - 1) / kThreads;
-    k_seed<<<blocks, kThreads, 0, st>>>(g, P, H, n, seed_hits, state, info, state6, cov21, info3);
+    k_seed<<<blocks, kThreads, 0, st>>>(g, P, H, n, seed_hits, state, state64, info, state6, cov21, info3);
     k_seed_key<<<blocks, kThreads, 0, st>>>(n, state, info, key_of, key_counts);
     return cudaGetLastError();
 }

@@ -563,33 +563,35 @@ __device__ __forceinline__ int propagate(const DevLayer& L, float cBf, int mater
 
 // ----------------------------------------------------------------- window (a8)
 
-struct Window {
-    float eta, phi, deta, dphi;
+template <class F> struct WindowT {
+    F eta, phi, deta, dphi;
 };
+using Window = WindowT<float>;
 
-__device__ __forceinline__ Window window(const DevLayer& L, const DevParams& P, const Pred& q,
-                                         const FrameT<float>& fr) {
-    const float x = q.xh, y = q.yh, z = q.zh;
-    const float rt2 = x * x + y * y, rt = sqrtf(rt2), r3 = sqrtf(rt2 + z * z);
-    Window w;
-    w.eta = asinhf(z / rt);
-    w.phi = atan2f(y, x);
-    const float c = x / rt, sn = y / rt;
+template <class F>
+__device__ __forceinline__ WindowT<F> window(const DevLayer& L, const DevParams& P, const PredT<F>& q,
+                                             const FrameT<F>& fr) {
+    const F x = q.xh, y = q.yh, z = q.zh;
+    const F rt2 = x * x + y * y, rt = sqrt(rt2), r3 = sqrt(rt2 + z * z);
+    WindowT<F> w;
+    w.eta = asinh(z / rt);
+    w.phi = atan2(y, x);
+    const F c = x / rt, sn = y / rt;
     // gradients in (r-hat, phi-hat, z-hat) at the predicted point
-    const float ge_r = -z / (rt * r3), ge_z = 1.0f / r3;
-    const float gp_p = 1.0f / rt;
-    const float sr2 = L.sig[0] * L.sig[0], sp2 = L.sig[1] * L.sig[1], sz2 = L.sig[2] * L.sig[2];
-    float ve = ge_r * ge_r * sr2 + ge_z * ge_z * sz2;
-    float vp = gp_p * gp_p * sp2;
+    const F ge_r = -z / (rt * r3), ge_z = F(1) / r3;
+    const F gp_p = F(1) / rt;
+    const F sr2 = F(L.sig[0]) * F(L.sig[0]), sp2 = F(L.sig[1]) * F(L.sig[1]), sz2 = F(L.sig[2]) * F(L.sig[2]);
+    F ve = ge_r * ge_r * sr2 + ge_z * ge_z * sz2;
+    F vp = gp_p * gp_p * sp2;
     // surface part: gradient components along e1, e2
-    const float geg[3] = {ge_r * c, ge_r * sn, ge_z};       // eta gradient, global
-    const float gpg[3] = {-gp_p * sn, gp_p * c, 0.0f};     // phi gradient, global
-    const float ge1 = dot3(fr.e1, geg), ge2 = dot3(fr.e2, geg);
-    const float gp1 = dot3(fr.e1, gpg), gp2 = dot3(fr.e2, gpg);
-    ve += ge1 * ge1 * q.c[0] + 2.0f * ge1 * ge2 * q.c[1] + ge2 * ge2 * q.c[2];
-    vp += gp1 * gp1 * q.c[0] + 2.0f * gp1 * gp2 * q.c[1] + gp2 * gp2 * q.c[2];
-    w.deta = fminf(fmaxf(P.nsig * sqrtf(fmaxf(ve, 0.0f)), P.deta_min), P.deta_max);
-    w.dphi = fminf(fmaxf(P.nsig * sqrtf(fmaxf(vp, 0.0f)), P.dphi_min), P.dphi_max);
+    const F geg[3] = {ge_r * c, ge_r * sn, ge_z};       // eta gradient, global
+    const F gpg[3] = {-gp_p * sn, gp_p * c, F(0)};      // phi gradient, global
+    const F ge1 = dot3(fr.e1, geg), ge2 = dot3(fr.e2, geg);
+    const F gp1 = dot3(fr.e1, gpg), gp2 = dot3(fr.e2, gpg);
+    ve += ge1 * ge1 * q.c[0] + F(2) * ge1 * ge2 * q.c[1] + ge2 * ge2 * q.c[2];
+    vp += gp1 * gp1 * q.c[0] + F(2) * gp1 * gp2 * q.c[1] + gp2 * gp2 * q.c[2];
+    w.deta = fmin(fmax(F(P.nsig) * sqrt(fmax(ve, F(0))), F(P.deta_min)), F(P.deta_max));
+    w.dphi = fmin(fmax(F(P.nsig) * sqrt(fmax(vp, F(0))), F(P.dphi_min)), F(P.dphi_max));
     return w;
 }
 

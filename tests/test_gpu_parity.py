@@ -184,6 +184,28 @@ def test_build_matches_oracle(lib, which, request):
         assert abs(gc[k] - oc[k]) <= 0.02 * oc[k] + 10, (k, gc, oc)
 
 
+def test_all_fp64_path_matches_oracle(lib, phase2_small):
+    """The plain comparison path (precision MKGB_FP64: every Kalman step of the search and the fit
+    in FP64) against the oracle with the same tolerances as the FP32 path."""
+    g, batch, params = phase2_small
+    p64 = dict(params, precision=2)
+    ctx = _ctx(g, p64)
+    fi = pipeline.fit_inputs(batch)
+    res = pipeline.run_host(ctx, batch, g.max_plan, fi)
+    orc = oracle.Oracle(g, p64)
+    o = PR.oracle_build(orc, batch)
+    rep = _report("build_fp64_phase2_small", PR.compare_build(res["build"], o))
+    assert len(rep["hit_mismatch"]) == 0, rep
+    assert rep["failed_mismatch"] == 0, rep
+    assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0 and rep["count_bad"] == 0, rep
+    r = orc.fit_batch(fi.layers, fi.hits, batch.hit_xyz.astype(np.float64), batch.hit_cov.astype(np.float64),
+                      fi.p0.astype(np.float64), fi.c0.astype(np.float64))
+    rf = _report("fit_fp64_phase2_small", PR.compare_fit(res["fit"], r))
+    assert rf["status_bad"] == 0 and rf["param_bad"] == 0 and rf["cov_bad"] == 0 and rf["chi2_bad"] == 0, rf
+    # FP64 sits far inside the tolerances that FP32 uses
+    assert rep["worst_param"] < 0.05 and rf["worst_param"] < 0.05, (rep["worst_param"], rf["worst_param"])
+
+
 def test_device_and_host_paths_agree_and_are_deterministic(lib, phase2_small):
     import torch
     g, batch, params = phase2_small
