@@ -261,6 +261,39 @@ def measure_fp64_plain(args, g, params, evs, stream, local, rank, dist):
             "mode": "seed, search and fit all in FP64; events one at a time; same events as the FP32 line"}
 
 
+def measure_fit_grad(args, local, rank, dist, stream):
+    """The fit's derivative on the differentiable-fit workload (100,000 tracks over 22 layers of
+    a misaligned detector): one mkgb_fit_grad call after a warm-up call, CUDA-event timed."""
+    import torch
+    from paper_2312_11728_gb300 import pipeline, synth as S
+    g, evs, _, _ = S.workload_aligned_fit(n_tracks=100_000, seed=rank)
+    b = S.concat_events(evs, g.n_layers)
+    fi = pipeline.fit_inputs(b, seed=rank)
+    ctx = pipeline.make_context(g, S.default_params(), device=local, stream=stream)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(f"cuda:{local}")
+    ctx.load_hits(b.n_events, b.hit_off, dev(b.hit_xyz), dev(b.hit_cov))
+    n, L = fi.layers.shape[0], g.n_layers
+    ins = dict(layers=dev(fi.layers), hits=dev(fi.hits), p0=dev(fi.p0), c0=dev(fi.c0),
+               align=torch.zeros((L, 6), device=f"cuda:{local}"), xscale=torch.ones(L, device=f"cuda:{local}"))
+    outs = dict(chi2=torch.zeros(n, device=f"cuda:{local}"), dp0=torch.zeros((n, 6), device=f"cuda:{local}"),
+                dal=torch.zeros((L, 6), device=f"cuda:{local}"), dxs=torch.zeros(L, device=f"cuda:{local}"),
+                status=torch.zeros(n, dtype=torch.int32, device=f"cuda:{local}"))
+    call = lambda: ctx.fit_grad(ins["layers"], ins["hits"], ins["p0"], ins["c0"], ins["align"], ins["xscale"],
+                                outs["chi2"], outs["dp0"], outs["dal"], outs["dxs"], outs["status"])
+    call()
+    torch.cuda.synchronize()
+    steps = int((fi.layers >= 0).sum())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    value, wall, _ = pipeline.replica_throughput(e0.elapsed_time(e1) / 1e3, steps, dist, f"cuda:{local}")
+    return {"value": value, "unit": "fit track-layer steps/s with derivatives", "ms": wall * 1e3, "tracks": n,
+            "layers": int(np.unique(fi.layers[fi.layers >= 0]).size), "derivatives_per_track": "6 starting parameters + 7 per crossed layer",
+            "workload": "100k tracks, 22 layers, misaligned detector (50 um, 0.1 mrad), material x[0.8, 1.2]"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -271,6 +304,7 @@ def main():
     ap.add_argument("--events", type=int, default=N_EVENTS, help="events per batch (profiling of small cases)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison path")
+    ap.add_argument("--no-grad", action="store_true", help="skip the fit-derivative measurement")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -345,6 +379,10 @@ def main():
         fp64 = measure_fp64_plain(args, g, params, evs, stream, local, rank, dist)
         fp64["factor"] = value / fp64["value"]
 
+    grad = None
+    if not args.no_grad:
+        grad = measure_fit_grad(args, local, rank, dist, stream)
+
     # ---- end to end through the C ABI with host (pinned) buffers, copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -393,6 +431,7 @@ def main():
                      "launch": "one mkgb_build call per step, timed with CUDA events on its stream"},
         "e2e": e2e,
         "fp64_plain": fp64,
+        "fit_grad": grad,
         "gpu_launches": int(launches_per_step * args.steps),
         "clocks": clocks,
         "counters": {"build": [int(x) for x in bc], "fit": [int(x) for x in fc]},

@@ -152,6 +152,23 @@ int mkgb_fit(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const i
              const float* p0, const float* c0, float* p_out, float* c_out, float* chi2_out,
              int32_t* status_out, int on_device);
 
+/* Derivative of the fit (growth of Sec. 4's final fit): the fit over a known assignment with
+ * per-layer alignment and material applied, and the derivatives of its total chi2.  Alignment:
+ * align[l*6 + (0..5)] = (dx, dy, dz, wx, wy, wz) moves every hit of layer l as
+ * h' = h + d + w x (h - c_l), c_l = (0, 0, 0) for a cylinder and (0, 0, z_l) for a disk (the
+ * layer surfaces stay nominal); xscale[l] multiplies the layer's x/X0.  Arguments as mkgb_fit
+ * (layers, hits, p0, c0: n tracks x max_steps), plus align (n_layers x 6) and xscale (n_layers).
+ * Outputs: chi2_out (n: the track's summed predicted chi2 at these parameters, 0 if it failed),
+ * d_p0 (n x 6: d chi2_i / d p0_i), d_align (n_layers x 6) and d_xscale (n_layers): derivatives
+ * of the total chi2 over the tracks with status 0; status_out (n, optional) as mkgb_fit.  The
+ * derivatives are exact for the FP32 arithmetic of the fit (forward-mode dual numbers; no FP64
+ * refit).  Errors: MKGB_ESTATE without geometry, params or hits; MKGB_EINVAL on NULL arrays or a
+ * hit index beyond the loaded hits (host arrays). */
+int mkgb_fit_grad(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const int32_t* hits,
+                  const float* p0, const float* c0, const float* align, const float* xscale,
+                  float* chi2_out, float* d_p0, float* d_align, float* d_xscale, int32_t* status_out,
+                  int on_device);
+
 /* Kalman fit over a known assignment that allocates nothing.  The paper has no counterpart:
  * this is a library service, not a step of the method.  Same arguments, outputs and
  * arithmetic as mkgb_fit with on_device = 1 (every array a device pointer on the context's

@@ -48,7 +48,7 @@ struct DevGuard {
     }
 };
 
-enum Stage { S_A, S_B, S_C, S_D, S_E, S_F, S_G, S_H, S_I, S_COUNT };
+enum Stage { S_A, S_B, S_C, S_D, S_E, S_F, S_G, S_H, S_I, S_J, S_K, S_COUNT };
 
 }  // namespace
 
@@ -488,6 +488,48 @@ int mkgb_fit(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const i
     CK(copy_back(ctx, p_out, po, 24 * N, on_device));
     CK(copy_back(ctx, c_out, co, 84 * N, on_device));
     CK(copy_back(ctx, chi2_out, xo, 4 * N, on_device));
+    CK(copy_back(ctx, status_out, so, 4 * N, on_device));
+    if (!on_device) CK(cudaStreamSynchronize(st));
+    return MKGB_OK;
+}
+
+int mkgb_fit_grad(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const int32_t* hits, const float* p0,
+                  const float* c0, const float* align, const float* xscale, float* chi2_out, float* d_p0,
+                  float* d_align, float* d_xscale, int32_t* status_out, int on_device) {
+    if (!ctx) return MKGB_EINVAL;
+    if (!ctx->has_geom || !ctx->has_params) return fail(ctx, MKGB_ESTATE, "fit_grad before geometry/params");
+    if (!ctx->has_hits) return fail(ctx, MKGB_ESTATE, "fit_grad before load_hits");
+    if (n < 0 || max_steps < 0) return fail(ctx, MKGB_EINVAL, "negative size");
+    if (!align || !xscale || !d_align || !d_xscale) return fail(ctx, MKGB_EINVAL, "null alignment/material array");
+    if (n > 0 && (!layers || !hits || !p0 || !c0 || !chi2_out || !d_p0)) return fail(ctx, MKGB_EINVAL, "null fit array");
+    if (!on_device)
+        for (size_t q = 0; q < (size_t)n * max_steps; ++q)
+            if (hits[q] >= ctx->n_hits) return fail(ctx, MKGB_EINVAL, "hit index %d out of range", hits[q]);
+    DevGuard guard(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const size_t N = (size_t)n, M = (size_t)max_steps, NL = (size_t)ctx->n_layers;
+    const void *dl, *dh, *dp0, *dc0, *dal, *dxs;
+    CK(stage_in(ctx, S_A, layers, 4 * N * M, on_device, &dl));
+    CK(stage_in(ctx, S_B, hits, 4 * N * M, on_device, &dh));
+    CK(stage_in(ctx, S_C, p0, 24 * N, on_device, &dp0));
+    CK(stage_in(ctx, S_D, c0, 84 * N, on_device, &dc0));
+    CK(stage_in(ctx, S_E, align, 24 * NL, on_device, &dal));
+    CK(stage_in(ctx, S_F, xscale, 4 * NL, on_device, &dxs));
+    void *xo, *gp, *ga, *gx, *so;
+    CK(stage_out(ctx, S_G, chi2_out, 4 * N, on_device, &xo));
+    CK(stage_out(ctx, S_H, d_p0, 24 * N, on_device, &gp));
+    CK(stage_out(ctx, S_I, d_align, 24 * NL, on_device, &ga));
+    CK(stage_out(ctx, S_J, d_xscale, 4 * NL, on_device, &gx));
+    CK(stage_out(ctx, S_K, status_out, 4 * N, on_device, &so));
+    CK(cudaMemsetAsync(ga, 0, 24 * NL, st));   // summed over tracks by the kernel
+    CK(cudaMemsetAsync(gx, 0, 4 * NL, st));
+    CK(launch_fit_grad(st, (const DevGeom*)ctx->geom_d.p, ctx->params, (const float4*)ctx->pay.p, ctx->n_hits, n,
+                       max_steps, (const int*)dl, (const int*)dh, (const float*)dp0, (const float*)dc0,
+                       (const float*)dal, (const float*)dxs, (float*)xo, (float*)gp, (float*)ga, (float*)gx, (int*)so));
+    CK(copy_back(ctx, chi2_out, xo, 4 * N, on_device));
+    CK(copy_back(ctx, d_p0, gp, 24 * N, on_device));
+    CK(copy_back(ctx, d_align, ga, 24 * NL, on_device));
+    CK(copy_back(ctx, d_xscale, gx, 4 * NL, on_device));
     CK(copy_back(ctx, status_out, so, 4 * N, on_device));
     if (!on_device) CK(cudaStreamSynchronize(st));
     return MKGB_OK;

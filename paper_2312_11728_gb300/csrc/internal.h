@@ -86,6 +86,12 @@ cudaError_t launch_build(cudaStream_t st, const DevGeom* g, int max_plan_len, De
                          BuildOutDev out, BuildWork w, unsigned long long* counters, int n_sms);
 
 // ---- k_fit.cu
+// ---- k_grad.cu
+cudaError_t launch_fit_grad(cudaStream_t st, const DevGeom* g, DevParams P, const float4* pay, int64_t n_hits, int n,
+                            int max_steps, const int* layers, const int* hits, const float* p0, const float* c0,
+                            const float* align, const float* xscale, float* chi2_out, float* d_p0, float* d_align,
+                            float* d_xscale, int* status_out);
+
 // Static scratch of mkgb_fit_static: [0, 64) work counters (kNumCounters x u64), [64, 80) the
 // FP64 refit counter, [256, 256 + 4 * kFitStaticMaxTracks) the refit list.  The counters and the
 // refit counter must be zero when a fit starts; the list needs no initial value.

@@ -21,6 +21,7 @@
 
 #include <cuda_runtime.h>
 
+#include "dual.cuh"
 #include "trig.cuh"
 #include <math.h>
 #include <stdint.h>
@@ -33,17 +34,19 @@ constexpr float kCLight = 0.00299792458f;   // curvature [1/cm] per (T / GeV)
 constexpr float kPi = 3.14159265358979f;
 constexpr float kTwoPi = 6.28318530717959f;
 
+// Physical constants in the scalar type of F (dual numbers take the constants of their value type).
 template <class F> struct Phys {
-    static constexpr F mpi = F(0.13957039);       // pion mass, GeV
-    static constexpr F me = F(0.51099895e-3);     // electron mass, GeV
-    static constexpr F K = F(0.307075);           // MeV cm^2/mol
-    static constexpr F ZA = F(0.49848);           // silicon Z/A
-    static constexpr F rho = F(2.329);            // g/cm^3
-    static constexpr F X0 = F(9.37);              // cm
-    static constexpr F I = F(173.0e-9);           // GeV
-    static constexpr F inc_cap = F(10.0);
-    static constexpr F pi = F(3.14159265358979323846);
-    static constexpr F two_pi = F(6.28318530717959647692);
+    using S = typename ScalarOf<F>::type;
+    static constexpr S mpi = S(0.13957039);       // pion mass, GeV
+    static constexpr S me = S(0.51099895e-3);     // electron mass, GeV
+    static constexpr S K = S(0.307075);           // MeV cm^2/mol
+    static constexpr S ZA = S(0.49848);           // silicon Z/A
+    static constexpr S rho = S(2.329);            // g/cm^3
+    static constexpr S X0 = S(9.37);              // cm
+    static constexpr S I = S(173.0e-9);           // GeV
+    static constexpr S inc_cap = S(10.0);
+    static constexpr S pi = S(3.14159265358979323846);
+    static constexpr S two_pi = S(6.28318530717959647692);
 };
 
 struct DevLayer {
@@ -112,6 +115,46 @@ __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
 // hardware logarithm (__logf, at most 3 ulp off outside [0.5, 2]).
 __device__ __forceinline__ float log_mat(float x) { return __logf(x); }
 __device__ __forceinline__ double log_mat(double x) { return log(x); }
+
+// The same helpers on dual numbers (derivative of the fit): values through the scalar helper,
+// derivatives by the chain rule.
+template <class T, int K> __device__ __forceinline__ Dual<T, K> add_rn(const Dual<T, K>& a, const Dual<T, K>& b) {
+    Dual<T, K> r = a + b;
+    r.v = add_rn(a.v, b.v);
+    return r;
+}
+template <class T, int K> __device__ __forceinline__ Dual<T, K> sub_rn(const Dual<T, K>& a, const Dual<T, K>& b) {
+    Dual<T, K> r = a - b;
+    r.v = sub_rn(a.v, b.v);
+    return r;
+}
+template <class T, int K> __device__ __forceinline__ Dual<T, K> mul_rn(const Dual<T, K>& a, const Dual<T, K>& b) {
+    Dual<T, K> r = a * b;
+    r.v = mul_rn(a.v, b.v);
+    return r;
+}
+template <class T, int K>
+__device__ __forceinline__ Dual<T, K> fma_rn(const Dual<T, K>& a, const Dual<T, K>& b, const Dual<T, K>& c) {
+    Dual<T, K> r = fma(a, b, c);
+    r.v = fma_rn(a.v, b.v, c.v);
+    return r;
+}
+template <class T, int K> __device__ __forceinline__ void sin_cos(const Dual<T, K>& x, Dual<T, K>* s, Dual<T, K>* c) {
+    T sv, cv;
+    sin_cos(x.v, &sv, &cv);
+    *s = x.chain(sv, cv);
+    *c = x.chain(cv, -sv);
+}
+template <class T, int K> __device__ __forceinline__ Dual<T, K> rsq(const Dual<T, K>& x) {
+    const T r = rsq(x.v);
+    return x.chain(r, T(-0.5) * r * r * r);
+}
+template <class T, int K> __device__ __forceinline__ Dual<T, K> log_mat(const Dual<T, K>& x) {
+    return x.chain(log_mat(x.v), T(1) / x.v);
+}
+
+// FP32 arithmetic (float, or dual numbers over float): looser iteration tolerances
+template <class F> __host__ __device__ constexpr bool is_fp32() { return sizeof(typename ScalarOf<F>::type) == 4; }
 __device__ __forceinline__ double rsq(double x) { return rsqrt(x); }
 
 template <class F> __device__ __forceinline__ void two_sum(F a, F b, F& s, F& e) {
@@ -166,7 +209,7 @@ template <class F> __device__ __forceinline__ void s1c1(F a, F& S1, F& C1) {
 
 // Derivatives of S1 and C1 with respect to a (power series for small |a|).
 template <class F> __device__ __forceinline__ void s1c1_deriv(F a, F S1, F C1, F& dS1, F& dC1) {
-    const F lim = sizeof(F) == 4 ? F(0.3) : F(0.05);
+    const F lim = is_fp32<F>() ? F(0.3) : F(0.05);
     if (fabs(a) < lim) {
         const F a2 = a * a;
         dS1 = a * (F(-1) / F(3) + a2 * (F(1) / F(30) + a2 * (F(-1) / F(840) + a2 * (F(1) / F(45360) - a2 * (F(1) / F(3991680))))));
@@ -289,7 +332,7 @@ template <class F> __device__ __forceinline__ void pred_to_state(int kind, const
 // particle stops).  Computed in the trajectory precision F.
 template <class F>
 __device__ __forceinline__ int material_terms(const DevLayer& L, F xh, F yh, F k, F st, F ct, F sfp, F cfp,
-                                              F& th02, F& kc, F& a) {
+                                              F& th02, F& kc, F& a, const F* xscale = nullptr) {
     using P = Phys<F>;
     F cosi;
     if (L.kind == MKGB_BARREL) {
@@ -299,7 +342,8 @@ __device__ __forceinline__ int material_terms(const DevLayer& L, F xh, F yh, F k
         cosi = fabs(ct);
     }
     const F fac = (cosi * P::inc_cap > F(1)) ? F(1) / cosi : P::inc_cap;
-    const F tt = F(L.xx0) * fac;
+    F tt = F(L.xx0) * fac;
+    if (xscale) tt = tt * *xscale;   // thickness scale (derivative of the fit)
     if (!(tt > F(0)) || k == F(0)) return 0;
     const F pm = F(1) / (fabs(k) * st);
     const F e2 = pm * pm + P::mpi * P::mpi;
@@ -344,7 +388,7 @@ __device__ __forceinline__ void material_cov(G qc[15], F th02, F kc, F st, F a) 
 template <class F, class G>
 __device__ __forceinline__ int propagate_core(const DevLayer& L, float cBf, int material, const StateT<F>& t,
                                               const G cin[21], PredT<F>& q, G qc[15], int& newton_it,
-                                              F* dir = nullptr) {
+                                              F* dir = nullptr, const F* xscale = nullptr) {
     using P = Phys<F>;
     const F cB = F(cBf);
     F sf, cf, st, ct;
@@ -373,7 +417,7 @@ __device__ __forceinline__ int propagate_core(const DevLayer& L, float cBf, int 
             hi = turn * rho;
         }
         s = (s0 > lo && s0 < hi) ? s0 : F(0.5) * (lo + hi);
-        const F tol = sizeof(F) == 4 ? F(1e-6) : F(1e-13);
+        const F tol = is_fp32<F>() ? F(1e-6) : F(1e-13);
         for (int it = 0; it < 60; ++it) {
             ++newton_it;
             const F a = om * s;
@@ -545,7 +589,7 @@ __device__ __forceinline__ int propagate_core(const DevLayer& L, float cBf, int 
     }
     if (material) {
         F th02, kc, ea;
-        const int mr = material_terms(L, q.xh, q.yh, q.k, st, ct, sfp, cfp, th02, kc, ea);
+        const int mr = material_terms(L, q.xh, q.yh, q.k, st, ct, sfp, cfp, th02, kc, ea, xscale);
         if (mr < 0) return -1;
         if (mr > 0) {
             material_cov(qc, th02, kc, st, ea);
@@ -614,10 +658,15 @@ template <class F> __device__ __forceinline__ bool chol3(const F S[6], F L[6], F
 }
 
 // Residual m - x' (compensated position) and hit covariance in the local frame; S = V + C_surface.
+// dm (optional): a small displacement of the hit (alignment), added to the residual after the
+// compensated subtraction so that it is not rounded to the hit's own ulp.
 template <class F>
 __device__ __forceinline__ void local_meas(const FrameT<F>& f, const PredT<F>& q, F mx, F my, F mz, const F v[6],
-                                           F rl[3], F vl[6], F S[6]) {
-    const F r[3] = {sub_rn(sub_rn(mx, q.xh), q.xl), sub_rn(sub_rn(my, q.yh), q.yl), sub_rn(sub_rn(mz, q.zh), q.zl)};
+                                           F rl[3], F vl[6], F S[6], const F* dm = nullptr) {
+    F r[3] = {sub_rn(sub_rn(mx, q.xh), q.xl), sub_rn(sub_rn(my, q.yh), q.yl), sub_rn(sub_rn(mz, q.zh), q.zl)};
+    if (dm) {
+        r[0] += dm[0]; r[1] += dm[1]; r[2] += dm[2];
+    }
     to_local3(f, r, rl);
     to_local_sym3(f, v, vl);
     S[0] = vl[0]; S[1] = vl[1]; S[3] = vl[3];
@@ -626,9 +675,9 @@ __device__ __forceinline__ void local_meas(const FrameT<F>& f, const PredT<F>& q
 
 template <class F>
 __device__ __forceinline__ bool chi2_hit(const FrameT<F>& f, const PredT<F>& q, F mx, F my, F mz, const F v[6],
-                                         F& chi2) {
+                                         F& chi2, const F* dm = nullptr) {
     F rl[3], vl[6], S[6], L[6], inv[3];
-    local_meas(f, q, mx, my, mz, v, rl, vl, S);
+    local_meas(f, q, mx, my, mz, v, rl, vl, S, dm);
     if (!chol3(S, L, inv)) return false;
     const F y0 = rl[0] * inv[0];
     const F y1 = (rl[1] - L[1] * y0) * inv[1];
@@ -638,8 +687,9 @@ __device__ __forceinline__ bool chi2_hit(const FrameT<F>& f, const PredT<F>& q, 
 }
 
 template <class F>
-__device__ __forceinline__ bool chi2_hit(int kind, const PredT<F>& q, F mx, F my, F mz, const F v[6], F& chi2) {
-    return chi2_hit(frame_of(kind, q), q, mx, my, mz, v, chi2);
+__device__ __forceinline__ bool chi2_hit(int kind, const PredT<F>& q, F mx, F my, F mz, const F v[6], F& chi2,
+                                         const F* dm = nullptr) {
+    return chi2_hit(frame_of(kind, q), q, mx, my, mz, v, chi2, dm);
 }
 
 // Kalman update of a predicted state with one hit, Joseph form in the surface frame:
@@ -650,10 +700,10 @@ __device__ __forceinline__ bool chi2_hit(int kind, const PredT<F>& q, F mx, F my
 // condition number.
 template <class F>
 __device__ __forceinline__ bool kalman_update(int kind, const PredT<F>& q, F mx, F my, F mz, const F v[6],
-                                              StateT<F>& out, float* kappa = nullptr) {
+                                              StateT<F>& out, float* kappa = nullptr, const F* dm = nullptr) {
     const FrameT<F> f = frame_of(kind, q);
     F rl[3], vl[6], S[6], L[6], inv[3];
-    local_meas(f, q, mx, my, mz, v, rl, vl, S);
+    local_meas(f, q, mx, my, mz, v, rl, vl, S, dm);
     if (!chol3(S, L, inv)) return false;
     if (kappa) {
         const F lmax = fmax(fmax(L[0], L[2]), L[5]), lmin = fmin(fmin(L[0], L[2]), L[5]);

@@ -43,7 +43,7 @@ class Tracks(C.Structure):
 
 EXPORTS = ["mkgb_create", "mkgb_destroy", "mkgb_last_error", "mkgb_version", "mkgb_load_geometry",
            "mkgb_set_params", "mkgb_load_hits", "mkgb_seed", "mkgb_build", "mkgb_fit", "mkgb_fit_static",
-           "mkgb_propagate", "mkgb_update", "mkgb_counters"]
+           "mkgb_fit_grad", "mkgb_propagate", "mkgb_update", "mkgb_counters"]
 
 _lib = None
 
@@ -75,6 +75,7 @@ def load_library(path: str = LIB_PATH):
     lib.mkgb_build.argtypes = [vp, C.POINTER(Tracks), i32]
     lib.mkgb_fit.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32]
     lib.mkgb_fit_static.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.mkgb_fit_grad.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32]
     lib.mkgb_propagate.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, i32]
     lib.mkgb_update.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32]
     lib.mkgb_counters.argtypes = [vp, i32, vp]
@@ -226,6 +227,17 @@ class Context:
         if _same(*[d for _, d in args]) != 1:
             raise MkgbError("mkgb_fit_static takes CUDA tensors only")
         self._check(self.lib.mkgb_fit_static(self.h, int(n), int(m), *[p for p, _ in args]), "mkgb_fit_static")
+
+    def fit_grad(self, layers, hits, p0, c0, align, xscale, chi2_out, d_p0, d_align, d_xscale, status_out=None):
+        """mkgb_fit_grad: per-track chi2 at the given alignment / thickness scales and the
+        derivatives of the total chi2 (outputs written in place)."""
+        n, m = layers.shape
+        args = [_ptr(layers, np.int32), _ptr(hits, np.int32), _ptr(p0, np.float32), _ptr(c0, np.float32),
+                _ptr(align, np.float32), _ptr(xscale, np.float32), _ptr(chi2_out, np.float32, True),
+                _ptr(d_p0, np.float32, True), _ptr(d_align, np.float32, True), _ptr(d_xscale, np.float32, True),
+                _ptr(status_out, np.int32, True)]
+        self._check(self.lib.mkgb_fit_grad(self.h, int(n), int(m), *[p for p, _ in args],
+                                           _same(*[d for _, d in args])), "mkgb_fit_grad")
 
     def propagate(self, layers, p_in, c_in, p_out, c_out, crossed):
         args = [_ptr(layers, np.int32), _ptr(p_in, np.float32), _ptr(c_in, np.float32), _ptr(p_out, np.float32, True),

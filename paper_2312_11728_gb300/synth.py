@@ -330,6 +330,13 @@ def sample_pt_phase2(rng, n, frac_low=0.7):
     return np.where(low, sample_pt_loguniform(rng, n, 0.5, 2.0), sample_pt_loguniform(rng, n, 2.0, 50.0))
 
 
+def sample_pt_loopers(rng, n, frac_loop=0.1):
+    """A fraction frac_loop uniform in [0.5, 0.7] GeV (tracks that curl inside the tracker at
+    3.8 T), the rest as sample_pt_phase2."""
+    loop = rng.random(n) < frac_loop
+    return np.where(loop, rng.uniform(0.5, 0.7, n), sample_pt_phase2(rng, n))
+
+
 def simulate_event(geom: Geometry, n_tracks: int, seed: int = 0, event: int = 0, *,
                    pt_sampler=None, eta_max=1.0, eta_min=None, noise_per_layer=None,
                    noise_total=None, material=True, smear=True, min_hits_seed=3) -> Event:
@@ -540,3 +547,63 @@ def workload_phase2(n_events=64, n_tracks=20000, seed=0, noise_total=50000):
     evs = [simulate_event(g, n_tracks, seed, e, pt_sampler=sample_pt_phase2, eta_max=3.0,
                           noise_total=noise_total) for e in range(n_events)]
     return g, evs
+
+
+def workload_uneven(n_events=256, mean=8000, lo=200, hi=25000, seed=0, noise_per_track=2.5, counts=None):
+    """Events with Poisson track counts (clipped to [lo, hi]; or the given counts) on the
+    Phase-2-like geometry, noise in proportion to the tracks (50,000 per 20,000 tracks)."""
+    g = geometry_phase2()
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 104729])))
+    if counts is None:
+        counts = np.clip(rng.poisson(mean, n_events), lo, hi)
+    evs = [simulate_event(g, int(n), seed, e, pt_sampler=sample_pt_phase2, eta_max=3.0,
+                          noise_total=int(noise_per_track * n)) for e, n in enumerate(counts)]
+    return g, evs
+
+
+def workload_loopers(n_events=50, n_tracks=20000, seed=0):
+    """Phase-2-like events with 10% of the tracks at 0.5-0.7 GeV (curling, ill-conditioned S)."""
+    g = geometry_phase2()
+    evs = [simulate_event(g, n_tracks, seed, e, pt_sampler=sample_pt_loopers, eta_max=3.0, noise_total=0)
+           for e in range(n_events)]
+    return g, evs
+
+
+def move_hits(geom: Geometry, ev: Event, align) -> Event:
+    """The event with the hits of every layer l moved by align[l] = (d, w): h' = h + d + w x (h - c_l),
+    c_l the origin for a cylinder and (0, 0, z_l) for a disk; covariances unchanged."""
+    import dataclasses
+    X = ev.hit_xyz.astype(np.float64)
+    for l in range(geom.n_layers):
+        a, b = int(ev.layer_off[l]), int(ev.layer_off[l + 1])
+        if a == b:
+            continue
+        c = np.array([0.0, 0.0, float(geom.pos[l]) if geom.kind[l] == DISK else 0.0])
+        X[a:b] = X[a:b] + align[l, :3] + np.cross(align[l, 3:], X[a:b] - c)
+    return dataclasses.replace(ev, hit_xyz=X.astype(np.float32))
+
+
+def workload_aligned_fit(n_tracks=100_000, seed=0, sig_shift=50e-4, sig_rot=1e-4, mat_frac=0.2,
+                         tracks_per_event=20_000):
+    """Known-assignment fit workload with a misaligned detector: tracks with eta in [0, 3) cross
+    the 10 cylinders and the 12 disks at +z (22 layers); each layer carries a random alignment
+    (shifts of sigma 50 um, rotations of sigma 0.1 mrad) and a material thickness off by a
+    uniform factor in [0.8, 1.2].  Hits are simulated through the true material and moved by
+    the true alignment; the fit uses the nominal geometry.  Returns (nominal geometry, events,
+    true alignment [L, 6], true thickness scales [L])."""
+    import dataclasses
+    g = geometry_phase2()
+    L = g.n_layers
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 15485863])))
+    align = np.zeros((L, 6))
+    align[:, :3] = rng.normal(0.0, sig_shift, (L, 3))
+    align[:, 3:] = rng.normal(0.0, sig_rot, (L, 3))
+    xscale = rng.uniform(1.0 - mat_frac, 1.0 + mat_frac, L)
+    g_true = dataclasses.replace(g, x_over_x0=_f32(g.x_over_x0 * xscale))
+    evs = []
+    for e in range(int(np.ceil(n_tracks / tracks_per_event))):
+        nt = min(tracks_per_event, n_tracks - e * tracks_per_event)
+        ev = simulate_event(g_true, nt, seed, e, pt_sampler=sample_pt_phase2, eta_min=0.0, eta_max=3.0,
+                            noise_total=0)
+        evs.append(move_hits(g, ev, align))
+    return g, evs, align, xscale

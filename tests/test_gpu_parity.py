@@ -305,3 +305,67 @@ def test_full_size_phase2_sampled_against_oracle(lib, phase2_full):
     gf = {k: db.fit[k].cpu().numpy()[tsample] for k in ("p", "c", "chi2", "status")}
     rep = _report("fit_full_size", PR.compare_fit(gf, r))
     assert rep["status_bad"] == 0 and rep["param_bad"] == 0 and rep["chi2_bad"] == 0, rep
+
+
+# ------------------------------------------------------------------ uneven events, loopers at scale
+
+def test_uneven_events_match_oracle(lib):
+    """Events of very different sizes in one call (Poisson track counts as in the uneven-batch
+    workload, plus a 20-track, a 1,500-track and a track-less event with noise only): every
+    seed and every fit track against the oracle."""
+    rng = np.random.default_rng(3)
+    counts = list(np.clip(rng.poisson(400, 5), 200, 25000)) + [20, 1500, 0]
+    g, evs = S.workload_uneven(counts=counts, seed=3, noise_per_track=2.5)
+    batch = S.concat_events(evs, g.n_layers)
+    params = S.default_params()
+    ctx = _ctx(g, params)
+    fi = pipeline.fit_inputs(batch)
+    res = pipeline.run_host(ctx, batch, g.max_plan, fi)
+    orc = oracle.Oracle(g, params)
+    o = PR.oracle_build(orc, batch)
+    rep = _report("build_uneven", PR.compare_build(res["build"], o))
+    assert len(rep["hit_mismatch"]) == 0 and rep["failed_mismatch"] == 0, rep
+    assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0 and rep["count_bad"] == 0, rep
+    r = orc.fit_batch(fi.layers, fi.hits, batch.hit_xyz.astype(np.float64), batch.hit_cov.astype(np.float64),
+                      fi.p0.astype(np.float64), fi.c0.astype(np.float64))
+    rf = PR.compare_fit(res["fit"], r)
+    assert rf["status_bad"] == 0 and rf["param_bad"] == 0 and rf["cov_bad"] == 0 and rf["chi2_bad"] == 0, rf
+
+
+@pytest.fixture(scope="module")
+def loopers_1m():
+    g, evs = S.workload_loopers(n_events=50, n_tracks=20000, seed=5)
+    return g, S.concat_events(evs, g.n_layers)
+
+
+def test_loopers_precision_sweep_1m_tracks(lib, loopers_1m):
+    """1,000,000 tracks over 34 layers, 10% at 0.5-0.7 GeV: the FP32 fit (FP64 refit of the
+    tracks with an ill-conditioned S) and the all-FP64 fit against the oracle on a sample;
+    errors in units of the tolerances and pulls against the generator's truth are reported."""
+    import torch
+    g, batch = loopers_1m
+    fi = pipeline.fit_inputs(batch)
+    assert fi.layers.shape[0] > 900_000
+    rng = np.random.default_rng(11)
+    sample = np.sort(rng.choice(fi.layers.shape[0], 3000, replace=False))
+    orc = oracle.Oracle(g, S.default_params())
+    X, V = batch.hit_xyz.astype(np.float64), batch.hit_cov.astype(np.float64)
+    r = orc.fit_batch(fi.layers[sample], fi.hits[sample], X, V, fi.p0[sample].astype(np.float64),
+                      fi.c0[sample].astype(np.float64))
+    out = {}
+    for name, prec in (("fp32", 0), ("fp64", 2)):
+        ctx = _ctx(g, dict(S.default_params(), precision=prec))
+        ctx.load_hits(batch.n_events, batch.hit_off, torch.from_numpy(batch.hit_xyz).cuda(),
+                      torch.from_numpy(batch.hit_cov).cuda())
+        d = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda()
+             for k, v in dict(layers=fi.layers, hits=fi.hits, p0=fi.p0, c0=fi.c0).items()}
+        n = fi.layers.shape[0]
+        o = dict(p=torch.zeros((n, 6), device="cuda"), c=torch.zeros((n, 21), device="cuda"),
+                 chi2=torch.zeros(n, device="cuda"), status=torch.zeros(n, dtype=torch.int32, device="cuda"))
+        ctx.fit(d["layers"], d["hits"], d["p0"], d["c0"], o["p"], o["c"], o["chi2"], o["status"])
+        torch.cuda.synchronize()
+        h = {k: v.cpu().numpy()[sample] for k, v in o.items()}
+        rep = _report(f"fit_loopers_1m_{name}", PR.compare_fit(h, r))
+        assert rep["status_bad"] == 0 and rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0, rep
+        out[name] = rep
+    assert out["fp64"]["worst_param"] <= out["fp32"]["worst_param"] + 1e-6
