@@ -152,6 +152,18 @@ int mkgb_fit(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const i
              const float* p0, const float* c0, float* p_out, float* c_out, float* chi2_out,
              int32_t* status_out, int on_device);
 
+/* One pass of the hot path in one call (Sec. 2.2 search and Sec. 4 fit on one batch of events):
+ * mkgb_load_hits, mkgb_seed (no optional outputs), mkgb_build and mkgb_fit with the same
+ * arguments as those calls, every array a device pointer (their on_device = 1 rules).  Inside,
+ * the fit runs on a second stream beside the seed fit and the search (it needs the prepared hits
+ * only); the context's stream waits for it, so all outputs are complete when the context's
+ * stream passes the call.  Errors: those of the four calls (the first failing one is returned;
+ * the work already enqueued stays enqueued). */
+int mkgb_run(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz, const float* cov6,
+             int n_seeds, const int32_t* seed_hits, const mkgb_tracks* out, int n_fit, int max_steps,
+             const int32_t* layers, const int32_t* hits, const float* p0, const float* c0, float* p_out,
+             float* c_out, float* chi2_out, int32_t* status_out);
+
 /* Derivative of the fit (growth of Sec. 4's final fit): the fit over a known assignment with
  * per-layer alignment and material applied, and the derivatives of its total chi2.  Alignment:
  * align[l*6 + (0..5)] = (dx, dy, dz, wx, wy, wz) moves every hit of layer l as

@@ -56,6 +56,13 @@ struct mkgb_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // side stream for the hit binning (needed by the search only), forked after the hit
+    // preparation and joined by the next user of the binned hits
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_prep = nullptr, ev_bins = nullptr;
+    // side stream and events of mkgb_run's fit
+    cudaStream_t fit_st = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_fit = nullptr;
     int n_sms = 0;
     std::string err;
     bool has_geom = false, has_params = false, has_hits = false, has_seeds = false, seeds_fp64 = false;
@@ -187,6 +194,18 @@ void mkgb_destroy(mkgb_ctx* ctx) {
     {
         DevGuard guard(ctx->device);
         cudaStreamSynchronize(ctx->stream);
+        if (ctx->aux) {
+            cudaStreamSynchronize(ctx->aux);
+            cudaStreamDestroy(ctx->aux);
+        }
+        if (ctx->ev_prep) cudaEventDestroy(ctx->ev_prep);
+        if (ctx->ev_bins) cudaEventDestroy(ctx->ev_bins);
+        if (ctx->fit_st) {
+            cudaStreamSynchronize(ctx->fit_st);
+            cudaStreamDestroy(ctx->fit_st);
+        }
+        if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+        if (ctx->ev_fit) cudaEventDestroy(ctx->ev_fit);
         DevBuf* all[] = {&ctx->geom_d, &ctx->seg_off, &ctx->in_xyz, &ctx->in_cov, &ctx->pay, &ctx->ep_tmp,
                          &ctx->bin_of_hit, &ctx->hit_seg, &ctx->bins, &ctx->hb_ep, &ctx->hb_pay, &ctx->cursor,
                          &ctx->scan_tmp, &ctx->seed_hits, &ctx->seed_state, &ctx->seed_state64, &ctx->seed_info, &ctx->seed_key,
@@ -314,6 +333,14 @@ int mkgb_load_hits(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const fl
     if (nbins > ((int64_t)1 << 31) - 2) return fail(ctx, MKGB_EINVAL, "too many bins (%lld)", (long long)nbins);
     DevGuard guard(ctx->device);
     cudaStream_t st = ctx->stream;
+    if (!ctx->aux) {
+        CK(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ctx->ev_prep, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_bins, cudaEventDisableTiming));
+        CK(cudaEventRecord(ctx->ev_bins, ctx->aux));
+    }
+    // the previous call's binning must be done before its inputs and outputs are rewritten
+    CK(cudaStreamWaitEvent(st, ctx->ev_bins, 0));
     // The offsets are copied only when they change (a repeated batch costs no host round trip).
     // A copy from pageable memory returns once the source has been staged, so the host vector
     // may be rewritten after the call.
@@ -347,11 +374,16 @@ int mkgb_load_hits(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const fl
     CK(launch_hit_prep(st, (const DevGeom*)ctx->geom_d.p, L, (const int64_t*)ctx->seg_off.p, (int)nseg, n, dx, dc,
                        ctx->geom_h.bins_per_event, (float4*)ctx->pay.p, (float2*)ctx->ep_tmp.p,
                        (int*)ctx->bin_of_hit.p, (int*)ctx->hit_seg.p, (int*)ctx->bins.p));
-    CK(exclusive_scan(st, (const int*)ctx->bins.p, (int*)ctx->bins.p, nbins, (int*)ctx->scan_tmp.p));
-    CK(cudaMemcpyAsync(ctx->cursor.p, ctx->bins.p, 4 * nbins, cudaMemcpyDeviceToDevice, st));
-    CK(launch_hit_scatter(st, n, (const float4*)ctx->pay.p, (const float2*)ctx->ep_tmp.p,
+    // The binned copy is used by the search only: it is built on the side stream, overlapping
+    // the seed fit and the fit on the context's stream, and mkgb_build waits for it.
+    CK(cudaEventRecord(ctx->ev_prep, st));
+    CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_prep, 0));
+    CK(exclusive_scan(ctx->aux, (const int*)ctx->bins.p, (int*)ctx->bins.p, nbins, (int*)ctx->scan_tmp.p));
+    CK(cudaMemcpyAsync(ctx->cursor.p, ctx->bins.p, 4 * nbins, cudaMemcpyDeviceToDevice, ctx->aux));
+    CK(launch_hit_scatter(ctx->aux, n, (const float4*)ctx->pay.p, (const float2*)ctx->ep_tmp.p,
                           (const int*)ctx->bin_of_hit.p, (int*)ctx->cursor.p, (float2*)ctx->hb_ep.p,
                           (float4*)ctx->hb_pay.p));
+    CK(cudaEventRecord(ctx->ev_bins, ctx->aux));
     if (!on_device) CK(cudaStreamSynchronize(st));
     ctx->n_events = n_events;
     ctx->n_hits = n;
@@ -430,6 +462,7 @@ int mkgb_build(mkgb_ctx* ctx, const mkgb_tracks* out, int on_device) {
     SeedStore S{ctx->n_seeds, (const float*)ctx->seed_state.p, (const double*)ctx->seed_state64.p,
                 (const int4*)ctx->seed_info.p,
                 (const int*)ctx->seed_order.p};
+    CK(cudaStreamWaitEvent(st, ctx->ev_bins, 0));   // the binned hits (mkgb_load_hits)
     const int prec = ctx->params.precision;
     if (prec == MKGB_FP64 && !ctx->seeds_fp64)
         return fail(ctx, MKGB_ESTATE, "FP64 search needs seeds made under the FP64 precision");
@@ -584,6 +617,34 @@ int mkgb_fit_static(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, 
                   reinterpret_cast<int*>(b + kFitStaticListOff), reinterpret_cast<int*>(b + kFitStaticRescueCountOff),
                   ctx->n_sms));
     return MKGB_OK;
+}
+
+int mkgb_run(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz, const float* cov6, int n_seeds,
+             const int32_t* seed_hits, const mkgb_tracks* out, int n_fit, int max_steps, const int32_t* layers,
+             const int32_t* hits, const float* p0, const float* c0, float* p_out, float* c_out, float* chi2_out,
+             int32_t* status_out) {
+    if (!ctx) return MKGB_EINVAL;
+    DevGuard guard(ctx->device);
+    const cudaStream_t main_st = ctx->stream;
+    if (!ctx->fit_st) {
+        CK(cudaStreamCreateWithFlags(&ctx->fit_st, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_fit, cudaEventDisableTiming));
+    }
+    int rc = mkgb_load_hits(ctx, n_events, seg_off, xyz, cov6, 1);
+    if (rc != MKGB_OK) return rc;
+    // the fit needs the prepared hits only: it runs on its own stream beside the seed fit and
+    // the search, and the context's stream waits for it before the call ends
+    CK(cudaEventRecord(ctx->ev_fork, main_st));
+    CK(cudaStreamWaitEvent(ctx->fit_st, ctx->ev_fork, 0));
+    ctx->stream = ctx->fit_st;
+    rc = mkgb_fit(ctx, n_fit, max_steps, layers, hits, p0, c0, p_out, c_out, chi2_out, status_out, 1);
+    ctx->stream = main_st;
+    CK(cudaEventRecord(ctx->ev_fit, ctx->fit_st));
+    if (rc == MKGB_OK) rc = mkgb_seed(ctx, n_seeds, seed_hits, 1, nullptr, nullptr, nullptr);
+    if (rc == MKGB_OK) rc = mkgb_build(ctx, out, 1);
+    CK(cudaStreamWaitEvent(main_st, ctx->ev_fit, 0));
+    return rc;
 }
 
 int mkgb_propagate(mkgb_ctx* ctx, int n, const int32_t* layers, const float* p_in, const float* c_in, float* p_out,

@@ -43,7 +43,7 @@ class Tracks(C.Structure):
 
 EXPORTS = ["mkgb_create", "mkgb_destroy", "mkgb_last_error", "mkgb_version", "mkgb_load_geometry",
            "mkgb_set_params", "mkgb_load_hits", "mkgb_seed", "mkgb_build", "mkgb_fit", "mkgb_fit_static",
-           "mkgb_fit_grad", "mkgb_propagate", "mkgb_update", "mkgb_counters"]
+           "mkgb_fit_grad", "mkgb_run", "mkgb_propagate", "mkgb_update", "mkgb_counters"]
 
 _lib = None
 
@@ -76,6 +76,8 @@ def load_library(path: str = LIB_PATH):
     lib.mkgb_fit.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32]
     lib.mkgb_fit_static.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.mkgb_fit_grad.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32]
+    lib.mkgb_run.argtypes = [vp, i32, vp, vp, vp, i32, vp, C.POINTER(Tracks), i32, i32, vp, vp, vp, vp, vp, vp, vp,
+                             vp]
     lib.mkgb_propagate.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, i32]
     lib.mkgb_update.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32]
     lib.mkgb_counters.argtypes = [vp, i32, vp]
@@ -216,6 +218,27 @@ class Context:
                 _ptr(status_out, np.int32, True)]
         self._check(self.lib.mkgb_fit(self.h, int(n), int(m), *[p for p, _ in args], _same(*[d for _, d in args])),
                     "mkgb_fit")
+
+    def run(self, n_events, seg_off, xyz, cov, seed_hits, out: dict, layers, hits, p0, c0, p_out, c_out, chi2_out,
+            status_out=None):
+        """mkgb_run: load_hits + seed + build + fit in one call, device tensors only; the fit runs
+        beside the seed fit and the search inside the call."""
+        so = np.ascontiguousarray(seg_off, np.int64)
+        f, i = np.float32, np.int32
+        ptrs = [_ptr(out[k], t, out=True) for k, t in (("params", f), ("cov", f), ("chi2", f), ("score", f),
+                                              ("nfound", i), ("nholes", i), ("hits", i))]
+        t = Tracks(*[p for p, _ in ptrs], int(out["hits"].shape[1]))
+        args = [_ptr(xyz, f), _ptr(cov, f), _ptr(seed_hits, i), _ptr(layers, i), _ptr(hits, i), _ptr(p0, f),
+                _ptr(c0, f), _ptr(p_out, f, True), _ptr(c_out, f, True), _ptr(chi2_out, f, True),
+                _ptr(status_out, i, True)]
+        if _same(*[d for _, d in args + ptrs]) != 1:
+            raise MkgbError("mkgb_run takes CUDA tensors only")
+        (px, _), (pc, _), (ps, _), (pl, _), (ph, _), (pp, _), (pq, _), (po, _), (pco, _), (px2, _), (pst, _) = args
+        n, m = layers.shape
+        self._check(self.lib.mkgb_run(self.h, int(n_events), so.ctypes.data, px, pc, int(seed_hits.shape[0]), ps,
+                                      C.byref(t), int(n), int(m), pl, ph, pp, pq, po, pco, px2, pst), "mkgb_run")
+        self.n_seeds = int(seed_hits.shape[0])
+        return out
 
     def fit_static(self, layers, hits, p0, c0, p_out, c_out, chi2_out, status_out=None):
         """mkgb_fit_static: the fit without device allocations (device tensors only, at most

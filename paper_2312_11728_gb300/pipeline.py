@@ -81,6 +81,14 @@ def run_step(ctx: mkgb.Context, db: DeviceBatch):
         ctx.fit(f["layers"], f["hits"], f["p0"], f["c0"], f["p"], f["c"], f["chi2"], f["status"])
 
 
+def run_step_fused(ctx: mkgb.Context, db: DeviceBatch):
+    """The same pass as run_step through mkgb_run (one call; the fit overlaps the seed fit and
+    the search inside it)."""
+    f = db.fit
+    ctx.run(db.n_events, db.seg_off, db.xyz, db.cov, db.seeds, db.out, f["layers"], f["hits"], f["p0"], f["c0"],
+            f["p"], f["c"], f["chi2"], f["status"])
+
+
 def run_host(ctx: mkgb.Context, batch: Batch, max_plan: int, fit: FitInputs | None = None):
     """Same pass with host arrays (the library copies in and out); returns numpy results."""
     ctx.load_hits(batch.n_events, batch.hit_off, np.ascontiguousarray(batch.hit_xyz, np.float32),

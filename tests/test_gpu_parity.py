@@ -224,6 +224,27 @@ def test_device_and_host_paths_agree_and_are_deterministic(lib, phase2_small):
     assert np.array_equal(db.fit["p"].cpu().numpy(), host["fit"]["p"])
 
 
+def test_one_call_run_matches_separate_calls(lib, phase2_small):
+    """mkgb_run (the fit on a second stream inside the call) gives the separate calls' results
+    bit for bit, twice in a row."""
+    import torch
+    g, batch, params = phase2_small
+    fi = pipeline.fit_inputs(batch)
+    ref_ctx = _ctx(g, params)
+    ref = pipeline.DeviceBatch(batch, fi, g.max_plan, "cuda")
+    pipeline.run_step(ref_ctx, ref)
+    torch.cuda.synchronize()
+    ctx = _ctx(g, params)
+    db = pipeline.DeviceBatch(batch, fi, g.max_plan, "cuda")
+    for _ in range(2):
+        pipeline.run_step_fused(ctx, db)
+        torch.cuda.synchronize()
+        for k in ref.out:
+            assert torch.equal(ref.out[k], db.out[k]), k
+        for k in ("p", "c", "chi2", "status"):
+            assert torch.equal(ref.fit[k], db.fit[k]), k
+
+
 # ------------------------------------------------------------------ edge cases
 
 def test_edge_cases_empty_single_and_ragged(lib):
