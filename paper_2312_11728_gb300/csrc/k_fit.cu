@@ -40,7 +40,7 @@ __device__ __forceinline__ int fit_track(const DevGeom& g, const DevParams& P, c
         if (l < 0 || l >= g.n_layers) break;
         const DevLayer& L = g.layers[l];
         PredT<F> q;
-        const int r = propagate(L, g.cB, P.material, t, q, c_newton);
+        const int r = propagate_refined(L, g.cB, P.material, t, q, c_newton, sizeof(F) == 8 && P.precision != MKGB_FP64);
         if (r != 1) return r == 0 ? 1 : 2;
         ++c_steps;
         const int h = __ldg(hrow + j);

@@ -383,12 +383,17 @@ __device__ __forceinline__ void material_cov(G qc[15], F th02, F kc, F st, F a) 
 // 0 (not crossed) or -1 (particle stopped in the material).  newton_it counts iterations.
 // dir (optional) gets sin(phi'), cos(phi'), sin(theta), cos(theta) at the crossing.
 // The trajectory, its Jacobian and the material terms are computed in F; the covariance cin (21,
-// global frame) is transported into qc (15, surface frame) in G (G = F for the plain step; the
-// seed fit takes F = float, G = double).  q.c is not touched.
+// global frame) is transported into qc (15, surface frame) in G.  q.c is not touched.
+// Options: xscale scales the layer's thickness; s_guess starts the barrel Newton iteration at a
+// path length solved in a lower precision (the FP64 steps then need one or two iterations);
+// s_out returns the path length; mat_fp32 computes the material terms (Highland angle, energy-
+// loss factor: small corrections, ~1e-7 relative in FP32) in FP32 for an FP64 step.
 template <class F, class G>
 __device__ __forceinline__ int propagate_core(const DevLayer& L, float cBf, int material, const StateT<F>& t,
                                               const G cin[21], PredT<F>& q, G qc[15], int& newton_it,
-                                              F* dir = nullptr, const F* xscale = nullptr) {
+                                              F* dir = nullptr, const F* xscale = nullptr,
+                                              const F* s_guess = nullptr, F* s_out = nullptr,
+                                              bool mat_fp32 = false) {
     using P = Phys<F>;
     const F cB = F(cBf);
     F sf, cf, st, ct;
@@ -417,6 +422,7 @@ __device__ __forceinline__ int propagate_core(const DevLayer& L, float cBf, int 
             hi = turn * rho;
         }
         s = (s0 > lo && s0 < hi) ? s0 : F(0.5) * (lo + hi);
+        if (s_guess && *s_guess > lo && *s_guess < hi) s = *s_guess;
         const F tol = is_fp32<F>() ? F(1e-6) : F(1e-13);
         for (int it = 0; it < 60; ++it) {
             ++newton_it;
@@ -589,13 +595,22 @@ __device__ __forceinline__ int propagate_core(const DevLayer& L, float cBf, int 
     }
     if (material) {
         F th02, kc, ea;
-        const int mr = material_terms(L, q.xh, q.yh, q.k, st, ct, sfp, cfp, th02, kc, ea, xscale);
+        int mr;
+        if (mat_fp32) {
+            float th02f = 0.0f, kcf = 0.0f, eaf = 1.0f;
+            mr = material_terms(L, float(q.xh), float(q.yh), float(q.k), float(st), float(ct), float(sfp),
+                                float(cfp), th02f, kcf, eaf);
+            th02 = F(th02f); kc = F(kcf); ea = F(eaf);
+        } else {
+            mr = material_terms(L, q.xh, q.yh, q.k, st, ct, sfp, cfp, th02, kc, ea, xscale);
+        }
         if (mr < 0) return -1;
         if (mr > 0) {
             material_cov(qc, th02, kc, st, ea);
             q.k = q.k * ea;
         }
     }
+    if (s_out) *s_out = s;
     return 1;
 }
 
@@ -604,6 +619,14 @@ __device__ __forceinline__ int propagate(const DevLayer& L, float cBf, int mater
                                          int& newton_it, F* dir = nullptr) {
     return propagate_core<F, F>(L, cBf, material, t, t.c, q, q.c, newton_it, dir);
 }
+
+// The propagation of the FP64 steps that serve the FP32 path (seed fits, refits of ill-conditioned
+// fits) when fast: the crossing is solved in FP32 first and refined by FP64 Newton iterations
+// from there (one or two instead of ~5), and the material terms are FP32.  The plain all-FP64
+// path takes fast = false.
+template <class F>
+__device__ __forceinline__ int propagate_refined(const DevLayer& L, float cBf, int material, const StateT<F>& t,
+                                                 PredT<F>& q, int& newton_it, bool fast);
 
 // ----------------------------------------------------------------- window (a8)
 
@@ -859,4 +882,39 @@ __device__ __forceinline__ void load_hit(const float4* __restrict__ pay, long lo
     v[0] = F(b.x); v[1] = F(b.y); v[2] = F(b.z); v[3] = F(b.w); v[4] = F(c.x); v[5] = F(c.y);
 }
 
+}  // namespace mk
+
+namespace mk {
+// The FP32 image of a state of any precision (a float state is copied).
+__device__ __forceinline__ void narrow_to_fp32(const StateT<double>& d, State& t) { narrow_state(d, t); }
+__device__ __forceinline__ void narrow_to_fp32(const State& d, State& t) { t = d; }
+template <class T, int K> __device__ __forceinline__ void narrow_to_fp32(const StateT<Dual<T, K>>& d, State& t) {
+    t.xh = float(d.xh); t.yh = float(d.yh); t.zh = float(d.zh);
+    t.xl = float(d.xl); t.yl = float(d.yl); t.zl = float(d.zl);
+    t.k = float(d.k); t.phi = float(d.phi); t.th = float(d.th);
+#pragma unroll
+    for (int i = 0; i < 21; ++i) t.c[i] = float(d.c[i]);
+}
+}  // namespace mk
+
+namespace mk {
+template <class F>
+__device__ __forceinline__ int propagate_refined(const DevLayer& L, float cBf, int material, const StateT<F>& t,
+                                                 PredT<F>& q, int& newton_it, bool fast) {
+    F sg = F(0);
+    bool have = false;
+    if (fast) {
+        State t32;
+        narrow_to_fp32(t, t32);
+        Pred q32;
+        float s32 = 0.0f;
+        int nw = 0;
+        if (propagate_core<float, float>(L, cBf, 0, t32, t32.c, q32, q32.c, nw, nullptr, nullptr, nullptr, &s32) == 1) {
+            sg = F(s32);
+            have = true;
+        }
+    }
+    return propagate_core<F, F>(L, cBf, material, t, t.c, q, q.c, newton_it, nullptr, nullptr, have ? &sg : nullptr,
+                                nullptr, fast);
+}
 }  // namespace mk

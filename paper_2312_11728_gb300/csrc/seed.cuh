@@ -71,11 +71,14 @@ __device__ __forceinline__ bool seed_fit(const DevGeom& g, const DevParams& P, c
     bool ok = seed_prior(g, H, seed_hits, i, m, v, lay, event, t);
     int newton = 0;
     ok = ok && state_update(t, m[0][0], m[0][1], m[0][2], v[0]);
+    // the FP64 fit of the FP32 path refines FP32 crossings (propagate_refined); the plain
+    // all-FP64 path solves them in FP64 from the start
+    const bool fast = sizeof(F) == 8 && P.precision != MKGB_FP64;
 #pragma unroll
     for (int j = 1; j < 3; ++j) {
         PredT<F> q;
         const DevLayer& L = g.layers[lay[j]];
-        ok = ok && propagate(L, g.cB, P.material, t, q, newton) == 1;
+        ok = ok && propagate_refined(L, g.cB, P.material, t, q, newton, fast) == 1;
         ok = ok && kalman_update(L.kind, q, m[j][0], m[j][1], m[j][2], v[j], t);
     }
     return ok;
