@@ -47,6 +47,7 @@ __device__ __forceinline__ void write_seed(const State& t, int i, int region, in
     }
 }
 
+template <bool FAST>
 __global__ void __launch_bounds__(kThreads) k_seed(const DevGeom* __restrict__ gp, DevParams P, HitStore H, int n,
                                                    const int* __restrict__ seed_hits, float* __restrict__ state,
                                                    double* __restrict__ state64, int4* __restrict__ info,
@@ -57,7 +58,7 @@ __global__ void __launch_bounds__(kThreads) k_seed(const DevGeom* __restrict__ g
     if (i >= n) return;
     StateT<double> td;
     int lay[3], event, region, start;
-    const bool ok = seed_fit<double>(g, P, H, seed_hits, i, td, lay, event);
+    const bool ok = seed_fit<double, FAST>(g, P, H, seed_hits, i, td, lay, event);
     State t;
     narrow_state(td, t);
     seed_region(g, P, t.th, lay[2], ok, region, start);
@@ -96,7 +97,11 @@ cudaError_t launch_seed(cudaStream_t st, const DevGeom* g, DevParams P, HitStore
                         float* cov21, int* info3) {
     if (n == 0) return cudaSuccess;
     const int blocks = (n + kThreads - 1) / kThreads;
-    k_seed<<<blocks, kThreads, 0, st>>>(g, P, H, n, seed_hits, state, state64, info, state6, cov21, info3);
+    // the FP32 path's seed fits take the FP32-assisted FP64 steps; the plain all-FP64 path does not
+    if (P.precision == MKGB_FP64)
+        k_seed<false><<<blocks, kThreads, 0, st>>>(g, P, H, n, seed_hits, state, state64, info, state6, cov21, info3);
+    else
+        k_seed<true><<<blocks, kThreads, 0, st>>>(g, P, H, n, seed_hits, state, state64, info, state6, cov21, info3);
     k_seed_key<<<blocks, kThreads, 0, st>>>(n, state, info, key_of, key_counts);
     return cudaGetLastError();
 }

@@ -626,7 +626,7 @@ __device__ __forceinline__ int propagate(const DevLayer& L, float cBf, int mater
 // path takes fast = false.
 template <class F>
 __device__ __forceinline__ int propagate_refined(const DevLayer& L, float cBf, int material, const StateT<F>& t,
-                                                 PredT<F>& q, int& newton_it, bool fast);
+                                                 PredT<F>& q, int& newton_it, bool fast, F* dir = nullptr);
 
 // ----------------------------------------------------------------- window (a8)
 
@@ -722,9 +722,9 @@ __device__ __forceinline__ bool chi2_hit(int kind, const PredT<F>& q, F mx, F my
 // kappa (optional) gets (max L_ii / min L_ii)^2 of the Cholesky factor of S, an estimate of its
 // condition number.
 template <class F>
-__device__ __forceinline__ bool kalman_update(int kind, const PredT<F>& q, F mx, F my, F mz, const F v[6],
-                                              StateT<F>& out, float* kappa = nullptr, const F* dm = nullptr) {
-    const FrameT<F> f = frame_of(kind, q);
+__device__ __forceinline__ bool kalman_update_f(const FrameT<F>& f, const PredT<F>& q, F mx, F my, F mz,
+                                                const F v[6], StateT<F>& out, float* kappa = nullptr,
+                                                const F* dm = nullptr) {
     F rl[3], vl[6], S[6], L[6], inv[3];
     local_meas(f, q, mx, my, mz, v, rl, vl, S, dm);
     if (!chol3(S, L, inv)) return false;
@@ -781,6 +781,13 @@ __device__ __forceinline__ bool kalman_update(int kind, const PredT<F>& q, F mx,
     out.th = q.th + dp[4];
     embed_cov(f, cn, out.c);
     return out.th > F(0) && out.th < Phys<F>::pi;
+}
+
+// The same with the surface frame built from the prediction.
+template <class F>
+__device__ __forceinline__ bool kalman_update(int kind, const PredT<F>& q, F mx, F my, F mz, const F v[6],
+                                              StateT<F>& out, float* kappa = nullptr, const F* dm = nullptr) {
+    return kalman_update_f(frame_of(kind, q), q, mx, my, mz, v, out, kappa, dm);
 }
 
 // Kalman update of a global-frame state that is not constrained to a surface (the first hit of
@@ -900,7 +907,7 @@ template <class T, int K> __device__ __forceinline__ void narrow_to_fp32(const S
 namespace mk {
 template <class F>
 __device__ __forceinline__ int propagate_refined(const DevLayer& L, float cBf, int material, const StateT<F>& t,
-                                                 PredT<F>& q, int& newton_it, bool fast) {
+                                                 PredT<F>& q, int& newton_it, bool fast, F* dir) {
     F sg = F(0);
     bool have = false;
     if (fast) {
@@ -914,7 +921,38 @@ __device__ __forceinline__ int propagate_refined(const DevLayer& L, float cBf, i
             have = true;
         }
     }
-    return propagate_core<F, F>(L, cBf, material, t, t.c, q, q.c, newton_it, nullptr, nullptr, have ? &sg : nullptr,
+    return propagate_core<F, F>(L, cBf, material, t, t.c, q, q.c, newton_it, dir, nullptr, have ? &sg : nullptr,
                                 nullptr, fast);
+}
+}  // namespace mk
+
+namespace mk {
+// Kalman update with a hit at the state's own position under a prior whose position block is
+// diagonal and uncorrelated with the other parameters (the seed fit's first hit): the residual is
+// zero and only the position block changes, to C' = C0 S^-1 V with S = C0 + V (the same matrix
+// as C0 - C0 S^-1 C0, without its cancellation).  Returns false if S is not positive definite.
+template <class F> __device__ __forceinline__ bool prior_update_at_hit(StateT<F>& t, const F v[6]) {
+    const F c0[3] = {t.c[ix(0, 0)], t.c[ix(1, 1)], t.c[ix(2, 2)]};
+    F S[6], L[6], inv[3];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) S[i] = v[i];
+    S[ix(0, 0)] += c0[0]; S[ix(1, 1)] += c0[1]; S[ix(2, 2)] += c0[2];
+    if (!chol3(S, L, inv)) return false;
+    const F Vm[3][3] = {{v[0], v[1], v[3]}, {v[1], v[2], v[4]}, {v[3], v[4], v[5]}};
+    F X[3][3];   // S^-1 V by forward and back substitution with L (L[0], L[2], L[5] diagonal)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const F y0 = Vm[0][c] * inv[0];
+        const F y1 = (Vm[1][c] - L[1] * y0) * inv[1];
+        const F y2 = (Vm[2][c] - L[3] * y0 - L[4] * y1) * inv[2];
+        X[2][c] = y2 * inv[2];
+        X[1][c] = (y1 - L[4] * X[2][c]) * inv[1];
+        X[0][c] = (y0 - L[1] * X[1][c] - L[3] * X[2][c]) * inv[0];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) t.c[ix(i, j)] = F(0.5) * (c0[i] * X[i][j] + c0[j] * X[j][i]);
+    return true;
 }
 }  // namespace mk

@@ -61,25 +61,33 @@ __device__ __forceinline__ bool seed_prior(const DevGeom& g, const HitStore& H, 
     return ok;
 }
 
-// Seed fit of seed i entirely in precision F (the all-FP64 path takes F = double): update with
-// hit 1, then propagate to and update with hits 2 and 3.  Returns ok.
-template <class F>
+// Seed fit of seed i in precision F: update with hit 1, then propagate to and update with hits
+// 2 and 3.  FAST (FP64 fits of the FP32 path): the first update in closed form (zero residual,
+// diagonal prior), FP32 crossings refined in FP64 (propagate_refined) and the update's frame from
+// the propagation's direction; the plain all-FP64 path takes the general steps.  Returns ok.
+template <class F, bool FAST = false>
 __device__ __forceinline__ bool seed_fit(const DevGeom& g, const DevParams& P, const HitStore& H,
                                          const int* __restrict__ seed_hits, int i, StateT<F>& t, int lay[3],
                                          int& event) {
     F m[3][3], v[3][6];
     bool ok = seed_prior(g, H, seed_hits, i, m, v, lay, event, t);
     int newton = 0;
-    ok = ok && state_update(t, m[0][0], m[0][1], m[0][2], v[0]);
-    // the FP64 fit of the FP32 path refines FP32 crossings (propagate_refined); the plain
-    // all-FP64 path solves them in FP64 from the start
-    const bool fast = sizeof(F) == 8 && P.precision != MKGB_FP64;
+    constexpr bool fast = FAST && sizeof(F) == 8;
+    if constexpr (fast)
+        ok = ok && prior_update_at_hit(t, v[0]);
+    else
+        ok = ok && state_update(t, m[0][0], m[0][1], m[0][2], v[0]);
 #pragma unroll
     for (int j = 1; j < 3; ++j) {
         PredT<F> q;
         const DevLayer& L = g.layers[lay[j]];
-        ok = ok && propagate_refined(L, g.cB, P.material, t, q, newton, fast) == 1;
-        ok = ok && kalman_update(L.kind, q, m[j][0], m[j][1], m[j][2], v[j], t);
+        F dir[4];
+        ok = ok && propagate_refined(L, g.cB, P.material, t, q, newton, fast, dir) == 1;
+        if constexpr (fast)
+            ok = ok && kalman_update_f(frame_of(L.kind, q.xh, q.yh, dir[0], dir[1], dir[2], dir[3]), q, m[j][0],
+                                       m[j][1], m[j][2], v[j], t);
+        else
+            ok = ok && kalman_update(L.kind, q, m[j][0], m[j][1], m[j][2], v[j], t);
     }
     return ok;
 }
