@@ -19,6 +19,11 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmkgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The FP32 Kalman-step kernels take the approximate FP32 division and square root (at most
+# 2 ulp instead of 0.5: well inside the error budget of the FP32 step, ~5% faster search);
+# FP64 arithmetic is not affected by these flags.
+FILE_FLAGS = {"k_build.cu": ["-prec-div=false", "-prec-sqrt=false"],
+              "k_fit.cu": ["-prec-div=false", "-prec-sqrt=false"]}
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
          "--expt-relaxed-constexpr"]
 
@@ -35,7 +40,8 @@ def sources():
 
 
 def _deps():
-    return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "mkgb.h")]
+    return ([os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "mkgb.h")] +
+            [os.path.abspath(__file__)])
 
 
 def up_to_date() -> bool:
@@ -54,7 +60,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def one(src):
         obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
-        cmd = [cc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *FILE_FLAGS.get(os.path.basename(src), []), "-c", src, "-o", obj]
         if verbose:
             cmd += ["-Xptxas", "-v"]
         r = subprocess.run(cmd, capture_output=True, text=True)
