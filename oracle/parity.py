@@ -106,7 +106,10 @@ def compare_build(gpu: dict, orc: dict):
                 worst_cov=float(c_ratio.max()) if c_ratio.size else 0.0,
                 worst_chi2=float(x_ratio.max()) if x_ratio.size else 0.0,
                 bad_seeds=idx[cmp][(~p_ok).any(1) | (~c_ok).any(1) | ~x_ok][:20],
-                worst_cov_elem=int(np.argmax(c_ratio.max(0))) if c_ratio.size else -1)
+                worst_cov_elem=int(np.argmax(c_ratio.max(0))) if c_ratio.size else -1,
+                worst_param_elem=int(np.argmax(p_ratio.max(0))) if p_ratio.size else -1,
+                worst_param_seeds=(idx[cmp][np.argsort(-p_ratio.max(1))[:5]].tolist() if p_ratio.size else []),
+                worst_param_ratios=(np.sort(p_ratio.max(1))[::-1][:5].tolist() if p_ratio.size else []))
 
 
 def compare_fit(gpu: dict, orc: dict, mask=None):

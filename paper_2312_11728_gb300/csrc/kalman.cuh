@@ -110,6 +110,10 @@ __device__ __forceinline__ double fma_rn(double a, double b, double c) { return 
 __device__ __forceinline__ void sin_cos(float x, float* s, float* c) { sin_cos_cw(x, s, c); }
 __device__ __forceinline__ void sin_cos(double x, double* s, double* c) { sincos(x, s, c); }
 __device__ __forceinline__ float rsq(float x) { return rsqrtf(x); }
+// Correctly rounded division where it sets the trajectory (path length, chord, dz/ds): kernels
+// built with approximate FP32 division keep these at 0.5 ulp.
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return a / b; }
 // Logarithm inside the material terms (Highland's log correction, Bethe-Bloch's log term): an
 // absolute error of ~1e-6 there moves theta0 and dE/dx by ~1e-7 relative, so FP32 takes the
 // hardware logarithm (__logf, at most 3 ulp off outside [0.5, 2]).
@@ -144,6 +148,11 @@ template <class T, int K> __device__ __forceinline__ void sin_cos(const Dual<T, 
     sin_cos(x.v, &sv, &cv);
     *s = x.chain(sv, cv);
     *c = x.chain(cv, -sv);
+}
+template <class T, int K> __device__ __forceinline__ Dual<T, K> div_rn(const Dual<T, K>& a, const Dual<T, K>& b) {
+    Dual<T, K> r = a / b;
+    r.v = div_rn(a.v, b.v);
+    return r;
 }
 template <class T, int K> __device__ __forceinline__ Dual<T, K> rsq(const Dual<T, K>& x) {
     const T r = rsq(x.v);
@@ -455,7 +464,7 @@ __device__ __forceinline__ int propagate_core(const DevLayer& L, float cBf, int 
     } else {
         if (fabs(ct) < F(1e-7)) return 0;
         const F dzp = sub_rn(sub_rn(zd, t.zh), t.zl);
-        s = dzp * st / ct;
+        s = div_rn(dzp * st, ct);
         if (!(s > F(0))) return 0;
         // loopers are followed on the outgoing part of their current turn only: the disk must be
         // reached before the next point of largest radius (and moving outward, checked below)
@@ -489,13 +498,13 @@ __device__ __forceinline__ int propagate_core(const DevLayer& L, float cBf, int 
             const F h2 = h * h;
             sinc = F(1) + h2 * (F(-1) / F(6) + h2 * (F(1) / F(120) + h2 * (F(-1) / F(5040) + h2 * (F(1) / F(362880)))));
         } else {
-            sinc = sh / h;
+            sinc = div_rn(sh, h);
         }
         const F chord = s * sinc;
         dx = chord * cp;
         dy = chord * sp;
     }
-    const F cot = ct / st;
+    const F cot = div_rn(ct, st);
     const F dz = (L.kind == MKGB_BARREL) ? s * cot : sub_rn(sub_rn(zd, t.zh), t.zl);
     F xh = t.xh, xl = t.xl, yh = t.yh, yl = t.yl, zh = t.zh, zl = t.zl;
     add_ff(xh, xl, dx);
@@ -508,7 +517,7 @@ __device__ __forceinline__ int propagate_core(const DevLayer& L, float cBf, int 
         // 30 um; the gap R^2 - r'^2 of the compensated position is exact to ~eps^2, so one
         // more Newton step along the track puts the predicted point on the surface
         const F gap = r2_gap(Rl, xh, xl, yh, yl);
-        const F dsp = gap / (F(2) * (xh * cfp + yh * sfp));
+        const F dsp = div_rn(gap, F(2) * (xh * cfp + yh * sfp));
         add_ff(xh, xl, dsp * cfp);
         add_ff(yh, yl, dsp * sfp);
         add_ff(zh, zl, dsp * cot);
