@@ -78,8 +78,9 @@ typedef struct {
     int32_t material;      /* 1: multiple scattering and energy loss at every crossed layer */
     int32_t precision;     /* MKGB_FP32: Kalman steps of the search and the fit in FP32 (seed fits in FP64);
                               MKGB_FP64: every step in FP64 (the plain comparison path) */
-    float kappa_fp64;      /* fit: a track with an update whose innovation covariance S has a condition
-                              estimate above this is refit in FP64; 0 = never */
+    float kappa_fp64;      /* an update whose innovation covariance S has a condition estimate above this
+                              is redone in FP64: the search redoes that update, the fit refits the whole
+                              track; 0 = never (both only in the FP32 precision) */
 } mkgb_params;
 
 #define MKGB_FP32 0

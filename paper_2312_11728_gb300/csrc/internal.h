@@ -57,7 +57,8 @@ struct BuildWork {
     int4* sinfo;      // per ordered seed: (plan position of its first step, first step, steps, event)
     int* fin;         // per ordered seed: buffer holding its final slots, -1 none
     int* trail;       // per ordered seed: longest plan x 8 ints ((code + 4) << 3 | parent slot)
-    int* counts;      // [live0, live1, seeds0, seeds1]
+    int* rescue;      // kept children of the round whose update is redone in FP64
+    int* counts;      // [live0, live1, seeds0, seeds1, rescue]
 };
 
 // counters (64-bit): [0] steps, [1] chi2 evaluations, [2] updates, [3] hits tested, [4] Newton iterations

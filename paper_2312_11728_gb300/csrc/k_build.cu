@@ -219,9 +219,10 @@ __global__ void __launch_bounds__(kThreads) k_find(BuildArgs a, int tau) {
     load_geom_smem(a.geom, g);
     const int tx = threadIdx.x;
     const int cur = tau & 1, nxt = cur ^ 1;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {   // next round's lists are filled by k_select
+    if (blockIdx.x == 0 && threadIdx.x == 0) {   // lists filled by this round's k_select
         a.w.counts[nxt] = 0;
         a.w.counts[2 + nxt] = 0;
+        a.w.counts[4] = 0;
     }
     const DevParams& P = a.P;
     const int n = a.w.counts[cur];
@@ -238,9 +239,13 @@ __global__ void __launch_bounds__(kThreads) k_find(BuildArgs a, int tau) {
         const int4 si = a.w.sinfo[i];
         const int layer = g.plan[si.x + tau];
         const DevLayer& L = g.layers[layer];
+        const int4 mt = a.w.meta[cur][sl];
+        if (mt.w == 0) {   // dropped after the selection (its FP64 update redo failed)
+            a.w.ls[(int64_t)sl * 5] = make_int4(0, K_NONE, 0, 0);
+            continue;
+        }
         StateT<F> t;
         load_state_rec(a.w.st[cur] + (int64_t)sl * state_bytes<F>(), t);
-        const int4 mt = a.w.meta[cur][sl];
         const float score = __int_as_float(mt.x);
         const int nholes = (mt.z >> 8) & 0xff;
 
@@ -454,6 +459,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_select(BuildArgs a, int tau) {
         int nfound = pm.z & 0xff, nholes = (pm.z >> 8) & 0xff;
         int code = MKGB_HIT_STOP;
         const int csl = i * kGroup + slot;
+        bool rescue = false;
         if (gact && my_kind != K_NONE) {
             const int psl = i * kGroup + my_parent;
             c_alive = true;
@@ -471,11 +477,15 @@ __global__ void __launch_bounds__(kThreads, 5) k_select(BuildArgs a, int tau) {
                     F m[3], v[6];
                     int id;
                     load_hit(a.H.hb_pay, my_q, m, v, &id);
-                    if (kalman_update(L.kind, pq, m[0], m[1], m[2], v, t)) {
+                    float kap = 0.0f;
+                    if (kalman_update(L.kind, pq, m[0], m[1], m[2], v, t, &kap)) {
                         chi2s += my_x2;
                         ++nfound;
                         ++c_upd;
                         code = id;
+                        // FP32 cannot resolve an innovation covariance this ill-conditioned: the
+                        // update is redone in FP64 by k_rescue (mixed precision, growth G3)
+                        rescue = sizeof(F) == 4 && P.kappa_fp64 > 0.0f && kap > P.kappa_fp64;
                     } else {
                         c_alive = false;
                     }
@@ -493,6 +503,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_select(BuildArgs a, int tau) {
             a.w.trail[((int64_t)i * a.max_steps + tau) * kGroup + slot] = ((code + 4) << 3) | my_parent;
         }
         if (gact) a.w.meta[nxt][csl] = pack_meta(my_score, chi2s, nfound, nholes, c_stopped, c_alive);
+        warp_append(rescue, csl, a.w.rescue, a.w.counts + 4);
         const bool more = gact && tau + 1 < si.z;
         warp_append(more && c_alive && !c_stopped, csl, a.w.live[nxt], a.w.counts + nxt);
         const unsigned am = __ballot_sync(kFull, c_alive);
@@ -501,6 +512,44 @@ __global__ void __launch_bounds__(kThreads, 5) k_select(BuildArgs a, int tau) {
         if (gact && slot == 0 && (!more || !any)) a.w.fin[i] = nxt;
     }
     add_counters(a.counters, 0ull, 0ull, c_upd, 0ull, 0ull);
+}
+
+// ---- FP64 redo of the round's flagged updates (kept children of round tau whose innovation
+// covariance had a condition estimate above kappa_fp64); one thread per child
+__global__ void __launch_bounds__(kThreads) k_rescue(BuildArgs a, int tau) {
+    __shared__ DevGeom g;
+    load_geom_smem(a.geom, g);
+    const int cur = tau & 1, nxt = cur ^ 1;
+    const int n = a.w.counts[4];
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+        const int csl = a.w.rescue[r];
+        const int i = csl / kGroup;
+        const int slot = csl % kGroup;
+        const int v = a.w.trail[((int64_t)i * a.max_steps + tau) * kGroup + slot];
+        const int psl = i * kGroup + (v & 7);
+        const int4 si = a.w.sinfo[i];
+        const int lkind = g.layers[g.plan[si.x + tau]].kind;
+        Pred pq;
+        load_pred_rec(a.w.pr + (int64_t)psl * pred_bytes<float>(), pq);
+        PredT<double> qd;
+        qd.xh = pq.xh; qd.yh = pq.yh; qd.zh = pq.zh; qd.xl = pq.xl; qd.yl = pq.yl; qd.zl = pq.zl;
+        qd.k = pq.k; qd.phi = pq.phi; qd.th = pq.th;
+#pragma unroll
+        for (int q = 0; q < 15; ++q) qd.c[q] = pq.c[q];
+        // the hit: its binned index is not in the trail (which holds the hit id), so it is looked
+        // up through the hit id in the payload's original order
+        const int id = (v >> 3) - 4;
+        double m[3], vv[6];
+        load_hit(a.H.pay, id, m, vv, nullptr);
+        StateT<double> td;
+        if (kalman_update(lkind, qd, m[0], m[1], m[2], vv, td)) {
+            State t;
+            narrow_state(td, t);
+            store_state_rec(a.w.st[nxt] + (int64_t)csl * state_bytes<float>(), t);
+        } else {
+            a.w.meta[nxt][csl].w = 0;   // dropped; k_find skips it
+        }
+    }
 }
 
 // ---- best candidate per seed and its hit list (a13); 8 lanes per seed
@@ -586,7 +635,8 @@ size_t layout_build_work(char* base, int n_seeds, int max_plan_len, int word_byt
     t.sinfo = reinterpret_cast<int4*>(take(ns * 16));
     t.fin = reinterpret_cast<int*>(take(ns * 4));
     t.trail = reinterpret_cast<int*>(take(ns * (size_t)max_plan_len * kGroup * 4));
-    t.counts = reinterpret_cast<int*>(take(16));
+    t.rescue = reinterpret_cast<int*>(take(slots * 4));
+    t.counts = reinterpret_cast<int*>(take(32));
     if (w) *w = t;
     return off;
 }
@@ -600,6 +650,7 @@ cudaError_t launch_rounds(cudaStream_t st, const BuildArgs& a, int n, int max_pl
     for (int tau = 0; tau < max_plan_len; ++tau) {
         k_find<F><<<grid_find, kThreads, 0, st>>>(a, tau);
         k_select<F><<<grid_sel, kThreads, 0, st>>>(a, tau);
+        if (sizeof(F) == 4 && a.P.kappa_fp64 > 0.0f) k_rescue<<<n_sms, kThreads, 0, st>>>(a, tau);
     }
     k_finish<F><<<(n * kGroup + kThreads - 1) / kThreads, kThreads, 0, st>>>(a);
     return cudaGetLastError();
@@ -621,7 +672,7 @@ cudaError_t launch_build(cudaStream_t st, const DevGeom* g, int max_plan_len, De
                          BuildOutDev out, BuildWork w, unsigned long long* counters, int n_sms) {
     if (S.n == 0) return cudaSuccess;
     BuildArgs a{g, P, H, S, out, w, counters, max_plan_len};
-    cudaError_t e = cudaMemsetAsync(w.counts, 0, 16, st);
+    cudaError_t e = cudaMemsetAsync(w.counts, 0, 32, st);
     if (e != cudaSuccess) return e;
     // MKGB_FP64: the plain all-FP64 comparison path (same rounds, every Kalman step in FP64)
     return P.precision == MKGB_FP64 ? launch_rounds<double>(st, a, S.n, max_plan_len, n_sms)

@@ -224,6 +224,24 @@ def test_device_and_host_paths_agree_and_are_deterministic(lib, phase2_small):
     assert np.array_equal(db.fit["p"].cpu().numpy(), host["fit"]["p"])
 
 
+def test_search_fp64_redo_of_ill_conditioned_updates(lib, phase2_small):
+    """With a low condition threshold many search updates are redone in FP64 (k_rescue): the
+    results still match the oracle, and they differ from the run without the redo."""
+    g, batch, params = phase2_small
+    outs = {}
+    for kappa in (1e3, 0.0):
+        p = dict(params, kappa_fp64=kappa)
+        res = pipeline.run_host(_ctx(g, p), batch, g.max_plan)
+        outs[kappa] = res["build"]
+        if kappa > 0:
+            o = PR.oracle_build(oracle.Oracle(g, p), batch)
+            rep = _report("build_redo_phase2_small", PR.compare_build(res["build"], o))
+            assert len(rep["hit_mismatch"]) == 0 and rep["failed_mismatch"] == 0, rep
+            assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0, rep
+    changed = np.any(outs[1e3]["cov"] != outs[0.0]["cov"], axis=1)
+    assert changed.sum() > 10
+
+
 def test_one_call_run_matches_separate_calls(lib, phase2_small):
     """mkgb_run (the fit on a second stream inside the call) gives the separate calls' results
     bit for bit, twice in a row."""
