@@ -306,6 +306,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison path")
     ap.add_argument("--no-grad", action="store_true", help="skip the fit-derivative measurement")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shapes of the search kernels")
+    ap.add_argument("--no-graph", action="store_true", help="launch the search rounds one by one")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -353,6 +355,10 @@ def main():
     bc = ctx.counters(0)
     fc = ctx.counters(1)
     kalman_steps = int(bc[0] + fc[0])
+    shapes = (0, 0, None)
+    if not args.no_autotune:
+        shapes = ctx.autotune(reps=2)   # block shapes of the search kernels on this batch
+    ctx.set_launch(shapes[0], shapes[1], use_graph=not args.no_graph)
     for _ in range(max(0, args.warmup - 1)):
         pipeline.run_step_fused(ctx, db)
     torch.cuda.synchronize()
@@ -423,10 +429,11 @@ def main():
             traffic = tr["dram_bytes_per_crossed_step"] * int(bc[0])
     bins_total = batch.n_events * int((g.n_eta.astype(np.int64) * g.n_phi).sum())
     keys_total = batch.n_events * 32 * 64
-    # hits: prep, scatter, scans; seeds: fit, key, scans, scatter; search: start, (find, select)
-    # per plan step of the longest plan, finish; fit: FP32 fit and FP64 refit
-    launches_per_step = ((2 + scan_launches(bins_total)) + (2 + scan_launches(keys_total)) + 2 + 2 * g.max_plan
-                         + 1 + (1 if params["kappa_fp64"] > 0 else 0))
+    # hits: prep, scatter, scans; seeds: fit, key, scans, scatter; search: start, (find, select,
+    # FP64 redo) per plan step of the longest plan, finish; fit: FP32 fit and FP64 refit
+    redo = 1 if params["kappa_fp64"] > 0 else 0
+    launches_per_step = ((2 + scan_launches(bins_total)) + (2 + scan_launches(keys_total)) + 2
+                         + (2 + redo) * g.max_plan + 1 + redo)
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -437,14 +444,17 @@ def main():
                    "seeds": int(n_seeds), "fit_tracks": int(n_tracks), "hits": int(batch.hit_xyz.shape[0]),
                    "kalman_steps_per_step": kalman_steps, "build_steps": int(bc[0]), "fit_steps": int(fc[0]),
                    "l2": f"inputs larger than L2: {batch.hit_xyz.shape[0] * 92 / 1e9:.2f} GB of hit data resident",
-                   "parallelism": f"replicas{world}"},
+                   "parallelism": f"replicas{world}",
+                   "search_launch": {"find_shape": shapes[0], "select_shape": shapes[1],
+                                     "autotune_ms_per_search": shapes[2], "cuda_graph": not args.no_graph}},
         "stages_ms": {k: round(float(v), 4) for k, v in stage.items()},
         "roofline": {"bound": "alu", "kernel": "search (k_start, k_find + k_select per plan step, k_finish)",
                      "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                      "peak_note": f"FP32: {n_sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz ({src} max clock)",
                      "flops_per_launch": int(build_flops(bc)),
-                     "launch": "one mkgb_build call per step, timed with CUDA events on its stream"},
+                     "launch": "one mkgb_build call per step (its rounds replayed as one CUDA graph), "
+                               "timed with CUDA events on its stream"},
         "e2e": e2e,
         "fp64_plain": fp64,
         "fit_grad": grad,

@@ -165,6 +165,29 @@ int mkgb_run(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* x
              const int32_t* layers, const int32_t* hits, const float* p0, const float* c0, float* p_out,
              float* c_out, float* chi2_out, int32_t* status_out);
 
+/* Launch configuration of the search rounds (mkgb_build, mkgb_run).  The paper has no
+ * counterpart: this is a library service that changes neither results nor arithmetic.
+ * find_shape / select_shape pick the block shape of the two per-layer kernels of the search
+ * (0: 128 threads, the default; 1: 64 threads; 2: 256 threads; each with its own register bound
+ * and a grid of as many blocks as stay resident on the device).  use_graph = 1 (the default)
+ * records the ~(2 + 3 x longest plan) launches of one search as a CUDA graph on the first call
+ * and replays it while the arguments, shapes and stream stay the same (a change re-records);
+ * the graph is used only on a stream created by the caller or the library (not the legacy or
+ * per-thread default stream) and not while the stream is being captured by the caller, where
+ * the launches are made one by one and join the caller's capture.  Results are identical for
+ * every choice.  Errors: MKGB_EINVAL for a shape outside 0..2. */
+int mkgb_set_launch(mkgb_ctx* ctx, int find_shape, int select_shape, int use_graph);
+
+/* Autotuner of the search launch shapes (library service, no counterpart in the paper): runs
+ * the search over the seeds loaded now (mkgb_seed) once per shape pair (3 x 3 pairs), each
+ * warmed once and then timed reps times with CUDA events on the context's stream, keeps the
+ * fastest pair as the context's shapes (mkgb_set_launch) and writes it to find_shape /
+ * select_shape (may be NULL) and its mean time per search to ms_out (may be NULL).  The outputs
+ * of these searches go to the library's own buffers; loaded hits and seeds are not changed.
+ * Synchronises the stream.  Errors: MKGB_ESTATE without seeds, MKGB_EINVAL for reps < 1, the
+ * errors of mkgb_build. */
+int mkgb_autotune(mkgb_ctx* ctx, int reps, int* find_shape, int* select_shape, float* ms_out);
+
 /* Derivative of the fit (growth of Sec. 4's final fit): the fit over a known assignment with
  * per-layer alignment and material applied, and the derivatives of its total chi2.  Alignment:
  * align[l*6 + (0..5)] = (dx, dy, dz, wx, wy, wz) moves every hit of layer l as

@@ -60,6 +60,7 @@ struct mkgb_ctx {
     // preparation and joined by the next user of the binned hits
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_prep = nullptr, ev_bins = nullptr;
+    bool bins_pending = false;   // ev_bins recorded and not yet waited for on the context's stream
     // side stream and events of mkgb_run's fit
     cudaStream_t fit_st = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_fit = nullptr;
@@ -78,6 +79,10 @@ struct mkgb_ctx {
     DevBuf seed_hits, seed_state, seed_state64, seed_info, seed_key, key_counts, key_cursor, seed_order, seed_scan_tmp;
     DevBuf counters_build, counters_fit, queue, rescue_list, rescue_count, build_work;
     DevBuf stage[S_COUNT];
+    // launch shapes of the search rounds and the graph cache replaying them
+    int find_shape = 0, select_shape = 0;
+    bool use_graph = true;
+    BuildGraph* graph = nullptr;
 };
 
 namespace {
@@ -137,9 +142,39 @@ cudaError_t stage_out(mkgb_ctx* c, Stage s, void* dst, size_t bytes, bool on_dev
     return e;
 }
 
+// A library-owned device buffer of the given bytes (outputs nobody reads back).
+cudaError_t stage_buf(mkgb_ctx* c, Stage s, size_t bytes, void** out) {
+    cudaError_t e = ensure(c->stage[s], bytes);
+    *out = c->stage[s].p;
+    return e;
+}
+
 cudaError_t copy_back(mkgb_ctx* c, void* dst, const void* dev, size_t bytes, bool on_device) {
     if (on_device || dst == nullptr || bytes == 0) return cudaSuccess;
     return cudaMemcpyAsync(dst, dev, bytes, cudaMemcpyDeviceToHost, c->stream);
+}
+
+// The search of mkgb_build on the context's stream into device outputs d (seeds and binned hits
+// loaded); the rounds go through the context's graph cache unless graphs are switched off.
+int enqueue_build(mkgb_ctx* ctx, const BuildOutDev& d, int find_shape, int select_shape) {
+    cudaStream_t st = ctx->stream;
+    SeedStore S{ctx->n_seeds, (const float*)ctx->seed_state.p, (const double*)ctx->seed_state64.p,
+                (const int4*)ctx->seed_info.p, (const int*)ctx->seed_order.p};
+    if (ctx->bins_pending) {   // the binned hits (mkgb_load_hits)
+        CK(cudaStreamWaitEvent(st, ctx->ev_bins, 0));
+        ctx->bins_pending = false;
+    }
+    const int prec = ctx->params.precision;
+    if (prec == MKGB_FP64 && !ctx->seeds_fp64)
+        return fail(ctx, MKGB_ESTATE, "FP64 search needs seeds made under the FP64 precision");
+    CK(ensure(ctx->build_work, build_work_bytes(ctx->n_seeds, ctx->max_plan_len, prec)));
+    const BuildWork w = carve_build_work(ctx->build_work.p, ctx->n_seeds, ctx->max_plan_len, prec);
+    CK(cudaMemsetAsync(ctx->counters_build.p, 0, 8 * kNumCounters, st));
+    if (ctx->use_graph && !ctx->graph) ctx->graph = build_graph_create();
+    CK(launch_build(st, (const DevGeom*)ctx->geom_d.p, ctx->max_plan_len, ctx->params, hit_store(ctx), S, d, w,
+                    (unsigned long long*)ctx->counters_build.p, ctx->n_sms, find_shape, select_shape,
+                    ctx->use_graph ? ctx->graph : nullptr));
+    return MKGB_OK;
 }
 
 }  // namespace
@@ -214,6 +249,7 @@ void mkgb_destroy(mkgb_ctx* ctx) {
                          &ctx->rescue_count, &ctx->build_work};
         for (DevBuf* b : all) release(*b);
         for (auto& b : ctx->stage) release(b);
+        build_graph_destroy(ctx->graph);
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     }
     delete ctx;
@@ -337,10 +373,12 @@ int mkgb_load_hits(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const fl
         CK(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&ctx->ev_prep, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&ctx->ev_bins, cudaEventDisableTiming));
-        CK(cudaEventRecord(ctx->ev_bins, ctx->aux));
     }
     // the previous call's binning must be done before its inputs and outputs are rewritten
-    CK(cudaStreamWaitEvent(st, ctx->ev_bins, 0));
+    if (ctx->bins_pending) {
+        CK(cudaStreamWaitEvent(st, ctx->ev_bins, 0));
+        ctx->bins_pending = false;
+    }
     // The offsets are copied only when they change (a repeated batch costs no host round trip).
     // A copy from pageable memory returns once the source has been staged, so the host vector
     // may be rewritten after the call.
@@ -384,6 +422,7 @@ int mkgb_load_hits(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const fl
                           (const int*)ctx->bin_of_hit.p, (int*)ctx->cursor.p, (float2*)ctx->hb_ep.p,
                           (float4*)ctx->hb_pay.p));
     CK(cudaEventRecord(ctx->ev_bins, ctx->aux));
+    ctx->bins_pending = true;
     if (!on_device) CK(cudaStreamSynchronize(st));
     ctx->n_events = n_events;
     ctx->n_hits = n;
@@ -447,7 +486,6 @@ int mkgb_build(mkgb_ctx* ctx, const mkgb_tracks* out, int on_device) {
         return fail(ctx, MKGB_EINVAL, "%lld hits loaded: the search takes fewer than 2^28 - 8",
                     (long long)ctx->n_hits);
     DevGuard guard(ctx->device);
-    cudaStream_t st = ctx->stream;
     const size_t n = (size_t)ctx->n_seeds;
     BuildOutDev d;
     void* p;
@@ -459,18 +497,9 @@ int mkgb_build(mkgb_ctx* ctx, const mkgb_tracks* out, int on_device) {
     CK(stage_out(ctx, S_F, out->nholes, 4 * n, on_device, &p)); d.nholes = (int*)p;
     CK(stage_out(ctx, S_G, out->hits, 4 * n * out->max_plan, on_device, &p)); d.hits = (int*)p;
     d.max_plan = out->max_plan;
-    SeedStore S{ctx->n_seeds, (const float*)ctx->seed_state.p, (const double*)ctx->seed_state64.p,
-                (const int4*)ctx->seed_info.p,
-                (const int*)ctx->seed_order.p};
-    CK(cudaStreamWaitEvent(st, ctx->ev_bins, 0));   // the binned hits (mkgb_load_hits)
-    const int prec = ctx->params.precision;
-    if (prec == MKGB_FP64 && !ctx->seeds_fp64)
-        return fail(ctx, MKGB_ESTATE, "FP64 search needs seeds made under the FP64 precision");
-    CK(ensure(ctx->build_work, build_work_bytes(ctx->n_seeds, ctx->max_plan_len, prec)));
-    const BuildWork w = carve_build_work(ctx->build_work.p, ctx->n_seeds, ctx->max_plan_len, prec);
-    CK(cudaMemsetAsync(ctx->counters_build.p, 0, 8 * kNumCounters, st));
-    CK(launch_build(st, (const DevGeom*)ctx->geom_d.p, ctx->max_plan_len, ctx->params, hit_store(ctx), S, d, w,
-                    (unsigned long long*)ctx->counters_build.p, ctx->n_sms));
+    const int rc = enqueue_build(ctx, d, ctx->find_shape, ctx->select_shape);
+    if (rc != MKGB_OK) return rc;
+    cudaStream_t st = ctx->stream;
     CK(copy_back(ctx, out->params, d.params, 24 * n, on_device));
     CK(copy_back(ctx, out->cov, d.cov, 84 * n, on_device));
     CK(copy_back(ctx, out->chi2, d.chi2, 4 * n, on_device));
@@ -645,6 +674,71 @@ int mkgb_run(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* x
     if (rc == MKGB_OK) rc = mkgb_build(ctx, out, 1);
     CK(cudaStreamWaitEvent(main_st, ctx->ev_fit, 0));
     return rc;
+}
+
+int mkgb_set_launch(mkgb_ctx* ctx, int find_shape, int select_shape, int use_graph) {
+    if (!ctx) return MKGB_EINVAL;
+    if (find_shape < 0 || find_shape > 2 || select_shape < 0 || select_shape > 2)
+        return fail(ctx, MKGB_EINVAL, "launch shapes (%d, %d) outside 0..2", find_shape, select_shape);
+    ctx->find_shape = find_shape;
+    ctx->select_shape = select_shape;
+    ctx->use_graph = use_graph != 0;
+    return MKGB_OK;
+}
+
+int mkgb_autotune(mkgb_ctx* ctx, int reps, int* find_shape, int* select_shape, float* ms_out) {
+    if (!ctx) return MKGB_EINVAL;
+    if (!ctx->has_seeds) return fail(ctx, MKGB_ESTATE, "autotune before seed");
+    if (reps < 1) return fail(ctx, MKGB_EINVAL, "reps %d < 1", reps);
+    DevGuard guard(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const size_t n = (size_t)ctx->n_seeds;
+    BuildOutDev d;
+    void* p;
+    CK(stage_buf(ctx, S_A, 24 * n, &p)); d.params = (float*)p;
+    CK(stage_buf(ctx, S_B, 84 * n, &p)); d.cov = (float*)p;
+    CK(stage_buf(ctx, S_C, 4 * n, &p)); d.chi2 = (float*)p;
+    CK(stage_buf(ctx, S_D, 4 * n, &p)); d.score = (float*)p;
+    CK(stage_buf(ctx, S_E, 4 * n, &p)); d.nfound = (int*)p;
+    CK(stage_buf(ctx, S_F, 4 * n, &p)); d.nholes = (int*)p;
+    CK(stage_buf(ctx, S_G, 4 * n * (size_t)ctx->max_plan_len, &p)); d.hits = (int*)p;
+    d.max_plan = ctx->max_plan_len;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(ctx, MKGB_ECUDA, "event creation failed");
+    }
+    int best_f = ctx->find_shape, best_s = ctx->select_shape, rc = MKGB_OK;
+    float best = -1.0f;
+    for (int f = 0; f < 3 && rc == MKGB_OK; ++f)
+        for (int s = 0; s < 3 && rc == MKGB_OK; ++s) {
+            rc = enqueue_build(ctx, d, f, s);   // warm-up (and the graph's recording)
+            if (rc == MKGB_OK) cudaEventRecord(e0, st);
+            for (int r = 0; r < reps && rc == MKGB_OK; ++r) rc = enqueue_build(ctx, d, f, s);
+            if (rc != MKGB_OK) break;
+            float ms = 0.0f;
+            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                rc = fail(ctx, MKGB_ECUDA, "autotune timing failed");
+                break;
+            }
+            ms /= reps;
+            if (best < 0.0f || ms < best) {
+                best = ms;
+                best_f = f;
+                best_s = s;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != MKGB_OK) return rc;
+    ctx->find_shape = best_f;
+    ctx->select_shape = best_s;
+    if (find_shape) *find_shape = best_f;
+    if (select_shape) *select_shape = best_s;
+    if (ms_out) *ms_out = best;
+    return MKGB_OK;
 }
 
 int mkgb_propagate(mkgb_ctx* ctx, int n, const int32_t* layers, const float* p_in, const float* c_in, float* p_out,

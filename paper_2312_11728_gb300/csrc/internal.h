@@ -83,8 +83,14 @@ cudaError_t launch_seed(cudaStream_t st, const DevGeom* g, DevParams P, HitStore
 // ---- k_build.cu
 size_t build_work_bytes(int n_seeds, int max_plan_len, int precision);
 BuildWork carve_build_work(void* base, int n_seeds, int max_plan_len, int precision);
+struct BuildGraph;
+BuildGraph* build_graph_create();
+void build_graph_destroy(BuildGraph* gph);
+// find_shape / select_shape: launch shapes of the round kernels (0 default; 1, 2 alternatives the
+// autotuner tries); gph: graph cache of the context (nullptr: plain launches).
 cudaError_t launch_build(cudaStream_t st, const DevGeom* g, int max_plan_len, DevParams P, HitStore H, SeedStore S,
-                         BuildOutDev out, BuildWork w, unsigned long long* counters, int n_sms);
+                         BuildOutDev out, BuildWork w, unsigned long long* counters, int n_sms, int find_shape,
+                         int select_shape, BuildGraph* gph);
 
 // ---- k_fit.cu
 // ---- k_grad.cu

@@ -22,6 +22,8 @@
 // every loop is bounded by a list length, a window's bin range or the Newton iteration limit.
 #include "internal.h"
 
+#include <cstring>
+
 namespace mk {
 
 namespace {
@@ -209,13 +211,13 @@ __global__ void __launch_bounds__(kThreads) k_start(BuildArgs a) {
 }
 
 // ---- a4-a9 for every live candidate of round tau
-template <class F>
-__global__ void __launch_bounds__(kThreads) k_find(BuildArgs a, int tau) {
+template <class F, int TH, int MINB>
+__global__ void __launch_bounds__(TH, MINB) k_find(BuildArgs a, int tau) {
     __shared__ DevGeom g;
     // per-thread sorted list of hit children (chi2 asc, id asc), one column per thread
-    __shared__ float s_x2[kGroup][kThreads];
-    __shared__ int s_id[kGroup][kThreads];
-    __shared__ int s_hq[kGroup][kThreads];
+    __shared__ float s_x2[kGroup][TH];
+    __shared__ int s_id[kGroup][TH];
+    __shared__ int s_hq[kGroup][TH];
     load_geom_smem(a.geom, g);
     const int tx = threadIdx.x;
     const int cur = tau & 1, nxt = cur ^ 1;
@@ -341,8 +343,8 @@ __global__ void __launch_bounds__(kThreads) k_find(BuildArgs a, int tau) {
 }
 
 // ---- a10-a11 for every seed with a live candidate in round tau
-template <class F>
-__global__ void __launch_bounds__(kThreads, 5) k_select(BuildArgs a, int tau) {
+template <class F, int TH, int MINB>
+__global__ void __launch_bounds__(TH, MINB) k_select(BuildArgs a, int tau) {
     __shared__ DevGeom g;
     load_geom_smem(a.geom, g);
     const int cur = tau & 1, nxt = cur ^ 1;
@@ -352,7 +354,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_select(BuildArgs a, int tau) {
     const int n = a.w.counts[2 + cur];
     const int* __restrict__ list = a.w.seeds[cur];
     unsigned long long c_upd = 0;
-    const int groups_per_block = kThreads / kGroup;
+    const int groups_per_block = TH / kGroup;
     const int gstride = gridDim.x * groups_per_block;
     // loop bound uniform over the warp: the first group index of the warp
     const int g0 = blockIdx.x * groups_per_block + (threadIdx.x >> 5) * 4;
@@ -600,9 +602,9 @@ __global__ void __launch_bounds__(kThreads) k_finish(BuildArgs a) {
     }
 }
 
-int resident_grid(const void* kernel, int n_sms, size_t smem) {
+int resident_grid(const void* kernel, int n_sms, int threads = kThreads) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess || per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     return n_sms * per_sm;
 }
@@ -641,19 +643,84 @@ size_t layout_build_work(char* base, int n_seeds, int max_plan_len, int word_byt
     return off;
 }
 
+// Launch shapes of the round kernels (threads per block, minimum resident blocks per SM), one of
+// which the autotuner picks: k_find x k_select.  The resident grid of each shape is computed once,
+// before any capture.
+template <class F, int TH, int MINB> struct FindShape {
+    static int grid(int n_sms) {
+        static int g = 0;
+        if (!g) g = resident_grid((const void*)k_find<F, TH, MINB>, n_sms, TH);
+        return g;
+    }
+    static void launch(cudaStream_t st, const BuildArgs& a, int tau, int n_sms) {
+        k_find<F, TH, MINB><<<grid(n_sms), TH, 0, st>>>(a, tau);
+    }
+};
+template <class F, int TH, int MINB> struct SelectShape {
+    static int grid(int n_sms) {
+        static int g = 0;
+        if (!g) g = resident_grid((const void*)k_select<F, TH, MINB>, n_sms, TH);
+        return g;
+    }
+    static void launch(cudaStream_t st, const BuildArgs& a, int tau, int n_sms) {
+        k_select<F, TH, MINB><<<grid(n_sms), TH, 0, st>>>(a, tau);
+    }
+};
+
+template <class F> void prime_shapes(int n_sms) {
+    FindShape<F, 64, 8>::grid(n_sms);
+    FindShape<F, 128, 1>::grid(n_sms);
+    FindShape<F, 256, 1>::grid(n_sms);
+    SelectShape<F, 64, 10>::grid(n_sms);
+    SelectShape<F, 128, 5>::grid(n_sms);
+    SelectShape<F, 256, 2>::grid(n_sms);
+}
+
+template <class F> void launch_find(int shape, cudaStream_t st, const BuildArgs& a, int tau, int n_sms) {
+    switch (shape) {
+        case 1: FindShape<F, 64, 8>::launch(st, a, tau, n_sms); break;
+        case 2: FindShape<F, 256, 1>::launch(st, a, tau, n_sms); break;
+        default: FindShape<F, 128, 1>::launch(st, a, tau, n_sms); break;
+    }
+}
+
+template <class F> void launch_select(int shape, cudaStream_t st, const BuildArgs& a, int tau, int n_sms) {
+    switch (shape) {
+        case 1: SelectShape<F, 64, 10>::launch(st, a, tau, n_sms); break;
+        case 2: SelectShape<F, 256, 2>::launch(st, a, tau, n_sms); break;
+        default: SelectShape<F, 128, 5>::launch(st, a, tau, n_sms); break;
+    }
+}
+
 template <class F>
-cudaError_t launch_rounds(cudaStream_t st, const BuildArgs& a, int n, int max_plan_len, int n_sms) {
+cudaError_t launch_rounds(cudaStream_t st, const BuildArgs& a, int n, int max_plan_len, int n_sms, int find_shape,
+                          int select_shape) {
+    cudaError_t e = cudaMemsetAsync(a.w.counts, 0, 32, st);
+    if (e != cudaSuccess) return e;
     const int nb = (n + kThreads - 1) / kThreads;
     k_start<F><<<nb, kThreads, 0, st>>>(a);
-    const int grid_find = resident_grid((const void*)k_find<F>, n_sms, 0);
-    const int grid_sel = resident_grid((const void*)k_select<F>, n_sms, 0);
     for (int tau = 0; tau < max_plan_len; ++tau) {
-        k_find<F><<<grid_find, kThreads, 0, st>>>(a, tau);
-        k_select<F><<<grid_sel, kThreads, 0, st>>>(a, tau);
+        launch_find<F>(find_shape, st, a, tau, n_sms);
+        launch_select<F>(select_shape, st, a, tau, n_sms);
         if (sizeof(F) == 4 && a.P.kappa_fp64 > 0.0f) k_rescue<<<n_sms, kThreads, 0, st>>>(a, tau);
     }
     k_finish<F><<<(n * kGroup + kThreads - 1) / kThreads, kThreads, 0, st>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t enqueue_rounds(cudaStream_t st, const BuildArgs& a, int n, int max_plan_len, int n_sms, int find_shape,
+                           int select_shape) {
+    // MKGB_FP64: the plain all-FP64 comparison path (same rounds, every Kalman step in FP64)
+    return a.P.precision == MKGB_FP64
+               ? launch_rounds<double>(st, a, n, max_plan_len, n_sms, find_shape, select_shape)
+               : launch_rounds<float>(st, a, n, max_plan_len, n_sms, find_shape, select_shape);
+}
+
+bool capturable(cudaStream_t st) {
+    if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return false;
+    return cs == cudaStreamCaptureStatusNone;   // inside a caller's capture: plain launches join it
 }
 
 }  // namespace
@@ -668,15 +735,73 @@ BuildWork carve_build_work(void* base, int n_seeds, int max_plan_len, int precis
     return w;
 }
 
+// The search of one call as a CUDA graph: the ~70 launches of the rounds (counters reset, k_start,
+// per plan step k_find, k_select and k_rescue, k_finish) are captured once and replayed while the
+// arguments, the launch shapes and the stream stay the same.
+struct BuildGraph {
+    cudaGraphExec_t exec = nullptr;
+    BuildArgs key;
+    int n = -1, max_plan = -1, find_shape = -1, select_shape = -1;
+    cudaStream_t st = nullptr;
+    bool disabled = false;
+};
+
+BuildGraph* build_graph_create() { return new BuildGraph(); }
+
+void build_graph_destroy(BuildGraph* gph) {
+    if (!gph) return;
+    if (gph->exec) cudaGraphExecDestroy(gph->exec);
+    delete gph;
+}
+
 cudaError_t launch_build(cudaStream_t st, const DevGeom* g, int max_plan_len, DevParams P, HitStore H, SeedStore S,
-                         BuildOutDev out, BuildWork w, unsigned long long* counters, int n_sms) {
+                         BuildOutDev out, BuildWork w, unsigned long long* counters, int n_sms, int find_shape,
+                         int select_shape, BuildGraph* gph) {
     if (S.n == 0) return cudaSuccess;
-    BuildArgs a{g, P, H, S, out, w, counters, max_plan_len};
-    cudaError_t e = cudaMemsetAsync(w.counts, 0, 32, st);
-    if (e != cudaSuccess) return e;
-    // MKGB_FP64: the plain all-FP64 comparison path (same rounds, every Kalman step in FP64)
-    return P.precision == MKGB_FP64 ? launch_rounds<double>(st, a, S.n, max_plan_len, n_sms)
-                                    : launch_rounds<float>(st, a, S.n, max_plan_len, n_sms);
+    BuildArgs a;
+    memset(&a, 0, sizeof(a));   // padding included: the graph cache compares arguments bytewise
+    a.geom = g; a.P = P; a.H = H; a.S = S; a.out = out; a.w = w; a.counters = counters; a.max_steps = max_plan_len;
+    if (a.P.precision == MKGB_FP64)
+        prime_shapes<double>(n_sms);
+    else
+        prime_shapes<float>(n_sms);
+    if (!gph || gph->disabled || !capturable(st))
+        return enqueue_rounds(st, a, S.n, max_plan_len, n_sms, find_shape, select_shape);
+    const bool same = gph->exec && gph->st == st && gph->n == S.n && gph->max_plan == max_plan_len &&
+                      gph->find_shape == find_shape && gph->select_shape == select_shape &&
+                      memcmp(&gph->key, &a, sizeof(a)) == 0;
+    if (!same) {
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            gph->disabled = true;
+            return enqueue_rounds(st, a, S.n, max_plan_len, n_sms, find_shape, select_shape);
+        }
+        const cudaError_t le = enqueue_rounds(st, a, S.n, max_plan_len, n_sms, find_shape, select_shape);
+        e = cudaStreamEndCapture(st, &graph);
+        if (le != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return le;
+        }
+        if (e != cudaSuccess) return e;
+        if (gph->exec) {
+            cudaGraphExecDestroy(gph->exec);
+            gph->exec = nullptr;
+        }
+        e = cudaGraphInstantiate(&gph->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            gph->exec = nullptr;
+            return e;
+        }
+        gph->key = a;
+        gph->st = st;
+        gph->n = S.n;
+        gph->max_plan = max_plan_len;
+        gph->find_shape = find_shape;
+        gph->select_shape = select_shape;
+    }
+    return cudaGraphLaunch(gph->exec, st);
 }
 
 }  // namespace mk

@@ -43,7 +43,8 @@ class Tracks(C.Structure):
 
 EXPORTS = ["mkgb_create", "mkgb_destroy", "mkgb_last_error", "mkgb_version", "mkgb_load_geometry",
            "mkgb_set_params", "mkgb_load_hits", "mkgb_seed", "mkgb_build", "mkgb_fit", "mkgb_fit_static",
-           "mkgb_fit_grad", "mkgb_run", "mkgb_propagate", "mkgb_update", "mkgb_counters"]
+           "mkgb_fit_grad", "mkgb_run", "mkgb_set_launch", "mkgb_autotune", "mkgb_propagate", "mkgb_update",
+           "mkgb_counters"]
 
 _lib = None
 
@@ -78,6 +79,8 @@ def load_library(path: str = LIB_PATH):
     lib.mkgb_fit_grad.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32]
     lib.mkgb_run.argtypes = [vp, i32, vp, vp, vp, i32, vp, C.POINTER(Tracks), i32, i32, vp, vp, vp, vp, vp, vp, vp,
                              vp]
+    lib.mkgb_set_launch.argtypes = [vp, i32, i32, i32]
+    lib.mkgb_autotune.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(f32)]
     lib.mkgb_propagate.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, i32]
     lib.mkgb_update.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32]
     lib.mkgb_counters.argtypes = [vp, i32, vp]
@@ -261,6 +264,19 @@ class Context:
                 _ptr(status_out, np.int32, True)]
         self._check(self.lib.mkgb_fit_grad(self.h, int(n), int(m), *[p for p, _ in args],
                                            _same(*[d for _, d in args])), "mkgb_fit_grad")
+
+    def set_launch(self, find_shape: int = 0, select_shape: int = 0, use_graph: bool = True):
+        """mkgb_set_launch: block shapes of the search kernels and CUDA-graph replay."""
+        self._check(self.lib.mkgb_set_launch(self.h, int(find_shape), int(select_shape), int(bool(use_graph))),
+                    "mkgb_set_launch")
+
+    def autotune(self, reps: int = 3):
+        """mkgb_autotune over the loaded seeds: returns (find_shape, select_shape, ms per search)
+        and keeps the fastest shapes for later searches."""
+        f, s, ms = C.c_int(0), C.c_int(0), C.c_float(0.0)
+        self._check(self.lib.mkgb_autotune(self.h, int(reps), C.byref(f), C.byref(s), C.byref(ms)),
+                    "mkgb_autotune")
+        return f.value, s.value, ms.value
 
     def propagate(self, layers, p_in, c_in, p_out, c_out, crossed):
         args = [_ptr(layers, np.int32), _ptr(p_in, np.float32), _ptr(c_in, np.float32), _ptr(p_out, np.float32, True),
