@@ -308,6 +308,8 @@ def main():
     ap.add_argument("--no-grad", action="store_true", help="skip the fit-derivative measurement")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes of the search kernels")
     ap.add_argument("--no-graph", action="store_true", help="launch the search rounds one by one")
+    ap.add_argument("--shapes", default=None,
+                    help="fixed launch shapes 'find,select' of the search kernels (no autotuning)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -356,7 +358,10 @@ def main():
     fc = ctx.counters(1)
     kalman_steps = int(bc[0] + fc[0])
     shapes = (0, 0, None)
-    if not args.no_autotune:
+    if args.shapes:
+        f_s, s_s = (int(x) for x in args.shapes.split(","))
+        shapes = (f_s, s_s, None)
+    elif not args.no_autotune:
         shapes = ctx.autotune(reps=2)   # block shapes of the search kernels on this batch
     ctx.set_launch(shapes[0], shapes[1], use_graph=not args.no_graph)
     for _ in range(max(0, args.warmup - 1)):

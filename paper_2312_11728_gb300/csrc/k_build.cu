@@ -69,6 +69,14 @@ template <class F, int N> __device__ __forceinline__ void store_words(unsigned c
     for (int i = 0; i < N / per; ++i) v[i] = pack16(f + per * i);
 }
 
+// Asynchronous 16-byte copy global -> shared (cached in L2 only), its commit and wait.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 template <class F> constexpr size_t state_bytes() { return 32 * sizeof(F); }
 template <class F> constexpr size_t pred_bytes() { return 24 * sizeof(F); }
 
@@ -211,6 +219,7 @@ __global__ void __launch_bounds__(kThreads) k_start(BuildArgs a) {
 }
 
 // ---- a4-a9 for every live candidate of round tau
+
 template <class F, int TH, int MINB>
 __global__ void __launch_bounds__(TH, MINB) k_find(BuildArgs a, int tau) {
     __shared__ DevGeom g;
@@ -233,21 +242,71 @@ __global__ void __launch_bounds__(TH, MINB) k_find(BuildArgs a, int tau) {
     const int stride = gridDim.x * blockDim.x;
     // every lane of a warp runs the same number of iterations (warp_append inside k_select
     // needs converged warps; here it keeps the loop uniform)
+    const int lane = threadIdx.x & 31;
+    // The next item's records (state, meta, seed info) are copied into this thread's column of
+    // s_rec while the current item is processed, so their load latency is hidden.  A column is
+    // read into registers before the next copy into it is issued (the copy's shared-memory write
+    // follows its global read, after these reads).  FP32 records and blocks of up to 128 threads
+    // only (static shared memory); the FP64 comparison path loads directly.
+    constexpr bool kPf = sizeof(F) == 4 && TH <= 128;
+    constexpr int kSW = kPf ? (int)(state_bytes<F>() / 16) : 1;   // 16-byte words of a state record
+    __shared__ int4 s_rec[kSW + 2][kPf ? TH : 1];
+    auto fetch = [&](int slot) {
+        const int4* src = reinterpret_cast<const int4*>(a.w.st[cur] + (int64_t)slot * state_bytes<F>());
+#pragma unroll
+        for (int j = 0; j < kSW; ++j) cp_async16(&s_rec[j][tx], src + j);
+        cp_async16(&s_rec[kSW][tx], a.w.meta[cur] + slot);
+        cp_async16(&s_rec[kSW + 1][tx], a.w.sinfo + slot / kGroup);
+    };
+    int sl_cur = -1, sl_next = -1;
+    {
+        const int first = blockIdx.x * blockDim.x + (threadIdx.x & ~31) + lane;
+        sl_cur = first < n ? list[first] : -1;
+        if constexpr (kPf) {
+            if (sl_cur >= 0) fetch(sl_cur);
+            cp_async_commit();
+        }
+        if (first + stride < n) sl_next = list[first + stride];
+    }
     for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
-        const int idx = base + (threadIdx.x & 31);
+        const int idx = base + lane;
+        const int sl = sl_cur;
+        int4 si = make_int4(0, 0, 0, 0), mt = make_int4(0, 0, 0, 0);
+        StateT<F> t;
+        if constexpr (kPf) {
+            cp_async_wait_all();
+            if (sl >= 0) {
+                si = s_rec[kSW + 1][tx];
+                mt = s_rec[kSW][tx];
+                F f[32];
+#pragma unroll
+                for (int j = 0; j < kSW; ++j)
+                    unpack16(*reinterpret_cast<const typename Vec16<F>::T*>(&s_rec[j][tx]), f + j * (16 / sizeof(F)));
+                t.xh = f[0]; t.yh = f[1]; t.zh = f[2]; t.xl = f[3]; t.yl = f[4]; t.zl = f[5];
+                t.k = f[6]; t.phi = f[7]; t.th = f[8];
+#pragma unroll
+                for (int q = 0; q < 21; ++q) t.c[q] = f[9 + q];
+            }
+            asm volatile("" ::: "memory");
+            sl_cur = sl_next;
+            if (sl_cur >= 0) fetch(sl_cur);
+            cp_async_commit();
+        } else {
+            if (sl >= 0) {
+                si = a.w.sinfo[sl / kGroup];
+                mt = a.w.meta[cur][sl];
+                load_state_rec(a.w.st[cur] + (int64_t)sl * state_bytes<F>(), t);
+            }
+            sl_cur = sl_next;
+        }
+        sl_next = idx + 2 * stride < n ? list[idx + 2 * stride] : -1;
         if (idx >= n) continue;
-        const int sl = list[idx];
-        const int i = sl / kGroup;
-        const int4 si = a.w.sinfo[i];
         const int layer = g.plan[si.x + tau];
         const DevLayer& L = g.layers[layer];
-        const int4 mt = a.w.meta[cur][sl];
         if (mt.w == 0) {   // dropped after the selection (its FP64 update redo failed)
             a.w.ls[(int64_t)sl * 5] = make_int4(0, K_NONE, 0, 0);
             continue;
         }
-        StateT<F> t;
-        load_state_rec(a.w.st[cur] + (int64_t)sl * state_bytes<F>(), t);
         const float score = __int_as_float(mt.x);
         const int nholes = (mt.z >> 8) & 0xff;
 

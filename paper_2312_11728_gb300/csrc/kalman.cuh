@@ -415,24 +415,33 @@ __device__ __forceinline__ int propagate_core(const DevLayer& L, float cBf, int 
     if (L.kind == MKGB_BARREL) {
         const F c0 = r2_gap(Rl, t.xh, t.xl, t.yh, t.yl);   // R^2 - |u|^2
         if (!(c0 > F(0))) return 0;
-        const F b = ux * cf + uy * sf;
-        const F sq = sqrt(b * b + c0);
-        const F s0 = (b > F(0)) ? c0 / (b + sq) : sq - b;
         F lo = F(0), hi = F(3.0e38);
-        if (fabs(om) > F(1e-12)) {
-            const F inv = F(1) / om;
-            const F cx = ux - sf * inv, cy = uy + cf * inv;
-            const F rho = fabs(inv);
-            const F reach = sqrt(cx * cx + cy * cy) + rho - Rl;
-            if (reach < F(0)) return 0;
-            const F sg = om > F(0) ? F(1) : F(-1);
-            F turn = (atan2(sg * cx, -sg * cy) - t.phi) * sg;
-            turn -= P::two_pi * floor(turn * (F(1) / P::two_pi));
-            hi = turn * rho;
+        // refinement of a crossing solved in a lower precision (s_guess within ~1e-6 of the
+        // root, reach and turn checked there): the root lies inside (0, 2 s_guess), and Newton
+        // from s_guess stops once its step is below 1e-5 of s (the error after that step is of
+        // order the step squared, ~1e-12 of s)
+        const bool refine = s_guess && *s_guess > F(0);
+        if (refine) {
+            s = *s_guess;
+            hi = F(2) * s;
+        } else {
+            const F b = ux * cf + uy * sf;
+            const F sq = sqrt(b * b + c0);
+            const F s0 = (b > F(0)) ? c0 / (b + sq) : sq - b;
+            if (fabs(om) > F(1e-12)) {
+                const F inv = F(1) / om;
+                const F cx = ux - sf * inv, cy = uy + cf * inv;
+                const F rho = fabs(inv);
+                const F reach = sqrt(cx * cx + cy * cy) + rho - Rl;
+                if (reach < F(0)) return 0;
+                const F sg = om > F(0) ? F(1) : F(-1);
+                F turn = (atan2(sg * cx, -sg * cy) - t.phi) * sg;
+                turn -= P::two_pi * floor(turn * (F(1) / P::two_pi));
+                hi = turn * rho;
+            }
+            s = (s0 > lo && s0 < hi) ? s0 : F(0.5) * (lo + hi);
         }
-        s = (s0 > lo && s0 < hi) ? s0 : F(0.5) * (lo + hi);
-        if (s_guess && *s_guess > lo && *s_guess < hi) s = *s_guess;
-        const F tol = is_fp32<F>() ? F(1e-6) : F(1e-13);
+        const F tol = is_fp32<F>() ? F(1e-6) : refine ? F(1e-5) : F(1e-13);
         for (int it = 0; it < 60; ++it) {
             ++newton_it;
             const F a = om * s;
@@ -730,7 +739,11 @@ __device__ __forceinline__ bool chi2_hit(int kind, const PredT<F>& q, F mx, F my
 // Returns false if S is not positive definite or theta leaves (0, pi).
 // kappa (optional) gets (max L_ii / min L_ii)^2 of the Cholesky factor of S, an estimate of its
 // condition number.
-template <class F>
+// JOSEPH = false takes the equal (in exact arithmetic) short form C+ = (I - K H) C, lower
+// triangle only: 30 instead of ~170 multiply-adds.  For FP64 steps only, where rounding of the
+// short form (relative error ~ kappa(S) x 1e-16) stays far below the tolerances; FP32 steps keep
+// the Joseph form, whose result stays symmetric positive definite under rounding.
+template <class F, bool JOSEPH = true>
 __device__ __forceinline__ bool kalman_update_f(const FrameT<F>& f, const PredT<F>& q, F mx, F my, F mz,
                                                 const F v[6], StateT<F>& out, float* kappa = nullptr,
                                                 const F* dm = nullptr) {
@@ -757,28 +770,37 @@ __device__ __forceinline__ bool kalman_update_f(const FrameT<F>& f, const PredT<
     F dp[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) dp[i] = fma(K[i][0], rl[0], fma(K[i][1], rl[1], K[i][2] * rl[2]));
-    // T = (I - K H) C : row i minus K_i1 * row u1 minus K_i2 * row u2
-    F T[5][5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i)
-#pragma unroll
-        for (int j = 0; j < 5; ++j) T[i][j] = fma(-K[i][1], q.c[ix(0, j)], fma(-K[i][2], q.c[ix(1, j)], q.c[ix(i, j)]));
-    const F V[3][3] = {{vl[0], vl[1], vl[3]}, {vl[1], vl[2], vl[4]}, {vl[3], vl[4], vl[5]}};
-    F KV[5][3];
-#pragma unroll
-    for (int i = 0; i < 5; ++i)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) KV[i][a] = fma(K[i][0], V[0][a], fma(K[i][1], V[1][a], K[i][2] * V[2][a]));
     F cn[15];
+    if constexpr (JOSEPH) {
+        // T = (I - K H) C : row i minus K_i1 * row u1 minus K_i2 * row u2
+        F T[5][5];
 #pragma unroll
-    for (int i = 0; i < 5; ++i)
+        for (int i = 0; i < 5; ++i)
 #pragma unroll
-        for (int j = 0; j <= i; ++j) {
-            F acc = fma(-T[i][0], K[j][1], fma(-T[i][1], K[j][2], T[i][j]));
+            for (int j = 0; j < 5; ++j)
+                T[i][j] = fma(-K[i][1], q.c[ix(0, j)], fma(-K[i][2], q.c[ix(1, j)], q.c[ix(i, j)]));
+        const F V[3][3] = {{vl[0], vl[1], vl[3]}, {vl[1], vl[2], vl[4]}, {vl[3], vl[4], vl[5]}};
+        F KV[5][3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) acc = fma(KV[i][a], K[j][a], acc);
-            cn[ix(i, j)] = acc;
-        }
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) KV[i][a] = fma(K[i][0], V[0][a], fma(K[i][1], V[1][a], K[i][2] * V[2][a]));
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j) {
+                F acc = fma(-T[i][0], K[j][1], fma(-T[i][1], K[j][2], T[i][j]));
+#pragma unroll
+                for (int a = 0; a < 3; ++a) acc = fma(KV[i][a], K[j][a], acc);
+                cn[ix(i, j)] = acc;
+            }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int j = 0; j <= i; ++j)
+                cn[ix(i, j)] = fma(-K[i][1], q.c[ix(0, j)], fma(-K[i][2], q.c[ix(1, j)], q.c[ix(i, j)]));
+    }
     F dg[3];
     surface_to_global(f, dp[0], dp[1], dg);
     out.xh = q.xh; out.xl = q.xl; out.yh = q.yh; out.yl = q.yl; out.zh = q.zh; out.zl = q.zl;

@@ -63,8 +63,9 @@ __device__ __forceinline__ bool seed_prior(const DevGeom& g, const HitStore& H, 
 
 // Seed fit of seed i in precision F: update with hit 1, then propagate to and update with hits
 // 2 and 3.  FAST (FP64 fits of the FP32 path): the first update in closed form (zero residual,
-// diagonal prior), FP32 crossings refined in FP64 (propagate_refined) and the update's frame from
-// the propagation's direction; the plain all-FP64 path takes the general steps.  Returns ok.
+// diagonal prior), FP32 crossings refined in FP64 (propagate_refined), the update's frame from
+// the propagation's direction and the short covariance update (I - K H) C; the plain all-FP64
+// path takes the general steps.  Returns ok.
 template <class F, bool FAST = false>
 __device__ __forceinline__ bool seed_fit(const DevGeom& g, const DevParams& P, const HitStore& H,
                                          const int* __restrict__ seed_hits, int i, StateT<F>& t, int lay[3],
@@ -84,8 +85,8 @@ __device__ __forceinline__ bool seed_fit(const DevGeom& g, const DevParams& P, c
         F dir[4];
         ok = ok && propagate_refined(L, g.cB, P.material, t, q, newton, fast, dir) == 1;
         if constexpr (fast)
-            ok = ok && kalman_update_f(frame_of(L.kind, q.xh, q.yh, dir[0], dir[1], dir[2], dir[3]), q, m[j][0],
-                                       m[j][1], m[j][2], v[j], t);
+            ok = ok && kalman_update_f<F, false>(frame_of(L.kind, q.xh, q.yh, dir[0], dir[1], dir[2], dir[3]), q,
+                                                 m[j][0], m[j][1], m[j][2], v[j], t);
         else
             ok = ok && kalman_update(L.kind, q, m[j][0], m[j][1], m[j][2], v[j], t);
     }
