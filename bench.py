@@ -39,7 +39,7 @@ WORKLOAD = "phase2_like_{events}ev_20k_tracks_50k_noise_bestN6"
 #         update (a10-a11);
 #   fit: per track-layer step of k_fit (a4-a9, a11 on one hit).
 # Multi-function-unit work (sqrt, rsqrt, division seeds, sincos, log, atan2) is not counted.
-FLOPS = dict(find=1203.0, update=706.1, fit=1613.2)
+FLOPS = dict(find=1206.9, update=716.1, fit=1613.2, seed_fp64=3078.0)
 # the search and fit kernel sources the counts (and the DRAM traffic in profiles/) belong to
 KERNEL_SOURCES = ("paper_2312_11728_gb300/csrc/k_build.cu", "paper_2312_11728_gb300/csrc/kalman.cuh",
                   "paper_2312_11728_gb300/csrc/trig.cuh", "paper_2312_11728_gb300/csrc/dual.cuh",
@@ -154,6 +154,36 @@ def cpu_baseline(g, batch, fit, params, n_events_sample=2):
     return {"value": steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{n_events_sample} of {batch.n_events} events: {len(sel)} seeds built + {len(tsel)} tracks "
                       f"fitted ({steps} Kalman steps, {dt:.1f} s, FP64, single thread)"}
+
+
+def _oracle_event(args):
+    """One event through the oracle (search of all its seeds, fit of all its tracks) in a worker
+    process; returns (Kalman steps, seconds of compute)."""
+    g, ev, params, seed = args
+    import oracle
+    from oracle import parity as PR
+    from paper_2312_11728_gb300 import pipeline, synth as S
+    b = S.concat_events([ev], g.n_layers)
+    fi = pipeline.fit_inputs(b, seed=seed)
+    orc = oracle.Oracle(g, params)
+    t0 = time.perf_counter()
+    o = PR.oracle_build(orc, b)
+    r = orc.fit_batch(fi.layers, fi.hits, b.hit_xyz.astype(np.float64), b.hit_cov.astype(np.float64),
+                      fi.p0.astype(np.float64), fi.c0.astype(np.float64))
+    return int(o["counters"][0] + r["counters"][0]), time.perf_counter() - t0
+
+
+def cpu_baseline_all_cores(g, evs, params):
+    """The same oracle on every host core at once: one event per worker process (spawned), the
+    throughput = all workers' steps / the slowest worker's compute time."""
+    n = max(1, min(os.cpu_count() or 1, len(evs), 64))
+    with mp.get_context("spawn").Pool(n) as pool:
+        res = pool.map(_oracle_event, [(g, evs[e], params, e) for e in range(n)])
+    steps = sum(r[0] for r in res)
+    dt = max(r[1] for r in res)
+    return {"value": steps / dt, "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": f"{n} of {len(evs)} events, one per process: every seed built and every track fitted "
+                      f"({steps} Kalman steps, slowest worker {dt:.1f} s, FP64)"}
 
 
 def run_reference(args, rank):
@@ -279,18 +309,22 @@ def measure_fit_grad(args, local, rank, dist, stream):
     outs = dict(chi2=torch.zeros(n, device=f"cuda:{local}"), dp0=torch.zeros((n, 6), device=f"cuda:{local}"),
                 dal=torch.zeros((L, 6), device=f"cuda:{local}"), dxs=torch.zeros(L, device=f"cuda:{local}"),
                 status=torch.zeros(n, dtype=torch.int32, device=f"cuda:{local}"))
-    call = lambda: ctx.fit_grad(ins["layers"], ins["hits"], ins["p0"], ins["c0"], ins["align"], ins["xscale"],
-                                outs["chi2"], outs["dp0"], outs["dal"], outs["dxs"], outs["status"])
-    call()
-    torch.cuda.synchronize()
+    call = lambda mode: ctx.fit_grad(ins["layers"], ins["hits"], ins["p0"], ins["c0"], ins["align"], ins["xscale"],
+                                     outs["chi2"], outs["dp0"], outs["dal"], outs["dxs"], outs["status"], mode=mode)
     steps = int((fi.layers >= 0).sum())
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    call()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    value, wall, _ = pipeline.replica_throughput(e0.elapsed_time(e1) / 1e3, steps, dist, f"cuda:{local}")
-    return {"value": value, "unit": "fit track-layer steps/s with derivatives", "ms": wall * 1e3, "tracks": n,
+    ms = {}
+    for mode in (1, 0):   # forward mode, then the reverse sweep (the default)
+        call(mode)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        call(mode)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms[mode] = e0.elapsed_time(e1)
+    value, wall, _ = pipeline.replica_throughput(ms[0] / 1e3, steps, dist, f"cuda:{local}")
+    return {"value": value, "unit": "fit track-layer steps/s with derivatives", "ms": wall * 1e3,
+            "mode": "reverse sweep over checkpointed steps", "forward_mode_ms": ms[1], "tracks": n,
             "layers": int(np.unique(fi.layers[fi.layers >= 0]).size), "derivatives_per_track": "6 starting parameters + 7 per crossed layer",
             "workload": "100k tracks, 22 layers, misaligned detector (50 um, 0.1 mrad), material x[0.8, 1.2]"}
 
@@ -352,6 +386,8 @@ def main():
 
     # warm-up with the separate calls (their counters give the work of one pass), then with the
     # one-call pass that the timed steps use
+    if args.shapes:   # fixed shapes from the first pass on (profiling runs)
+        ctx.set_launch(*(int(x) for x in args.shapes.split(",")), use_graph=not args.no_graph)
     step()
     torch.cuda.synchronize()
     bc = ctx.counters(0)
@@ -420,6 +456,7 @@ def main():
             dist.destroy_process_group()
         return
 
+    probe = {"fp32_tflops": ctx.probe_peak(0), "fp64_tflops": ctx.probe_peak(1)}
     hbm, sm_max, src = peaks()
     n_sms = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_peak = n_sms * 128 * 2 * sm_max * 1e6 / 1e12        # TFLOP/s at the maximum SM clock
@@ -457,18 +494,29 @@ def main():
                      "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                      "peak_note": f"FP32: {n_sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz ({src} max clock)",
+                     "probe_tflops": probe["fp32_tflops"],
+                     "frac_of_probe": achieved / probe["fp32_tflops"],
                      "flops_per_launch": int(build_flops(bc)),
                      "launch": "one mkgb_build call per step (its rounds replayed as one CUDA graph), "
                                "timed with CUDA events on its stream"},
+        # the FP64 seed fit against the measured FP64 multiply-add rate of the same device
+        "seed_fp64_roofline": {"bound": "fp64", "achieved": FLOPS["seed_fp64"] * n_seeds / (stage["seed"] * 1e9),
+                               "peak_probe": probe["fp64_tflops"], "unit": "TFLOP/s",
+                               "frac": FLOPS["seed_fp64"] * n_seeds / (stage["seed"] * 1e9) / probe["fp64_tflops"],
+                               "flops_per_seed": FLOPS["seed_fp64"]},
         "e2e": e2e,
         "fp64_plain": fp64,
         "fit_grad": grad,
         "gpu_launches": int(launches_per_step * args.steps),
         "clocks": clocks,
         "counters": {"build": [int(x) for x in bc], "fit": [int(x) for x in fc]},
+        # rank 0's timed passes counted in chi2 evaluations and Kalman updates (search + fit)
+        "rates_per_gpu": {"chi2_per_s": (int(bc[1]) + int(fc[1])) * args.steps / wall,
+                          "updates_per_s": (int(bc[2]) + int(fc[2])) * args.steps / wall},
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, batch, fit, params)
+        line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(g, evs, params)
     print(json.dumps(line, default=lambda o: o.item() if hasattr(o, "item") else str(o)), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -196,14 +196,21 @@ int mkgb_autotune(mkgb_ctx* ctx, int reps, int* find_shape, int* select_shape, f
  * (layers, hits, p0, c0: n tracks x max_steps), plus align (n_layers x 6) and xscale (n_layers).
  * Outputs: chi2_out (n: the track's summed predicted chi2 at these parameters, 0 if it failed),
  * d_p0 (n x 6: d chi2_i / d p0_i), d_align (n_layers x 6) and d_xscale (n_layers): derivatives
- * of the total chi2 over the tracks with status 0; status_out (n, optional) as mkgb_fit.  The
- * derivatives are exact for the FP32 arithmetic of the fit (forward-mode dual numbers; no FP64
- * refit).  Errors: MKGB_ESTATE without geometry, params or hits; MKGB_EINVAL on NULL arrays or a
- * hit index beyond the loaded hits (host arrays). */
+ * of the total chi2 over the tracks with status 0; status_out (n, optional) as mkgb_fit, plus
+ * 5 = a step redone by the reverse sweep failed where the plain pass passed it (a rounding
+ * difference at a layer edge; the track is left out).  The derivatives are exact for the FP32
+ * arithmetic of the fit (dual numbers; no FP64 refit).
+ * mode 0: reverse sweep (one plain pass storing each step's input state, then the steps from
+ * the last to the first, each redone with its 34 inputs seeded, contracting the adjoint of its
+ * output; device scratch of 128 bytes per track and step, kept by the context).  mode 1: forward
+ * mode over all 6 + 7 L parameters of a track (no scratch, ~4x the arithmetic at 22 layers).
+ * Errors: MKGB_ESTATE without geometry, params or hits; MKGB_EINVAL on a mode other than 0 or 1,
+ * NULL arrays or a hit index beyond the loaded hits (host arrays); MKGB_ENOMEM if the scratch
+ * cannot be allocated. */
 int mkgb_fit_grad(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const int32_t* hits,
                   const float* p0, const float* c0, const float* align, const float* xscale,
                   float* chi2_out, float* d_p0, float* d_align, float* d_xscale, int32_t* status_out,
-                  int on_device);
+                  int mode, int on_device);
 
 /* Kalman fit over a known assignment that allocates nothing.  The paper has no counterpart:
  * this is a library service, not a step of the method.  Same arguments, outputs and
@@ -231,6 +238,15 @@ int mkgb_fit_grad(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, co
 int mkgb_fit_static(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const int32_t* hits,
                     const float* p0, const float* c0, float* p_out, float* c_out, float* chi2_out,
                     int32_t* status_out);
+
+/* Arithmetic-throughput probe (library service, no counterpart in the paper): the fused
+ * multiply-add rate of this device, kind 0 = FP32, kind 1 = FP64, in TFLOP/s (2 flops per
+ * multiply-add) written to tflops_out.  One resident grid of independent multiply-add chains,
+ * timed with CUDA events on the context's stream after a sizing launch (~20 ms timed); it is the
+ * measured denominator beside the nominal one in the rooflines of the FP32 search and the FP64
+ * seed fit.  Synchronises the stream.  Errors: MKGB_EINVAL for another kind or a NULL output,
+ * MKGB_ECUDA if a launch fails. */
+int mkgb_probe_peak(mkgb_ctx* ctx, int kind, double* tflops_out);
 
 /* Single propagation step (Sec. 3.1 propagation; a4-a7): n states to the given layers.
  * crossed_out: 1 crossed, 0 not crossed (state copied through), -1 stopped. */

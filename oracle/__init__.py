@@ -83,6 +83,8 @@ def lib():
             d, i = C.POINTER(C.c_double), C.POINTER(C.c_int)
             _lib.orc_path.restype = C.c_int
             _lib.orc_propagate.restype = C.c_int
+            _lib.orc_path_inward.restype = C.c_int
+            _lib.orc_propagate_backward.restype = C.c_int
             _lib.orc_chi2.restype = C.c_int
             _lib.orc_update.restype = C.c_int
             _lib.orc_seed.restype = C.c_int
@@ -145,6 +147,30 @@ class Oracle:
         m = C.c_double(0.0)
         ok = self.lib.orc_path(self.gp, int(layer), _p(np.ascontiguousarray(p, np.float64)), C.byref(s), C.byref(m))
         return bool(ok), s.value, m.value
+
+    def path_inward(self, layer, p):
+        """Inward crossing of a state moving inward (the reversed state of the backward fit)."""
+        s = C.c_double(0.0)
+        m = C.c_double(0.0)
+        ok = self.lib.orc_path_inward(self.gp, int(layer), _p(np.ascontiguousarray(p, np.float64)), C.byref(s),
+                                      C.byref(m))
+        return bool(ok), s.value, m.value
+
+    def reverse(self, p, c21):
+        """The same trajectory traversed in the opposite direction (backward fit, Sec. 2.2)."""
+        pr, cr = np.zeros(6), np.zeros(21)
+        self.lib.orc_reverse(_p(np.ascontiguousarray(p, np.float64)), _p(np.ascontiguousarray(c21, np.float64)),
+                             _p(pr), _p(cr))
+        return pr, cr
+
+    def propagate_backward(self, layer, p, c21, material=None):
+        """Backward-fit propagation step to an inner layer (Sec. 2.2)."""
+        mat = self.params["material"] if material is None else int(material)
+        po, co, s = np.zeros(6), np.zeros(21), C.c_double(0.0)
+        r = self.lib.orc_propagate_backward(self.gp, int(layer), _p(np.ascontiguousarray(p, np.float64)),
+                                            _p(np.ascontiguousarray(c21, np.float64)), int(mat), _p(po), _p(co),
+                                            C.byref(s))
+        return r, po, co, s.value
 
     def jacobian(self, layer, p, s):
         J = np.zeros(36)
@@ -240,6 +266,25 @@ class Oracle:
         self.lib.orc_fit_batch(self.gp, int(mat), int(n), int(m), _p(la, C.c_int), _p(hi, C.c_int), _p(x), _p(cv),
                                _p(q0), _p(d0), _p(p), _p(c), _p(chi2), _p(nupd, C.c_int), _p(status, C.c_int),
                                _p(ctr, C.c_longlong))
+        return dict(p=p, c=c, chi2=chi2, nupd=nupd, status=status, counters=ctr)
+
+    def bkfit_batch(self, layers, hits, xyz, cov, p_start, c_start, cov_scale, material=None):
+        """Backward fit (Sec. 2.2) of tracks listed in forward order, from their state on the
+        last listed layer (covariance scaled by cov_scale) to the innermost listed layer."""
+        mat = self.params["material"] if material is None else int(material)
+        n, m = layers.shape
+        la = np.ascontiguousarray(layers, np.int32)
+        hi = np.ascontiguousarray(hits, np.int32)
+        x = np.ascontiguousarray(xyz, np.float64)
+        cv = np.ascontiguousarray(cov, np.float64)
+        q0 = np.ascontiguousarray(p_start, np.float64)
+        d0 = np.ascontiguousarray(c_start, np.float64)
+        p, c, chi2 = np.zeros((n, 6)), np.zeros((n, 21)), np.zeros(n)
+        nupd, status = np.zeros(n, np.int32), np.zeros(n, np.int32)
+        ctr = np.zeros(4, np.int64)
+        self.lib.orc_bkfit_batch(self.gp, int(mat), int(n), int(m), _p(la, C.c_int), _p(hi, C.c_int), _p(x),
+                                 _p(cv), _p(q0), _p(d0), C.c_double(cov_scale), _p(p), _p(c), _p(chi2),
+                                 _p(nupd, C.c_int), _p(status, C.c_int), _p(ctr, C.c_longlong))
         return dict(p=p, c=c, chi2=chi2, nupd=nupd, status=status, counters=ctr)
 
     def build_event(self, layer_off, xyz, cov, seed_hits, seed_layers, binned=True):

@@ -157,6 +157,85 @@ int orc_path(const orc_geom* g, int layer, const double p[6], double* s_out, dou
     return (v >= L->lo && v <= L->hi) ? 1 : 0;
 }
 
+/* Inward crossing of a state whose direction of motion points inward (the reversed state of
+ * the backward fit): smallest s > 0 at which the helix meets the layer surface while its
+ * transverse radius decreases, before the point of smallest radius of the current turn.
+ * Barrel: the start lies outside the cylinder and moves inward; g(s) = x'^2 + y'^2 - R^2
+ * decreases from g(0) > 0 over [0, s_near] (s_near = path to the point of smallest radius,
+ * where g < 0 if the helix reaches R); Newton on g from the straight-line root, kept inside
+ * the bracket by bisection.  Disk: s = (z_d - z) tan(theta) > 0, reached before s_near and
+ * moving inward in r.  Then the extent check.  edge_margin as in orc_path. */
+int orc_path_inward(const orc_geom* g, int layer, const double p[6], double* s_out, double* edge_margin) {
+    const orc_layer* L = &g->layers[layer];
+    double om = -C_LIGHT * g->bz * p[3];
+    double cf = cos(p[4]), sf = sin(p[4]);
+    double margin = INFINITY;
+    double s;
+    /* path to the point of smallest transverse radius (infinite for a straight line) */
+    double s_near = INFINITY, r_near = 0.0;
+    if (fabs(om) >= 1e-14) {
+        double rho = 1.0 / fabs(om);
+        double cx = p[0] - sf / om, cy = p[1] + cf / om, d = hypot(cx, cy);
+        double sg = om > 0 ? 1.0 : -1.0;
+        double psi_near = atan2(sg * cx / d, -sg * cy / d) + PI;
+        double turn = fmod((psi_near - p[4]) * sg, TWO_PI);
+        if (turn < 0) turn += TWO_PI;
+        s_near = turn * rho;
+        r_near = fabs(d - rho);
+    } else {
+        r_near = fabs(p[0] * sf - p[1] * cf);
+    }
+    if (L->kind == ORC_DISK) {
+        double ct = cos(p[5]), st = sin(p[5]);
+        if (fabs(ct) < 1e-15) { *edge_margin = margin; return 0; }
+        s = (L->pos - p[2]) * st / ct;
+        if (!(s > 0)) { *edge_margin = margin; return 0; }
+        if (isfinite(s_near)) {
+            double q[6];
+            orc_helix(g->bz, p, s, q);
+            double vr = (q[0] * cos(q[4]) + q[1] * sin(q[4])) / fmax(hypot(q[0], q[1]), 1e-300);
+            margin = fmin(fabs(s - s_near) / s_near, fabs(vr));
+            if (s > s_near || vr > 0) { *edge_margin = margin; return 0; }
+        }
+    } else {
+        double R = L->pos, x = p[0], y = p[1];
+        double b = x * cf + y * sf;
+        if (x * x + y * y <= R * R || !(b < 0)) { *edge_margin = margin; return 0; }
+        double reach = R - r_near;
+        margin = fabs(reach) / R;
+        if (reach < 0) { *edge_margin = margin; return 0; }
+        double c = x * sf - y * cf;
+        double s0 = -b - sqrt(fmax(R * R - c * c, 0.0));
+        if (!isfinite(s_near)) {
+            s = s0;
+        } else {
+            double lo = 0.0, hi = s_near;
+            s = (s0 > lo && s0 < hi) ? s0 : 0.5 * (lo + hi);
+            for (int it = 0; it < 300; ++it) {
+                double q[6];
+                orc_helix(g->bz, p, s, q);
+                double gv = q[0] * q[0] + q[1] * q[1] - R * R;
+                if (gv > 0) lo = s; else hi = s;
+                double dg = 2.0 * (q[0] * cos(q[4]) + q[1] * sin(q[4]));
+                double sn = dg < 0 ? s - gv / dg : 0.5 * (lo + hi);
+                if (!(sn > lo && sn < hi)) sn = 0.5 * (lo + hi);
+                double ds = sn - s;
+                s = sn;
+                if (fabs(ds) < 1e-12 * R || hi - lo < 1e-13 * R) break;
+            }
+        }
+    }
+    double q[6];
+    orc_helix(g->bz, p, s, q);
+    double v = (L->kind == ORC_BARREL) ? q[2] : hypot(q[0], q[1]);
+    double m_lo = fabs(v - L->lo) / fmax(fabs(L->lo), 1.0);
+    double m_hi = fabs(v - L->hi) / fmax(fabs(L->hi), 1.0);
+    margin = fmin(margin, fmin(m_lo, m_hi));
+    *edge_margin = margin;
+    *s_out = s;
+    return (v >= L->lo && v <= L->hi) ? 1 : 0;
+}
+
 /* d f(p, s) / d p at fixed s (rows and columns in state order x, y, z, k, phi, theta). */
 void orc_jacobian_fixed_s(double bz, const double p[6], double s, double A[36]) {
     double cB = C_LIGHT * bz;
@@ -289,6 +368,39 @@ int orc_propagate(const orc_geom* g, int layer, const double p[6], const double 
     orc_transport(J, C, Cout);
     if (material && !orc_material(&g->layers[layer], pout, Cout, +1.0)) return -1;
     pout[4] = wrap_phi(pout[4]);
+    *s_out = s;
+    return 1;
+}
+
+/* The same trajectory traversed in the opposite direction: position unchanged, direction
+ * reversed (phi + pi, pi - theta) and charge sign flipped (k -> -k) so that the reversed
+ * particle follows the same circle.  C -> D C D with D = diag(1, 1, 1, -1, 1, -1). */
+void orc_reverse(const double p[6], const double C[21], double pr[6], double Cr[21]) {
+    static const double d[6] = {1, 1, 1, -1, 1, -1};
+    pr[0] = p[0]; pr[1] = p[1]; pr[2] = p[2];
+    pr[3] = -p[3];
+    pr[4] = wrap_phi(p[4] + PI);
+    pr[5] = PI - p[5];
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j <= i; ++j) Cr[ix(i, j)] = d[i] * d[j] * C[ix(i, j)];
+}
+
+/* Propagation step of the backward fit (Sec. 2.2: the found track re-traversed inwards):
+ * reverse the state, cross the (inner) layer along the reversed helix (orc_path_inward), the
+ * new parameters and J C J^T as in orc_propagate, the material with the energy loss added back
+ * (direction -1; the Highland variance is added as always), then reverse back.
+ * 1 crossed, 0 not crossed, -1 stopped. */
+int orc_propagate_backward(const orc_geom* g, int layer, const double p[6], const double C[21],
+                           int material, double pout[6], double Cout[21], double* s_out) {
+    double pr[6], Cr[21], qr[6], Cq[21], s, em, J[36];
+    orc_reverse(p, C, pr, Cr);
+    if (!orc_path_inward(g, layer, pr, &s, &em)) return 0;
+    orc_jacobian(g, layer, pr, s, J);
+    orc_helix(g->bz, pr, s, qr);
+    orc_transport(J, Cr, Cq);
+    if (material && !orc_material(&g->layers[layer], qr, Cq, -1.0)) return -1;
+    qr[4] = wrap_phi(qr[4]);
+    orc_reverse(qr, Cq, pout, Cout);
     *s_out = s;
     return 1;
 }
@@ -551,6 +663,58 @@ void orc_fit_batch(const orc_geom* g, int material, int n, int max_steps, const 
             int h = hits[(long long)i * max_steps + j];
             if (h >= 0) {
                 double x2;
+                if (!orc_update(pp, Cp, &xyz[3 * (long long)h], &cov[6 * (long long)h], 1, q, Cq, &x2)) {
+                    st = 3;
+                    break;
+                }
+                sum += x2;
+                nu++;
+                counters[1]++;
+                counters[2]++;
+            }
+        }
+        memcpy(&p[6 * i], q, sizeof(q));
+        memcpy(&C[21 * i], Cq, sizeof(Cq));
+        chi2[i] = sum;
+        nupd[i] = nu;
+        status[i] = st;
+    }
+}
+
+/* Backward fit (Sec. 2.2): each track re-traversed from its outermost listed layer to its
+ * innermost.  layers/hits list the track's layers in the forward (outward) order as for
+ * orc_fit_batch; p_start/C_start is its state on the last listed layer (the forward fit's
+ * result there), whose covariance is scaled by cov_scale to release the forward fit's
+ * information.  The hit on the last layer is used first (update), then for each earlier
+ * listed layer: backward propagation and, with a hit, chi2 + update.  Outputs: the state at
+ * the innermost listed layer, the summed predicted chi2, the number of updates and the status
+ * (0 ok, 1 a listed layer not crossed, 2 stopped, 3 update failed). */
+void orc_bkfit_batch(const orc_geom* g, int material, int n, int max_steps, const int* layers,
+                     const int* hits, const double* xyz, const double* cov, const double* p_start,
+                     const double* C_start, double cov_scale, double* p, double* C, double* chi2,
+                     int* nupd, int* status, long long* counters) {
+    for (int i = 0; i < n; ++i) {
+        double q[6], Cq[21], pp[6], Cp[21], s;
+        memcpy(q, &p_start[6 * i], sizeof(q));
+        for (int k = 0; k < 21; ++k) Cq[k] = cov_scale * C_start[21 * i + k];
+        int nl = 0;
+        while (nl < max_steps && layers[(long long)i * max_steps + nl] >= 0) ++nl;
+        double sum = 0.0;
+        int nu = 0, st = 0;
+        for (int j = nl - 1; j >= 0; --j) {
+            int L = layers[(long long)i * max_steps + j];
+            if (j < nl - 1) {
+                int r = orc_propagate_backward(g, L, q, Cq, material, pp, Cp, &s);
+                if (r != 1) { st = (r == 0) ? 1 : 2; break; }
+                counters[0]++;
+                memcpy(q, pp, sizeof(q));
+                memcpy(Cq, Cp, sizeof(Cq));
+            }
+            int h = hits[(long long)i * max_steps + j];
+            if (h >= 0) {
+                double x2;
+                memcpy(pp, q, sizeof(q));
+                memcpy(Cp, Cq, sizeof(Cq));
                 if (!orc_update(pp, Cp, &xyz[3 * (long long)h], &cov[6 * (long long)h], 1, q, Cq, &x2)) {
                     st = 3;
                     break;

@@ -96,6 +96,10 @@ void orc_ms_theta0(double pmag, double t, double* theta0);
 double orc_eloss(double pmag, double t);
 int  orc_propagate(const orc_geom* g, int layer, const double p[6], const double C[21],
                    int material, double pout[6], double Cout[21], double* s_out);
+int  orc_path_inward(const orc_geom* g, int layer, const double p[6], double* s_out, double* edge_margin);
+void orc_reverse(const double p[6], const double C[21], double pr[6], double Cr[21]);
+int  orc_propagate_backward(const orc_geom* g, int layer, const double p[6], const double C[21],
+                            int material, double pout[6], double Cout[21], double* s_out);
 void orc_window(const orc_layer* L, const orc_params* P, const double p[6], const double C[21],
                 double out[4]);
 void orc_hit_eta_phi(const double m[3], double* eta, double* phi);
@@ -115,6 +119,10 @@ void orc_fit_batch(const orc_geom* g, int material, int n, int max_steps, const 
                    const int* hits, const double* xyz, const double* cov, const double* p0,
                    const double* C0, double* p, double* C, double* chi2, int* nupd,
                    int* status, long long* counters);
+void orc_bkfit_batch(const orc_geom* g, int material, int n, int max_steps, const int* layers,
+                     const int* hits, const double* xyz, const double* cov, const double* p_start,
+                     const double* C_start, double cov_scale, double* p, double* C, double* chi2,
+                     int* nupd, int* status, long long* counters);
 int  orc_build_event(const orc_geom* g, const orc_params* P, const orc_tie* T,
                      const long long* layer_off, const double* xyz, const double* cov,
                      int n_seeds, const int* seed_hits, const int* seed_layers,

@@ -77,7 +77,7 @@ struct mkgb_ctx {
     DevBuf seg_off, in_xyz, in_cov, pay, ep_tmp, bin_of_hit, hit_seg, bins, hb_ep, hb_pay, cursor, scan_tmp;
     int n_seeds = 0;
     DevBuf seed_hits, seed_state, seed_state64, seed_info, seed_key, key_counts, key_cursor, seed_order, seed_scan_tmp;
-    DevBuf counters_build, counters_fit, queue, rescue_list, rescue_count, build_work;
+    DevBuf counters_build, counters_fit, queue, rescue_list, rescue_count, build_work, probe_sink, grad_ck;
     DevBuf stage[S_COUNT];
     // launch shapes of the search rounds and the graph cache replaying them
     int find_shape = 0, select_shape = 0;
@@ -246,7 +246,7 @@ void mkgb_destroy(mkgb_ctx* ctx) {
                          &ctx->scan_tmp, &ctx->seed_hits, &ctx->seed_state, &ctx->seed_state64, &ctx->seed_info, &ctx->seed_key,
                          &ctx->key_counts, &ctx->key_cursor, &ctx->seed_order, &ctx->seed_scan_tmp,
                          &ctx->counters_build, &ctx->counters_fit, &ctx->queue, &ctx->rescue_list,
-                         &ctx->rescue_count, &ctx->build_work};
+                         &ctx->rescue_count, &ctx->build_work, &ctx->probe_sink, &ctx->grad_ck};
         for (DevBuf* b : all) release(*b);
         for (auto& b : ctx->stage) release(b);
         build_graph_destroy(ctx->graph);
@@ -557,8 +557,9 @@ int mkgb_fit(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const i
 
 int mkgb_fit_grad(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const int32_t* hits, const float* p0,
                   const float* c0, const float* align, const float* xscale, float* chi2_out, float* d_p0,
-                  float* d_align, float* d_xscale, int32_t* status_out, int on_device) {
+                  float* d_align, float* d_xscale, int32_t* status_out, int mode, int on_device) {
     if (!ctx) return MKGB_EINVAL;
+    if (mode != 0 && mode != 1) return fail(ctx, MKGB_EINVAL, "fit_grad mode %d (0 reverse sweep, 1 forward)", mode);
     if (!ctx->has_geom || !ctx->has_params) return fail(ctx, MKGB_ESTATE, "fit_grad before geometry/params");
     if (!ctx->has_hits) return fail(ctx, MKGB_ESTATE, "fit_grad before load_hits");
     if (n < 0 || max_steps < 0) return fail(ctx, MKGB_EINVAL, "negative size");
@@ -585,9 +586,15 @@ int mkgb_fit_grad(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, co
     CK(stage_out(ctx, S_K, status_out, 4 * N, on_device, &so));
     CK(cudaMemsetAsync(ga, 0, 24 * NL, st));   // summed over tracks by the kernel
     CK(cudaMemsetAsync(gx, 0, 4 * NL, st));
+    float* ck = nullptr;
+    if (mode == 0) {   // checkpoints of the reverse sweep: 128 bytes per track and step
+        CK(ensure(ctx->grad_ck, 128 * N * std::max<size_t>(M, 1)));
+        ck = (float*)ctx->grad_ck.p;
+    }
     CK(launch_fit_grad(st, (const DevGeom*)ctx->geom_d.p, ctx->params, (const float4*)ctx->pay.p, ctx->n_hits, n,
                        max_steps, (const int*)dl, (const int*)dh, (const float*)dp0, (const float*)dc0,
-                       (const float*)dal, (const float*)dxs, (float*)xo, (float*)gp, (float*)ga, (float*)gx, (int*)so));
+                       (const float*)dal, (const float*)dxs, (float*)xo, (float*)gp, (float*)ga, (float*)gx, (int*)so,
+                       ck));
     CK(copy_back(ctx, chi2_out, xo, 4 * N, on_device));
     CK(copy_back(ctx, d_p0, gp, 24 * N, on_device));
     CK(copy_back(ctx, d_align, ga, 24 * NL, on_device));
@@ -738,6 +745,42 @@ int mkgb_autotune(mkgb_ctx* ctx, int reps, int* find_shape, int* select_shape, f
     if (find_shape) *find_shape = best_f;
     if (select_shape) *select_shape = best_s;
     if (ms_out) *ms_out = best;
+    return MKGB_OK;
+}
+
+int mkgb_probe_peak(mkgb_ctx* ctx, int kind, double* tflops_out) {
+    if (!ctx) return MKGB_EINVAL;
+    if ((kind != 0 && kind != 1) || !tflops_out) return fail(ctx, MKGB_EINVAL, "probe kind %d or null output", kind);
+    DevGuard guard(ctx->device);
+    cudaStream_t st = ctx->stream;
+    CK(ensure(ctx->probe_sink, probe_sink_bytes(ctx->n_sms)));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(ctx, MKGB_ECUDA, "event creation failed");
+    }
+    // a short launch sizes the timed one to ~20 ms
+    int iters = kind == 0 ? 512 : 16;
+    double rate = 0.0;
+    cudaError_t e = cudaSuccess;
+    for (int pass = 0; pass < 3 && e == cudaSuccess; ++pass) {
+        int64_t fmas = 0;
+        float ms = 0.0f;
+        e = cudaEventRecord(e0, st);
+        if (e == cudaSuccess) e = launch_probe_fma(st, kind, ctx->n_sms, iters, ctx->probe_sink.p, &fmas);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess || ms <= 0.0f) break;
+        rate = 2.0 * (double)fmas / (ms * 1e-3) / 1e12;
+        const double scale = 20.0 / ms;
+        iters = (int)std::min(1e7, std::max(1.0, iters * scale));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail(ctx, MKGB_ECUDA, "probe: %s", cudaGetErrorString(e));
+    *tflops_out = rate;
     return MKGB_OK;
 }
 

@@ -94,10 +94,17 @@ cudaError_t launch_build(cudaStream_t st, const DevGeom* g, int max_plan_len, De
 
 // ---- k_fit.cu
 // ---- k_grad.cu
+// FMA-throughput probe (kind 0 FP32, 1 FP64): one resident grid of iters x 16 x 8 chained
+// multiply-adds per thread into sink (probe_sink_bytes); fma_count gets the multiply-adds issued.
+cudaError_t launch_probe_fma(cudaStream_t st, int kind, int n_sms, int iters, void* sink, int64_t* fma_count);
+size_t probe_sink_bytes(int n_sms);
+
+// Derivative of the fit's total chi2: reverse sweep when ck (n x max_steps x 32 floats of
+// checkpoints) is given, forward mode when it is nullptr.
 cudaError_t launch_fit_grad(cudaStream_t st, const DevGeom* g, DevParams P, const float4* pay, int64_t n_hits, int n,
                             int max_steps, const int* layers, const int* hits, const float* p0, const float* c0,
                             const float* align, const float* xscale, float* chi2_out, float* d_p0, float* d_align,
-                            float* d_xscale, int* status_out);
+                            float* d_xscale, int* status_out, float* ck);
 
 // Static scratch of mkgb_fit_static: [0, 64) work counters (kNumCounters x u64), [64, 80) the
 // FP64 refit counter, [256, 256 + 4 * kFitStaticMaxTracks) the refit list.  The counters and the

@@ -563,14 +563,27 @@ __global__ void __launch_bounds__(TH, MINB) k_select(BuildArgs a, int tau) {
             }
             a.w.trail[((int64_t)i * a.max_steps + tau) * kGroup + slot] = ((code + 4) << 3) | my_parent;
         }
-        if (gact) a.w.meta[nxt][csl] = pack_meta(my_score, chi2s, nfound, nholes, c_stopped, c_alive);
-        warp_append(rescue, csl, a.w.rescue, a.w.counts + 4);
         const bool more = gact && tau + 1 < si.z;
-        warp_append(more && c_alive && !c_stopped, csl, a.w.live[nxt], a.w.counts + nxt);
         const unsigned am = __ballot_sync(kFull, c_alive);
         const bool any = ((am >> gbase) & 0xffu) != 0u;
-        warp_append(more && any && slot == 0, i, a.w.seeds[nxt], a.w.counts + 2 + nxt);
+        const bool p_live = more && c_alive && !c_stopped, p_seed = more && any && slot == 0;
+        const unsigned m0 = __ballot_sync(kFull, rescue), m1 = __ballot_sync(kFull, p_live),
+                       m2 = __ballot_sync(kFull, p_seed);
+        int b0 = 0, b1 = 0, b2 = 0;
+        if (lane == 0) {   // the three list reservations of the warp, in flight together
+            if (m0) b0 = atomicAdd(a.w.counts + 4, __popc(m0));
+            if (m1) b1 = atomicAdd(a.w.counts + nxt, __popc(m1));
+            if (m2) b2 = atomicAdd(a.w.counts + 2 + nxt, __popc(m2));
+        }
+        if (gact) a.w.meta[nxt][csl] = pack_meta(my_score, chi2s, nfound, nholes, c_stopped, c_alive);
         if (gact && slot == 0 && (!more || !any)) a.w.fin[i] = nxt;
+        b0 = __shfl_sync(kFull, b0, 0);
+        b1 = __shfl_sync(kFull, b1, 0);
+        b2 = __shfl_sync(kFull, b2, 0);
+        const unsigned below = (1u << lane) - 1u;
+        if (rescue) a.w.rescue[b0 + __popc(m0 & below)] = csl;
+        if (p_live) a.w.live[nxt][b1 + __popc(m1 & below)] = csl;
+        if (p_seed) a.w.seeds[nxt][b2 + __popc(m2 & below)] = i;
     }
     add_counters(a.counters, 0ull, 0ull, c_upd, 0ull, 0ull);
 }

@@ -11,9 +11,9 @@ from . import mkgb
 class FitChi2(torch.autograd.Function):
     """total = FitChi2.apply(align [L,6], xscale [L], p0 [n,6], ctx, layers, hits, c0).
 
-    The forward call runs mkgb_fit_grad, which returns the derivatives with the value (forward
-    mode); backward scales them by the incoming gradient.  Tracks whose fit fails (status != 0)
-    add nothing."""
+    The forward call runs mkgb_fit_grad, which returns the derivatives with the value (its
+    reverse sweep over checkpointed steps); backward scales them by the incoming gradient.
+    Tracks whose fit fails (status != 0) add nothing."""
 
     @staticmethod
     def forward(fctx, align, xscale, p0, ctx: mkgb.Context, layers, hits, c0):

@@ -43,8 +43,8 @@ class Tracks(C.Structure):
 
 EXPORTS = ["mkgb_create", "mkgb_destroy", "mkgb_last_error", "mkgb_version", "mkgb_load_geometry",
            "mkgb_set_params", "mkgb_load_hits", "mkgb_seed", "mkgb_build", "mkgb_fit", "mkgb_fit_static",
-           "mkgb_fit_grad", "mkgb_run", "mkgb_set_launch", "mkgb_autotune", "mkgb_propagate", "mkgb_update",
-           "mkgb_counters"]
+           "mkgb_fit_grad", "mkgb_run", "mkgb_set_launch", "mkgb_autotune", "mkgb_probe_peak",
+           "mkgb_propagate", "mkgb_update", "mkgb_counters"]
 
 _lib = None
 
@@ -76,11 +76,12 @@ def load_library(path: str = LIB_PATH):
     lib.mkgb_build.argtypes = [vp, C.POINTER(Tracks), i32]
     lib.mkgb_fit.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32]
     lib.mkgb_fit_static.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
-    lib.mkgb_fit_grad.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32]
+    lib.mkgb_fit_grad.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32]
     lib.mkgb_run.argtypes = [vp, i32, vp, vp, vp, i32, vp, C.POINTER(Tracks), i32, i32, vp, vp, vp, vp, vp, vp, vp,
                              vp]
     lib.mkgb_set_launch.argtypes = [vp, i32, i32, i32]
     lib.mkgb_autotune.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(f32)]
+    lib.mkgb_probe_peak.argtypes = [vp, i32, C.POINTER(C.c_double)]
     lib.mkgb_propagate.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, i32]
     lib.mkgb_update.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32]
     lib.mkgb_counters.argtypes = [vp, i32, vp]
@@ -254,15 +255,16 @@ class Context:
             raise MkgbError("mkgb_fit_static takes CUDA tensors only")
         self._check(self.lib.mkgb_fit_static(self.h, int(n), int(m), *[p for p, _ in args]), "mkgb_fit_static")
 
-    def fit_grad(self, layers, hits, p0, c0, align, xscale, chi2_out, d_p0, d_align, d_xscale, status_out=None):
+    def fit_grad(self, layers, hits, p0, c0, align, xscale, chi2_out, d_p0, d_align, d_xscale, status_out=None,
+                 mode: int = 0):
         """mkgb_fit_grad: per-track chi2 at the given alignment / thickness scales and the
-        derivatives of the total chi2 (outputs written in place)."""
+        derivatives of the total chi2 (outputs written in place); mode 0 reverse sweep, 1 forward."""
         n, m = layers.shape
         args = [_ptr(layers, np.int32), _ptr(hits, np.int32), _ptr(p0, np.float32), _ptr(c0, np.float32),
                 _ptr(align, np.float32), _ptr(xscale, np.float32), _ptr(chi2_out, np.float32, True),
                 _ptr(d_p0, np.float32, True), _ptr(d_align, np.float32, True), _ptr(d_xscale, np.float32, True),
                 _ptr(status_out, np.int32, True)]
-        self._check(self.lib.mkgb_fit_grad(self.h, int(n), int(m), *[p for p, _ in args],
+        self._check(self.lib.mkgb_fit_grad(self.h, int(n), int(m), *[p for p, _ in args], int(mode),
                                            _same(*[d for _, d in args])), "mkgb_fit_grad")
 
     def set_launch(self, find_shape: int = 0, select_shape: int = 0, use_graph: bool = True):
@@ -277,6 +279,12 @@ class Context:
         self._check(self.lib.mkgb_autotune(self.h, int(reps), C.byref(f), C.byref(s), C.byref(ms)),
                     "mkgb_autotune")
         return f.value, s.value, ms.value
+
+    def probe_peak(self, kind: int = 0) -> float:
+        """mkgb_probe_peak: measured FMA throughput in TFLOP/s (kind 0 FP32, 1 FP64)."""
+        r = C.c_double(0.0)
+        self._check(self.lib.mkgb_probe_peak(self.h, int(kind), C.byref(r)), "mkgb_probe_peak")
+        return r.value
 
     def propagate(self, layers, p_in, c_in, p_out, c_out, crossed):
         args = [_ptr(layers, np.int32), _ptr(p_in, np.float32), _ptr(c_in, np.float32), _ptr(p_out, np.float32, True),

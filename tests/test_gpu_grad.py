@@ -1,6 +1,6 @@
-"""Derivative of the fit's total chi2 on the GPU (mkgb_fit_grad, FP32 forward-mode dual numbers)
-against the oracle's FP64 central differences (oracle/gradient.py) and against the symmetries of
-a barrel-only detector.
+"""Derivative of the fit's total chi2 on the GPU (mkgb_fit_grad, FP32 dual numbers: the reverse
+sweep over checkpointed steps and the forward mode) against the oracle's FP64 central differences
+(oracle/gradient.py), against each other and against the symmetries of a barrel-only detector.
 
 Tolerances, derived from the arithmetic: the derivative of a track's chi2 carries FP32 rounding
 (2^-24) amplified by the conditioning of its fit (condition numbers of S of 1e3-1e5 for typical
@@ -33,7 +33,7 @@ def _hit_layer(batch):
     return hl
 
 
-def _gpu_grad(g, batch, fi, align=None, xscale=None, params=None):
+def _gpu_grad(g, batch, fi, align=None, xscale=None, params=None, mode=0):
     params = params or S.default_params()
     ctx = pipeline.make_context(g, params)
     ctx.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov)
@@ -43,7 +43,7 @@ def _gpu_grad(g, batch, fi, align=None, xscale=None, params=None):
     out = dict(chi2=np.zeros(n, np.float32), dp0=np.zeros((n, 6), np.float32), dal=np.zeros((L, 6), np.float32),
                dxs=np.zeros(L, np.float32), status=np.zeros(n, np.int32))
     ctx.fit_grad(fi.layers, fi.hits, fi.p0, fi.c0, align, xscale, out["chi2"], out["dp0"], out["dal"], out["dxs"],
-                 out["status"])
+                 out["status"], mode=mode)
     return out
 
 
@@ -73,18 +73,19 @@ def test_fit_gradient_matches_oracle_differences(lib, aligned_small, at_truth):
     first order: the opposite shifts and rotations) with the true material."""
     g, batch, fi, al, xs = aligned_small
     align, xscale = (-al, xs) if at_truth else (None, None)
-    got = _gpu_grad(g, batch, fi, align, xscale)
     chi2, status, dp0, dal, dxs = OG.fd_gradient(g, S.default_params(), fi.layers, fi.hits, batch.hit_xyz,
                                                  batch.hit_cov, _hit_layer(batch), fi.p0, fi.c0, align, xscale)
-    assert np.array_equal(got["status"], status)
     ok = status == 0
     assert ok.mean() > 0.98
-    c_ok, _ = PR.chi2_close(got["chi2"][ok], chi2[ok])
-    assert c_ok.all()
     used = np.unique(fi.layers[fi.layers >= 0])
-    _check_layer_grads(got["dal"][used], dal[used], "align")
-    _check_layer_grads(got["dxs"][used], dxs[used], "xscale")
-    _check_track_grads(got["dp0"][ok], dp0[ok], "p0")
+    for mode in (0, 1):   # reverse sweep, forward mode
+        got = _gpu_grad(g, batch, fi, align, xscale, mode=mode)
+        assert np.array_equal(got["status"], status), mode
+        c_ok, _ = PR.chi2_close(got["chi2"][ok], chi2[ok])
+        assert c_ok.all(), mode
+        _check_layer_grads(got["dal"][used], dal[used], f"align mode {mode}")
+        _check_layer_grads(got["dxs"][used], dxs[used], f"xscale mode {mode}")
+        _check_track_grads(got["dp0"][ok], dp0[ok], f"p0 mode {mode}")
     if at_truth:
         # undoing the misalignment lowers the chi2
         assert got["chi2"][ok].sum() < _gpu_grad(g, batch, fi)["chi2"][ok].sum()
@@ -152,3 +153,22 @@ def test_fit_gradient_full_size_sampled(lib):
                                              batch.hit_cov, _hit_layer(batch), fi.p0[s], fi.c0[s])
     ok = (status == 0) & (got["status"][s] == 0)
     _check_track_grads(got["dp0"][s][ok], dp0[ok], "p0 sampled")
+
+
+def test_reverse_sweep_matches_forward_mode(lib, aligned_small):
+    """The two derivative modes evaluate the same FP32 derivatives in a different order: they
+    agree to a few FP32 roundings times the fit's conditioning, far inside the oracle tolerances."""
+    g, batch, fi, al, xs = aligned_small
+    rev = _gpu_grad(g, batch, fi, -al, xs, mode=0)
+    fwd = _gpu_grad(g, batch, fi, -al, xs, mode=1)
+    assert np.array_equal(rev["status"], fwd["status"])
+    # the reverse sweep's values come from its plain FP32 pass, the forward mode's from the value
+    # part of its dual numbers: the same operations, contracted into multiply-adds differently
+    assert np.allclose(rev["chi2"], fwd["chi2"], rtol=1e-4, atol=1e-4)
+    for k in ("dal", "dxs"):
+        r, f = rev[k].astype(np.float64), fwd[k].astype(np.float64)
+        assert np.all(np.abs(r - f) <= 1e-3 * np.abs(f) + 1e-4 * np.abs(f).max()), k
+    ok = rev["status"] == 0
+    r, f = rev["dp0"][ok].astype(np.float64), fwd["dp0"][ok].astype(np.float64)
+    rel = np.abs(r - f) / np.maximum(np.abs(f), 1e-3 * np.abs(f).max(axis=0))
+    assert np.median(rel) < 1e-4 and np.percentile(rel, 99) < 1e-2, (np.median(rel), np.percentile(rel, 99))

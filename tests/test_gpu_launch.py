@@ -115,3 +115,15 @@ def test_autotune_before_seeds_is_an_error(lib):
     ctx = pipeline.make_context(g, S.default_params())
     with pytest.raises(mkgb.MkgbError):
         ctx.autotune()
+
+
+def test_probe_peak(lib):
+    """The FMA-throughput probe returns plausible rates (FP32 above FP64)."""
+    g = S.geometry_phase2()
+    ctx = pipeline.make_context(g, S.default_params())
+    f32 = ctx.probe_peak(0)
+    f64 = ctx.probe_peak(1)
+    assert 5.0 < f32 < 500.0, f32
+    assert 0.01 < f64 < f32, (f64, f32)
+    with pytest.raises(mkgb.MkgbError):
+        ctx.probe_peak(2)
