@@ -292,6 +292,33 @@ def measure_fp64_plain(args, g, params, evs, stream, local, rank, dist):
             "mode": "seed, search and fit all in FP64; events one at a time; same events as the FP32 line"}
 
 
+def measure_fit_backward(ctx, db, fi, stream, dist, local):
+    """The backward fit (Sec. 2.2) of the batch's fit workload from its forward fit's results:
+    one mkgb_fit_backward call after a warm-up call, CUDA-event timed; one step per listed
+    layer (the first an update on the start layer, the others a backward crossing + update)."""
+    import torch
+    from paper_2312_11728_gb300 import pipeline
+    f = db.fit
+    n = f["layers"].shape[0]
+    o = dict(p=torch.zeros((n, 6), device=f"cuda:{local}"), c=torch.zeros((n, 21), device=f"cuda:{local}"),
+             chi2=torch.zeros(n, device=f"cuda:{local}"),
+             status=torch.zeros(n, dtype=torch.int32, device=f"cuda:{local}"))
+    call = lambda: ctx.fit_backward(f["layers"], f["hits"], f["p"], f["c"], o["p"], o["c"], o["chi2"], o["status"])
+    call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    steps = int((fi.layers >= 0).sum())
+    value, wall, _ = pipeline.replica_throughput(e0.elapsed_time(e1) / 1e3, steps, dist, f"cuda:{local}")
+    ok = float((o["status"] == 0).float().mean().item())
+    return {"value": value, "unit": "backward-fit track-layer steps/s", "ms": wall * 1e3, "tracks": n,
+            "steps": steps, "status_ok_fraction": ok, "cov_scale": 100.0,
+            "workload": "the fit workload of the timed batch, started from its forward fit's results"}
+
+
 def measure_fit_grad(args, local, rank, dist, stream):
     """The fit's derivative on the differentiable-fit workload (100,000 tracks over 22 layers of
     a misaligned detector): one mkgb_fit_grad call after a warm-up call, CUDA-event timed."""
@@ -442,6 +469,8 @@ def main():
         fp64 = measure_fp64_plain(args, g, params, evs, stream, local, rank, dist)
         fp64["factor"] = value / fp64["value"]
 
+    bkfit = measure_fit_backward(ctx, db, fit, stream, dist, local)
+
     grad = None
     if not args.no_grad:
         grad = measure_fit_grad(args, local, rank, dist, stream)
@@ -507,6 +536,7 @@ def main():
         "e2e": e2e,
         "fp64_plain": fp64,
         "fit_grad": grad,
+        "fit_backward": bkfit,
         "gpu_launches": int(launches_per_step * args.steps),
         "clocks": clocks,
         "counters": {"build": [int(x) for x in bc], "fit": [int(x) for x in fc]},

@@ -153,6 +153,28 @@ int mkgb_fit(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const i
              const float* p0, const float* c0, float* p_out, float* c_out, float* chi2_out,
              int32_t* status_out, int on_device);
 
+/* Backward fit (Sec. 2.2: each found track re-traversed backwards, refitting its parameters).
+ * n tracks listed as for mkgb_fit, in the forward (outward) order: layers[i*max_steps + j] (-1
+ * ends the list), hits[i*max_steps + j] (-1: no hit on that layer).  p_start (n x 6) and
+ * c_start (n x 21) give each track's state on its LAST listed layer (the forward fit's output
+ * there); the covariance is multiplied by cov_scale (> 0; 100 releases the forward fit's
+ * information) before the fit.  The track is then fitted from the last listed layer to the
+ * first: the hit on the last layer is used first (global-frame update, the state lies on that
+ * layer), then for each earlier layer the inward crossing along the reversed trajectory (the
+ * mean energy loss in each crossed layer's material is added back; the scattering variance is
+ * added as forward), chi2 and the update.  Outputs: p_out, c_out (n x 6, n x 21): the state on
+ * the FIRST listed layer describing the segment inside that layer (its material included);
+ * chi2_out (n): the sum of the predicted chi2 of the backward updates; status_out (n, may be
+ * NULL): 0 ok, 1 a listed layer not crossed inwards, 2 stopped, 3 update failed, 4 hit index
+ * beyond the loaded hits.  Tracks whose largest kappa(S) exceeds params.kappa_fp64 are refit in
+ * FP64; precision = MKGB_FP64 fits all tracks in FP64.  mkgb_counters kind 1 reports the call.
+ * Errors: MKGB_ESTATE without geometry/params (or hits, when a hit is listed), MKGB_EINVAL for
+ * a negative size, a NULL array, cov_scale <= 0 or a hit index beyond the loaded hits (host
+ * arrays). */
+int mkgb_fit_backward(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const int32_t* hits,
+                      const float* p_start, const float* c_start, float cov_scale, float* p_out,
+                      float* c_out, float* chi2_out, int32_t* status_out, int on_device);
+
 /* One pass of the hot path in one call (Sec. 2.2 search and Sec. 4 fit on one batch of events):
  * mkgb_load_hits, mkgb_seed (no optional outputs), mkgb_build and mkgb_fit with the same
  * arguments as those calls, every array a device pointer (their on_device = 1 rules).  Inside,
@@ -259,7 +281,7 @@ int mkgb_update(mkgb_ctx* ctx, int n, const float* p_in, const float* c_in, cons
                 const float* hit_cov, float* p_out, float* c_out, float* chi2_out, int32_t* ok_out,
                 int on_device);
 
-/* Work counters of the last mkgb_build (kind 0) or mkgb_fit (kind 1), after the call's stream
+/* Work counters of the last mkgb_build (kind 0) or mkgb_fit / mkgb_fit_backward (kind 1), after the call's stream
  * work has finished: [0] candidate-layer (build) or track-layer (fit) steps on crossed layers,
  * [1] chi2 evaluations of hits inside windows, [2] Kalman updates, [3] hits tested against a
  * window, [4] Newton iterations of the barrel crossing.  Synchronises the stream. */

@@ -22,15 +22,19 @@ def param_close(pg, po, rel=1e-4):
     return d <= tol, d / tol
 
 
-def cov_close(cg, co, rel=1e-3):
-    """|dC_ij| <= rel * sqrt(d_i d_j).  d_i = C_ii, floored at 1e-12 of the largest variance of
-    its block (position or not): a state on a disk has exactly zero z variance, where the
-    oracle holds FP64 rounding noise of ~1e-16 of the position variances."""
+def cov_close(cg, co, rel=1e-3, floor=1e-5):
+    """|dC_ij| <= rel * sqrt(d_i d_j).  d_i = C_ii, the position variances floored at `floor` of
+    the largest position variance.  A state on a layer surface has no variance along the surface
+    normal in exact arithmetic (a disk state none in z; a barrel state at x ~ R, y ~ 0 almost
+    none in x), so such an entry is a projection of the in-surface variance through a small
+    angle plus rounding residue: FP32 arithmetic resolves it to ~1e-9 of the largest position
+    variance (a fraction of FP32's 6e-8 epsilon), which the 1e-3 relative test cannot ask of an
+    entry below 1e-5 of that largest variance."""
     cg = np.asarray(cg, np.float64)
     diag_idx = [i * (i + 1) // 2 + i for i in range(6)]
     dg = np.abs(co[..., diag_idx])
     pos_max = dg[..., :3].max(axis=-1, keepdims=True)
-    dg = np.concatenate([np.maximum(dg[..., :3], 1e-12 * pos_max), dg[..., 3:]], axis=-1)
+    dg = np.concatenate([np.maximum(dg[..., :3], floor * pos_max), dg[..., 3:]], axis=-1)
     scale = np.sqrt(dg[..., TRI[0]] * dg[..., TRI[1]])
     d = np.abs(cg - co)
     return d <= rel * scale + 1e-30, d / (rel * scale + 1e-30)

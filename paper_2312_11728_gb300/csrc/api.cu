@@ -555,6 +555,52 @@ int mkgb_fit(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const i
     return MKGB_OK;
 }
 
+int mkgb_fit_backward(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const int32_t* hits,
+                      const float* p_start, const float* c_start, float cov_scale, float* p_out, float* c_out,
+                      float* chi2_out, int32_t* status_out, int on_device) {
+    if (!ctx) return MKGB_EINVAL;
+    if (!ctx->has_geom || !ctx->has_params) return fail(ctx, MKGB_ESTATE, "fit_backward before geometry/params");
+    if (n < 0 || max_steps < 0) return fail(ctx, MKGB_EINVAL, "negative size");
+    if (!(cov_scale > 0.0f) || !(cov_scale < 3.0e38f)) return fail(ctx, MKGB_EINVAL, "cov_scale must be positive");
+    if (n > 0 && (!layers || !hits || !p_start || !c_start || !p_out || !c_out || !chi2_out))
+        return fail(ctx, MKGB_EINVAL, "null fit array");
+    bool any_hit = false;
+    if (!on_device)
+        for (size_t q = 0; q < (size_t)n * max_steps && !any_hit; ++q) any_hit = hits[q] >= 0;
+    if ((on_device || any_hit) && !ctx->has_hits) return fail(ctx, MKGB_ESTATE, "fit_backward with hits before load_hits");
+    if (!on_device)
+        for (size_t q = 0; q < (size_t)n * max_steps; ++q)
+            if (hits[q] >= ctx->n_hits) return fail(ctx, MKGB_EINVAL, "hit index %d out of range", hits[q]);
+    DevGuard guard(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const size_t N = (size_t)n, M = (size_t)max_steps;
+    const void *dl, *dh, *dp0, *dc0;
+    CK(stage_in(ctx, S_A, layers, 4 * N * M, on_device, &dl));
+    CK(stage_in(ctx, S_B, hits, 4 * N * M, on_device, &dh));
+    CK(stage_in(ctx, S_C, p_start, 24 * N, on_device, &dp0));
+    CK(stage_in(ctx, S_D, c_start, 84 * N, on_device, &dc0));
+    void *po, *co, *xo, *so;
+    CK(stage_out(ctx, S_E, p_out, 24 * N, on_device, &po));
+    CK(stage_out(ctx, S_F, c_out, 84 * N, on_device, &co));
+    CK(stage_out(ctx, S_G, chi2_out, 4 * N, on_device, &xo));
+    CK(stage_out(ctx, S_H, status_out, 4 * N, on_device, &so));
+    CK(cudaMemsetAsync(ctx->counters_fit.p, 0, 8 * kNumCounters, st));
+    CK(ensure(ctx->rescue_list, 4 * (N > 0 ? N : 1)));
+    CK(ensure(ctx->rescue_count, 16));
+    CK(cudaMemsetAsync(ctx->rescue_count.p, 0, 16, st));
+    CK(launch_bkfit(st, (const DevGeom*)ctx->geom_d.p, ctx->params, (const float4*)ctx->pay.p,
+                    ctx->has_hits ? ctx->n_hits : 0, n, max_steps, (const int*)dl, (const int*)dh, (const float*)dp0,
+                    (const float*)dc0, cov_scale, (float*)po, (float*)co, (float*)xo, (int*)so,
+                    (unsigned long long*)ctx->counters_fit.p, (int*)ctx->rescue_list.p, (int*)ctx->rescue_count.p,
+                    ctx->n_sms));
+    CK(copy_back(ctx, p_out, po, 24 * N, on_device));
+    CK(copy_back(ctx, c_out, co, 84 * N, on_device));
+    CK(copy_back(ctx, chi2_out, xo, 4 * N, on_device));
+    CK(copy_back(ctx, status_out, so, 4 * N, on_device));
+    if (!on_device) CK(cudaStreamSynchronize(st));
+    return MKGB_OK;
+}
+
 int mkgb_fit_grad(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const int32_t* hits, const float* p0,
                   const float* c0, const float* align, const float* xscale, float* chi2_out, float* d_p0,
                   float* d_align, float* d_xscale, int32_t* status_out, int mode, int on_device) {

@@ -121,6 +121,12 @@ cudaError_t launch_fit(cudaStream_t st, const DevGeom* g, DevParams P, const flo
                        int max_steps, const int* layers, const int* hits, const float* p0, const float* c0,
                        float* p_out, float* c_out, float* chi2_out, int* status_out, unsigned long long* counters,
                        int* rescue_list, int* rescue_count, int n_sms);
+// Backward fit (Sec. 2.2) of n tracks listed in forward order from their state on the last
+// listed layer (covariance scaled by cov_scale); FP64 refit of tracks above kappa_fp64.
+cudaError_t launch_bkfit(cudaStream_t st, const DevGeom* g, DevParams P, const float4* pay, int64_t n_hits, int n,
+                         int max_steps, const int* layers, const int* hits, const float* p_start, const float* c_start,
+                         float cov_scale, float* p_out, float* c_out, float* chi2_out, int* status_out,
+                         unsigned long long* counters, int* rescue_list, int* rescue_count, int n_sms);
 cudaError_t launch_step_propagate(cudaStream_t st, const DevGeom* g, DevParams P, int n, const int* layers,
                                   const float* p_in, const float* c_in, float* p_out, float* c_out, int* crossed);
 cudaError_t launch_step_update(cudaStream_t st, int n, const float* p_in, const float* c_in, const float* hxyz,

@@ -337,11 +337,13 @@ template <class F> __device__ __forceinline__ void pred_to_state(int kind, const
 
 // Material of layer L at the predicted state (Sec. 3.1 material; a7): the Highland variance
 // th02 of the scattering angle, kc = k cot(theta), and the factor a = p / p' of the mean energy
-// loss.  Returns 1 (material applied), 0 (no material: zero thickness or k = 0) or -1 (the
-// particle stops).  Computed in the trajectory precision F.
+// loss (gain: the energy is added instead, for the backward fit).  Returns 1 (material applied),
+// 0 (no material: zero thickness or k = 0) or -1 (the particle stops).  Computed in the
+// trajectory precision F.
 template <class F>
 __device__ __forceinline__ int material_terms(const DevLayer& L, F xh, F yh, F k, F st, F ct, F sfp, F cfp,
-                                              F& th02, F& kc, F& a, const F* xscale = nullptr) {
+                                              F& th02, F& kc, F& a, const F* xscale = nullptr,
+                                              bool gain = false) {
     using P = Phys<F>;
     F cosi;
     if (L.kind == MKGB_BARREL) {
@@ -369,7 +371,7 @@ __device__ __forceinline__ int material_terms(const DevLayer& L, F xh, F yh, F k
     const F tmax = F(2) * P::me * bg2 / (F(1) + F(2) * gam * rme + rme * rme);
     const F dedx = P::K * P::ZA / beta2 * (F(0.5) * log_mat(F(2) * P::me * bg2 * tmax / (P::I * P::I)) - beta2);
     const F de = dedx * P::rho * (tt * P::X0) * F(1e-3);
-    const F en = e - de;
+    const F en = gain ? e + de : e - de;   // gain: the backward fit adds the loss back
     if (!(en > P::mpi)) return -1;
     a = pm / sqrt((en - P::mpi) * (en + P::mpi));
     return 1;
@@ -393,11 +395,18 @@ __device__ __forceinline__ void material_cov(G qc[15], F th02, F kc, F st, F a) 
 // dir (optional) gets sin(phi'), cos(phi'), sin(theta), cos(theta) at the crossing.
 // The trajectory, its Jacobian and the material terms are computed in F; the covariance cin (21,
 // global frame) is transported into qc (15, surface frame) in G.  q.c is not touched.
+// BACKWARD (the backward fit, Sec. 2.2): the crossing behind the state, at a negative path length
+// s, as the trajectory is traversed backwards from an outer layer: barrel from outside the
+// cylinder, the radius falling as s decreases, no further back than the point of smallest
+// radius of the current turn; disk behind the state, no further back than that point; the
+// material then adds the mean energy loss back (the state describes the segment on the inner
+// side of the layer).  The parametrisation, the frame and the Jacobian are those of the forward
+// step with s < 0.
 // Options: xscale scales the layer's thickness; s_guess starts the barrel Newton iteration at a
 // path length solved in a lower precision (the FP64 steps then need one or two iterations);
 // s_out returns the path length; mat_fp32 computes the material terms (Highland angle, energy-
 // loss factor: small corrections, ~1e-7 relative in FP32) in FP32 for an FP64 step.
-template <class F, class G>
+template <class F, class G, bool BACKWARD = false>
 __device__ __forceinline__ int propagate_core(const DevLayer& L, float cBf, int material, const StateT<F>& t,
                                               const G cin[21], PredT<F>& q, G qc[15], int& newton_it,
                                               F* dir = nullptr, const F* xscale = nullptr,
@@ -414,7 +423,7 @@ __device__ __forceinline__ int propagate_core(const DevLayer& L, float cBf, int 
     F s, S1, C1, dx, dy;
     if (L.kind == MKGB_BARREL) {
         const F c0 = r2_gap(Rl, t.xh, t.xl, t.yh, t.yl);   // R^2 - |u|^2
-        if (!(c0 > F(0))) return 0;
+        if (BACKWARD ? !(c0 < F(0)) : !(c0 > F(0))) return 0;
         F lo = F(0), hi = F(3.0e38);
         // refinement of a crossing solved in a lower precision (s_guess within ~1e-6 of the
         // root, reach and turn checked there): the root lies inside (0, 2 s_guess), and Newton
@@ -424,6 +433,30 @@ __device__ __forceinline__ int propagate_core(const DevLayer& L, float cBf, int 
         if (refine) {
             s = *s_guess;
             hi = F(2) * s;
+        } else if constexpr (BACKWARD) {
+            // from outside, moving outward at s = 0: backwards the radius falls to its minimum
+            // at the point of smallest radius behind the state; on that stretch g(s) = |u + d|^2
+            // - R^2 rises with s through the root, so Newton runs as forward on the bracket
+            // [-s_near, 0] from the straight-line root c0 / (b + sqrt(b^2 + c0)) < 0
+            const F b = ux * cf + uy * sf;
+            if (!(b > F(0))) return 0;
+            const F disc = b * b + c0;
+            lo = F(-3.0e38);
+            hi = F(0);
+            if (fabs(om) > F(1e-12)) {
+                const F inv = F(1) / om;
+                const F cx = ux - sf * inv, cy = uy + cf * inv;
+                const F rho = fabs(inv);
+                if (fabs(sqrt(cx * cx + cy * cy) - rho) > Rl) return 0;   // never comes down to R
+                const F sg = om > F(0) ? F(1) : F(-1);
+                F back = (t.phi - atan2(sg * cx, -sg * cy) - P::pi) * sg;   // turn since that point
+                back -= P::two_pi * floor(back * (F(1) / P::two_pi));
+                lo = -back * rho;
+            } else if (!(disc >= F(0))) {
+                return 0;
+            }
+            const F s0 = c0 / (b + sqrt(fmax(disc, F(0))));
+            s = (s0 > lo && s0 < hi) ? s0 : F(0.5) * (lo + hi);
         } else {
             const F b = ux * cf + uy * sf;
             const F sq = sqrt(b * b + c0);
@@ -468,22 +501,24 @@ __device__ __forceinline__ int propagate_core(const DevLayer& L, float cBf, int 
             if (!(sn >= lo && sn <= hi)) sn = F(0.5) * (lo + hi);
             const F ds = sn - s;
             s = sn;
-            if (fabs(ds) <= tol * s) break;
+            if (fabs(ds) <= tol * fabs(s)) break;
         }
     } else {
         if (fabs(ct) < F(1e-7)) return 0;
         const F dzp = sub_rn(sub_rn(zd, t.zh), t.zl);
         s = div_rn(dzp * st, ct);
-        if (!(s > F(0))) return 0;
+        if (BACKWARD ? !(s < F(0)) : !(s > F(0))) return 0;
         // loopers are followed on the outgoing part of their current turn only: the disk must be
-        // reached before the next point of largest radius (and moving outward, checked below)
+        // reached before the next point of largest radius (and moving outward, checked below);
+        // backwards, no further back than the point of smallest radius
         if (fabs(om) > F(1e-12)) {
             const F inv = F(1) / om;
             const F cx = ux - sf * inv, cy = uy + cf * inv;
             const F sg = om > F(0) ? F(1) : F(-1);
-            F turn = (atan2(sg * cx, -sg * cy) - t.phi) * sg;
+            const F psi_far = atan2(sg * cx, -sg * cy);
+            F turn = BACKWARD ? (t.phi - psi_far - P::pi) * sg : (psi_far - t.phi) * sg;
             turn -= P::two_pi * floor(turn * (F(1) / P::two_pi));
-            if (s > turn * fabs(inv)) return 0;
+            if (fabs(s) > turn * fabs(inv)) return 0;
         }
     }
     const F a = om * s;
@@ -616,11 +651,11 @@ __device__ __forceinline__ int propagate_core(const DevLayer& L, float cBf, int 
         int mr;
         if (mat_fp32) {
             float th02f = 0.0f, kcf = 0.0f, eaf = 1.0f;
-            mr = material_terms(L, float(q.xh), float(q.yh), float(q.k), float(st), float(ct), float(sfp),
-                                float(cfp), th02f, kcf, eaf);
+            mr = material_terms<float>(L, float(q.xh), float(q.yh), float(q.k), float(st), float(ct),
+                                       float(sfp), float(cfp), th02f, kcf, eaf, nullptr, BACKWARD);
             th02 = F(th02f); kc = F(kcf); ea = F(eaf);
         } else {
-            mr = material_terms(L, q.xh, q.yh, q.k, st, ct, sfp, cfp, th02, kc, ea, xscale);
+            mr = material_terms(L, q.xh, q.yh, q.k, st, ct, sfp, cfp, th02, kc, ea, xscale, BACKWARD);
         }
         if (mr < 0) return -1;
         if (mr > 0) {
@@ -823,12 +858,19 @@ __device__ __forceinline__ bool kalman_update(int kind, const PredT<F>& q, F mx,
 
 // Kalman update of a global-frame state that is not constrained to a surface (the first hit of
 // a seed, whose starting covariance is a diagonal prior): Joseph form in global coordinates.
-template <class F> __device__ __forceinline__ bool state_update(StateT<F>& t, F mx, F my, F mz, const F v[6]) {
+template <class F>
+__device__ __forceinline__ bool state_update(StateT<F>& t, F mx, F my, F mz, const F v[6], F* chi2 = nullptr) {
     F S[6], L[6], inv[3];
 #pragma unroll
     for (int i = 0; i < 6; ++i) S[i] = t.c[i] + v[i];
     if (!chol3(S, L, inv)) return false;
     const F r[3] = {sub_rn(sub_rn(mx, t.xh), t.xl), sub_rn(sub_rn(my, t.yh), t.yl), sub_rn(sub_rn(mz, t.zh), t.zl)};
+    if (chi2) {   // r^T S^-1 r = |L^-1 r|^2
+        const F y0 = r[0] * inv[0];
+        const F y1 = (r[1] - L[1] * y0) * inv[1];
+        const F y2 = (r[2] - L[3] * y0 - L[4] * y1) * inv[2];
+        *chi2 = y0 * y0 + y1 * y1 + y2 * y2;
+    }
     const F i00 = inv[0], i11 = inv[1], i22 = inv[2];
     const F i10 = -L[1] * i00 * i11;
     const F i21 = -L[4] * i11 * i22;

@@ -42,9 +42,9 @@ class Tracks(C.Structure):
 
 
 EXPORTS = ["mkgb_create", "mkgb_destroy", "mkgb_last_error", "mkgb_version", "mkgb_load_geometry",
-           "mkgb_set_params", "mkgb_load_hits", "mkgb_seed", "mkgb_build", "mkgb_fit", "mkgb_fit_static",
-           "mkgb_fit_grad", "mkgb_run", "mkgb_set_launch", "mkgb_autotune", "mkgb_probe_peak",
-           "mkgb_propagate", "mkgb_update", "mkgb_counters"]
+           "mkgb_set_params", "mkgb_load_hits", "mkgb_seed", "mkgb_build", "mkgb_fit", "mkgb_fit_backward",
+           "mkgb_fit_static", "mkgb_fit_grad", "mkgb_run", "mkgb_set_launch", "mkgb_autotune",
+           "mkgb_probe_peak", "mkgb_propagate", "mkgb_update", "mkgb_counters"]
 
 _lib = None
 
@@ -75,6 +75,7 @@ def load_library(path: str = LIB_PATH):
     lib.mkgb_seed.argtypes = [vp, i32, vp, i32, vp, vp, vp]
     lib.mkgb_build.argtypes = [vp, C.POINTER(Tracks), i32]
     lib.mkgb_fit.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32]
+    lib.mkgb_fit_backward.argtypes = [vp, i32, i32, vp, vp, vp, vp, f32, vp, vp, vp, vp, i32]
     lib.mkgb_fit_static.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.mkgb_fit_grad.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32]
     lib.mkgb_run.argtypes = [vp, i32, vp, vp, vp, i32, vp, C.POINTER(Tracks), i32, i32, vp, vp, vp, vp, vp, vp, vp,
@@ -243,6 +244,18 @@ class Context:
                                       C.byref(t), int(n), int(m), pl, ph, pp, pq, po, pco, px2, pst), "mkgb_run")
         self.n_seeds = int(seed_hits.shape[0])
         return out
+
+    def fit_backward(self, layers, hits, p_start, c_start, p_out, c_out, chi2_out, status_out=None,
+                     cov_scale: float = 100.0):
+        """mkgb_fit_backward: tracks listed in forward order, from their state on the last listed
+        layer (covariance x cov_scale) back to the first listed layer (outputs written in place)."""
+        n, m = layers.shape
+        args = [_ptr(layers, np.int32), _ptr(hits, np.int32), _ptr(p_start, np.float32), _ptr(c_start, np.float32)]
+        outs = [_ptr(p_out, np.float32, True), _ptr(c_out, np.float32, True), _ptr(chi2_out, np.float32, True),
+                _ptr(status_out, np.int32, True)]
+        self._check(self.lib.mkgb_fit_backward(self.h, int(n), int(m), *[p for p, _ in args], float(cov_scale),
+                                               *[p for p, _ in outs], _same(*[d for _, d in args + outs])),
+                    "mkgb_fit_backward")
 
     def fit_static(self, layers, hits, p0, c0, p_out, c_out, chi2_out, status_out=None):
         """mkgb_fit_static: the fit without device allocations (device tensors only, at most
