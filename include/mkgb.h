@@ -143,6 +143,24 @@ int mkgb_seed(mkgb_ctx* ctx, int n_seeds, const int32_t* seed_hits, int on_devic
  * 2^28 - 8 or more hits loaded (the hit trail packs hit indices in 28 bits). */
 int mkgb_build(mkgb_ctx* ctx, const mkgb_tracks* out, int on_device);
 
+/* Combinatorial backward search (Sec. 2.2: when the seeding region does not reach the vertex
+ * region, a backward search inwards from the first known hit).  n tracks, each with its event
+ * (track_event[i], an event of the loaded hits), its innermost found layer (first_layer[i]) and
+ * its state on that layer (p_start n x 6, c_start n x 21: the backward fit's output there,
+ * mkgb_fit_backward).  The region comes from the state's eta as for a seed; the search runs
+ * through that region's plan in reverse order (inner layers last), from the step after
+ * first_layer, with the crossing behind each candidate (negative path length, the energy loss
+ * added back) and otherwise the forward search's rules (windows, chi2 cut, best-N, holes),
+ * from score 0 and no hits.  out: as mkgb_build, one row per track, out->hits indexed by the
+ * steps of the reversed plan (MKGB_HIT_PRE before the first searched step); nfound counts the
+ * hits found by this search.  A track whose first_layer is not in its region's plan, or is its
+ * innermost layer, gets score -inf.  FP32 (with the FP64 redo of ill-conditioned updates);
+ * MKGB_EINVAL under precision MKGB_FP64.  Errors: MKGB_ESTATE without geometry, params or hits;
+ * MKGB_EINVAL for a negative size, NULL arrays, max_plan short of the longest plan, or (host
+ * arrays) an event or layer index out of range. */
+int mkgb_build_backward(mkgb_ctx* ctx, int n, const int32_t* track_event, const int32_t* first_layer,
+                        const float* p_start, const float* c_start, const mkgb_tracks* out, int on_device);
+
 /* Kalman fit over a known assignment (Sec. 4): n tracks, each from p0/c0 through up to
  * max_steps layers (layers[i*max_steps + j], -1 ends the list) taking hits[i*max_steps + j]
  * (-1: propagate only).  Outputs: p_out n x 6, c_out n x 21, chi2_out (sum of predicted chi2),

@@ -311,6 +311,37 @@ class Oracle:
             raise RuntimeError(f"orc_build_event failed ({rc})")
         return res
 
+    def build_backward_event(self, layer_off, xyz, cov, p_start, c_start, first_layer, binned=True):
+        """Combinatorial backward search (Sec. 2.2) for tracks of one event from their state on
+        their innermost found layer; hits indexed by the steps of the reversed region plan."""
+        self.P.binned = int(binned)
+        S = int(np.asarray(first_layer).shape[0])
+        mp = max(len(p) for p in self.geom.plans)
+        lo = np.ascontiguousarray(layer_off, np.int64)
+        x = np.ascontiguousarray(xyz, np.float64)
+        cv = np.ascontiguousarray(cov, np.float64)
+        ps = np.ascontiguousarray(p_start, np.float64)
+        cs = np.ascontiguousarray(c_start, np.float64)
+        fl = np.ascontiguousarray(first_layer, np.int32)
+        res, out = _build_out(S, mp)
+        rc = self.lib.orc_build_backward_event(self.gp, C.byref(self.P), C.byref(self.tie), _p(lo, C.c_longlong),
+                                               _p(x), _p(cv), S, _p(ps), _p(cs), _p(fl, C.c_int), C.byref(out))
+        if rc != 0:
+            raise RuntimeError(f"orc_build_backward_event failed ({rc})")
+        return res
+
+
+def _build_out(S, mp):
+    res = dict(params=np.zeros((S, 6)), cov=np.zeros((S, 21)), score=np.zeros(S), chi2=np.zeros(S),
+               nfound=np.zeros(S, np.int32), nholes=np.zeros(S, np.int32),
+               hits=np.zeros((S, mp), np.int32), tie_step=np.zeros(S, np.int32),
+               region=np.zeros(S, np.int32), start=np.zeros(S, np.int32), counters=np.zeros(4, np.int64))
+    out = BuildOut(_p(res["params"]), _p(res["cov"]), _p(res["score"]), _p(res["chi2"]),
+                   _p(res["nfound"], C.c_int), _p(res["nholes"], C.c_int), _p(res["hits"], C.c_int), mp,
+                   _p(res["tie_step"], C.c_int), _p(res["region"], C.c_int), _p(res["start"], C.c_int),
+                   _p(res["counters"], C.c_longlong))
+    return res, out
+
 
 def hit_layers(layer_off, ids):
     """Layer of each (global) hit id given the per-layer offsets of its event (host bookkeeping)."""

@@ -863,228 +863,318 @@ static double cond_frob(const double C[21], const double V[6]) {
     return sqrt(a * b);
 }
 
-int orc_build_event(const orc_geom* g, const orc_params* P, const orc_tie* T,
-                    const long long* layer_off, const double* xyz, const double* cov,
-                    int n_seeds, const int* seed_hits, const int* seed_layers,
-                    orc_build_out* out) {
+/* Per-event hit index: eta, phi and bins (Sec. 3.1: layers aggregate hits for uniform search). */
+static void build_index(const orc_geom* g, const long long* layer_off, const double* xyz, evidx_t* ev) {
     const int NL = g->n_layers;
-    const int N = P->max_cands;
-    if (N < 1 || N > ORC_MAX_CANDS) return -1;
-    /* per-event hit index: eta, phi and bins (Sec. 3.1: layers aggregate hits for uniform search) */
-    evidx_t ev;
-    ev.base = layer_off[0];
+    ev->base = layer_off[0];
     long long nh = layer_off[NL] - layer_off[0];
-    ev.eta = (double*)malloc((nh + 1) * sizeof(double));
-    ev.phi = (double*)malloc((nh + 1) * sizeof(double));
-    for (long long i = 0; i < nh; ++i) orc_hit_eta_phi(&xyz[3 * (ev.base + i)], &ev.eta[i], &ev.phi[i]);
-    ev.layer_bin_base = (int*)malloc(NL * sizeof(int));
+    ev->eta = (double*)malloc((nh + 1) * sizeof(double));
+    ev->phi = (double*)malloc((nh + 1) * sizeof(double));
+    for (long long i = 0; i < nh; ++i) orc_hit_eta_phi(&xyz[3 * (ev->base + i)], &ev->eta[i], &ev->phi[i]);
+    ev->layer_bin_base = (int*)malloc(NL * sizeof(int));
     long long tot = 0;
     for (int l = 0; l < NL; ++l) {
-        ev.layer_bin_base[l] = (int)tot;
+        ev->layer_bin_base[l] = (int)tot;
         tot += (long long)g->layers[l].n_eta * g->layers[l].n_phi + 1;
     }
-    ev.bin_start = (int*)calloc(tot, sizeof(int));
-    ev.bin_ids = (int*)malloc((nh + 1) * sizeof(int));
+    ev->bin_start = (int*)calloc(tot, sizeof(int));
+    ev->bin_ids = (int*)malloc((nh + 1) * sizeof(int));
     for (int l = 0; l < NL; ++l) {
         const orc_layer* L = &g->layers[l];
         int nb = L->n_eta * L->n_phi;
-        int* bs = &ev.bin_start[ev.layer_bin_base[l]];
+        int* bs = &ev->bin_start[ev->layer_bin_base[l]];
         for (long long id = layer_off[l]; id < layer_off[l + 1]; ++id) {
-            long long i = id - ev.base;
-            bs[eta_bin(L, ev.eta[i]) * L->n_phi + phi_bin(L, ev.phi[i]) + 1]++;
+            long long i = id - ev->base;
+            bs[eta_bin(L, ev->eta[i]) * L->n_phi + phi_bin(L, ev->phi[i]) + 1]++;
         }
-        bs[0] = (int)(layer_off[l] - ev.base);
+        bs[0] = (int)(layer_off[l] - ev->base);
         for (int b = 0; b < nb; ++b) bs[b + 1] += bs[b];
         int* fill = (int*)malloc((nb + 1) * sizeof(int));
         memcpy(fill, bs, (nb + 1) * sizeof(int));
         for (long long id = layer_off[l]; id < layer_off[l + 1]; ++id) {  /* ascending ids -> sorted within bin */
-            long long i = id - ev.base;
-            int b = eta_bin(L, ev.eta[i]) * L->n_phi + phi_bin(L, ev.phi[i]);
-            ev.bin_ids[fill[b]++] = (int)id;
+            long long i = id - ev->base;
+            int b = eta_bin(L, ev->eta[i]) * L->n_phi + phi_bin(L, ev->phi[i]);
+            ev->bin_ids[fill[b]++] = (int)id;
         }
         free(fill);
     }
+}
 
-    cand_t* cur = (cand_t*)malloc(ORC_MAX_CANDS * sizeof(cand_t));
-    cand_t* nxt = (cand_t*)malloc(ORC_MAX_CANDS * sizeof(cand_t));
-    double (*pp)[6] = malloc(ORC_MAX_CANDS * sizeof(*pp));
-    double (*CC)[21] = malloc(ORC_MAX_CANDS * sizeof(*CC));
-    childvec kids = {0, 0, 0}, amb = {0, 0, 0};
-    idvec ids = {0, 0, 0};
+static void free_index(evidx_t* ev) {
+    free(ev->eta); free(ev->phi); free(ev->layer_bin_base); free(ev->bin_start); free(ev->bin_ids);
+}
+
+typedef struct {
+    cand_t *cur, *nxt;
+    double (*pp)[6];
+    double (*CC)[21];
+    childvec kids, amb;
+    idvec ids;
+} search_ws;
+
+static void ws_init(search_ws* w) {
+    w->cur = (cand_t*)malloc(ORC_MAX_CANDS * sizeof(cand_t));
+    w->nxt = (cand_t*)malloc(ORC_MAX_CANDS * sizeof(cand_t));
+    w->pp = malloc(ORC_MAX_CANDS * sizeof(*w->pp));
+    w->CC = malloc(ORC_MAX_CANDS * sizeof(*w->CC));
+    w->kids = (childvec){0, 0, 0};
+    w->amb = (childvec){0, 0, 0};
+    w->ids = (idvec){0, 0, 0};
+}
+
+static void ws_free(search_ws* w) {
+    free(w->cur); free(w->nxt); free(w->pp); free(w->CC);
+    free(w->kids.v); free(w->amb.v); free(w->ids.v);
+}
+
+/* Combinatorial search of one track (Sec. 2.2) from the state in w->cur[0] through plan steps
+ * start .. plan_len - 1 of `plan`: per step every candidate is propagated to the layer (forwards,
+ * or backwards for the backward search), the hits in its eta-phi window get a chi2, children
+ * are ranked and the N best kept and updated; the best final candidate goes to slot si of out.
+ * nfound0: hits the track already has (3 seed hits forwards, none backwards). */
+static void search_track(const orc_geom* g, const orc_params* P, const orc_tie* T, const long long* layer_off,
+                         const double* xyz, const double* cov, const evidx_t* evp, search_ws* w,
+                         const int* plan, int plan_len, int start, int backward, int nfound0,
+                         orc_build_out* out, int si) {
+    const int N = P->max_cands;
+    evidx_t ev = *evp;
+    cand_t* cur = w->cur;
+    cand_t* nxt = w->nxt;
+    double (*pp)[6] = w->pp;
+    double (*CC)[21] = w->CC;
     long long* ctr = out->counters;
+    double* op = &out->params[6 * si];
+    double* oC = &out->cov[21 * si];
+    int* oh = &out->hits[(long long)si * out->max_plan];
+    int ncur = 1;
+    cur[0].score = 0.0;
+    cur[0].chi2 = 0.0;
+    cur[0].nfound = nfound0;
+    cur[0].nholes = 0;
+    cur[0].stopped = 0;
+    for (int t = 0; t < ORC_MAX_PLAN; ++t) cur[0].hist[t] = ORC_PRE;
 
+    for (int t = start; t < plan_len; ++t) {
+        const int layer = plan[t];
+        const orc_layer* L = &g->layers[layer];
+        int tie = 0;
+        w->kids.n = 0;
+        w->amb.n = 0;
+        for (int c = 0; c < ncur; ++c) {
+            cand_t* cd = &cur[c];
+            child_t ch = {cd->score, 0.0, c, K_CARRY, -1};
+            if (cd->stopped) { push_child(&w->kids, ch); continue; }
+            double s, em;
+            int r;
+            if (backward) {
+                double pr[6], Cr[21];
+                orc_reverse(cd->p, cd->C, pr, Cr);
+                orc_path_inward(g, layer, pr, &s, &em);
+                r = orc_propagate_backward(g, layer, cd->p, cd->C, P->material, pp[c], CC[c], &s);
+            } else {
+                orc_path(g, layer, cd->p, &s, &em);
+                r = orc_propagate(g, layer, cd->p, cd->C, P->material, pp[c], CC[c], &s);
+            }
+            if (em < T->edge_rel) tie = 1;
+            if (r < 0) continue;
+            if (r == 0) { ch.kind = K_SKIP; push_child(&w->kids, ch); continue; }
+            ctr[0]++;
+            double wn[4];
+            orc_window(L, P, pp[c], CC[c], wn);
+            window_hits(P, L, layer, layer_off, &ev, wn, &w->ids);
+            qsort(w->ids.v, w->ids.n, sizeof(long long), cmp_ll);
+            double me = T->win_abs + T->win_rel * wn[2], mp = T->win_abs + T->win_rel * wn[3];
+            for (int q = 0; q < w->ids.n; ++q) {
+                long long id = w->ids.v[q];
+                ctr[3]++;
+                double de = fabs(ev.eta[id - ev.base] - wn[0]);
+                double dp = fabs(wrap_phi(ev.phi[id - ev.base] - wn[1]));
+                int in = de <= wn[2] && dp <= wn[3];
+                int near_e = fabs(de - wn[2]) < me, near_p = fabs(dp - wn[3]) < mp;
+                int near = (near_e && dp <= wn[3] + mp) || (near_p && de <= wn[2] + me);
+                if (!in && !near) continue;
+                double x2;
+                if (!orc_chi2(pp[c], CC[c], &xyz[3 * id], &cov[6 * id], &x2)) continue;
+                if (in) ctr[1]++;
+                child_t hc = {cd->score + P->score_hit - x2, x2, c, K_HIT, id};
+                if (in && x2 < P->chi2_cut) push_child(&w->kids, hc);
+                if ((near || fabs(x2 - P->chi2_cut) < T->chi2_rel * P->chi2_cut) &&
+                    x2 < P->chi2_cut * (1.0 + T->chi2_rel))
+                    push_child(&w->amb, hc);
+            }
+            if (cd->nholes < P->max_holes) {
+                ch.kind = K_MISS;
+                ch.score = cd->score - P->score_hole;
+            } else {
+                ch.kind = K_STOP;
+            }
+            push_child(&w->kids, ch);
+        }
+        childvec* kids = &w->kids;
+        qsort(kids->v, kids->n, sizeof(child_t), child_cmp);
+        int nkeep = kids->n < N ? kids->n : N;
+        if (kids->n > N && kids->v[N - 1].score - kids->v[N].score < gap_tol(T, kids->v[N - 1].score)) tie = 1;
+        for (int a = 0; a < w->amb.n; ++a) {
+            double thr = kids->n >= N ? kids->v[N - 1].score : -INFINITY;
+            if (w->amb.v[a].score >= thr - gap_tol(T, w->amb.v[a].score)) tie = 1;
+        }
+        if (tie && out->tie_step[si] < 0) out->tie_step[si] = t;
+
+        /* precision limit: an update (or, for a non-hit child, a prediction measured with the
+           layer's resolution) whose innovation covariance is too ill-conditioned for FP32 */
+        for (int q = 0; q < nkeep && !tie; ++q) {
+            child_t* k = &kids->v[q];
+            if (k->kind == K_SKIP || k->kind == K_CARRY) continue;
+            double Vc[6];
+            if (k->kind == K_HIT) {
+                memcpy(Vc, &cov[6 * k->gid], sizeof(Vc));
+            } else {
+                local_cov(L, atan2(pp[k->parent][1], pp[k->parent][0]), Vc);
+            }
+            if (cond_frob(CC[k->parent], Vc) > T->kappa) tie = 1;
+        }
+        if (tie && out->tie_step[si] < 0) out->tie_step[si] = t;
+
+        int nn = 0;
+        for (int q = 0; q < nkeep; ++q) {
+            child_t* k = &kids->v[q];
+            cand_t* par = &cur[k->parent];
+            cand_t* nc = &nxt[nn];
+            memcpy(nc->hist, par->hist, sizeof(nc->hist));
+            nc->score = k->score;
+            nc->chi2 = par->chi2;
+            nc->nfound = par->nfound;
+            nc->nholes = par->nholes;
+            nc->stopped = par->stopped;
+            if (k->kind == K_HIT) {
+                double x2;
+                if (!orc_update(pp[k->parent], CC[k->parent], &xyz[3 * k->gid], &cov[6 * k->gid], 1,
+                                nc->p, nc->C, &x2))
+                    continue;
+                ctr[2]++;
+                nc->chi2 += x2;
+                nc->nfound++;
+                nc->hist[t] = (int)k->gid;
+            } else if (k->kind == K_MISS) {
+                memcpy(nc->p, pp[k->parent], sizeof(nc->p));
+                memcpy(nc->C, CC[k->parent], sizeof(nc->C));
+                nc->nholes++;
+                nc->hist[t] = ORC_MISS;
+            } else if (k->kind == K_STOP) {
+                memcpy(nc->p, pp[k->parent], sizeof(nc->p));
+                memcpy(nc->C, CC[k->parent], sizeof(nc->C));
+                nc->stopped = 1;
+                nc->hist[t] = ORC_STOP;
+            } else {
+                memcpy(nc->p, par->p, sizeof(nc->p));
+                memcpy(nc->C, par->C, sizeof(nc->C));
+                nc->hist[t] = (k->kind == K_SKIP) ? ORC_SKIP : ORC_STOP;
+            }
+            nn++;
+        }
+        cand_t* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+        ncur = nn;
+        if (ncur == 0) break;
+    }
+    w->cur = cur;
+    w->nxt = nxt;
+    if (ncur == 0) return;
+    if (ncur >= 2 && cur[0].score - cur[1].score < gap_tol(T, cur[0].score)) {
+        int first = start;
+        while (first < plan_len && cur[0].hist[first] == cur[1].hist[first]) ++first;
+        if (out->tie_step[si] < 0 || first < out->tie_step[si]) out->tie_step[si] = first;
+    }
+    memcpy(op, cur[0].p, 6 * sizeof(double));
+    memcpy(oC, cur[0].C, 21 * sizeof(double));
+    out->score[si] = cur[0].score;
+    out->chi2[si] = cur[0].chi2;
+    out->nfound[si] = cur[0].nfound;
+    out->nholes[si] = cur[0].nholes;
+    for (int t = 0; t < plan_len && t < out->max_plan; ++t) oh[t] = cur[0].hist[t];
+}
+
+static void clear_out(orc_build_out* out, int si) {
+    int* oh = &out->hits[(long long)si * out->max_plan];
+    for (int t = 0; t < out->max_plan; ++t) oh[t] = ORC_PRE;
+    out->tie_step[si] = -1;
+    out->score[si] = -INFINITY;
+    out->chi2[si] = 0.0;
+    out->nfound[si] = 0;
+    out->nholes[si] = 0;
+    memset(&out->params[6 * si], 0, 6 * sizeof(double));
+    memset(&out->cov[21 * si], 0, 21 * sizeof(double));
+}
+
+int orc_build_event(const orc_geom* g, const orc_params* P, const orc_tie* T,
+                    const long long* layer_off, const double* xyz, const double* cov,
+                    int n_seeds, const int* seed_hits, const int* seed_layers,
+                    orc_build_out* out) {
+    if (P->max_cands < 1 || P->max_cands > ORC_MAX_CANDS) return -1;
+    evidx_t ev;
+    build_index(g, layer_off, xyz, &ev);
+    search_ws w;
+    ws_init(&w);
     for (int si = 0; si < n_seeds; ++si) {
-        double* op = &out->params[6 * si];
-        double* oC = &out->cov[21 * si];
-        int* oh = &out->hits[(long long)si * out->max_plan];
-        for (int t = 0; t < out->max_plan; ++t) oh[t] = ORC_PRE;
-        out->tie_step[si] = -1;
-        out->score[si] = -INFINITY;
-        out->chi2[si] = 0.0;
-        out->nfound[si] = 0;
-        out->nholes[si] = 0;
-        memset(op, 0, 6 * sizeof(double));
-        memset(oC, 0, 21 * sizeof(double));
-
+        clear_out(out, si);
         double h[9], V[18], pinit[6];
         for (int j = 0; j < 3; ++j) {
             long long id = seed_hits[3 * si + j];
             memcpy(&h[3 * j], &xyz[3 * id], 3 * sizeof(double));
             memcpy(&V[6 * j], &cov[6 * id], 6 * sizeof(double));
         }
-        int ncur = 0;
-        if (orc_seed(g, P->material, h, V, &seed_layers[3 * si], cur[0].p, cur[0].C, pinit)) {
-            int region = orc_select_region(g, cur[0].p);
-            int start = plan_start(g, region, seed_layers[3 * si + 2]);
-            out->region[si] = region;
-            out->start[si] = start;
-            if (start >= 0) ncur = 1;
-        } else {
-            out->region[si] = -1;
-            out->start[si] = -1;
-        }
-        if (ncur == 0) continue;
-        const int region = out->region[si];
-        const int* plan = &g->plan[g->plan_off[region]];
-        const int plan_len = g->plan_off[region + 1] - g->plan_off[region];
-        cur[0].score = 0.0;
-        cur[0].chi2 = 0.0;
-        cur[0].nfound = 3;
-        cur[0].nholes = 0;
-        cur[0].stopped = 0;
-        for (int t = 0; t < ORC_MAX_PLAN; ++t) cur[0].hist[t] = ORC_PRE;
-
-        for (int t = out->start[si]; t < plan_len; ++t) {
-            const int layer = plan[t];
-            const orc_layer* L = &g->layers[layer];
-            int tie = 0;
-            kids.n = 0;
-            amb.n = 0;
-            for (int c = 0; c < ncur; ++c) {
-                cand_t* cd = &cur[c];
-                child_t ch = {cd->score, 0.0, c, K_CARRY, -1};
-                if (cd->stopped) { push_child(&kids, ch); continue; }
-                double s, em;
-                orc_path(g, layer, cd->p, &s, &em);
-                if (em < T->edge_rel) tie = 1;
-                int r = orc_propagate(g, layer, cd->p, cd->C, P->material, pp[c], CC[c], &s);
-                if (r < 0) continue;
-                if (r == 0) { ch.kind = K_SKIP; push_child(&kids, ch); continue; }
-                ctr[0]++;
-                double w[4];
-                orc_window(L, P, pp[c], CC[c], w);
-                window_hits(P, L, layer, layer_off, &ev, w, &ids);
-                qsort(ids.v, ids.n, sizeof(long long), cmp_ll);
-                double me = T->win_abs + T->win_rel * w[2], mp = T->win_abs + T->win_rel * w[3];
-                for (int q = 0; q < ids.n; ++q) {
-                    long long id = ids.v[q];
-                    ctr[3]++;
-                    double de = fabs(ev.eta[id - ev.base] - w[0]);
-                    double dp = fabs(wrap_phi(ev.phi[id - ev.base] - w[1]));
-                    int in = de <= w[2] && dp <= w[3];
-                    int near_e = fabs(de - w[2]) < me, near_p = fabs(dp - w[3]) < mp;
-                    int near = (near_e && dp <= w[3] + mp) || (near_p && de <= w[2] + me);
-                    if (!in && !near) continue;
-                    double x2;
-                    if (!orc_chi2(pp[c], CC[c], &xyz[3 * id], &cov[6 * id], &x2)) continue;
-                    if (in) ctr[1]++;
-                    child_t hc = {cd->score + P->score_hit - x2, x2, c, K_HIT, id};
-                    if (in && x2 < P->chi2_cut) push_child(&kids, hc);
-                    if ((near || fabs(x2 - P->chi2_cut) < T->chi2_rel * P->chi2_cut) &&
-                        x2 < P->chi2_cut * (1.0 + T->chi2_rel))
-                        push_child(&amb, hc);
-                }
-                if (cd->nholes < P->max_holes) {
-                    ch.kind = K_MISS;
-                    ch.score = cd->score - P->score_hole;
-                } else {
-                    ch.kind = K_STOP;
-                }
-                push_child(&kids, ch);
-            }
-            qsort(kids.v, kids.n, sizeof(child_t), child_cmp);
-            int nkeep = kids.n < N ? kids.n : N;
-            if (kids.n > N && kids.v[N - 1].score - kids.v[N].score < gap_tol(T, kids.v[N - 1].score)) tie = 1;
-            for (int a = 0; a < amb.n; ++a) {
-                double thr = kids.n >= N ? kids.v[N - 1].score : -INFINITY;
-                if (amb.v[a].score >= thr - gap_tol(T, amb.v[a].score)) tie = 1;
-            }
-            if (tie && out->tie_step[si] < 0) out->tie_step[si] = t;
-
-            /* precision limit: an update (or, for a non-hit child, a prediction measured with the
-               layer's resolution) whose innovation covariance is too ill-conditioned for FP32 */
-            for (int q = 0; q < nkeep && !tie; ++q) {
-                child_t* k = &kids.v[q];
-                if (k->kind == K_SKIP || k->kind == K_CARRY) continue;
-                double Vc[6];
-                if (k->kind == K_HIT) {
-                    memcpy(Vc, &cov[6 * k->gid], sizeof(Vc));
-                } else {
-                    local_cov(L, atan2(pp[k->parent][1], pp[k->parent][0]), Vc);
-                }
-                if (cond_frob(CC[k->parent], Vc) > T->kappa) tie = 1;
-            }
-            if (tie && out->tie_step[si] < 0) out->tie_step[si] = t;
-
-            int nn = 0;
-            for (int q = 0; q < nkeep; ++q) {
-                child_t* k = &kids.v[q];
-                cand_t* par = &cur[k->parent];
-                cand_t* nc = &nxt[nn];
-                memcpy(nc->hist, par->hist, sizeof(nc->hist));
-                nc->score = k->score;
-                nc->chi2 = par->chi2;
-                nc->nfound = par->nfound;
-                nc->nholes = par->nholes;
-                nc->stopped = par->stopped;
-                if (k->kind == K_HIT) {
-                    double x2;
-                    if (!orc_update(pp[k->parent], CC[k->parent], &xyz[3 * k->gid], &cov[6 * k->gid], 1,
-                                    nc->p, nc->C, &x2))
-                        continue;
-                    ctr[2]++;
-                    nc->chi2 += x2;
-                    nc->nfound++;
-                    nc->hist[t] = (int)k->gid;
-                } else if (k->kind == K_MISS) {
-                    memcpy(nc->p, pp[k->parent], sizeof(nc->p));
-                    memcpy(nc->C, CC[k->parent], sizeof(nc->C));
-                    nc->nholes++;
-                    nc->hist[t] = ORC_MISS;
-                } else if (k->kind == K_STOP) {
-                    memcpy(nc->p, pp[k->parent], sizeof(nc->p));
-                    memcpy(nc->C, CC[k->parent], sizeof(nc->C));
-                    nc->stopped = 1;
-                    nc->hist[t] = ORC_STOP;
-                } else {
-                    memcpy(nc->p, par->p, sizeof(nc->p));
-                    memcpy(nc->C, par->C, sizeof(nc->C));
-                    nc->hist[t] = (k->kind == K_SKIP) ? ORC_SKIP : ORC_STOP;
-                }
-                nn++;
-            }
-            cand_t* tmp = cur;
-            cur = nxt;
-            nxt = tmp;
-            ncur = nn;
-            if (ncur == 0) break;
-        }
-        if (ncur == 0) continue;
-        if (ncur >= 2 && cur[0].score - cur[1].score < gap_tol(T, cur[0].score)) {
-            int first = out->start[si];
-            while (first < plan_len && cur[0].hist[first] == cur[1].hist[first]) ++first;
-            if (out->tie_step[si] < 0 || first < out->tie_step[si]) out->tie_step[si] = first;
-        }
-        memcpy(op, cur[0].p, 6 * sizeof(double));
-        memcpy(oC, cur[0].C, 21 * sizeof(double));
-        out->score[si] = cur[0].score;
-        out->chi2[si] = cur[0].chi2;
-        out->nfound[si] = cur[0].nfound;
-        out->nholes[si] = cur[0].nholes;
-        for (int t = 0; t < plan_len && t < out->max_plan; ++t) oh[t] = cur[0].hist[t];
+        out->region[si] = -1;
+        out->start[si] = -1;
+        if (!orc_seed(g, P->material, h, V, &seed_layers[3 * si], w.cur[0].p, w.cur[0].C, pinit)) continue;
+        int region = orc_select_region(g, w.cur[0].p);
+        int start = plan_start(g, region, seed_layers[3 * si + 2]);
+        out->region[si] = region;
+        out->start[si] = start;
+        if (start < 0) continue;
+        search_track(g, P, T, layer_off, xyz, cov, &ev, &w, &g->plan[g->plan_off[region]],
+                     g->plan_off[region + 1] - g->plan_off[region], start, 0, 3, out, si);
     }
-    free(cur); free(nxt); free(pp); free(CC);
-    free(kids.v); free(amb.v); free(ids.v);
-    free(ev.eta); free(ev.phi); free(ev.layer_bin_base); free(ev.bin_start); free(ev.bin_ids);
+    ws_free(&w);
+    free_index(&ev);
+    return 0;
+}
+
+/* Combinatorial backward search (Sec. 2.2: going inwards from the first known hit).  For each
+ * track: its state on its innermost found layer first_layer (the backward fit's output there);
+ * the region from its eta as for a seed; the region's plan in reverse order (inner layers last);
+ * the search runs through the reversed plan's steps after first_layer with backward
+ * propagation, from score 0 and no hits.  out->hits is indexed by the reversed plan's steps;
+ * out->start gets the first step searched (-1: first_layer not in the plan or no inner layer). */
+int orc_build_backward_event(const orc_geom* g, const orc_params* P, const orc_tie* T,
+                             const long long* layer_off, const double* xyz, const double* cov,
+                             int n, const double* p_start, const double* C_start, const int* first_layer,
+                             orc_build_out* out) {
+    if (P->max_cands < 1 || P->max_cands > ORC_MAX_CANDS) return -1;
+    evidx_t ev;
+    build_index(g, layer_off, xyz, &ev);
+    search_ws w;
+    ws_init(&w);
+    int rplan[ORC_MAX_PLAN];
+    for (int si = 0; si < n; ++si) {
+        clear_out(out, si);
+        memcpy(w.cur[0].p, &p_start[6 * si], 6 * sizeof(double));
+        memcpy(w.cur[0].C, &C_start[21 * si], 21 * sizeof(double));
+        int region = orc_select_region(g, w.cur[0].p);
+        const int* plan = &g->plan[g->plan_off[region]];
+        int plan_len = g->plan_off[region + 1] - g->plan_off[region];
+        int start = -1;
+        for (int k = 0; k < plan_len; ++k) {
+            rplan[k] = plan[plan_len - 1 - k];
+            if (rplan[k] == first_layer[si]) start = k + 1;
+        }
+        if (start >= plan_len) start = -1;
+        out->region[si] = region;
+        out->start[si] = start;
+        if (start < 0) continue;
+        search_track(g, P, T, layer_off, xyz, cov, &ev, &w, rplan, plan_len, start, 1, 0, out, si);
+    }
+    ws_free(&w);
+    free_index(&ev);
     return 0;
 }

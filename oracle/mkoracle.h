@@ -123,6 +123,10 @@ void orc_bkfit_batch(const orc_geom* g, int material, int n, int max_steps, cons
                      const int* hits, const double* xyz, const double* cov, const double* p_start,
                      const double* C_start, double cov_scale, double* p, double* C, double* chi2,
                      int* nupd, int* status, long long* counters);
+int  orc_build_backward_event(const orc_geom* g, const orc_params* P, const orc_tie* T,
+                              const long long* layer_off, const double* xyz, const double* cov,
+                              int n, const double* p_start, const double* C_start, const int* first_layer,
+                              orc_build_out* out);
 int  orc_build_event(const orc_geom* g, const orc_params* P, const orc_tie* T,
                      const long long* layer_off, const double* xyz, const double* cov,
                      int n_seeds, const int* seed_hits, const int* seed_layers,

@@ -75,6 +75,39 @@ def oracle_build(orc: Oracle, batch, seed_index=None, binned=True):
     return res
 
 
+def oracle_build_backward(orc: Oracle, batch, track_event, p_start, c_start, first_layer, index=None,
+                          binned=True):
+    """Oracle backward search (Sec. 2.2) of the given tracks (all by default), event by event; the
+    result has the layout of oracle_build (seed_index = the track indices)."""
+    T = len(first_layer)
+    idx = np.arange(T) if index is None else np.asarray(index)
+    L = batch.n_layers
+    xyz = batch.hit_xyz.astype(np.float64)
+    cov = batch.hit_cov.astype(np.float64)
+    mp = max(len(p) for p in orc.geom.plans)
+    res = None
+    ev = np.asarray(track_event)
+    for e in np.unique(ev[idx]):
+        sel = idx[ev[idx] == e]
+        lo = batch.hit_off[e * L:(e + 1) * L + 1]
+        r = orc.build_backward_event(lo, xyz, cov, np.asarray(p_start, np.float64)[sel],
+                                     np.asarray(c_start, np.float64)[sel], np.asarray(first_layer)[sel],
+                                     binned=binned)
+        if res is None:
+            res = {k: (np.zeros((len(idx),) + v.shape[1:], v.dtype) if k != "counters" else np.zeros(4, np.int64))
+                   for k, v in r.items()}
+            pos = {s: i for i, s in enumerate(idx)}
+        rows = [pos[s] for s in sel]
+        for k, v in r.items():
+            if k == "counters":
+                res[k] += v
+            else:
+                res[k][rows] = v
+    res["seed_index"] = idx
+    res["max_plan"] = mp
+    return res
+
+
 def compare_build(gpu: dict, orc: dict):
     """Per-seed comparison of build outputs.  gpu: numpy arrays over all seeds; orc: oracle_build
     result for orc['seed_index'].  Returns a report dict; callers assert on it."""

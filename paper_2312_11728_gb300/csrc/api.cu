@@ -78,6 +78,8 @@ struct mkgb_ctx {
     int n_seeds = 0;
     DevBuf seed_hits, seed_state, seed_state64, seed_info, seed_key, key_counts, key_cursor, seed_order, seed_scan_tmp;
     DevBuf counters_build, counters_fit, queue, rescue_list, rescue_count, build_work, probe_sink, grad_ck;
+    // backward search: the geometry with reversed plans and the tracks' start records
+    DevBuf geom_bwd_d, bw_state, bw_info, bw_order;
     DevBuf stage[S_COUNT];
     // launch shapes of the search rounds and the graph cache replaying them
     int find_shape = 0, select_shape = 0;
@@ -246,7 +248,8 @@ void mkgb_destroy(mkgb_ctx* ctx) {
                          &ctx->scan_tmp, &ctx->seed_hits, &ctx->seed_state, &ctx->seed_state64, &ctx->seed_info, &ctx->seed_key,
                          &ctx->key_counts, &ctx->key_cursor, &ctx->seed_order, &ctx->seed_scan_tmp,
                          &ctx->counters_build, &ctx->counters_fit, &ctx->queue, &ctx->rescue_list,
-                         &ctx->rescue_count, &ctx->build_work, &ctx->probe_sink, &ctx->grad_ck};
+                         &ctx->rescue_count, &ctx->build_work, &ctx->probe_sink, &ctx->grad_ck,
+                         &ctx->geom_bwd_d, &ctx->bw_state, &ctx->bw_info, &ctx->bw_order};
         for (DevBuf* b : all) release(*b);
         for (auto& b : ctx->stage) release(b);
         build_graph_destroy(ctx->graph);
@@ -313,6 +316,15 @@ int mkgb_load_geometry(mkgb_ctx* ctx, const mkgb_layer* layers, int n_layers, co
     DevGuard guard(ctx->device);
     ctx->geom_h = g;
     CK(cudaMemcpyAsync(ctx->geom_d.p, &ctx->geom_h, sizeof(DevGeom), cudaMemcpyHostToDevice, ctx->stream));
+    // the same geometry with every region's plan in reverse order (the backward search)
+    CK(ensure(ctx->geom_bwd_d, sizeof(DevGeom)));
+    {
+        DevGeom gb = ctx->geom_h;
+        for (int r = 0; r < gb.n_regions; ++r)
+            std::reverse(gb.plan + gb.plan_off[r], gb.plan + gb.plan_off[r + 1]);
+        CK(cudaMemcpyAsync(ctx->geom_bwd_d.p, &gb, sizeof(DevGeom), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));   // gb lives on this stack frame
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->max_plan_len = maxp;
     ctx->n_layers = n_layers;
@@ -507,6 +519,73 @@ int mkgb_build(mkgb_ctx* ctx, const mkgb_tracks* out, int on_device) {
     CK(copy_back(ctx, out->nfound, d.nfound, 4 * n, on_device));
     CK(copy_back(ctx, out->nholes, d.nholes, 4 * n, on_device));
     CK(copy_back(ctx, out->hits, d.hits, 4 * n * out->max_plan, on_device));
+    if (!on_device) CK(cudaStreamSynchronize(st));
+    return MKGB_OK;
+}
+
+int mkgb_build_backward(mkgb_ctx* ctx, int n, const int32_t* track_event, const int32_t* first_layer,
+                        const float* p_start, const float* c_start, const mkgb_tracks* out, int on_device) {
+    if (!ctx) return MKGB_EINVAL;
+    if (!ctx->has_geom || !ctx->has_params) return fail(ctx, MKGB_ESTATE, "build_backward before geometry/params");
+    if (!ctx->has_hits) return fail(ctx, MKGB_ESTATE, "build_backward before load_hits");
+    if (n < 0) return fail(ctx, MKGB_EINVAL, "negative size");
+    if (ctx->params.precision == MKGB_FP64)
+        return fail(ctx, MKGB_EINVAL, "the backward search runs in FP32 (precision MKGB_FP32)");
+    if (n > 0 && (!track_event || !first_layer || !p_start || !c_start)) return fail(ctx, MKGB_EINVAL, "null input");
+    if (!out || !out->params || !out->cov || !out->chi2 || !out->score || !out->nfound || !out->nholes || !out->hits)
+        return fail(ctx, MKGB_EINVAL, "null output array");
+    if (out->max_plan < ctx->max_plan_len) return fail(ctx, MKGB_EINVAL, "max_plan %d < longest plan %d", out->max_plan, ctx->max_plan_len);
+    if (ctx->n_hits >= ((int64_t)1 << 28) - 8)
+        return fail(ctx, MKGB_EINVAL, "%lld hits loaded: the search takes fewer than 2^28 - 8", (long long)ctx->n_hits);
+    if (!on_device)
+        for (int i = 0; i < n; ++i) {
+            if (track_event[i] < 0 || track_event[i] >= ctx->n_events)
+                return fail(ctx, MKGB_EINVAL, "track %d: event %d outside the loaded events", i, track_event[i]);
+            if (first_layer[i] < 0 || first_layer[i] >= ctx->n_layers)
+                return fail(ctx, MKGB_EINVAL, "track %d: layer %d outside the geometry", i, first_layer[i]);
+        }
+    if (n == 0) return MKGB_OK;
+    DevGuard guard(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const size_t N = (size_t)n;
+    const void *dev_ev, *dfl, *dp, *dc;
+    CK(stage_in(ctx, S_H, track_event, 4 * N, on_device, &dev_ev));
+    CK(stage_in(ctx, S_I, first_layer, 4 * N, on_device, &dfl));
+    CK(stage_in(ctx, S_J, p_start, 24 * N, on_device, &dp));
+    CK(stage_in(ctx, S_K, c_start, 84 * N, on_device, &dc));
+    BuildOutDev d;
+    void* p;
+    CK(stage_out(ctx, S_A, out->params, 24 * N, on_device, &p)); d.params = (float*)p;
+    CK(stage_out(ctx, S_B, out->cov, 84 * N, on_device, &p)); d.cov = (float*)p;
+    CK(stage_out(ctx, S_C, out->chi2, 4 * N, on_device, &p)); d.chi2 = (float*)p;
+    CK(stage_out(ctx, S_D, out->score, 4 * N, on_device, &p)); d.score = (float*)p;
+    CK(stage_out(ctx, S_E, out->nfound, 4 * N, on_device, &p)); d.nfound = (int*)p;
+    CK(stage_out(ctx, S_F, out->nholes, 4 * N, on_device, &p)); d.nholes = (int*)p;
+    CK(stage_out(ctx, S_G, out->hits, 4 * N * out->max_plan, on_device, &p)); d.hits = (int*)p;
+    d.max_plan = out->max_plan;
+    CK(ensure(ctx->bw_state, 4 * (size_t)kSeedStateStride * N));
+    CK(ensure(ctx->bw_info, 16 * N));
+    CK(ensure(ctx->bw_order, 4 * N));
+    CK(launch_bw_seed(st, (const DevGeom*)ctx->geom_bwd_d.p, ctx->params, n, (const float*)dp, (const float*)dc,
+                      (const int*)dfl, (const int*)dev_ev, (float*)ctx->bw_state.p, (int4*)ctx->bw_info.p,
+                      (int*)ctx->bw_order.p));
+    if (ctx->bins_pending) {   // the binned hits (mkgb_load_hits)
+        CK(cudaStreamWaitEvent(st, ctx->ev_bins, 0));
+        ctx->bins_pending = false;
+    }
+    SeedStore S{n, (const float*)ctx->bw_state.p, nullptr, (const int4*)ctx->bw_info.p, (const int*)ctx->bw_order.p};
+    CK(ensure(ctx->build_work, build_work_bytes(n, ctx->max_plan_len, MKGB_FP32)));
+    const BuildWork w = carve_build_work(ctx->build_work.p, n, ctx->max_plan_len, MKGB_FP32);
+    CK(cudaMemsetAsync(ctx->counters_build.p, 0, 8 * kNumCounters, st));
+    CK(launch_build(st, (const DevGeom*)ctx->geom_bwd_d.p, ctx->max_plan_len, ctx->params, hit_store(ctx), S, d, w,
+                    (unsigned long long*)ctx->counters_build.p, ctx->n_sms, 0, 0, nullptr, true));
+    CK(copy_back(ctx, out->params, d.params, 24 * N, on_device));
+    CK(copy_back(ctx, out->cov, d.cov, 84 * N, on_device));
+    CK(copy_back(ctx, out->chi2, d.chi2, 4 * N, on_device));
+    CK(copy_back(ctx, out->score, d.score, 4 * N, on_device));
+    CK(copy_back(ctx, out->nfound, d.nfound, 4 * N, on_device));
+    CK(copy_back(ctx, out->nholes, d.nholes, 4 * N, on_device));
+    CK(copy_back(ctx, out->hits, d.hits, 4 * N * out->max_plan, on_device));
     if (!on_device) CK(cudaStreamSynchronize(st));
     return MKGB_OK;
 }

@@ -90,7 +90,10 @@ void build_graph_destroy(BuildGraph* gph);
 // autotuner tries); gph: graph cache of the context (nullptr: plain launches).
 cudaError_t launch_build(cudaStream_t st, const DevGeom* g, int max_plan_len, DevParams P, HitStore H, SeedStore S,
                          BuildOutDev out, BuildWork w, unsigned long long* counters, int n_sms, int find_shape,
-                         int select_shape, BuildGraph* gph);
+                         int select_shape, BuildGraph* gph, bool backward = false);
+// Start records of the backward search; g holds the geometry with every region's plan reversed.
+cudaError_t launch_bw_seed(cudaStream_t st, const DevGeom* g, DevParams P, int n, const float* p, const float* c,
+                           const int* first_layer, const int* event, float* state, int4* info, int* order);
 
 // ---- k_fit.cu
 // ---- k_grad.cu

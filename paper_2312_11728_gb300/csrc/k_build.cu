@@ -77,44 +77,54 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-template <class F> constexpr size_t state_bytes() { return 32 * sizeof(F); }
-template <class F> constexpr size_t pred_bytes() { return 24 * sizeof(F); }
+// Words of a slot's state record (hi/lo positions, k, phi, theta, 21 covariance words, theta's
+// and phi's low parts) and of its prediction record (the same with 15 surface-frame covariance
+// words, padded to 16-byte words); layout_build_work sizes its arrays with them.
+constexpr int kStateWords = 32, kPredWords = 28;
+static_assert(kStateWords == kSeedStateStride, "seed records are copied into state records");
+template <class F> constexpr size_t state_bytes() { return kStateWords * sizeof(F); }
+template <class F> constexpr size_t pred_bytes() { return kPredWords * sizeof(F); }
 
 template <class F> __device__ __forceinline__ void load_state_rec(const unsigned char* r, StateT<F>& t) {
-    F f[32];
-    load_words<F, 32>(r, f);
+    F f[kStateWords];
+    load_words<F, kStateWords>(r, f);
     t.xh = f[0]; t.yh = f[1]; t.zh = f[2]; t.xl = f[3]; t.yl = f[4]; t.zl = f[5];
     t.k = f[6]; t.phi = f[7]; t.th = f[8];
 #pragma unroll
     for (int i = 0; i < 21; ++i) t.c[i] = f[9 + i];
+    t.tl = f[30];
+    t.pl = f[31];
 }
 
 template <class F> __device__ __forceinline__ void store_state_rec(unsigned char* r, const StateT<F>& t) {
-    F f[32];
+    F f[kStateWords];
     f[0] = t.xh; f[1] = t.yh; f[2] = t.zh; f[3] = t.xl; f[4] = t.yl; f[5] = t.zl;
     f[6] = t.k; f[7] = t.phi; f[8] = t.th;
 #pragma unroll
     for (int i = 0; i < 21; ++i) f[9 + i] = t.c[i];
-    f[30] = F(0); f[31] = F(0);
-    store_words<F, 32>(r, f);
+    f[30] = t.tl; f[31] = t.pl;
+    store_words<F, kStateWords>(r, f);
 }
 
 template <class F> __device__ __forceinline__ void load_pred_rec(const unsigned char* r, PredT<F>& q) {
-    F f[24];
-    load_words<F, 24>(r, f);
+    F f[kPredWords];
+    load_words<F, kPredWords>(r, f);
     q.xh = f[0]; q.yh = f[1]; q.zh = f[2]; q.xl = f[3]; q.yl = f[4]; q.zl = f[5];
     q.k = f[6]; q.phi = f[7]; q.th = f[8];
 #pragma unroll
     for (int i = 0; i < 15; ++i) q.c[i] = f[9 + i];
+    q.tl = f[24];
+    q.pl = f[25];
 }
 
 template <class F> __device__ __forceinline__ void store_pred_rec(unsigned char* r, const PredT<F>& q) {
-    F f[24];
+    F f[kPredWords];
     f[0] = q.xh; f[1] = q.yh; f[2] = q.zh; f[3] = q.xl; f[4] = q.yl; f[5] = q.zl;
     f[6] = q.k; f[7] = q.phi; f[8] = q.th;
 #pragma unroll
     for (int i = 0; i < 15; ++i) f[9 + i] = q.c[i];
-    store_words<F, 24>(r, f);
+    f[24] = q.tl; f[25] = q.pl; f[26] = F(0); f[27] = F(0);
+    store_words<F, kPredWords>(r, f);
 }
 
 template <class F> __device__ __forceinline__ void copy_state_rec(const unsigned char* src, unsigned char* dst) {
@@ -178,6 +188,7 @@ struct BuildArgs {
     BuildWork w;
     unsigned long long* counters;
     int max_steps;   // trail rows per seed (longest plan)
+    int nfound0;     // hits a track has when its search starts (3 seed hits forwards, 0 backwards)
 };
 
 // ---- round 0: slot 0 of every seed with work takes the seed state
@@ -209,7 +220,7 @@ __global__ void __launch_bounds__(kThreads) k_start(BuildArgs a) {
                 ? reinterpret_cast<const unsigned char*>(a.S.state + (int64_t)seed * kSeedStateStride)
                 : reinterpret_cast<const unsigned char*>(a.S.state64 + (int64_t)seed * kSeedStateStride);
             copy_state_rec<F>(src, a.w.st[0] + (int64_t)i * kGroup * state_bytes<F>());
-            a.w.meta[0][i * kGroup] = pack_meta(0.0f, 0.0f, 3, 0, false, true);
+            a.w.meta[0][i * kGroup] = pack_meta(0.0f, 0.0f, a.nfound0, 0, false, true);
         } else {
             a.w.meta[0][i * kGroup] = dead;
         }
@@ -220,7 +231,7 @@ __global__ void __launch_bounds__(kThreads) k_start(BuildArgs a) {
 
 // ---- a4-a9 for every live candidate of round tau
 
-template <class F, int TH, int MINB>
+template <class F, int TH, int MINB, bool BWD = false>
 __global__ void __launch_bounds__(TH, MINB) k_find(BuildArgs a, int tau) {
     __shared__ DevGeom g;
     // per-thread sorted list of hit children (chi2 asc, id asc), one column per thread
@@ -286,6 +297,8 @@ __global__ void __launch_bounds__(TH, MINB) k_find(BuildArgs a, int tau) {
                 t.k = f[6]; t.phi = f[7]; t.th = f[8];
 #pragma unroll
                 for (int q = 0; q < 21; ++q) t.c[q] = f[9 + q];
+                t.tl = f[30];
+                t.pl = f[31];
             }
             asm volatile("" ::: "memory");
             sl_cur = sl_next;
@@ -313,7 +326,8 @@ __global__ void __launch_bounds__(TH, MINB) k_find(BuildArgs a, int tau) {
         PredT<F> q;
         F dir[4];
         int newton = 0;
-        const int r = propagate(L, g.cB, P.material, t, q, newton, dir);
+        // BWD: the backward search (Sec. 2.2), crossing the plan's layers behind the candidate
+        const int r = propagate_core<F, F, BWD>(L, g.cB, P.material, t, t.c, q, q.c, newton, dir);
         c_newton += newton;
         int nh_kind = K_NONE, n_h = 0;
         float nh_score = 0.0f;
@@ -607,7 +621,7 @@ __global__ void __launch_bounds__(kThreads) k_rescue(BuildArgs a, int tau) {
         load_pred_rec(a.w.pr + (int64_t)psl * pred_bytes<float>(), pq);
         PredT<double> qd;
         qd.xh = pq.xh; qd.yh = pq.yh; qd.zh = pq.zh; qd.xl = pq.xl; qd.yl = pq.yl; qd.zl = pq.zl;
-        qd.k = pq.k; qd.phi = pq.phi; qd.th = pq.th;
+        qd.k = pq.k; qd.phi = pq.phi; qd.th = pq.th; qd.tl = pq.tl; qd.pl = pq.pl;
 #pragma unroll
         for (int q = 0; q < 15; ++q) qd.c[q] = pq.c[q];
         // the hit: its binned index is not in the trail (which holds the hit id), so it is looked
@@ -696,11 +710,11 @@ size_t layout_build_work(char* base, int n_seeds, int max_plan_len, int word_byt
         return r;
     };
     BuildWork t;
-    t.st[0] = reinterpret_cast<unsigned char*>(take(slots * 32 * wb));
-    t.st[1] = reinterpret_cast<unsigned char*>(take(slots * 32 * wb));
+    t.st[0] = reinterpret_cast<unsigned char*>(take(slots * kStateWords * wb));
+    t.st[1] = reinterpret_cast<unsigned char*>(take(slots * kStateWords * wb));
     t.meta[0] = reinterpret_cast<int4*>(take(slots * 16));
     t.meta[1] = reinterpret_cast<int4*>(take(slots * 16));
-    t.pr = reinterpret_cast<unsigned char*>(take(slots * 24 * wb));
+    t.pr = reinterpret_cast<unsigned char*>(take(slots * kPredWords * wb));
     t.ls = reinterpret_cast<int4*>(take(slots * 80));
     t.live[0] = reinterpret_cast<int*>(take(slots * 4));
     t.live[1] = reinterpret_cast<int*>(take(slots * 4));
@@ -715,17 +729,50 @@ size_t layout_build_work(char* base, int n_seeds, int max_plan_len, int word_byt
     return off;
 }
 
+// Start records of the backward search (Sec. 2.2): per track its state on its innermost found
+// layer (p, c: 6 + 21 floats), the region from its eta as for a seed, and the first step of the
+// geometry's reversed plan after that layer (info = (region, start, event, status); status 1
+// when the layer is not in the plan or no layer lies inside it); the search order is the input
+// order.
+__global__ void __launch_bounds__(kThreads) k_bw_seed(const DevGeom* __restrict__ g, DevParams P, int n,
+                                                      const float* __restrict__ p, const float* __restrict__ c,
+                                                      const int* __restrict__ first_layer,
+                                                      const int* __restrict__ event, float* state, int4* info,
+                                                      int* order) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float* o = state + (int64_t)i * kSeedStateStride;
+    const float* pi = p + 6 * (int64_t)i;
+    const float* ci = c + 21 * (int64_t)i;
+    o[0] = pi[0]; o[1] = pi[1]; o[2] = pi[2]; o[3] = 0.0f; o[4] = 0.0f; o[5] = 0.0f;
+    o[6] = pi[3]; o[7] = pi[4]; o[8] = pi[5];
+#pragma unroll
+    for (int q = 0; q < 21; ++q) o[9 + q] = ci[q];
+    o[30] = 0.0f; o[31] = 0.0f;
+    const float eta = -logf(tanf(0.5f * pi[5]));
+    int region = 0;
+    if (g->n_regions > 1 && !(fabsf(eta) < P.barrel_eta_max)) region = eta > 0.0f ? 1 : 2;
+    if (region >= g->n_regions) region = 0;
+    int start = -1;
+    const int pb = g->plan_off[region], len = g->plan_off[region + 1] - pb;
+    for (int k = 0; k < len; ++k)   // g holds the reversed plans
+        if (g->plan[pb + k] == first_layer[i]) start = k + 1;
+    const bool ok = start > 0 && start < len;
+    info[i] = make_int4(region, ok ? start : 0, event[i], ok ? 0 : 1);
+    order[i] = i;
+}
+
 // Launch shapes of the round kernels (threads per block, minimum resident blocks per SM), one of
 // which the autotuner picks: k_find x k_select.  The resident grid of each shape is computed once,
 // before any capture.
-template <class F, int TH, int MINB> struct FindShape {
+template <class F, int TH, int MINB, bool BWD = false> struct FindShape {
     static int grid(int n_sms) {
         static int g = 0;
-        if (!g) g = resident_grid((const void*)k_find<F, TH, MINB>, n_sms, TH);
+        if (!g) g = resident_grid((const void*)k_find<F, TH, MINB, BWD>, n_sms, TH);
         return g;
     }
     static void launch(cudaStream_t st, const BuildArgs& a, int tau, int n_sms) {
-        k_find<F, TH, MINB><<<grid(n_sms), TH, 0, st>>>(a, tau);
+        k_find<F, TH, MINB, BWD><<<grid(n_sms), TH, 0, st>>>(a, tau);
     }
 };
 template <class F, int TH, int MINB> struct SelectShape {
@@ -740,6 +787,7 @@ template <class F, int TH, int MINB> struct SelectShape {
 };
 
 template <class F> void prime_shapes(int n_sms) {
+    if (sizeof(F) == 4) FindShape<float, 128, 1, true>::grid(n_sms);
     FindShape<F, 64, 8>::grid(n_sms);
     FindShape<F, 128, 1>::grid(n_sms);
     FindShape<F, 256, 1>::grid(n_sms);
@@ -748,7 +796,12 @@ template <class F> void prime_shapes(int n_sms) {
     SelectShape<F, 256, 2>::grid(n_sms);
 }
 
-template <class F> void launch_find(int shape, cudaStream_t st, const BuildArgs& a, int tau, int n_sms) {
+template <class F, bool BWD = false>
+void launch_find(int shape, cudaStream_t st, const BuildArgs& a, int tau, int n_sms) {
+    if constexpr (BWD) {   // the backward search: one shape, FP32 only
+        FindShape<F, 128, 1, true>::launch(st, a, tau, n_sms);
+        return;
+    }
     switch (shape) {
         case 1: FindShape<F, 64, 8>::launch(st, a, tau, n_sms); break;
         case 2: FindShape<F, 256, 1>::launch(st, a, tau, n_sms); break;
@@ -764,7 +817,7 @@ template <class F> void launch_select(int shape, cudaStream_t st, const BuildArg
     }
 }
 
-template <class F>
+template <class F, bool BWD = false>
 cudaError_t launch_rounds(cudaStream_t st, const BuildArgs& a, int n, int max_plan_len, int n_sms, int find_shape,
                           int select_shape) {
     cudaError_t e = cudaMemsetAsync(a.w.counts, 0, 32, st);
@@ -772,7 +825,7 @@ cudaError_t launch_rounds(cudaStream_t st, const BuildArgs& a, int n, int max_pl
     const int nb = (n + kThreads - 1) / kThreads;
     k_start<F><<<nb, kThreads, 0, st>>>(a);
     for (int tau = 0; tau < max_plan_len; ++tau) {
-        launch_find<F>(find_shape, st, a, tau, n_sms);
+        launch_find<F, BWD>(find_shape, st, a, tau, n_sms);
         launch_select<F>(select_shape, st, a, tau, n_sms);
         if (sizeof(F) == 4 && a.P.kappa_fp64 > 0.0f) k_rescue<<<n_sms, kThreads, 0, st>>>(a, tau);
     }
@@ -781,7 +834,8 @@ cudaError_t launch_rounds(cudaStream_t st, const BuildArgs& a, int n, int max_pl
 }
 
 cudaError_t enqueue_rounds(cudaStream_t st, const BuildArgs& a, int n, int max_plan_len, int n_sms, int find_shape,
-                           int select_shape) {
+                           int select_shape, bool backward = false) {
+    if (backward) return launch_rounds<float, true>(st, a, n, max_plan_len, n_sms, find_shape, select_shape);
     // MKGB_FP64: the plain all-FP64 comparison path (same rounds, every Kalman step in FP64)
     return a.P.precision == MKGB_FP64
                ? launch_rounds<double>(st, a, n, max_plan_len, n_sms, find_shape, select_shape)
@@ -828,15 +882,20 @@ void build_graph_destroy(BuildGraph* gph) {
 
 cudaError_t launch_build(cudaStream_t st, const DevGeom* g, int max_plan_len, DevParams P, HitStore H, SeedStore S,
                          BuildOutDev out, BuildWork w, unsigned long long* counters, int n_sms, int find_shape,
-                         int select_shape, BuildGraph* gph) {
+                         int select_shape, BuildGraph* gph, bool backward) {
     if (S.n == 0) return cudaSuccess;
     BuildArgs a;
     memset(&a, 0, sizeof(a));   // padding included: the graph cache compares arguments bytewise
     a.geom = g; a.P = P; a.H = H; a.S = S; a.out = out; a.w = w; a.counters = counters; a.max_steps = max_plan_len;
+    a.nfound0 = backward ? 0 : 3;
     if (a.P.precision == MKGB_FP64)
         prime_shapes<double>(n_sms);
     else
         prime_shapes<float>(n_sms);
+    if (backward) {   // plain launches (the search's graph cache serves the forward search)
+        if (P.precision == MKGB_FP64) return cudaErrorInvalidValue;
+        return enqueue_rounds(st, a, S.n, max_plan_len, n_sms, find_shape, select_shape, true);
+    }
     if (!gph || gph->disabled || !capturable(st))
         return enqueue_rounds(st, a, S.n, max_plan_len, n_sms, find_shape, select_shape);
     const bool same = gph->exec && gph->st == st && gph->n == S.n && gph->max_plan == max_plan_len &&
@@ -874,6 +933,14 @@ cudaError_t launch_build(cudaStream_t st, const DevGeom* g, int max_plan_len, De
         gph->select_shape = select_shape;
     }
     return cudaGraphLaunch(gph->exec, st);
+}
+
+cudaError_t launch_bw_seed(cudaStream_t st, const DevGeom* g, DevParams P, int n, const float* p, const float* c,
+                           const int* first_layer, const int* event, float* state, int4* info, int* order) {
+    if (n == 0) return cudaSuccess;
+    k_bw_seed<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(g, P, n, p, c, first_layer, event, state, info,
+                                                                  order);
+    return cudaGetLastError();
 }
 
 }  // namespace mk

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kThreads) k_fit_grad(const DevGeom* __restrict
 }
 
 // Checkpoint of a step's input state: 32 floats (hi positions, lo positions, k, phi, theta, 21
-// covariance words, 2 unused), record j of track i at ((j * n + i) * 32).
+// covariance words, theta's and phi's low parts), record j of track i at ((j * n + i) * 32).
 __device__ __forceinline__ void store_ck(float* __restrict__ p, const State& t) {
     float4* v = reinterpret_cast<float4*>(p);
     v[0] = make_float4(t.xh, t.yh, t.zh, t.xl);
@@ -165,7 +165,7 @@ __device__ __forceinline__ void store_ck(float* __restrict__ p, const State& t) 
     v[2] = make_float4(t.th, t.c[0], t.c[1], t.c[2]);
 #pragma unroll
     for (int q = 0; q < 4; ++q) v[3 + q] = make_float4(t.c[3 + 4 * q], t.c[4 + 4 * q], t.c[5 + 4 * q], t.c[6 + 4 * q]);
-    v[7] = make_float4(t.c[19], t.c[20], 0.0f, 0.0f);
+    v[7] = make_float4(t.c[19], t.c[20], t.tl, t.pl);
 }
 
 __device__ __forceinline__ void load_ck(const float* __restrict__ p, State& t) {
@@ -182,7 +182,7 @@ __device__ __forceinline__ void load_ck(const float* __restrict__ p, State& t) {
         t.c[3 + 4 * q] = a.x; t.c[4 + 4 * q] = a.y; t.c[5 + 4 * q] = a.z; t.c[6 + 4 * q] = a.w;
     }
     a = v[7];
-    t.c[19] = a.x; t.c[20] = a.y;
+    t.c[19] = a.x; t.c[20] = a.y; t.tl = a.z; t.pl = a.w;
 }
 
 // Inputs of one step, in the adjoint's order: x, y, z, k, phi, theta, the 21 covariance words,
@@ -243,6 +243,8 @@ __global__ void __launch_bounds__(kThreads) k_fit_adjoint(
                 td.xh = seeded(t0.xh, 0, base); td.yh = seeded(t0.yh, 1, base); td.zh = seeded(t0.zh, 2, base);
                 td.xl = D(t0.xl); td.yl = D(t0.yl); td.zl = D(t0.zl);
                 td.k = seeded(t0.k, 3, base); td.phi = seeded(t0.phi, 4, base); td.th = seeded(t0.th, 5, base);
+                td.tl = D(t0.tl);
+                td.pl = D(t0.pl);
 #pragma unroll 1
                 for (int q = 0; q < 21; ++q) td.c[q] = seeded(t0.c[q], 6 + q, base);
                 D ald[6];
@@ -263,8 +265,8 @@ __global__ void __launch_bounds__(kThreads) k_fit_adjoint(
                     a = fmaf(lam[1], td.yh.d[k] + td.yl.d[k], a);
                     a = fmaf(lam[2], td.zh.d[k] + td.zl.d[k], a);
                     a = fmaf(lam[3], td.k.d[k], a);
-                    a = fmaf(lam[4], td.phi.d[k], a);
-                    a = fmaf(lam[5], td.th.d[k], a);
+                    a = fmaf(lam[4], td.phi.d[k] + td.pl.d[k], a);
+                    a = fmaf(lam[5], td.th.d[k] + td.tl.d[k], a);
 #pragma unroll
                     for (int q = 0; q < 21; ++q) a = fmaf(lam[6 + q], td.c[q].d[k], a);
                     if (comp < kStateIn)

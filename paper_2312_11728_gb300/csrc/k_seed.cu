@@ -37,6 +37,8 @@ __device__ __forceinline__ void write_seed(const State& t, int i, int region, in
     o[6] = t.k; o[7] = t.phi; o[8] = t.th;
 #pragma unroll
     for (int q = 0; q < 21; ++q) o[9 + q] = t.c[q];
+    o[30] = t.tl;
+    o[31] = t.pl;
     const int status = region >= 0 ? 0 : 1;
     info[i] = make_int4(region, start, event, status);
     if (state6) store_state6(t, state6 + 6 * (int64_t)i, cov21 + 21 * (int64_t)i);
@@ -69,7 +71,7 @@ __global__ void __launch_bounds__(kThreads) k_seed(const DevGeom* __restrict__ g
         o[6] = td.k; o[7] = td.phi; o[8] = td.th;
 #pragma unroll
         for (int q = 0; q < 21; ++q) o[9 + q] = td.c[q];
-        o[30] = 0.0; o[31] = 0.0;
+        o[30] = td.tl; o[31] = td.pl;
     }
 }
 

@@ -47,6 +47,7 @@ template <class F> struct Phys {
     static constexpr S inc_cap = S(10.0);
     static constexpr S pi = S(3.14159265358979323846);
     static constexpr S two_pi = S(6.28318530717959647692);
+    static constexpr S two_pi_lo = S(6.28318530717959647692 - double(S(6.28318530717959647692)));   // 2 pi - two_pi
 };
 
 struct DevLayer {
@@ -83,6 +84,11 @@ template <class F> struct StateT {
     F xh, yh, zh;   // position, high part
     F xl, yl, zl;   // position, low part (|lo| <= ulp(hi)/2)
     F k, phi, th;   // q/pT, direction phi, polar angle
+    // theta's and phi's low parts (theta = th + tl, phi = phi + pl): an FP32 angle near pi has
+    // an ulp of 2.4e-7 rad, which moves a steep track's z by s / sin^2(theta) x 1.2e-7 (~1 um
+    // over 10 cm at eta 2.7) and every predicted transverse position by s x 1.2e-7, enough to
+    // shift the fitted curvature of a 40 GeV track by 1e-4
+    F tl = F(0), pl = F(0);
     F c[21];        // covariance of (x, y, z, k, phi, theta), packed
 };
 
@@ -90,6 +96,7 @@ template <class F> struct StateT {
 // are coordinates along the surface frame axes e1, e2 (see frame_of).
 template <class F> struct PredT {
     F xh, yh, zh, xl, yl, zl, k, phi, th;
+    F tl = F(0), pl = F(0);   // theta's and phi's low parts, as StateT
     F c[15];
 };
 
@@ -192,6 +199,24 @@ template <class F> __device__ __forceinline__ F r2_gap(F R, F xh, F xl, F yh, F 
     F tail = add_rn(add_rn(t1, t2), sub_rn(sub_rn(eR, e1), e2));
     tail = sub_rn(tail, F(2) * (xh * xl + yh * yl));
     return add_rn(s2, tail);
+}
+
+// phi = hi + lo (float-float) into (-pi, pi]: whole turns of 2 pi taken off as the two-word
+// constant two_pi + two_pi_lo, so that the wrap adds no rounding of 2 pi to phi.
+template <class F> __device__ __forceinline__ void wrap_pi_ff(F& hi, F& lo) {
+    const F n = rint(hi * (F(1) / Phys<F>::two_pi));
+    if (n != F(0)) {
+        add_ff(hi, lo, -n * Phys<F>::two_pi);
+        add_ff(hi, lo, -n * Phys<F>::two_pi_lo);
+    }
+    if (hi <= -Phys<F>::pi) {
+        add_ff(hi, lo, F(Phys<F>::two_pi));
+        add_ff(hi, lo, F(Phys<F>::two_pi_lo));
+    }
+    if (hi > Phys<F>::pi) {
+        add_ff(hi, lo, F(-Phys<F>::two_pi));
+        add_ff(hi, lo, F(-Phys<F>::two_pi_lo));
+    }
 }
 
 template <class F> __device__ __forceinline__ F wrap_pi(F a) {
@@ -329,7 +354,7 @@ template <class F> __device__ __forceinline__ void embed_cov(const FrameT<F>& f,
 
 template <class F> __device__ __forceinline__ void pred_to_state(int kind, const PredT<F>& q, StateT<F>& t) {
     t.xh = q.xh; t.yh = q.yh; t.zh = q.zh; t.xl = q.xl; t.yl = q.yl; t.zl = q.zl;
-    t.k = q.k; t.phi = q.phi; t.th = q.th;
+    t.k = q.k; t.phi = q.phi; t.th = q.th; t.tl = q.tl; t.pl = q.pl;
     embed_cov(frame_of(kind, q), q.c, t.c);
 }
 
@@ -417,6 +442,13 @@ __device__ __forceinline__ int propagate_core(const DevLayer& L, float cBf, int 
     F sf, cf, st, ct;
     sin_cos(t.phi, &sf, &cf);
     sin_cos(t.th, &st, &ct);
+    {   // phi + pl, theta + tl: first order in the low parts (below 1.2e-7; second order < 1e-14)
+        const F s0 = st, f0 = sf;
+        st = fma(ct, t.tl, st);
+        ct = fma(-s0, t.tl, ct);
+        sf = fma(cf, t.pl, sf);
+        cf = fma(-f0, t.pl, cf);
+    }
     const F om = -cB * t.k;
     const F ux = t.xh + t.xl, uy = t.yh + t.yl;
     const F Rl = F(L.pos), zd = F(L.pos);
@@ -641,8 +673,12 @@ __device__ __forceinline__ int propagate_core(const DevLayer& L, float cBf, int 
     qc[ix(4, 4)] = cin[ix(5, 5)];
     q.xh = xh; q.xl = xl; q.yh = yh; q.yl = yl; q.zh = zh; q.zl = zl;
     q.k = t.k;
-    q.phi = wrap_pi(t.phi + a);
+    q.phi = t.phi;
+    q.pl = t.pl;
+    add_ff(q.phi, q.pl, a);
+    wrap_pi_ff(q.phi, q.pl);
     q.th = t.th;
+    q.tl = t.tl;
     if (dir) {
         dir[0] = sfp; dir[1] = cfp; dir[2] = st; dir[3] = ct;
     }
@@ -843,8 +879,13 @@ __device__ __forceinline__ bool kalman_update_f(const FrameT<F>& f, const PredT<
     add_ff(out.yh, out.yl, dg[1]);
     add_ff(out.zh, out.zl, dg[2]);
     out.k = q.k + dp[2];
-    out.phi = wrap_pi(q.phi + dp[3]);
-    out.th = q.th + dp[4];
+    out.phi = q.phi;
+    out.pl = q.pl;
+    add_ff(out.phi, out.pl, dp[3]);
+    wrap_pi_ff(out.phi, out.pl);
+    out.th = q.th;
+    out.tl = q.tl;
+    add_ff(out.th, out.tl, dp[4]);
     embed_cov(f, cn, out.c);
     return out.th > F(0) && out.th < Phys<F>::pi;
 }
@@ -920,8 +961,9 @@ __device__ __forceinline__ bool state_update(StateT<F>& t, F mx, F my, F mz, con
     add_ff(t.yh, t.yl, dp[1]);
     add_ff(t.zh, t.zl, dp[2]);
     t.k += dp[3];
-    t.phi = wrap_pi(t.phi + dp[4]);
-    t.th += dp[5];
+    add_ff(t.phi, t.pl, dp[4]);
+    wrap_pi_ff(t.phi, t.pl);
+    add_ff(t.th, t.tl, dp[5]);
     return t.th > F(0) && t.th < Phys<F>::pi;
 }
 
@@ -930,14 +972,14 @@ __device__ __forceinline__ bool state_update(StateT<F>& t, F mx, F my, F mz, con
 template <class F, class G> __device__ __forceinline__ void load_state6(const G* p, const G* c, StateT<F>& t) {
     t.xh = F(p[0]); t.yh = F(p[1]); t.zh = F(p[2]);
     t.xl = F(0); t.yl = F(0); t.zl = F(0);
-    t.k = F(p[3]); t.phi = F(p[4]); t.th = F(p[5]);
+    t.k = F(p[3]); t.phi = F(p[4]); t.th = F(p[5]); t.tl = F(0); t.pl = F(0);
 #pragma unroll
     for (int i = 0; i < 21; ++i) t.c[i] = F(c[i]);
 }
 
 template <class F> __device__ __forceinline__ void store_state6(const StateT<F>& t, float* p, float* c) {
     p[0] = float(t.xh + t.xl); p[1] = float(t.yh + t.yl); p[2] = float(t.zh + t.zl);
-    p[3] = float(t.k); p[4] = float(t.phi); p[5] = float(t.th);
+    p[3] = float(t.k); p[4] = float(t.phi + t.pl); p[5] = float(t.th + t.tl);
 #pragma unroll
     for (int i = 0; i < 21; ++i) c[i] = float(t.c[i]);
 }
@@ -948,7 +990,9 @@ __device__ __forceinline__ void narrow_state(const StateT<double>& d, State& t) 
     t.xh = float(x); t.xl = float(x - double(t.xh));
     t.yh = float(y); t.yl = float(y - double(t.yh));
     t.zh = float(z); t.zl = float(z - double(t.zh));
-    t.k = float(d.k); t.phi = float(d.phi); t.th = float(d.th);
+    const double th = d.th + d.tl, ph = d.phi + d.pl;
+    t.k = float(d.k); t.th = float(th); t.tl = float(th - double(t.th));
+    t.phi = float(ph); t.pl = float(ph - double(t.phi));
 #pragma unroll
     for (int i = 0; i < 21; ++i) t.c[i] = float(d.c[i]);
 }
@@ -971,7 +1015,7 @@ __device__ __forceinline__ void narrow_to_fp32(const State& d, State& t) { t = d
 template <class T, int K> __device__ __forceinline__ void narrow_to_fp32(const StateT<Dual<T, K>>& d, State& t) {
     t.xh = float(d.xh); t.yh = float(d.yh); t.zh = float(d.zh);
     t.xl = float(d.xl); t.yl = float(d.yl); t.zl = float(d.zl);
-    t.k = float(d.k); t.phi = float(d.phi); t.th = float(d.th);
+    t.k = float(d.k); t.phi = float(d.phi); t.th = float(d.th); t.tl = float(d.tl); t.pl = float(d.pl);
 #pragma unroll
     for (int i = 0; i < 21; ++i) t.c[i] = float(d.c[i]);
 }

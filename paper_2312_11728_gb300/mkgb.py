@@ -42,7 +42,8 @@ class Tracks(C.Structure):
 
 
 EXPORTS = ["mkgb_create", "mkgb_destroy", "mkgb_last_error", "mkgb_version", "mkgb_load_geometry",
-           "mkgb_set_params", "mkgb_load_hits", "mkgb_seed", "mkgb_build", "mkgb_fit", "mkgb_fit_backward",
+           "mkgb_set_params", "mkgb_load_hits", "mkgb_seed", "mkgb_build", "mkgb_build_backward", "mkgb_fit",
+           "mkgb_fit_backward",
            "mkgb_fit_static", "mkgb_fit_grad", "mkgb_run", "mkgb_set_launch", "mkgb_autotune",
            "mkgb_probe_peak", "mkgb_propagate", "mkgb_update", "mkgb_counters"]
 
@@ -76,6 +77,7 @@ def load_library(path: str = LIB_PATH):
     lib.mkgb_build.argtypes = [vp, C.POINTER(Tracks), i32]
     lib.mkgb_fit.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32]
     lib.mkgb_fit_backward.argtypes = [vp, i32, i32, vp, vp, vp, vp, f32, vp, vp, vp, vp, i32]
+    lib.mkgb_build_backward.argtypes = [vp, i32, vp, vp, vp, vp, C.POINTER(Tracks), i32]
     lib.mkgb_fit_static.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.mkgb_fit_grad.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32]
     lib.mkgb_run.argtypes = [vp, i32, vp, vp, vp, i32, vp, C.POINTER(Tracks), i32, i32, vp, vp, vp, vp, vp, vp, vp,
@@ -214,6 +216,19 @@ class Context:
                                               ("nfound", i), ("nholes", i), ("hits", i))]
         t = Tracks(*[p for p, _ in ptrs], int(out["hits"].shape[1]))
         self._check(self.lib.mkgb_build(self.h, C.byref(t), _same(*[d for _, d in ptrs])), "mkgb_build")
+        return out
+
+    def build_backward(self, track_event, first_layer, p_start, c_start, out: dict):
+        """mkgb_build_backward: the backward search of tracks from their state on their innermost
+        found layer; out as for build (hits indexed by the reversed plan's steps)."""
+        f, i = np.float32, np.int32
+        args = [_ptr(track_event, i), _ptr(first_layer, i), _ptr(p_start, f), _ptr(c_start, f)]
+        ptrs = [_ptr(out[k], t, out=True) for k, t in (("params", f), ("cov", f), ("chi2", f), ("score", f),
+                                              ("nfound", i), ("nholes", i), ("hits", i))]
+        t = Tracks(*[p for p, _ in ptrs], int(out["hits"].shape[1]))
+        n = int(np.asarray(first_layer).shape[0]) if not _is_torch(first_layer) else int(first_layer.shape[0])
+        self._check(self.lib.mkgb_build_backward(self.h, n, *[p for p, _ in args], C.byref(t),
+                                                 _same(*[d for _, d in args + ptrs])), "mkgb_build_backward")
         return out
 
     def fit(self, layers, hits, p0, c0, p_out, c_out, chi2_out, status_out=None):

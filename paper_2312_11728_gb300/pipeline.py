@@ -44,6 +44,18 @@ def fit_inputs(batch: Batch, seed: int = 0) -> FitInputs:
                      np.concatenate([np.full(p[0].shape[0], e, np.int32) for e, p in enumerate(parts)]))
 
 
+def outer_fit_inputs(fi: FitInputs, n_skip: int) -> FitInputs:
+    """The fit workload without each track's first n_skip listed layers (the lists shifted left):
+    the tracks as a search seeded further out would have found them, the input of a backward
+    search that should find the inner hits again (host bookkeeping)."""
+    L = np.full_like(fi.layers, -1)
+    H = np.full_like(fi.hits, -1)
+    m = fi.layers.shape[1] - n_skip
+    L[:, :m] = fi.layers[:, n_skip:]
+    H[:, :m] = fi.hits[:, n_skip:]
+    return FitInputs(L, H, fi.p0, fi.c0, fi.event)
+
+
 def to_device(a, device):
     import torch
     return torch.from_numpy(np.ascontiguousarray(a)).to(device)

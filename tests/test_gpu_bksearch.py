@@ -1,0 +1,104 @@
+"""Combinatorial backward search (Sec. 2.2, mkgb_build_backward) against the oracle's backward
+search, on the same inputs: tracks whose first three layers are removed are fitted forwards and
+backwards on the GPU, and from that FP32 state on their innermost remaining layer both searches
+go inwards through the reversed region plan.  Hit lists bit-exact outside the near ties the oracle
+flags; parameters, covariance and chi2 within the forward search's tolerances."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import parity as PR
+from paper_2312_11728_gb300 import build as B
+from paper_2312_11728_gb300 import mkgb, pipeline, synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return mkgb.load_library()
+
+
+def _workload(which):
+    if which == "barrel":
+        g = S.geometry_barrel()
+        evs = [S.simulate_event(g, 1000, 31, e, eta_max=1.0, noise_per_layer=200) for e in range(2)]
+    else:
+        g = S.geometry_phase2()
+        evs = [S.simulate_event(g, 1501, 32, e, pt_sampler=S.sample_pt_phase2, eta_max=3.0, noise_total=4000)
+               for e in range(3)]
+    return g, S.concat_events(evs, g.n_layers)
+
+
+def _starts(ctx, batch, n_skip=3):
+    """Forward then backward GPU fit of the tracks without their first n_skip layers."""
+    fi = pipeline.fit_inputs(batch)
+    keep = (fi.layers >= 0).sum(1) >= n_skip + 3
+    fo = pipeline.outer_fit_inputs(fi, n_skip)
+    sel = np.nonzero(keep)[0]
+    L, H = np.ascontiguousarray(fo.layers[sel]), np.ascontiguousarray(fo.hits[sel])
+    n = len(sel)
+    z = lambda *s, t=np.float32: np.zeros(s, t)
+    f = dict(p=z(n, 6), c=z(n, 21), chi2=z(n), status=z(n, t=np.int32))
+    ctx.fit(L, H, fo.p0[sel], fo.c0[sel], f["p"], f["c"], f["chi2"], f["status"])
+    b = dict(p=z(n, 6), c=z(n, 21), chi2=z(n), status=z(n, t=np.int32))
+    ctx.fit_backward(L, H, f["p"], f["c"], b["p"], b["c"], b["chi2"], b["status"])
+    ok = (f["status"] == 0) & (b["status"] == 0)
+    sel, L = sel[ok], L[ok]
+    return fi, sel, np.ascontiguousarray(fi.event[sel].astype(np.int32)), np.ascontiguousarray(L[:, 0]), \
+        np.ascontiguousarray(b["p"][ok]), np.ascontiguousarray(b["c"][ok])
+
+
+@pytest.mark.parametrize("which", ["barrel", "phase2"])
+def test_backward_search_matches_oracle(lib, which):
+    g, batch = _workload(which)
+    params = S.default_params()
+    ctx = pipeline.make_context(g, params)
+    ctx.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov)
+    fi, sel, ev, first, p, c = _starts(ctx, batch)
+    n = len(sel)
+    assert n > 0.9 * ((fi.layers >= 0).sum(1) >= 6).sum()
+    out = ctx.build_backward(ev, first, p, c, mkgb.alloc_tracks(n, g.max_plan))
+    orc = oracle.Oracle(g, params)
+    o = PR.oracle_build_backward(orc, batch, ev, p, c, first)
+    rep = PR.compare_build(out, o)
+    assert len(rep["hit_mismatch"]) == 0, rep
+    assert rep["failed_mismatch"] == 0 and rep["count_bad"] == 0, rep
+    assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0, rep
+    assert rep["n_tie"] < 0.05 * n, rep
+    # the removed inner hits are found again
+    plan_len = np.array([len(g.plans[r]) for r in o["region"]])
+    inner = []
+    for k, i in enumerate(sel):
+        lay = list(g.plans[o["region"][k]][::-1])
+        steps = [lay.index(l) for l in fi.layers[i, :3]]
+        inner.append(np.array_equal(out["hits"][k, steps], fi.hits[i, :3]))
+    assert np.mean(inner) > 0.9, np.mean(inner)
+    assert np.all(plan_len <= g.max_plan)
+
+
+def test_backward_search_edge_cases(lib):
+    g, batch = _workload("barrel")
+    params = S.default_params()
+    ctx = pipeline.make_context(g, params)
+    ctx.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov)
+    fi, sel, ev, first, p, c = _starts(ctx, batch)
+    # no tracks
+    ctx.build_backward(ev[:0], first[:0], p[:0], c[:0], mkgb.alloc_tracks(0, g.max_plan))
+    # a track already on the innermost layer has nothing to search
+    f2 = first[:4].copy()
+    f2[0] = 0
+    out = ctx.build_backward(ev[:4], f2, p[:4], c[:4], mkgb.alloc_tracks(4, g.max_plan))
+    assert out["score"][0] == -np.inf and np.all(out["hits"][0] == mkgb.HIT_PRE)
+    assert np.all(np.isfinite(out["score"][1:]))
+    bad = ev[:4].copy()
+    bad[1] = batch.n_events
+    with pytest.raises(mkgb.MkgbError):
+        ctx.build_backward(bad, first[:4], p[:4], c[:4], mkgb.alloc_tracks(4, g.max_plan))
+    with pytest.raises(mkgb.MkgbError):
+        ctx.build_backward(ev[:4], first[:4], p[:4], c[:4], mkgb.alloc_tracks(4, g.max_plan - 1))
+    ctx64 = pipeline.make_context(g, dict(params, precision=2))
+    ctx64.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov)
+    with pytest.raises(mkgb.MkgbError):
+        ctx64.build_backward(ev[:4], first[:4], p[:4], c[:4], mkgb.alloc_tracks(4, g.max_plan))

@@ -199,3 +199,57 @@ def test_backward_fit_pulls_at_the_first_hit_are_unit_normal():
         assert abs(pl.std() - 1.0) < 0.06, (name, pl.std())
     # the inner-layer state knows the track better than the forward fit's first hit prior did
     assert np.median(Cm[:, 9]) < np.median(f["c"][ok, 9]) * 10
+
+
+def _backward_search_inputs(g, ev, o, n_skip=3):
+    """Tracks with their first n_skip layers removed, forward- then backward-fitted: the start
+    states of a backward search on their innermost remaining layer."""
+    from paper_2312_11728_gb300 import pipeline
+    batch = S.concat_events([ev], g.n_layers)
+    fi = pipeline.fit_inputs(batch)
+    keep = (fi.layers >= 0).sum(1) >= n_skip + 3
+    fo = pipeline.outer_fit_inputs(fi, n_skip)
+    X, V = batch.hit_xyz.astype(np.float64), batch.hit_cov.astype(np.float64)
+    f = o.fit_batch(fo.layers, fo.hits, X, V, fo.p0, fo.c0)
+    b = o.bkfit_batch(fo.layers, fo.hits, X, V, f["p"], f["c"], 100.0)
+    ok = keep & (f["status"] == 0) & (b["status"] == 0)
+    return batch, fi, fo, b, ok
+
+
+def test_backward_search_recovers_the_inner_hits():
+    """Barrel tracks with 200 noise hits per layer: started from the backward fit of their hits
+    beyond the first three layers, the backward search finds the true hits on those three
+    layers for nearly every track (the plan reversed: steps 7, 8, 9 are layers 2, 1, 0)."""
+    g = S.geometry_barrel()
+    o = oracle.Oracle(g)
+    ev = S.simulate_event(g, 800, 21, 0, eta_max=1.0, noise_per_layer=200,
+                          pt_sampler=lambda rng, n: S.sample_pt_loguniform(rng, n, 1.0, 10.0))
+    batch, fi, fo, b, ok = _backward_search_inputs(g, ev, o)
+    assert ok.mean() > 0.95
+    idx = np.nonzero(ok)[0]
+    r = o.build_backward_event(batch.hit_off[:g.n_layers + 1], batch.hit_xyz.astype(np.float64),
+                               batch.hit_cov.astype(np.float64), b["p"][idx], b["c"][idx], fo.layers[idx, 0])
+    assert np.all(r["start"] == g.n_layers - fo.layers[idx, 0])
+    # reversed barrel plan: step k is layer 9 - k; the removed layers 2, 1, 0 are steps 7, 8, 9
+    found = r["hits"][:, 7:10]
+    truth = fi.hits[idx, 2::-1]
+    rate = (found == truth).all(1).mean()
+    assert rate > 0.95, rate
+    assert np.all(r["nfound"] <= 3) and np.mean(r["nfound"] == 3) > 0.95
+
+
+def test_backward_search_binned_equals_brute_force():
+    """The eta-phi bins are an index only: the backward search with the binned lookup and with
+    a scan of every hit of the layer gives the same results."""
+    g = S.geometry_phase2()
+    o = oracle.Oracle(g)
+    ev = S.simulate_event(g, 300, 22, 0, eta_max=3.0, noise_total=3000, pt_sampler=S.sample_pt_phase2)
+    batch, fi, fo, b, ok = _backward_search_inputs(g, ev, o)
+    idx = np.nonzero(ok)[0]
+    args = (batch.hit_off[:g.n_layers + 1], batch.hit_xyz.astype(np.float64), batch.hit_cov.astype(np.float64),
+            b["p"][idx], b["c"][idx], fo.layers[idx, 0])
+    r1 = o.build_backward_event(*args, binned=True)
+    r2 = o.build_backward_event(*args, binned=False)
+    for k in ("hits", "nfound", "nholes", "start"):
+        assert np.array_equal(r1[k], r2[k]), k
+    assert np.array_equal(r1["params"], r2["params"]) and np.array_equal(r1["score"], r2["score"])
