@@ -319,6 +319,31 @@ def measure_fit_backward(ctx, db, fi, stream, dist, local):
             "workload": "the fit workload of the timed batch, started from its forward fit's results"}
 
 
+def measure_cleaning(ctx, db, g, stream, local):
+    """Seed cleaning over the batch's seeds and the quality filter + duplicate removal over its
+    found tracks (seed hits + found hits), one call each after a warm-up, CUDA-event timed."""
+    import torch
+    n = db.seeds.shape[0]
+    keep = torch.zeros(n, dtype=torch.int32, device=f"cuda:{local}")
+    hits = torch.cat([db.seeds, torch.where(db.out["hits"] >= 0, db.out["hits"], -1)], dim=1).contiguous()
+    score = torch.where(torch.isfinite(db.out["score"]), db.out["score"],
+                        torch.full_like(db.out["score"], -1e30)).contiguous()
+    calls = {"clean_seeds": lambda: ctx.clean_seeds(db.seeds, keep),
+             "remove_duplicates": lambda: ctx.remove_duplicates(hits, score, keep, min_hits=6, frac=0.5)}
+    res = {"seeds": int(n), "track_width": int(hits.shape[1])}
+    for name, call in calls.items():
+        call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name + "_ms"] = e0.elapsed_time(e1)
+        res[name + "_kept"] = int(keep.sum().item())
+    return res
+
+
 def measure_fit_grad(args, local, rank, dist, stream):
     """The fit's derivative on the differentiable-fit workload (100,000 tracks over 22 layers of
     a misaligned detector): one mkgb_fit_grad call after a warm-up call, CUDA-event timed."""
@@ -470,6 +495,7 @@ def main():
         fp64["factor"] = value / fp64["value"]
 
     bkfit = measure_fit_backward(ctx, db, fit, stream, dist, local)
+    cleaning = measure_cleaning(ctx, db, g, stream, local)
 
     grad = None
     if not args.no_grad:
@@ -537,6 +563,7 @@ def main():
         "fp64_plain": fp64,
         "fit_grad": grad,
         "fit_backward": bkfit,
+        "cleaning": cleaning,
         "gpu_launches": int(launches_per_step * args.steps),
         "clocks": clocks,
         "counters": {"build": [int(x) for x in bc], "fit": [int(x) for x in fc]},

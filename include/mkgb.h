@@ -81,6 +81,10 @@ typedef struct {
     float kappa_fp64;      /* an update whose innovation covariance S has a condition estimate above this
                               is redone in FP64: the search redoes that update, the fit refits the whole
                               track; 0 = never (both only in the FP32 precision) */
+    float fit_outlier_chi2;/* fits over a known assignment (mkgb_fit, mkgb_fit_static, mkgb_fit_backward;
+                              the final fit's outlier rejection, Sec. 2.2): a listed hit whose predicted chi2
+                              exceeds this is not used (the layer is crossed, the state is not updated);
+                              0 = every listed hit is used.  mkgb_fit_grad ignores it */
 } mkgb_params;
 
 #define MKGB_FP32 0
@@ -160,6 +164,24 @@ int mkgb_build(mkgb_ctx* ctx, const mkgb_tracks* out, int on_device);
  * arrays) an event or layer index out of range. */
 int mkgb_build_backward(mkgb_ctx* ctx, int n, const int32_t* track_event, const int32_t* first_layer,
                         const float* p_start, const float* c_start, const mkgb_tracks* out, int on_device);
+
+/* Seed cleaning (Sec. 2.2: seeds are processed in parallel, so hits consumed by earlier tracks
+ * cannot be masked).  seed_hits: n x 3 global hit ids of the loaded hits.  keep_out[i] = 0 if
+ * seed i shares at least two of its three hits with a seed of lower index, else 1 (each seed is
+ * judged against all others, not transitively; the index order stands for the order sequential
+ * processing would use).  Errors: MKGB_ESTATE before mkgb_load_hits; MKGB_EINVAL for n < 0, NULL
+ * arrays or (host arrays) a hit id beyond the loaded hits; device arrays: such ids are not hits. */
+int mkgb_clean_seeds(mkgb_ctx* ctx, int n, const int32_t* seed_hits, int32_t* keep_out, int on_device);
+
+/* Quality filter and duplicate removal on found tracks (Sec. 2.2).  hits: n x width global hit
+ * ids per track (< 0: none; e.g. the seed hits followed by mkgb_tracks.hits), score: n.  keep_out
+ * [i] = 0 if track i has fewer than min_hits hits, or if a better track (higher score; equal score
+ * and lower index) shares at least frac x min(hits of the two) hits with it (each track judged
+ * against all others, not transitively), else 1.  Errors: MKGB_ESTATE before mkgb_load_hits;
+ * MKGB_EINVAL for n < 0, width < 1, frac outside (0, 1], NULL arrays or (host arrays) a hit id
+ * beyond the loaded hits. */
+int mkgb_remove_duplicates(mkgb_ctx* ctx, int n, int width, const int32_t* hits, const float* score,
+                           int min_hits, float frac, int32_t* keep_out, int on_device);
 
 /* Kalman fit over a known assignment (Sec. 4): n tracks, each from p0/c0 through up to
  * max_steps layers (layers[i*max_steps + j], -1 ends the list) taking hits[i*max_steps + j]

@@ -251,8 +251,10 @@ class Oracle:
                                 _p(p), _p(c), _p(pi), _p(reg, C.c_int), _p(st, C.c_int), _p(status, C.c_int))
         return dict(p=p, c=c, pinit=pi, region=reg, start=st, status=status)
 
-    def fit_batch(self, layers, hits, xyz, cov, p0, c0, material=None):
+    def fit_batch(self, layers, hits, xyz, cov, p0, c0, material=None, outlier_chi2=None):
+        """Kalman fit over a known assignment (Sec. 4); outlier_chi2 > 0 rejects hits above it."""
         mat = self.params["material"] if material is None else int(material)
+        cut = float(self.params.get("fit_outlier_chi2", 0.0) if outlier_chi2 is None else outlier_chi2)
         n, m = layers.shape
         la = np.ascontiguousarray(layers, np.int32)
         hi = np.ascontiguousarray(hits, np.int32)
@@ -261,17 +263,18 @@ class Oracle:
         q0 = np.ascontiguousarray(p0, np.float64)
         d0 = np.ascontiguousarray(c0, np.float64)
         p, c, chi2 = np.zeros((n, 6)), np.zeros((n, 21)), np.zeros(n)
-        nupd, status = np.zeros(n, np.int32), np.zeros(n, np.int32)
+        nupd, status, near = np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n, np.int32)
         ctr = np.zeros(4, np.int64)
         self.lib.orc_fit_batch(self.gp, int(mat), int(n), int(m), _p(la, C.c_int), _p(hi, C.c_int), _p(x), _p(cv),
-                               _p(q0), _p(d0), _p(p), _p(c), _p(chi2), _p(nupd, C.c_int), _p(status, C.c_int),
-                               _p(ctr, C.c_longlong))
-        return dict(p=p, c=c, chi2=chi2, nupd=nupd, status=status, counters=ctr)
+                               _p(q0), _p(d0), C.c_double(cut), _p(p), _p(c), _p(chi2), _p(nupd, C.c_int),
+                               _p(status, C.c_int), _p(near, C.c_int), _p(ctr, C.c_longlong))
+        return dict(p=p, c=c, chi2=chi2, nupd=nupd, status=status, near_cut=near, counters=ctr)
 
-    def bkfit_batch(self, layers, hits, xyz, cov, p_start, c_start, cov_scale, material=None):
+    def bkfit_batch(self, layers, hits, xyz, cov, p_start, c_start, cov_scale, material=None, outlier_chi2=None):
         """Backward fit (Sec. 2.2) of tracks listed in forward order, from their state on the
         last listed layer (covariance scaled by cov_scale) to the innermost listed layer."""
         mat = self.params["material"] if material is None else int(material)
+        cut = float(self.params.get("fit_outlier_chi2", 0.0) if outlier_chi2 is None else outlier_chi2)
         n, m = layers.shape
         la = np.ascontiguousarray(layers, np.int32)
         hi = np.ascontiguousarray(hits, np.int32)
@@ -280,12 +283,13 @@ class Oracle:
         q0 = np.ascontiguousarray(p_start, np.float64)
         d0 = np.ascontiguousarray(c_start, np.float64)
         p, c, chi2 = np.zeros((n, 6)), np.zeros((n, 21)), np.zeros(n)
-        nupd, status = np.zeros(n, np.int32), np.zeros(n, np.int32)
+        nupd, status, near = np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n, np.int32)
         ctr = np.zeros(4, np.int64)
         self.lib.orc_bkfit_batch(self.gp, int(mat), int(n), int(m), _p(la, C.c_int), _p(hi, C.c_int), _p(x),
-                                 _p(cv), _p(q0), _p(d0), C.c_double(cov_scale), _p(p), _p(c), _p(chi2),
-                                 _p(nupd, C.c_int), _p(status, C.c_int), _p(ctr, C.c_longlong))
-        return dict(p=p, c=c, chi2=chi2, nupd=nupd, status=status, counters=ctr)
+                                 _p(cv), _p(q0), _p(d0), C.c_double(cov_scale), C.c_double(cut), _p(p), _p(c),
+                                 _p(chi2), _p(nupd, C.c_int), _p(status, C.c_int), _p(near, C.c_int),
+                                 _p(ctr, C.c_longlong))
+        return dict(p=p, c=c, chi2=chi2, nupd=nupd, status=status, near_cut=near, counters=ctr)
 
     def build_event(self, layer_off, xyz, cov, seed_hits, seed_layers, binned=True):
         """Combinatorial forward search for the seeds of one event (hits [layer_off[0], layer_off[-1]))."""
@@ -329,6 +333,26 @@ class Oracle:
         if rc != 0:
             raise RuntimeError(f"orc_build_backward_event failed ({rc})")
         return res
+
+
+def clean_seeds(seed_hits, n_hits):
+    """Seed cleaning (Sec. 2.2): keep flags; a seed sharing >= 2 hits with a lower-index seed is dropped."""
+    lib_ = lib()
+    sh = np.ascontiguousarray(seed_hits, np.int32)
+    keep = np.zeros(sh.shape[0], np.int32)
+    lib_.orc_clean_seeds(int(sh.shape[0]), _p(sh, C.c_int), C.c_longlong(int(n_hits)), _p(keep, C.c_int))
+    return keep
+
+
+def remove_duplicates(hits, score, n_hits, min_hits=0, frac=0.5):
+    """Quality filter and duplicate removal (Sec. 2.2): keep flags over the rows of `hits`."""
+    lib_ = lib()
+    h = np.ascontiguousarray(hits, np.int32)
+    sc = np.ascontiguousarray(score, np.float64)
+    keep = np.zeros(h.shape[0], np.int32)
+    lib_.orc_remove_duplicates(int(h.shape[0]), int(h.shape[1]), _p(h, C.c_int), _p(sc), C.c_longlong(int(n_hits)),
+                              int(min_hits), C.c_double(frac), _p(keep, C.c_int))
+    return keep
 
 
 def _build_out(S, mp):

@@ -644,14 +644,14 @@ void orc_seed_batch(const orc_geom* g, int material, int n, const int* seed_hits
 
 void orc_fit_batch(const orc_geom* g, int material, int n, int max_steps, const int* layers,
                    const int* hits, const double* xyz, const double* cov, const double* p0,
-                   const double* C0, double* p, double* C, double* chi2, int* nupd,
-                   int* status, long long* counters) {
+                   const double* C0, double outlier_chi2, double* p, double* C, double* chi2, int* nupd,
+                   int* status, int* near_cut, long long* counters) {
     for (int i = 0; i < n; ++i) {
         double q[6], Cq[21], pp[6], Cp[21], s;
         memcpy(q, &p0[6 * i], sizeof(q));
         memcpy(Cq, &C0[21 * i], sizeof(Cq));
         double sum = 0.0;
-        int nu = 0, st = 0;
+        int nu = 0, st = 0, near = 0;
         for (int j = 0; j < max_steps; ++j) {
             int L = layers[(long long)i * max_steps + j];
             if (L < 0) break;
@@ -663,6 +663,14 @@ void orc_fit_batch(const orc_geom* g, int material, int n, int max_steps, const 
             int h = hits[(long long)i * max_steps + j];
             if (h >= 0) {
                 double x2;
+                if (outlier_chi2 > 0.0) {   /* outlier rejection: a hit above the cut is not used */
+                    if (!orc_chi2(pp, Cp, &xyz[3 * (long long)h], &cov[6 * (long long)h], &x2)) {
+                        st = 3;
+                        break;
+                    }
+                    if (fabs(x2 - outlier_chi2) < 1e-3 * outlier_chi2) near = 1;
+                    if (x2 > outlier_chi2) continue;
+                }
                 if (!orc_update(pp, Cp, &xyz[3 * (long long)h], &cov[6 * (long long)h], 1, q, Cq, &x2)) {
                     st = 3;
                     break;
@@ -678,6 +686,7 @@ void orc_fit_batch(const orc_geom* g, int material, int n, int max_steps, const 
         chi2[i] = sum;
         nupd[i] = nu;
         status[i] = st;
+        if (near_cut) near_cut[i] = near;
     }
 }
 
@@ -691,8 +700,8 @@ void orc_fit_batch(const orc_geom* g, int material, int n, int max_steps, const 
  * (0 ok, 1 a listed layer not crossed, 2 stopped, 3 update failed). */
 void orc_bkfit_batch(const orc_geom* g, int material, int n, int max_steps, const int* layers,
                      const int* hits, const double* xyz, const double* cov, const double* p_start,
-                     const double* C_start, double cov_scale, double* p, double* C, double* chi2,
-                     int* nupd, int* status, long long* counters) {
+                     const double* C_start, double cov_scale, double outlier_chi2, double* p, double* C,
+                     double* chi2, int* nupd, int* status, int* near_cut, long long* counters) {
     for (int i = 0; i < n; ++i) {
         double q[6], Cq[21], pp[6], Cp[21], s;
         memcpy(q, &p_start[6 * i], sizeof(q));
@@ -700,7 +709,36 @@ void orc_bkfit_batch(const orc_geom* g, int material, int n, int max_steps, cons
         int nl = 0;
         while (nl < max_steps && layers[(long long)i * max_steps + nl] >= 0) ++nl;
         double sum = 0.0;
-        int nu = 0, st = 0;
+        int nu = 0, st = 0, near = 0;
+        if (nl > 0) {
+            /* the start state lies on the last listed layer: its covariance is taken on that
+               surface, without variance along the surface normal n (zero in exact arithmetic
+               for a fitted state; the FP32 rounding residue of an input is dropped):
+               C -> Pi C Pi^T with Pi = I - n n^T on the position block */
+            const orc_layer* Ls = &g->layers[layers[(long long)i * max_steps + nl - 1]];
+            double nv[3] = {0.0, 0.0, 1.0};
+            if (Ls->kind == ORC_BARREL) {
+                double r = hypot(q[0], q[1]);
+                nv[0] = q[0] / r; nv[1] = q[1] / r; nv[2] = 0.0;
+            }
+            double M[6][6], Pi[6][6], T[6][6];
+            unpack6(Cq, M);
+            for (int a = 0; a < 6; ++a)
+                for (int b = 0; b < 6; ++b) Pi[a][b] = (a == b) - (a < 3 && b < 3 ? nv[a] * nv[b] : 0.0);
+            for (int a = 0; a < 6; ++a)
+                for (int b = 0; b < 6; ++b) {
+                    double acc = 0.0;
+                    for (int l = 0; l < 6; ++l) acc += Pi[a][l] * M[l][b];
+                    T[a][b] = acc;
+                }
+            for (int a = 0; a < 6; ++a)
+                for (int b = 0; b < 6; ++b) {
+                    double acc = 0.0;
+                    for (int l = 0; l < 6; ++l) acc += T[a][l] * Pi[b][l];
+                    M[a][b] = acc;
+                }
+            pack6(M, Cq);
+        }
         for (int j = nl - 1; j >= 0; --j) {
             int L = layers[(long long)i * max_steps + j];
             if (j < nl - 1) {
@@ -715,6 +753,14 @@ void orc_bkfit_batch(const orc_geom* g, int material, int n, int max_steps, cons
                 double x2;
                 memcpy(pp, q, sizeof(q));
                 memcpy(Cp, Cq, sizeof(Cq));
+                if (outlier_chi2 > 0.0) {   /* outlier rejection: a hit above the cut is not used */
+                    if (!orc_chi2(pp, Cp, &xyz[3 * (long long)h], &cov[6 * (long long)h], &x2)) {
+                        st = 3;
+                        break;
+                    }
+                    if (fabs(x2 - outlier_chi2) < 1e-3 * outlier_chi2) near = 1;
+                    if (x2 > outlier_chi2) continue;
+                }
                 if (!orc_update(pp, Cp, &xyz[3 * (long long)h], &cov[6 * (long long)h], 1, q, Cq, &x2)) {
                     st = 3;
                     break;
@@ -730,6 +776,7 @@ void orc_bkfit_batch(const orc_geom* g, int material, int n, int max_steps, cons
         chi2[i] = sum;
         nupd[i] = nu;
         status[i] = st;
+        if (near_cut) near_cut[i] = near;
     }
 }
 
@@ -1177,4 +1224,107 @@ int orc_build_backward_event(const orc_geom* g, const orc_params* P, const orc_t
     ws_free(&w);
     free_index(&ev);
     return 0;
+}
+
+/* ------------------------------------------------------------------ seed cleaning, duplicate removal */
+
+/* Number of hit ids two lists have in common (entries < 0 are not hits; a list holds no id twice). */
+static int shared_hits(const int* a, int na, const int* b, int nb) {
+    int s = 0;
+    for (int i = 0; i < na; ++i) {
+        if (a[i] < 0) continue;
+        for (int j = 0; j < nb; ++j)
+            if (b[j] == a[i]) { ++s; break; }
+    }
+    return s;
+}
+
+static int count_hits(const int* a, int na) {
+    int c = 0;
+    for (int i = 0; i < na; ++i) c += a[i] >= 0;
+    return c;
+}
+
+/* Items (rows of `width` hit ids, < 0 = none) that share a hit, found through a list of the
+ * items on each hit: calls visit(t, u) once per ordered pair t != u sharing at least one hit. */
+typedef void (*pair_fn)(int t, int u, void* ctx);
+static void for_sharing_pairs(int n, int width, const int* hits, long long n_hits, pair_fn visit, void* ctx) {
+    long long* cnt = (long long*)calloc((size_t)n_hits + 1, sizeof(long long));
+    for (long long q = 0; q < (long long)n * width; ++q)
+        if (hits[q] >= 0) cnt[hits[q] + 1]++;
+    for (long long h = 0; h < n_hits; ++h) cnt[h + 1] += cnt[h];
+    int* items = (int*)malloc(((size_t)cnt[n_hits] + 1) * sizeof(int));
+    long long* fill = (long long*)malloc(((size_t)n_hits + 1) * sizeof(long long));
+    memcpy(fill, cnt, ((size_t)n_hits + 1) * sizeof(long long));
+    for (int t = 0; t < n; ++t)
+        for (int i = 0; i < width; ++i) {
+            int h = hits[(long long)t * width + i];
+            if (h >= 0) items[fill[h]++] = t;
+        }
+    int* seen = (int*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int));
+    for (int t = 0; t < n; ++t) seen[t] = -1;
+    for (int t = 0; t < n; ++t) {
+        for (int i = 0; i < width; ++i) {
+            int h = hits[(long long)t * width + i];
+            if (h < 0) continue;
+            for (long long q = cnt[h]; q < cnt[h + 1]; ++q) {
+                int u = items[q];
+                if (u == t || seen[u] == t) continue;
+                seen[u] = t;
+                visit(t, u, ctx);
+            }
+        }
+    }
+    free(cnt); free(items); free(fill); free(seen);
+}
+
+typedef struct { const int* hits; int* keep; } seed_ctx;
+
+static void seed_visit(int t, int u, void* vc) {
+    seed_ctx* c = (seed_ctx*)vc;
+    if (u < t && shared_hits(&c->hits[3 * (long long)t], 3, &c->hits[3 * (long long)u], 3) >= 2) c->keep[t] = 0;
+}
+
+/* Seed cleaning (Sec. 2.2: seeds are processed in parallel, so hits consumed by earlier tracks
+ * cannot be masked).  Reading: a seed that shares at least two of its three hits with a seed of
+ * lower index is dropped (keep = 0), each seed judged against all others (not transitively). */
+void orc_clean_seeds(int n, const int* seed_hits, long long n_hits, int* keep) {
+    for (int t = 0; t < n; ++t) keep[t] = 1;
+    seed_ctx c = {seed_hits, keep};
+    for_sharing_pairs(n, 3, seed_hits, n_hits, seed_visit, &c);
+}
+
+typedef struct {
+    const int* hits;
+    const double* score;
+    int width;
+    double frac;
+    int* keep;
+} dup_ctx;
+
+static void dup_visit(int t, int u, void* vc) {
+    dup_ctx* c = (dup_ctx*)vc;
+    int better = c->score[u] > c->score[t] || (c->score[u] == c->score[t] && u < t);
+    if (!better) return;
+    const int* a = &c->hits[(long long)t * c->width];
+    const int* b = &c->hits[(long long)u * c->width];
+    int na = count_hits(a, c->width), nb = count_hits(b, c->width);
+    int s = shared_hits(a, c->width, b, c->width);
+    if ((double)s >= c->frac * (double)(na < nb ? na : nb)) c->keep[t] = 0;
+}
+
+/* Quality filter and duplicate removal (Sec. 2.2, on the resulting tracks).  Reading: a track
+ * with fewer than min_hits hits is dropped; a track is dropped if a better track (higher score,
+ * or equal score and lower index) shares at least frac x (the smaller hit count) of its hits,
+ * each track judged against all others (not transitively).  hits: n x width hit ids, < 0 none. */
+void orc_remove_duplicates(int n, int width, const int* hits, const double* score, long long n_hits,
+                           int min_hits, double frac, int* keep) {
+    for (int t = 0; t < n; ++t) keep[t] = count_hits(&hits[(long long)t * width], width) >= min_hits;
+    dup_ctx c = {hits, score, width, frac, keep};
+    int* k2 = (int*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int));
+    for (int t = 0; t < n; ++t) k2[t] = 1;
+    c.keep = k2;
+    for_sharing_pairs(n, width, hits, n_hits, dup_visit, &c);
+    for (int t = 0; t < n; ++t) keep[t] = keep[t] && k2[t];
+    free(k2);
 }

@@ -115,14 +115,17 @@ int  orc_select_region(const orc_geom* g, const double p[6]);
 void orc_seed_batch(const orc_geom* g, int material, int n, const int* seed_hits,
                     const int* seed_layers, const double* xyz, const double* cov,
                     double* p, double* C, double* pinit, int* region, int* start, int* status);
+/* outlier_chi2 > 0: a hit whose predicted chi2 exceeds it is not used (the final fit's outlier
+ * rejection, Sec. 2.2 / Sec. 4); near_cut (may be NULL) flags tracks with a chi2 within 1e-3 of
+ * the cut, where FP32 and FP64 may decide differently. */
 void orc_fit_batch(const orc_geom* g, int material, int n, int max_steps, const int* layers,
                    const int* hits, const double* xyz, const double* cov, const double* p0,
-                   const double* C0, double* p, double* C, double* chi2, int* nupd,
-                   int* status, long long* counters);
+                   const double* C0, double outlier_chi2, double* p, double* C, double* chi2, int* nupd,
+                   int* status, int* near_cut, long long* counters);
 void orc_bkfit_batch(const orc_geom* g, int material, int n, int max_steps, const int* layers,
                      const int* hits, const double* xyz, const double* cov, const double* p_start,
-                     const double* C_start, double cov_scale, double* p, double* C, double* chi2,
-                     int* nupd, int* status, long long* counters);
+                     const double* C_start, double cov_scale, double outlier_chi2, double* p, double* C,
+                     double* chi2, int* nupd, int* status, int* near_cut, long long* counters);
 int  orc_build_backward_event(const orc_geom* g, const orc_params* P, const orc_tie* T,
                               const long long* layer_off, const double* xyz, const double* cov,
                               int n, const double* p_start, const double* C_start, const int* first_layer,
@@ -131,6 +134,11 @@ int  orc_build_event(const orc_geom* g, const orc_params* P, const orc_tie* T,
                      const long long* layer_off, const double* xyz, const double* cov,
                      int n_seeds, const int* seed_hits, const int* seed_layers,
                      orc_build_out* out);
+
+/* --- seed cleaning, quality filter and duplicate removal (Sec. 2.2) --- */
+void orc_clean_seeds(int n, const int* seed_hits, long long n_hits, int* keep);
+void orc_remove_duplicates(int n, int width, const int* hits, const double* score, long long n_hits,
+                           int min_hits, double frac, int* keep);
 
 #ifdef __cplusplus
 }

@@ -80,6 +80,7 @@ struct mkgb_ctx {
     DevBuf counters_build, counters_fit, queue, rescue_list, rescue_count, build_work, probe_sink, grad_ck;
     // backward search: the geometry with reversed plans and the tracks' start records
     DevBuf geom_bwd_d, bw_state, bw_info, bw_order;
+    DevBuf clean_scratch;   // seed cleaning / duplicate removal index
     DevBuf stage[S_COUNT];
     // launch shapes of the search rounds and the graph cache replaying them
     int find_shape = 0, select_shape = 0;
@@ -249,7 +250,8 @@ void mkgb_destroy(mkgb_ctx* ctx) {
                          &ctx->key_counts, &ctx->key_cursor, &ctx->seed_order, &ctx->seed_scan_tmp,
                          &ctx->counters_build, &ctx->counters_fit, &ctx->queue, &ctx->rescue_list,
                          &ctx->rescue_count, &ctx->build_work, &ctx->probe_sink, &ctx->grad_ck,
-                         &ctx->geom_bwd_d, &ctx->bw_state, &ctx->bw_info, &ctx->bw_order};
+                         &ctx->geom_bwd_d, &ctx->bw_state, &ctx->bw_info, &ctx->bw_order,
+                         &ctx->clean_scratch};
         for (DevBuf* b : all) release(*b);
         for (auto& b : ctx->stage) release(b);
         build_graph_destroy(ctx->graph);
@@ -360,6 +362,8 @@ int mkgb_set_params(mkgb_ctx* ctx, const mkgb_params* p) {
     d.precision = p->precision;
     if (!(p->kappa_fp64 >= 0.0f)) return fail(ctx, MKGB_EINVAL, "kappa_fp64 must be >= 0");
     d.kappa_fp64 = p->kappa_fp64;
+    if (!(p->fit_outlier_chi2 >= 0.0f)) return fail(ctx, MKGB_EINVAL, "fit_outlier_chi2 must be >= 0");
+    d.fit_outlier_chi2 = p->fit_outlier_chi2;
     ctx->has_params = true;
     return MKGB_OK;
 }
@@ -588,6 +592,47 @@ int mkgb_build_backward(mkgb_ctx* ctx, int n, const int32_t* track_event, const 
     CK(copy_back(ctx, out->hits, d.hits, 4 * N * out->max_plan, on_device));
     if (!on_device) CK(cudaStreamSynchronize(st));
     return MKGB_OK;
+}
+
+namespace {
+
+int item_decide(mkgb_ctx* ctx, int mode, int n, int width, const int32_t* hits, const float* score, int min_hits,
+                float frac, int32_t* keep_out, int on_device, const char* what) {
+    if (!ctx->has_hits) return fail(ctx, MKGB_ESTATE, "%s before load_hits (hit ids index the loaded hits)", what);
+    if (n < 0 || width < 1) return fail(ctx, MKGB_EINVAL, "%s: bad sizes", what);
+    if (n > 0 && (!hits || !keep_out || (mode == 1 && !score))) return fail(ctx, MKGB_EINVAL, "%s: null array", what);
+    if (!on_device)
+        for (size_t q = 0; q < (size_t)n * width; ++q)
+            if (hits[q] >= ctx->n_hits) return fail(ctx, MKGB_EINVAL, "%s: hit id %d beyond the loaded hits", what, hits[q]);
+    if (n == 0) return MKGB_OK;
+    DevGuard guard(ctx->device);
+    cudaStream_t st = ctx->stream;
+    const size_t N = (size_t)n;
+    const void *dh, *ds = nullptr;
+    CK(stage_in(ctx, S_A, hits, 4 * N * width, on_device, &dh));
+    if (mode == 1) CK(stage_in(ctx, S_B, score, 4 * N, on_device, &ds));
+    void* ko;
+    CK(stage_out(ctx, S_C, keep_out, 4 * N, on_device, &ko));
+    CK(ensure(ctx->clean_scratch, 4 * clean_scratch_ints(n, width, ctx->n_hits)));
+    CK(launch_item_decide(st, mode, n, width, (const int*)dh, (const float*)ds, ctx->n_hits, min_hits, frac,
+                          (int*)ctx->clean_scratch.p, (int*)ko, ctx->n_sms));
+    CK(copy_back(ctx, keep_out, ko, 4 * N, on_device));
+    if (!on_device) CK(cudaStreamSynchronize(st));
+    return MKGB_OK;
+}
+
+}  // namespace
+
+int mkgb_clean_seeds(mkgb_ctx* ctx, int n, const int32_t* seed_hits, int32_t* keep_out, int on_device) {
+    if (!ctx) return MKGB_EINVAL;
+    return item_decide(ctx, 0, n, 3, seed_hits, nullptr, 0, 0.0f, keep_out, on_device, "clean_seeds");
+}
+
+int mkgb_remove_duplicates(mkgb_ctx* ctx, int n, int width, const int32_t* hits, const float* score, int min_hits,
+                           float frac, int32_t* keep_out, int on_device) {
+    if (!ctx) return MKGB_EINVAL;
+    if (!(frac > 0.0f && frac <= 1.0f)) return fail(ctx, MKGB_EINVAL, "remove_duplicates: frac %g outside (0, 1]", frac);
+    return item_decide(ctx, 1, n, width, hits, score, min_hits, frac, keep_out, on_device, "remove_duplicates");
 }
 
 int mkgb_fit(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const int32_t* hits, const float* p0,

@@ -130,6 +130,11 @@ cudaError_t launch_bkfit(cudaStream_t st, const DevGeom* g, DevParams P, const f
                          int max_steps, const int* layers, const int* hits, const float* p_start, const float* c_start,
                          float cov_scale, float* p_out, float* c_out, float* chi2_out, int* status_out,
                          unsigned long long* counters, int* rescue_list, int* rescue_count, int n_sms);
+// Seed cleaning (mode 0) and quality filter + duplicate removal (mode 1) over n rows of `width`
+// hit ids; scratch holds clean_scratch_ints(n, width, n_hits) ints; keep gets 0/1 per row.
+size_t clean_scratch_ints(int n, int width, int64_t n_hits);
+cudaError_t launch_item_decide(cudaStream_t st, int mode, int n, int width, const int* hits, const float* score,
+                               int64_t n_hits, int min_hits, float frac, int* scratch, int* keep, int n_sms);
 cudaError_t launch_step_propagate(cudaStream_t st, const DevGeom* g, DevParams P, int n, const int* layers,
                                   const float* p_in, const float* c_in, float* p_out, float* c_out, int* crossed);
 cudaError_t launch_step_update(cudaStream_t st, int n, const float* p_in, const float* c_in, const float* hxyz,

@@ -3,7 +3,8 @@
 // One track per lane, as the forward fit.  The track's state on its last listed layer (the
 // forward fit's result there) has its covariance scaled by cov_scale, so that the forward fit's
 // information is released, and is fitted through the listed layers from the last to the first:
-// the hit on the last layer with a global-frame update, then for each earlier layer the crossing
+// the hit on the last layer first (the state taken in that layer's surface frame, as every
+// prediction, so the update is the same local-frame one), then for each earlier layer the crossing
 // behind the state (propagate_core with BACKWARD: negative path length, material adding the
 // energy loss back), chi2 and update.  The result is the state on the innermost listed layer for
 // the segment inside it (its material included).  Traversing the trajectory backwards with s < 0
@@ -48,12 +49,25 @@ __device__ __forceinline__ int bkfit_track(const DevGeom& g, const DevParams& P,
         const DevLayer& L = g.layers[l];
         F m[3], v[6], x2;
         if (h >= 0) load_hit(pay, h, m, v, nullptr);
-        if (j == nl - 1) {   // the start state lies on this layer: global-frame update
+        if (j == nl - 1) {
+            // the start state lies on this layer: taken in the layer's surface frame (its
+            // covariance without variance along the normal), then updated as every other step
+            PredT<F> q;
+            q.xh = t.xh; q.yh = t.yh; q.k = t.k; q.phi = t.phi; q.th = t.th;
+            const FrameT<F> fr = frame_of(L.kind, q);
+            state_to_pred(fr, t, q);
             if (h >= 0) {
-                if (!state_update(t, m[0], m[1], m[2], v, &x2)) return 3;
-                sum += x2;
-                ++c_upd;
+                float kap = 0.0f;
+                if (!chi2_hit(fr, q, m[0], m[1], m[2], v, x2)) return 3;
+                if (!(P.fit_outlier_chi2 > 0.0f && x2 > F(P.fit_outlier_chi2))) {   // else an outlier
+                    if (!kalman_update_f(fr, q, m[0], m[1], m[2], v, t, &kap)) return 3;
+                    kmax = fmaxf(kmax, kap);
+                    sum += x2;
+                    ++c_upd;
+                    continue;
+                }
             }
+            pred_to_state(L.kind, q, t);
             continue;
         }
         PredT<F> q;
@@ -62,9 +76,12 @@ __device__ __forceinline__ int bkfit_track(const DevGeom& g, const DevParams& P,
         ++c_steps;
         if (h >= 0) {
             float kap = 0.0f;
-            if (!chi2_hit(L.kind, q, m[0], m[1], m[2], v, x2) ||
-                !kalman_update(L.kind, q, m[0], m[1], m[2], v, t, &kap))
-                return 3;
+            if (!chi2_hit(L.kind, q, m[0], m[1], m[2], v, x2)) return 3;
+            if (P.fit_outlier_chi2 > 0.0f && x2 > F(P.fit_outlier_chi2)) {   // outlier: not used
+                pred_to_state(L.kind, q, t);
+                continue;
+            }
+            if (!kalman_update(L.kind, q, m[0], m[1], m[2], v, t, &kap)) return 3;
             kmax = fmaxf(kmax, kap);
             sum += x2;
             ++c_upd;

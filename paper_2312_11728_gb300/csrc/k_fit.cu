@@ -52,9 +52,12 @@ __device__ __forceinline__ int fit_track(const DevGeom& g, const DevParams& P, c
             F m[3], v[6], x2;
             float kap = 0.0f;
             load_hit(pay, h, m, v, nullptr);
-            if (!chi2_hit(L.kind, q, m[0], m[1], m[2], v, x2) ||
-                !kalman_update(L.kind, q, m[0], m[1], m[2], v, t, &kap))
-                return 3;
+            if (!chi2_hit(L.kind, q, m[0], m[1], m[2], v, x2)) return 3;
+            if (P.fit_outlier_chi2 > 0.0f && x2 > F(P.fit_outlier_chi2)) {   // outlier: not used
+                pred_to_state(L.kind, q, t);
+                continue;
+            }
+            if (!kalman_update(L.kind, q, m[0], m[1], m[2], v, t, &kap)) return 3;
             kmax = fmaxf(kmax, kap);
             sum += x2;
             ++c_upd;

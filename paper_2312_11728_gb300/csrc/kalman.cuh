@@ -75,6 +75,7 @@ struct DevParams {
     float score_hit, score_hole, barrel_eta_max;
     int precision;      // MKGB_FP32: FP32 Kalman steps (FP64 seed fit); MKGB_FP64: every step in FP64
     float kappa_fp64;   // fit: tracks with an update whose S condition estimate exceeds this are refit in FP64
+    float fit_outlier_chi2;   // fits: a listed hit with a predicted chi2 above this is not used (0: off)
 };
 
 // Packed lower-triangle index of a symmetric matrix (i, j >= 0).
@@ -350,6 +351,34 @@ template <class F> __device__ __forceinline__ void embed_cov(const FrameT<F>& f,
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b <= a; ++b) c[ix(3 + a, 3 + b)] = q[ix(2 + a, 2 + b)];
+}
+
+// Global-frame state on a surface -> predicted state in the surface frame f (the inverse of
+// embed_cov): positions and angles copied, the covariance projected onto (u1, u2) along e1, e2;
+// any variance along the surface normal (zero for a state on the surface) is dropped.
+template <class F> __device__ __forceinline__ void state_to_pred(const FrameT<F>& f, const StateT<F>& t, PredT<F>& q) {
+    q.xh = t.xh; q.yh = t.yh; q.zh = t.zh; q.xl = t.xl; q.yl = t.yl; q.zl = t.zl;
+    q.k = t.k; q.phi = t.phi; q.pl = t.pl; q.th = t.th; q.tl = t.tl;
+    const F* e[2] = {f.e1, f.e2};
+    F Ce[2][3];   // C_pos e_a
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            Ce[a][i] = t.c[ix(i, 0)] * e[a][0] + t.c[ix(i, 1)] * e[a][1] + t.c[ix(i, 2)] * e[a][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b <= a; ++b) q.c[ix(a, b)] = dot3(e[a], Ce[b]);
+#pragma unroll
+    for (int o = 0; o < 3; ++o)
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+            q.c[ix(2 + o, a)] = t.c[ix(3 + o, 0)] * e[a][0] + t.c[ix(3 + o, 1)] * e[a][1] + t.c[ix(3 + o, 2)] * e[a][2];
+#pragma unroll
+    for (int o = 0; o < 3; ++o)
+#pragma unroll
+        for (int r = 0; r <= o; ++r) q.c[ix(2 + o, 2 + r)] = t.c[ix(3 + o, 3 + r)];
 }
 
 template <class F> __device__ __forceinline__ void pred_to_state(int kind, const PredT<F>& q, StateT<F>& t) {

@@ -33,7 +33,7 @@ class Params(C.Structure):
                 ("win_nsigma", C.c_float), ("deta_min", C.c_float), ("deta_max", C.c_float),
                 ("dphi_min", C.c_float), ("dphi_max", C.c_float), ("score_hit", C.c_float),
                 ("score_hole", C.c_float), ("barrel_eta_max", C.c_float), ("material", C.c_int32),
-                ("precision", C.c_int32), ("kappa_fp64", C.c_float)]
+                ("precision", C.c_int32), ("kappa_fp64", C.c_float), ("fit_outlier_chi2", C.c_float)]
 
 
 class Tracks(C.Structure):
@@ -45,7 +45,8 @@ EXPORTS = ["mkgb_create", "mkgb_destroy", "mkgb_last_error", "mkgb_version", "mk
            "mkgb_set_params", "mkgb_load_hits", "mkgb_seed", "mkgb_build", "mkgb_build_backward", "mkgb_fit",
            "mkgb_fit_backward",
            "mkgb_fit_static", "mkgb_fit_grad", "mkgb_run", "mkgb_set_launch", "mkgb_autotune",
-           "mkgb_probe_peak", "mkgb_propagate", "mkgb_update", "mkgb_counters"]
+           "mkgb_probe_peak", "mkgb_clean_seeds", "mkgb_remove_duplicates", "mkgb_propagate", "mkgb_update",
+           "mkgb_counters"]
 
 _lib = None
 
@@ -85,6 +86,8 @@ def load_library(path: str = LIB_PATH):
     lib.mkgb_set_launch.argtypes = [vp, i32, i32, i32]
     lib.mkgb_autotune.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(f32)]
     lib.mkgb_probe_peak.argtypes = [vp, i32, C.POINTER(C.c_double)]
+    lib.mkgb_clean_seeds.argtypes = [vp, i32, vp, vp, i32]
+    lib.mkgb_remove_duplicates.argtypes = [vp, i32, i32, vp, vp, i32, f32, vp, i32]
     lib.mkgb_propagate.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, i32]
     lib.mkgb_update.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32]
     lib.mkgb_counters.argtypes = [vp, i32, vp]
@@ -189,7 +192,7 @@ class Context:
                    float(params["dphi_min"]), float(params["dphi_max"]), float(params["score_hit"]),
                    float(params["score_hole"]), float(params.get("barrel_eta_max", self.barrel_eta_max)),
                    int(params["material"]), int(params.get("precision", 0)),
-                   float(params.get("kappa_fp64", 0.0)))
+                   float(params.get("kappa_fp64", 0.0)), float(params.get("fit_outlier_chi2", 0.0)))
         self._check(self.lib.mkgb_set_params(self.h, C.byref(p)), "mkgb_set_params")
 
     # ---- data
@@ -313,6 +316,21 @@ class Context:
         r = C.c_double(0.0)
         self._check(self.lib.mkgb_probe_peak(self.h, int(kind), C.byref(r)), "mkgb_probe_peak")
         return r.value
+
+    def clean_seeds(self, seed_hits, keep_out):
+        """mkgb_clean_seeds: keep flags (written in place)."""
+        args = [_ptr(seed_hits, np.int32), _ptr(keep_out, np.int32, True)]
+        self._check(self.lib.mkgb_clean_seeds(self.h, int(seed_hits.shape[0]), *[p for p, _ in args],
+                                              _same(*[d for _, d in args])), "mkgb_clean_seeds")
+        return keep_out
+
+    def remove_duplicates(self, hits, score, keep_out, min_hits: int = 0, frac: float = 0.5):
+        """mkgb_remove_duplicates: keep flags over the rows of hits (written in place)."""
+        args = [_ptr(hits, np.int32), _ptr(score, np.float32), _ptr(keep_out, np.int32, True)]
+        self._check(self.lib.mkgb_remove_duplicates(self.h, int(hits.shape[0]), int(hits.shape[1]), args[0][0],
+                                                    args[1][0], int(min_hits), float(frac), args[2][0],
+                                                    _same(*[d for _, d in args])), "mkgb_remove_duplicates")
+        return keep_out
 
     def propagate(self, layers, p_in, c_in, p_out, c_out, crossed):
         args = [_ptr(layers, np.int32), _ptr(p_in, np.float32), _ptr(c_in, np.float32), _ptr(p_out, np.float32, True),

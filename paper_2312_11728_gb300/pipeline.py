@@ -56,6 +56,29 @@ def outer_fit_inputs(fi: FitInputs, n_skip: int) -> FitInputs:
     return FitInputs(L, H, fi.p0, fi.c0, fi.event)
 
 
+def plant_wrong_hits(batch: Batch, fi: FitInputs, frac: float, seed: int):
+    """Known assignments with wrong hits planted: for a fraction of the tracks one listed hit
+    (not the first) is replaced by a random hit of the same layer and event (host bookkeeping
+    for the outlier rejection's tests).  Returns the new hit lists and the (track, step) swaps."""
+    rng = np.random.default_rng(seed)
+    hits = fi.hits.copy()
+    L = batch.n_layers
+    swaps = []
+    for i in np.nonzero(rng.random(hits.shape[0]) < frac)[0]:
+        n = int((fi.layers[i] >= 0).sum())
+        if n < 4:
+            continue
+        j = int(rng.integers(1, n))
+        e, l = int(fi.event[i]), int(fi.layers[i, j])
+        lo, hi = batch.hit_off[e * L + l], batch.hit_off[e * L + l + 1]
+        h = int(rng.integers(lo, hi))
+        if h == hits[i, j]:
+            continue
+        hits[i, j] = h
+        swaps.append((i, j))
+    return hits, swaps
+
+
 def to_device(a, device):
     import torch
     return torch.from_numpy(np.ascontiguousarray(a)).to(device)

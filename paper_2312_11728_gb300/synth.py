@@ -163,7 +163,7 @@ def default_params(**kw) -> dict:
     """Search parameters (Sec. 3.2 IterationParams / IterationLayerConfig), one set for all layers."""
     p = dict(chi2_cut=30.0, max_cands=6, max_holes=3, win_nsigma=3.5,
              deta_min=0.002, deta_max=0.1, dphi_min=0.002, dphi_max=0.1,
-             score_hit=4.0, score_hole=8.0, material=1, precision=0, kappa_fp64=2.0 ** 24)
+             score_hit=4.0, score_hole=8.0, material=1, precision=0, kappa_fp64=2.0 ** 24, fit_outlier_chi2=0.0)
     p.update(kw)
     return p
 

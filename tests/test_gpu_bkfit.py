@@ -139,3 +139,32 @@ def test_backward_fit_full_size_sampled(lib):
         fh["p"][s].astype(np.float64), fh["c"][s].astype(np.float64), 100.0)
     rep = PR.compare_fit({k: v[s] for k, v in bh.items()}, r, mask=fh["status"][s] == 0)
     assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0, rep
+
+
+def test_fits_with_outlier_rejection_match_oracle(lib):
+    """Known assignments with wrong hits planted in 30% of the tracks, fitted forwards and then
+    backwards with the outlier cut at 30: the same hits rejected and the same results as the
+    oracle's fits, on the tracks without a chi2 within 1e-3 of the cut."""
+    g, batch = _workload("phase2_small")
+    params = dict(S.default_params(), fit_outlier_chi2=30.0)
+    fi0 = pipeline.fit_inputs(batch)
+    bad, swaps = pipeline.plant_wrong_hits(batch, fi0, 0.3, 9)
+    assert len(swaps) > 0.2 * fi0.layers.shape[0]
+    fi = pipeline.FitInputs(fi0.layers, bad, fi0.p0, fi0.c0, fi0.event)
+    ctx, _, f, b = _forward_then_backward(g, batch, params, fi=fi)
+    orc = oracle.Oracle(g, params)
+    X, V = batch.hit_xyz.astype(np.float64), batch.hit_cov.astype(np.float64)
+    rf = orc.fit_batch(fi.layers, fi.hits, X, V, fi.p0, fi.c0)
+    rep = PR.compare_fit(f, rf, mask=rf["near_cut"] == 0)
+    assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0, rep
+    assert rep["n"] > 0.95 * fi.layers.shape[0]
+    rb = orc.bkfit_batch(fi.layers, fi.hits, X, V, f["p"].astype(np.float64), f["c"].astype(np.float64), 100.0)
+    m = (f["status"] == 0) & (rf["near_cut"] == 0) & (rb["near_cut"] == 0)
+    rep = PR.compare_fit(b, rb, mask=m)
+    assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0, rep
+    # the planted hits are gone: the forward fit used one update fewer on the swapped tracks
+    ref = orc.fit_batch(fi0.layers, fi0.hits, X, V, fi0.p0, fi0.c0, outlier_chi2=0.0)
+    sw = np.zeros(fi.layers.shape[0], bool)
+    sw[[i for i, _ in swaps]] = True
+    ok = (rf["status"] == 0) & (ref["status"] == 0)
+    assert np.mean((ref["nupd"] - rf["nupd"])[ok & sw] == 1) > 0.9
