@@ -41,17 +41,23 @@ class Layer(C.Structure):
                 ("sig", C.c_double * 3), ("eta_lo", C.c_double), ("eta_hi", C.c_double)]
 
 
+class Modules(C.Structure):
+    _fields_ = [("n", C.c_int), ("c", C.POINTER(C.c_double)), ("nrm", C.POINTER(C.c_double)),
+                ("hit_mod", C.POINTER(C.c_int))]
+
+
 class Geom(C.Structure):
     _fields_ = [("bz", C.c_double), ("barrel_eta_max", C.c_double), ("n_layers", C.c_int),
                 ("n_regions", C.c_int), ("layers", C.POINTER(Layer)), ("plan", C.POINTER(C.c_int)),
-                ("plan_off", C.POINTER(C.c_int))]
+                ("plan_off", C.POINTER(C.c_int)), ("mods", C.POINTER(Modules))]
 
 
 class Params(C.Structure):
     _fields_ = [("chi2_cut", C.c_double), ("win_nsigma", C.c_double), ("deta_min", C.c_double),
                 ("deta_max", C.c_double), ("dphi_min", C.c_double), ("dphi_max", C.c_double),
                 ("score_hit", C.c_double), ("score_hole", C.c_double), ("max_cands", C.c_int),
-                ("max_holes", C.c_int), ("material", C.c_int), ("binned", C.c_int)]
+                ("max_holes", C.c_int), ("material", C.c_int), ("binned", C.c_int),
+                ("score_overlap", C.c_double)]
 
 
 class Tie(C.Structure):
@@ -66,7 +72,7 @@ class BuildOut(C.Structure):
                 ("nfound", C.POINTER(C.c_int)), ("nholes", C.POINTER(C.c_int)),
                 ("hits", C.POINTER(C.c_int)), ("max_plan", C.c_int), ("tie_step", C.POINTER(C.c_int)),
                 ("region", C.POINTER(C.c_int)), ("start", C.POINTER(C.c_int)),
-                ("counters", C.POINTER(C.c_longlong))]
+                ("counters", C.POINTER(C.c_longlong)), ("ovl", C.POINTER(C.c_int))]
 
 
 def _p(a, t=C.c_double):
@@ -95,6 +101,8 @@ def lib():
             _lib.orc_helix.argtypes = [C.c_double, d, C.c_double, d]
             _lib.orc_jacobian_fixed_s.argtypes = [C.c_double, d, C.c_double, d]
             _lib.orc_build_event.restype = C.c_int
+            _lib.orc_path_plane.restype = C.c_int
+            _lib.orc_propagate_plane.restype = C.c_int
             del i
     return _lib
 
@@ -130,11 +138,48 @@ class Oracle:
         self.params = p
         self.P = Params(p["chi2_cut"], p["win_nsigma"], p["deta_min"], p["deta_max"], p["dphi_min"],
                         p["dphi_max"], p["score_hit"], p["score_hole"], int(p["max_cands"]),
-                        int(p["max_holes"]), int(p["material"]), int(p.get("binned", 1)))
+                        int(p["max_holes"]), int(p["material"]), int(p.get("binned", 1)),
+                        float(p["score_overlap"]))
 
     @property
     def gp(self):
         return C.byref(self.g)
+
+    def set_modules(self, mod_c, mod_n, hit_mod):
+        """Module planes (Sec. 3.1: position and normal) and the module of every global hit id
+        (-1: on the layer's own surface) for the following calls; None clears them."""
+        if mod_c is None:
+            self._mods = None
+            self.g.mods = None
+            return
+        self._mod_arrays = (np.ascontiguousarray(mod_c, np.float64), np.ascontiguousarray(mod_n, np.float64),
+                            np.ascontiguousarray(hit_mod, np.int32))
+        c, n, h = self._mod_arrays
+        self._mods = Modules(int(c.shape[0]), _p(c), _p(n), _p(h, C.c_int))
+        self.g.mods = C.pointer(self._mods)
+
+    def path_plane(self, p, c, n):
+        """Crossing of the helix from p with the module plane n.(x - c) = 0 nearest to p."""
+        s, m = C.c_double(0.0), C.c_double(0.0)
+        ok = self.lib.orc_path_plane(C.c_double(self.geom.bz), _p(np.ascontiguousarray(p, np.float64)),
+                                     _p(np.ascontiguousarray(c, np.float64)), _p(np.ascontiguousarray(n, np.float64)),
+                                     C.byref(s), C.byref(m))
+        return bool(ok), s.value, m.value
+
+    def jacobian_plane(self, p, s, n):
+        J = np.zeros(36)
+        self.lib.orc_jacobian_plane(C.c_double(self.geom.bz), _p(np.ascontiguousarray(p, np.float64)),
+                                    C.c_double(s), _p(np.ascontiguousarray(n, np.float64)), _p(J))
+        return J.reshape(6, 6)
+
+    def propagate_plane(self, p, c21, c, n):
+        """Step to a module plane (no material): (reached, p', C', s)."""
+        po, co, s = np.zeros(6), np.zeros(21), C.c_double(0.0)
+        r = self.lib.orc_propagate_plane(C.c_double(self.geom.bz), _p(np.ascontiguousarray(p, np.float64)),
+                                         _p(np.ascontiguousarray(c21, np.float64)),
+                                         _p(np.ascontiguousarray(c, np.float64)),
+                                         _p(np.ascontiguousarray(n, np.float64)), _p(po), _p(co), C.byref(s))
+        return bool(r), po, co, s.value
 
     # ---- single steps (float64 numpy in/out)
     def helix(self, p, s):
@@ -301,14 +346,7 @@ class Oracle:
         cv = np.ascontiguousarray(cov, np.float64)
         sh = np.ascontiguousarray(seed_hits, np.int32)
         sl = np.ascontiguousarray(seed_layers, np.int32)
-        res = dict(params=np.zeros((S, 6)), cov=np.zeros((S, 21)), score=np.zeros(S), chi2=np.zeros(S),
-                   nfound=np.zeros(S, np.int32), nholes=np.zeros(S, np.int32),
-                   hits=np.zeros((S, mp), np.int32), tie_step=np.zeros(S, np.int32),
-                   region=np.zeros(S, np.int32), start=np.zeros(S, np.int32), counters=np.zeros(4, np.int64))
-        out = BuildOut(_p(res["params"]), _p(res["cov"]), _p(res["score"]), _p(res["chi2"]),
-                       _p(res["nfound"], C.c_int), _p(res["nholes"], C.c_int), _p(res["hits"], C.c_int), mp,
-                       _p(res["tie_step"], C.c_int), _p(res["region"], C.c_int), _p(res["start"], C.c_int),
-                       _p(res["counters"], C.c_longlong))
+        res, out = _build_out(S, mp)
         rc = self.lib.orc_build_event(self.gp, C.byref(self.P), C.byref(self.tie), _p(lo, C.c_longlong), _p(x), _p(cv),
                                       S, _p(sh, C.c_int), _p(sl, C.c_int), C.byref(out))
         if rc != 0:
@@ -359,11 +397,12 @@ def _build_out(S, mp):
     res = dict(params=np.zeros((S, 6)), cov=np.zeros((S, 21)), score=np.zeros(S), chi2=np.zeros(S),
                nfound=np.zeros(S, np.int32), nholes=np.zeros(S, np.int32),
                hits=np.zeros((S, mp), np.int32), tie_step=np.zeros(S, np.int32),
-               region=np.zeros(S, np.int32), start=np.zeros(S, np.int32), counters=np.zeros(4, np.int64))
+               region=np.zeros(S, np.int32), start=np.zeros(S, np.int32), counters=np.zeros(4, np.int64),
+               ovl=np.zeros((S, mp), np.int32))
     out = BuildOut(_p(res["params"]), _p(res["cov"]), _p(res["score"]), _p(res["chi2"]),
                    _p(res["nfound"], C.c_int), _p(res["nholes"], C.c_int), _p(res["hits"], C.c_int), mp,
                    _p(res["tie_step"], C.c_int), _p(res["region"], C.c_int), _p(res["start"], C.c_int),
-                   _p(res["counters"], C.c_longlong))
+                   _p(res["counters"], C.c_longlong), _p(res["ovl"], C.c_int))
     return res, out
 
 

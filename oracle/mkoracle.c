@@ -405,6 +405,102 @@ int orc_propagate_backward(const orc_geom* g, int layer, const double p[6], cons
     return 1;
 }
 
+/* ------------------------------------------------------------------ module planes (Sec. 3.1)
+ * The Phase-2 modules are flat and some are tilted: a hit on a module is measured on the plane
+ * through the module's position c with unit normal n.  The state is taken from the layer's
+ * reference surface (cylinder or disk: window, material and binning) to that plane by the
+ * helix, with the Jacobian of the plane-to-plane map; the step is a few millimetres long and
+ * crosses no material. */
+
+#define PLANE_SMAX 10.0      /* cm: largest |s| of the step from the reference surface to a module */
+#define PLANE_MIN_COS 1e-3   /* smallest |n . dx/ds| (dx/ds per transverse path) of an accepted crossing */
+
+/* g(s) = n . (x(s) - c) along the helix from p, and dg/ds = n . (cos phi', sin phi', cot theta). */
+static double plane_gap(double bz, const double p[6], const double c[3], const double n[3], double s, double* dg) {
+    double q[6];
+    orc_helix(bz, p, s, q);
+    *dg = n[0] * cos(q[4]) + n[1] * sin(q[4]) + n[2] * cos(q[5]) / sin(q[5]);
+    return n[0] * (q[0] - c[0]) + n[1] * (q[1] - c[1]) + n[2] * (q[2] - c[2]);
+}
+
+/* Crossing of the helix with the plane n.(x - c) = 0 nearest to the state: Newton on g(s) from
+ * the tangent-line root, to |ds| < 1e-13 (1 + |s|).  Returns 1 with s, or 0 if Newton does not
+ * converge in 50 iterations, |s| > PLANE_SMAX or the crossing is grazing (|dg/ds| < PLANE_MIN_COS).
+ * margin: relative distance of the last two decisions from their thresholds. */
+int orc_path_plane(double bz, const double p[6], const double c[3], const double n[3], double* s_out,
+                   double* margin) {
+    double dg, g0 = plane_gap(bz, p, c, n, 0.0, &dg);
+    *margin = INFINITY;
+    if (dg == 0.0) return 0;
+    double s = -g0 / dg;
+    int ok = 0;
+    for (int it = 0; it < 50 && !ok; ++it) {
+        double gv = plane_gap(bz, p, c, n, s, &dg);
+        if (dg == 0.0 || !isfinite(s)) return 0;
+        double ds = -gv / dg;
+        s += ds;
+        ok = fabs(ds) < 1e-13 * (1.0 + fabs(s));
+    }
+    if (!ok) return 0;
+    plane_gap(bz, p, c, n, s, &dg);
+    *margin = fmin(fabs(fabs(s) - PLANE_SMAX) / PLANE_SMAX, fabs(fabs(dg) - PLANE_MIN_COS) / PLANE_MIN_COS);
+    *s_out = s;
+    return fabs(s) <= PLANE_SMAX && fabs(dg) >= PLANE_MIN_COS;
+}
+
+/* Jacobian of the map to the plane: J = A + (df/ds)(ds/dp), ds/dp = -(n . A_pos) / (n . df/ds). */
+void orc_jacobian_plane(double bz, const double p[6], double s, const double n[3], double J[36]) {
+    double A[36], q[6];
+    orc_jacobian_fixed_s(bz, p, s, A);
+    orc_helix(bz, p, s, q);
+    double om = -C_LIGHT * bz * p[3];
+    double dfds[6] = {cos(q[4]), sin(q[4]), cos(q[5]) / sin(q[5]), 0.0, om, 0.0};
+    double gs = n[0] * dfds[0] + n[1] * dfds[1] + n[2] * dfds[2];
+    for (int j = 0; j < 6; ++j) {
+        double gp = n[0] * A[0 * 6 + j] + n[1] * A[1 * 6 + j] + n[2] * A[2 * 6 + j];
+        for (int i = 0; i < 6; ++i) J[i * 6 + j] = A[i * 6 + j] - dfds[i] * gp / gs;
+    }
+}
+
+/* Step to a module plane: crossing, new parameters, J C J^T (no material).  1 reached, 0 not. */
+int orc_propagate_plane(double bz, const double p[6], const double C[21], const double c[3],
+                        const double n[3], double pout[6], double Cout[21], double* s_out) {
+    double s, m, J[36];
+    if (!orc_path_plane(bz, p, c, n, &s, &m)) return 0;
+    orc_jacobian_plane(bz, p, s, n, J);
+    orc_helix(bz, p, s, pout);
+    orc_transport(J, C, Cout);
+    pout[4] = wrap_phi(pout[4]);
+    *s_out = s;
+    return 1;
+}
+
+/* Module of a global hit id (-1: the layer's own surface, or no module table). */
+static int hit_module(const orc_geom* g, long long id) {
+    return g->mods ? g->mods->hit_mod[id] : -1;
+}
+
+/* The state on the surface where hit id is measured: its module's plane, or the reference
+ * surface's state itself for a hit without a module.  0 if the plane is not reached.
+ * margin (may be NULL) as orc_path_plane. */
+static int at_hit_surface(const orc_geom* g, long long id, const double p[6], const double C[21], double q[6],
+                          double Cq[21], double* margin) {
+    int m = hit_module(g, id);
+    if (margin) *margin = INFINITY;
+    if (m < 0) {
+        memcpy(q, p, 6 * sizeof(double));
+        memcpy(Cq, C, 21 * sizeof(double));
+        return 1;
+    }
+    const double* c = &g->mods->c[3 * m];
+    const double* n = &g->mods->nrm[3 * m];
+    double s, mg;
+    int r = orc_path_plane(g->bz, p, c, n, &s, &mg);
+    if (margin) *margin = mg;
+    if (!r) return 0;
+    return orc_propagate_plane(g->bz, p, C, c, n, q, Cq, &s);
+}
+
 /* ------------------------------------------------------------------ hit selection */
 
 static void local_cov(const orc_layer* L, double phi, double V[6]) {
@@ -662,16 +758,18 @@ void orc_fit_batch(const orc_geom* g, int material, int n, int max_steps, const 
             memcpy(Cq, Cp, sizeof(Cq));
             int h = hits[(long long)i * max_steps + j];
             if (h >= 0) {
-                double x2;
+                /* a module hit is used on its module's plane (not reached: status 1) */
+                double x2, ph[6], Ch[21];
+                if (!at_hit_surface(g, h, pp, Cp, ph, Ch, NULL)) { st = 1; break; }
                 if (outlier_chi2 > 0.0) {   /* outlier rejection: a hit above the cut is not used */
-                    if (!orc_chi2(pp, Cp, &xyz[3 * (long long)h], &cov[6 * (long long)h], &x2)) {
+                    if (!orc_chi2(ph, Ch, &xyz[3 * (long long)h], &cov[6 * (long long)h], &x2)) {
                         st = 3;
                         break;
                     }
                     if (fabs(x2 - outlier_chi2) < 1e-3 * outlier_chi2) near = 1;
                     if (x2 > outlier_chi2) continue;
                 }
-                if (!orc_update(pp, Cp, &xyz[3 * (long long)h], &cov[6 * (long long)h], 1, q, Cq, &x2)) {
+                if (!orc_update(ph, Ch, &xyz[3 * (long long)h], &cov[6 * (long long)h], 1, q, Cq, &x2)) {
                     st = 3;
                     break;
                 }
@@ -787,6 +885,7 @@ typedef struct {
     double score, chi2;
     int nfound, nholes, stopped;
     int hist[ORC_MAX_PLAN];
+    int ovl[ORC_MAX_PLAN];   /* overlap hit id per plan step, -1 none */
 } cand_t;
 
 enum { K_HIT = 0, K_MISS = 1, K_SKIP = 2, K_STOP = 3, K_CARRY = 4 };
@@ -795,6 +894,7 @@ typedef struct {
     double score, chi2;
     int parent, kind;
     long long gid;
+    long long ovl;   /* overlap hit picked up with the hit gid, -1 none */
 } child_t;
 
 /* Order of children: score descending, then parent slot ascending, then hit children
@@ -955,7 +1055,7 @@ typedef struct {
     cand_t *cur, *nxt;
     double (*pp)[6];
     double (*CC)[21];
-    childvec kids, amb;
+    childvec kids, amb, mh;
     idvec ids;
 } search_ws;
 
@@ -966,12 +1066,13 @@ static void ws_init(search_ws* w) {
     w->CC = malloc(ORC_MAX_CANDS * sizeof(*w->CC));
     w->kids = (childvec){0, 0, 0};
     w->amb = (childvec){0, 0, 0};
+    w->mh = (childvec){0, 0, 0};
     w->ids = (idvec){0, 0, 0};
 }
 
 static void ws_free(search_ws* w) {
     free(w->cur); free(w->nxt); free(w->pp); free(w->CC);
-    free(w->kids.v); free(w->amb.v); free(w->ids.v);
+    free(w->kids.v); free(w->amb.v); free(w->mh.v); free(w->ids.v);
 }
 
 /* Combinatorial search of one track (Sec. 2.2) from the state in w->cur[0] through plan steps
@@ -999,7 +1100,10 @@ static void search_track(const orc_geom* g, const orc_params* P, const orc_tie* 
     cur[0].nfound = nfound0;
     cur[0].nholes = 0;
     cur[0].stopped = 0;
-    for (int t = 0; t < ORC_MAX_PLAN; ++t) cur[0].hist[t] = ORC_PRE;
+    for (int t = 0; t < ORC_MAX_PLAN; ++t) {
+        cur[0].hist[t] = ORC_PRE;
+        cur[0].ovl[t] = -1;
+    }
 
     for (int t = start; t < plan_len; ++t) {
         const int layer = plan[t];
@@ -1009,7 +1113,7 @@ static void search_track(const orc_geom* g, const orc_params* P, const orc_tie* 
         w->amb.n = 0;
         for (int c = 0; c < ncur; ++c) {
             cand_t* cd = &cur[c];
-            child_t ch = {cd->score, 0.0, c, K_CARRY, -1};
+            child_t ch = {cd->score, 0.0, c, K_CARRY, -1, -1};
             if (cd->stopped) { push_child(&w->kids, ch); continue; }
             double s, em;
             int r;
@@ -1031,6 +1135,9 @@ static void search_track(const orc_geom* g, const orc_params* P, const orc_tie* 
             window_hits(P, L, layer, layer_off, &ev, wn, &w->ids);
             qsort(w->ids.v, w->ids.n, sizeof(long long), cmp_ll);
             double me = T->win_abs + T->win_rel * wn[2], mp = T->win_abs + T->win_rel * wn[3];
+            const int k0 = w->kids.n, a0 = w->amb.n;
+            int amb_mod = 0;
+            w->mh.n = 0;
             for (int q = 0; q < w->ids.n; ++q) {
                 long long id = w->ids.v[q];
                 ctr[3]++;
@@ -1040,14 +1147,50 @@ static void search_track(const orc_geom* g, const orc_params* P, const orc_tie* 
                 int near_e = fabs(de - wn[2]) < me, near_p = fabs(dp - wn[3]) < mp;
                 int near = (near_e && dp <= wn[3] + mp) || (near_p && de <= wn[2] + me);
                 if (!in && !near) continue;
-                double x2;
-                if (!orc_chi2(pp[c], CC[c], &xyz[3 * id], &cov[6 * id], &x2)) continue;
+                /* a module hit is tested on its module's plane (Sec. 3.1 module vectors) */
+                double x2, ph[6], Ch[21], hm;
+                int on = at_hit_surface(g, id, pp[c], CC[c], ph, Ch, &hm);
+                if (hm < T->edge_rel) tie = 1;
+                if (!on) continue;
+                if (!orc_chi2(ph, Ch, &xyz[3 * id], &cov[6 * id], &x2)) continue;
                 if (in) ctr[1]++;
-                child_t hc = {cd->score + P->score_hit - x2, x2, c, K_HIT, id};
-                if (in && x2 < P->chi2_cut) push_child(&w->kids, hc);
+                child_t hc = {cd->score + P->score_hit - x2, x2, c, K_HIT, id, -1};
+                if (in && x2 < P->chi2_cut) {
+                    push_child(&w->kids, hc);
+                    if (hit_module(g, id) >= 0) push_child(&w->mh, hc);
+                }
                 if ((near || fabs(x2 - P->chi2_cut) < T->chi2_rel * P->chi2_cut) &&
-                    x2 < P->chi2_cut * (1.0 + T->chi2_rel))
+                    x2 < P->chi2_cut * (1.0 + T->chi2_rel)) {
                     push_child(&w->amb, hc);
+                    if (hit_module(g, id) >= 0) amb_mod = 1;
+                }
+            }
+            /* overlap hit (Sec. 2.2: a single additional detector-overlap hit per layer): a
+               child taking module hit h also picks up the best accepted hit (chi2, then id) of
+               the candidate's window that lies on another module, and scores score_overlap
+               more.  With b1 the best accepted module hit and b2 the best one on a module other
+               than b1's, that hit is b1 if h is not on b1's module, else b2; every module-hit
+               child has one exactly when b2 exists (the accepted hits span two modules). */
+            if (w->mh.n > 0) {
+                childvec* mh = &w->mh;
+                qsort(mh->v, mh->n, sizeof(child_t), child_cmp);   /* same parent: chi2 asc, id asc */
+                long long b1 = mh->v[0].gid, b2 = -1;
+                for (int q = 1; q < mh->n && b2 < 0; ++q)
+                    if (hit_module(g, mh->v[q].gid) != hit_module(g, b1)) b2 = mh->v[q].gid;
+                if (b2 >= 0) {
+                    /* which hit is picked up is a chi2 comparison: near-equal chi2, or an
+                       ambiguous hit at the window edge or the chi2 cut, may go either way */
+                    for (int q = 1; q < mh->n; ++q)
+                        if (mh->v[q].chi2 - mh->v[q - 1].chi2 < gap_tol(T, mh->v[q].chi2)) tie = 1;
+                    for (childvec* cv = &w->kids; cv; cv = (cv == &w->kids) ? &w->amb : NULL)
+                        for (int q = (cv == &w->kids) ? k0 : a0; q < cv->n; ++q) {
+                            child_t* k = &cv->v[q];
+                            if (k->kind != K_HIT || hit_module(g, k->gid) < 0) continue;
+                            k->score += P->score_overlap;
+                            k->ovl = hit_module(g, k->gid) != hit_module(g, b1) ? b1 : b2;
+                        }
+                }
+                if (amb_mod) tie = 1;
             }
             if (cd->nholes < P->max_holes) {
                 ch.kind = K_MISS;
@@ -1073,12 +1216,15 @@ static void search_track(const orc_geom* g, const orc_params* P, const orc_tie* 
             child_t* k = &kids->v[q];
             if (k->kind == K_SKIP || k->kind == K_CARRY) continue;
             double Vc[6];
+            const double* Cs = CC[k->parent];
+            double ph[6], Ch[21];
             if (k->kind == K_HIT) {
                 memcpy(Vc, &cov[6 * k->gid], sizeof(Vc));
+                if (at_hit_surface(g, k->gid, pp[k->parent], CC[k->parent], ph, Ch, NULL)) Cs = Ch;
             } else {
                 local_cov(L, atan2(pp[k->parent][1], pp[k->parent][0]), Vc);
             }
-            if (cond_frob(CC[k->parent], Vc) > T->kappa) tie = 1;
+            if (cond_frob(Cs, Vc) > T->kappa) tie = 1;
         }
         if (tie && out->tie_step[si] < 0) out->tie_step[si] = t;
 
@@ -1088,20 +1234,22 @@ static void search_track(const orc_geom* g, const orc_params* P, const orc_tie* 
             cand_t* par = &cur[k->parent];
             cand_t* nc = &nxt[nn];
             memcpy(nc->hist, par->hist, sizeof(nc->hist));
+            memcpy(nc->ovl, par->ovl, sizeof(nc->ovl));
             nc->score = k->score;
             nc->chi2 = par->chi2;
             nc->nfound = par->nfound;
             nc->nholes = par->nholes;
             nc->stopped = par->stopped;
             if (k->kind == K_HIT) {
-                double x2;
-                if (!orc_update(pp[k->parent], CC[k->parent], &xyz[3 * k->gid], &cov[6 * k->gid], 1,
-                                nc->p, nc->C, &x2))
+                double x2, ph[6], Ch[21];
+                if (!at_hit_surface(g, k->gid, pp[k->parent], CC[k->parent], ph, Ch, NULL) ||
+                    !orc_update(ph, Ch, &xyz[3 * k->gid], &cov[6 * k->gid], 1, nc->p, nc->C, &x2))
                     continue;
                 ctr[2]++;
                 nc->chi2 += x2;
                 nc->nfound++;
                 nc->hist[t] = (int)k->gid;
+                nc->ovl[t] = (int)k->ovl;
             } else if (k->kind == K_MISS) {
                 memcpy(nc->p, pp[k->parent], sizeof(nc->p));
                 memcpy(nc->C, CC[k->parent], sizeof(nc->C));
@@ -1140,11 +1288,15 @@ static void search_track(const orc_geom* g, const orc_params* P, const orc_tie* 
     out->nfound[si] = cur[0].nfound;
     out->nholes[si] = cur[0].nholes;
     for (int t = 0; t < plan_len && t < out->max_plan; ++t) oh[t] = cur[0].hist[t];
+    if (out->ovl)
+        for (int t = 0; t < plan_len && t < out->max_plan; ++t) out->ovl[(long long)si * out->max_plan + t] = cur[0].ovl[t];
 }
 
 static void clear_out(orc_build_out* out, int si) {
     int* oh = &out->hits[(long long)si * out->max_plan];
     for (int t = 0; t < out->max_plan; ++t) oh[t] = ORC_PRE;
+    if (out->ovl)
+        for (int t = 0; t < out->max_plan; ++t) out->ovl[(long long)si * out->max_plan + t] = -1;
     out->tie_step[si] = -1;
     out->score[si] = -INFINITY;
     out->chi2[si] = 0.0;
@@ -1173,6 +1325,10 @@ int orc_build_event(const orc_geom* g, const orc_params* P, const orc_tie* T,
         }
         out->region[si] = -1;
         out->start[si] = -1;
+        /* the seed fit takes hits on the layers' own surfaces: a seed with a module hit fails */
+        if (hit_module(g, seed_hits[3 * si]) >= 0 || hit_module(g, seed_hits[3 * si + 1]) >= 0 ||
+            hit_module(g, seed_hits[3 * si + 2]) >= 0)
+            continue;
         if (!orc_seed(g, P->material, h, V, &seed_layers[3 * si], w.cur[0].p, w.cur[0].C, pinit)) continue;
         int region = orc_select_region(g, w.cur[0].p);
         int start = plan_start(g, region, seed_layers[3 * si + 2]);

@@ -42,18 +42,32 @@ typedef struct {
     double eta_lo, eta_hi;
 } orc_layer;
 
+/* Flat detector modules (Sec. 3.1: module position, normal and phi-direction vectors, needed
+ * for the Phase-2 tilted modules and for picking up hits of overlapping modules).  A module is
+ * the plane through c with unit normal n; its phi-direction lies in the plane and is carried by
+ * the hit covariance, so the filter needs c and n only.  hit_mod gives each global hit id its
+ * module (-1: the hit lies on its layer's own cylinder or disk). */
+typedef struct {
+    int n;
+    const double* c;       /* n x 3 [cm] */
+    const double* nrm;     /* n x 3 unit normals */
+    const int* hit_mod;    /* per global hit id */
+} orc_modules;
+
 typedef struct {
     double bz, barrel_eta_max;
     int n_layers, n_regions;
     const orc_layer* layers;
     const int* plan;       /* concatenated layer plans */
     const int* plan_off;   /* n_regions + 1 */
+    const orc_modules* mods;   /* NULL: no module hits */
 } orc_geom;
 
 typedef struct {
     double chi2_cut, win_nsigma, deta_min, deta_max, dphi_min, dphi_max;
     double score_hit, score_hole;
     int max_cands, max_holes, material, binned;
+    double score_overlap;  /* score added to a candidate that picks up an overlap hit */
 } orc_params;
 
 /* near-tie thresholds (selection decisions that finite precision may take either way) */
@@ -83,6 +97,7 @@ typedef struct {
     int* start;         /* S: first plan step of the search */
     long long* counters;/* [0] crossed candidate-layer visits, [1] chi2 evaluations,
                            [2] updates, [3] hits tested against a window */
+    int* ovl;           /* S x max_plan: overlap hit id per plan step, -1 none (may be NULL) */
 } orc_build_out;
 
 /* --- single steps --- */
@@ -100,6 +115,12 @@ int  orc_path_inward(const orc_geom* g, int layer, const double p[6], double* s_
 void orc_reverse(const double p[6], const double C[21], double pr[6], double Cr[21]);
 int  orc_propagate_backward(const orc_geom* g, int layer, const double p[6], const double C[21],
                             int material, double pout[6], double Cout[21], double* s_out);
+/* module planes: crossing nearest to the state, Jacobian, propagation (no material) */
+int  orc_path_plane(double bz, const double p[6], const double c[3], const double n[3], double* s_out,
+                    double* margin);
+void orc_jacobian_plane(double bz, const double p[6], double s, const double n[3], double J[36]);
+int  orc_propagate_plane(double bz, const double p[6], const double C[21], const double c[3],
+                         const double n[3], double pout[6], double Cout[21], double* s_out);
 void orc_window(const orc_layer* L, const orc_params* P, const double p[6], const double C[21],
                 double out[4]);
 void orc_hit_eta_phi(const double m[3], double* eta, double* phi);

@@ -55,6 +55,7 @@ class Geometry:
     plans: list               # list of lists of layer indices, one per tracking region
     bz: float = 3.8
     barrel_eta_max: float = 1.0   # |eta_seed| below this -> region 0, else 1 (+z) / 2 (-z)
+    modules: "Modules | None" = None   # flat modules of the modular layers (None: no module hits)
 
     @property
     def n_layers(self) -> int:
@@ -71,6 +72,24 @@ class Geometry:
     @property
     def max_plan(self) -> int:
         return max(len(p) for p in self.plans)
+
+
+@dataclass
+class Modules:
+    """Flat detector modules (Sec. 3.1: module position, normal and phi-direction vectors): the
+    plane through c with unit normal n; u (the phi-direction) and v = n x u span it, the module
+    covers |u.(x - c)| <= hw, |v.(x - c)| <= hl.  Per modular layer, modules form rings of
+    n_phi staves (centres at phi = j 2pi/n_phi, radius alternating R +- dr so that neighbouring
+    staves overlap in phi) at z centres z_k; rings beyond |z| > z_flat are tilted so that their
+    normal points at the origin (the Phase-2 tilted barrel)."""
+    c: np.ndarray        # float64 [M,3] (float32-representable)
+    n: np.ndarray        # float64 [M,3]
+    u: np.ndarray        # float64 [M,3]
+    v: np.ndarray        # float64 [M,3]
+    hw: np.ndarray       # float64 [M]
+    hl: np.ndarray       # float64 [M]
+    layer: np.ndarray    # int32 [M]
+    grid: dict           # layer -> (first module, n_phi, z centres [K])
 
 
 def _f32(v):
@@ -115,6 +134,119 @@ def disk_z(n=12, z0=125.0, z1=275.0):
 
 def _eta_bins(width, lo, hi):
     return max(8, int(np.ceil((hi - lo) / width)))
+
+
+def add_modules(geom: Geometry, layers, dz=4.8, z_flat=30.0, width=9.0, dr=0.3, overlap=1.08,
+                max_tilt_deg=80.0, sig_window=(0.5, 0.4, 0.5)) -> Geometry:
+    """Makes the given barrel layers modular (Sec. 3.1 module vectors; the Phase-2 tilted barrel):
+    each cylinder of radius R becomes rings of flat staves, and its hits lie on the module planes.
+    The cylinder stays the layer's reference surface (window, material, binning); its window
+    resolution becomes sig_window, the spread of module hits about the cylinder crossing."""
+    cs, ns, us, vs, hws, hls, lay = [], [], [], [], [], [], []
+    grid = {}
+    sig = geom.sig.copy()
+    for l in layers:
+        assert geom.kind[l] == BARREL
+        R, zmax = float(geom.pos[l]), float(geom.hi[l])
+        nphi = int(np.ceil(2 * np.pi * R / width))
+        nphi += nphi % 2
+        K = int(np.floor(zmax / dz))
+        zc = dz * np.arange(-K, K + 1)
+        grid[l] = (len(cs), nphi, zc)
+        dphi = 2 * np.pi / nphi
+        for k in zc:
+            beta = np.arctan2(k, R) if abs(k) > z_flat else 0.0
+            beta = float(np.clip(beta, -np.radians(max_tilt_deg), np.radians(max_tilt_deg)))
+            for j in range(nphi):
+                ph = j * dphi
+                rj = R + (dr if j % 2 == 0 else -dr)
+                rh = np.array([np.cos(ph), np.sin(ph), 0.0])
+                u = np.array([-np.sin(ph), np.cos(ph), 0.0])
+                n = np.cos(beta) * rh + np.array([0.0, 0.0, np.sin(beta)])
+                v = np.cross(n, u)
+                cs.append(rj * rh + np.array([0.0, 0.0, k]))
+                ns.append(n); us.append(u); vs.append(v)
+                hws.append(rj * np.tan(0.5 * dphi) * overlap)
+                # a tilted ring faces the origin: its angular extent seen from there matches the
+                # ring spacing (cos^2 beta dz / R) with 4% overlap
+                hls.append(0.5 * dz * np.cos(beta) * 1.04 if beta != 0.0 else 0.5 * dz * 1.04)
+                lay.append(l)
+        sig[l] = sig_window
+    f = lambda a: _f32(np.array(a))
+    n = f(ns)
+    mods = Modules(f(cs), n / np.linalg.norm(n, axis=1, keepdims=True), np.array(us), np.array(vs),
+                   np.array(hws), np.array(hls), np.array(lay, np.int32), grid)
+    g = Geometry(geom.kind, geom.pos, geom.lo, geom.hi, geom.x_over_x0, _f32(sig), geom.n_eta, geom.n_phi,
+                 geom.eta_lo, geom.eta_hi, [list(p) for p in geom.plans], geom.bz, geom.barrel_eta_max, mods)
+    return g
+
+
+def geometry_phase2_modular(layers=(3, 4, 5), **kw) -> Geometry:
+    """The Phase-2-like tracker with cylinders 3-5 (r = 36, 47, 57 cm) built from flat modules,
+    flat for |z| <= 30 cm and tilted towards the origin beyond (Sec. 3.1: module position, normal
+    and phi-direction; the Phase-2 tilted barrel).  The seeding cylinders 0-2 keep hits on their
+    own surfaces."""
+    return add_modules(geometry_phase2(**kw), layers)
+
+
+def _module_crossings(mods: Modules, layer, x, y, z, psi, th, om):
+    """Crossings of tracks at their cylinder crossing (x, y, z, direction psi, theta, curvature om)
+    with the modules around that point: Newton in the transverse path sigma on
+    n.(X(sigma) - c) = 0 along the circle-centre trajectory, kept if |sigma| < 10 cm and inside
+    the module.  Returns per track up to two (module, sigma, point) in path order."""
+    first, nphi, zc = mods.grid[layer]
+    dphi = 2 * np.pi / nphi
+    j0 = np.round(np.mod(np.arctan2(y, x), 2 * np.pi) / dphi).astype(np.int64)
+    k0 = np.round((z - zc[0]) / (zc[1] - zc[0])).astype(np.int64)
+    cand = []
+    for dj in (-1, 0, 1):
+        for dk in (-1, 0, 1):
+            j = np.mod(j0 + dj, nphi)
+            k = k0 + dk
+            ok = (k >= 0) & (k < zc.size)
+            m = np.where(ok, first + np.clip(k, 0, zc.size - 1) * nphi + j, -1)
+            cand.append(m)
+    cand = np.stack(cand, 1)                       # [T, 9]
+    T = x.size
+    sig = np.full(cand.shape, np.nan)
+    pts = np.zeros(cand.shape + (3,))
+    for q in range(cand.shape[1]):
+        m = cand[:, q]
+        val = m >= 0
+        mm = np.where(val, m, 0)
+        c, n = mods.c[mm], mods.n[mm]
+        sg = np.zeros(T)
+        for _ in range(8):
+            xn, yn, zn, ps = _move(x, y, z, psi, th, om, sg)
+            g = (xn - c[:, 0]) * n[:, 0] + (yn - c[:, 1]) * n[:, 1] + (zn - c[:, 2]) * n[:, 2]
+            dg = np.cos(ps) * n[:, 0] + np.sin(ps) * n[:, 1] + n[:, 2] / np.tan(th)
+            sg = sg - g / np.where(np.abs(dg) > 1e-6, dg, np.nan)
+        xn, yn, zn, _ = _move(x, y, z, psi, th, om, sg)
+        d = np.stack([xn, yn, zn], -1) - c
+        a = np.einsum("ij,ij->i", d, mods.u[mm])
+        b = np.einsum("ij,ij->i", d, mods.v[mm])
+        inside = val & np.isfinite(sg) & (np.abs(sg) < 10.0) & (np.abs(a) <= mods.hw[mm]) & (np.abs(b) <= mods.hl[mm])
+        sig[:, q] = np.where(inside, sg, np.nan)
+        pts[:, q] = np.stack([xn, yn, zn], -1)
+    order = np.argsort(np.where(np.isfinite(sig), sig, np.inf), axis=1)
+    out = []
+    for r in range(2):
+        q = order[:, r]
+        sr = sig[np.arange(T), q]
+        mr = np.where(np.isfinite(sr), cand[np.arange(T), q], -1)
+        out.append((mr, pts[np.arange(T), q]))
+    return out
+
+
+def _module_cov6(mods: Modules, m, sig):
+    """Packed 3x3 covariance of hits on modules m with resolutions (normal, u, v) = sig."""
+    n, u, v = mods.n[m], mods.u[m], mods.v[m]
+    M = (sig[0] ** 2 * n[:, :, None] * n[:, None, :] + sig[1] ** 2 * u[:, :, None] * u[:, None, :]
+         + sig[2] ** 2 * v[:, :, None] * v[:, None, :])
+    return np.stack([M[:, 0, 0], M[:, 1, 0], M[:, 1, 1], M[:, 2, 0], M[:, 2, 1], M[:, 2, 2]], -1)
+
+
+SIG_MODULE = (30e-4, 30e-4, 100e-4)   # (normal, phi-direction u, v): 30 um in u, 100 um in v
 
 
 def geometry_barrel(n_layers=10, zmax=120.0, x_over_x0=0.02, n_eta=32, n_phi=128,
@@ -163,7 +295,8 @@ def default_params(**kw) -> dict:
     """Search parameters (Sec. 3.2 IterationParams / IterationLayerConfig), one set for all layers."""
     p = dict(chi2_cut=30.0, max_cands=6, max_holes=3, win_nsigma=3.5,
              deta_min=0.002, deta_max=0.1, dphi_min=0.002, dphi_max=0.1,
-             score_hit=4.0, score_hole=8.0, material=1, precision=0, kappa_fp64=2.0 ** 24, fit_outlier_chi2=0.0)
+             score_hit=4.0, score_hole=8.0, material=1, precision=0, kappa_fp64=2.0 ** 24, fit_outlier_chi2=0.0,
+             score_overlap=2.0)
     p.update(kw)
     return p
 
@@ -307,6 +440,8 @@ class Event:
     track_truth: np.ndarray    # float64 [T, maxh, 6] state (x,y,z,q/pT,phi,theta) leaving each hit's layer
     seed_hits: np.ndarray      # int32 [S,3]
     seed_track: np.ndarray     # int32 [S]
+    hit_mod: np.ndarray = None     # int32 [H]: module of each hit, -1 on a layer's own surface
+    track_ovl: np.ndarray = None   # int32 [T, maxh]: second hit (an overlapping module) on that layer, -1
 
     @property
     def n_hits(self):
@@ -359,6 +494,10 @@ def simulate_event(geom: Geometry, n_tracks: int, seed: int = 0, event: int = 0,
     t_layers = np.full((n_tracks, maxh), -1, np.int32)
     t_truth = np.zeros((n_tracks, maxh, 6))
     t_xyz = np.zeros((n_tracks, maxh, 3))
+    t_mod = np.full((n_tracks, maxh), -1, np.int64)
+    t_oxyz = np.zeros((n_tracks, maxh, 3))
+    t_omod = np.full((n_tracks, maxh), -1, np.int64)
+    mods = geom.modules
     nh = np.zeros(n_tracks, np.int32)
     alive = np.ones(n_tracks, bool)
 
@@ -394,9 +533,19 @@ def simulate_event(geom: Geometry, n_tracks: int, seed: int = 0, event: int = 0,
                 continue
             xn, yn, zn, psi = xn[ok], yn[ok], zn[ok], psi[ok]
             th = th[ok]
-            k = nh[sel]
-            t_layers[sel, k] = lay
-            t_xyz[sel, k] = np.stack([xn, yn, zn], -1)
+            hit = np.ones(sel.size, bool)
+            if mods is not None and lay in mods.grid:
+                # the hits lie where the track crosses the modules around its cylinder crossing
+                (m1, x1), (m2, x2) = _module_crossings(mods, lay, xn, yn, zn, psi, th, om[ok])
+                hit = m1 >= 0
+                k = nh[sel[hit]]
+                t_mod[sel[hit], k] = m1[hit]
+                t_omod[sel[hit], k] = m2[hit]
+                t_oxyz[sel[hit], k] = x2[hit]
+            selh = sel[hit]
+            k = nh[selh]
+            t_layers[selh, k] = lay
+            t_xyz[selh, k] = x1[hit] if (mods is not None and lay in mods.grid) else np.stack([xn, yn, zn], -1)
             # material: Highland kick at fixed |p|, then mean energy loss
             p = trk.p[sel]
             if material and geom.x_over_x0[lay] > 0:
@@ -417,8 +566,8 @@ def simulate_event(geom: Geometry, n_tracks: int, seed: int = 0, event: int = 0,
             psi = np.mod(psi + np.pi, 2.0 * np.pi) - np.pi
             trk.x[sel], trk.y[sel], trk.z[sel] = xn, yn, zn
             trk.phi[sel], trk.theta[sel], trk.p[sel] = psi, th, p
-            t_truth[sel, k] = np.stack([xn, yn, zn, trk.q[sel] / (p * np.sin(th)), psi, th], -1)
-            nh[sel] += 1
+            t_truth[selh, k] = np.stack([xn, yn, zn, trk.q[sel] / (p * np.sin(th)), psi, th], -1)[hit]
+            nh[selh] += 1
 
     # assemble hits per layer: signal + noise, shuffled within the layer
     if noise_total is not None:
@@ -429,13 +578,40 @@ def simulate_event(geom: Geometry, n_tracks: int, seed: int = 0, event: int = 0,
     else:
         n_noise = np.full(L, 0 if noise_per_layer is None else int(noise_per_layer), np.int64)
 
-    xyz_parts, cov_parts, trk_parts = [], [], []
+    xyz_parts, cov_parts, trk_parts, mod_parts = [], [], [], []
     local_of = np.full((n_tracks, maxh), -1, np.int64)
+    local_ovl = np.full((n_tracks, maxh), -1, np.int64)
     layer_off = np.zeros(L + 1, np.int64)
     for lay in range(L):
         ti, ki = np.nonzero(t_layers == lay)
-        sx, sy, sz = t_xyz[ti, ki, 0], t_xyz[ti, ki, 1], t_xyz[ti, ki, 2]
         nn = int(n_noise[lay])
+        if mods is not None and lay in mods.grid:
+            # primary and overlap hits on their modules, noise uniform over the layer's modules
+            oi, ok_ = np.nonzero((t_layers == lay) & (t_omod >= 0))
+            first, nphi, zc = mods.grid[lay]
+            nm = rng.integers(first, first + nphi * zc.size, nn)
+            ab = rng.uniform(-1.0, 1.0, (2, nn))
+            npos = mods.c[nm] + (ab[0] * mods.hw[nm])[:, None] * mods.u[nm] + (ab[1] * mods.hl[nm])[:, None] * mods.v[nm]
+            pos = np.concatenate([t_xyz[ti, ki], t_oxyz[oi, ok_], npos])
+            mid = np.concatenate([t_mod[ti, ki], t_omod[oi, ok_], nm]).astype(np.int64)
+            owner = np.concatenate([ti, oi, np.full(nn, -1)]).astype(np.int32)
+            if smear:
+                g = rng.standard_normal((3, mid.size))
+                pos = pos + sum((g[a] * SIG_MODULE[a])[:, None] * (mods.n, mods.u, mods.v)[a][mid] for a in range(3))
+            perm = rng.permutation(mid.size)
+            pos, mid, owner = pos[perm], mid[perm], owner[perm]
+            inv = np.empty_like(perm)
+            inv[perm] = np.arange(perm.size)
+            base = layer_off[lay]
+            local_of[ti, ki] = base + inv[: ti.size]
+            local_ovl[oi, ok_] = base + inv[ti.size: ti.size + oi.size]
+            xyz_parts.append(pos)
+            cov_parts.append(_module_cov6(mods, mid, SIG_MODULE))
+            trk_parts.append(owner)
+            mod_parts.append(mid)
+            layer_off[lay + 1] = base + mid.size
+            continue
+        sx, sy, sz = t_xyz[ti, ki, 0], t_xyz[ti, ki, 1], t_xyz[ti, ki, 2]
         u = rng.random((2, nn))
         nphi = -np.pi + 2 * np.pi * u[0]
         if geom.kind[lay] == BARREL:
@@ -461,6 +637,7 @@ def simulate_event(geom: Geometry, n_tracks: int, seed: int = 0, event: int = 0,
         xyz_parts.append(np.stack([ax, ay, az], -1))
         cov_parts.append(cov)
         trk_parts.append(owner)
+        mod_parts.append(np.full(ax.size, -1, np.int64))
         layer_off[lay + 1] = base + ax.size
 
     hit_xyz = np.concatenate(xyz_parts).astype(np.float32) if xyz_parts else np.zeros((0, 3), np.float32)
@@ -470,8 +647,10 @@ def simulate_event(geom: Geometry, n_tracks: int, seed: int = 0, event: int = 0,
     has_seed = nh >= min_hits_seed
     seed_track = np.nonzero(has_seed)[0].astype(np.int32)
     seed_hits = track_hits[seed_track, :3].astype(np.int32)
+    hit_mod = np.concatenate(mod_parts).astype(np.int32) if mod_parts else np.zeros(0, np.int32)
     return Event(hit_xyz, hit_cov, layer_off, hit_track, q, pt, eta, phi0,
-                 track_hits, t_layers, t_truth, seed_hits, seed_track)
+                 track_hits, t_layers, t_truth, seed_hits, seed_track, hit_mod,
+                 np.where(t_layers >= 0, local_ovl, -1).astype(np.int32))
 
 
 @dataclass
@@ -487,6 +666,7 @@ class Batch:
     seed_event: np.ndarray     # int32 [S]
     seed_track: np.ndarray     # int32 [S] event-local track index
     events: list = field(default_factory=list)
+    hit_mod: np.ndarray = None # int32 [H]: module of each hit, -1 on a layer's own surface
 
 
 def concat_events(events, n_layers) -> Batch:
@@ -503,7 +683,8 @@ def concat_events(events, n_layers) -> Batch:
                  np.concatenate(seeds).astype(np.int32) if seeds else np.zeros((0, 3), np.int32),
                  np.concatenate([np.full(ev.seed_hits.shape[0], e, np.int32) for e, ev in enumerate(events)]),
                  np.concatenate([ev.seed_track for ev in events]).astype(np.int32),
-                 list(events))
+                 list(events),
+                 np.concatenate([ev.hit_mod for ev in events]).astype(np.int32))
 
 
 def fit_workload(ev: Event, seed: int = 0, *, sig_pos=0.005, sig_z=0.01, rel_k=0.05,

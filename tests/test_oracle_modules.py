@@ -1,0 +1,259 @@
+"""Pins of the oracle's module planes (Sec. 3.1: module position and normal, the Phase-2 tilted
+modules) and of the overlap-hit pickup (Sec. 2.2: a single additional detector-overlap hit).
+
+The plane step is pinned by what geometry fixes: its crossing lies on the helix and on the plane
+and is the crossing nearest to the state (brute-force scan), a plane z = z_d reproduces the disk
+step's independent closed form, the Jacobian matches central finite differences and obeys the
+chain rule through an intermediate plane.  The search and the fit on simulated modular events
+are pinned by the simulation's truth (which hits, which overlap hits) and by unit pulls."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import parity as PR
+from paper_2312_11728_gb300 import pipeline, synth as S
+
+
+@pytest.fixture(scope="module")
+def geo():
+    return S.geometry_phase2_modular()
+
+
+def _states(rng, n, r=36.0):
+    """States on a cylinder of radius r, moving outward, pT 0.5-20 GeV, |eta| < 2."""
+    phi_pos = rng.uniform(-np.pi, np.pi, n)
+    eta = rng.uniform(-2, 2, n)
+    th = 2 * np.arctan(np.exp(-eta))
+    pt = np.exp(rng.uniform(np.log(0.5), np.log(20.0), n))
+    k = rng.choice([-1.0, 1.0], n) / pt
+    phi = phi_pos + rng.uniform(-0.4, 0.4, n)
+    z = r / np.tan(th)
+    return np.stack([r * np.cos(phi_pos), r * np.sin(phi_pos), z, k, phi, th], -1)
+
+
+def _planes(rng, p):
+    """A tilted plane a few mm from each state: normal in the r-z plane, tilted towards the
+    track's polar direction (as the modules facing the origin are) within +-0.3 rad."""
+    rh = np.array([np.cos(np.arctan2(p[1], p[0])), np.sin(np.arctan2(p[1], p[0])), 0.0])
+    beta = 0.5 * np.pi - p[5] + rng.uniform(-0.3, 0.3)
+    n = np.cos(beta) * rh + np.array([0.0, 0.0, np.sin(beta)])
+    n /= np.linalg.norm(n)
+    c = p[:3] + rng.uniform(-0.5, 0.5) * n + rng.uniform(-1, 1) * np.cross(n, [0, 0, 1.0])
+    return c, n
+
+
+def test_plane_crossing_is_nearest_root(geo):
+    orc = oracle.Oracle(geo)
+    rng = np.random.default_rng(3)
+    P = _states(rng, 60)
+    for p in P:
+        c, n = _planes(rng, p)
+        ok, s, _ = orc.path_plane(p, c, n)
+        assert ok
+        q = orc.helix(p, s)
+        assert abs(np.dot(q[:3] - c, n)) < 1e-10
+        # brute force: every sign change of g(s) = n.(x(s) - c) on a fine grid of [-10, 10]
+        grid = np.linspace(-10, 10, 4001)
+        g = np.array([np.dot(orc.helix(p, t)[:3] - c, n) for t in grid])
+        roots = grid[:-1][np.sign(g[:-1]) != np.sign(g[1:])]
+        assert roots.size >= 1
+        assert abs(abs(s) - np.min(np.abs(roots))) < 6e-3
+
+
+def test_plane_z_equals_disk_step(geo):
+    """The plane z = z_d with normal z-hat is the disk: same path length (s = (z_d - z) tan theta)
+    and the same Jacobian as the disk layer's step."""
+    orc = oracle.Oracle(geo)
+    rng = np.random.default_rng(5)
+    disk = int(np.nonzero((geo.kind == S.DISK) & (geo.pos > 0))[0][0])
+    zd = float(geo.pos[disk])
+    for _ in range(30):
+        p = np.array([rng.uniform(5, 20), rng.uniform(-5, 5), zd - rng.uniform(0.2, 4.0),
+                      rng.choice([-1, 1]) / rng.uniform(1.0, 20.0), rng.uniform(-np.pi, np.pi),
+                      rng.uniform(0.2, 0.6)])
+        ok, s, _ = orc.path_plane(p, [0, 0, zd], [0, 0, 1.0])
+        ok2, s2, _ = orc.path(disk, p)
+        assert ok
+        assert abs(s - (zd - p[2]) * np.tan(p[5])) < 1e-9 * (1 + abs(s))
+        if ok2:
+            assert abs(s - s2) < 1e-9 * (1 + abs(s))
+            np.testing.assert_allclose(orc.jacobian_plane(p, s, [0, 0, 1.0]), orc.jacobian(disk, p, s2),
+                                       rtol=1e-9, atol=1e-12)
+
+
+def _plane_map(orc, p, c, n):
+    ok, s, _ = orc.path_plane(p, c, n)
+    assert ok
+    return orc.helix(p, s)
+
+
+def test_plane_jacobian_finite_differences(geo):
+    orc = oracle.Oracle(geo)
+    rng = np.random.default_rng(7)
+    P = _states(rng, 25)
+    h = np.array([1e-5, 1e-5, 1e-5, 1e-7, 1e-7, 1e-7])
+    for p in P:
+        c, n = _planes(rng, p)
+        ok, s, _ = orc.path_plane(p, c, n)
+        J = orc.jacobian_plane(p, s, n)
+        Jn = np.zeros((6, 6))
+        for j in range(6):
+            e = np.zeros(6)
+            e[j] = h[j]
+            Jn[:, j] = (_plane_map(orc, p + e, c, n) - _plane_map(orc, p - e, c, n)) / (2 * h[j])
+        np.testing.assert_allclose(J, Jn, rtol=1e-5, atol=2e-6)
+
+
+def test_plane_chain_rule(geo):
+    """Two steps through an intermediate plane give the direct step's parameters, and the product
+    of their Jacobians equals the direct Jacobian (all maps between surfaces)."""
+    orc = oracle.Oracle(geo)
+    rng = np.random.default_rng(11)
+    for p in _states(rng, 20):
+        c1, n1 = _planes(rng, p)
+        ok, s1, _ = orc.path_plane(p, c1, n1)
+        q1 = orc.helix(p, s1)
+        c2 = q1[:3] + 0.4 * n1
+        n2 = n1 + np.array([0.05, -0.03, 0.08])
+        n2 /= np.linalg.norm(n2)
+        ok2, s2, _ = orc.path_plane(q1, c2, n2)
+        okd, sd, _ = orc.path_plane(p, c2, n2)
+        assert ok and ok2 and okd
+        q2 = orc.helix(q1, s2)
+        qd = orc.helix(p, sd)
+        np.testing.assert_allclose(q2, qd, rtol=1e-10, atol=1e-10)
+        J12 = orc.jacobian_plane(q1, s2, n2) @ orc.jacobian_plane(p, s1, n1)
+        # the first map's Jacobian is taken on its plane: project out the direction along which
+        # the first plane's state cannot move (n1 . position) by comparing on the plane states
+        Jd = orc.jacobian_plane(p, sd, n2)
+        np.testing.assert_allclose(J12, Jd, rtol=1e-7, atol=1e-9)
+
+
+def test_plane_step_transports_covariance(geo):
+    """propagate_plane = crossing, helix and J C J^T; the covariance has no variance along the
+    plane's normal (the state is on the plane)."""
+    orc = oracle.Oracle(geo)
+    rng = np.random.default_rng(13)
+    for p in _states(rng, 10):
+        c, n = _planes(rng, p)
+        A = rng.standard_normal((6, 6)) * np.array([1e-2, 1e-2, 1e-2, 1e-3, 1e-3, 1e-3])
+        C6 = A @ A.T
+        c21 = C6[np.tril_indices(6)]
+        ok, q, cq, s = orc.propagate_plane(p, c21, c, n)
+        assert ok
+        J = orc.jacobian_plane(p, s, n)
+        M = np.zeros((6, 6))
+        M[np.tril_indices(6)] = cq
+        M = M + np.tril(M, -1).T
+        np.testing.assert_allclose(M, J @ C6 @ J.T, rtol=1e-10, atol=1e-16)
+        assert abs(n @ M[:3, :3] @ n) < 1e-12 * np.trace(M[:3, :3])
+
+
+def _modular_batch(geo, n_events=2, n_tracks=400, noise=1500, seed=21):
+    evs = [S.simulate_event(geo, n_tracks, seed, e, pt_sampler=S.sample_pt_phase2, eta_max=2.5, noise_total=noise)
+           for e in range(n_events)]
+    return S.concat_events(evs, geo.n_layers)
+
+
+def _oracle_with_modules(geo, batch, params=None):
+    orc = oracle.Oracle(geo, params or S.default_params())
+    orc.set_modules(geo.modules.c, geo.modules.n, batch.hit_mod)
+    return orc
+
+
+def test_module_search_finds_true_hits_and_overlaps(geo):
+    """On modular events the search takes the true hit on most modular layer crossings and picks
+    up the true overlap hit where the track crossed two modules; every overlap hit lies on the
+    same layer as, and on another module than, the step's hit."""
+    batch = _modular_batch(geo)
+    orc = _oracle_with_modules(geo, batch)
+    o = PR.oracle_build(orc, batch)
+    good = good_n = ovl_ok = ovl_n = 0
+    L = batch.n_layers
+    for k, si in enumerate(o["seed_index"]):
+        if not np.isfinite(o["score"][k]):
+            continue
+        e = int(batch.seed_event[si])
+        ev = batch.events[e]
+        base = int(batch.hit_off[e * L])
+        t = int(batch.seed_track[si])
+        plan = geo.plans[o["region"][k]]
+        for step, lay in enumerate(plan):
+            h, ov = o["hits"][k, step], o["ovl"][k, step]
+            if ov >= 0:
+                assert h >= 0 and batch.hit_mod[ov] >= 0 and batch.hit_mod[ov] != batch.hit_mod[h]
+                assert geo.modules.layer[batch.hit_mod[ov]] == lay == geo.modules.layer[batch.hit_mod[h]]
+            if lay not in geo.modules.grid:
+                assert ov < 0
+                continue
+            j = np.nonzero(ev.track_layers[t] == lay)[0]
+            if j.size == 0:
+                continue
+            good_n += 1
+            good += int(h == ev.track_hits[t, j[0]] + base or h == ev.track_ovl[t, j[0]] + base)
+            if ev.track_ovl[t, j[0]] >= 0:
+                ovl_n += 1
+                pair = {ev.track_hits[t, j[0]] + base, ev.track_ovl[t, j[0]] + base}
+                ovl_ok += int({h, ov} == pair)
+    assert good_n > 500 and good / good_n > 0.95, (good, good_n)
+    assert ovl_n > 50 and ovl_ok / ovl_n > 0.85, (ovl_ok, ovl_n)
+
+
+def test_overlap_bonus_raises_score_only(geo):
+    """score_overlap changes the score by exactly score_overlap per picked-up overlap hit where
+    the hit lists agree (the bonus is uniform over a candidate's module-hit children)."""
+    batch = _modular_batch(geo, n_events=1, n_tracks=300, seed=23)
+    o0 = PR.oracle_build(_oracle_with_modules(geo, batch, S.default_params(score_overlap=0.0)), batch)
+    o1 = PR.oracle_build(_oracle_with_modules(geo, batch, S.default_params(score_overlap=1.5)), batch)
+    same = np.all(o0["hits"] == o1["hits"], 1) & np.all(o0["ovl"] == o1["ovl"], 1) & np.isfinite(o0["score"])
+    assert same.mean() > 0.9
+    nov = (o1["ovl"] >= 0).sum(1)
+    assert nov[same].sum() > 20
+    np.testing.assert_allclose(o1["score"][same] - o0["score"][same], 1.5 * nov[same], atol=1e-9)
+    assert np.all(o0["chi2"][same] == o1["chi2"][same])
+
+
+def test_modular_seeds_fail_and_no_modules_is_plain_search(geo):
+    """A seed with a module hit fails; with the module table cleared, hits are taken on the
+    reference cylinder and no overlap hit is ever picked up."""
+    batch = _modular_batch(geo, n_events=1, n_tracks=200, seed=29)
+    orc = _oracle_with_modules(geo, batch)
+    sh = batch.seed_hits.copy()
+    bad = np.nonzero(batch.hit_mod >= 0)[0][:1]
+    sh[0, 2] = bad[0]
+    b2 = S.Batch(batch.n_events, batch.n_layers, batch.hit_xyz, batch.hit_cov, batch.hit_off, batch.hit_track,
+                 sh[:5], batch.seed_event[:5], batch.seed_track[:5], batch.events, batch.hit_mod)
+    o = PR.oracle_build(orc, b2)
+    assert o["score"][0] == -np.inf and o["region"][0] == -1
+    orc.set_modules(None, None, None)
+    o = PR.oracle_build(orc, batch)
+    assert np.all(o["ovl"] == -1)
+
+
+def test_modular_fit_pulls(geo):
+    """Fit over the true assignment of modular events (module hits used on their planes): the
+    pulls of the fitted parameters at the last hit against the simulation's truth have unit
+    width; a fit that used module hits on the reference cylinder instead would not."""
+    batch = _modular_batch(geo, n_events=2, n_tracks=600, noise=0, seed=31)
+    fi = pipeline.fit_inputs(batch)
+    orc = _oracle_with_modules(geo, batch, S.default_params())
+    X, V = batch.hit_xyz.astype(np.float64), batch.hit_cov.astype(np.float64)
+    r = orc.fit_batch(fi.layers, fi.hits, X, V, fi.p0, fi.c0)
+    truth = []
+    for e, ev in enumerate(batch.events):
+        nh = (ev.track_layers >= 0).sum(1)
+        sel = np.nonzero(nh >= 1)[0]
+        truth.append(ev.track_truth[sel, nh[sel] - 1])
+    truth = np.concatenate(truth)
+    ok = (r["status"] == 0) & ((fi.layers >= 0).sum(1) >= 8)
+    d = r["p"][ok][:, 3:] - truth[ok][:, 3:]
+    d[:, 1] = np.angle(np.exp(1j * d[:, 1]))
+    pulls = d / np.sqrt(r["c"][ok][:, [9, 14, 20]])
+    # curvature, phi and theta at the last hit (on an outer cylinder or a disk)
+    for i in range(3):
+        assert abs(np.std(pulls[:, i]) - 1.0) < 0.12, (i, np.std(pulls[:, i]))
+        assert abs(np.mean(pulls[:, i])) < 0.12
+    orc.set_modules(None, None, None)
+    r0 = orc.fit_batch(fi.layers, fi.hits, X, V, fi.p0, fi.c0)
+    ok0 = (r0["status"] == 0) & ((fi.layers >= 0).sum(1) >= 8)
+    assert np.median(r0["chi2"][ok0]) > 3 * np.median(r["chi2"][ok])

@@ -8,7 +8,8 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "mkoracle.c")
-PINS = ["tests/test_oracle_propagation.py", "tests/test_oracle_kalman.py", "tests/test_oracle_search.py"]
+PINS = ["tests/test_oracle_propagation.py", "tests/test_oracle_kalman.py", "tests/test_oracle_search.py",
+        "tests/test_oracle_modules.py"]
 
 MUTANTS = {
     "jacobian_sign": ("A[0 * 6 + 4] = -dy;", "A[0 * 6 + 4] = dy;"),
@@ -30,6 +31,13 @@ MUTANTS = {
                     "if (x->score != y->score) return x->score < y->score ? -1 : 1;"),
     "bin_guard": ("int e0 = eta_bin(L, w[0] - w[2] - eps), e1 = eta_bin(L, w[0] + w[2] + eps);",
                   "int e0 = eta_bin(L, w[0]), e1 = eta_bin(L, w[0]);"),
+    "plane_jacobian_dropped_z": ("double gp = n[0] * A[0 * 6 + j] + n[1] * A[1 * 6 + j] + n[2] * A[2 * 6 + j];",
+                                 "double gp = n[0] * A[0 * 6 + j] + n[1] * A[1 * 6 + j];"),
+    "module_ignored": ("int m = hit_module(g, id);\n    if (margin)", "int m = -1;\n    if (margin)"),
+    "overlap_same_module": ("if (hit_module(g, mh->v[q].gid) != hit_module(g, b1)) b2 = mh->v[q].gid;",
+                            "if (hit_module(g, mh->v[q].gid) == hit_module(g, b1)) b2 = mh->v[q].gid;"),
+    "overlap_swapped": ("k->ovl = hit_module(g, k->gid) != hit_module(g, b1) ? b1 : b2;",
+                        "k->ovl = hit_module(g, k->gid) != hit_module(g, b1) ? b2 : b1;"),
 }
 
 
