@@ -71,6 +71,23 @@ def _gen_event(args):
     return S.simulate_event(g, N_TRACKS, seed, e, pt_sampler=S.sample_pt_phase2, eta_max=3.0, noise_total=N_NOISE)
 
 
+def _gen_modular_event(args):
+    e, seed = args
+    from paper_2312_11728_gb300 import synth as S
+    g = S.geometry_phase2_modular()
+    return S.simulate_event(g, N_TRACKS, seed, e, pt_sampler=S.sample_pt_phase2, eta_max=3.0, noise_total=N_NOISE)
+
+
+def make_modular_batch(seed, n_events):
+    """The same events' recipe on the modular tracker (cylinders 3-5 built from flat and tilted
+    modules), generated in a spawn pool."""
+    from paper_2312_11728_gb300 import synth as S
+    g = S.geometry_phase2_modular()
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        evs = pool.map(_gen_modular_event, [(e, seed) for e in range(n_events)])
+    return g, S.concat_events(evs, g.n_layers)
+
+
 def make_batch(seed, n_events=N_EVENTS):
     """Events generated in a spawn pool (before any CUDA call in this process)."""
     from paper_2312_11728_gb300 import synth as S
@@ -344,6 +361,54 @@ def measure_cleaning(ctx, db, g, stream, local):
     return res
 
 
+def measure_modular(mod, params, shapes, stream, local, dist):
+    """The search and the fit on the modular tracker (Sec. 3.1 module planes, the Phase-2 tilted
+    barrel; Sec. 2.2 overlap hits): module hits tested and updated on their planes, overlap hits
+    picked up.  One warm-up then one CUDA-event timed search and fit; the same hits loaded
+    without module ids (every hit taken on its cylinder) give the cost of the plane steps."""
+    import torch
+    from paper_2312_11728_gb300 import mkgb, pipeline
+    g, batch = mod
+    fi = pipeline.fit_inputs(batch)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(f"cuda:{local}")
+    ctx = pipeline.make_context(g, params, device=local, stream=stream)
+    ctx.set_launch(shapes[0], shapes[1])
+    xyz, cov, hm, seeds = dev(batch.hit_xyz), dev(batch.hit_cov), dev(batch.hit_mod), dev(batch.seed_hits)
+    n, nt = int(batch.seed_hits.shape[0]), int(fi.layers.shape[0])
+    out = mkgb.alloc_tracks(n, g.max_plan, device=f"cuda:{local}", ovl=True)
+    L, H, P0, C0 = dev(fi.layers), dev(fi.hits), dev(fi.p0), dev(fi.c0)
+    fo = [torch.zeros((nt, 6), device=f"cuda:{local}"), torch.zeros((nt, 21), device=f"cuda:{local}"),
+          torch.zeros(nt, device=f"cuda:{local}"), torch.zeros(nt, dtype=torch.int32, device=f"cuda:{local}")]
+    res = {"events": int(batch.n_events), "seeds": n, "tracks": nt, "modules": int(g.modules.c.shape[0]),
+           "modular_layers": sorted(int(l) for l in g.modules.grid)}
+    for label, hmod in (("planes", hm), ("cylinders_only", None)):
+        ctx.load_hits(batch.n_events, batch.hit_off, xyz, cov, hit_module=hmod)
+        ctx.seed(seeds)
+        ctx.build(out)
+        ctx.fit(L, H, P0, C0, *fo)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        ctx.build(out)
+        e[1].record(stream)
+        ctx.fit(L, H, P0, C0, *fo)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        bc, fc = ctx.counters(0), ctx.counters(1)
+        ms_s, ms_f = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+        steps = int(bc[0] + fc[0])
+        value, wall, _ = pipeline.replica_throughput((ms_s + ms_f) / 1e3, steps, dist, f"cuda:{local}")
+        r = {"value": value, "unit": UNIT, "search_ms": ms_s, "fit_ms": ms_f, "kalman_steps": steps,
+             "search_chi2": int(bc[1]), "search_updates": int(bc[2]),
+             "found_fraction": float(torch.isfinite(out["score"]).float().mean().item())}
+        if hmod is not None:
+            r["overlap_hits"] = int((out["ovl"] >= 0).sum().item())
+            r["tracks_with_overlap"] = int((out["ovl"] >= 0).any(1).sum().item())
+            r["fit_status_ok_fraction"] = float((fo[3] == 0).float().mean().item())
+        res[label] = r
+    return res
+
+
 def measure_fit_grad(args, local, rank, dist, stream):
     """The fit's derivative on the differentiable-fit workload (100,000 tracks over 22 layers of
     a misaligned detector): one mkgb_fit_grad call after a warm-up call, CUDA-event timed."""
@@ -392,6 +457,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison path")
     ap.add_argument("--no-grad", action="store_true", help="skip the fit-derivative measurement")
+    ap.add_argument("--no-modular", action="store_true", help="skip the modular-tracker measurement")
+    ap.add_argument("--modular-events", type=int, default=16, help="events of the modular-tracker measurement")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes of the search kernels")
     ap.add_argument("--no-graph", action="store_true", help="launch the search rounds one by one")
     ap.add_argument("--shapes", default=None,
@@ -406,6 +473,7 @@ def main():
 
     from paper_2312_11728_gb300 import pipeline, synth as S
     g, batch, evs = make_batch(seed=rank, n_events=args.events)   # before the first CUDA call (spawn pool)
+    mod = None if args.no_modular else make_modular_batch(rank, args.modular_events)
     fit = pipeline.fit_inputs(batch, seed=rank)
     params = S.default_params()
 
@@ -496,6 +564,7 @@ def main():
 
     bkfit = measure_fit_backward(ctx, db, fit, stream, dist, local)
     cleaning = measure_cleaning(ctx, db, g, stream, local)
+    modular = None if mod is None else measure_modular(mod, params, shapes, stream, local, dist)
 
     grad = None
     if not args.no_grad:
@@ -564,6 +633,7 @@ def main():
         "fit_grad": grad,
         "fit_backward": bkfit,
         "cleaning": cleaning,
+        "modular": modular,
         "gpu_launches": int(launches_per_step * args.steps),
         "clocks": clocks,
         "counters": {"build": [int(x) for x in bc], "fit": [int(x) for x in fc]},

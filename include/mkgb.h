@@ -85,6 +85,8 @@ typedef struct {
                               the final fit's outlier rejection, Sec. 2.2): a listed hit whose predicted chi2
                               exceeds this is not used (the layer is crossed, the state is not updated);
                               0 = every listed hit is used.  mkgb_fit_grad ignores it */
+    float score_overlap;   /* search on modular layers (mkgb_load_modules): score added to a child that picks
+                              up an overlap hit (Sec. 2.2: a single additional detector-overlap hit) */
 } mkgb_params;
 
 #define MKGB_FP32 0
@@ -100,6 +102,7 @@ typedef struct {
     int32_t* nholes;       /* n_seeds */
     int32_t* hits;         /* n_seeds x max_plan: global hit index or MKGB_HIT_* per plan step */
     int32_t max_plan;      /* row stride of hits, >= the longest plan */
+    int32_t* ovl_hits;     /* n_seeds x max_plan (NULL to skip): overlap hit index per plan step, -1 none */
 } mkgb_tracks;
 
 /* Creates a context on `device` that launches on `stream` (a cudaStream_t, including
@@ -119,6 +122,19 @@ const char* mkgb_version(void);
 int mkgb_load_geometry(mkgb_ctx* ctx, const mkgb_layer* layers, int n_layers,
                        const int32_t* plan, const int32_t* plan_off, int n_regions, float bz_tesla);
 
+/* Flat detector modules (Sec. 3.1: module position, normal and phi-direction vectors; the Phase-2
+ * tilted modules and the overlap hits of neighbouring modules).  Module m lies on layer[m] and is
+ * the plane through pos[3m..3m+2] [cm] with unit normal normal[3m..3m+2]; its phi-direction lies in
+ * the plane and enters through the hit covariances, which carry the module's measurement axes.  A
+ * layer with at least one module is modular: its hits lie on module planes, and its own cylinder
+ * or disk stays the reference surface of the window, the material and the eta-phi bins.  The search
+ * and mkgb_fit move a candidate from that surface to the plane of each module hit (the helix to
+ * the plane, its Jacobian and the covariance transport; no material) before the chi2 and update.
+ * Host arrays; n_modules = 0 removes the modules.  Loaded hits are dropped (load them again with
+ * mkgb_load_hits_modular).  Errors: MKGB_ESTATE before mkgb_load_geometry; MKGB_EINVAL for a layer
+ * out of range, a normal that is not a unit vector (|n|^2 off 1 by 1e-4 or more) or a NaN position. */
+int mkgb_load_modules(mkgb_ctx* ctx, int n_modules, const int32_t* layer, const float* pos, const float* normal);
+
 /* Iteration parameters (Sec. 3.2).  Host struct.  Errors: MKGB_EINVAL if max_cands is outside
  * 1..MKGB_MAX_CANDS, max_holes < 0 or a window bound is negative. */
 int mkgb_set_params(mkgb_ctx* ctx, const mkgb_params* params);
@@ -131,6 +147,20 @@ int mkgb_set_params(mkgb_ctx* ctx, const mkgb_params* params);
  * Errors: MKGB_ESTATE without geometry, MKGB_EINVAL on bad offsets, MKGB_ENOMEM. */
 int mkgb_load_hits(mkgb_ctx* ctx, int n_events, const int64_t* seg_off,
                    const float* xyz, const float* cov6, int on_device);
+
+/* mkgb_load_hits with the module of every hit: hit_module (n ints, host or device per on_device)
+ * gives the module index of each hit on a modular layer and -1 for every other hit.  The search
+ * then tests and updates module hits on their planes and picks up overlap hits (mkgb_build,
+ * mkgb_tracks.ovl_hits: with the best accepted module hit b1 of a candidate's window and the best
+ * one b2 on a module other than b1's, a child taking module hit h also takes b1 if h is not on b1's
+ * module, else b2, and scores params.score_overlap more; its update uses h only).  Seeds with a
+ * module hit fail (the seed fit takes hits on the layers' own surfaces).  mkgb_fit uses module hits
+ * on their planes (status 1 if a plane is not reached within 10 cm, or only at grazing incidence);
+ * mkgb_fit_backward, mkgb_build_backward and mkgb_fit_grad take no module hits.  Synchronises the
+ * stream (the module ids are checked on the device).  Errors: those of mkgb_load_hits; MKGB_ESTATE
+ * without modules; MKGB_EINVAL for a NULL hit_module or a hit whose module does not fit its layer. */
+int mkgb_load_hits_modular(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz,
+                           const float* cov6, const int32_t* hit_module, int on_device);
 
 /* Seeds (Sec. 2.2): n_seeds x 3 hit indices on three consecutive crossed layers of one event,
  * innermost first.  Computes each seed's state at its third hit (circle estimate + 3-hit

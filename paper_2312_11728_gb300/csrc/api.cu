@@ -81,6 +81,9 @@ struct mkgb_ctx {
     // backward search: the geometry with reversed plans and the tracks' start records
     DevBuf geom_bwd_d, bw_state, bw_info, bw_order;
     DevBuf clean_scratch;   // seed cleaning / duplicate removal index
+    // module planes (Sec. 3.1) and whether the loaded hits carry module ids
+    DevBuf mods_d, in_mod, mod_bad;
+    bool mod_hits = false;
     DevBuf stage[S_COUNT];
     // launch shapes of the search rounds and the graph cache replaying them
     int find_shape = 0, select_shape = 0;
@@ -170,13 +173,26 @@ int enqueue_build(mkgb_ctx* ctx, const BuildOutDev& d, int find_shape, int selec
     const int prec = ctx->params.precision;
     if (prec == MKGB_FP64 && !ctx->seeds_fp64)
         return fail(ctx, MKGB_ESTATE, "FP64 search needs seeds made under the FP64 precision");
-    CK(ensure(ctx->build_work, build_work_bytes(ctx->n_seeds, ctx->max_plan_len, prec)));
-    const BuildWork w = carve_build_work(ctx->build_work.p, ctx->n_seeds, ctx->max_plan_len, prec);
+    const bool ovl = ctx->mod_hits;   // overlap hits need their own trail
+    CK(ensure(ctx->build_work, build_work_bytes(ctx->n_seeds, ctx->max_plan_len, prec, ovl)));
+    const BuildWork w = carve_build_work(ctx->build_work.p, ctx->n_seeds, ctx->max_plan_len, prec, ovl);
     CK(cudaMemsetAsync(ctx->counters_build.p, 0, 8 * kNumCounters, st));
     if (ctx->use_graph && !ctx->graph) ctx->graph = build_graph_create();
     CK(launch_build(st, (const DevGeom*)ctx->geom_d.p, ctx->max_plan_len, ctx->params, hit_store(ctx), S, d, w,
                     (unsigned long long*)ctx->counters_build.p, ctx->n_sms, find_shape, select_shape,
                     ctx->use_graph ? ctx->graph : nullptr));
+    return MKGB_OK;
+}
+
+// Copies the host geometry to the device, and the same geometry with every region's plan in
+// reverse order (the backward search); synchronises the context's stream.
+int upload_geometry(mkgb_ctx* ctx) {
+    CK(cudaMemcpyAsync(ctx->geom_d.p, &ctx->geom_h, sizeof(DevGeom), cudaMemcpyHostToDevice, ctx->stream));
+    CK(ensure(ctx->geom_bwd_d, sizeof(DevGeom)));
+    DevGeom gb = ctx->geom_h;
+    for (int r = 0; r < gb.n_regions; ++r) std::reverse(gb.plan + gb.plan_off[r], gb.plan + gb.plan_off[r + 1]);
+    CK(cudaMemcpyAsync(ctx->geom_bwd_d.p, &gb, sizeof(DevGeom), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));   // gb lives on this stack frame
     return MKGB_OK;
 }
 
@@ -251,7 +267,7 @@ void mkgb_destroy(mkgb_ctx* ctx) {
                          &ctx->counters_build, &ctx->counters_fit, &ctx->queue, &ctx->rescue_list,
                          &ctx->rescue_count, &ctx->build_work, &ctx->probe_sink, &ctx->grad_ck,
                          &ctx->geom_bwd_d, &ctx->bw_state, &ctx->bw_info, &ctx->bw_order,
-                         &ctx->clean_scratch};
+                         &ctx->clean_scratch, &ctx->mods_d, &ctx->in_mod, &ctx->mod_bad};
         for (DevBuf* b : all) release(*b);
         for (auto& b : ctx->stage) release(b);
         build_graph_destroy(ctx->graph);
@@ -317,22 +333,52 @@ int mkgb_load_geometry(mkgb_ctx* ctx, const mkgb_layer* layers, int n_layers, co
     g.max_plan = maxp;
     DevGuard guard(ctx->device);
     ctx->geom_h = g;
-    CK(cudaMemcpyAsync(ctx->geom_d.p, &ctx->geom_h, sizeof(DevGeom), cudaMemcpyHostToDevice, ctx->stream));
-    // the same geometry with every region's plan in reverse order (the backward search)
-    CK(ensure(ctx->geom_bwd_d, sizeof(DevGeom)));
-    {
-        DevGeom gb = ctx->geom_h;
-        for (int r = 0; r < gb.n_regions; ++r)
-            std::reverse(gb.plan + gb.plan_off[r], gb.plan + gb.plan_off[r + 1]);
-        CK(cudaMemcpyAsync(ctx->geom_bwd_d.p, &gb, sizeof(DevGeom), cudaMemcpyHostToDevice, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));   // gb lives on this stack frame
-    }
-    CK(cudaStreamSynchronize(ctx->stream));
+    const int rc = upload_geometry(ctx);
+    if (rc != MKGB_OK) return rc;
     ctx->max_plan_len = maxp;
     ctx->n_layers = n_layers;
     ctx->has_geom = true;
     ctx->has_hits = false;
     ctx->has_seeds = false;
+    ctx->mod_hits = false;
+    return MKGB_OK;
+}
+
+int mkgb_load_modules(mkgb_ctx* ctx, int n_modules, const int32_t* layer, const float* pos, const float* normal) {
+    if (!ctx) return MKGB_EINVAL;
+    if (!ctx->has_geom) return fail(ctx, MKGB_ESTATE, "load_modules before load_geometry");
+    if (n_modules < 0 || (n_modules > 0 && (!layer || !pos || !normal))) return fail(ctx, MKGB_EINVAL, "bad module arrays");
+    if (n_modules >= (1 << 30)) return fail(ctx, MKGB_EINVAL, "too many modules");
+    std::vector<float4> tab(2 * (size_t)n_modules);
+    bool modular[MKGB_MAX_LAYERS] = {false};
+    for (int m = 0; m < n_modules; ++m) {
+        const int l = layer[m];
+        if (l < 0 || l >= ctx->n_layers) return fail(ctx, MKGB_EINVAL, "module %d: layer %d out of range", m, l);
+        const float nx = normal[3 * m], ny = normal[3 * m + 1], nz = normal[3 * m + 2];
+        const float n2 = nx * nx + ny * ny + nz * nz;
+        if (!(fabsf(n2 - 1.0f) < 1e-4f)) return fail(ctx, MKGB_EINVAL, "module %d: normal is not a unit vector", m);
+        if (!(pos[3 * m] == pos[3 * m] && pos[3 * m + 1] == pos[3 * m + 1] && pos[3 * m + 2] == pos[3 * m + 2]))
+            return fail(ctx, MKGB_EINVAL, "module %d: bad position", m);
+        int li = l;
+        float lw;
+        memcpy(&lw, &li, 4);
+        tab[2 * m] = make_float4(pos[3 * m], pos[3 * m + 1], pos[3 * m + 2], lw);
+        tab[2 * m + 1] = make_float4(nx, ny, nz, 0.0f);
+        modular[l] = true;
+    }
+    DevGuard guard(ctx->device);
+    if (n_modules > 0) {
+        CK(ensure(ctx->mods_d, 32 * (size_t)n_modules));
+        CK(cudaMemcpyAsync(ctx->mods_d.p, tab.data(), 32 * (size_t)n_modules, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    ctx->geom_h.mods = n_modules > 0 ? (const float4*)ctx->mods_d.p : nullptr;
+    ctx->geom_h.n_mods = n_modules;
+    for (int l = 0; l < ctx->n_layers; ++l) ctx->geom_h.layers[l].modular = modular[l] ? 1 : 0;
+    const int rc = upload_geometry(ctx);   // synchronises: tab may go
+    if (rc != MKGB_OK) return rc;
+    ctx->has_hits = false;   // hits are matched to the modules when they are loaded
+    ctx->has_seeds = false;
+    ctx->mod_hits = false;
     return MKGB_OK;
 }
 
@@ -364,13 +410,17 @@ int mkgb_set_params(mkgb_ctx* ctx, const mkgb_params* p) {
     d.kappa_fp64 = p->kappa_fp64;
     if (!(p->fit_outlier_chi2 >= 0.0f)) return fail(ctx, MKGB_EINVAL, "fit_outlier_chi2 must be >= 0");
     d.fit_outlier_chi2 = p->fit_outlier_chi2;
+    if (!(p->score_overlap == p->score_overlap) || !(fabsf(p->score_overlap) < 1e30f))
+        return fail(ctx, MKGB_EINVAL, "score_overlap must be finite");
+    d.score_overlap = p->score_overlap;
     ctx->has_params = true;
     return MKGB_OK;
 }
 
-int mkgb_load_hits(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz, const float* cov6,
-                   int on_device) {
-    if (!ctx) return MKGB_EINVAL;
+namespace {
+
+int load_hits_impl(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz, const float* cov6,
+                   const int32_t* hit_module, int on_device) {
     if (!ctx->has_geom) return fail(ctx, MKGB_ESTATE, "load_hits before load_geometry");
     if (n_events < 1 || !seg_off) return fail(ctx, MKGB_EINVAL, "need n_events >= 1 and seg_off");
     const int L = ctx->n_layers;
@@ -424,10 +474,27 @@ int mkgb_load_hits(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const fl
     CK(ensure(ctx->bins, 4 * (nbins + 1)));
     CK(ensure(ctx->cursor, 4 * (nbins + 1)));
     CK(ensure(ctx->scan_tmp, 4 * scan_tmp_ints(nbins + 1)));
+    const int* dm = hit_module;
+    if (hit_module && !on_device && n > 0) {
+        CK(ensure(ctx->in_mod, 4 * n));
+        CK(cudaMemcpyAsync(ctx->in_mod.p, hit_module, 4 * n, cudaMemcpyHostToDevice, st));
+        dm = (const int*)ctx->in_mod.p;
+    }
     CK(cudaMemsetAsync(ctx->bins.p, 0, 4 * (nbins + 1), st));
     CK(launch_hit_prep(st, (const DevGeom*)ctx->geom_d.p, L, (const int64_t*)ctx->seg_off.p, (int)nseg, n, dx, dc,
-                       ctx->geom_h.bins_per_event, (float4*)ctx->pay.p, (float2*)ctx->ep_tmp.p,
+                       n > 0 ? dm : nullptr, ctx->geom_h.bins_per_event, (float4*)ctx->pay.p, (float2*)ctx->ep_tmp.p,
                        (int*)ctx->bin_of_hit.p, (int*)ctx->hit_seg.p, (int*)ctx->bins.p));
+    ctx->has_hits = false;
+    if (hit_module && n > 0) {   // every module id must fit its hit's layer (synchronises)
+        CK(ensure(ctx->mod_bad, 16));
+        CK(cudaMemsetAsync(ctx->mod_bad.p, 0, 4, st));
+        CK(launch_check_modules(st, (const DevGeom*)ctx->geom_d.p, L, n, (const int*)ctx->hit_seg.p, dm,
+                                (int*)ctx->mod_bad.p));
+        int bad = 0;
+        CK(cudaMemcpyAsync(&bad, ctx->mod_bad.p, 4, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (bad) return fail(ctx, MKGB_EINVAL, "%d hits with a module that does not fit their layer", bad);
+    }
     // The binned copy is used by the search only: it is built on the side stream, overlapping
     // the seed fit and the fit on the context's stream, and mkgb_build waits for it.
     CK(cudaEventRecord(ctx->ev_prep, st));
@@ -444,7 +511,24 @@ int mkgb_load_hits(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const fl
     ctx->n_hits = n;
     ctx->has_hits = true;
     ctx->has_seeds = false;
+    ctx->mod_hits = hit_module != nullptr && n > 0;
     return MKGB_OK;
+}
+
+}  // namespace
+
+int mkgb_load_hits(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz, const float* cov6,
+                   int on_device) {
+    if (!ctx) return MKGB_EINVAL;
+    return load_hits_impl(ctx, n_events, seg_off, xyz, cov6, nullptr, on_device);
+}
+
+int mkgb_load_hits_modular(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz, const float* cov6,
+                           const int32_t* hit_module, int on_device) {
+    if (!ctx) return MKGB_EINVAL;
+    if (!hit_module) return fail(ctx, MKGB_EINVAL, "null hit_module");
+    if (ctx->has_geom && ctx->geom_h.n_mods == 0) return fail(ctx, MKGB_ESTATE, "load_hits_modular before load_modules");
+    return load_hits_impl(ctx, n_events, seg_off, xyz, cov6, hit_module, on_device);
 }
 
 int mkgb_seed(mkgb_ctx* ctx, int n_seeds, const int32_t* seed_hits, int on_device, float* state_out,
@@ -513,6 +597,10 @@ int mkgb_build(mkgb_ctx* ctx, const mkgb_tracks* out, int on_device) {
     CK(stage_out(ctx, S_F, out->nholes, 4 * n, on_device, &p)); d.nholes = (int*)p;
     CK(stage_out(ctx, S_G, out->hits, 4 * n * out->max_plan, on_device, &p)); d.hits = (int*)p;
     d.max_plan = out->max_plan;
+    if (out->ovl_hits) {
+        CK(stage_out(ctx, S_H, out->ovl_hits, 4 * n * out->max_plan, on_device, &p));
+        d.ovl = (int*)p;
+    }
     const int rc = enqueue_build(ctx, d, ctx->find_shape, ctx->select_shape);
     if (rc != MKGB_OK) return rc;
     cudaStream_t st = ctx->stream;
@@ -523,6 +611,7 @@ int mkgb_build(mkgb_ctx* ctx, const mkgb_tracks* out, int on_device) {
     CK(copy_back(ctx, out->nfound, d.nfound, 4 * n, on_device));
     CK(copy_back(ctx, out->nholes, d.nholes, 4 * n, on_device));
     CK(copy_back(ctx, out->hits, d.hits, 4 * n * out->max_plan, on_device));
+    if (d.ovl) CK(copy_back(ctx, out->ovl_hits, d.ovl, 4 * n * out->max_plan, on_device));
     if (!on_device) CK(cudaStreamSynchronize(st));
     return MKGB_OK;
 }
@@ -535,6 +624,7 @@ int mkgb_build_backward(mkgb_ctx* ctx, int n, const int32_t* track_event, const 
     if (n < 0) return fail(ctx, MKGB_EINVAL, "negative size");
     if (ctx->params.precision == MKGB_FP64)
         return fail(ctx, MKGB_EINVAL, "the backward search runs in FP32 (precision MKGB_FP32)");
+    if (ctx->mod_hits) return fail(ctx, MKGB_EINVAL, "the backward search takes hits without modules");
     if (n > 0 && (!track_event || !first_layer || !p_start || !c_start)) return fail(ctx, MKGB_EINVAL, "null input");
     if (!out || !out->params || !out->cov || !out->chi2 || !out->score || !out->nfound || !out->nholes || !out->hits)
         return fail(ctx, MKGB_EINVAL, "null output array");
@@ -670,7 +760,7 @@ int mkgb_fit(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, const i
                   ctx->has_hits ? ctx->n_hits : 0, n, max_steps, (const int*)dl, (const int*)dh, (const float*)dp0,
                   (const float*)dc0, (float*)po, (float*)co, (float*)xo, (int*)so,
                   (unsigned long long*)ctx->counters_fit.p, (int*)ctx->rescue_list.p, (int*)ctx->rescue_count.p,
-                  ctx->n_sms));
+                  ctx->n_sms, ctx->mod_hits));
     CK(copy_back(ctx, p_out, po, 24 * N, on_device));
     CK(copy_back(ctx, c_out, co, 84 * N, on_device));
     CK(copy_back(ctx, chi2_out, xo, 4 * N, on_device));
@@ -686,6 +776,7 @@ int mkgb_fit_backward(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers
     if (!ctx->has_geom || !ctx->has_params) return fail(ctx, MKGB_ESTATE, "fit_backward before geometry/params");
     if (n < 0 || max_steps < 0) return fail(ctx, MKGB_EINVAL, "negative size");
     if (!(cov_scale > 0.0f) || !(cov_scale < 3.0e38f)) return fail(ctx, MKGB_EINVAL, "cov_scale must be positive");
+    if (ctx->mod_hits) return fail(ctx, MKGB_EINVAL, "the backward fit takes hits without modules");
     if (n > 0 && (!layers || !hits || !p_start || !c_start || !p_out || !c_out || !chi2_out))
         return fail(ctx, MKGB_EINVAL, "null fit array");
     bool any_hit = false;
@@ -732,6 +823,7 @@ int mkgb_fit_grad(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, co
     if (mode != 0 && mode != 1) return fail(ctx, MKGB_EINVAL, "fit_grad mode %d (0 reverse sweep, 1 forward)", mode);
     if (!ctx->has_geom || !ctx->has_params) return fail(ctx, MKGB_ESTATE, "fit_grad before geometry/params");
     if (!ctx->has_hits) return fail(ctx, MKGB_ESTATE, "fit_grad before load_hits");
+    if (ctx->mod_hits) return fail(ctx, MKGB_EINVAL, "the fit derivative takes hits without modules");
     if (n < 0 || max_steps < 0) return fail(ctx, MKGB_EINVAL, "negative size");
     if (!align || !xscale || !d_align || !d_xscale) return fail(ctx, MKGB_EINVAL, "null alignment/material array");
     if (n > 0 && (!layers || !hits || !p0 || !c0 || !chi2_out || !d_p0)) return fail(ctx, MKGB_EINVAL, "null fit array");
@@ -821,7 +913,7 @@ int mkgb_fit_static(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, 
                   max_steps, layers, hits, p0, c0, p_out, c_out, chi2_out, status_out,
                   reinterpret_cast<unsigned long long*>(b + kFitStaticCountersOff),
                   reinterpret_cast<int*>(b + kFitStaticListOff), reinterpret_cast<int*>(b + kFitStaticRescueCountOff),
-                  ctx->n_sms));
+                  ctx->n_sms, ctx->mod_hits));
     return MKGB_OK;
 }
 

@@ -44,6 +44,7 @@ struct BuildOutDev {
     int* nholes;
     int* hits;
     int max_plan;
+    int* ovl = nullptr;   // n x max_plan overlap hit ids (-1 none), nullptr: not wanted
 };
 
 // Work buffers of the search (k_build.cu): per seed 8 candidate slots, double-buffered.
@@ -57,6 +58,7 @@ struct BuildWork {
     int4* sinfo;      // per ordered seed: (plan position of its first step, first step, steps, event)
     int* fin;         // per ordered seed: buffer holding its final slots, -1 none
     int* trail;       // per ordered seed: longest plan x 8 ints ((code + 4) << 3 | parent slot)
+    int* otrail;      // the same layout: overlap hit id of the step (-1 none); nullptr without modules
     int* rescue;      // kept children of the round whose update is redone in FP64
     int* counts;      // [live0, live1, seeds0, seeds1, rescue]
 };
@@ -65,9 +67,15 @@ struct BuildWork {
 constexpr int kNumCounters = 5;
 
 // ---- k_hits.cu
+// hit_mod (may be nullptr: every hit on its layer's own surface) goes into the payload.
 cudaError_t launch_hit_prep(cudaStream_t st, const DevGeom* g, int n_layers, const int64_t* seg_off, int n_seg,
-                            int64_t n_hits, const float* xyz, const float* cov, int bins_per_event,
-                            float4* pay, float2* ep_tmp, int* bin_of_hit, int* hit_seg, int* counts);
+                            int64_t n_hits, const float* xyz, const float* cov, const int* hit_mod,
+                            int bins_per_event, float4* pay, float2* ep_tmp, int* bin_of_hit, int* hit_seg,
+                            int* counts);
+// Counts into *bad the hits whose module does not fit their layer (a module hit on a layer without
+// modules or on another layer's module, a hit without module on a modular layer, an index out of range).
+cudaError_t launch_check_modules(cudaStream_t st, const DevGeom* g, int n_layers, int64_t n_hits,
+                                 const int* hit_seg, const int* hit_mod, int* bad);
 cudaError_t launch_hit_scatter(cudaStream_t st, int64_t n_hits, const float4* pay, const float2* ep_tmp,
                                const int* bin_of_hit, int* cursor, float2* hb_ep, float4* hb_pay);
 // Exclusive scan of n ints (out[n] gets the total); tmp must hold scan_tmp_ints(n) ints.
@@ -81,8 +89,9 @@ cudaError_t launch_seed(cudaStream_t st, const DevGeom* g, DevParams P, HitStore
                         float* cov21, int* info3);
 
 // ---- k_build.cu
-size_t build_work_bytes(int n_seeds, int max_plan_len, int precision);
-BuildWork carve_build_work(void* base, int n_seeds, int max_plan_len, int precision);
+// with_ovl: room for the overlap hits of modular layers (the otrail array)
+size_t build_work_bytes(int n_seeds, int max_plan_len, int precision, bool with_ovl = false);
+BuildWork carve_build_work(void* base, int n_seeds, int max_plan_len, int precision, bool with_ovl = false);
 struct BuildGraph;
 BuildGraph* build_graph_create();
 void build_graph_destroy(BuildGraph* gph);
@@ -123,7 +132,7 @@ cudaError_t fit_static_scratch_address(void** base);
 cudaError_t launch_fit(cudaStream_t st, const DevGeom* g, DevParams P, const float4* pay, int64_t n_hits, int n,
                        int max_steps, const int* layers, const int* hits, const float* p0, const float* c0,
                        float* p_out, float* c_out, float* chi2_out, int* status_out, unsigned long long* counters,
-                       int* rescue_list, int* rescue_count, int n_sms);
+                       int* rescue_list, int* rescue_count, int n_sms, bool modular = false);
 // Backward fit (Sec. 2.2) of n tracks listed in forward order from their state on the last
 // listed layer (covariance scaled by cov_scale); FP64 refit of tracks above kappa_fp64.
 cudaError_t launch_bkfit(cudaStream_t st, const DevGeom* g, DevParams P, const float4* pay, int64_t n_hits, int n,

@@ -231,7 +231,9 @@ __global__ void __launch_bounds__(kThreads) k_start(BuildArgs a) {
 
 // ---- a4-a9 for every live candidate of round tau
 
-template <class F, int TH, int MINB, bool BWD = false>
+// MOD: module hits loaded (their chi2 on the module planes, the overlap bookkeeping); the plain
+// instantiation keeps the layers-only path's registers.
+template <class F, int TH, int MINB, bool BWD = false, bool MOD = false>
 __global__ void __launch_bounds__(TH, MINB) k_find(BuildArgs a, int tau) {
     __shared__ DevGeom g;
     // per-thread sorted list of hit children (chi2 asc, id asc), one column per thread
@@ -331,6 +333,11 @@ __global__ void __launch_bounds__(TH, MINB) k_find(BuildArgs a, int tau) {
         c_newton += newton;
         int nh_kind = K_NONE, n_h = 0;
         float nh_score = 0.0f;
+        // overlap pickup (Sec. 2.2): the best accepted module hit b1 (the list's first entry on a
+        // modular layer) and the best one on another module b2 (binned index, -1 none)
+        int b1m = -1, b2 = -1, b2id = 0;
+        float b1x = 0.0f, b2x = 0.0f;
+        int b1id = 0, b1q = -1;
         if (r == 0) {
             nh_kind = K_SKIP;
             nh_score = score;
@@ -376,11 +383,30 @@ __global__ void __launch_bounds__(TH, MINB) k_find(BuildArgs a, int tau) {
                         if (fabs(F(ep.x) - w.eta) <= w.deta && fabs(wrap_pi(F(ep.y) - w.phi)) <= w.dphi) {
                             ++c_chi2;
                             F m[3], v[6];
-                            int id;
-                            load_hit(a.H.hb_pay, hq, m, v, &id);
+                            int id, md = -1;
                             F x2f;
-                            if (chi2_hit(fr, q, m[0], m[1], m[2], v, x2f) && x2f < F(P.chi2_cut)) {
+                            bool okx;
+                            if constexpr (MOD) {
+                                load_hit(a.H.hb_pay, hq, m, v, &id, &md);
+                                // a module hit: chi2 on its module's plane (Sec. 3.1)
+                                okx = md >= 0 ? module_chi2(L.kind, q, g.mods, md, g.cB, m, v, x2f)
+                                              : chi2_hit(fr, q, m[0], m[1], m[2], v, x2f);
+                            } else {
+                                load_hit(a.H.hb_pay, hq, m, v, &id);
+                                okx = chi2_hit(fr, q, m[0], m[1], m[2], v, x2f);
+                            }
+                            if (okx && x2f < F(P.chi2_cut)) {
                                 const float x2 = float(x2f);   // scores and child order in FP32
+                                if (MOD && md >= 0) {
+                                    if (b1m < 0 || x2 < b1x || (x2 == b1x && id < b1id)) {
+                                        if (b1m >= 0 && md != b1m) {   // the previous b1 becomes b2
+                                            b2 = b1q; b2x = b1x; b2id = b1id;
+                                        }
+                                        b1q = hq; b1x = x2; b1id = id; b1m = md;
+                                    } else if (md != b1m && (b2 < 0 || x2 < b2x || (x2 == b2x && id < b2id))) {
+                                        b2 = hq; b2x = x2; b2id = id;
+                                    }
+                                }
                                 // insert into the sorted list (kept to its first kGroup entries)
                                 int j = n_h < kGroup ? n_h : kGroup - 1;
                                 const bool fits = n_h < kGroup ||
@@ -406,7 +432,7 @@ __global__ void __launch_bounds__(TH, MINB) k_find(BuildArgs a, int tau) {
             store_pred_rec(a.w.pr + (int64_t)sl * pred_bytes<F>(), q);
         }
         int4* lrec = a.w.ls + (int64_t)sl * 5;
-        lrec[0] = make_int4(n_h, nh_kind, __float_as_int(nh_score), 0);
+        lrec[0] = make_int4(n_h, nh_kind, __float_as_int(nh_score), MOD ? b2 : -1);
         for (int j = 0; j < n_h; j += 2)
             lrec[1 + j / 2] = make_int4(__float_as_int(s_x2[j][tx]), s_hq[j][tx],
                                         __float_as_int(j + 1 < n_h ? s_x2[j + 1][tx] : kBig),
@@ -416,7 +442,7 @@ __global__ void __launch_bounds__(TH, MINB) k_find(BuildArgs a, int tau) {
 }
 
 // ---- a10-a11 for every seed with a live candidate in round tau
-template <class F, int TH, int MINB>
+template <class F, int TH, int MINB, bool MOD = false>
 __global__ void __launch_bounds__(TH, MINB) k_select(BuildArgs a, int tau) {
     __shared__ DevGeom g;
     load_geom_smem(a.geom, g);
@@ -444,6 +470,7 @@ __global__ void __launch_bounds__(TH, MINB) k_select(BuildArgs a, int tau) {
 
         int nh_kind = K_NONE;
         float nh_score = -kBig;
+        int b1q = -1, b2q = -1;   // the parent's best module hit and best hit on another module
         float lx[kGroup];
         int lq[kGroup];
 #pragma unroll
@@ -473,16 +500,24 @@ __global__ void __launch_bounds__(TH, MINB) k_select(BuildArgs a, int tau) {
                         lq[j + 1] = e[1 + j / 2].w;
                     }
                 }
+                if constexpr (MOD) {
+                    b2q = e[0].w;
+                    b1q = e[0].x > 0 ? lq[0] : -1;
+                }
             }
         }
+        // a parent whose accepted module hits span two modules gives every hit child an overlap
+        // hit (Sec. 2.2) and its score
+        const float ovl_bonus = MOD && b2q >= 0 ? P.score_overlap : 0.0f;
 
         // ---- the N best children of the seed (a10)
         bool nh_avail = nh_kind != K_NONE;
-        int my_parent = -1, my_kind = K_NONE, my_q = 0;
+        int my_parent = -1, my_kind = K_NONE, my_q = 0, my_b1 = -1, my_b2 = -1;
         float my_x2 = 0.0f, my_score = 0.0f;
         for (int r = 0; r < P.max_cands; ++r) {
             const bool has_hit = lx[0] < kBig;
-            const float hit_score = score + P.score_hit - lx[0];
+            float hit_score = score + P.score_hit - lx[0];
+            if constexpr (MOD) hit_score += ovl_bonus;
             int hk = K_NONE;
             float hs = 0.0f;
             if (has_hit && (!nh_avail || hit_score >= nh_score)) {
@@ -512,6 +547,13 @@ __global__ void __launch_bounds__(TH, MINB) k_select(BuildArgs a, int tau) {
                 my_x2 = w_x2;
                 my_score = w_score;
             }
+            if constexpr (MOD) {
+                const int w_b1 = shfl_i(b1q, src), w_b2 = shfl_i(b2q, src);
+                if (valid && slot == r) {
+                    my_b1 = w_b1;
+                    my_b2 = w_b2;
+                }
+            }
             if (valid && slot == wslot) {
                 if (hk == K_HIT) {
 #pragma unroll
@@ -535,6 +577,7 @@ __global__ void __launch_bounds__(TH, MINB) k_select(BuildArgs a, int tau) {
         int code = MKGB_HIT_STOP;
         const int csl = i * kGroup + slot;
         bool rescue = false;
+        int ovl = -1;
         if (gact && my_kind != K_NONE) {
             const int psl = i * kGroup + my_parent;
             c_alive = true;
@@ -550,10 +593,25 @@ __global__ void __launch_bounds__(TH, MINB) k_select(BuildArgs a, int tau) {
                 StateT<F> t;
                 if (my_kind == K_HIT) {
                     F m[3], v[6];
-                    int id;
-                    load_hit(a.H.hb_pay, my_q, m, v, &id);
+                    int id, md = -1;
+                    if constexpr (MOD)
+                        load_hit(a.H.hb_pay, my_q, m, v, &id, &md);
+                    else
+                        load_hit(a.H.hb_pay, my_q, m, v, &id);
                     float kap = 0.0f;
-                    if (kalman_update(L.kind, pq, m[0], m[1], m[2], v, t, &kap)) {
+                    bool ok;
+                    if (MOD && md >= 0) {   // a module hit: the update on its module's plane (Sec. 3.1)
+                        F x2u;
+                        ok = module_update(L.kind, pq, g.mods, md, g.cB, m, v, 0.0f, t, x2u, kap) == 0;
+                        if (my_b2 >= 0) {   // the overlap hit: b1 unless the hit is on b1's module
+                            const int m1 = __float_as_int(__ldg(a.H.hb_pay + 3 * (int64_t)my_b1 + 2).z);
+                            const int oq = md != m1 ? my_b1 : my_b2;
+                            ovl = __float_as_int(__ldg(a.H.hb_pay + 3 * (int64_t)oq).w);
+                        }
+                    } else {
+                        ok = kalman_update(L.kind, pq, m[0], m[1], m[2], v, t, &kap);
+                    }
+                    if (ok) {
                         chi2s += my_x2;
                         ++nfound;
                         ++c_upd;
@@ -576,6 +634,7 @@ __global__ void __launch_bounds__(TH, MINB) k_select(BuildArgs a, int tau) {
                 store_state_rec(a.w.st[nxt] + (int64_t)csl * state_bytes<F>(), t);
             }
             a.w.trail[((int64_t)i * a.max_steps + tau) * kGroup + slot] = ((code + 4) << 3) | my_parent;
+            if (MOD && a.w.otrail) a.w.otrail[((int64_t)i * a.max_steps + tau) * kGroup + slot] = c_alive ? ovl : -1;
         }
         const bool more = gact && tau + 1 < si.z;
         const unsigned am = __ballot_sync(kFull, c_alive);
@@ -628,9 +687,18 @@ __global__ void __launch_bounds__(kThreads) k_rescue(BuildArgs a, int tau) {
         // up through the hit id in the payload's original order
         const int id = (v >> 3) - 4;
         double m[3], vv[6];
-        load_hit(a.H.pay, id, m, vv, nullptr);
+        int md;
+        load_hit(a.H.pay, id, m, vv, nullptr, &md);
         StateT<double> td;
-        if (kalman_update(lkind, qd, m[0], m[1], m[2], vv, td)) {
+        bool ok;
+        if (md >= 0) {
+            double x2u;
+            float kap;
+            ok = module_update(lkind, qd, g.mods, md, g.cB, m, vv, 0.0f, td, x2u, kap) == 0;
+        } else {
+            ok = kalman_update(lkind, qd, m[0], m[1], m[2], vv, td);
+        }
+        if (ok) {
             State t;
             narrow_state(td, t);
             store_state_rec(a.w.st[nxt] + (int64_t)csl * state_bytes<float>(), t);
@@ -656,7 +724,11 @@ __global__ void __launch_bounds__(kThreads) k_finish(BuildArgs a) {
     const int best = gm ? __ffs(gm) - 1 : -1;
     const int seed = a.S.order[i];
     int* hrow = a.out.hits + (int64_t)seed * a.out.max_plan;
-    for (int q = slot; q < a.out.max_plan; q += kGroup) hrow[q] = MKGB_HIT_PRE;
+    int* orow = a.out.ovl ? a.out.ovl + (int64_t)seed * a.out.max_plan : nullptr;
+    for (int q = slot; q < a.out.max_plan; q += kGroup) {
+        hrow[q] = MKGB_HIT_PRE;
+        if (orow) orow[q] = -1;
+    }
     __syncwarp(0xffu << gbase);
     if (slot != (best >= 0 ? best : 0)) return;
     float* po = a.out.params + 6 * (int64_t)seed;
@@ -672,8 +744,10 @@ __global__ void __launch_bounds__(kThreads) k_finish(BuildArgs a) {
         const int4 si = a.w.sinfo[i];
         int s_ = best;
         for (int tau = si.z - 1; tau >= 0; --tau) {
-            const int v = a.w.trail[((int64_t)i * a.max_steps + tau) * kGroup + s_];
+            const int64_t at = ((int64_t)i * a.max_steps + tau) * kGroup + s_;
+            const int v = a.w.trail[at];
             hrow[si.y + tau] = (v >> 3) - 4;
+            if (orow && a.w.otrail) orow[si.y + tau] = a.w.otrail[at];
             s_ = v & 7;
         }
     } else {
@@ -701,7 +775,7 @@ namespace {
 
 // Carves the work buffers out of one allocation (256-byte aligned pieces); with base == nullptr
 // only the total size is computed.
-size_t layout_build_work(char* base, int n_seeds, int max_plan_len, int word_bytes, BuildWork* w) {
+size_t layout_build_work(char* base, int n_seeds, int max_plan_len, int word_bytes, bool with_ovl, BuildWork* w) {
     const size_t ns = (size_t)n_seeds, slots = ns * kGroup, wb = (size_t)word_bytes;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -723,6 +797,7 @@ size_t layout_build_work(char* base, int n_seeds, int max_plan_len, int word_byt
     t.sinfo = reinterpret_cast<int4*>(take(ns * 16));
     t.fin = reinterpret_cast<int*>(take(ns * 4));
     t.trail = reinterpret_cast<int*>(take(ns * (size_t)max_plan_len * kGroup * 4));
+    t.otrail = with_ovl ? reinterpret_cast<int*>(take(ns * (size_t)max_plan_len * kGroup * 4)) : nullptr;
     t.rescue = reinterpret_cast<int*>(take(slots * 4));
     t.counts = reinterpret_cast<int*>(take(32));
     if (w) *w = t;
@@ -765,59 +840,65 @@ __global__ void __launch_bounds__(kThreads) k_bw_seed(const DevGeom* __restrict_
 // Launch shapes of the round kernels (threads per block, minimum resident blocks per SM), one of
 // which the autotuner picks: k_find x k_select.  The resident grid of each shape is computed once,
 // before any capture.
-template <class F, int TH, int MINB, bool BWD = false> struct FindShape {
+template <class F, int TH, int MINB, bool BWD = false, bool MOD = false> struct FindShape {
     static int grid(int n_sms) {
         static int g = 0;
-        if (!g) g = resident_grid((const void*)k_find<F, TH, MINB, BWD>, n_sms, TH);
+        if (!g) g = resident_grid((const void*)k_find<F, TH, MINB, BWD, MOD>, n_sms, TH);
         return g;
     }
     static void launch(cudaStream_t st, const BuildArgs& a, int tau, int n_sms) {
-        k_find<F, TH, MINB, BWD><<<grid(n_sms), TH, 0, st>>>(a, tau);
+        k_find<F, TH, MINB, BWD, MOD><<<grid(n_sms), TH, 0, st>>>(a, tau);
     }
 };
-template <class F, int TH, int MINB> struct SelectShape {
+template <class F, int TH, int MINB, bool MOD = false> struct SelectShape {
     static int grid(int n_sms) {
         static int g = 0;
-        if (!g) g = resident_grid((const void*)k_select<F, TH, MINB>, n_sms, TH);
+        if (!g) g = resident_grid((const void*)k_select<F, TH, MINB, MOD>, n_sms, TH);
         return g;
     }
     static void launch(cudaStream_t st, const BuildArgs& a, int tau, int n_sms) {
-        k_select<F, TH, MINB><<<grid(n_sms), TH, 0, st>>>(a, tau);
+        k_select<F, TH, MINB, MOD><<<grid(n_sms), TH, 0, st>>>(a, tau);
     }
 };
+
+template <class F, bool MOD> void prime_shapes_of(int n_sms) {
+    FindShape<F, 64, 8, false, MOD>::grid(n_sms);
+    FindShape<F, 128, 1, false, MOD>::grid(n_sms);
+    FindShape<F, 256, 1, false, MOD>::grid(n_sms);
+    SelectShape<F, 64, 10, MOD>::grid(n_sms);
+    SelectShape<F, 128, 5, MOD>::grid(n_sms);
+    SelectShape<F, 256, 2, MOD>::grid(n_sms);
+}
 
 template <class F> void prime_shapes(int n_sms) {
     if (sizeof(F) == 4) FindShape<float, 128, 1, true>::grid(n_sms);
-    FindShape<F, 64, 8>::grid(n_sms);
-    FindShape<F, 128, 1>::grid(n_sms);
-    FindShape<F, 256, 1>::grid(n_sms);
-    SelectShape<F, 64, 10>::grid(n_sms);
-    SelectShape<F, 128, 5>::grid(n_sms);
-    SelectShape<F, 256, 2>::grid(n_sms);
+    prime_shapes_of<F, false>(n_sms);
+    prime_shapes_of<F, true>(n_sms);
 }
 
-template <class F, bool BWD = false>
+template <class F, bool BWD = false, bool MOD = false>
 void launch_find(int shape, cudaStream_t st, const BuildArgs& a, int tau, int n_sms) {
-    if constexpr (BWD) {   // the backward search: one shape, FP32 only
+    if constexpr (BWD) {   // the backward search: one shape, FP32 only, no module hits
         FindShape<F, 128, 1, true>::launch(st, a, tau, n_sms);
         return;
     }
     switch (shape) {
-        case 1: FindShape<F, 64, 8>::launch(st, a, tau, n_sms); break;
-        case 2: FindShape<F, 256, 1>::launch(st, a, tau, n_sms); break;
-        default: FindShape<F, 128, 1>::launch(st, a, tau, n_sms); break;
+        case 1: FindShape<F, 64, 8, false, MOD>::launch(st, a, tau, n_sms); break;
+        case 2: FindShape<F, 256, 1, false, MOD>::launch(st, a, tau, n_sms); break;
+        default: FindShape<F, 128, 1, false, MOD>::launch(st, a, tau, n_sms); break;
     }
 }
 
-template <class F> void launch_select(int shape, cudaStream_t st, const BuildArgs& a, int tau, int n_sms) {
+template <class F, bool MOD = false>
+void launch_select(int shape, cudaStream_t st, const BuildArgs& a, int tau, int n_sms) {
     switch (shape) {
-        case 1: SelectShape<F, 64, 10>::launch(st, a, tau, n_sms); break;
-        case 2: SelectShape<F, 256, 2>::launch(st, a, tau, n_sms); break;
-        default: SelectShape<F, 128, 5>::launch(st, a, tau, n_sms); break;
+        case 1: SelectShape<F, 64, 10, MOD>::launch(st, a, tau, n_sms); break;
+        case 2: SelectShape<F, 256, 2, MOD>::launch(st, a, tau, n_sms); break;
+        default: SelectShape<F, 128, 5, MOD>::launch(st, a, tau, n_sms); break;
     }
 }
 
-template <class F, bool BWD = false>
+template <class F, bool BWD = false, bool MOD = false>
 cudaError_t launch_rounds(cudaStream_t st, const BuildArgs& a, int n, int max_plan_len, int n_sms, int find_shape,
                           int select_shape) {
     cudaError_t e = cudaMemsetAsync(a.w.counts, 0, 32, st);
@@ -825,8 +906,8 @@ cudaError_t launch_rounds(cudaStream_t st, const BuildArgs& a, int n, int max_pl
     const int nb = (n + kThreads - 1) / kThreads;
     k_start<F><<<nb, kThreads, 0, st>>>(a);
     for (int tau = 0; tau < max_plan_len; ++tau) {
-        launch_find<F, BWD>(find_shape, st, a, tau, n_sms);
-        launch_select<F>(select_shape, st, a, tau, n_sms);
+        launch_find<F, BWD, MOD>(find_shape, st, a, tau, n_sms);
+        launch_select<F, MOD>(select_shape, st, a, tau, n_sms);
         if (sizeof(F) == 4 && a.P.kappa_fp64 > 0.0f) k_rescue<<<n_sms, kThreads, 0, st>>>(a, tau);
     }
     k_finish<F><<<(n * kGroup + kThreads - 1) / kThreads, kThreads, 0, st>>>(a);
@@ -836,9 +917,13 @@ cudaError_t launch_rounds(cudaStream_t st, const BuildArgs& a, int n, int max_pl
 cudaError_t enqueue_rounds(cudaStream_t st, const BuildArgs& a, int n, int max_plan_len, int n_sms, int find_shape,
                            int select_shape, bool backward = false) {
     if (backward) return launch_rounds<float, true>(st, a, n, max_plan_len, n_sms, find_shape, select_shape);
+    // module hits loaded (their overlap trail exists): the module-aware kernels
+    const bool mod = a.w.otrail != nullptr;
     // MKGB_FP64: the plain all-FP64 comparison path (same rounds, every Kalman step in FP64)
-    return a.P.precision == MKGB_FP64
-               ? launch_rounds<double>(st, a, n, max_plan_len, n_sms, find_shape, select_shape)
+    if (a.P.precision == MKGB_FP64)
+        return mod ? launch_rounds<double, false, true>(st, a, n, max_plan_len, n_sms, find_shape, select_shape)
+                   : launch_rounds<double>(st, a, n, max_plan_len, n_sms, find_shape, select_shape);
+    return mod ? launch_rounds<float, false, true>(st, a, n, max_plan_len, n_sms, find_shape, select_shape)
                : launch_rounds<float>(st, a, n, max_plan_len, n_sms, find_shape, select_shape);
 }
 
@@ -851,13 +936,14 @@ bool capturable(cudaStream_t st) {
 
 }  // namespace
 
-size_t build_work_bytes(int n_seeds, int max_plan_len, int precision) {
-    return layout_build_work(nullptr, n_seeds, max_plan_len, precision == MKGB_FP64 ? 8 : 4, nullptr);
+size_t build_work_bytes(int n_seeds, int max_plan_len, int precision, bool with_ovl) {
+    return layout_build_work(nullptr, n_seeds, max_plan_len, precision == MKGB_FP64 ? 8 : 4, with_ovl, nullptr);
 }
 
-BuildWork carve_build_work(void* base, int n_seeds, int max_plan_len, int precision) {
+BuildWork carve_build_work(void* base, int n_seeds, int max_plan_len, int precision, bool with_ovl) {
     BuildWork w;
-    layout_build_work(static_cast<char*>(base), n_seeds, max_plan_len, precision == MKGB_FP64 ? 8 : 4, &w);
+    layout_build_work(static_cast<char*>(base), n_seeds, max_plan_len, precision == MKGB_FP64 ? 8 : 4, with_ovl,
+                      &w);
     return w;
 }
 

@@ -25,8 +25,9 @@ __device__ __forceinline__ void load_geom(const DevGeom* __restrict__ gp, DevGeo
     __syncthreads();
 }
 
-// One track in precision F; returns its status and the largest kappa(S) of its updates.
-template <class F>
+// One track in precision F; returns its status and the largest kappa(S) of its updates.  MOD:
+// module hits loaded (used on their module planes).
+template <class F, bool MOD>
 __device__ __forceinline__ int fit_track(const DevGeom& g, const DevParams& P, const float4* __restrict__ pay,
                                          int64_t n_hits, int max_steps, const int* __restrict__ lrow,
                                          const int* __restrict__ hrow, const float* p0, const float* c0,
@@ -51,7 +52,22 @@ __device__ __forceinline__ int fit_track(const DevGeom& g, const DevParams& P, c
         if (h >= 0) {
             F m[3], v[6], x2;
             float kap = 0.0f;
-            load_hit(pay, h, m, v, nullptr);
+            int md = -1;
+            if constexpr (MOD)
+                load_hit(pay, h, m, v, nullptr, &md);
+            else
+                load_hit(pay, h, m, v, nullptr);
+            if (MOD && md >= 0) {   // a module hit is used on its module's plane (Sec. 3.1)
+                const int r = module_update(L.kind, q, g.mods, md, g.cB, m, v, P.fit_outlier_chi2, t, x2, kap);
+                if (r == 1 || r == 3) pred_to_state(L.kind, q, t);   // not reached; outlier: not used
+                if (r == 1) return 1;
+                if (r == 2) return 3;
+                if (r == 3) continue;
+                kmax = fmaxf(kmax, kap);
+                sum += x2;
+                ++c_upd;
+                continue;
+            }
             if (!chi2_hit(L.kind, q, m[0], m[1], m[2], v, x2)) return 3;
             if (P.fit_outlier_chi2 > 0.0f && x2 > F(P.fit_outlier_chi2)) {   // outlier: not used
                 pred_to_state(L.kind, q, t);
@@ -68,6 +84,7 @@ __device__ __forceinline__ int fit_track(const DevGeom& g, const DevParams& P, c
     return 0;
 }
 
+template <bool MOD>
 __global__ void __launch_bounds__(kThreads) k_fit(const DevGeom* __restrict__ gp, DevParams P,
                                                   const float4* __restrict__ pay, int64_t n_hits, int n, int max_steps,
                                                   const int* __restrict__ layers, const int* __restrict__ hits,
@@ -84,7 +101,7 @@ __global__ void __launch_bounds__(kThreads) k_fit(const DevGeom* __restrict__ gp
     if (i < n) {
         State t;
         float sum, kmax;
-        const int status = fit_track<float>(g, P, pay, n_hits, max_steps, layers + (int64_t)i * max_steps,
+        const int status = fit_track<float, MOD>(g, P, pay, n_hits, max_steps, layers + (int64_t)i * max_steps,
                                             hits + (int64_t)i * max_steps, p0 + 6 * (int64_t)i, c0 + 21 * (int64_t)i,
                                             t, sum, kmax, c_steps, c_upd, c_newton);
         store_state6(t, p_out + 6 * (int64_t)i, c_out + 21 * (int64_t)i);
@@ -109,6 +126,7 @@ __global__ void __launch_bounds__(kThreads) k_fit(const DevGeom* __restrict__ gp
 }
 
 // FP64 refit of the listed tracks (kappa rescue) or of all tracks (all-FP64 path, list == null).
+template <bool MOD>
 __global__ void __launch_bounds__(kThreads) k_fit64(const DevGeom* __restrict__ gp, DevParams P,
                                                     const float4* __restrict__ pay, int64_t n_hits, int n,
                                                     int max_steps, const int* __restrict__ layers,
@@ -127,7 +145,7 @@ __global__ void __launch_bounds__(kThreads) k_fit64(const DevGeom* __restrict__ 
         StateT<double> t;
         double sum;
         float kmax;
-        const int status = fit_track<double>(g, P, pay, n_hits, max_steps, layers + (int64_t)i * max_steps,
+        const int status = fit_track<double, MOD>(g, P, pay, n_hits, max_steps, layers + (int64_t)i * max_steps,
                                              hits + (int64_t)i * max_steps, p0 + 6 * (int64_t)i, c0 + 21 * (int64_t)i,
                                              t, sum, kmax, c_steps, c_upd, c_newton);
         store_state6(t, p_out + 6 * (int64_t)i, c_out + 21 * (int64_t)i);
@@ -210,20 +228,22 @@ __global__ void __launch_bounds__(kThreads) k_step_update(int n, const float* __
 cudaError_t launch_fit(cudaStream_t st, const DevGeom* g, DevParams P, const float4* pay, int64_t n_hits, int n,
                        int max_steps, const int* layers, const int* hits, const float* p0, const float* c0,
                        float* p_out, float* c_out, float* chi2_out, int* status_out, unsigned long long* counters,
-                       int* rescue_list, int* rescue_count, int n_sms) {
+                       int* rescue_list, int* rescue_count, int n_sms, bool modular) {
     if (n == 0) return cudaSuccess;
     const int blocks = (n + kThreads - 1) / kThreads;
+    auto fit64 = modular ? k_fit64<true> : k_fit64<false>;
     if (P.precision == MKGB_FP64) {
-        k_fit64<<<blocks, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p0, c0, p_out, c_out,
-                                            chi2_out, status_out, counters, nullptr, nullptr);
+        fit64<<<blocks, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p0, c0, p_out, c_out,
+                                          chi2_out, status_out, counters, nullptr, nullptr);
         return cudaGetLastError();
     }
-    k_fit<<<blocks, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p0, c0, p_out, c_out, chi2_out,
-                                      status_out, counters, rescue_list, rescue_count);
+    auto fit = modular ? k_fit<true> : k_fit<false>;
+    fit<<<blocks, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p0, c0, p_out, c_out, chi2_out,
+                                    status_out, counters, rescue_list, rescue_count);
     if (P.kappa_fp64 > 0.0f && rescue_list) {
         const int rb = blocks < 2 * n_sms ? blocks : 2 * n_sms;
-        k_fit64<<<rb, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p0, c0, p_out, c_out,
-                                        chi2_out, status_out, counters, rescue_list, rescue_count);
+        fit64<<<rb, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p0, c0, p_out, c_out,
+                                      chi2_out, status_out, counters, rescue_list, rescue_count);
     }
     return cudaGetLastError();
 }

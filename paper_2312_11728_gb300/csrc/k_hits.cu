@@ -29,7 +29,8 @@ __device__ __forceinline__ int upper_seg(const int64_t* __restrict__ off, int n_
 __global__ void __launch_bounds__(kThreads) k_hit_prep(const DevGeom* __restrict__ g, int n_layers,
                                                        const int64_t* __restrict__ seg_off, int n_seg,
                                                        int64_t n_hits, const float* __restrict__ xyz,
-                                                       const float* __restrict__ cov, int bins_per_event,
+                                                       const float* __restrict__ cov,
+                                                       const int* __restrict__ hit_mod, int bins_per_event,
                                                        float4* __restrict__ pay, float2* __restrict__ ep_tmp,
                                                        int* __restrict__ bin_of_hit, int* __restrict__ hit_seg,
                                                        int* __restrict__ counts) {
@@ -44,7 +45,7 @@ __global__ void __launch_bounds__(kThreads) k_hit_prep(const DevGeom* __restrict
         for (int j = 0; j < 6; ++j) v[j] = __ldg(cov + 6 * i + j);
         pay[3 * i] = make_float4(x, y, z, __int_as_float((int)i));
         pay[3 * i + 1] = make_float4(v[0], v[1], v[2], v[3]);
-        pay[3 * i + 2] = make_float4(v[4], v[5], 0.0f, 0.0f);
+        pay[3 * i + 2] = make_float4(v[4], v[5], __int_as_float(hit_mod ? __ldg(hit_mod + i) : -1), 0.0f);
         const float eta = asinhf(z / sqrtf(x * x + y * y));
         const float phi = atan2f(y, x);
         const float fe = (eta - L.eta_lo) * L.eta_scale;
@@ -147,13 +148,43 @@ int grid_for(int64_t n) {
     return (int)(b < 1 ? 1 : (b > 152 * 64 ? 152 * 64 : b));
 }
 
+// Hits whose module does not fit their layer: a module hit on a layer without modules or on another
+// layer's module, a hit without module on a modular layer, a module index out of range.
+__global__ void __launch_bounds__(kThreads) k_check_modules(const DevGeom* __restrict__ g, int n_layers,
+                                                            int64_t n_hits, const int* __restrict__ hit_seg,
+                                                            const int* __restrict__ hit_mod, int* bad) {
+    int nb = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_hits;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int l = hit_seg[i] % n_layers;
+        const int m = hit_mod[i];
+        const bool modular = g->layers[l].modular != 0;
+        bool ok;
+        if (m < 0) {
+            ok = m == -1 && !modular;
+        } else {
+            ok = modular && m < g->n_mods && __float_as_int(__ldg(g->mods + 2 * m).w) == l;
+        }
+        nb += ok ? 0 : 1;
+    }
+    if (nb) atomicAdd(bad, nb);
+}
+
 }  // namespace
 
-cudaError_t launch_hit_prep(cudaStream_t st, const DevGeom* g, int n_layers, const int64_t* seg_off, int n_seg,
-                            int64_t n_hits, const float* xyz, const float* cov, int bins_per_event, float4* pay,
-                            float2* ep_tmp, int* bin_of_hit, int* hit_seg, int* counts) {
+cudaError_t launch_check_modules(cudaStream_t st, const DevGeom* g, int n_layers, int64_t n_hits,
+                                 const int* hit_seg, const int* hit_mod, int* bad) {
     if (n_hits == 0) return cudaSuccess;
-    k_hit_prep<<<grid_for(n_hits), kThreads, 0, st>>>(g, n_layers, seg_off, n_seg, n_hits, xyz, cov,
+    k_check_modules<<<grid_for(n_hits), kThreads, 0, st>>>(g, n_layers, n_hits, hit_seg, hit_mod, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hit_prep(cudaStream_t st, const DevGeom* g, int n_layers, const int64_t* seg_off, int n_seg,
+                            int64_t n_hits, const float* xyz, const float* cov, const int* hit_mod,
+                            int bins_per_event, float4* pay, float2* ep_tmp, int* bin_of_hit, int* hit_seg,
+                            int* counts) {
+    if (n_hits == 0) return cudaSuccess;
+    k_hit_prep<<<grid_for(n_hits), kThreads, 0, st>>>(g, n_layers, seg_off, n_seg, n_hits, xyz, cov, hit_mod,
                                                       bins_per_event, pay, ep_tmp, bin_of_hit, hit_seg, counts);
     return cudaGetLastError();
 }

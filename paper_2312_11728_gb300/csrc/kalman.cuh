@@ -57,16 +57,21 @@ struct DevLayer {
     int n_eta, n_phi;
     float eta_lo, eta_scale;   // bin = floor((eta - eta_lo) * eta_scale)
     int bin_base;              // first bin of this layer inside an event's bin block
-    int pad;
+    int modular;               // 1: the layer is built from flat modules (its hits lie on module planes)
 };
 
-struct DevGeom {
+// 16-byte aligned so that kernels copy it into shared memory as whole int4 words.
+struct alignas(16) DevGeom {
     int n_layers, n_regions, bins_per_event, max_plan;
     float bz, cB, barrel_eta_max, pad;
     DevLayer layers[MKGB_MAX_LAYERS];
     int plan_off[MKGB_MAX_REGIONS + 1];
     int plan[MKGB_MAX_REGIONS * MKGB_MAX_PLAN];
+    // module planes (Sec. 3.1): per module (cx, cy, cz, layer) and (nx, ny, nz, 0); nullptr: none
+    const float4* mods;
+    int n_mods;
 };
+static_assert(sizeof(DevGeom) % 16 == 0, "DevGeom is copied as int4 words");
 
 struct DevParams {
     float chi2_cut;
@@ -76,6 +81,7 @@ struct DevParams {
     int precision;      // MKGB_FP32: FP32 Kalman steps (FP64 seed fit); MKGB_FP64: every step in FP64
     float kappa_fp64;   // fit: tracks with an update whose S condition estimate exceeds this are refit in FP64
     float fit_outlier_chi2;   // fits: a listed hit with a predicted chi2 above this is not used (0: off)
+    float score_overlap;      // search: score of a picked-up overlap hit (Sec. 2.2)
 };
 
 // Packed lower-triangle index of a symmetric matrix (i, j >= 0).
@@ -746,6 +752,246 @@ template <class F>
 __device__ __forceinline__ int propagate_refined(const DevLayer& L, float cBf, int material, const StateT<F>& t,
                                                  PredT<F>& q, int& newton_it, bool fast, F* dir = nullptr);
 
+// ----------------------------------------------------------------- module planes (Sec. 3.1)
+//
+// A Phase-2 module is flat (and tilted in the outer rings of the barrel): a hit on a module is
+// measured on the plane through the module's position c with unit normal n.  The search and the
+// fit take the state on the layer's reference surface (cylinder or disk: window, material,
+// binning) and move it along the helix to the hit's module plane before its chi2 and update.
+// The step is a few millimetres, in either direction, and crosses no material.
+
+constexpr float kPlaneMaxPath = 10.0f;   // cm: longest |s| accepted for the step to a module
+constexpr float kPlaneMinCos = 1e-3f;    // smallest |n . dx/ds| (per transverse path) accepted
+
+// Frame of a state on a plane with unit normal n: e1 the direction projected onto the plane,
+// e2 = n x e1 (for n = r-hat this is the barrel frame of frame_of).
+template <class F> __device__ __forceinline__ FrameT<F> plane_frame(const F n[3], F sfp, F cfp, F st, F ct) {
+    FrameT<F> f;
+    const F d[3] = {st * cfp, st * sfp, ct};
+    const F dn = dot3(n, d);
+    F e[3] = {d[0] - dn * n[0], d[1] - dn * n[1], d[2] - dn * n[2]};
+    F nrm2 = dot3(e, e);
+    if (!(nrm2 > F(1e-12))) {   // moving along the normal: any axis of the plane
+        const F a[3] = {fabs(n[2]) < F(0.9) ? F(0) : F(1), F(0), fabs(n[2]) < F(0.9) ? F(1) : F(0)};
+        const F an = dot3(a, n);
+        e[0] = a[0] - an * n[0]; e[1] = a[1] - an * n[1]; e[2] = a[2] - an * n[2];
+        nrm2 = dot3(e, e);
+    }
+    const F inv = rsq(nrm2);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        f.n[i] = n[i];
+        f.e1[i] = e[i] * inv;
+    }
+    f.e2[0] = n[1] * f.e1[2] - n[2] * f.e1[1];
+    f.e2[1] = n[2] * f.e1[0] - n[0] * f.e1[2];
+    f.e2[2] = n[0] * f.e1[1] - n[1] * f.e1[0];
+    return f;
+}
+
+// Moves t (global frame, on or near a surface) to the plane through cm.xyz with normal nm.xyz:
+// the crossing nearest to t (Newton on g(s) = n.(u + d(s) - c) from the tangent-line root,
+// written relative to the current position; the crossing point polished onto the plane with the
+// compensated gap), the Jacobian of the plane map and the covariance transported into the plane
+// frame fr (q.c, 15).  Returns 1, or 0 if Newton fails, |s| > kPlaneMaxPath or the crossing is
+// grazing (|n . dx/ds| < kPlaneMinCos).  newton_it counts iterations.
+template <class F>
+__device__ __forceinline__ int propagate_plane(const StateT<F>& t, const float4 cm, const float4 nm, float cBf,
+                                               PredT<F>& q, FrameT<F>& fr, int& newton_it) {
+    const F cB = F(cBf);
+    const F n[3] = {F(nm.x), F(nm.y), F(nm.z)};
+    F sf, cf, st, ct;
+    sin_cos(t.phi, &sf, &cf);
+    sin_cos(t.th, &st, &ct);
+    {
+        const F s0 = st, f0 = sf;
+        st = fma(ct, t.tl, st);
+        ct = fma(-s0, t.tl, ct);
+        sf = fma(cf, t.pl, sf);
+        cf = fma(-f0, t.pl, cf);
+    }
+    const F om = -cB * t.k;
+    const F cot = div_rn(ct, st);
+    // n.(c - u) with the compensated position: terms of the size of the distance, not of |c|
+    const F g0 = n[0] * sub_rn(sub_rn(F(cm.x), t.xh), t.xl) + n[1] * sub_rn(sub_rn(F(cm.y), t.yh), t.yl) +
+                 n[2] * sub_rn(sub_rn(F(cm.z), t.zh), t.zl);
+    const F dg0 = n[0] * cf + n[1] * sf + n[2] * cot;
+    if (dg0 == F(0)) return 0;
+    F s = g0 / dg0;
+    const F tol = is_fp32<F>() ? F(1e-6) : F(1e-13);
+    bool conv = false;
+    for (int it = 0; it < 20 && !conv; ++it) {
+        ++newton_it;
+        const F a = om * s;
+        F sh, ch;
+        sin_cos(F(0.5) * a, &sh, &ch);
+        const F sa = F(2) * sh * ch, oc = F(2) * sh * sh;
+        F S1, C1;
+        if (fabs(a) < F(1e-4)) {
+            S1 = F(1) - a * a * (F(1) / F(6));
+            C1 = a * (F(0.5) - a * a * (F(1) / F(24)));
+        } else {
+            S1 = sa / a;
+            C1 = oc / a;
+        }
+        const F dx = s * (cf * S1 - sf * C1), dy = s * (sf * S1 + cf * C1);
+        const F g = n[0] * dx + n[1] * dy + n[2] * (s * cot) - g0;
+        const F cpn = cf * (F(1) - oc) - sf * sa, spn = sf * (F(1) - oc) + cf * sa;
+        const F dg = n[0] * cpn + n[1] * spn + n[2] * cot;
+        if (dg == F(0)) return 0;
+        const F ds = -g / dg;
+        s += ds;
+        conv = fabs(ds) <= tol * (F(1) + fabs(s));
+    }
+    if (!conv || !(fabs(s) <= F(2 * kPlaneMaxPath))) return 0;
+    const F a = om * s;
+    F sh, ch;
+    sin_cos(F(0.5) * a, &sh, &ch);
+    const F sa = F(2) * sh * ch, ca = fma(F(-2) * sh, sh, F(1));
+    F S1, C1;
+    if (fabs(a) < F(1e-4)) {
+        S1 = F(1) - a * a * (F(1) / F(6));
+        C1 = a * (F(0.5) - a * a * (F(1) / F(24)));
+    } else {
+        S1 = sa / a;
+        C1 = F(2) * sh * sh / a;
+    }
+    F dx, dy;
+    {
+        const F sp = fma(sf, ch, cf * sh), cp = fma(cf, ch, -sf * sh);
+        const F h = F(0.5) * a;
+        F sinc;
+        if (fabs(h) < F(0.05)) {
+            const F h2 = h * h;
+            sinc = F(1) + h2 * (F(-1) / F(6) + h2 * (F(1) / F(120) + h2 * (F(-1) / F(5040) + h2 * (F(1) / F(362880)))));
+        } else {
+            sinc = div_rn(sh, h);
+        }
+        const F chord = s * sinc;
+        dx = chord * cp;
+        dy = chord * sp;
+    }
+    F xh = t.xh, xl = t.xl, yh = t.yh, yl = t.yl, zh = t.zh, zl = t.zl;
+    add_ff(xh, xl, dx);
+    add_ff(yh, yl, dy);
+    add_ff(zh, zl, s * cot);
+    const F sfp = fma(sf, ca, cf * sa), cfp = fma(cf, ca, -sf * sa);
+    const F den = n[0] * cfp + n[1] * sfp + n[2] * cot;   // n . dx/ds at the crossing
+    {   // polish onto the plane along the track with the compensated gap
+        const F gap = n[0] * sub_rn(sub_rn(F(cm.x), xh), xl) + n[1] * sub_rn(sub_rn(F(cm.y), yh), yl) +
+                      n[2] * sub_rn(sub_rn(F(cm.z), zh), zl);
+        const F dsp = div_rn(gap, den);
+        add_ff(xh, xl, dsp * cfp);
+        add_ff(yh, yl, dsp * sfp);
+        add_ff(zh, zl, dsp * cot);
+    }
+    if (!(fabs(s) <= F(kPlaneMaxPath)) || !(fabs(den) >= F(kPlaneMinCos))) return 0;
+
+    // ---- Jacobian: J = A + (df/ds)(ds/dp), ds/dp = -(n . A_pos) / (n . df/ds); rows k, theta identity
+    F dS1, dC1;
+    s1c1_deriv(a, S1, C1, dS1, dC1);
+    const F A03 = -cB * s * s * (cf * dS1 - sf * dC1);
+    const F A13 = -cB * s * s * (sf * dS1 + cf * dC1);
+    const F A04 = -dy, A14 = dx;
+    const F A25 = -s / (st * st);
+    const F A43 = -cB * s;
+    const F ig = F(-1) / den;
+    F ds[6];
+    ds[0] = n[0] * ig; ds[1] = n[1] * ig; ds[2] = n[2] * ig;
+    ds[3] = (n[0] * A03 + n[1] * A13) * ig;
+    ds[4] = (n[0] * A04 + n[1] * A14) * ig;
+    ds[5] = n[2] * A25 * ig;
+    fr = plane_frame(n, sfp, cfp, st, ct);
+    const F Apos[3][6] = {{F(1), F(0), F(0), A03, A04, F(0)},
+                          {F(0), F(1), F(0), A13, A14, F(0)},
+                          {F(0), F(0), F(1), F(0), F(0), A25}};
+    const F fpos[3] = {cfp, sfp, cot};
+    const F f1 = dot3(fr.e1, fpos);
+    F J[3][6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const F a1 = fr.e1[0] * Apos[0][j] + fr.e1[1] * Apos[1][j] + fr.e1[2] * Apos[2][j];
+        const F a2 = fr.e2[0] * Apos[0][j] + fr.e2[1] * Apos[1][j] + fr.e2[2] * Apos[2][j];
+        J[0][j] = fma(f1, ds[j], a1);
+        J[1][j] = a2;   // e2 . df/ds = 0: the direction projects onto e1
+        J[2][j] = om * ds[j];
+    }
+    J[2][3] += A43; J[2][4] += F(1);
+    constexpr int D[3] = {0, 1, 3};
+    F T[3][6];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            F acc = F(0);
+#pragma unroll
+            for (int l = 0; l < 6; ++l) acc = fma(J[r][l], t.c[ix(l, j)], acc);
+            T[r][j] = acc;
+        }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+        for (int p = 0; p <= r; ++p) {
+            F acc = F(0);
+#pragma unroll
+            for (int l = 0; l < 6; ++l) acc = fma(T[r][l], J[p][l], acc);
+            q.c[ix(D[r], D[p])] = acc;
+        }
+        q.c[ix(D[r], 2)] = T[r][3];
+        q.c[ix(4, D[r])] = T[r][5];
+    }
+    q.c[ix(2, 2)] = t.c[ix(3, 3)];
+    q.c[ix(4, 2)] = t.c[ix(5, 3)];
+    q.c[ix(4, 4)] = t.c[ix(5, 5)];
+    q.xh = xh; q.xl = xl; q.yh = yh; q.yl = yl; q.zh = zh; q.zl = zl;
+    q.k = t.k;
+    q.phi = t.phi;
+    q.pl = t.pl;
+    add_ff(q.phi, q.pl, a);
+    wrap_pi_ff(q.phi, q.pl);
+    q.th = t.th;
+    q.tl = t.tl;
+    return 1;
+}
+
+// The prediction q on a layer's reference surface (kind) moved to module mod's plane (table mods:
+// two float4 per module): qp and its frame fp.
+template <class F>
+__device__ __forceinline__ int to_module_plane(int kind, const PredT<F>& q, const float4* __restrict__ mods, int mod,
+                                               float cBf, PredT<F>& qp, FrameT<F>& fp) {
+    StateT<F> t;
+    pred_to_state(kind, q, t);
+    int it = 0;
+    return propagate_plane(t, __ldg(mods + 2 * mod), __ldg(mods + 2 * mod + 1), cBf, qp, fp, it);
+}
+
+// The chi2 of a module hit (m, v) on its module's plane, from the prediction q on the layer's
+// reference surface.  False if the plane is not reached or S is not positive definite.  The
+// module-hit steps below are not inlined, so that the search and fit kernels keep their
+// register allocation for the layers without modules.
+template <class F>
+__device__ __noinline__ bool module_chi2(int kind, const PredT<F>& q, const float4* __restrict__ mods, int mod,
+                                         float cBf, const F m[3], const F v[6], F& x2) {
+    PredT<F> qp;
+    FrameT<F> fp;
+    return to_module_plane(kind, q, mods, mod, cBf, qp, fp) && chi2_hit(fp, qp, m[0], m[1], m[2], v, x2);
+}
+
+// Update with a module hit on its module's plane.  Returns 0 (out updated), 1 (plane not reached),
+// 2 (the update failed) or, with outlier_cut > 0 and a predicted chi2 above it, 3 (out untouched).
+// x2 gets the predicted chi2, kappa the condition estimate of S.
+template <class F>
+__device__ __noinline__ int module_update(int kind, const PredT<F>& q, const float4* __restrict__ mods, int mod,
+                                          float cBf, const F m[3], const F v[6], float outlier_cut, StateT<F>& out,
+                                          F& x2, float& kappa) {
+    PredT<F> qp;
+    FrameT<F> fp;
+    if (!to_module_plane(kind, q, mods, mod, cBf, qp, fp)) return 1;
+    if (!chi2_hit(fp, qp, m[0], m[1], m[2], v, x2)) return 2;
+    if (outlier_cut > 0.0f && x2 > F(outlier_cut)) return 3;
+    return kalman_update_f(fp, qp, m[0], m[1], m[2], v, out, &kappa) ? 0 : 2;
+}
+
 // ----------------------------------------------------------------- window (a8)
 
 template <class F> struct WindowT {
@@ -1026,12 +1272,15 @@ __device__ __forceinline__ void narrow_state(const StateT<double>& d, State& t) 
     for (int i = 0; i < 21; ++i) t.c[i] = float(d.c[i]);
 }
 
-// Hit payload: 3 x float4 = (x, y, z, id) (v0, v1, v2, v3) (v4, v5, -, -)
+// Hit payload: 3 x float4 = (x, y, z, id) (v0, v1, v2, v3) (v4, v5, module, -); module -1: the hit
+// lies on its layer's own surface
 template <class F>
-__device__ __forceinline__ void load_hit(const float4* __restrict__ pay, long long q, F m[3], F v[6], int* id) {
+__device__ __forceinline__ void load_hit(const float4* __restrict__ pay, long long q, F m[3], F v[6], int* id,
+                                         int* mod = nullptr) {
     const float4 a = __ldg(pay + 3 * q), b = __ldg(pay + 3 * q + 1), c = __ldg(pay + 3 * q + 2);
     m[0] = F(a.x); m[1] = F(a.y); m[2] = F(a.z);
     if (id) *id = __float_as_int(a.w);
+    if (mod) *mod = __float_as_int(c.z);
     v[0] = F(b.x); v[1] = F(b.y); v[2] = F(b.z); v[3] = F(b.w); v[4] = F(c.x); v[5] = F(c.y);
 }
 

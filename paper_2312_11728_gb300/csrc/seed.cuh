@@ -23,7 +23,9 @@ __device__ __forceinline__ bool seed_prior(const DevGeom& g, const HitStore& H, 
         const int seg = H.hit_seg[id[j]];
         ev[j] = seg / H.n_layers;
         lay[j] = seg - ev[j] * H.n_layers;
-        load_hit(H.pay, id[j], m[j], v[j], nullptr);
+        int md;
+        load_hit(H.pay, id[j], m[j], v[j], nullptr, &md);
+        ok = ok && md < 0;   // the seed fit takes hits on the layers' own surfaces
     }
     event = ev[0];
     ok = ok && ev[0] == ev[1] && ev[1] == ev[2];

@@ -33,16 +33,18 @@ class Params(C.Structure):
                 ("win_nsigma", C.c_float), ("deta_min", C.c_float), ("deta_max", C.c_float),
                 ("dphi_min", C.c_float), ("dphi_max", C.c_float), ("score_hit", C.c_float),
                 ("score_hole", C.c_float), ("barrel_eta_max", C.c_float), ("material", C.c_int32),
-                ("precision", C.c_int32), ("kappa_fp64", C.c_float), ("fit_outlier_chi2", C.c_float)]
+                ("precision", C.c_int32), ("kappa_fp64", C.c_float), ("fit_outlier_chi2", C.c_float),
+                ("score_overlap", C.c_float)]
 
 
 class Tracks(C.Structure):
     _fields_ = [("params", C.c_void_p), ("cov", C.c_void_p), ("chi2", C.c_void_p), ("score", C.c_void_p),
-                ("nfound", C.c_void_p), ("nholes", C.c_void_p), ("hits", C.c_void_p), ("max_plan", C.c_int32)]
+                ("nfound", C.c_void_p), ("nholes", C.c_void_p), ("hits", C.c_void_p), ("max_plan", C.c_int32),
+                ("ovl_hits", C.c_void_p)]
 
 
 EXPORTS = ["mkgb_create", "mkgb_destroy", "mkgb_last_error", "mkgb_version", "mkgb_load_geometry",
-           "mkgb_set_params", "mkgb_load_hits", "mkgb_seed", "mkgb_build", "mkgb_build_backward", "mkgb_fit",
+           "mkgb_set_params", "mkgb_load_hits", "mkgb_load_modules", "mkgb_load_hits_modular", "mkgb_seed", "mkgb_build", "mkgb_build_backward", "mkgb_fit",
            "mkgb_fit_backward",
            "mkgb_fit_static", "mkgb_fit_grad", "mkgb_run", "mkgb_set_launch", "mkgb_autotune",
            "mkgb_probe_peak", "mkgb_clean_seeds", "mkgb_remove_duplicates", "mkgb_propagate", "mkgb_update",
@@ -192,14 +194,33 @@ class Context:
                    float(params["dphi_min"]), float(params["dphi_max"]), float(params["score_hit"]),
                    float(params["score_hole"]), float(params.get("barrel_eta_max", self.barrel_eta_max)),
                    int(params["material"]), int(params.get("precision", 0)),
-                   float(params.get("kappa_fp64", 0.0)), float(params.get("fit_outlier_chi2", 0.0)))
+                   float(params.get("kappa_fp64", 0.0)), float(params.get("fit_outlier_chi2", 0.0)),
+                   float(params.get("score_overlap", 0.0)))
         self._check(self.lib.mkgb_set_params(self.h, C.byref(p)), "mkgb_set_params")
 
     # ---- data
-    def load_hits(self, n_events, seg_off, xyz, cov):
+    def load_modules(self, modules):
+        """mkgb_load_modules: module planes (layer, position, unit normal) of a synth.Modules
+        table (None removes them)."""
+        if modules is None:
+            self._check(self.lib.mkgb_load_modules(self.h, 0, None, None, None), "mkgb_load_modules")
+            return
+        lay = np.ascontiguousarray(modules.layer, np.int32)
+        pos = np.ascontiguousarray(modules.c, np.float32)
+        nrm = np.ascontiguousarray(modules.n, np.float32)
+        self._check(self.lib.mkgb_load_modules(self.h, int(lay.shape[0]), lay.ctypes.data, pos.ctypes.data,
+                                               nrm.ctypes.data), "mkgb_load_modules")
+
+    def load_hits(self, n_events, seg_off, xyz, cov, hit_module=None):
+        """mkgb_load_hits, or mkgb_load_hits_modular when hit_module (module per hit) is given."""
         so = np.ascontiguousarray(seg_off, np.int64)
         px, dx = _ptr(xyz, np.float32)
         pc, dc = _ptr(cov, np.float32)
+        if hit_module is not None:
+            pm, dm = _ptr(hit_module, np.int32)
+            self._check(self.lib.mkgb_load_hits_modular(self.h, int(n_events), so.ctypes.data, px, pc, pm,
+                                                        _same(dx, dc, dm)), "mkgb_load_hits_modular")
+            return
         self._check(self.lib.mkgb_load_hits(self.h, int(n_events), so.ctypes.data, px, pc, _same(dx, dc)),
                     "mkgb_load_hits")
 
@@ -213,11 +234,14 @@ class Context:
         self.n_seeds = n
 
     def build(self, out: dict):
-        """out: dict of arrays params (n,6) cov (n,21) chi2 score nfound nholes hits (n, max_plan)."""
+        """out: dict of arrays params (n,6) cov (n,21) chi2 score nfound nholes hits (n, max_plan), and
+        optionally ovl (n, max_plan): the overlap hits on modular layers."""
         f, i = np.float32, np.int32
         ptrs = [_ptr(out[k], t, out=True) for k, t in (("params", f), ("cov", f), ("chi2", f), ("score", f),
                                               ("nfound", i), ("nholes", i), ("hits", i))]
-        t = Tracks(*[p for p, _ in ptrs], int(out["hits"].shape[1]))
+        if "ovl" in out:
+            ptrs.append(_ptr(out["ovl"], i, out=True))
+        t = Tracks(*[p for p, _ in ptrs[:7]], int(out["hits"].shape[1]), ptrs[7][0] if len(ptrs) > 7 else None)
         self._check(self.lib.mkgb_build(self.h, C.byref(t), _same(*[d for _, d in ptrs])), "mkgb_build")
         return out
 
@@ -351,11 +375,14 @@ class Context:
         return out
 
 
-def alloc_tracks(n, max_plan, device=None):
-    """Output arrays of Context.build: numpy (device None) or torch CUDA tensors."""
+def alloc_tracks(n, max_plan, device=None, ovl=False):
+    """Output arrays of Context.build: numpy (device None) or torch CUDA tensors; ovl adds the
+    overlap-hit array."""
     shapes = dict(params=((n, 6), np.float32), cov=((n, 21), np.float32), chi2=((n,), np.float32),
                   score=((n,), np.float32), nfound=((n,), np.int32), nholes=((n,), np.int32),
                   hits=((n, max_plan), np.int32))
+    if ovl:
+        shapes["ovl"] = ((n, max_plan), np.int32)
     if device is None:
         return {k: np.zeros(s, t) for k, (s, t) in shapes.items()}
     import torch

@@ -147,6 +147,8 @@ def run_host(ctx: mkgb.Context, batch: Batch, max_plan: int, fit: FitInputs | No
 def make_context(geom, params: dict, device: int = 0, stream=None) -> mkgb.Context:
     ctx = mkgb.Context(device, stream)
     ctx.load_geometry(geom)
+    if geom.modules is not None:   # modular layers: their hits are loaded with load_hits(hit_module=...)
+        ctx.load_modules(geom.modules)
     ctx.set_params(dict(params, barrel_eta_max=params.get("barrel_eta_max", geom.barrel_eta_max)))
     return ctx
 

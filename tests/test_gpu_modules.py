@@ -1,0 +1,190 @@
+"""Module planes and overlap hits on the GPU (Sec. 3.1 module position and normal: the Phase-2
+tilted barrel; Sec. 2.2: a single additional detector-overlap hit) against the oracle, on the same
+inputs: the Phase-2-like tracker with cylinders 3-5 built from flat and tilted modules.
+
+Search: hit lists and overlap hits bit-exact up to the first near-tie step the oracle flags;
+parameters, covariance and chi2 within the forward search's tolerances (oracle/parity.py).  Fit
+over the true assignment: the fit's tolerances."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import parity as PR
+from paper_2312_11728_gb300 import build as B
+from paper_2312_11728_gb300 import mkgb, pipeline, synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return mkgb.load_library()
+
+
+@pytest.fixture(scope="module")
+def work():
+    g = S.geometry_phase2_modular()
+    evs = [S.simulate_event(g, 1501, 41, e, pt_sampler=S.sample_pt_phase2, eta_max=3.0, noise_total=4000)
+           for e in range(3)]
+    return g, S.concat_events(evs, g.n_layers)
+
+
+def _ctx(g, batch, params):
+    ctx = pipeline.make_context(g, params)
+    ctx.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov, hit_module=batch.hit_mod)
+    return ctx
+
+
+def _oracle(g, batch, params):
+    orc = oracle.Oracle(g, params)
+    orc.set_modules(g.modules.c, g.modules.n, batch.hit_mod)
+    return orc
+
+
+def _check_ovl(out, o):
+    """Overlap hits equal up to each seed's first near-tie step (the whole row without a tie)."""
+    idx, mp = o["seed_index"], o["max_plan"]
+    bad = []
+    for k, si in enumerate(idx):
+        t = o["tie_step"][k]
+        n = mp if t < 0 else t
+        if not np.array_equal(out["ovl"][si, :n], o["ovl"][k, :n]):
+            bad.append(int(si))
+    return bad
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_modular_search_matches_oracle(lib, work, precision):
+    g, batch = work
+    params = S.default_params(precision=precision)
+    ctx = _ctx(g, batch, params)
+    ctx.seed(batch.seed_hits)
+    out = ctx.build(mkgb.alloc_tracks(batch.seed_hits.shape[0], g.max_plan, ovl=True))
+    o = PR.oracle_build(_oracle(g, batch, params), batch)
+    rep = PR.compare_build(out, o)
+    assert len(rep["hit_mismatch"]) == 0, rep
+    assert rep["failed_mismatch"] == 0 and rep["count_bad"] == 0, rep
+    assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0, rep
+    assert rep["n_tie"] < 0.05 * rep["n"], rep
+    assert _check_ovl(out, o) == []
+    # the modular layers are searched and overlap hits picked up
+    n_ovl = int((out["ovl"] >= 0).sum())
+    assert n_ovl > 0.05 * batch.seed_hits.shape[0], n_ovl
+    if precision == 0:
+        assert rep["worst_param"] < 0.5 and rep["worst_chi2"] < 0.5, rep
+
+
+def test_modular_fit_matches_oracle(lib, work):
+    g, batch = work
+    params = S.default_params()
+    ctx = _ctx(g, batch, params)
+    fi = pipeline.fit_inputs(batch)
+    n = fi.layers.shape[0]
+    f = dict(p=np.zeros((n, 6), np.float32), c=np.zeros((n, 21), np.float32), chi2=np.zeros(n, np.float32),
+             status=np.zeros(n, np.int32))
+    ctx.fit(fi.layers, fi.hits, fi.p0, fi.c0, f["p"], f["c"], f["chi2"], f["status"])
+    r = _oracle(g, batch, params).fit_batch(fi.layers, fi.hits, batch.hit_xyz.astype(np.float64),
+                                            batch.hit_cov.astype(np.float64), fi.p0, fi.c0)
+    rep = PR.compare_fit(f, r)
+    assert rep["status_bad"] == 0, rep
+    assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0, rep
+    assert rep["n"] > 0.95 * n
+    # the fit's work counters: crossed layers and updates as the oracle counts them
+    cg = ctx.counters(1)
+    assert cg[0] == r["counters"][0] and cg[2] == r["counters"][2]
+
+
+def test_modular_fit_outlier_and_fp64(lib, work):
+    """FP64 fit of modular tracks, and the outlier rule on module hits (a planted wrong hit on a
+    module is rejected on its plane)."""
+    g, batch = work
+    fi0 = pipeline.fit_inputs(batch)
+    bad, swaps = pipeline.plant_wrong_hits(batch, fi0, 0.3, 5)
+    X, V = batch.hit_xyz.astype(np.float64), batch.hit_cov.astype(np.float64)
+    for params, fi in ((S.default_params(precision=2), fi0),
+                       (S.default_params(fit_outlier_chi2=30.0),
+                        pipeline.FitInputs(fi0.layers, bad, fi0.p0, fi0.c0, fi0.event))):
+        ctx = _ctx(g, batch, params)
+        n = fi.layers.shape[0]
+        f = dict(p=np.zeros((n, 6), np.float32), c=np.zeros((n, 21), np.float32), chi2=np.zeros(n, np.float32),
+                 status=np.zeros(n, np.int32))
+        ctx.fit(fi.layers, fi.hits, fi.p0, fi.c0, f["p"], f["c"], f["chi2"], f["status"])
+        r = _oracle(g, batch, params).fit_batch(fi.layers, fi.hits, X, V, fi.p0, fi.c0)
+        rep = PR.compare_fit(f, r, mask=r["near_cut"] == 0)
+        assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0, rep
+        assert rep["n"] > 0.9 * n
+
+
+def test_modular_edge_cases(lib, work):
+    g, batch = work
+    params = S.default_params()
+    ctx = pipeline.make_context(g, params)
+    # module ids that do not fit the layers
+    hm = batch.hit_mod.copy()
+    i = int(np.nonzero(hm >= 0)[0][0])
+    for v in (-1, int(g.modules.c.shape[0]), int(np.nonzero(g.modules.layer != g.modules.layer[hm[i]])[0][0])):
+        hm2 = hm.copy()
+        hm2[i] = v
+        with pytest.raises(mkgb.MkgbError):
+            ctx.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov, hit_module=hm2)
+    j = int(np.nonzero(hm < 0)[0][0])
+    hm2 = hm.copy()
+    hm2[j] = int(hm[i])
+    with pytest.raises(mkgb.MkgbError):
+        ctx.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov, hit_module=hm2)
+    # without modules loaded, module ids are refused
+    plain = pipeline.make_context(S.geometry_phase2(), params)
+    with pytest.raises(mkgb.MkgbError):
+        plain.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov, hit_module=hm)
+    # the backward steps and the derivative take no module hits
+    ctx.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov, hit_module=hm)
+    fi = pipeline.fit_inputs(batch)
+    z = lambda *s, t=np.float32: np.zeros(s, t)
+    n = 4
+    with pytest.raises(mkgb.MkgbError):
+        ctx.fit_backward(fi.layers[:n], fi.hits[:n], z(n, 6), z(n, 21), z(n, 6), z(n, 21), z(n), z(n, t=np.int32))
+    # a seed with a module hit fails, as in the oracle
+    sh = batch.seed_hits[:6].copy()
+    sh[0, 2] = i
+    ctx.seed(sh)
+    out = ctx.build(mkgb.alloc_tracks(6, g.max_plan, ovl=True))
+    assert out["score"][0] == -np.inf and np.all(out["ovl"][0] == -1)
+    # no overlap array requested: the search runs the same
+    ctx.seed(batch.seed_hits[:200])
+    a = ctx.build(mkgb.alloc_tracks(200, g.max_plan, ovl=True))
+    b = ctx.build(mkgb.alloc_tracks(200, g.max_plan))
+    assert np.array_equal(a["hits"], b["hits"]) and np.array_equal(a["score"], b["score"])
+    # hits loaded without module ids: every hit on its layer's cylinder, no overlaps
+    ctx.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov)
+    ctx.seed(batch.seed_hits[:200])
+    c = ctx.build(mkgb.alloc_tracks(200, g.max_plan, ovl=True))
+    assert np.all(c["ovl"] == -1)
+
+
+def test_modular_search_full_size_sampled(lib):
+    """16 modular events x 20,000 tracks + 50,000 noise hits on the device, the launch
+    configuration of the benchmark; a sample of 300 seeds against the oracle."""
+    import torch
+    g = S.geometry_phase2_modular()
+    evs = [S.simulate_event(g, 20000, 0, e, pt_sampler=S.sample_pt_phase2, eta_max=3.0, noise_total=50000)
+           for e in range(16)]
+    batch = S.concat_events(evs, g.n_layers)
+    params = S.default_params()
+    ctx = pipeline.make_context(g, params)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ctx.load_hits(batch.n_events, batch.hit_off, dev(batch.hit_xyz), dev(batch.hit_cov), hit_module=dev(batch.hit_mod))
+    S_ = batch.seed_hits.shape[0]
+    ctx.seed(dev(batch.seed_hits))
+    out = mkgb.alloc_tracks(S_, g.max_plan, device="cuda", ovl=True)
+    ctx.build(out)
+    torch.cuda.synchronize()
+    out = {k: v.cpu().numpy() for k, v in out.items()}
+    rng = np.random.default_rng(17)
+    idx = np.sort(rng.choice(S_, 300, replace=False))
+    o = PR.oracle_build(_oracle(g, batch, params), batch, seed_index=idx)
+    rep = PR.compare_build(out, o)
+    assert len(rep["hit_mismatch"]) == 0, rep
+    assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0, rep
+    assert _check_ovl(out, o) == []
+    assert (out["ovl"] >= 0).sum() > 0.05 * S_
