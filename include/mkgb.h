@@ -154,9 +154,11 @@ int mkgb_load_hits(mkgb_ctx* ctx, int n_events, const int64_t* seg_off,
  * mkgb_tracks.ovl_hits: with the best accepted module hit b1 of a candidate's window and the best
  * one b2 on a module other than b1's, a child taking module hit h also takes b1 if h is not on b1's
  * module, else b2, and scores params.score_overlap more; its update uses h only).  Seeds with a
- * module hit fail (the seed fit takes hits on the layers' own surfaces).  mkgb_fit uses module hits
- * on their planes (status 1 if a plane is not reached within 10 cm, or only at grazing incidence);
- * mkgb_fit_backward, mkgb_build_backward and mkgb_fit_grad take no module hits.  Synchronises the
+ * module hit fail (the seed fit takes hits on the layers' own surfaces).  mkgb_fit and
+ * mkgb_fit_backward use module hits on their planes (status 1 if a plane is not reached within
+ * 10 cm, or only at grazing incidence; the backward fit's start state is taken on the plane of its
+ * last hit's module); mkgb_build_backward tests and picks up module hits as mkgb_build does (its
+ * out->ovl_hits likewise); mkgb_fit_grad takes no module hits (MKGB_EINVAL).  Synchronises the
  * stream (the module ids are checked on the device).  Errors: those of mkgb_load_hits; MKGB_ESTATE
  * without modules; MKGB_EINVAL for a NULL hit_module or a hit whose module does not fit its layer. */
 int mkgb_load_hits_modular(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz,

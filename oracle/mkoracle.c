@@ -809,13 +809,18 @@ void orc_bkfit_batch(const orc_geom* g, int material, int n, int max_steps, cons
         double sum = 0.0;
         int nu = 0, st = 0, near = 0;
         if (nl > 0) {
-            /* the start state lies on the last listed layer: its covariance is taken on that
-               surface, without variance along the surface normal n (zero in exact arithmetic
-               for a fitted state; the FP32 rounding residue of an input is dropped):
-               C -> Pi C Pi^T with Pi = I - n n^T on the position block */
+            /* the start state lies on the last listed layer (on the plane of its hit's module
+               for a module hit): its covariance is taken on that surface, without variance
+               along the surface normal n (zero in exact arithmetic for a fitted state; the FP32
+               rounding residue of an input is dropped): C -> Pi C Pi^T with Pi = I - n n^T on
+               the position block */
             const orc_layer* Ls = &g->layers[layers[(long long)i * max_steps + nl - 1]];
+            const int hl = hits[(long long)i * max_steps + nl - 1];
+            const int ml = hl >= 0 ? hit_module(g, hl) : -1;
             double nv[3] = {0.0, 0.0, 1.0};
-            if (Ls->kind == ORC_BARREL) {
+            if (ml >= 0) {
+                memcpy(nv, &g->mods->nrm[3 * ml], sizeof(nv));
+            } else if (Ls->kind == ORC_BARREL) {
                 double r = hypot(q[0], q[1]);
                 nv[0] = q[0] / r; nv[1] = q[1] / r; nv[2] = 0.0;
             }
@@ -849,8 +854,12 @@ void orc_bkfit_batch(const orc_geom* g, int material, int n, int max_steps, cons
             int h = hits[(long long)i * max_steps + j];
             if (h >= 0) {
                 double x2;
-                memcpy(pp, q, sizeof(q));
-                memcpy(Cp, Cq, sizeof(Cq));
+                if (j < nl - 1) {   /* a module hit is used on its module's plane (not reached: 1) */
+                    if (!at_hit_surface(g, h, q, Cq, pp, Cp, NULL)) { st = 1; break; }
+                } else {            /* the start state already lies on its hit's surface */
+                    memcpy(pp, q, sizeof(q));
+                    memcpy(Cp, Cq, sizeof(Cq));
+                }
                 if (outlier_chi2 > 0.0) {   /* outlier rejection: a hit above the cut is not used */
                     if (!orc_chi2(pp, Cp, &xyz[3 * (long long)h], &cov[6 * (long long)h], &x2)) {
                         st = 3;

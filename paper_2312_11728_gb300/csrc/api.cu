@@ -48,7 +48,7 @@ struct DevGuard {
     }
 };
 
-enum Stage { S_A, S_B, S_C, S_D, S_E, S_F, S_G, S_H, S_I, S_J, S_K, S_COUNT };
+enum Stage { S_A, S_B, S_C, S_D, S_E, S_F, S_G, S_H, S_I, S_J, S_K, S_L, S_COUNT };
 
 }  // namespace
 
@@ -624,7 +624,6 @@ int mkgb_build_backward(mkgb_ctx* ctx, int n, const int32_t* track_event, const 
     if (n < 0) return fail(ctx, MKGB_EINVAL, "negative size");
     if (ctx->params.precision == MKGB_FP64)
         return fail(ctx, MKGB_EINVAL, "the backward search runs in FP32 (precision MKGB_FP32)");
-    if (ctx->mod_hits) return fail(ctx, MKGB_EINVAL, "the backward search takes hits without modules");
     if (n > 0 && (!track_event || !first_layer || !p_start || !c_start)) return fail(ctx, MKGB_EINVAL, "null input");
     if (!out || !out->params || !out->cov || !out->chi2 || !out->score || !out->nfound || !out->nholes || !out->hits)
         return fail(ctx, MKGB_EINVAL, "null output array");
@@ -657,6 +656,10 @@ int mkgb_build_backward(mkgb_ctx* ctx, int n, const int32_t* track_event, const 
     CK(stage_out(ctx, S_F, out->nholes, 4 * N, on_device, &p)); d.nholes = (int*)p;
     CK(stage_out(ctx, S_G, out->hits, 4 * N * out->max_plan, on_device, &p)); d.hits = (int*)p;
     d.max_plan = out->max_plan;
+    if (out->ovl_hits) {
+        CK(stage_out(ctx, S_L, out->ovl_hits, 4 * N * out->max_plan, on_device, &p));
+        d.ovl = (int*)p;
+    }
     CK(ensure(ctx->bw_state, 4 * (size_t)kSeedStateStride * N));
     CK(ensure(ctx->bw_info, 16 * N));
     CK(ensure(ctx->bw_order, 4 * N));
@@ -668,8 +671,8 @@ int mkgb_build_backward(mkgb_ctx* ctx, int n, const int32_t* track_event, const 
         ctx->bins_pending = false;
     }
     SeedStore S{n, (const float*)ctx->bw_state.p, nullptr, (const int4*)ctx->bw_info.p, (const int*)ctx->bw_order.p};
-    CK(ensure(ctx->build_work, build_work_bytes(n, ctx->max_plan_len, MKGB_FP32)));
-    const BuildWork w = carve_build_work(ctx->build_work.p, n, ctx->max_plan_len, MKGB_FP32);
+    CK(ensure(ctx->build_work, build_work_bytes(n, ctx->max_plan_len, MKGB_FP32, ctx->mod_hits)));
+    const BuildWork w = carve_build_work(ctx->build_work.p, n, ctx->max_plan_len, MKGB_FP32, ctx->mod_hits);
     CK(cudaMemsetAsync(ctx->counters_build.p, 0, 8 * kNumCounters, st));
     CK(launch_build(st, (const DevGeom*)ctx->geom_bwd_d.p, ctx->max_plan_len, ctx->params, hit_store(ctx), S, d, w,
                     (unsigned long long*)ctx->counters_build.p, ctx->n_sms, 0, 0, nullptr, true));
@@ -680,6 +683,7 @@ int mkgb_build_backward(mkgb_ctx* ctx, int n, const int32_t* track_event, const 
     CK(copy_back(ctx, out->nfound, d.nfound, 4 * N, on_device));
     CK(copy_back(ctx, out->nholes, d.nholes, 4 * N, on_device));
     CK(copy_back(ctx, out->hits, d.hits, 4 * N * out->max_plan, on_device));
+    if (d.ovl) CK(copy_back(ctx, out->ovl_hits, d.ovl, 4 * N * out->max_plan, on_device));
     if (!on_device) CK(cudaStreamSynchronize(st));
     return MKGB_OK;
 }
@@ -776,7 +780,6 @@ int mkgb_fit_backward(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers
     if (!ctx->has_geom || !ctx->has_params) return fail(ctx, MKGB_ESTATE, "fit_backward before geometry/params");
     if (n < 0 || max_steps < 0) return fail(ctx, MKGB_EINVAL, "negative size");
     if (!(cov_scale > 0.0f) || !(cov_scale < 3.0e38f)) return fail(ctx, MKGB_EINVAL, "cov_scale must be positive");
-    if (ctx->mod_hits) return fail(ctx, MKGB_EINVAL, "the backward fit takes hits without modules");
     if (n > 0 && (!layers || !hits || !p_start || !c_start || !p_out || !c_out || !chi2_out))
         return fail(ctx, MKGB_EINVAL, "null fit array");
     bool any_hit = false;
@@ -807,7 +810,7 @@ int mkgb_fit_backward(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers
                     ctx->has_hits ? ctx->n_hits : 0, n, max_steps, (const int*)dl, (const int*)dh, (const float*)dp0,
                     (const float*)dc0, cov_scale, (float*)po, (float*)co, (float*)xo, (int*)so,
                     (unsigned long long*)ctx->counters_fit.p, (int*)ctx->rescue_list.p, (int*)ctx->rescue_count.p,
-                    ctx->n_sms));
+                    ctx->n_sms, ctx->mod_hits));
     CK(copy_back(ctx, p_out, po, 24 * N, on_device));
     CK(copy_back(ctx, c_out, co, 84 * N, on_device));
     CK(copy_back(ctx, chi2_out, xo, 4 * N, on_device));

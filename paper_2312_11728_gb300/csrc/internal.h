@@ -138,7 +138,8 @@ cudaError_t launch_fit(cudaStream_t st, const DevGeom* g, DevParams P, const flo
 cudaError_t launch_bkfit(cudaStream_t st, const DevGeom* g, DevParams P, const float4* pay, int64_t n_hits, int n,
                          int max_steps, const int* layers, const int* hits, const float* p_start, const float* c_start,
                          float cov_scale, float* p_out, float* c_out, float* chi2_out, int* status_out,
-                         unsigned long long* counters, int* rescue_list, int* rescue_count, int n_sms);
+                         unsigned long long* counters, int* rescue_list, int* rescue_count, int n_sms,
+                         bool modular = false);
 // Seed cleaning (mode 0) and quality filter + duplicate removal (mode 1) over n rows of `width`
 // hit ids; scratch holds clean_scratch_ints(n, width, n_hits) ints; keep gets 0/1 per row.
 size_t clean_scratch_ints(int n, int width, int64_t n_hits);

@@ -28,8 +28,9 @@ __device__ __forceinline__ void load_geom(const DevGeom* __restrict__ gp, DevGeo
     __syncthreads();
 }
 
-// One track in precision F; its status and the largest kappa(S).
-template <class F>
+// One track in precision F; its status and the largest kappa(S).  MOD: module hits loaded (used on
+// their module planes).
+template <class F, bool MOD>
 __device__ __forceinline__ int bkfit_track(const DevGeom& g, const DevParams& P, const float4* __restrict__ pay,
                                            int64_t n_hits, int max_steps, const int* __restrict__ lrow,
                                            const int* __restrict__ hrow, const float* p_start, const float* c_start,
@@ -48,7 +49,35 @@ __device__ __forceinline__ int bkfit_track(const DevGeom& g, const DevParams& P,
         if (h >= n_hits) return 4;   // hit index outside the loaded hits
         const DevLayer& L = g.layers[l];
         F m[3], v[6], x2;
-        if (h >= 0) load_hit(pay, h, m, v, nullptr);
+        int md = -1;
+        if (h >= 0) {
+            if constexpr (MOD)
+                load_hit(pay, h, m, v, nullptr, &md);
+            else
+                load_hit(pay, h, m, v, nullptr);
+        }
+        if (MOD && md >= 0) {   // a module hit (Sec. 3.1): on its module's plane
+            float kap = 0.0f;
+            int r;
+            if (j == nl - 1) {   // the start state lies on that plane
+                r = module_update_on_plane(t, g.mods, md, m, v, P.fit_outlier_chi2, t, x2, kap);
+            } else {
+                PredT<F> q;
+                const int rp = propagate_core<F, F, true>(L, g.cB, P.material, t, t.c, q, q.c, c_newton);
+                if (rp != 1) return rp == 0 ? 1 : 2;
+                ++c_steps;
+                r = module_update(L.kind, q, g.mods, md, g.cB, m, v, P.fit_outlier_chi2, t, x2, kap);
+                if (r == 1 || r == 3) pred_to_state(L.kind, q, t);   // not reached; outlier: not used
+                if (r == 1) return 1;
+            }
+            if (r == 2) return 3;
+            if (r == 0) {
+                kmax = fmaxf(kmax, kap);
+                sum += x2;
+                ++c_upd;
+            }
+            continue;
+        }
         if (j == nl - 1) {
             // the start state lies on this layer: taken in the layer's surface frame (its
             // covariance without variance along the normal), then updated as every other step
@@ -93,7 +122,7 @@ __device__ __forceinline__ int bkfit_track(const DevGeom& g, const DevParams& P,
 }
 
 // All tracks (list == nullptr) or the listed ones (the FP64 refit of the flagged FP32 fits).
-template <class F>
+template <class F, bool MOD>
 __global__ void __launch_bounds__(kThreads) k_bkfit(const DevGeom* __restrict__ gp, DevParams P,
                                                     const float4* __restrict__ pay, int64_t n_hits, int n,
                                                     int max_steps, const int* __restrict__ layers,
@@ -113,7 +142,7 @@ __global__ void __launch_bounds__(kThreads) k_bkfit(const DevGeom* __restrict__ 
         StateT<F> t;
         F sum;
         float kmax;
-        const int status = bkfit_track<F>(g, P, pay, n_hits, max_steps, layers + (int64_t)i * max_steps,
+        const int status = bkfit_track<F, MOD>(g, P, pay, n_hits, max_steps, layers + (int64_t)i * max_steps,
                                           hits + (int64_t)i * max_steps, p_start + 6 * (int64_t)i,
                                           c_start + 21 * (int64_t)i, cov_scale, t, sum, kmax, c_steps, c_upd,
                                           c_newton);
@@ -143,21 +172,23 @@ __global__ void __launch_bounds__(kThreads) k_bkfit(const DevGeom* __restrict__ 
 cudaError_t launch_bkfit(cudaStream_t st, const DevGeom* g, DevParams P, const float4* pay, int64_t n_hits, int n,
                          int max_steps, const int* layers, const int* hits, const float* p_start, const float* c_start,
                          float cov_scale, float* p_out, float* c_out, float* chi2_out, int* status_out,
-                         unsigned long long* counters, int* rescue_list, int* rescue_count, int n_sms) {
+                         unsigned long long* counters, int* rescue_list, int* rescue_count, int n_sms, bool modular) {
     if (n == 0) return cudaSuccess;
     const int blocks = (n + kThreads - 1) / kThreads;
+    auto fit64 = modular ? k_bkfit<double, true> : k_bkfit<double, false>;
+    auto fit32 = modular ? k_bkfit<float, true> : k_bkfit<float, false>;
     if (P.precision == MKGB_FP64) {
-        k_bkfit<double><<<blocks, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p_start, c_start,
+        fit64<<<blocks, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p_start, c_start,
                                                      cov_scale, p_out, c_out, chi2_out, status_out, counters,
                                                      nullptr, nullptr, nullptr, nullptr);
         return cudaGetLastError();
     }
-    k_bkfit<float><<<blocks, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p_start, c_start,
+    fit32<<<blocks, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p_start, c_start,
                                                 cov_scale, p_out, c_out, chi2_out, status_out, counters, rescue_list,
                                                 rescue_count, nullptr, nullptr);
     if (P.kappa_fp64 > 0.0f && rescue_list) {
         const int rb = blocks < 2 * n_sms ? blocks : 2 * n_sms;
-        k_bkfit<double><<<rb, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p_start, c_start,
+        fit64<<<rb, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p_start, c_start,
                                                  cov_scale, p_out, c_out, chi2_out, status_out, counters, nullptr,
                                                  nullptr, rescue_list, rescue_count);
     }

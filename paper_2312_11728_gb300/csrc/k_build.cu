@@ -871,15 +871,18 @@ template <class F, bool MOD> void prime_shapes_of(int n_sms) {
 }
 
 template <class F> void prime_shapes(int n_sms) {
-    if (sizeof(F) == 4) FindShape<float, 128, 1, true>::grid(n_sms);
+    if (sizeof(F) == 4) {
+        FindShape<float, 128, 1, true>::grid(n_sms);
+        FindShape<float, 128, 1, true, true>::grid(n_sms);
+    }
     prime_shapes_of<F, false>(n_sms);
     prime_shapes_of<F, true>(n_sms);
 }
 
 template <class F, bool BWD = false, bool MOD = false>
 void launch_find(int shape, cudaStream_t st, const BuildArgs& a, int tau, int n_sms) {
-    if constexpr (BWD) {   // the backward search: one shape, FP32 only, no module hits
-        FindShape<F, 128, 1, true>::launch(st, a, tau, n_sms);
+    if constexpr (BWD) {   // the backward search: one shape, FP32 only
+        FindShape<F, 128, 1, true, MOD>::launch(st, a, tau, n_sms);
         return;
     }
     switch (shape) {
@@ -916,9 +919,11 @@ cudaError_t launch_rounds(cudaStream_t st, const BuildArgs& a, int n, int max_pl
 
 cudaError_t enqueue_rounds(cudaStream_t st, const BuildArgs& a, int n, int max_plan_len, int n_sms, int find_shape,
                            int select_shape, bool backward = false) {
-    if (backward) return launch_rounds<float, true>(st, a, n, max_plan_len, n_sms, find_shape, select_shape);
     // module hits loaded (their overlap trail exists): the module-aware kernels
     const bool mod = a.w.otrail != nullptr;
+    if (backward)
+        return mod ? launch_rounds<float, true, true>(st, a, n, max_plan_len, n_sms, find_shape, select_shape)
+                   : launch_rounds<float, true>(st, a, n, max_plan_len, n_sms, find_shape, select_shape);
     // MKGB_FP64: the plain all-FP64 comparison path (same rounds, every Kalman step in FP64)
     if (a.P.precision == MKGB_FP64)
         return mod ? launch_rounds<double, false, true>(st, a, n, max_plan_len, n_sms, find_shape, select_shape)

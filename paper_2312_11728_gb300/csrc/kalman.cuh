@@ -981,15 +981,45 @@ __device__ __noinline__ bool module_chi2(int kind, const PredT<F>& q, const floa
 // 2 (the update failed) or, with outlier_cut > 0 and a predicted chi2 above it, 3 (out untouched).
 // x2 gets the predicted chi2, kappa the condition estimate of S.
 template <class F>
+__device__ __forceinline__ int plane_update_core(const FrameT<F>& fp, const PredT<F>& qp, const F m[3], const F v[6],
+                                                 float outlier_cut, StateT<F>& out, F& x2, float& kappa) {
+    if (!chi2_hit(fp, qp, m[0], m[1], m[2], v, x2)) return 2;
+    if (outlier_cut > 0.0f && x2 > F(outlier_cut)) return 3;
+    return kalman_update_f(fp, qp, m[0], m[1], m[2], v, out, &kappa) ? 0 : 2;
+}
+
+template <class F>
 __device__ __noinline__ int module_update(int kind, const PredT<F>& q, const float4* __restrict__ mods, int mod,
                                           float cBf, const F m[3], const F v[6], float outlier_cut, StateT<F>& out,
                                           F& x2, float& kappa) {
     PredT<F> qp;
     FrameT<F> fp;
     if (!to_module_plane(kind, q, mods, mod, cBf, qp, fp)) return 1;
-    if (!chi2_hit(fp, qp, m[0], m[1], m[2], v, x2)) return 2;
-    if (outlier_cut > 0.0f && x2 > F(outlier_cut)) return 3;
-    return kalman_update_f(fp, qp, m[0], m[1], m[2], v, out, &kappa) ? 0 : 2;
+    return plane_update_core(fp, qp, m, v, outlier_cut, out, x2, kappa);
+}
+
+// The same for a global-frame state t that already lies on module mod's plane (the start state
+// of the backward fit): its covariance is taken in the plane's frame (the variance along the
+// normal dropped), then chi2 and update.  Return codes as module_update without 1; with 3 (an
+// outlier) out gets t taken on the plane.
+template <class F>
+__device__ __noinline__ int module_update_on_plane(const StateT<F>& t, const float4* __restrict__ mods, int mod,
+                                                   const F m[3], const F v[6], float outlier_cut, StateT<F>& out,
+                                                   F& x2, float& kappa) {
+    const float4 nm = __ldg(mods + 2 * mod + 1);
+    const F n[3] = {F(nm.x), F(nm.y), F(nm.z)};
+    F sf, cf, st, ct;
+    sin_cos(t.phi, &sf, &cf);
+    sin_cos(t.th, &st, &ct);
+    const FrameT<F> fp = plane_frame(n, sf, cf, st, ct);
+    PredT<F> qp;
+    state_to_pred(fp, t, qp);
+    const int r = plane_update_core(fp, qp, m, v, outlier_cut, out, x2, kappa);
+    if (r == 3) {
+        out = t;
+        embed_cov(fp, qp.c, out.c);
+    }
+    return r;
 }
 
 // ----------------------------------------------------------------- window (a8)

@@ -247,12 +247,15 @@ class Context:
 
     def build_backward(self, track_event, first_layer, p_start, c_start, out: dict):
         """mkgb_build_backward: the backward search of tracks from their state on their innermost
-        found layer; out as for build (hits indexed by the reversed plan's steps)."""
+        found layer; out as for build (hits and the optional ovl indexed by the reversed plan's
+        steps)."""
         f, i = np.float32, np.int32
         args = [_ptr(track_event, i), _ptr(first_layer, i), _ptr(p_start, f), _ptr(c_start, f)]
         ptrs = [_ptr(out[k], t, out=True) for k, t in (("params", f), ("cov", f), ("chi2", f), ("score", f),
                                               ("nfound", i), ("nholes", i), ("hits", i))]
-        t = Tracks(*[p for p, _ in ptrs], int(out["hits"].shape[1]))
+        if "ovl" in out:
+            ptrs.append(_ptr(out["ovl"], i, out=True))
+        t = Tracks(*[p for p, _ in ptrs[:7]], int(out["hits"].shape[1]), ptrs[7][0] if len(ptrs) > 7 else None)
         n = int(np.asarray(first_layer).shape[0]) if not _is_torch(first_layer) else int(first_layer.shape[0])
         self._check(self.lib.mkgb_build_backward(self.h, n, *[p for p, _ in args], C.byref(t),
                                                  _same(*[d for _, d in args + ptrs])), "mkgb_build_backward")

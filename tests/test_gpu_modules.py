@@ -137,13 +137,14 @@ def test_modular_edge_cases(lib, work):
     plain = pipeline.make_context(S.geometry_phase2(), params)
     with pytest.raises(mkgb.MkgbError):
         plain.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov, hit_module=hm)
-    # the backward steps and the derivative take no module hits
+    # the fit derivative takes no module hits
     ctx.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov, hit_module=hm)
     fi = pipeline.fit_inputs(batch)
     z = lambda *s, t=np.float32: np.zeros(s, t)
-    n = 4
+    n, NL = 4, g.n_layers
     with pytest.raises(mkgb.MkgbError):
-        ctx.fit_backward(fi.layers[:n], fi.hits[:n], z(n, 6), z(n, 21), z(n, 6), z(n, 21), z(n), z(n, t=np.int32))
+        ctx.fit_grad(fi.layers[:n], fi.hits[:n], fi.p0[:n], fi.c0[:n], z(NL, 6), np.ones(NL, np.float32), z(n),
+                     z(n, 6), z(NL, 6), z(NL))
     # a seed with a module hit fails, as in the oracle
     sh = batch.seed_hits[:6].copy()
     sh[0, 2] = i
@@ -160,6 +161,72 @@ def test_modular_edge_cases(lib, work):
     ctx.seed(batch.seed_hits[:200])
     c = ctx.build(mkgb.alloc_tracks(200, g.max_plan, ovl=True))
     assert np.all(c["ovl"] == -1)
+
+
+def test_modular_backward_fit_matches_oracle(lib, work):
+    """The backward fit (Sec. 2.2) through the modular layers from the GPU forward fit's states:
+    module hits used on their planes (the start state on its last hit's plane)."""
+    g, batch = work
+    params = S.default_params()
+    ctx = _ctx(g, batch, params)
+    fi = pipeline.fit_inputs(batch)
+    n = fi.layers.shape[0]
+    mk = lambda: dict(p=np.zeros((n, 6), np.float32), c=np.zeros((n, 21), np.float32), chi2=np.zeros(n, np.float32),
+                      status=np.zeros(n, np.int32))
+    f, b = mk(), mk()
+    ctx.fit(fi.layers, fi.hits, fi.p0, fi.c0, f["p"], f["c"], f["chi2"], f["status"])
+    ctx.fit_backward(fi.layers, fi.hits, f["p"], f["c"], b["p"], b["c"], b["chi2"], b["status"])
+    X, V = batch.hit_xyz.astype(np.float64), batch.hit_cov.astype(np.float64)
+    r = _oracle(g, batch, params).bkfit_batch(fi.layers, fi.hits, X, V, f["p"].astype(np.float64),
+                                              f["c"].astype(np.float64), 100.0)
+    ok = f["status"] == 0
+    rep = PR.compare_fit(b, r, mask=ok)
+    assert np.array_equal(b["status"][ok], r["status"][ok]), rep
+    assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0, rep
+    assert rep["n"] > 0.95 * n
+
+
+def test_modular_backward_search_matches_oracle(lib, work):
+    """The backward search (Sec. 2.2) through modular layers: tracks without their first five
+    layers (so that the search crosses modular layers 4 and 3 and the plain 2, 1, 0) are fitted
+    forwards and backwards on the GPU, then both searches run inwards from that state; hit lists
+    and overlap hits bit-exact outside near ties."""
+    g, batch = work
+    params = S.default_params()
+    ctx = _ctx(g, batch, params)
+    fi = pipeline.fit_inputs(batch)
+    n_skip = 5
+    keep = ((fi.layers >= 0).sum(1) >= n_skip + 3) & (fi.layers[:, 0] == 0)
+    fo = pipeline.outer_fit_inputs(fi, n_skip)
+    sel = np.nonzero(keep)[0]
+    L, H = np.ascontiguousarray(fo.layers[sel]), np.ascontiguousarray(fo.hits[sel])
+    n = len(sel)
+    mk = lambda: dict(p=np.zeros((n, 6), np.float32), c=np.zeros((n, 21), np.float32), chi2=np.zeros(n, np.float32),
+                      status=np.zeros(n, np.int32))
+    f, b = mk(), mk()
+    ctx.fit(L, H, fo.p0[sel], fo.c0[sel], f["p"], f["c"], f["chi2"], f["status"])
+    ctx.fit_backward(L, H, f["p"], f["c"], b["p"], b["c"], b["chi2"], b["status"])
+    ok = (f["status"] == 0) & (b["status"] == 0)
+    sel, L = sel[ok], L[ok]
+    ev = np.ascontiguousarray(fi.event[sel].astype(np.int32))
+    first = np.ascontiguousarray(L[:, 0])
+    p, c = np.ascontiguousarray(b["p"][ok]), np.ascontiguousarray(b["c"][ok])
+    out = ctx.build_backward(ev, first, p, c, mkgb.alloc_tracks(len(sel), g.max_plan, ovl=True))
+    o = PR.oracle_build_backward(_oracle(g, batch, params), batch, ev, p, c, first)
+    rep = PR.compare_build(out, o)
+    assert len(rep["hit_mismatch"]) == 0, rep
+    assert rep["failed_mismatch"] == 0 and rep["count_bad"] == 0, rep
+    assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0, rep
+    assert rep["n_tie"] < 0.05 * len(sel), rep
+    assert _check_ovl(out, o) == []
+    assert (out["ovl"] >= 0).sum() > 0.02 * len(sel)
+    # the removed inner hits, on module planes included, are found again
+    found = []
+    for k, i in enumerate(sel):
+        lay = list(g.plans[o["region"][k]][::-1])
+        steps = [lay.index(l) for l in fi.layers[i, :n_skip]]
+        found.append(np.mean(out["hits"][k, steps] == fi.hits[i, :n_skip]))
+    assert np.mean(found) > 0.9, np.mean(found)
 
 
 def test_modular_search_full_size_sampled(lib):

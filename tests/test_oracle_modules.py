@@ -257,3 +257,37 @@ def test_modular_fit_pulls(geo):
     r0 = orc.fit_batch(fi.layers, fi.hits, X, V, fi.p0, fi.c0)
     ok0 = (r0["status"] == 0) & ((fi.layers >= 0).sum(1) >= 8)
     assert np.median(r0["chi2"][ok0]) > 3 * np.median(r["chi2"][ok])
+
+
+def test_modular_backward_fit_pulls_at_the_first_hit():
+    """The backward fit (Sec. 2.2) through modular layers, module hits used on their planes:
+    forward fit, then backward fit from the last hit; the pulls of the state on the innermost
+    (plain) cylinder against the truth of the segment entering it (the helix from the origin, by
+    the generator's own crossing and motion) have unit width."""
+    g = S.add_modules(S.geometry_barrel(), [3, 4, 5])
+    ev = S.simulate_event(g, 3000, 12, 0, eta_max=1.0,
+                          pt_sampler=lambda rng, n: S.sample_pt_loguniform(rng, n, 1.0, 10.0))
+    batch = S.concat_events([ev], g.n_layers)
+    orc = _oracle_with_modules(geo=g, batch=batch)
+    layers, hits, p0, c0, _, nh, sel = S.fit_workload(ev)
+    X, V = ev.hit_xyz.astype(np.float64), ev.hit_cov.astype(np.float64)
+    f = orc.fit_batch(layers, hits, X, V, p0, c0)
+    b = orc.bkfit_batch(layers, hits, X, V, f["p"], f["c"], 100.0)
+    ok = (f["status"] == 0) & (b["status"] == 0) & (layers[:, 0] == 0) & (nh >= 8)
+    assert ok.mean() > 0.9
+    assert (batch.hit_mod[hits[ok]] >= 0).any(1).mean() > 0.8   # the tracks cross module layers
+    k0 = ev.track_q[sel] / ev.track_pt[sel]
+    th0 = 2 * np.arctan(np.exp(-ev.track_eta[sel]))
+    ph0 = ev.track_phi[sel]
+    w = -S.C_LIGHT * g.bz * k0
+    z0 = np.zeros_like(k0)
+    s0 = S._cylinder_crossing(z0, z0, ph0, w, g.pos[0])
+    xn, yn, zn, psi = S._move(z0, z0, z0, ph0, th0, w, s0)
+    truth_in = np.stack([xn, yn, zn, k0, np.angle(np.exp(1j * psi)), th0], -1)
+    P, Cm, T = b["p"][ok], b["c"][ok], truth_in[ok]
+    d = P - T
+    d[:, 4] = np.angle(np.exp(1j * d[:, 4]))
+    for i, ci in ((3, 9), (4, 14), (5, 20), (2, 5)):
+        pl = d[:, i] / np.sqrt(Cm[:, ci])
+        assert abs(pl.mean()) < 0.08, i
+        assert abs(pl.std() - 1.0) < 0.08, (i, pl.std())

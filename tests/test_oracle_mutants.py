@@ -36,6 +36,8 @@ MUTANTS = {
     "module_ignored": ("int m = hit_module(g, id);\n    if (margin)", "int m = -1;\n    if (margin)"),
     "overlap_same_module": ("if (hit_module(g, mh->v[q].gid) != hit_module(g, b1)) b2 = mh->v[q].gid;",
                             "if (hit_module(g, mh->v[q].gid) == hit_module(g, b1)) b2 = mh->v[q].gid;"),
+    "bkfit_module_ignored": ("if (!at_hit_surface(g, h, q, Cq, pp, Cp, NULL)) { st = 1; break; }",
+                             "memcpy(pp, q, sizeof(q)); memcpy(Cp, Cq, sizeof(Cq));"),
     "overlap_swapped": ("k->ovl = hit_module(g, k->gid) != hit_module(g, b1) ? b1 : b2;",
                         "k->ovl = hit_module(g, k->gid) != hit_module(g, b1) ? b2 : b1;"),
 }
