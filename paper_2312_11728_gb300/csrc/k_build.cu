@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(TH, MINB) k_find(BuildArgs a, int tau) {
                             if constexpr (MOD) {
                                 load_hit(a.H.hb_pay, hq, m, v, &id, &md);
                                 // a module hit: chi2 on its module's plane (Sec. 3.1)
-                                okx = md >= 0 ? module_chi2(L.kind, q, g.mods, md, g.cB, m, v, x2f)
+                                okx = md >= 0 ? module_chi2_dir(q, fr, dir, g.mods, md, g.cB, m, v, x2f)
                                               : chi2_hit(fr, q, m[0], m[1], m[2], v, x2f);
                             } else {
                                 load_hit(a.H.hb_pay, hq, m, v, &id);

@@ -965,16 +965,155 @@ __device__ __forceinline__ int to_module_plane(int kind, const PredT<F>& q, cons
     return propagate_plane(t, __ldg(mods + 2 * mod), __ldg(mods + 2 * mod + 1), cBf, qp, fp, it);
 }
 
-// The chi2 of a module hit (m, v) on its module's plane, from the prediction q on the layer's
-// reference surface.  False if the plane is not reached or S is not positive definite.  The
-// module-hit steps below are not inlined, so that the search and fit kernels keep their
-// register allocation for the layers without modules.
+// The chi2 of a module hit (m, v) on its module's plane, for the search's window loop: from the
+// prediction q on the layer's reference surface, in its surface frame fr, with the direction
+// dir = (sin phi', cos phi', sin theta, cos theta) at the crossing (as propagate returns it).  The
+// plane crossing as propagate_plane finds it, but only the two rows of the Jacobian that the
+// position covariance on the plane needs, contracted with the surface-frame covariance directly
+// (the 21-term global covariance is never formed).  False if the plane is not reached or S is
+// not positive definite.  The module-hit steps are not inlined, so that the search and fit
+// kernels keep their register allocation for the layers without modules.
 template <class F>
-__device__ __noinline__ bool module_chi2(int kind, const PredT<F>& q, const float4* __restrict__ mods, int mod,
-                                         float cBf, const F m[3], const F v[6], F& x2) {
+__device__ __noinline__ bool module_chi2_dir(const PredT<F>& q, const FrameT<F>& fr, const F dir[4],
+                                             const float4* __restrict__ mods, int mod, float cBf, const F m[3],
+                                             const F v[6], F& x2) {
+    const float4 cm = __ldg(mods + 2 * mod), nm = __ldg(mods + 2 * mod + 1);
+    const F n[3] = {F(nm.x), F(nm.y), F(nm.z)};
+    const F cB = F(cBf);
+    const F sf = dir[0], cf = dir[1], st = dir[2], ct = dir[3];
+    const F om = -cB * q.k;
+    const F cot = div_rn(ct, st);
+    const F g0 = n[0] * sub_rn(sub_rn(F(cm.x), q.xh), q.xl) + n[1] * sub_rn(sub_rn(F(cm.y), q.yh), q.yl) +
+                 n[2] * sub_rn(sub_rn(F(cm.z), q.zh), q.zl);
+    const F dg0 = n[0] * cf + n[1] * sf + n[2] * cot;
+    if (dg0 == F(0)) return false;
+    F s = g0 / dg0;
+    const F tol = is_fp32<F>() ? F(1e-6) : F(1e-13);
+    bool conv = false;
+    for (int it = 0; it < 20 && !conv; ++it) {
+        const F a = om * s;
+        F sh, ch;
+        sin_cos(F(0.5) * a, &sh, &ch);
+        const F sa = F(2) * sh * ch, oc = F(2) * sh * sh;
+        F S1, C1;
+        if (fabs(a) < F(1e-4)) {
+            S1 = F(1) - a * a * (F(1) / F(6));
+            C1 = a * (F(0.5) - a * a * (F(1) / F(24)));
+        } else {
+            S1 = sa / a;
+            C1 = oc / a;
+        }
+        const F dx = s * (cf * S1 - sf * C1), dy = s * (sf * S1 + cf * C1);
+        const F g = n[0] * dx + n[1] * dy + n[2] * (s * cot) - g0;
+        const F cpn = cf * (F(1) - oc) - sf * sa, spn = sf * (F(1) - oc) + cf * sa;
+        const F dg = n[0] * cpn + n[1] * spn + n[2] * cot;
+        if (dg == F(0)) return false;
+        const F ds = -g / dg;
+        s += ds;
+        conv = fabs(ds) <= tol * (F(1) + fabs(s));
+    }
+    if (!conv || !(fabs(s) <= F(2 * kPlaneMaxPath))) return false;
+    const F a = om * s;
+    F sh, ch;
+    sin_cos(F(0.5) * a, &sh, &ch);
+    const F sa = F(2) * sh * ch, ca = fma(F(-2) * sh, sh, F(1));
+    F S1, C1;
+    if (fabs(a) < F(1e-4)) {
+        S1 = F(1) - a * a * (F(1) / F(6));
+        C1 = a * (F(0.5) - a * a * (F(1) / F(24)));
+    } else {
+        S1 = sa / a;
+        C1 = F(2) * sh * sh / a;
+    }
+    F dx, dy;
+    {
+        const F sp = fma(sf, ch, cf * sh), cp = fma(cf, ch, -sf * sh);
+        const F h = F(0.5) * a;
+        F sinc;
+        if (fabs(h) < F(0.05)) {
+            const F h2 = h * h;
+            sinc = F(1) + h2 * (F(-1) / F(6) + h2 * (F(1) / F(120) + h2 * (F(-1) / F(5040) + h2 * (F(1) / F(362880)))));
+        } else {
+            sinc = div_rn(sh, h);
+        }
+        const F chord = s * sinc;
+        dx = chord * cp;
+        dy = chord * sp;
+    }
     PredT<F> qp;
-    FrameT<F> fp;
-    return to_module_plane(kind, q, mods, mod, cBf, qp, fp) && chi2_hit(fp, qp, m[0], m[1], m[2], v, x2);
+    qp.xh = q.xh; qp.xl = q.xl; qp.yh = q.yh; qp.yl = q.yl; qp.zh = q.zh; qp.zl = q.zl;
+    add_ff(qp.xh, qp.xl, dx);
+    add_ff(qp.yh, qp.yl, dy);
+    add_ff(qp.zh, qp.zl, s * cot);
+    const F sfp = fma(sf, ca, cf * sa), cfp = fma(cf, ca, -sf * sa);
+    const F den = n[0] * cfp + n[1] * sfp + n[2] * cot;
+    {
+        const F gap = n[0] * sub_rn(sub_rn(F(cm.x), qp.xh), qp.xl) + n[1] * sub_rn(sub_rn(F(cm.y), qp.yh), qp.yl) +
+                      n[2] * sub_rn(sub_rn(F(cm.z), qp.zh), qp.zl);
+        const F dsp = div_rn(gap, den);
+        add_ff(qp.xh, qp.xl, dsp * cfp);
+        add_ff(qp.yh, qp.yl, dsp * sfp);
+        add_ff(qp.zh, qp.zl, dsp * cot);
+    }
+    if (!(fabs(s) <= F(kPlaneMaxPath)) || !(fabs(den) >= F(kPlaneMinCos))) return false;
+    // rows u1, u2 of the plane map's Jacobian in the global parameters (as propagate_plane) ...
+    F dS1, dC1;
+    s1c1_deriv(a, S1, C1, dS1, dC1);
+    const F A03 = -cB * s * s * (cf * dS1 - sf * dC1);
+    const F A13 = -cB * s * s * (sf * dS1 + cf * dC1);
+    const F A04 = -dy, A14 = dx;
+    const F A25 = -s / (st * st);
+    const F ig = F(-1) / den;
+    F ds[6];
+    ds[0] = n[0] * ig; ds[1] = n[1] * ig; ds[2] = n[2] * ig;
+    ds[3] = (n[0] * A03 + n[1] * A13) * ig;
+    ds[4] = (n[0] * A04 + n[1] * A14) * ig;
+    ds[5] = n[2] * A25 * ig;
+    const FrameT<F> fp = plane_frame(n, sfp, cfp, st, ct);
+    const F Apos[3][6] = {{F(1), F(0), F(0), A03, A04, F(0)},
+                          {F(0), F(1), F(0), A13, A14, F(0)},
+                          {F(0), F(0), F(1), F(0), F(0), A25}};
+    const F fpos[3] = {cfp, sfp, cot};
+    const F f1 = dot3(fp.e1, fpos);
+    F J[2][6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        const F a1 = fp.e1[0] * Apos[0][j] + fp.e1[1] * Apos[1][j] + fp.e1[2] * Apos[2][j];
+        const F a2 = fp.e2[0] * Apos[0][j] + fp.e2[1] * Apos[1][j] + fp.e2[2] * Apos[2][j];
+        J[0][j] = fma(f1, ds[j], a1);
+        J[1][j] = a2;
+    }
+    // ... times the map from the reference surface's parameters (u1, u2, k, phi, theta) to the
+    // global ones (position columns e1, e2 of fr; the angles and k one to one)
+    F Js[2][5];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        Js[r][0] = J[r][0] * fr.e1[0] + J[r][1] * fr.e1[1] + J[r][2] * fr.e1[2];
+        Js[r][1] = J[r][0] * fr.e2[0] + J[r][1] * fr.e2[1] + J[r][2] * fr.e2[2];
+        Js[r][2] = J[r][3];
+        Js[r][3] = J[r][4];
+        Js[r][4] = J[r][5];
+    }
+    F T[2][5];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            F acc = F(0);
+#pragma unroll
+            for (int l = 0; l < 5; ++l) acc = fma(Js[r][l], q.c[ix(l, j)], acc);
+            T[r][j] = acc;
+        }
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int p = 0; p <= r; ++p) {
+            F acc = F(0);
+#pragma unroll
+            for (int l = 0; l < 5; ++l) acc = fma(T[r][l], Js[p][l], acc);
+            qp.c[ix(r, p)] = acc;
+        }
+    return chi2_hit(fp, qp, m[0], m[1], m[2], v, x2);
 }
 
 // Update with a module hit on its module's plane.  Returns 0 (out updated), 1 (plane not reached),
