@@ -74,15 +74,15 @@ def _gen_event(args):
 def _gen_modular_event(args):
     e, seed = args
     from paper_2312_11728_gb300 import synth as S
-    g = S.geometry_phase2_modular()
+    g = S.geometry_phase2_modular_disks()
     return S.simulate_event(g, N_TRACKS, seed, e, pt_sampler=S.sample_pt_phase2, eta_max=3.0, noise_total=N_NOISE)
 
 
 def make_modular_batch(seed, n_events):
     """The same events' recipe on the modular tracker (cylinders 3-5 built from flat and tilted
-    modules), generated in a spawn pool."""
+    modules, the 4th-6th disk of each endcap from planar modules), generated in a spawn pool."""
     from paper_2312_11728_gb300 import synth as S
-    g = S.geometry_phase2_modular()
+    g = S.geometry_phase2_modular_disks()
     with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
         evs = pool.map(_gen_modular_event, [(e, seed) for e in range(n_events)])
     return g, S.concat_events(evs, g.n_layers)

@@ -152,7 +152,7 @@ def add_modules(geom: Geometry, layers, dz=4.8, z_flat=30.0, width=9.0, dr=0.3, 
         nphi += nphi % 2
         K = int(np.floor(zmax / dz))
         zc = dz * np.arange(-K, K + 1)
-        grid[l] = (len(cs), nphi, zc)
+        grid[l] = (len(cs), nphi, zc, "z")
         dphi = 2 * np.pi / nphi
         for k in zc:
             beta = np.arctan2(k, R) if abs(k) > z_flat else 0.0
@@ -172,13 +172,67 @@ def add_modules(geom: Geometry, layers, dz=4.8, z_flat=30.0, width=9.0, dr=0.3, 
                 hls.append(0.5 * dz * np.cos(beta) * 1.04 if beta != 0.0 else 0.5 * dz * 1.04)
                 lay.append(l)
         sig[l] = sig_window
+    return _with_modules(geom, cs, ns, us, vs, hws, hls, lay, grid, sig)
+
+
+def _with_modules(geom, cs, ns, us, vs, hws, hls, lay, grid, sig):
+    """geom with these modules added to those it has (module indices continue after them)."""
     f = lambda a: _f32(np.array(a))
     n = f(ns)
-    mods = Modules(f(cs), n / np.linalg.norm(n, axis=1, keepdims=True), np.array(us), np.array(vs),
-                   np.array(hws), np.array(hls), np.array(lay, np.int32), grid)
-    g = Geometry(geom.kind, geom.pos, geom.lo, geom.hi, geom.x_over_x0, _f32(sig), geom.n_eta, geom.n_phi,
-                 geom.eta_lo, geom.eta_hi, [list(p) for p in geom.plans], geom.bz, geom.barrel_eta_max, mods)
-    return g
+    n = n / np.linalg.norm(n, axis=1, keepdims=True)
+    new = Modules(f(cs), n, np.array(us), np.array(vs), np.array(hws), np.array(hls), np.array(lay, np.int32), grid)
+    old = geom.modules
+    if old is not None:
+        M = old.c.shape[0]
+        new = Modules(np.concatenate([old.c, new.c]), np.concatenate([old.n, new.n]),
+                      np.concatenate([old.u, new.u]), np.concatenate([old.v, new.v]),
+                      np.concatenate([old.hw, new.hw]), np.concatenate([old.hl, new.hl]),
+                      np.concatenate([old.layer, new.layer]),
+                      {**old.grid, **{l: (e[0] + M,) + tuple(e[1:]) for l, e in grid.items()}})
+    return Geometry(geom.kind, geom.pos, geom.lo, geom.hi, geom.x_over_x0, _f32(sig), geom.n_eta, geom.n_phi,
+                    geom.eta_lo, geom.eta_hi, [list(p) for p in geom.plans], geom.bz, geom.barrel_eta_max, new)
+
+
+def add_disk_modules(geom: Geometry, layers, n_rings=6, nphi=48, dz=0.2, overlap=1.08,
+                     sig_window=(0.1, 0.1, 0.1)) -> Geometry:
+    """Makes the given disks modular (Sec. 3.1 module vectors; the Phase-2 endcap's planar
+    modules): each disk becomes n_rings rings of nphi flat modules facing along z, the rings
+    equal in r, the modules alternating z_d +- dz so that neighbours overlap in phi (8%) and r
+    (4%).  The disk stays the layer's reference surface; its window resolution becomes
+    sig_window (a module hit lies on the track within dz of the disk crossing, so at nearly the
+    crossing's eta and phi)."""
+    cs, ns, us, vs, hws, hls, lay = [], [], [], [], [], [], []
+    grid = {}
+    sig = geom.sig.copy()
+    for l in layers:
+        assert geom.kind[l] == DISK
+        zd, r0, r1 = float(geom.pos[l]), float(geom.lo[l]), float(geom.hi[l])
+        dr = (r1 - r0) / n_rings
+        rc = r0 + dr * (np.arange(n_rings) + 0.5)
+        grid[l] = (len(cs), nphi, rc, "r")
+        dphi = 2 * np.pi / nphi
+        for k, rk in enumerate(rc):
+            for j in range(nphi):
+                ph = j * dphi
+                rh = np.array([np.cos(ph), np.sin(ph), 0.0])
+                u = np.array([-np.sin(ph), np.cos(ph), 0.0])
+                n = np.array([0.0, 0.0, 1.0])
+                cs.append(rk * rh + np.array([0.0, 0.0, zd + (dz if (j + k) % 2 == 0 else -dz)]))
+                ns.append(n); us.append(u); vs.append(np.cross(n, u))
+                hws.append(rk * np.tan(0.5 * dphi) * overlap)
+                hls.append(0.5 * dr * 1.04)
+                lay.append(l)
+        sig[l] = sig_window
+    return _with_modules(geom, cs, ns, us, vs, hws, hls, lay, grid, sig)
+
+
+def geometry_phase2_modular_disks(**kw) -> Geometry:
+    """geometry_phase2_modular with the 4th to 6th disk of each endcap (|z| = 166-193 cm) built
+    from planar modules too."""
+    g = geometry_phase2_modular(**kw)
+    disks = [l for l in range(g.n_layers) if g.kind[l] == DISK]
+    by_side = {s: sorted([l for l in disks if np.sign(g.pos[l]) == s], key=lambda l: abs(g.pos[l])) for s in (1, -1)}
+    return add_disk_modules(g, by_side[1][3:6] + by_side[-1][3:6])
 
 
 def geometry_phase2_modular(layers=(3, 4, 5), **kw) -> Geometry:
@@ -194,10 +248,11 @@ def _module_crossings(mods: Modules, layer, x, y, z, psi, th, om):
     with the modules around that point: Newton in the transverse path sigma on
     n.(X(sigma) - c) = 0 along the circle-centre trajectory, kept if |sigma| < 10 cm and inside
     the module.  Returns per track up to two (module, sigma, point) in path order."""
-    first, nphi, zc = mods.grid[layer]
+    first, nphi, zc, coord = mods.grid[layer]
     dphi = 2 * np.pi / nphi
     j0 = np.round(np.mod(np.arctan2(y, x), 2 * np.pi) / dphi).astype(np.int64)
-    k0 = np.round((z - zc[0]) / (zc[1] - zc[0])).astype(np.int64)
+    w = z if coord == "z" else np.hypot(x, y)   # ring coordinate: z on a cylinder, r on a disk
+    k0 = np.round((w - zc[0]) / (zc[1] - zc[0])).astype(np.int64)
     cand = []
     for dj in (-1, 0, 1):
         for dk in (-1, 0, 1):
@@ -588,7 +643,7 @@ def simulate_event(geom: Geometry, n_tracks: int, seed: int = 0, event: int = 0,
         if mods is not None and lay in mods.grid:
             # primary and overlap hits on their modules, noise uniform over the layer's modules
             oi, ok_ = np.nonzero((t_layers == lay) & (t_omod >= 0))
-            first, nphi, zc = mods.grid[lay]
+            first, nphi, zc, _ = mods.grid[lay]
             nm = rng.integers(first, first + nphi * zc.size, nn)
             ab = rng.uniform(-1.0, 1.0, (2, nn))
             npos = mods.c[nm] + (ab[0] * mods.hw[nm])[:, None] * mods.u[nm] + (ab[1] * mods.hl[nm])[:, None] * mods.v[nm]

@@ -1,6 +1,7 @@
 """Module planes and overlap hits on the GPU (Sec. 3.1 module position and normal: the Phase-2
 tilted barrel; Sec. 2.2: a single additional detector-overlap hit) against the oracle, on the same
-inputs: the Phase-2-like tracker with cylinders 3-5 built from flat and tilted modules.
+inputs: the Phase-2-like tracker with cylinders 3-5 built from flat and tilted modules, and the
+same with the 4th-6th disk of each endcap built from planar modules.
 
 Search: hit lists and overlap hits bit-exact up to the first near-tie step the oracle flags;
 parameters, covariance and chi2 within the forward search's tolerances (oracle/parity.py).  Fit
@@ -22,9 +23,9 @@ def lib():
     return mkgb.load_library()
 
 
-@pytest.fixture(scope="module")
-def work():
-    g = S.geometry_phase2_modular()
+@pytest.fixture(scope="module", params=["barrel_modules", "barrel_and_disk_modules"])
+def work(request):
+    g = S.geometry_phase2_modular() if request.param == "barrel_modules" else S.geometry_phase2_modular_disks()
     evs = [S.simulate_event(g, 1501, 41, e, pt_sampler=S.sample_pt_phase2, eta_max=3.0, noise_total=4000)
            for e in range(3)]
     return g, S.concat_events(evs, g.n_layers)
@@ -233,7 +234,7 @@ def test_modular_search_full_size_sampled(lib):
     """16 modular events x 20,000 tracks + 50,000 noise hits on the device, the launch
     configuration of the benchmark; a sample of 300 seeds against the oracle."""
     import torch
-    g = S.geometry_phase2_modular()
+    g = S.geometry_phase2_modular_disks()
     evs = [S.simulate_event(g, 20000, 0, e, pt_sampler=S.sample_pt_phase2, eta_max=3.0, noise_total=50000)
            for e in range(16)]
     batch = S.concat_events(evs, g.n_layers)

@@ -161,10 +161,14 @@ def _oracle_with_modules(geo, batch, params=None):
     return orc
 
 
-def test_module_search_finds_true_hits_and_overlaps(geo):
+@pytest.mark.parametrize("disks", [False, True])
+def test_module_search_finds_true_hits_and_overlaps(geo, disks):
     """On modular events the search takes the true hit on most modular layer crossings and picks
     up the true overlap hit where the track crossed two modules; every overlap hit lies on the
-    same layer as, and on another module than, the step's hit."""
+    same layer as, and on another module than, the step's hit.  disks: the endcaps' 4th-6th disks
+    built from planar modules too."""
+    if disks:
+        geo = S.geometry_phase2_modular_disks()
     batch = _modular_batch(geo)
     orc = _oracle_with_modules(geo, batch)
     o = PR.oracle_build(orc, batch)
