@@ -158,7 +158,8 @@ int mkgb_load_hits(mkgb_ctx* ctx, int n_events, const int64_t* seg_off,
  * mkgb_fit_backward use module hits on their planes (status 1 if a plane is not reached within
  * 10 cm, or only at grazing incidence; the backward fit's start state is taken on the plane of its
  * last hit's module); mkgb_build_backward tests and picks up module hits as mkgb_build does (its
- * out->ovl_hits likewise); mkgb_fit_grad takes no module hits (MKGB_EINVAL).  Synchronises the
+ * out->ovl_hits likewise); mkgb_fit_grad uses them on their planes as mkgb_fit (the alignment
+ * moves the hits, the module planes stay nominal).  Synchronises the
  * stream (the module ids are checked on the device).  Errors: those of mkgb_load_hits; MKGB_ESTATE
  * without modules; MKGB_EINVAL for a NULL hit_module or a hit whose module does not fit its layer. */
 int mkgb_load_hits_modular(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz,

@@ -41,8 +41,11 @@ def _geom_scaled(geom, xscale):
     return g2
 
 
-def total_chi2(geom, params, layers, hits, hit_xyz, hit_cov, hit_layer, p0, c0, align, xscale, per_track=False):
+def total_chi2(geom, params, layers, hits, hit_xyz, hit_cov, hit_layer, p0, c0, align, xscale, per_track=False,
+               hit_mod=None):
     orc = Oracle(_geom_scaled(geom, xscale), params)
+    if hit_mod is not None:   # module hits used on their module planes (nominal, not aligned)
+        orc.set_modules(geom.modules.c, geom.modules.n, hit_mod)
     X = aligned_hits(geom, hit_xyz, hit_layer, align)
     r = orc.fit_batch(layers, hits, X, np.asarray(hit_cov, np.float64), np.asarray(p0, np.float64),
                       np.asarray(c0, np.float64))
@@ -51,7 +54,7 @@ def total_chi2(geom, params, layers, hits, hit_xyz, hit_cov, hit_layer, p0, c0, 
 
 
 def fd_gradient(geom, params, layers, hits, hit_xyz, hit_cov, hit_layer, p0, c0, align=None, xscale=None,
-                h_shift=1e-4, h_rot=1e-6, h_scale=1e-3, h_p0=(1e-4, 1e-4, 1e-4, 1e-5, 1e-6, 1e-6)):
+                h_shift=1e-4, h_rot=1e-6, h_scale=1e-3, h_p0=(1e-4, 1e-4, 1e-4, 1e-5, 1e-6, 1e-6), hit_mod=None):
     """FP64 central differences: (chi2 per track, status, d/dp0 [n, 6], d/dalign [L, 6], d/dxscale [L]).
 
     Steps: the oracle's chi2 carries ~1e-8 absolute noise from its Newton stopping rule, so the
@@ -63,15 +66,16 @@ def fd_gradient(geom, params, layers, hits, hit_xyz, hit_cov, hit_layer, p0, c0,
     xscale = np.ones(L) if xscale is None else np.asarray(xscale, np.float64)
     p0 = np.asarray(p0, np.float64)
     args = (geom, params, layers, hits, hit_xyz, hit_cov, hit_layer)
-    chi2, status = total_chi2(*args, p0, c0, align, xscale, per_track=True)
+    kw = dict(per_track=True, hit_mod=hit_mod)
+    chi2, status = total_chi2(*args, p0, c0, align, xscale, **kw)
     ok = status == 0
     # per-track starting parameters: each track's chi2 depends on its own p0 only
     dp0 = np.zeros_like(p0)
     for k in range(6):
         dp = np.zeros_like(p0)
         dp[:, k] = h_p0[k]
-        cp, sp = total_chi2(*args, p0 + dp, c0, align, xscale, per_track=True)
-        cm, sm = total_chi2(*args, p0 - dp, c0, align, xscale, per_track=True)
+        cp, sp = total_chi2(*args, p0 + dp, c0, align, xscale, **kw)
+        cm, sm = total_chi2(*args, p0 - dp, c0, align, xscale, **kw)
         dp0[:, k] = np.where(ok & (sp == 0) & (sm == 0), (cp - cm) / (2 * dp[:, k]), 0.0)
     used = np.unique(np.asarray(layers)[np.asarray(layers) >= 0])
     dal = np.zeros((L, 6))
@@ -82,14 +86,14 @@ def fd_gradient(geom, params, layers, hits, hit_xyz, hit_cov, hit_layer, p0, c0,
             h = h_shift if k < 3 else h_rot
             a = align.copy()
             a[l, k] += h
-            cp, sp = total_chi2(*args, p0, c0, a, xscale, per_track=True)
+            cp, sp = total_chi2(*args, p0, c0, a, xscale, **kw)
             a[l, k] -= 2 * h
-            cm, sm = total_chi2(*args, p0, c0, a, xscale, per_track=True)
+            cm, sm = total_chi2(*args, p0, c0, a, xscale, **kw)
             dal[l, k] = (keep(cp, sp) - keep(cm, sm)) / (2 * h)
         x = xscale.copy()
         x[l] += h_scale
-        cp, sp = total_chi2(*args, p0, c0, align, x, per_track=True)
+        cp, sp = total_chi2(*args, p0, c0, align, x, **kw)
         x[l] -= 2 * h_scale
-        cm, sm = total_chi2(*args, p0, c0, align, x, per_track=True)
+        cm, sm = total_chi2(*args, p0, c0, align, x, **kw)
         dxs[l] = (keep(cp, sp) - keep(cm, sm)) / (2 * h_scale)
     return chi2, status, dp0, dal, dxs

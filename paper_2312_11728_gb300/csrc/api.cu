@@ -826,7 +826,6 @@ int mkgb_fit_grad(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, co
     if (mode != 0 && mode != 1) return fail(ctx, MKGB_EINVAL, "fit_grad mode %d (0 reverse sweep, 1 forward)", mode);
     if (!ctx->has_geom || !ctx->has_params) return fail(ctx, MKGB_ESTATE, "fit_grad before geometry/params");
     if (!ctx->has_hits) return fail(ctx, MKGB_ESTATE, "fit_grad before load_hits");
-    if (ctx->mod_hits) return fail(ctx, MKGB_EINVAL, "the fit derivative takes hits without modules");
     if (n < 0 || max_steps < 0) return fail(ctx, MKGB_EINVAL, "negative size");
     if (!align || !xscale || !d_align || !d_xscale) return fail(ctx, MKGB_EINVAL, "null alignment/material array");
     if (n > 0 && (!layers || !hits || !p0 || !c0 || !chi2_out || !d_p0)) return fail(ctx, MKGB_EINVAL, "null fit array");
@@ -859,7 +858,7 @@ int mkgb_fit_grad(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, co
     CK(launch_fit_grad(st, (const DevGeom*)ctx->geom_d.p, ctx->params, (const float4*)ctx->pay.p, ctx->n_hits, n,
                        max_steps, (const int*)dl, (const int*)dh, (const float*)dp0, (const float*)dc0,
                        (const float*)dal, (const float*)dxs, (float*)xo, (float*)gp, (float*)ga, (float*)gx, (int*)so,
-                       ck));
+                       ck, ctx->mod_hits));
     CK(copy_back(ctx, chi2_out, xo, 4 * N, on_device));
     CK(copy_back(ctx, d_p0, gp, 24 * N, on_device));
     CK(copy_back(ctx, d_align, ga, 24 * NL, on_device));

@@ -116,7 +116,7 @@ size_t probe_sink_bytes(int n_sms);
 cudaError_t launch_fit_grad(cudaStream_t st, const DevGeom* g, DevParams P, const float4* pay, int64_t n_hits, int n,
                             int max_steps, const int* layers, const int* hits, const float* p0, const float* c0,
                             const float* align, const float* xscale, float* chi2_out, float* d_p0, float* d_align,
-                            float* d_xscale, int* status_out, float* ck);
+                            float* d_xscale, int* status_out, float* ck, bool modular = false);
 
 // Static scratch of mkgb_fit_static: [0, 64) work counters (kNumCounters x u64), [64, 80) the
 // FP64 refit counter, [256, 256 + 4 * kFitStaticMaxTracks) the refit list.  The counters and the

@@ -45,11 +45,26 @@ __device__ __forceinline__ D seeded(float v, int comp, int base) {
     return r;
 }
 
+// A module hit's chi2 and update on its module's plane (Sec. 3.1) with the alignment
+// displacement dm in the residual; 0 ok, 1 plane not reached, 3 update failed.  Not inlined: the
+// dual-number kernels keep their registers for the layers without modules.
+template <class T>
+__device__ __noinline__ int grad_module_update(int kind, const PredT<T>& q, const float4* __restrict__ mods, int mod,
+                                               float cB, T mx, T my, T mz, const T v[6], const T dm[3], StateT<T>& t,
+                                               T& x2) {
+    PredT<T> qp;
+    FrameT<T> fp;
+    if (!to_module_plane(kind, q, mods, mod, cB, qp, fp)) return 1;
+    if (!chi2_hit(fp, qp, mx, my, mz, v, x2, dm) || !kalman_update_f(fp, qp, mx, my, mz, v, t, nullptr, dm))
+        return 3;
+    return 0;
+}
+
 // One step of the fit in scalar T: propagate to layer l (its thickness scaled by xs), then, with
 // hit h >= 0, chi2 and update with the hit displaced by the alignment al (the displacement
 // d + w x (h - c) enters the residual, not the FP32 hit position, whose ulp at 1 m is 0.08 um);
 // h < 0 propagates only.  Returns 0 (ok; x2 = the step's chi2) or the fit's status code.
-template <class T>
+template <class T, bool MOD>
 __device__ __forceinline__ int fit_step(const DevGeom& g, const DevParams& P, const float4* __restrict__ pay,
                                         int64_t n_hits, int l, int h, StateT<T>& t, const T al[6], const T& xs,
                                         T& x2) {
@@ -65,7 +80,11 @@ __device__ __forceinline__ int fit_step(const DevGeom& g, const DevParams& P, co
         return 0;
     }
     float mf[3], vf[6];
-    load_hit(pay, h, mf, vf, nullptr);
+    int md = -1;
+    if constexpr (MOD)
+        load_hit(pay, h, mf, vf, nullptr, &md);
+    else
+        load_hit(pay, h, mf, vf, nullptr);
     const float cz = L.kind == MKGB_DISK ? L.pos : 0.0f;
     const T r0(mf[0]), r1(mf[1]), r2(mf[2] - cz);
     const T dm[3] = {al[0] + (al[4] * r2 - al[5] * r1), al[1] + (al[5] * r0 - al[3] * r2),
@@ -74,11 +93,17 @@ __device__ __forceinline__ int fit_step(const DevGeom& g, const DevParams& P, co
     T v[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) v[c] = T(vf[c]);
+    if (MOD && md >= 0) {   // a module hit, on its module's plane (not reached: status 1, as the fit)
+        const int rm = grad_module_update(L.kind, q, g.mods, md, g.cB, mx, my, mz, v, dm, t, x2);
+        if (rm == 1) pred_to_state(L.kind, q, t);
+        return rm;
+    }
     if (!chi2_hit(L.kind, q, mx, my, mz, v, x2, dm) || !kalman_update(L.kind, q, mx, my, mz, v, t, nullptr, dm))
         return 3;
     return 0;
 }
 
+template <bool MOD>
 __global__ void __launch_bounds__(kThreads) k_fit_grad(const DevGeom* __restrict__ gp, DevParams P,
                                                        const float4* __restrict__ pay, int64_t n_hits, int n,
                                                        int max_steps, const int* __restrict__ layers,
@@ -120,7 +145,7 @@ __global__ void __launch_bounds__(kThreads) k_fit_grad(const DevGeom* __restrict
                 for (int c = 0; c < 6; ++c) ald[c] = seeded(al[c], cj + c, base);
                 const D xs = seeded(xscale[l], cj + 6, base);
                 D x2;
-                status = fit_step<D>(g, P, pay, n_hits, l, hrow[j], t, ald, xs, x2);
+                status = fit_step<D, MOD>(g, P, pay, n_hits, l, hrow[j], t, ald, xs, x2);
                 if (status != 0) break;
                 sum += x2;
             }
@@ -189,6 +214,7 @@ __device__ __forceinline__ void load_ck(const float* __restrict__ p, State& t) {
 // the layer's 6 alignment parameters, its thickness scale.
 constexpr int kStateIn = 27, kStepIn = 34;
 
+template <bool MOD>
 __global__ void __launch_bounds__(kThreads) k_fit_adjoint(
     const DevGeom* __restrict__ gp, DevParams P, const float4* __restrict__ pay, int64_t n_hits, int n,
     int max_steps, const int* __restrict__ layers, const int* __restrict__ hits, const float* __restrict__ p0,
@@ -223,7 +249,7 @@ __global__ void __launch_bounds__(kThreads) k_fit_adjoint(
             const int l = lrow[j];
             store_ck(ck + ((int64_t)j * n + i) * 32, t);
             float x2 = 0.0f;
-            status = fit_step<float>(g, P, pay, n_hits, l, hrow[j], t, align + 6 * l, xscale[l], x2);
+            status = fit_step<float, MOD>(g, P, pay, n_hits, l, hrow[j], t, align + 6 * l, xscale[l], x2);
             chi2v += x2;
         }
         // ---- reverse sweep
@@ -252,7 +278,7 @@ __global__ void __launch_bounds__(kThreads) k_fit_adjoint(
                 for (int c = 0; c < 6; ++c) ald[c] = seeded(al[c], kStateIn + c, base);
                 const D xs = seeded(xscale[l], kStepIn - 1, base);
                 D x2;
-                if (fit_step<D>(g, P, pay, n_hits, l, h, td, ald, xs, x2) != 0) {
+                if (fit_step<D, MOD>(g, P, pay, n_hits, l, h, td, ald, xs, x2) != 0) {
                     status = 5;   // the redone step failed where the plain pass did not
                     break;
                 }
@@ -303,14 +329,16 @@ __global__ void __launch_bounds__(kThreads) k_fit_adjoint(
 cudaError_t launch_fit_grad(cudaStream_t st, const DevGeom* g, DevParams P, const float4* pay, int64_t n_hits, int n,
                             int max_steps, const int* layers, const int* hits, const float* p0, const float* c0,
                             const float* align, const float* xscale, float* chi2_out, float* d_p0, float* d_align,
-                            float* d_xscale, int* status_out, float* ck) {
+                            float* d_xscale, int* status_out, float* ck, bool modular) {
     if (n == 0) return cudaSuccess;
     const int blocks = (n + kThreads - 1) / kThreads;
+    auto adjoint = modular ? k_fit_adjoint<true> : k_fit_adjoint<false>;
+    auto forward = modular ? k_fit_grad<true> : k_fit_grad<false>;
     if (ck)
-        k_fit_adjoint<<<blocks, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p0, c0, align,
+        adjoint<<<blocks, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p0, c0, align,
                                                    xscale, chi2_out, d_p0, d_align, d_xscale, status_out, ck);
     else
-        k_fit_grad<<<blocks, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p0, c0, align, xscale,
+        forward<<<blocks, kThreads, 0, st>>>(g, P, pay, n_hits, n, max_steps, layers, hits, p0, c0, align, xscale,
                                                 chi2_out, d_p0, d_align, d_xscale, status_out);
     return cudaGetLastError();
 }

@@ -134,18 +134,21 @@ def test_modular_edge_cases(lib, work):
     hm2[j] = int(hm[i])
     with pytest.raises(mkgb.MkgbError):
         ctx.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov, hit_module=hm2)
+    # module tables that do not describe planes of this geometry
+    from types import SimpleNamespace
+    mods = g.modules
+    for bad_mod in (SimpleNamespace(layer=mods.layer, c=mods.c, n=mods.n * 1.1),
+                    SimpleNamespace(layer=np.full_like(mods.layer, g.n_layers), c=mods.c, n=mods.n),
+                    SimpleNamespace(layer=mods.layer, c=np.where(np.arange(mods.c.shape[0])[:, None] == 3, np.nan, mods.c),
+                                    n=mods.n)):
+        with pytest.raises(mkgb.MkgbError):
+            ctx.load_modules(bad_mod)
+    ctx.load_modules(mods)
     # without modules loaded, module ids are refused
     plain = pipeline.make_context(S.geometry_phase2(), params)
     with pytest.raises(mkgb.MkgbError):
         plain.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov, hit_module=hm)
-    # the fit derivative takes no module hits
     ctx.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov, hit_module=hm)
-    fi = pipeline.fit_inputs(batch)
-    z = lambda *s, t=np.float32: np.zeros(s, t)
-    n, NL = 4, g.n_layers
-    with pytest.raises(mkgb.MkgbError):
-        ctx.fit_grad(fi.layers[:n], fi.hits[:n], fi.p0[:n], fi.c0[:n], z(NL, 6), np.ones(NL, np.float32), z(n),
-                     z(n, 6), z(NL, 6), z(NL))
     # a seed with a module hit fails, as in the oracle
     sh = batch.seed_hits[:6].copy()
     sh[0, 2] = i
@@ -256,3 +259,50 @@ def test_modular_search_full_size_sampled(lib):
     assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0, rep
     assert _check_ovl(out, o) == []
     assert (out["ovl"] >= 0).sum() > 0.05 * S_
+
+
+def _hit_layer(batch):
+    hl = np.zeros(batch.hit_xyz.shape[0], np.int64)
+    for s in range(len(batch.hit_off) - 1):
+        hl[batch.hit_off[s]:batch.hit_off[s + 1]] = s % batch.n_layers
+    return hl
+
+
+def test_modular_fit_gradient_matches_oracle_differences(lib):
+    """The derivative of the fit's total chi2 (mkgb_fit_grad, reverse sweep and forward mode) with
+    module hits used on their planes, at an alignment and material off nominal, against the
+    oracle's FP64 central differences with the same modules (oracle/gradient.py); tolerances as
+    the layers-only derivative tests (tests/test_gpu_grad.py)."""
+    from oracle import gradient as OG
+    g = S.add_modules(S.geometry_barrel(), [3, 4, 5])
+    ev = S.simulate_event(g, 400, 5, 0, eta_max=1.0,
+                          pt_sampler=lambda rng, n: S.sample_pt_loguniform(rng, n, 1.0, 10.0))
+    batch = S.concat_events([ev], g.n_layers)
+    fi = pipeline.fit_inputs(batch)
+    L = g.n_layers
+    rng = np.random.default_rng(3)
+    align = np.zeros((L, 6))
+    align[:, :3] = 20e-4 * rng.standard_normal((L, 3))
+    align[:, 3:] = 5e-5 * rng.standard_normal((L, 3))
+    xscale = 1.0 + 0.1 * rng.standard_normal(L)
+    chi2, status, dp0, dal, dxs = OG.fd_gradient(g, S.default_params(), fi.layers, fi.hits, batch.hit_xyz,
+                                                 batch.hit_cov, _hit_layer(batch), fi.p0, fi.c0, align, xscale,
+                                                 hit_mod=batch.hit_mod)
+    ok = status == 0
+    assert ok.mean() > 0.95
+    assert (batch.hit_mod[fi.hits[ok]] >= 0).any(1).mean() > 0.8   # the tracks use module hits
+    used = np.unique(fi.layers[fi.layers >= 0])
+    ctx = _ctx(g, batch, S.default_params())
+    for mode in (0, 1):
+        out = dict(chi2=np.zeros(len(ok), np.float32), dp0=np.zeros((len(ok), 6), np.float32),
+                   dal=np.zeros((L, 6), np.float32), dxs=np.zeros(L, np.float32), status=np.zeros(len(ok), np.int32))
+        ctx.fit_grad(fi.layers, fi.hits, fi.p0, fi.c0, align.astype(np.float32), xscale.astype(np.float32),
+                     out["chi2"], out["dp0"], out["dal"], out["dxs"], out["status"], mode=mode)
+        assert np.array_equal(out["status"], status), mode
+        assert PR.chi2_close(out["chi2"][ok], chi2[ok])[0].all(), mode
+        for got, ref, name in ((out["dal"][used], dal[used], "align"), (out["dxs"][used], dxs[used], "xscale")):
+            lhs, rhs = np.abs(got - ref), 1e-2 * np.abs(ref) + 1e-3 * np.abs(ref).max()
+            assert np.all(lhs <= rhs), (name, mode, float((lhs / rhs).max()))
+        for k in range(6):
+            r = np.abs(out["dp0"][ok, k] - dp0[ok, k]) / np.maximum(np.abs(dp0[ok, k]), 1e-3 * np.abs(dp0[ok, k]).max())
+            assert np.median(r) < 1e-3 and np.percentile(r, 98) < 1e-2, (k, mode, np.median(r), np.percentile(r, 98))
