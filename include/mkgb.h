@@ -260,6 +260,14 @@ int mkgb_run(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* x
              const int32_t* layers, const int32_t* hits, const float* p0, const float* c0, float* p_out,
              float* c_out, float* chi2_out, int32_t* status_out);
 
+/* mkgb_run for modular layers: the hits loaded with mkgb_load_hits_modular (hit_module, a device
+ * array of n ints, its module per hit), then mkgb_seed, mkgb_build (out->ovl_hits as there) and
+ * mkgb_fit as in mkgb_run.  Errors: those of mkgb_run and mkgb_load_hits_modular. */
+int mkgb_run_modular(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz, const float* cov6,
+                     const int32_t* hit_module, int n_seeds, const int32_t* seed_hits, const mkgb_tracks* out,
+                     int n_fit, int max_steps, const int32_t* layers, const int32_t* hits, const float* p0,
+                     const float* c0, float* p_out, float* c_out, float* chi2_out, int32_t* status_out);
+
 /* Launch configuration of the search rounds (mkgb_build, mkgb_run).  The paper has no
  * counterpart: this is a library service that changes neither results nor arithmetic.
  * find_shape / select_shape pick the block shape of the two per-layer kernels of the search

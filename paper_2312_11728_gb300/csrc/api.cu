@@ -919,11 +919,14 @@ int mkgb_fit_static(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, 
     return MKGB_OK;
 }
 
-int mkgb_run(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz, const float* cov6, int n_seeds,
-             const int32_t* seed_hits, const mkgb_tracks* out, int n_fit, int max_steps, const int32_t* layers,
-             const int32_t* hits, const float* p0, const float* c0, float* p_out, float* c_out, float* chi2_out,
-             int32_t* status_out) {
-    if (!ctx) return MKGB_EINVAL;
+}  // extern "C"
+
+namespace {
+
+int run_impl(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz, const float* cov6,
+             const int32_t* hit_module, int n_seeds, const int32_t* seed_hits, const mkgb_tracks* out, int n_fit,
+             int max_steps, const int32_t* layers, const int32_t* hits, const float* p0, const float* c0,
+             float* p_out, float* c_out, float* chi2_out, int32_t* status_out) {
     DevGuard guard(ctx->device);
     const cudaStream_t main_st = ctx->stream;
     if (!ctx->fit_st) {
@@ -931,7 +934,8 @@ int mkgb_run(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* x
         CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&ctx->ev_fit, cudaEventDisableTiming));
     }
-    int rc = mkgb_load_hits(ctx, n_events, seg_off, xyz, cov6, 1);
+    int rc = hit_module ? mkgb_load_hits_modular(ctx, n_events, seg_off, xyz, cov6, hit_module, 1)
+                        : mkgb_load_hits(ctx, n_events, seg_off, xyz, cov6, 1);
     if (rc != MKGB_OK) return rc;
     // the fit needs the prepared hits only: it runs on its own stream beside the seed fit and
     // the search, and the context's stream waits for it before the call ends
@@ -945,6 +949,29 @@ int mkgb_run(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* x
     if (rc == MKGB_OK) rc = mkgb_build(ctx, out, 1);
     CK(cudaStreamWaitEvent(main_st, ctx->ev_fit, 0));
     return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mkgb_run(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz, const float* cov6, int n_seeds,
+             const int32_t* seed_hits, const mkgb_tracks* out, int n_fit, int max_steps, const int32_t* layers,
+             const int32_t* hits, const float* p0, const float* c0, float* p_out, float* c_out, float* chi2_out,
+             int32_t* status_out) {
+    if (!ctx) return MKGB_EINVAL;
+    return run_impl(ctx, n_events, seg_off, xyz, cov6, nullptr, n_seeds, seed_hits, out, n_fit, max_steps, layers,
+                    hits, p0, c0, p_out, c_out, chi2_out, status_out);
+}
+
+int mkgb_run_modular(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz, const float* cov6,
+                     const int32_t* hit_module, int n_seeds, const int32_t* seed_hits, const mkgb_tracks* out,
+                     int n_fit, int max_steps, const int32_t* layers, const int32_t* hits, const float* p0,
+                     const float* c0, float* p_out, float* c_out, float* chi2_out, int32_t* status_out) {
+    if (!ctx) return MKGB_EINVAL;
+    if (!hit_module) return fail(ctx, MKGB_EINVAL, "null hit_module");
+    return run_impl(ctx, n_events, seg_off, xyz, cov6, hit_module, n_seeds, seed_hits, out, n_fit, max_steps, layers,
+                    hits, p0, c0, p_out, c_out, chi2_out, status_out);
 }
 
 int mkgb_set_launch(mkgb_ctx* ctx, int find_shape, int select_shape, int use_graph) {

@@ -46,7 +46,7 @@ class Tracks(C.Structure):
 EXPORTS = ["mkgb_create", "mkgb_destroy", "mkgb_last_error", "mkgb_version", "mkgb_load_geometry",
            "mkgb_set_params", "mkgb_load_hits", "mkgb_load_modules", "mkgb_load_hits_modular", "mkgb_seed", "mkgb_build", "mkgb_build_backward", "mkgb_fit",
            "mkgb_fit_backward",
-           "mkgb_fit_static", "mkgb_fit_grad", "mkgb_run", "mkgb_set_launch", "mkgb_autotune",
+           "mkgb_fit_static", "mkgb_fit_grad", "mkgb_run", "mkgb_run_modular", "mkgb_set_launch", "mkgb_autotune",
            "mkgb_probe_peak", "mkgb_clean_seeds", "mkgb_remove_duplicates", "mkgb_propagate", "mkgb_update",
            "mkgb_counters"]
 
@@ -270,14 +270,17 @@ class Context:
                     "mkgb_fit")
 
     def run(self, n_events, seg_off, xyz, cov, seed_hits, out: dict, layers, hits, p0, c0, p_out, c_out, chi2_out,
-            status_out=None):
+            status_out=None, hit_module=None):
         """mkgb_run: load_hits + seed + build + fit in one call, device tensors only; the fit runs
-        beside the seed fit and the search inside the call."""
+        beside the seed fit and the search inside the call.  With hit_module (module per hit):
+        mkgb_run_modular, and out may hold ovl."""
         so = np.ascontiguousarray(seg_off, np.int64)
         f, i = np.float32, np.int32
         ptrs = [_ptr(out[k], t, out=True) for k, t in (("params", f), ("cov", f), ("chi2", f), ("score", f),
                                               ("nfound", i), ("nholes", i), ("hits", i))]
-        t = Tracks(*[p for p, _ in ptrs], int(out["hits"].shape[1]))
+        if "ovl" in out:
+            ptrs.append(_ptr(out["ovl"], i, out=True))
+        t = Tracks(*[p for p, _ in ptrs[:7]], int(out["hits"].shape[1]), ptrs[7][0] if len(ptrs) > 7 else None)
         args = [_ptr(xyz, f), _ptr(cov, f), _ptr(seed_hits, i), _ptr(layers, i), _ptr(hits, i), _ptr(p0, f),
                 _ptr(c0, f), _ptr(p_out, f, True), _ptr(c_out, f, True), _ptr(chi2_out, f, True),
                 _ptr(status_out, i, True)]
@@ -285,8 +288,17 @@ class Context:
             raise MkgbError("mkgb_run takes CUDA tensors only")
         (px, _), (pc, _), (ps, _), (pl, _), (ph, _), (pp, _), (pq, _), (po, _), (pco, _), (px2, _), (pst, _) = args
         n, m = layers.shape
-        self._check(self.lib.mkgb_run(self.h, int(n_events), so.ctypes.data, px, pc, int(seed_hits.shape[0]), ps,
-                                      C.byref(t), int(n), int(m), pl, ph, pp, pq, po, pco, px2, pst), "mkgb_run")
+        if hit_module is not None:
+            pm, dm = _ptr(hit_module, i)
+            if dm != 1:
+                raise MkgbError("mkgb_run_modular takes CUDA tensors only")
+            self._check(self.lib.mkgb_run_modular(self.h, int(n_events), so.ctypes.data, px, pc, pm,
+                                                  int(seed_hits.shape[0]), ps, C.byref(t), int(n), int(m), pl, ph,
+                                                  pp, pq, po, pco, px2, pst), "mkgb_run_modular")
+        else:
+            self._check(self.lib.mkgb_run(self.h, int(n_events), so.ctypes.data, px, pc, int(seed_hits.shape[0]),
+                                          ps, C.byref(t), int(n), int(m), pl, ph, pp, pq, po, pco, px2, pst),
+                        "mkgb_run")
         self.n_seeds = int(seed_hits.shape[0])
         return out
 

@@ -306,3 +306,37 @@ def test_modular_fit_gradient_matches_oracle_differences(lib):
         for k in range(6):
             r = np.abs(out["dp0"][ok, k] - dp0[ok, k]) / np.maximum(np.abs(dp0[ok, k]), 1e-3 * np.abs(dp0[ok, k]).max())
             assert np.median(r) < 1e-3 and np.percentile(r, 98) < 1e-2, (k, mode, np.median(r), np.percentile(r, 98))
+
+
+def test_modular_one_call_pass_equals_separate_calls(lib, work):
+    """mkgb_run_modular (load hits with module ids, seed, search, fit in one call; the fit on a
+    second stream) gives bit-identical outputs to the separate calls."""
+    import torch
+    g, batch = work
+    params = S.default_params()
+    fi = pipeline.fit_inputs(batch)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    n, nt = batch.seed_hits.shape[0], fi.layers.shape[0]
+    X, V, HM, SH = dev(batch.hit_xyz), dev(batch.hit_cov), dev(batch.hit_mod), dev(batch.seed_hits)
+    L, H, P0, C0 = dev(fi.layers), dev(fi.hits), dev(fi.p0), dev(fi.c0)
+    res = []
+    for one_call in (True, False):
+        ctx = pipeline.make_context(g, params)
+        out = mkgb.alloc_tracks(n, g.max_plan, device="cuda", ovl=True)
+        fo = [torch.zeros((nt, 6), device="cuda"), torch.zeros((nt, 21), device="cuda"), torch.zeros(nt, device="cuda"),
+              torch.zeros(nt, dtype=torch.int32, device="cuda")]
+        if one_call:
+            ctx.run(batch.n_events, batch.hit_off, X, V, SH, out, L, H, P0, C0, *fo, hit_module=HM)
+        else:
+            ctx.load_hits(batch.n_events, batch.hit_off, X, V, hit_module=HM)
+            ctx.fit(L, H, P0, C0, *fo)
+            ctx.seed(SH)
+            ctx.build(out)
+        torch.cuda.synchronize()
+        res.append(({k: v.cpu().numpy() for k, v in out.items()}, [f.cpu().numpy() for f in fo]))
+    (a, fa), (b, fb) = res
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    for x, y in zip(fa, fb):
+        assert np.array_equal(x, y)
+    assert (a["ovl"] >= 0).sum() > 0
