@@ -51,8 +51,10 @@ struct BuildOutDev {
 struct BuildWork {
     unsigned char* st[2];   // slot states, 32 words (FP32 or FP64 per the precision)
     int4* meta[2];    // slot (score, chi2 sum, nfound | nholes << 8 | stopped << 16, alive)
-    unsigned char* pr;      // slot predictions at the round's layer, 24 words
-    int4* ls;         // slot children: (n hits, non-hit kind, non-hit score, -) + 4 x (chi2, hit, chi2, hit)
+    unsigned char* pr;      // slot predictions at the round's layer, 28 words
+    // slot children: (n hits, non-hit kind, non-hit score, b2) + 4 x (chi2, hit, chi2, hit); b2: with
+    // module hits, the best accepted hit on another module than the first entry's (-1 none)
+    int4* ls;
     int* live[2];     // work list of live candidate slots per round
     int* seeds[2];    // work list of seeds with a live candidate per round
     int4* sinfo;      // per ordered seed: (plan position of its first step, first step, steps, event)

@@ -16,8 +16,10 @@
 // the trail back for its hit list (a13).
 //
 // Slot records are array-of-structures in HBM: a state is 32 floats (xh, yh, zh, xl, yl, zl, k,
-// phi, theta, 21 covariance terms, 2 spare), a prediction 24 floats, a child list 20 ints, the
-// slot's (score, chi2 sum, counts, alive) one int4.  Work lists are filled with warp-aggregated
+// phi, theta, 21 covariance terms, theta's and phi's low parts), a prediction 28 floats, a child
+// list 20 ints, the slot's (score, chi2 sum, counts, alive) one int4.  With module hits loaded
+// (Sec. 3.1), the child list also names the best accepted hit on another module than its first
+// entry's, and an overlap trail beside the hit trail keeps each step's overlap hit (Sec. 2.2).  Work lists are filled with warp-aggregated
 // atomics, so the threads of a warp read neighbouring slots.  No kernel waits on another block;
 // every loop is bounded by a list length, a window's bin range or the Newton iteration limit.
 #include "internal.h"
@@ -43,7 +45,7 @@ __device__ __forceinline__ float shfl_f(float v, int src) { return __shfl_sync(k
 __device__ __forceinline__ int shfl_i(int v, int src) { return __shfl_sync(kFull, v, src); }
 
 // ---- slot records: a state is 32 words (xh, yh, zh, xl, yl, zl, k, phi, theta, 21 covariance
-// terms, 2 spare), a prediction 24 words; words are F, moved as 16-byte vectors
+// terms, theta's and phi's low parts), a prediction 28 words; words are F, moved as 16-byte vectors
 
 __device__ __forceinline__ void unpack16(const float4& v, float* f) { f[0] = v.x; f[1] = v.y; f[2] = v.z; f[3] = v.w; }
 __device__ __forceinline__ void unpack16(const double2& v, double* f) { f[0] = v.x; f[1] = v.y; }

@@ -3,7 +3,8 @@
 // Propagation to a barrel cylinder or endcap disk in a uniform solenoid field with its
 // 6x6 Jacobian, covariance transport J C J^T, multiple scattering and mean energy loss
 // (a4-a7), the eta-phi window (a8), the 3D chi2 (a9) and the Joseph-form gain/update
-// (a11).  The paper (Sec. 3.1) names propagation, hit selection and the Kalman filter
+// (a11); the step from a layer's surface to the plane of a flat (or tilted) module
+// (Sec. 3.1 module position and normal) for the hits measured on modules.  The paper (Sec. 3.1) names propagation, hit selection and the Kalman filter
 // calculations as the per-layer work; the formulas are the textbook ones it cites.
 //
 // Every function is a template on the scalar type F: float is the bulk path, double the
