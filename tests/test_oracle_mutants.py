@@ -9,7 +9,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "mkoracle.c")
 PINS = ["tests/test_oracle_propagation.py", "tests/test_oracle_kalman.py", "tests/test_oracle_search.py",
-        "tests/test_oracle_modules.py"]
+        "tests/test_oracle_modules.py", "tests/test_oracle_highland.py"]
 
 MUTANTS = {
     "jacobian_sign": ("A[0 * 6 + 4] = -dy;", "A[0 * 6 + 4] = dy;"),
@@ -19,6 +19,8 @@ MUTANTS = {
     "ms_ktheta_sign": ("C[ix(5, 3)] += -k * cot * th02;", "C[ix(5, 3)] += k * cot * th02;"),
     "ms_phi_sin": ("C[ix(4, 4)] += th02 / (st * st);", "C[ix(4, 4)] += th02;"),
     "highland_log": ("log(t / (beta * beta))", "log(t * beta * beta)"),
+    "highland_scale": ("*theta0 = 0.0136 /", "*theta0 = 0.0141 /"),
+    "highland_log_coefficient": ("(1.0 + 0.038 * log", "(1.0 + 0.040 * log"),
     "eloss_sign": ("double e2 = e - direction * orc_eloss(pm, t);", "double e2 = e + direction * orc_eloss(pm, t);"),
     "update_sign": ("pout[i] = p[i] + K[i][0] * r[0]", "pout[i] = p[i] - K[i][0] * r[0]"),
     "chi2_index": ("double y2 = (r[2] - Lc[3] * y0 - Lc[4] * y1) / Lc[5];",
@@ -57,3 +59,39 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *PINS],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     assert r.returncode != 0, f"pins did not catch mutant {name}:\n{r.stdout[-2000:]}"
+
+
+def _compile(src_text, tmp_path):
+    mut = tmp_path / "mut.c"
+    mut.write_text(src_text)
+    so = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-I", os.path.join(ROOT, "oracle"), "-o", str(so), str(mut), "-lm"])
+    return so
+
+
+def test_highland_scale_shared_with_the_generator_is_caught(tmp_path):
+    """The same wrong Highland scale typed into the oracle and into the event generator: the
+    oracle still models the simulated detector (their agreement test passes), and only the PDG
+    pin fails."""
+    src = open(SRC).read()
+    old, new = MUTANTS["highland_scale"]
+    so = _compile(src.replace(old, new), tmp_path)
+    driver = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "import numpy as np\n"
+        "from paper_2312_11728_gb300 import synth as S\n"
+        "def _hl(p, t):\n"
+        "    beta = p / np.sqrt(p * p + 0.13957039 ** 2)\n"
+        "    return 0.0141 / (beta * p) * np.sqrt(t) * (1.0 + 0.038 * np.log(t / (beta * beta)))\n"
+        "S._highland = _hl\n"
+        "import pytest\n"
+        "sys.exit(pytest.main(['-q', '-p', 'no:cacheprovider', sys.argv[1]]))\n" % ROOT)
+    env = dict(os.environ, MKORACLE_LIB=str(so))
+    agree = subprocess.run([sys.executable, "-c", driver,
+                            "tests/test_oracle_propagation.py::test_material_model_equals_the_simulated_detector"],
+                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert agree.returncode == 0, agree.stdout[-2000:]
+    pin = subprocess.run([sys.executable, "-c", driver, "tests/test_oracle_highland.py"],
+                         cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert pin.returncode != 0, pin.stdout[-2000:]
