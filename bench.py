@@ -39,11 +39,67 @@ WORKLOAD = "phase2_like_{events}ev_20k_tracks_50k_noise_bestN6"
 #         update (a10-a11);
 #   fit: per track-layer step of k_fit (a4-a9, a11 on one hit).
 # Multi-function-unit work (sqrt, rsqrt, division seeds, sincos, log, atan2) is not counted.
-FLOPS = dict(find=1224.7, update=731.1, fit=1642.6, seed_fp64=3143.6)
+FLOPS = dict(find=1224.7, update=731.1, fit=1642.6, seed_fp64=3143.6, seed_fp32=1454.0)
 # the search and fit kernel sources the counts (and the DRAM traffic in profiles/) belong to
 KERNEL_SOURCES = ("paper_2312_11728_gb300/csrc/k_build.cu", "paper_2312_11728_gb300/csrc/kalman.cuh",
                   "paper_2312_11728_gb300/csrc/trig.cuh", "paper_2312_11728_gb300/csrc/dual.cuh",
                   "paper_2312_11728_gb300/csrc/internal.h", "paper_2312_11728_gb300/build.py")
+
+
+# Algorithmic HBM bytes per unit of work: the data each stage must read and write at least once,
+# whatever the kernel design (a state is 27 words = 108 B: 6 parameters + 21 covariance words):
+#   search: a crossed candidate-layer step reads the candidate's state (108 B); each kept child
+#     with a new state (a hit update, a miss or a stop) writes it (108 B) with its trail entry (the
+#     parent slot and hit, 4 B); every hit of the batch is read once (position, 6 covariance words
+#     and id, 40 B, with its binned (eta, phi), 8 B) with the bins' offsets (4 B per bin); each
+#     seed's start state is read (108 B) and its result written (27 words, chi2, score and two
+#     counts, 124 B, plus one hit id per plan step);
+#   fit: per track-layer step its hit (40 B) and hit id (4 B); per track its starting state (108 B)
+#     and its result (27 words, chi2, status: 116 B);
+#   seed: per seed its 3 hit ids (12 B) and hits (3 x 40 B), its state record written (128 B), its
+#     ordering key (8 B).
+ALG_BYTES = dict(state=108, child=112, hit=48, bin=4, seed_in=108, seed_out=124, hit_id=4,
+                 fit_step=44, fit_track=224, seed=268)
+
+
+def search_bytes(c, n_hits, n_bins, n_seeds, max_plan):
+    """c: build counters; c[5] (children with a new state) when reported, else the updates."""
+    kept = c[5] if len(c) > 5 else c[2]
+    return (ALG_BYTES["state"] * c[0] + ALG_BYTES["child"] * kept + ALG_BYTES["hit"] * n_hits
+            + ALG_BYTES["bin"] * n_bins
+            + (ALG_BYTES["seed_in"] + ALG_BYTES["seed_out"] + ALG_BYTES["hit_id"] * max_plan) * n_seeds)
+
+
+def fit_bytes(c, n_tracks):
+    return ALG_BYTES["fit_step"] * c[0] + ALG_BYTES["fit_track"] * n_tracks
+
+
+def roofline(name, ms, flops, nbytes, fp32_peak, hbm, traffic=None, fp64_flops=0.0, fp64_peak=None):
+    """Roofline of one stage: its time bound is the slower of the FP32 (or FP64) pipe and the
+    HBM bytes, max(F / P, B / BW); frac = that bound / the measured time (the larger of the two
+    fractions).  achieved / peak are given in the bound's own unit."""
+    t = ms / 1e3
+    t_fp32 = flops / (fp32_peak * 1e12)
+    t_fp64 = fp64_flops / (fp64_peak * 1e12) if fp64_peak else 0.0
+    t_hbm = nbytes / (hbm * 1e9)
+    if t_hbm >= max(t_fp32, t_fp64):
+        bound, achieved, peak, unit = "hbm", nbytes / t / 1e9, hbm, "GB/s"
+    elif t_fp64 > t_fp32:
+        bound, achieved, peak, unit = "fp64", fp64_flops / t / 1e12, fp64_peak, "TFLOP/s"
+    else:
+        bound, achieved, peak, unit = "alu", flops / t / 1e12, fp32_peak, "TFLOP/s"
+    r = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+         "traffic": traffic, "stage": name, "measured_ms": ms,
+         "bound_ms": {"hbm": t_hbm * 1e3, "fp32": t_fp32 * 1e3},
+         "hbm_frac": t_hbm / t, "fp32_frac": t_fp32 / t,
+         "algorithmic_bytes": int(nbytes), "algorithmic_fp32_flops": int(flops)}
+    if fp64_peak:
+        r["bound_ms"]["fp64"] = t_fp64 * 1e3
+        r["fp64_frac"] = t_fp64 / t
+        r["algorithmic_fp64_flops"] = int(fp64_flops)
+    if traffic:
+        r["traffic_over_algorithmic"] = traffic / nbytes
+    return r
 
 
 def build_flops(c):
@@ -203,8 +259,8 @@ def cpu_baseline_all_cores(g, evs, params):
                       f"({steps} Kalman steps, slowest worker {dt:.1f} s, FP64)"}
 
 
-def run_reference(args, rank):
-    if rank != 0:
+def run_reference(args, rank, world=1):
+    if rank != 0:   # the oracle baseline runs once, on rank 0's host cores
         return
     from paper_2312_11728_gb300 import pipeline, synth as S
     g, batch, _ = make_batch(0, n_events=2)
@@ -230,7 +286,7 @@ def run_reference(args, rank):
             steps.append(int(o["counters"][0] + r["counters"][0]))
     value = sum(steps) / sum(times)
     sample = f"per step {per_step} random seeds built + {per_step} tracks fitted from the same workload"
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD.format(events=N_EVENTS), "sample": sample},
@@ -240,10 +296,11 @@ def run_reference(args, rank):
 
 
 def measure_e2e(args, ctx, db, batch, fit, g, stream, kalman_steps, world, local, dist):
-    """The same pass through the C ABI with host (pinned) buffers: every step copies its inputs in
-    and its results out inside the timed region."""
+    """The same pass through the C ABI's host-array call (mkgb_run_host) with page-locked host
+    buffers: every step copies its inputs in and its results out inside the timed region (the
+    library overlaps the copies with the kernels); host wall-clock time of the synchronous calls."""
     import torch
-    from paper_2312_11728_gb300 import mkgb
+    from paper_2312_11728_gb300 import mkgb, pipeline
     n_seeds = batch.seed_hits.shape[0]
     n_tracks = fit.layers.shape[0]
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -258,26 +315,25 @@ def measure_e2e(args, ctx, db, batch, fit, g, stream, kalman_steps, world, local
     d2h = sum(v.numel() * v.element_size() for v in ho.values()) + sum(v.numel() * v.element_size() for v in hf.values())
 
     def e2e_step():
-        ctx.load_hits(db.n_events, db.seg_off, h["xyz"], h["cov"])
-        ctx.seed(h["seeds"])
-        ctx.build(ho)
-        ctx.fit(h["layers"], h["hits"], h["p0"], h["c0"], hf["p"], hf["c"], hf["chi2"], hf["status"])
+        ctx.run_host(db.n_events, db.seg_off, h["xyz"], h["cov"], h["seeds"], ho, h["layers"], h["hits"], h["p0"],
+                     h["c0"], hf["p"], hf["c"], hf["chi2"], hf["status"])
 
     for _ in range(max(1, args.warmup)):
         e2e_step()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     n_e2e = max(1, min(args.steps, 5))
-    e0.record(stream)
+    t0 = time.perf_counter()
     for _ in range(n_e2e):
         e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    from paper_2312_11728_gb300 import pipeline
-    value, _, _ = pipeline.replica_throughput(e0.elapsed_time(e1) / 1e3, kalman_steps * n_e2e, dist, f"cuda:{local}")
-    return {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    dt = time.perf_counter() - t0
+    # the host results equal the device-resident pass's (same kernels, same inputs)
+    same = bool(torch.equal(ho["hits"], db.out["hits"].cpu()) and torch.equal(hf["chi2"], db.fit["chi2"].cpu()))
+    value, _, _ = pipeline.replica_throughput(dt, kalman_steps * n_e2e, dist, f"cuda:{local}")
+    return {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": dt * 1e3 / n_e2e, "call": "mkgb_run_host (one call per step, page-locked host arrays)",
+            "same_results_as_device_pass": same}
 
 
 def measure_fp64_plain(args, g, params, evs, stream, local, rank, dist):
@@ -446,6 +502,18 @@ def measure_fit_grad(args, local, rank, dist, stream):
             "workload": "100k tracks, 22 layers, misaligned detector (50 um, 0.1 mrad), material x[0.8, 1.2]"}
 
 
+def spawn_replicas(n):
+    """Re-runs this script as n ranks (one process per GPU, rendezvous on 127.0.0.1); rank 0
+    prints the line.  Returns the launcher's exit status."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -464,11 +532,14 @@ def main():
     ap.add_argument("--shapes", default=None,
                     help="fixed launch shapes 'find,select' of the search kernels (no autotuning)")
     args = ap.parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # N replicas requested without a launcher: one process per GPU under torch.distributed.run
+        sys.exit(spawn_replicas(args.gpus))
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
-        run_reference(args, rank)
+        run_reference(args, rank, world)
         return
 
     from paper_2312_11728_gb300 import pipeline, synth as S
@@ -584,7 +655,6 @@ def main():
     hbm, sm_max, src = peaks()
     n_sms = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_peak = n_sms * 128 * 2 * sm_max * 1e6 / 1e12        # TFLOP/s at the maximum SM clock
-    achieved = build_flops(bc) / (np.mean(build_ms) / 1e3) / 1e12
     # DRAM bytes of the search kernels per crossed candidate-layer step, from an ncu capture of
     # the same sources (null if the kernels changed since)
     traffic = None
@@ -594,12 +664,26 @@ def main():
         if tr.get("sources_sha256_16") == kernel_sources_hash():
             traffic = tr["dram_bytes_per_crossed_step"] * int(bc[0])
     bins_total = batch.n_events * int((g.n_eta.astype(np.int64) * g.n_phi).sum())
+    n_hits = int(batch.hit_xyz.shape[0])
+    rf_search = roofline("search", stage["build"], build_flops(bc),
+                         search_bytes(bc, n_hits, bins_total, n_seeds, g.max_plan), fp32_peak, hbm, traffic)
+    rf_search.update({
+        "kernel": "search: k_start, one fused k_round per plan step (k_rescue after it when flagged), k_finish",
+        "peak_note": f"HBM {hbm:.1f} GB/s ({src} copy bandwidth); FP32 {n_sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
+                     f"({src} max clock) = {fp32_peak:.1f} TFLOP/s; FMA probe {probe['fp32_tflops']:.1f} TFLOP/s",
+        "launch": "algorithmic bytes and flops of one whole search over its CUDA-event time on the context's "
+                  "stream (all its launches, one mkgb_build call, its rounds replayed as a CUDA graph)"})
+    rf_fit = roofline("fit", stage["fit"], fit_flops(fc), fit_bytes(fc, n_tracks), fp32_peak, hbm)
+    rf_seed = roofline("seed", stage["seed"], FLOPS["seed_fp32"] * n_seeds, ALG_BYTES["seed"] * n_seeds, fp32_peak,
+                       hbm, fp64_flops=FLOPS["seed_fp64"] * n_seeds, fp64_peak=probe["fp64_tflops"])
     keys_total = batch.n_events * 32 * 64
-    # hits: prep, scatter, scans; seeds: fit, key, scans, scatter; search: start, (find, select,
-    # FP64 redo) per plan step of the longest plan, finish; fit: FP32 fit and FP64 refit
+    # hits: prep, scatter, scans; seeds: fit, key, scans, scatter; search: start, per plan step of
+    # the longest plan the fused round (or find and select) and the FP64 redo, finish; fit: FP32
+    # fit and FP64 refit
     redo = 1 if params["kappa_fp64"] > 0 else 0
+    per_round = (1 if shapes[0] >= 3 else 2) + redo
     launches_per_step = ((2 + scan_launches(bins_total)) + (2 + scan_launches(keys_total)) + 2
-                         + (2 + redo) * g.max_plan + 1 + redo)
+                         + per_round * g.max_plan + 1 + redo)
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -614,20 +698,10 @@ def main():
                    "search_launch": {"find_shape": shapes[0], "select_shape": shapes[1],
                                      "autotune_ms_per_search": shapes[2], "cuda_graph": not args.no_graph}},
         "stages_ms": {k: round(float(v), 4) for k, v in stage.items()},
-        "roofline": {"bound": "alu", "kernel": "search (k_start, k_find + k_select per plan step, k_finish)",
-                     "achieved": achieved, "peak": fp32_peak,
-                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
-                     "peak_note": f"FP32: {n_sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz ({src} max clock)",
-                     "probe_tflops": probe["fp32_tflops"],
-                     "frac_of_probe": achieved / probe["fp32_tflops"],
-                     "flops_per_launch": int(build_flops(bc)),
-                     "launch": "one mkgb_build call per step (its rounds replayed as one CUDA graph), "
-                               "timed with CUDA events on its stream"},
-        # the FP64 seed fit against the measured FP64 multiply-add rate of the same device
-        "seed_fp64_roofline": {"bound": "fp64", "achieved": FLOPS["seed_fp64"] * n_seeds / (stage["seed"] * 1e9),
-                               "peak_probe": probe["fp64_tflops"], "unit": "TFLOP/s",
-                               "frac": FLOPS["seed_fp64"] * n_seeds / (stage["seed"] * 1e9) / probe["fp64_tflops"],
-                               "flops_per_seed": FLOPS["seed_fp64"]},
+        "roofline": rf_search,
+        "roofline_stages": {"seed": rf_seed, "search": {k: rf_search[k] for k in rf_search
+                                                        if k not in ("peak_note", "launch", "kernel")},
+                            "fit": rf_fit},
         "e2e": e2e,
         "fp64_plain": fp64,
         "fit_grad": grad,

@@ -260,6 +260,24 @@ int mkgb_run(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* x
              const int32_t* layers, const int32_t* hits, const float* p0, const float* c0, float* p_out,
              float* c_out, float* chi2_out, int32_t* status_out);
 
+/* mkgb_run with every array in host memory (the call a host program makes with its event data):
+ * the same arguments, inputs and outputs as mkgb_run, and the same results bit for bit.  The
+ * library copies the inputs to the device and the outputs back, overlapping the copies with the
+ * kernels: the hits travel in up to 8 chunks of whole events (each chunk's hits are prepared as
+ * soon as it has arrived), the seeds and the fit's inputs follow while the seeds are fitted, the
+ * fit's outputs return while the search runs and the search's outputs at the end.  The overlap
+ * needs page-locked host arrays (cudaHostAlloc / cudaHostRegister); pageable arrays give the
+ * same results with the copies serialised.  The call returns when every output is in host
+ * memory (it synchronises the context's stream); device copies of the inputs and outputs are
+ * kept in one library buffer, reused by the next call.  Hit indices are checked on the device as
+ * in mkgb_run (a seed or fitted track with a hit index beyond the loaded hits gets a failure
+ * status instead of an error code).  Errors: MKGB_EINVAL for a NULL array with a nonzero size,
+ * negative sizes or bad seg_off, and those of mkgb_run. */
+int mkgb_run_host(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz, const float* cov6,
+                  int n_seeds, const int32_t* seed_hits, const mkgb_tracks* out, int n_fit, int max_steps,
+                  const int32_t* layers, const int32_t* hits, const float* p0, const float* c0, float* p_out,
+                  float* c_out, float* chi2_out, int32_t* status_out);
+
 /* mkgb_run for modular layers: the hits loaded with mkgb_load_hits_modular (hit_module, a device
  * array of n ints, its module per hit), then mkgb_seed, mkgb_build (out->ovl_hits as there) and
  * mkgb_fit as in mkgb_run.  Errors: those of mkgb_run and mkgb_load_hits_modular. */
@@ -270,25 +288,28 @@ int mkgb_run_modular(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const 
 
 /* Launch configuration of the search rounds (mkgb_build, mkgb_run).  The paper has no
  * counterpart: this is a library service that changes neither results nor arithmetic.
- * find_shape / select_shape pick the block shape of the two per-layer kernels of the search
- * (0: 128 threads, the default; 1: 64 threads; 2: 256 threads; each with its own register bound
- * and a grid of as many blocks as stay resident on the device).  use_graph = 1 (the default)
- * records the ~(2 + 3 x longest plan) launches of one search as a CUDA graph on the first call
- * and replays it while the arguments, shapes and stream stay the same (a change re-records);
- * the graph is used only on a stream created by the caller or the library (not the legacy or
- * per-thread default stream) and not while the stream is being captured by the caller, where
- * the launches are made one by one and join the caller's capture.  Results are identical for
- * every choice.  Errors: MKGB_EINVAL for a shape outside 0..2. */
+ * find_shape picks how a round of the search runs: 0, 1, 2 as two kernels per plan step (one
+ * thread per candidate for propagation, window and chi2; eight lanes per seed for the merge and
+ * the update) with blocks of 128, 64 or 256 threads for the first kernel and select_shape (0, 1,
+ * 2: 128, 64, 256 threads) for the second; 3, 4, 5 as one fused kernel per plan step (blocks of
+ * 128 threads with 4 or 3 resident per SM, or 256 threads with 2; select_shape is ignored).
+ * Each kernel launches as many blocks as stay resident on the device.  use_graph = 1 (the
+ * default) records the launches of one search as a CUDA graph on the first call and replays it
+ * while the arguments, shapes and stream stay the same (a change re-records); the graph is used
+ * only on a stream created by the caller or the library (not the legacy or per-thread default
+ * stream) and not while the stream is being captured by the caller, where the launches are made
+ * one by one and join the caller's capture.  Results are identical for every choice.  Errors:
+ * MKGB_EINVAL for find_shape outside 0..5 or select_shape outside 0..2. */
 int mkgb_set_launch(mkgb_ctx* ctx, int find_shape, int select_shape, int use_graph);
 
 /* Autotuner of the search launch shapes (library service, no counterpart in the paper): runs
- * the search over the seeds loaded now (mkgb_seed) once per shape pair (3 x 3 pairs), each
- * warmed once and then timed reps times with CUDA events on the context's stream, keeps the
- * fastest pair as the context's shapes (mkgb_set_launch) and writes it to find_shape /
- * select_shape (may be NULL) and its mean time per search to ms_out (may be NULL).  The outputs
- * of these searches go to the library's own buffers; loaded hits and seeds are not changed.
- * Synchronises the stream.  Errors: MKGB_ESTATE without seeds, MKGB_EINVAL for reps < 1, the
- * errors of mkgb_build. */
+ * the search over the seeds loaded now (mkgb_seed) once per launch configuration (the 3 x 3
+ * two-kernel pairs and the 3 fused shapes of mkgb_set_launch), each warmed once and then timed
+ * reps times with CUDA events on the context's stream, keeps the fastest as the context's
+ * shapes (mkgb_set_launch) and writes it to find_shape / select_shape (may be NULL) and its mean
+ * time per search to ms_out (may be NULL).  The outputs of these searches go to the library's
+ * own buffers; loaded hits and seeds are not changed.  Synchronises the stream.  Errors:
+ * MKGB_ESTATE without seeds, MKGB_EINVAL for reps < 1, the errors of mkgb_build. */
 int mkgb_autotune(mkgb_ctx* ctx, int reps, int* find_shape, int* select_shape, float* ms_out);
 
 /* Derivative of the fit (growth of Sec. 4's final fit): the fit over a known assignment with
@@ -326,7 +347,9 @@ int mkgb_fit_grad(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, co
  * pool) holds the free memory, so a stream-ordered loop that fits batch after batch keeps its
  * memory footprint fixed by calling this entry point instead.
  * Setup: the first call on a device looks up the scratch address (cudaGetSymbolAddress) and
- * keeps it for the process; make that first call before any stream capture begins.
+ * keeps it for the process; make that first call before any stream capture begins.  The kept
+ * address belongs to the device's primary context: after cudaDeviceReset in the same process it
+ * is stale, and calling this entry point again in that process is not supported.
  * Zero state: the work counters and the refit counter must be zero when a fit starts; the call
  * clears them itself (cudaMemsetAsync on the context's stream) before its kernels, and the
  * refit list needs no initial value.

@@ -282,6 +282,10 @@ class Oracle:
                                _p(np.ascontiguousarray(layers3, np.int32), C.c_int), _p(p), _p(c), _p(pi))
         return bool(ok), p, c, pi
 
+    def surfaces(self):
+        """(kind, position) of every layer surface: the frames in which results are compared."""
+        return np.asarray(self.geom.kind).copy(), np.asarray(self.geom.pos, np.float64).copy()
+
     # ---- batches
     def seed_batch(self, seed_hits, seed_layers, xyz, cov, material=None):
         mat = self.params["material"] if material is None else int(material)
@@ -294,7 +298,7 @@ class Oracle:
         reg, st, status = np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n, np.int32)
         self.lib.orc_seed_batch(self.gp, int(mat), n, _p(sh, C.c_int), _p(sl, C.c_int), _p(x), _p(cv),
                                 _p(p), _p(c), _p(pi), _p(reg, C.c_int), _p(st, C.c_int), _p(status, C.c_int))
-        return dict(p=p, c=c, pinit=pi, region=reg, start=st, status=status)
+        return dict(p=p, c=c, pinit=pi, region=reg, start=st, status=status, surf=self.surfaces())
 
     def fit_batch(self, layers, hits, xyz, cov, p0, c0, material=None, outlier_chi2=None):
         """Kalman fit over a known assignment (Sec. 4); outlier_chi2 > 0 rejects hits above it."""
@@ -313,7 +317,7 @@ class Oracle:
         self.lib.orc_fit_batch(self.gp, int(mat), int(n), int(m), _p(la, C.c_int), _p(hi, C.c_int), _p(x), _p(cv),
                                _p(q0), _p(d0), C.c_double(cut), _p(p), _p(c), _p(chi2), _p(nupd, C.c_int),
                                _p(status, C.c_int), _p(near, C.c_int), _p(ctr, C.c_longlong))
-        return dict(p=p, c=c, chi2=chi2, nupd=nupd, status=status, near_cut=near, counters=ctr)
+        return dict(p=p, c=c, chi2=chi2, nupd=nupd, status=status, near_cut=near, counters=ctr, surf=self.surfaces())
 
     def bkfit_batch(self, layers, hits, xyz, cov, p_start, c_start, cov_scale, material=None, outlier_chi2=None):
         """Backward fit (Sec. 2.2) of tracks listed in forward order, from their state on the
@@ -334,7 +338,7 @@ class Oracle:
                                  _p(cv), _p(q0), _p(d0), C.c_double(cov_scale), C.c_double(cut), _p(p), _p(c),
                                  _p(chi2), _p(nupd, C.c_int), _p(status, C.c_int), _p(near, C.c_int),
                                  _p(ctr, C.c_longlong))
-        return dict(p=p, c=c, chi2=chi2, nupd=nupd, status=status, near_cut=near, counters=ctr)
+        return dict(p=p, c=c, chi2=chi2, nupd=nupd, status=status, near_cut=near, counters=ctr, surf=self.surfaces())
 
     def build_event(self, layer_off, xyz, cov, seed_hits, seed_layers, binned=True):
         """Combinatorial forward search for the seeds of one event (hits [layer_off[0], layer_off[-1]))."""

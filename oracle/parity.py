@@ -40,6 +40,68 @@ def cov_close(cg, co, rel=1e-3, floor=1e-5):
     return d <= rel * scale + 1e-30, d / (rel * scale + 1e-30)
 
 
+def surface_frames(po, surf, tol=1e-4):
+    """Per state (oracle parameters po, n x 6) the rotation T = diag(R, I3), R's rows the surface
+    normal n, e1 (the direction projected onto the surface) and e2 = n x e1, of the layer surface
+    the state lies on (surf = (kind, position) per layer: a cylinder |r - R| or a disk |z - z_d|
+    within tol cm); on = False where no layer surface is that close (a module plane)."""
+    kind, pos = (np.asarray(a) for a in surf)
+    x, y, z = po[:, 0], po[:, 1], po[:, 2]
+    r = np.hypot(x, y)
+    d = np.where(kind[None, :] == 0, np.abs(r[:, None] - pos[None, :]), np.abs(z[:, None] - pos[None, :]))
+    lay = np.argmin(d, axis=1)
+    on = d[np.arange(len(po)), lay] < tol
+    barrel = kind[lay] == 0
+    rs = np.where(r > 0, r, 1.0)
+    nrm = np.where(barrel[:, None], np.stack([x / rs, y / rs, np.zeros_like(x)], 1),
+                   np.array([0.0, 0.0, 1.0])[None, :])
+    st = np.sin(po[:, 5])
+    u = np.stack([st * np.cos(po[:, 4]), st * np.sin(po[:, 4]), np.cos(po[:, 5])], 1)
+    e1 = u - (u * nrm).sum(1, keepdims=True) * nrm
+    l1 = np.linalg.norm(e1, axis=1, keepdims=True)
+    on &= l1[:, 0] > 1e-6
+    e1 = e1 / np.where(l1 > 0, l1, 1.0)
+    e2 = np.cross(nrm, e1)
+    T = np.zeros((len(po), 6, 6))
+    T[:, 0, :3], T[:, 1, :3], T[:, 2, :3] = nrm, e1, e2
+    T[:, 3, 3] = T[:, 4, 4] = T[:, 5, 5] = 1.0
+    return T, on
+
+
+def _full(c21):
+    M = np.zeros(c21.shape[:-1] + (6, 6))
+    M[..., TRI[0], TRI[1]] = c21
+    M[..., TRI[1], TRI[0]] = c21
+    return M
+
+
+def cov_close_surface(cg, co, po, surf, rel=1e-3, normal_floor=1e-4):
+    """The covariance test in the frame of the surface each state lies on: coordinates (n, e1,
+    e2, k, phi, theta), n the surface normal.  |dC_ij| <= rel * sqrt(d_i d_j) with d_i = C_ii of
+    the oracle, unfloored for the five in-surface coordinates; only the normal variance, zero in
+    exact arithmetic for a state on its surface, is floored at normal_floor of the largest
+    in-surface position variance: FP32 storage of the global-frame matrix alone leaves a few
+    1e-9 of that variance in the normal entries (the rotation mixes entries of that size), so
+    the normal row is held to ~1e-7 of it.  States on no layer surface within 1e-4 cm (a module
+    plane) take the global-frame test."""
+    cg = np.asarray(cg, np.float64)
+    co = np.asarray(co, np.float64)
+    if len(co) == 0:
+        return np.zeros((0, 21), bool), np.zeros((0, 21))
+    T, on = surface_frames(np.asarray(po, np.float64), surf)
+    Mg = T @ _full(cg) @ T.transpose(0, 2, 1)
+    Mo = T @ _full(co) @ T.transpose(0, 2, 1)
+    dg = np.abs(np.diagonal(Mo, axis1=1, axis2=2)).copy()
+    dg[:, 0] = np.maximum(dg[:, 0], normal_floor * dg[:, 1:3].max(1))
+    scale = np.sqrt(dg[:, TRI[0]] * dg[:, TRI[1]])
+    d = np.abs(Mg[:, TRI[0], TRI[1]] - Mo[:, TRI[0], TRI[1]])
+    ok, ratio = d <= rel * scale + 1e-30, d / (rel * scale + 1e-30)
+    if (~on).any():
+        ok_g, ratio_g = cov_close(cg[~on], co[~on], rel)
+        ok[~on], ratio[~on] = ok_g, ratio_g
+    return ok, ratio
+
+
 def chi2_close(xg, xo, rel=1e-3):
     d = np.abs(np.asarray(xg, np.float64) - xo)
     tol = rel * np.maximum(1.0, np.abs(xo))
@@ -72,6 +134,7 @@ def oracle_build(orc: Oracle, batch, seed_index=None, binned=True):
                 res[k][rows] = v
     res["seed_index"] = idx
     res["max_plan"] = mp
+    res["surf"] = orc.surfaces()
     return res
 
 
@@ -105,6 +168,7 @@ def oracle_build_backward(orc: Oracle, batch, track_event, p_start, c_start, fir
                 res[k][rows] = v
     res["seed_index"] = idx
     res["max_plan"] = mp
+    res["surf"] = orc.surfaces()
     return res
 
 
@@ -130,7 +194,10 @@ def compare_build(gpu: dict, orc: dict):
     pg = np.asarray(gpu["params"])[idx]
     cg = np.asarray(gpu["cov"])[idx]
     p_ok, p_ratio = param_close(pg[cmp], orc["params"][cmp])
-    c_ok, c_ratio = cov_close(cg[cmp], orc["cov"][cmp])
+    if "surf" in orc:
+        c_ok, c_ratio = cov_close_surface(cg[cmp], orc["cov"][cmp], orc["params"][cmp], orc["surf"])
+    else:
+        c_ok, c_ratio = cov_close(cg[cmp], orc["cov"][cmp])
     x_ok, x_ratio = chi2_close(np.asarray(gpu["chi2"])[idx][cmp], orc["chi2"][cmp])
     same_int = (np.asarray(gpu["nfound"])[idx][cmp] == orc["nfound"][cmp]) & \
                (np.asarray(gpu["nholes"])[idx][cmp] == orc["nholes"][cmp])
@@ -153,7 +220,10 @@ def compare_fit(gpu: dict, orc: dict, mask=None):
     st_ok = np.asarray(gpu["status"]) == orc["status"]
     m = (orc["status"] == 0) & st_ok if mask is None else mask & (orc["status"] == 0) & st_ok
     p_ok, p_ratio = param_close(np.asarray(gpu["p"])[m], orc["p"][m])
-    c_ok, c_ratio = cov_close(np.asarray(gpu["c"])[m], orc["c"][m])
+    if "surf" in orc:
+        c_ok, c_ratio = cov_close_surface(np.asarray(gpu["c"])[m], orc["c"][m], orc["p"][m], orc["surf"])
+    else:
+        c_ok, c_ratio = cov_close(np.asarray(gpu["c"])[m], orc["c"][m])
     x_ok, x_ratio = chi2_close(np.asarray(gpu["chi2"])[m], orc["chi2"][m])
     return dict(n=int(m.sum()), status_bad=int((~st_ok).sum()), param_bad=int((~p_ok).any(1).sum()),
                 cov_bad=int((~c_ok).any(1).sum()), chi2_bad=int((~x_ok).sum()),

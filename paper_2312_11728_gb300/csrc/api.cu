@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -64,6 +65,11 @@ struct mkgb_ctx {
     // side stream and events of mkgb_run's fit
     cudaStream_t fit_st = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_fit = nullptr;
+    // mkgb_run_host: host-to-device copy stream, per-chunk and per-input events, device copies
+    static constexpr int kHostChunks = 8;
+    cudaStream_t cp_in = nullptr;
+    cudaEvent_t ev_chunk[kHostChunks] = {}, ev_seedin = nullptr, ev_fitin = nullptr, ev_start = nullptr;
+    DevBuf host_run;
     int n_sms = 0;
     std::string err;
     bool has_geom = false, has_params = false, has_hits = false, has_seeds = false, seeds_fp64 = false;
@@ -86,7 +92,7 @@ struct mkgb_ctx {
     bool mod_hits = false;
     DevBuf stage[S_COUNT];
     // launch shapes of the search rounds and the graph cache replaying them
-    int find_shape = 0, select_shape = 0;
+    int find_shape = 1, select_shape = 0;   // two kernels per round: find 64 x 8, select 128 x 5
     bool use_graph = true;
     BuildGraph* graph = nullptr;
 };
@@ -158,6 +164,36 @@ cudaError_t stage_buf(mkgb_ctx* c, Stage s, size_t bytes, void** out) {
 cudaError_t copy_back(mkgb_ctx* c, void* dst, const void* dev, size_t bytes, bool on_device) {
     if (on_device || dst == nullptr || bytes == 0) return cudaSuccess;
     return cudaMemcpyAsync(dst, dev, bytes, cudaMemcpyDeviceToHost, c->stream);
+}
+
+// Device buffers of n seeds: the seed fit's states and infos, and the ordering's keys and scratch.
+int seed_buffers(mkgb_ctx* ctx, int n) {
+    const int64_t nkeys = (int64_t)ctx->n_events * kSeedEtaCells * kSeedPhiCells;
+    CK(ensure(ctx->seed_state, 4 * (size_t)kSeedStateStride * n));
+    if (ctx->params.precision == MKGB_FP64) CK(ensure(ctx->seed_state64, 8 * (size_t)kSeedStateStride * n));
+    CK(ensure(ctx->seed_info, 16 * (size_t)n));
+    CK(ensure(ctx->seed_key, 4 * (size_t)n));
+    CK(ensure(ctx->seed_order, 4 * (size_t)n));
+    CK(ensure(ctx->key_counts, 4 * (nkeys + 1)));
+    CK(ensure(ctx->key_cursor, 4 * (nkeys + 1)));
+    CK(ensure(ctx->seed_scan_tmp, 4 * scan_tmp_ints(nkeys + 1)));
+    return MKGB_OK;
+}
+
+// The (event, eta, phi) order of the n fitted seeds (a3): keys, their histogram, scan, scatter;
+// marks the seeds as loaded.
+int seed_order(mkgb_ctx* ctx, cudaStream_t st, int n) {
+    const int64_t nkeys = (int64_t)ctx->n_events * kSeedEtaCells * kSeedPhiCells;
+    CK(cudaMemsetAsync(ctx->key_counts.p, 0, 4 * (nkeys + 1), st));
+    CK(launch_seed_keys(st, n, (const float*)ctx->seed_state.p, (const int4*)ctx->seed_info.p, (int*)ctx->seed_key.p,
+                        (int*)ctx->key_counts.p));
+    CK(exclusive_scan(st, (const int*)ctx->key_counts.p, (int*)ctx->key_counts.p, nkeys, (int*)ctx->seed_scan_tmp.p));
+    CK(cudaMemcpyAsync(ctx->key_cursor.p, ctx->key_counts.p, 4 * nkeys, cudaMemcpyDeviceToDevice, st));
+    CK(launch_seed_scatter(st, n, (const int*)ctx->seed_key.p, (int*)ctx->key_cursor.p, (int*)ctx->seed_order.p));
+    ctx->n_seeds = n;
+    ctx->has_seeds = true;
+    ctx->seeds_fp64 = ctx->params.precision == MKGB_FP64;
+    return MKGB_OK;
 }
 
 // The search of mkgb_build on the context's stream into device outputs d (seeds and binned hits
@@ -260,7 +296,16 @@ void mkgb_destroy(mkgb_ctx* ctx) {
         }
         if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
         if (ctx->ev_fit) cudaEventDestroy(ctx->ev_fit);
-        DevBuf* all[] = {&ctx->geom_d, &ctx->seg_off, &ctx->in_xyz, &ctx->in_cov, &ctx->pay, &ctx->ep_tmp,
+        if (ctx->cp_in) {
+            cudaStreamSynchronize(ctx->cp_in);
+            cudaStreamDestroy(ctx->cp_in);
+        }
+        for (cudaEvent_t e : ctx->ev_chunk)
+            if (e) cudaEventDestroy(e);
+        if (ctx->ev_seedin) cudaEventDestroy(ctx->ev_seedin);
+        if (ctx->ev_fitin) cudaEventDestroy(ctx->ev_fitin);
+        if (ctx->ev_start) cudaEventDestroy(ctx->ev_start);
+        DevBuf* all[] = {&ctx->host_run, &ctx->geom_d, &ctx->seg_off, &ctx->in_xyz, &ctx->in_cov, &ctx->pay, &ctx->ep_tmp,
                          &ctx->bin_of_hit, &ctx->hit_seg, &ctx->bins, &ctx->hb_ep, &ctx->hb_pay, &ctx->cursor,
                          &ctx->scan_tmp, &ctx->seed_hits, &ctx->seed_state, &ctx->seed_state64, &ctx->seed_info, &ctx->seed_key,
                          &ctx->key_counts, &ctx->key_cursor, &ctx->seed_order, &ctx->seed_scan_tmp,
@@ -419,8 +464,18 @@ int mkgb_set_params(mkgb_ctx* ctx, const mkgb_params* p) {
 
 namespace {
 
+// Hits arriving in chunks of whole events: the preparation of chunk k, hits [hit_off[k],
+// hit_off[k + 1]), waits for ready[k] (recorded after the chunk's copy).
+struct HitChunks {
+    int n = 0;
+    const int64_t* hit_off = nullptr;
+    const cudaEvent_t* ready = nullptr;
+    // enqueued on the context's stream after chunk k's preparation (nullptr: nothing)
+    std::function<int(int k)> after;
+};
+
 int load_hits_impl(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz, const float* cov6,
-                   const int32_t* hit_module, int on_device) {
+                   const int32_t* hit_module, int on_device, const HitChunks* chunks = nullptr) {
     if (!ctx->has_geom) return fail(ctx, MKGB_ESTATE, "load_hits before load_geometry");
     if (n_events < 1 || !seg_off) return fail(ctx, MKGB_EINVAL, "need n_events >= 1 and seg_off");
     const int L = ctx->n_layers;
@@ -481,9 +536,23 @@ int load_hits_impl(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const fl
         dm = (const int*)ctx->in_mod.p;
     }
     CK(cudaMemsetAsync(ctx->bins.p, 0, 4 * (nbins + 1), st));
-    CK(launch_hit_prep(st, (const DevGeom*)ctx->geom_d.p, L, (const int64_t*)ctx->seg_off.p, (int)nseg, n, dx, dc,
-                       n > 0 ? dm : nullptr, ctx->geom_h.bins_per_event, (float4*)ctx->pay.p, (float2*)ctx->ep_tmp.p,
-                       (int*)ctx->bin_of_hit.p, (int*)ctx->hit_seg.p, (int*)ctx->bins.p));
+    if (chunks && chunks->n > 0) {
+        for (int k = 0; k < chunks->n; ++k) {
+            CK(cudaStreamWaitEvent(st, chunks->ready[k], 0));
+            CK(launch_hit_prep(st, (const DevGeom*)ctx->geom_d.p, L, (const int64_t*)ctx->seg_off.p, (int)nseg, n, dx,
+                               dc, n > 0 ? dm : nullptr, ctx->geom_h.bins_per_event, (float4*)ctx->pay.p,
+                               (float2*)ctx->ep_tmp.p, (int*)ctx->bin_of_hit.p, (int*)ctx->hit_seg.p,
+                               (int*)ctx->bins.p, chunks->hit_off[k], chunks->hit_off[k + 1]));
+            if (chunks->after) {
+                const int rc = chunks->after(k);
+                if (rc != MKGB_OK) return rc;
+            }
+        }
+    } else {
+        CK(launch_hit_prep(st, (const DevGeom*)ctx->geom_d.p, L, (const int64_t*)ctx->seg_off.p, (int)nseg, n, dx, dc,
+                           n > 0 ? dm : nullptr, ctx->geom_h.bins_per_event, (float4*)ctx->pay.p,
+                           (float2*)ctx->ep_tmp.p, (int*)ctx->bin_of_hit.p, (int*)ctx->hit_seg.p, (int*)ctx->bins.p));
+    }
     ctx->has_hits = false;
     if (hit_module && n > 0) {   // every module id must fit its hit's layer (synchronises)
         CK(ensure(ctx->mod_bad, 16));
@@ -542,37 +611,24 @@ int mkgb_seed(mkgb_ctx* ctx, int n_seeds, const int32_t* seed_hits, int on_devic
     DevGuard guard(ctx->device);
     cudaStream_t st = ctx->stream;
     const int n = n_seeds;
-    const int64_t nkeys = (int64_t)ctx->n_events * kSeedEtaCells * kSeedPhiCells;
     const void* sh = nullptr;
     CK(stage_in(ctx, S_A, seed_hits, 12 * (size_t)n, on_device, &sh));
-    CK(ensure(ctx->seed_state, 4 * (size_t)kSeedStateStride * n));
-    const bool fp64 = ctx->params.precision == MKGB_FP64;
-    if (fp64) CK(ensure(ctx->seed_state64, 8 * (size_t)kSeedStateStride * n));
-    CK(ensure(ctx->seed_info, 16 * (size_t)n));
-    CK(ensure(ctx->seed_key, 4 * (size_t)n));
-    CK(ensure(ctx->seed_order, 4 * (size_t)n));
-    CK(ensure(ctx->key_counts, 4 * (nkeys + 1)));
-    CK(ensure(ctx->key_cursor, 4 * (nkeys + 1)));
-    CK(ensure(ctx->seed_scan_tmp, 4 * scan_tmp_ints(nkeys + 1)));
+    int rc = seed_buffers(ctx, n);
+    if (rc != MKGB_OK) return rc;
     void *s6 = nullptr, *c21 = nullptr, *i3 = nullptr;
     CK(stage_out(ctx, S_B, state_out, 24 * (size_t)n, on_device, &s6));
     CK(stage_out(ctx, S_C, cov_out, 84 * (size_t)n, on_device, &c21));
     CK(stage_out(ctx, S_D, info_out, 12 * (size_t)n, on_device, &i3));
-    CK(cudaMemsetAsync(ctx->key_counts.p, 0, 4 * (nkeys + 1), st));
-    CK(launch_seed(st, (const DevGeom*)ctx->geom_d.p, ctx->params, hit_store(ctx), n, (const int*)sh,
-                   (float*)ctx->seed_state.p, fp64 ? (double*)ctx->seed_state64.p : nullptr,
-                   (int4*)ctx->seed_info.p, (int*)ctx->seed_key.p,
-                   (int*)ctx->key_counts.p, (float*)s6, (float*)c21, (int*)i3));
-    CK(exclusive_scan(st, (const int*)ctx->key_counts.p, (int*)ctx->key_counts.p, nkeys, (int*)ctx->seed_scan_tmp.p));
-    CK(cudaMemcpyAsync(ctx->key_cursor.p, ctx->key_counts.p, 4 * nkeys, cudaMemcpyDeviceToDevice, st));
-    CK(launch_seed_scatter(st, n, (const int*)ctx->seed_key.p, (int*)ctx->key_cursor.p, (int*)ctx->seed_order.p));
+    const bool fp64 = ctx->params.precision == MKGB_FP64;
+    CK(launch_seed_fit(st, (const DevGeom*)ctx->geom_d.p, ctx->params, hit_store(ctx), n, (const int*)sh,
+                       (float*)ctx->seed_state.p, fp64 ? (double*)ctx->seed_state64.p : nullptr,
+                       (int4*)ctx->seed_info.p, (float*)s6, (float*)c21, (int*)i3, SeedRange()));
+    rc = seed_order(ctx, st, n);
+    if (rc != MKGB_OK) return rc;
     CK(copy_back(ctx, state_out, s6, 24 * (size_t)n, on_device));
     CK(copy_back(ctx, cov_out, c21, 84 * (size_t)n, on_device));
     CK(copy_back(ctx, info_out, i3, 12 * (size_t)n, on_device));
     if (!on_device) CK(cudaStreamSynchronize(st));
-    ctx->n_seeds = n;
-    ctx->has_seeds = true;
-    ctx->seeds_fp64 = fp64;
     return MKGB_OK;
 }
 
@@ -675,7 +731,7 @@ int mkgb_build_backward(mkgb_ctx* ctx, int n, const int32_t* track_event, const 
     const BuildWork w = carve_build_work(ctx->build_work.p, n, ctx->max_plan_len, MKGB_FP32, ctx->mod_hits);
     CK(cudaMemsetAsync(ctx->counters_build.p, 0, 8 * kNumCounters, st));
     CK(launch_build(st, (const DevGeom*)ctx->geom_bwd_d.p, ctx->max_plan_len, ctx->params, hit_store(ctx), S, d, w,
-                    (unsigned long long*)ctx->counters_build.p, ctx->n_sms, 0, 0, nullptr, true));
+                    (unsigned long long*)ctx->counters_build.p, ctx->n_sms, ctx->find_shape >= 3 ? 3 : 0, 0, nullptr, true));
     CK(copy_back(ctx, out->params, d.params, 24 * N, on_device));
     CK(copy_back(ctx, out->cov, d.cov, 84 * N, on_device));
     CK(copy_back(ctx, out->chi2, d.chi2, 4 * N, on_device));
@@ -951,9 +1007,186 @@ int run_impl(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* x
     return rc;
 }
 
+// mkgb_run with host arrays.  The inputs go to the device on a copy stream: the hits in up to
+// kHostChunks chunks of whole events, each prepared as soon as it has arrived, then the seeds and
+// the fit's inputs, which arrive while the hits are prepared and the seeds fitted; the fit runs
+// on its own stream and its outputs go back while the search runs; the search's outputs go back
+// at the end.  Every copy is one cudaMemcpyAsync; with page-locked host arrays they overlap the
+// kernels.
+int run_host_impl(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz, const float* cov6,
+                  int n_seeds, const int32_t* seed_hits, const mkgb_tracks* out, int n_fit, int max_steps,
+                  const int32_t* layers, const int32_t* hits, const float* p0, const float* c0, float* p_out,
+                  float* c_out, float* chi2_out, int32_t* status_out) {
+    if (!ctx->has_geom) return fail(ctx, MKGB_ESTATE, "run before load_geometry");
+    if (n_events < 1 || !seg_off) return fail(ctx, MKGB_EINVAL, "need n_events >= 1 and seg_off");
+    if (!out) return fail(ctx, MKGB_EINVAL, "null track outputs");
+    if (n_seeds < 0 || n_fit < 0 || max_steps < 0) return fail(ctx, MKGB_EINVAL, "negative size");
+    if (n_seeds > 0 && !seed_hits) return fail(ctx, MKGB_EINVAL, "null seed hits");
+    if (n_fit > 0 && (!layers || !hits || !p0 || !c0 || !p_out || !c_out || !chi2_out))
+        return fail(ctx, MKGB_EINVAL, "null fit array");
+    const int L = ctx->n_layers;
+    const int64_t nseg = (int64_t)n_events * L;
+    if (seg_off[0] != 0) return fail(ctx, MKGB_EINVAL, "seg_off[0] must be 0");
+    for (int64_t q = 0; q < nseg; ++q)
+        if (seg_off[q + 1] < seg_off[q]) return fail(ctx, MKGB_EINVAL, "seg_off decreases at %lld", (long long)q);
+    const int64_t n = seg_off[nseg];
+    if (n > ((int64_t)1 << 28) - 8) return fail(ctx, MKGB_EINVAL, "too many hits (%lld)", (long long)n);
+    if (n > 0 && (!xyz || !cov6)) return fail(ctx, MKGB_EINVAL, "null hit arrays");
+    DevGuard guard(ctx->device);
+    const cudaStream_t main_st = ctx->stream;
+    if (!ctx->fit_st) {
+        CK(cudaStreamCreateWithFlags(&ctx->fit_st, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_fit, cudaEventDisableTiming));
+    }
+    if (!ctx->cp_in) {
+        CK(cudaStreamCreateWithFlags(&ctx->cp_in, cudaStreamNonBlocking));
+        for (int k = 0; k < mkgb_ctx::kHostChunks; ++k)
+            CK(cudaEventCreateWithFlags(&ctx->ev_chunk[k], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_seedin, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_fitin, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_start, cudaEventDisableTiming));
+    }
+    // device copies of the inputs and outputs, carved from one buffer (256-byte aligned pieces)
+    const size_t NS = (size_t)n_seeds, NF = (size_t)n_fit, MS = (size_t)max_steps, MP = (size_t)out->max_plan;
+    const bool ovl = out->ovl_hits != nullptr;
+    const size_t sizes[] = {12 * (size_t)n, 24 * (size_t)n, 12 * NS, 4 * NF * MS, 4 * NF * MS, 24 * NF, 84 * NF,
+                            24 * NF, 84 * NF, 4 * NF, 4 * NF, 24 * NS, 84 * NS, 4 * NS, 4 * NS, 4 * NS, 4 * NS,
+                            4 * NS * MP, ovl ? 4 * NS * MP : 0};
+    constexpr int kParts = sizeof(sizes) / sizeof(sizes[0]);
+    size_t offs[kParts], total = 0;
+    for (int q = 0; q < kParts; ++q) {
+        offs[q] = total;
+        total += (sizes[q] + 255) & ~(size_t)255;
+    }
+    CK(ensure(ctx->host_run, total > 0 ? total : 256));
+    char* base = static_cast<char*>(ctx->host_run.p);
+    auto part = [&](int q) { return static_cast<void*>(base + offs[q]); };
+    float *d_xyz = (float*)part(0), *d_cov = (float*)part(1);
+    int32_t* d_seeds = (int32_t*)part(2);
+    int32_t *d_layers = (int32_t*)part(3), *d_hits = (int32_t*)part(4);
+    float *d_p0 = (float*)part(5), *d_c0 = (float*)part(6);
+    float *d_po = (float*)part(7), *d_co = (float*)part(8), *d_x2 = (float*)part(9);
+    int32_t* d_st = (int32_t*)part(10);
+    mkgb_tracks dout;
+    dout.params = (float*)part(11); dout.cov = (float*)part(12); dout.chi2 = (float*)part(13);
+    dout.score = (float*)part(14); dout.nfound = (int32_t*)part(15); dout.nholes = (int32_t*)part(16);
+    dout.hits = (int32_t*)part(17); dout.max_plan = out->max_plan;
+    dout.ovl_hits = ovl ? (int32_t*)part(18) : nullptr;
+
+    // the copies start once the context's stream has passed everything enqueued before this call
+    CK(cudaEventRecord(ctx->ev_start, main_st));
+    CK(cudaStreamWaitEvent(ctx->cp_in, ctx->ev_start, 0));
+    const int K = n_events < mkgb_ctx::kHostChunks ? n_events : mkgb_ctx::kHostChunks;
+    int64_t hoff[mkgb_ctx::kHostChunks + 1];
+    for (int k = 0; k <= K; ++k) hoff[k] = seg_off[(int64_t)((int64_t)n_events * k / K) * L];
+    // the seeds first (each chunk's seeds are fitted as soon as its hits are prepared), then the
+    // hits chunk by chunk, then the fit's inputs
+    if (NS > 0) CK(cudaMemcpyAsync(d_seeds, seed_hits, 12 * NS, cudaMemcpyHostToDevice, ctx->cp_in));
+    CK(cudaEventRecord(ctx->ev_seedin, ctx->cp_in));
+    for (int k = 0; k < K; ++k) {
+        const int64_t h0 = hoff[k], nh = hoff[k + 1] - hoff[k];
+        if (nh > 0) {
+            CK(cudaMemcpyAsync(d_xyz + 3 * h0, xyz + 3 * h0, 12 * nh, cudaMemcpyHostToDevice, ctx->cp_in));
+            CK(cudaMemcpyAsync(d_cov + 6 * h0, cov6 + 6 * h0, 24 * nh, cudaMemcpyHostToDevice, ctx->cp_in));
+        }
+        CK(cudaEventRecord(ctx->ev_chunk[k], ctx->cp_in));
+    }
+    if (NF > 0) {
+        if (MS > 0) {
+            CK(cudaMemcpyAsync(d_layers, layers, 4 * NF * MS, cudaMemcpyHostToDevice, ctx->cp_in));
+            CK(cudaMemcpyAsync(d_hits, hits, 4 * NF * MS, cudaMemcpyHostToDevice, ctx->cp_in));
+        }
+        CK(cudaMemcpyAsync(d_p0, p0, 24 * NF, cudaMemcpyHostToDevice, ctx->cp_in));
+        CK(cudaMemcpyAsync(d_c0, c0, 84 * NF, cudaMemcpyHostToDevice, ctx->cp_in));
+    }
+    CK(cudaEventRecord(ctx->ev_fitin, ctx->cp_in));
+
+    if (!ctx->has_params) return fail(ctx, MKGB_ESTATE, "run before set_params");
+    ctx->n_events = n_events;   // sizes the seed ordering's keys
+    int rc = seed_buffers(ctx, n_seeds);
+    if (rc != MKGB_OK) return rc;
+    const bool fp64 = ctx->params.precision == MKGB_FP64;
+    SeedRange range;
+    range.n_chunks = K;
+    for (int k = 0; k <= K; ++k) range.off[k] = (int)hoff[k];
+    auto seed_launch = [&](int which) -> int {
+        HitStore H;
+        memset(&H, 0, sizeof(H));
+        H.seg_off = (const int64_t*)ctx->seg_off.p;
+        H.n_events = n_events;
+        H.n_layers = L;
+        H.n_hits = n;
+        H.pay = (const float4*)ctx->pay.p;
+        H.hit_seg = (const int*)ctx->hit_seg.p;
+        range.which = which;
+        CK(launch_seed_fit(main_st, (const DevGeom*)ctx->geom_d.p, ctx->params, H, n_seeds, d_seeds,
+                           (float*)ctx->seed_state.p, fp64 ? (double*)ctx->seed_state64.p : nullptr,
+                           (int4*)ctx->seed_info.p, nullptr, nullptr, nullptr, range));
+        return MKGB_OK;
+    };
+    CK(cudaStreamWaitEvent(main_st, ctx->ev_seedin, 0));
+    HitChunks hc;
+    hc.n = K;
+    hc.hit_off = hoff;
+    hc.ready = ctx->ev_chunk;
+    hc.after = seed_launch;
+    rc = load_hits_impl(ctx, n_events, seg_off, d_xyz, d_cov, nullptr, 1, &hc);
+    if (rc != MKGB_OK) {
+        cudaStreamSynchronize(ctx->cp_in);
+        return rc;
+    }
+    // the seeds not inside one chunk (hits of several events, invalid ids), then their order
+    rc = seed_launch(K);
+    if (rc == MKGB_OK) rc = seed_order(ctx, main_st, n_seeds);
+    if (rc != MKGB_OK) {
+        cudaStreamSynchronize(ctx->cp_in);
+        return rc;
+    }
+    // the fit: after the hit preparation and its inputs' arrival, on its own stream; its outputs
+    // go back on that stream while the search runs
+    CK(cudaEventRecord(ctx->ev_fork, main_st));
+    CK(cudaStreamWaitEvent(ctx->fit_st, ctx->ev_fork, 0));
+    CK(cudaStreamWaitEvent(ctx->fit_st, ctx->ev_fitin, 0));
+    ctx->stream = ctx->fit_st;
+    rc = mkgb_fit(ctx, n_fit, max_steps, d_layers, d_hits, d_p0, d_c0, d_po, d_co, d_x2, d_st, 1);
+    ctx->stream = main_st;
+    if (rc == MKGB_OK && NF > 0) {
+        CK(cudaMemcpyAsync(p_out, d_po, 24 * NF, cudaMemcpyDeviceToHost, ctx->fit_st));
+        CK(cudaMemcpyAsync(c_out, d_co, 84 * NF, cudaMemcpyDeviceToHost, ctx->fit_st));
+        CK(cudaMemcpyAsync(chi2_out, d_x2, 4 * NF, cudaMemcpyDeviceToHost, ctx->fit_st));
+        if (status_out) CK(cudaMemcpyAsync(status_out, d_st, 4 * NF, cudaMemcpyDeviceToHost, ctx->fit_st));
+    }
+    CK(cudaEventRecord(ctx->ev_fit, ctx->fit_st));
+    if (rc == MKGB_OK) rc = mkgb_build(ctx, &dout, 1);
+    if (rc == MKGB_OK && NS > 0) {
+        CK(cudaMemcpyAsync(out->params, dout.params, 24 * NS, cudaMemcpyDeviceToHost, main_st));
+        CK(cudaMemcpyAsync(out->cov, dout.cov, 84 * NS, cudaMemcpyDeviceToHost, main_st));
+        CK(cudaMemcpyAsync(out->chi2, dout.chi2, 4 * NS, cudaMemcpyDeviceToHost, main_st));
+        CK(cudaMemcpyAsync(out->score, dout.score, 4 * NS, cudaMemcpyDeviceToHost, main_st));
+        CK(cudaMemcpyAsync(out->nfound, dout.nfound, 4 * NS, cudaMemcpyDeviceToHost, main_st));
+        CK(cudaMemcpyAsync(out->nholes, dout.nholes, 4 * NS, cudaMemcpyDeviceToHost, main_st));
+        if (MP > 0) CK(cudaMemcpyAsync(out->hits, dout.hits, 4 * NS * MP, cudaMemcpyDeviceToHost, main_st));
+        if (ovl && MP > 0) CK(cudaMemcpyAsync(out->ovl_hits, dout.ovl_hits, 4 * NS * MP, cudaMemcpyDeviceToHost, main_st));
+    }
+    CK(cudaStreamWaitEvent(main_st, ctx->ev_fit, 0));
+    CK(cudaStreamWaitEvent(main_st, ctx->ev_fitin, 0));
+    CK(cudaStreamSynchronize(main_st));
+    return rc;
+}
+
 }  // namespace
 
 extern "C" {
+
+int mkgb_run_host(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz, const float* cov6,
+                  int n_seeds, const int32_t* seed_hits, const mkgb_tracks* out, int n_fit, int max_steps,
+                  const int32_t* layers, const int32_t* hits, const float* p0, const float* c0, float* p_out,
+                  float* c_out, float* chi2_out, int32_t* status_out) {
+    if (!ctx) return MKGB_EINVAL;
+    return run_host_impl(ctx, n_events, seg_off, xyz, cov6, n_seeds, seed_hits, out, n_fit, max_steps, layers, hits,
+                         p0, c0, p_out, c_out, chi2_out, status_out);
+}
 
 int mkgb_run(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz, const float* cov6, int n_seeds,
              const int32_t* seed_hits, const mkgb_tracks* out, int n_fit, int max_steps, const int32_t* layers,
@@ -976,8 +1209,8 @@ int mkgb_run_modular(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const 
 
 int mkgb_set_launch(mkgb_ctx* ctx, int find_shape, int select_shape, int use_graph) {
     if (!ctx) return MKGB_EINVAL;
-    if (find_shape < 0 || find_shape > 2 || select_shape < 0 || select_shape > 2)
-        return fail(ctx, MKGB_EINVAL, "launch shapes (%d, %d) outside 0..2", find_shape, select_shape);
+    if (find_shape < 0 || find_shape > 5 || select_shape < 0 || select_shape > 2)
+        return fail(ctx, MKGB_EINVAL, "launch shapes (%d, %d) outside 0..5, 0..2", find_shape, select_shape);
     ctx->find_shape = find_shape;
     ctx->select_shape = select_shape;
     ctx->use_graph = use_graph != 0;
@@ -1009,8 +1242,8 @@ int mkgb_autotune(mkgb_ctx* ctx, int reps, int* find_shape, int* select_shape, f
     }
     int best_f = ctx->find_shape, best_s = ctx->select_shape, rc = MKGB_OK;
     float best = -1.0f;
-    for (int f = 0; f < 3 && rc == MKGB_OK; ++f)
-        for (int s = 0; s < 3 && rc == MKGB_OK; ++s) {
+    for (int f = 0; f < 6 && rc == MKGB_OK; ++f)
+        for (int s = 0; s < (f < 3 ? 3 : 1) && rc == MKGB_OK; ++s) {   // fused shapes have no select kernel
             rc = enqueue_build(ctx, d, f, s);   // warm-up (and the graph's recording)
             if (rc == MKGB_OK) cudaEventRecord(e0, st);
             for (int r = 0; r < reps && rc == MKGB_OK; ++r) rc = enqueue_build(ctx, d, f, s);

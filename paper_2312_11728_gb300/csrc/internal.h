@@ -58,22 +58,27 @@ struct BuildWork {
     int* live[2];     // work list of live candidate slots per round
     int* seeds[2];    // work list of seeds with a live candidate per round
     int4* sinfo;      // per ordered seed: (plan position of its first step, first step, steps, event)
-    int* fin;         // per ordered seed: buffer holding its final slots, -1 none
+    int* fin;         // per ordered seed: buffer holding its final slots | (rounds searched << 1), -1 none
     int* trail;       // per ordered seed: longest plan x 8 ints ((code + 4) << 3 | parent slot)
     int* otrail;      // the same layout: overlap hit id of the step (-1 none); nullptr without modules
     int* rescue;      // kept children of the round whose update is redone in FP64
     int* counts;      // [live0, live1, seeds0, seeds1, rescue]
+    // fused rounds: [tau] length of round tau's live list, [kRescueCountBase + tau] its FP64 redo list
+    int* rcounts;
 };
+constexpr int kRescueCountBase = MKGB_MAX_PLAN + 2;
+constexpr int kRoundCountInts = 2 * kRescueCountBase;
 
 // counters (64-bit): [0] steps, [1] chi2 evaluations, [2] updates, [3] hits tested, [4] Newton iterations
 constexpr int kNumCounters = 5;
 
 // ---- k_hits.cu
-// hit_mod (may be nullptr: every hit on its layer's own surface) goes into the payload.
+// hit_mod (may be nullptr: every hit on its layer's own surface) goes into the payload.  Prepares
+// hits [h0, h1) (h1 < 0: up to n_hits), so that a batch arriving in chunks is prepared per chunk.
 cudaError_t launch_hit_prep(cudaStream_t st, const DevGeom* g, int n_layers, const int64_t* seg_off, int n_seg,
                             int64_t n_hits, const float* xyz, const float* cov, const int* hit_mod,
                             int bins_per_event, float4* pay, float2* ep_tmp, int* bin_of_hit, int* hit_seg,
-                            int* counts);
+                            int* counts, int64_t h0 = 0, int64_t h1 = -1);
 // Counts into *bad the hits whose module does not fit their layer (a module hit on a layer without
 // modules or on another layer's module, a hit without module on a modular layer, an index out of range).
 cudaError_t launch_check_modules(cudaStream_t st, const DevGeom* g, int n_layers, int64_t n_hits,
@@ -86,9 +91,24 @@ cudaError_t exclusive_scan(cudaStream_t st, const int* in, int* out, int64_t n, 
 cudaError_t launch_seed_scatter(cudaStream_t st, int n, const int* key_of, int* cursor, int* order);
 
 // ---- k_seed.cu
+// The seeds one launch of the seed fit takes: which < 0 all of them; with the hits arriving in
+// n_chunks chunks of whole events (hit ids [off[k], off[k + 1])), which = k the seeds whose three
+// hits lie in chunk k, which = n_chunks the rest (hits in several chunks or invalid ids), fitted
+// once every chunk has been prepared.
+constexpr int kMaxSeedChunks = 8;
+struct SeedRange {
+    int which = -1;
+    int n_chunks = 0;
+    int off[kMaxSeedChunks + 1] = {};
+};
 cudaError_t launch_seed(cudaStream_t st, const DevGeom* g, DevParams P, HitStore H, int n, const int* seed_hits,
                         float* state, double* state64, int4* info, int* key_of, int* key_counts, float* state6,
                         float* cov21, int* info3);
+cudaError_t launch_seed_fit(cudaStream_t st, const DevGeom* g, DevParams P, HitStore H, int n, const int* seed_hits,
+                            float* state, double* state64, int4* info, float* state6, float* cov21, int* info3,
+                            const SeedRange& range);
+cudaError_t launch_seed_keys(cudaStream_t st, int n, const float* state, const int4* info, int* key_of,
+                             int* key_counts);
 
 // ---- k_build.cu
 // with_ovl: room for the overlap hits of modular layers (the otrail array)

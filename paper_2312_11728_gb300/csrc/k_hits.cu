@@ -26,15 +26,16 @@ __device__ __forceinline__ int upper_seg(const int64_t* __restrict__ off, int n_
     return lo;
 }
 
+// Hits [h0, h1) of the n_seg segments (a chunk of whole events, or all of them).
 __global__ void __launch_bounds__(kThreads) k_hit_prep(const DevGeom* __restrict__ g, int n_layers,
                                                        const int64_t* __restrict__ seg_off, int n_seg,
-                                                       int64_t n_hits, const float* __restrict__ xyz,
+                                                       int64_t h0, int64_t h1, const float* __restrict__ xyz,
                                                        const float* __restrict__ cov,
                                                        const int* __restrict__ hit_mod, int bins_per_event,
                                                        float4* __restrict__ pay, float2* __restrict__ ep_tmp,
                                                        int* __restrict__ bin_of_hit, int* __restrict__ hit_seg,
                                                        int* __restrict__ counts) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_hits;
+    for (int64_t i = h0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < h1;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int seg = upper_seg(seg_off, n_seg, i);
         const int e = seg / n_layers, l = seg - e * n_layers;
@@ -182,10 +183,11 @@ cudaError_t launch_check_modules(cudaStream_t st, const DevGeom* g, int n_layers
 cudaError_t launch_hit_prep(cudaStream_t st, const DevGeom* g, int n_layers, const int64_t* seg_off, int n_seg,
                             int64_t n_hits, const float* xyz, const float* cov, const int* hit_mod,
                             int bins_per_event, float4* pay, float2* ep_tmp, int* bin_of_hit, int* hit_seg,
-                            int* counts) {
-    if (n_hits == 0) return cudaSuccess;
-    k_hit_prep<<<grid_for(n_hits), kThreads, 0, st>>>(g, n_layers, seg_off, n_seg, n_hits, xyz, cov, hit_mod,
-                                                      bins_per_event, pay, ep_tmp, bin_of_hit, hit_seg, counts);
+                            int* counts, int64_t h0, int64_t h1) {
+    if (h1 < 0) h1 = n_hits;
+    if (h1 <= h0) return cudaSuccess;
+    k_hit_prep<<<grid_for(h1 - h0), kThreads, 0, st>>>(g, n_layers, seg_off, n_seg, h0, h1, xyz, cov, hit_mod,
+                                                       bins_per_event, pay, ep_tmp, bin_of_hit, hit_seg, counts);
     return cudaGetLastError();
 }
 

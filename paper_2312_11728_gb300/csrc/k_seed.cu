@@ -49,15 +49,28 @@ __device__ __forceinline__ void write_seed(const State& t, int i, int region, in
     }
 }
 
+// The chunk of a hit id among the range's chunk offsets (-1: outside them all).
+__device__ __forceinline__ int chunk_of(const SeedRange& r, int h) {
+    for (int k = 0; k < r.n_chunks; ++k)
+        if (h >= r.off[k] && h < r.off[k + 1]) return k;
+    return -1;
+}
+
 template <bool FAST>
 __global__ void __launch_bounds__(kThreads) k_seed(const DevGeom* __restrict__ gp, DevParams P, HitStore H, int n,
                                                    const int* __restrict__ seed_hits, float* __restrict__ state,
                                                    double* __restrict__ state64, int4* __restrict__ info,
-                                                   float* state6, float* cov21, int* info3) {
+                                                   float* state6, float* cov21, int* info3, SeedRange range) {
     __shared__ DevGeom g;
     load_geom(gp, g);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (range.which >= 0) {   // hits arriving in chunks: the seeds of one chunk, or the rest
+        const int c0 = chunk_of(range, seed_hits[3 * i]), c1 = chunk_of(range, seed_hits[3 * i + 1]),
+                  c2 = chunk_of(range, seed_hits[3 * i + 2]);
+        const bool in_one = c0 >= 0 && c0 == c1 && c1 == c2;
+        if (range.which < range.n_chunks ? !(in_one && c0 == range.which) : in_one) return;
+    }
     StateT<double> td;
     int lay[3], event, region, start;
     const bool ok = seed_fit<double, FAST>(g, P, H, seed_hits, i, td, lay, event);
@@ -94,18 +107,35 @@ __global__ void __launch_bounds__(kThreads) k_seed_key(int n, const float* __res
 
 }  // namespace
 
-cudaError_t launch_seed(cudaStream_t st, const DevGeom* g, DevParams P, HitStore H, int n, const int* seed_hits,
-                        float* state, double* state64, int4* info, int* key_of, int* key_counts, float* state6,
-                        float* cov21, int* info3) {
+cudaError_t launch_seed_fit(cudaStream_t st, const DevGeom* g, DevParams P, HitStore H, int n, const int* seed_hits,
+                            float* state, double* state64, int4* info, float* state6, float* cov21, int* info3,
+                            const SeedRange& range) {
     if (n == 0) return cudaSuccess;
     const int blocks = (n + kThreads - 1) / kThreads;
     // the FP32 path's seed fits take the FP32-assisted FP64 steps; the plain all-FP64 path does not
     if (P.precision == MKGB_FP64)
-        k_seed<false><<<blocks, kThreads, 0, st>>>(g, P, H, n, seed_hits, state, state64, info, state6, cov21, info3);
+        k_seed<false><<<blocks, kThreads, 0, st>>>(g, P, H, n, seed_hits, state, state64, info, state6, cov21, info3,
+                                                   range);
     else
-        k_seed<true><<<blocks, kThreads, 0, st>>>(g, P, H, n, seed_hits, state, state64, info, state6, cov21, info3);
-    k_seed_key<<<blocks, kThreads, 0, st>>>(n, state, info, key_of, key_counts);
+        k_seed<true><<<blocks, kThreads, 0, st>>>(g, P, H, n, seed_hits, state, state64, info, state6, cov21, info3,
+                                                  range);
     return cudaGetLastError();
+}
+
+cudaError_t launch_seed_keys(cudaStream_t st, int n, const float* state, const int4* info, int* key_of,
+                             int* key_counts) {
+    if (n == 0) return cudaSuccess;
+    k_seed_key<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(n, state, info, key_of, key_counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed(cudaStream_t st, const DevGeom* g, DevParams P, HitStore H, int n, const int* seed_hits,
+                        float* state, double* state64, int4* info, int* key_of, int* key_counts, float* state6,
+                        float* cov21, int* info3) {
+    const cudaError_t e = launch_seed_fit(st, g, P, H, n, seed_hits, state, state64, info, state6, cov21, info3,
+                                          SeedRange());
+    if (e != cudaSuccess) return e;
+    return launch_seed_keys(st, n, state, info, key_of, key_counts);
 }
 
 }  // namespace mk

@@ -46,7 +46,8 @@ class Tracks(C.Structure):
 EXPORTS = ["mkgb_create", "mkgb_destroy", "mkgb_last_error", "mkgb_version", "mkgb_load_geometry",
            "mkgb_set_params", "mkgb_load_hits", "mkgb_load_modules", "mkgb_load_hits_modular", "mkgb_seed", "mkgb_build", "mkgb_build_backward", "mkgb_fit",
            "mkgb_fit_backward",
-           "mkgb_fit_static", "mkgb_fit_grad", "mkgb_run", "mkgb_run_modular", "mkgb_set_launch", "mkgb_autotune",
+           "mkgb_fit_static", "mkgb_fit_grad", "mkgb_run", "mkgb_run_host", "mkgb_run_modular", "mkgb_set_launch",
+           "mkgb_autotune",
            "mkgb_probe_peak", "mkgb_clean_seeds", "mkgb_remove_duplicates", "mkgb_propagate", "mkgb_update",
            "mkgb_counters"]
 
@@ -85,6 +86,8 @@ def load_library(path: str = LIB_PATH):
     lib.mkgb_fit_grad.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32]
     lib.mkgb_run.argtypes = [vp, i32, vp, vp, vp, i32, vp, C.POINTER(Tracks), i32, i32, vp, vp, vp, vp, vp, vp, vp,
                              vp]
+    lib.mkgb_run_host.argtypes = [vp, i32, vp, vp, vp, i32, vp, C.POINTER(Tracks), i32, i32, vp, vp, vp, vp, vp, vp,
+                                  vp, vp]
     lib.mkgb_set_launch.argtypes = [vp, i32, i32, i32]
     lib.mkgb_autotune.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(f32)]
     lib.mkgb_probe_peak.argtypes = [vp, i32, C.POINTER(C.c_double)]
@@ -299,6 +302,30 @@ class Context:
             self._check(self.lib.mkgb_run(self.h, int(n_events), so.ctypes.data, px, pc, int(seed_hits.shape[0]),
                                           ps, C.byref(t), int(n), int(m), pl, ph, pp, pq, po, pco, px2, pst),
                         "mkgb_run")
+        self.n_seeds = int(seed_hits.shape[0])
+        return out
+
+    def run_host(self, n_events, seg_off, xyz, cov, seed_hits, out: dict, layers, hits, p0, c0, p_out, c_out,
+                 chi2_out, status_out=None):
+        """mkgb_run_host: the one-call pass with every array in host memory (numpy arrays or CPU
+        tensors; page-locked ones let the library overlap its copies with the kernels)."""
+        so = np.ascontiguousarray(seg_off, np.int64)
+        f, i = np.float32, np.int32
+        ptrs = [_ptr(out[k], t, out=True) for k, t in (("params", f), ("cov", f), ("chi2", f), ("score", f),
+                                              ("nfound", i), ("nholes", i), ("hits", i))]
+        if "ovl" in out:
+            ptrs.append(_ptr(out["ovl"], i, out=True))
+        t = Tracks(*[p for p, _ in ptrs[:7]], int(out["hits"].shape[1]), ptrs[7][0] if len(ptrs) > 7 else None)
+        args = [_ptr(xyz, f), _ptr(cov, f), _ptr(seed_hits, i), _ptr(layers, i), _ptr(hits, i), _ptr(p0, f),
+                _ptr(c0, f), _ptr(p_out, f, True), _ptr(c_out, f, True), _ptr(chi2_out, f, True),
+                _ptr(status_out, i, True)]
+        if _same(*[d for _, d in args + ptrs]) != 0:
+            raise MkgbError("mkgb_run_host takes host arrays only")
+        (px, _), (pc, _), (ps, _), (pl, _), (ph, _), (pp, _), (pq, _), (po, _), (pco, _), (px2, _), (pst, _) = args
+        n, m = layers.shape
+        self._check(self.lib.mkgb_run_host(self.h, int(n_events), so.ctypes.data, px, pc, int(seed_hits.shape[0]),
+                                           ps, C.byref(t), int(n), int(m), pl, ph, pp, pq, po, pco, px2, pst),
+                    "mkgb_run_host")
         self.n_seeds = int(seed_hits.shape[0])
         return out
 

@@ -102,3 +102,49 @@ def test_backward_search_edge_cases(lib):
     ctx64.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov)
     with pytest.raises(mkgb.MkgbError):
         ctx64.build_backward(ev[:4], first[:4], p[:4], c[:4], mkgb.alloc_tracks(4, g.max_plan))
+
+
+def test_chained_fit_backward_fit_backward_search(lib):
+    """The chain forward fit -> backward fit -> backward search, run end to end on each side: the
+    GPU on its own outputs and the oracle on its own (no GPU value enters the oracle's side), so
+    the comparison bounds the drift accumulated over the three steps.  Tracks whose first three
+    layers are removed; both chains start from the same seed-like states on the fourth layer."""
+    g, batch = _workload("phase2")
+    params = S.default_params()
+    ctx = pipeline.make_context(g, params)
+    ctx.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov)
+    fi = pipeline.fit_inputs(batch)
+    keep = (fi.layers >= 0).sum(1) >= 6
+    fo = pipeline.outer_fit_inputs(fi, 3)
+    sel = np.nonzero(keep)[0]
+    L, H = np.ascontiguousarray(fo.layers[sel]), np.ascontiguousarray(fo.hits[sel])
+    p0, c0 = np.ascontiguousarray(fo.p0[sel]), np.ascontiguousarray(fo.c0[sel])
+    n = len(sel)
+    z = lambda *s, t=np.float32: np.zeros(s, t)
+    f = dict(p=z(n, 6), c=z(n, 21), chi2=z(n), status=z(n, t=np.int32))
+    ctx.fit(L, H, p0, c0, f["p"], f["c"], f["chi2"], f["status"])
+    b = dict(p=z(n, 6), c=z(n, 21), chi2=z(n), status=z(n, t=np.int32))
+    ctx.fit_backward(L, H, f["p"], f["c"], b["p"], b["c"], b["chi2"], b["status"], cov_scale=100.0)
+
+    orc = oracle.Oracle(g, params)
+    xyz, cov = batch.hit_xyz.astype(np.float64), batch.hit_cov.astype(np.float64)
+    rf = orc.fit_batch(L, H, xyz, cov, p0.astype(np.float64), c0.astype(np.float64))
+    rb = orc.bkfit_batch(L, H, xyz, cov, rf["p"], rf["c"], 100.0)
+    ok = (f["status"] == 0) & (b["status"] == 0) & (rf["status"] == 0) & (rb["status"] == 0)
+    assert ok.mean() > 0.95
+    # each intermediate step within the single-step tolerances
+    assert PR.compare_fit(f, rf, ok)["param_bad"] == 0
+    rep_b = PR.compare_fit(b, rb, ok)
+    assert rep_b["param_bad"] == 0 and rep_b["chi2_bad"] == 0, rep_b
+    ev = np.ascontiguousarray(fi.event[sel][ok].astype(np.int32))
+    first = np.ascontiguousarray(L[ok][:, 0])
+    out = ctx.build_backward(ev, first, np.ascontiguousarray(b["p"][ok]), np.ascontiguousarray(b["c"][ok]),
+                             mkgb.alloc_tracks(int(ok.sum()), g.max_plan))
+    o = PR.oracle_build_backward(orc, batch, ev, rb["p"][ok], rb["c"][ok], first)
+    rep = PR.compare_build(out, o)
+    m = int(ok.sum())
+    # drift over three chained steps: hit lists still agree outside the oracle's near ties for all
+    # but a few tracks, and the final states stay within the single-step tolerances
+    assert len(rep["hit_mismatch"]) <= max(2, 0.002 * m), rep
+    assert rep["param_bad"] <= max(2, 0.002 * m) and rep["chi2_bad"] <= max(2, 0.002 * m), rep
+    assert rep["worst_param"] < 3.0, rep

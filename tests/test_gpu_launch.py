@@ -1,6 +1,7 @@
 """Launch configuration of the search (library service; changes no arithmetic): the CUDA-graph
-replay of the search rounds, the three block shapes of each round kernel and the autotuner give
-the plain launches' results bit for bit, and a changed batch re-records the graph."""
+replay of the search rounds, the block shapes of the two-kernel rounds and of the fused round
+kernel, and the autotuner give the plain two-kernel launches' results bit for bit, and a changed
+batch re-records the graph."""
 import numpy as np
 import pytest
 
@@ -47,7 +48,7 @@ def test_graph_and_shapes_match_plain_launches(lib):
         ref = _search(plain, db)
         assert int(ref["nfound"].sum()) > 0
         ctx = pipeline.make_context(g, params, stream=side)
-        for f, s in [(0, 0), (1, 1), (2, 2), (1, 2), (2, 0)]:
+        for f, s in [(0, 0), (1, 1), (2, 2), (1, 2), (2, 0), (3, 0), (4, 0), (5, 0)]:
             ctx.set_launch(f, s, use_graph=True)
             for _ in range(2):   # record, then replay
                 assert _equal(_search(ctx, db), ref), (f, s)
@@ -102,10 +103,10 @@ def test_autotune_keeps_results(lib):
         ctx = pipeline.make_context(g, params, stream=side)
         ref = _search(ctx, db)
         f, s, ms = ctx.autotune(reps=2)
-        assert f in (0, 1, 2) and s in (0, 1, 2) and ms > 0.0
+        assert f in range(6) and s in (0, 1, 2) and ms > 0.0
         assert _equal(_search(ctx, db), ref)
         with pytest.raises(mkgb.MkgbError):
-            ctx.set_launch(3, 0)
+            ctx.set_launch(6, 0)
         with pytest.raises(mkgb.MkgbError):
             ctx.autotune(reps=0)
 

@@ -71,7 +71,7 @@ def test_step_propagation_matches_oracle(lib):
         assert cr[i] == rc, (i, cr[i], rc)
         if rc == 1:
             pok, _ = PR.param_close(po[i], pp)
-            cok, _ = PR.cov_close(co[i], cc)
+            cok, _ = PR.cov_close_surface(co[i][None], cc[None], pp[None], orc.surfaces())
             assert pok.all(), (i, po[i], pp)
             assert cok.all(), (i, co[i], cc)
             n_cmp += 1
@@ -137,14 +137,15 @@ def test_seed_states_match_oracle(lib, which, request):
                                  status_mismatch=np.nonzero(info[:, 2] != r["status"])[0],
                                  worst_param=float(PR.param_close(res["seed_state"][r["status"] == 0],
                                                                   r["p"][r["status"] == 0])[1].max()),
-                                 worst_cov=float(PR.cov_close(res["seed_cov"][r["status"] == 0],
-                                                              r["c"][r["status"] == 0])[1].max())))
+                                 worst_cov=float(PR.cov_close_surface(res["seed_cov"][r["status"] == 0],
+                                                                      r["c"][r["status"] == 0], r["p"][r["status"] == 0],
+                                                                      r["surf"])[1].max())))
     assert np.array_equal(info[:, 0], r["region"])
     assert np.array_equal(info[:, 1], r["start"])
     assert np.array_equal(info[:, 2], r["status"])
     ok = r["status"] == 0
     pok, prat = PR.param_close(res["seed_state"][ok], r["p"][ok])
-    cok, crat = PR.cov_close(res["seed_cov"][ok], r["c"][ok])
+    cok, crat = PR.cov_close_surface(res["seed_cov"][ok], r["c"][ok], r["p"][ok], r["surf"])
     assert pok.all(), prat.max()
     assert cok.all(), crat.max()
 
@@ -263,6 +264,54 @@ def test_one_call_run_matches_separate_calls(lib, phase2_small):
             assert torch.equal(ref.fit[k], db.fit[k]), k
 
 
+def _host_run(ctx, batch, fi, max_plan, pinned):
+    import torch
+    from paper_2312_11728_gb300 import mkgb as M
+    n, T = batch.seed_hits.shape[0], fi.layers.shape[0]
+    if pinned:
+        h = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        out = {k: torch.from_numpy(v).pin_memory() for k, v in M.alloc_tracks(n, max_plan).items()}
+        fo = [torch.zeros((T, 6)).pin_memory(), torch.zeros((T, 21)).pin_memory(), torch.zeros(T).pin_memory(),
+              torch.zeros(T, dtype=torch.int32).pin_memory()]
+    else:
+        h = lambda a: np.ascontiguousarray(a)
+        out = M.alloc_tracks(n, max_plan)
+        fo = [np.zeros((T, 6), np.float32), np.zeros((T, 21), np.float32), np.zeros(T, np.float32),
+              np.zeros(T, np.int32)]
+    ctx.run_host(batch.n_events, batch.hit_off, h(batch.hit_xyz), h(batch.hit_cov), h(batch.seed_hits), out,
+                 h(fi.layers), h(fi.hits), h(fi.p0), h(fi.c0), *fo)
+    cv = lambda a: a.numpy() if hasattr(a, "numpy") else a
+    return {k: cv(v) for k, v in out.items()}, [cv(a) for a in fo]
+
+
+@pytest.mark.parametrize("n_events", [1, 3, 11])
+def test_host_array_run_matches_device_run(lib, n_events):
+    """mkgb_run_host (host arrays; the hits copied in chunks of events and prepared per chunk, the
+    copies overlapping the kernels) gives mkgb_run's results bit for bit, with page-locked and
+    with pageable host arrays, twice in a row; 11 events make uneven chunks."""
+    import torch
+    g = S.geometry_phase2()
+    evs = [S.simulate_event(g, 300 + 97 * e, 5, e, pt_sampler=S.sample_pt_phase2, eta_max=3.0, noise_total=1500)
+           for e in range(n_events)]
+    batch = S.concat_events(evs, g.n_layers)
+    params = S.default_params()
+    fi = pipeline.fit_inputs(batch)
+    ref_ctx = _ctx(g, params)
+    ref = pipeline.DeviceBatch(batch, fi, g.max_plan, "cuda")
+    pipeline.run_step_fused(ref_ctx, ref)
+    torch.cuda.synchronize()
+    ctx = _ctx(g, params)
+    for pinned in (True, False, True):
+        out, fo = _host_run(ctx, batch, fi, g.max_plan, pinned)
+        for k in ref.out:
+            assert np.array_equal(ref.out[k].cpu().numpy(), out[k]), (k, pinned)
+        for k, a in zip(("p", "c", "chi2", "status"), fo):
+            assert np.array_equal(ref.fit[k].cpu().numpy(), a), (k, pinned)
+    with pytest.raises(mkgb.MkgbError):   # device tensors are refused
+        ctx.run_host(batch.n_events, batch.hit_off, ref.xyz, ref.cov, ref.seeds, ref.out, ref.fit["layers"],
+                     ref.fit["hits"], ref.fit["p0"], ref.fit["c0"], ref.fit["p"], ref.fit["c"], ref.fit["chi2"])
+
+
 # ------------------------------------------------------------------ edge cases
 
 def test_edge_cases_empty_single_and_ragged(lib):
@@ -344,6 +393,7 @@ def test_full_size_phase2_sampled_against_oracle(lib, phase2_full):
     gf = {k: db.fit[k].cpu().numpy()[tsample] for k in ("p", "c", "chi2", "status")}
     rep = _report("fit_full_size", PR.compare_fit(gf, r))
     assert rep["status_bad"] == 0 and rep["param_bad"] == 0 and rep["chi2_bad"] == 0, rep
+    assert rep["cov_bad"] == 0, rep
 
 
 # ------------------------------------------------------------------ uneven events, loopers at scale

@@ -51,3 +51,20 @@ def test_replica_throughput_single_process():
     from paper_2312_11728_gb300 import pipeline
     value, wall, total = pipeline.replica_throughput(0.5, 1000)
     assert (value, wall, total) == (2000.0, 0.5, 1000.0)
+
+
+def test_bench_spawns_its_own_ranks():
+    """`bench.py --gpus 2` without a launcher re-runs itself as two ranks (torch.distributed.run on
+    127.0.0.1); rank 0 alone prints the one JSON line, which reports both ranks.  The reference arm
+    (the FP64 oracle on the host cores) needs no GPU, so the ranks run here."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
+                        "--warmup", "0"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["steps"] == 1 and d["value"] > 0

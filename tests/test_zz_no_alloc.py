@@ -108,3 +108,53 @@ def test_limits_and_empty(setup):
     x0 = _device_fit_inputs(fi, 0, 0)
     _run(ctx.fit_static, x0, _outputs(0))
     torch.cuda.synchronize()
+
+
+def test_largest_batch_every_refit_slot(setup):
+    """Exactly 65536 tracks (the largest accepted batch) with a threshold low enough that a large
+    part of them goes through the refit list: the static call still equals mkgb_fit, and a second
+    call leaves the device's free memory unchanged (no allocation in the call)."""
+    import torch
+    g, batch, fi = setup
+    ctx = pipeline.make_context(g, dict(S.default_params(), kappa_fp64=1e3))
+    ctx.load_hits(batch.n_events, batch.hit_off, torch.from_numpy(batch.hit_xyz).cuda(),
+                  torch.from_numpy(batch.hit_cov).cuda())
+    reps = -(-MAX_TRACKS // fi.layers.shape[0])
+    tile = lambda a: np.ascontiguousarray(np.concatenate([a] * reps)[:MAX_TRACKS])
+    x = {k: torch.from_numpy(tile(v)).cuda() for k, v in
+         dict(layers=fi.layers, hits=fi.hits, p0=fi.p0, c0=fi.c0).items()}
+    ref, got = _outputs(MAX_TRACKS), _outputs(MAX_TRACKS)
+    _run(ctx.fit, x, ref)
+    _run(ctx.fit_static, x, got)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    _run(ctx.fit_static, x, got)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    a, b = _host(ref), _host(got)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    assert (b["status"] == 0).mean() > 0.95
+
+
+def test_module_hits_match_mkgb_fit():
+    """Module hits (taken on their module planes) go through the same static call."""
+    import torch
+    B.build()
+    mkgb.load_library()
+    g = S.geometry_phase2_modular_disks()
+    ev = S.simulate_event(g, 1500, 4, 0, pt_sampler=S.sample_pt_phase2, eta_max=2.5, noise_total=2000)
+    b = S.concat_events([ev], g.n_layers)
+    fi = pipeline.fit_inputs(b)
+    ctx = pipeline.make_context(g, S.default_params())
+    ctx.load_hits(b.n_events, b.hit_off, torch.from_numpy(b.hit_xyz).cuda(), torch.from_numpy(b.hit_cov).cuda(),
+                  hit_module=torch.from_numpy(b.hit_mod).cuda())
+    x = _device_fit_inputs(fi, 0, fi.layers.shape[0])
+    ref, got = _outputs(fi.layers.shape[0]), _outputs(fi.layers.shape[0])
+    _run(ctx.fit, x, ref)
+    for _ in range(2):
+        _run(ctx.fit_static, x, got)
+        a, c = _host(ref), _host(got)
+        for k in a:
+            assert np.array_equal(a[k], c[k]), k
+    assert (c["status"] == 0).mean() > 0.95
