@@ -153,6 +153,34 @@ def make_batch(seed, n_events=N_EVENTS):
     return g, S.concat_events(evs, g.n_layers), evs
 
 
+def _gen_uneven_event(args):
+    e, n, seed = args
+    from paper_2312_11728_gb300 import synth as S
+    g = S.geometry_phase2()
+    return S.simulate_event(g, int(n), seed, e, pt_sampler=S.sample_pt_phase2, eta_max=3.0,
+                            noise_total=int(2.5 * n))
+
+
+def _gen_looper_event(args):
+    e, seed = args
+    from paper_2312_11728_gb300 import synth as S
+    g = S.geometry_phase2()
+    return S.simulate_event(g, 20000, seed, e, pt_sampler=S.sample_pt_loopers, eta_max=3.0, noise_total=0)
+
+
+def make_config_batches(seed):
+    """The other configurations' inputs, generated in a spawn pool before any CUDA call:
+    the uneven batch (256 events, Poisson(8,000) tracks clipped to [200, 25,000], noise 2.5 per
+    track) and the looper sweep (50 events x 20,000 tracks, 10% at 0.5-0.7 GeV, no noise)."""
+    from paper_2312_11728_gb300 import synth as S
+    g = S.geometry_phase2()
+    counts = S.uneven_counts(256, 8000, 200, 25000, seed)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        uneven = pool.map(_gen_uneven_event, [(e, int(n), seed) for e, n in enumerate(counts)])
+        loop = pool.map(_gen_looper_event, [(e, seed + 5) for e in range(50)])
+    return g, S.concat_events(uneven, g.n_layers), S.concat_events(loop, g.n_layers)
+
+
 def scan_launches(n):
     """Kernels one device-wide exclusive scan of n ints launches (mirrors csrc/k_hits.cu)."""
     nb = (n + 2047) // 2048
@@ -465,6 +493,135 @@ def measure_modular(mod, params, shapes, stream, local, dist):
     return res
 
 
+def _fit_errors(gpu, r, sample):
+    """Worst errors of sampled fits against the oracle, in units of the tolerances."""
+    from oracle import parity as PR
+    rep = PR.compare_fit({k: v[sample] for k, v in gpu.items()}, r)
+    return {"tracks_compared": rep["n"], "status_mismatch": rep["status_bad"], "param_bad": rep["param_bad"],
+            "cov_bad": rep["cov_bad"], "chi2_bad": rep["chi2_bad"], "worst_param": rep["worst_param"],
+            "worst_cov": rep["worst_cov"], "worst_chi2": rep["worst_chi2"]}
+
+
+def measure_config_small(params, stream, local):
+    """1,000 tracks, 10 barrel cylinders, 200 noise hits per layer, one event: the whole pass
+    (CUDA events, mean of 10 after 3 warm-ups) and every seed and track against the oracle."""
+    import torch
+    import oracle
+    from oracle import parity as PR
+    from paper_2312_11728_gb300 import pipeline, synth as S
+    g, ev = S.workload_small_barrel()
+    b = S.concat_events([ev], g.n_layers)
+    fi = pipeline.fit_inputs(b)
+    ctx = pipeline.make_context(g, params, device=local, stream=stream)
+    db = pipeline.DeviceBatch(b, fi, g.max_plan, f"cuda:{local}")
+    for _ in range(3):
+        pipeline.run_step_fused(ctx, db)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record(stream)
+    for _ in range(10):
+        pipeline.run_step_fused(ctx, db)
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    ms = e[0].elapsed_time(e[1]) / 10
+    pipeline.run_step(ctx, db)
+    torch.cuda.synchronize()
+    steps = int(ctx.counters(0)[0] + ctx.counters(1)[0])
+    gpu = {k: v.cpu().numpy() for k, v in db.out.items()}
+    orc = oracle.Oracle(g, params)
+    t0 = time.perf_counter()
+    o = PR.oracle_build(orc, b)
+    X, V = b.hit_xyz.astype(np.float64), b.hit_cov.astype(np.float64)
+    r = orc.fit_batch(fi.layers, fi.hits, X, V, fi.p0.astype(np.float64), fi.c0.astype(np.float64))
+    t_orc = time.perf_counter() - t0
+    rep = PR.compare_build(gpu, o)
+    gf = {k: db.fit[k].cpu().numpy() for k in ("p", "c", "chi2", "status")}
+    return {"value": steps / (ms / 1e3), "unit": UNIT, "ms_per_pass": ms, "kalman_steps": steps,
+            "oracle": {"value": int(o["counters"][0] + r["counters"][0]) / t_orc, "unit": UNIT, "cores": 1,
+                       "seconds": t_orc},
+            "workload": "1,000 tracks, 10 barrel cylinders, 200 noise hits per layer, one event (launch-bound)",
+            "build_vs_oracle": {"seeds": rep["n"], "hit_mismatch": int(len(rep["hit_mismatch"])),
+                                "near_tie_seeds": rep["n_tie"], "param_bad": rep["param_bad"],
+                                "cov_bad": rep["cov_bad"], "chi2_bad": rep["chi2_bad"],
+                                "worst_param": rep["worst_param"], "worst_cov": rep["worst_cov"],
+                                "worst_chi2": rep["worst_chi2"]},
+            "fit_vs_oracle": _fit_errors(gf, r, np.arange(len(gf["chi2"])))}
+
+
+def measure_config_uneven(batch, g, params, stream, local):
+    """256 uneven events (~2.05M tracks) in one call: search shapes autotuned on the batch, then
+    the one-call pass timed (CUDA events, mean of 5 after 2 warm-ups)."""
+    import torch
+    from paper_2312_11728_gb300 import pipeline
+    fi = pipeline.fit_inputs(batch)
+    ctx = pipeline.make_context(g, params, device=local, stream=stream)
+    db = pipeline.DeviceBatch(batch, fi, g.max_plan, f"cuda:{local}")
+    pipeline.run_step(ctx, db)
+    torch.cuda.synchronize()
+    steps = int(ctx.counters(0)[0] + ctx.counters(1)[0])
+    f_s, s_s, tune_ms = ctx.autotune(reps=1)
+    for _ in range(2):
+        pipeline.run_step_fused(ctx, db)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record(stream)
+    for _ in range(5):
+        pipeline.run_step_fused(ctx, db)
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    ms = e[0].elapsed_time(e[1]) / 5
+    return {"value": steps / (ms / 1e3), "unit": UNIT, "ms_per_pass": ms, "kalman_steps": steps,
+            "events": int(batch.n_events), "seeds": int(batch.seed_hits.shape[0]), "tracks": int(fi.layers.shape[0]),
+            "search_launch": {"find_shape": f_s, "select_shape": s_s, "autotune_ms_per_search": tune_ms},
+            "workload": "256 events, Poisson(8,000) tracks clipped to [200, 25,000], 2.5 noise hits per track, "
+                        "one call (all events' seeds searched together)"}
+
+
+def measure_config_loopers(batch, g, params, stream, local):
+    """1,000,000 tracks over 34 layers, 10% at 0.5-0.7 GeV: the FP32 fit with the FP64 refit of
+    the flagged tracks against the all-FP64 fit (CUDA events, mean of 3 after a warm-up), and
+    both against the oracle on 1,000 sampled tracks."""
+    import torch
+    import oracle
+    from paper_2312_11728_gb300 import pipeline
+    fi = pipeline.fit_inputs(batch)
+    n = fi.layers.shape[0]
+    rng = np.random.default_rng(17)
+    sample = np.sort(rng.choice(n, 1000, replace=False))
+    X, V = batch.hit_xyz.astype(np.float64), batch.hit_cov.astype(np.float64)
+    t0 = time.perf_counter()
+    r = oracle.Oracle(g, params).fit_batch(fi.layers[sample], fi.hits[sample], X, V,
+                                           fi.p0[sample].astype(np.float64), fi.c0[sample].astype(np.float64))
+    t_orc = time.perf_counter() - t0
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(f"cuda:{local}")
+    d = dict(layers=dev(fi.layers), hits=dev(fi.hits), p0=dev(fi.p0), c0=dev(fi.c0))
+    res = {"tracks": int(n), "layers": int(g.n_layers), "steps": int((fi.layers >= 0).sum()),
+           "oracle": {"value": int(r["counters"][0]) / t_orc, "unit": "fit track-layer steps/s", "cores": 1,
+                      "sample": "the 1,000 compared tracks"},
+           "workload": "50 events x 20,000 tracks over 34 layers, 10% at 0.5-0.7 GeV (curling), no noise"}
+    for name, prec in (("fp32_fp64_refit", 0), ("fp64", 2)):
+        ctx = pipeline.make_context(g, dict(params, precision=prec), device=local, stream=stream)
+        ctx.load_hits(batch.n_events, batch.hit_off, dev(batch.hit_xyz), dev(batch.hit_cov))
+        o = dict(p=torch.zeros((n, 6), device=f"cuda:{local}"), c=torch.zeros((n, 21), device=f"cuda:{local}"),
+                 chi2=torch.zeros(n, device=f"cuda:{local}"),
+                 status=torch.zeros(n, dtype=torch.int32, device=f"cuda:{local}"))
+        call = lambda: ctx.fit(d["layers"], d["hits"], d["p0"], d["c0"], o["p"], o["c"], o["chi2"], o["status"])
+        call()
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record(stream)
+        for _ in range(3):
+            call()
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        ms = e[0].elapsed_time(e[1]) / 3
+        gf = {k: v.cpu().numpy() for k, v in o.items()}
+        res[name] = {"ms": ms, "value": res["steps"] / (ms / 1e3), "unit": "fit track-layer steps/s",
+                     "vs_oracle": _fit_errors(gf, r, sample)}
+    res["fp32_over_fp64"] = res["fp64"]["ms"] / res["fp32_fp64_refit"]["ms"]
+    return res
+
+
 def measure_fit_grad(args, local, rank, dist, stream):
     """The fit's derivative on the differentiable-fit workload (100,000 tracks over 22 layers of
     a misaligned detector): one mkgb_fit_grad call after a warm-up call, CUDA-event timed."""
@@ -526,6 +683,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the all-FP64 comparison path")
     ap.add_argument("--no-grad", action="store_true", help="skip the fit-derivative measurement")
     ap.add_argument("--no-modular", action="store_true", help="skip the modular-tracker measurement")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other configurations (1,000-track barrel, 256 uneven events, 1M-track sweep)")
     ap.add_argument("--modular-events", type=int, default=16, help="events of the modular-tracker measurement")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes of the search kernels")
     ap.add_argument("--no-graph", action="store_true", help="launch the search rounds one by one")
@@ -545,6 +704,7 @@ def main():
     from paper_2312_11728_gb300 import pipeline, synth as S
     g, batch, evs = make_batch(seed=rank, n_events=args.events)   # before the first CUDA call (spawn pool)
     mod = None if args.no_modular else make_modular_batch(rank, args.modular_events)
+    cfg = None if args.no_configs else make_config_batches(rank)
     fit = pipeline.fit_inputs(batch, seed=rank)
     params = S.default_params()
 
@@ -641,6 +801,13 @@ def main():
     if not args.no_grad:
         grad = measure_fit_grad(args, local, rank, dist, stream)
 
+    configs = None
+    if cfg is not None:
+        cg, uneven, loopers = cfg
+        configs = {"small_barrel_1k": measure_config_small(params, stream, local),
+                   "uneven_256ev": measure_config_uneven(uneven, cg, params, stream, local),
+                   "loopers_1m": measure_config_loopers(loopers, cg, params, stream, local)}
+
     # ---- end to end through the C ABI with host (pinned) buffers, copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -705,6 +872,7 @@ def main():
         "e2e": e2e,
         "fp64_plain": fp64,
         "fit_grad": grad,
+        "configs": configs,
         "fit_backward": bkfit,
         "cleaning": cleaning,
         "modular": modular,

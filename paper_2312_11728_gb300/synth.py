@@ -785,13 +785,18 @@ def workload_phase2(n_events=64, n_tracks=20000, seed=0, noise_total=50000):
     return g, evs
 
 
+def uneven_counts(n_events=256, mean=8000, lo=200, hi=25000, seed=0):
+    """Poisson track counts of the uneven-batch workload, clipped to [lo, hi]."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 104729])))
+    return np.clip(rng.poisson(mean, n_events), lo, hi)
+
+
 def workload_uneven(n_events=256, mean=8000, lo=200, hi=25000, seed=0, noise_per_track=2.5, counts=None):
     """Events with Poisson track counts (clipped to [lo, hi]; or the given counts) on the
     Phase-2-like geometry, noise in proportion to the tracks (50,000 per 20,000 tracks)."""
     g = geometry_phase2()
-    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 104729])))
     if counts is None:
-        counts = np.clip(rng.poisson(mean, n_events), lo, hi)
+        counts = uneven_counts(n_events, mean, lo, hi, seed)
     evs = [simulate_event(g, int(n), seed, e, pt_sampler=sample_pt_phase2, eta_max=3.0,
                           noise_total=int(noise_per_track * n)) for e, n in enumerate(counts)]
     return g, evs
