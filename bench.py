@@ -826,7 +826,7 @@ def main():
     # the same sources (null if the kernels changed since)
     traffic = None
     tr_path = os.path.join(ROOT, "profiles", "search_traffic.json")
-    if os.path.exists(tr_path):
+    if os.path.exists(tr_path) and shapes[0] < 3:   # captured on the two-kernel round
         tr = json.load(open(tr_path))
         if tr.get("sources_sha256_16") == kernel_sources_hash():
             traffic = tr["dram_bytes_per_crossed_step"] * int(bc[0])
@@ -835,7 +835,9 @@ def main():
     rf_search = roofline("search", stage["build"], build_flops(bc),
                          search_bytes(bc, n_hits, bins_total, n_seeds, g.max_plan), fp32_peak, hbm, traffic)
     rf_search.update({
-        "kernel": "search: k_start, one fused k_round per plan step (k_rescue after it when flagged), k_finish",
+        "kernel": ("search: k_start, one fused k_round per plan step (k_rescue after it when flagged), k_finish"
+                   if shapes[0] >= 3 else
+                   "search: k_start, per plan step k_find and k_select (k_rescue after them when flagged), k_finish"),
         "peak_note": f"HBM {hbm:.1f} GB/s ({src} copy bandwidth); FP32 {n_sms} SMs x 128 lanes x 2 x {sm_max:.0f} MHz "
                      f"({src} max clock) = {fp32_peak:.1f} TFLOP/s; FMA probe {probe['fp32_tflops']:.1f} TFLOP/s",
         "launch": "algorithmic bytes and flops of one whole search over its CUDA-event time on the context's "

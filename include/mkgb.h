@@ -153,8 +153,9 @@ int mkgb_load_hits(mkgb_ctx* ctx, int n_events, const int64_t* seg_off,
  * then tests and updates module hits on their planes and picks up overlap hits (mkgb_build,
  * mkgb_tracks.ovl_hits: with the best accepted module hit b1 of a candidate's window and the best
  * one b2 on a module other than b1's, a child taking module hit h also takes b1 if h is not on b1's
- * module, else b2, and scores params.score_overlap more; its update uses h only).  Seeds with a
- * module hit fail (the seed fit takes hits on the layers' own surfaces).  mkgb_fit and
+ * module, else b2, and scores params.score_overlap more; its update uses h only).  mkgb_seed
+ * uses a seed hit on a module on its module's plane (the seed's state is then the one on hit 3's
+ * plane; status 1 if a plane is not reached).  mkgb_fit and
  * mkgb_fit_backward use module hits on their planes (status 1 if a plane is not reached within
  * 10 cm, or only at grazing incidence; the backward fit's start state is taken on the plane of its
  * last hit's module); mkgb_build_backward tests and picks up module hits as mkgb_build does (its

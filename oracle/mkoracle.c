@@ -669,8 +669,10 @@ int orc_select_region(const orc_geom* g, const double p[6]) {
  * sign gives the charge, the tangent at hit 1 gives phi, and dz over the arc length
  * from hit 1 to hit 3 gives cot(theta).  Starting from that estimate at hit 1 with a
  * diffuse diagonal covariance, a Kalman fit through hits 1, 2, 3 gives the state at hit 3. */
-int orc_seed(const orc_geom* g, int material, const double h[9], const double V[18],
-             const int layers[3], double p[6], double C[21], double pinit[6]) {
+/* Seed fit (a1) of three hits; ids (may be NULL) names them so that a hit measured on a module
+ * (Sec. 3.1) is used on its module's plane, reached from the layer's reference surface. */
+static int seed_fit(const orc_geom* g, int material, const double h[9], const double V[18],
+                    const int layers[3], const long long* ids, double p[6], double C[21], double pinit[6]) {
     double cB = C_LIGHT * g->bz;
     double ax = h[3] - h[0], ay = h[4] - h[1], bx = h[6] - h[0], by = h[7] - h[1];
     double cross = ax * by - ay * bx;
@@ -702,15 +704,27 @@ int orc_seed(const orc_geom* g, int material, const double h[9], const double V[
     double sk = 0.5 * fabs(k) + 0.05;
     Cq[ix(0, 0)] = 0.01; Cq[ix(1, 1)] = 0.01; Cq[ix(2, 2)] = 0.01;
     Cq[ix(3, 3)] = sk * sk; Cq[ix(4, 4)] = 0.0025; Cq[ix(5, 5)] = 0.0025;
-    double pu[6], Cu[21], pp[6], Cp[21], s;
+    double pu[6], Cu[21], pp[6], Cp[21], ph[6], Ch[21], s;
+    /* hit 1 is the estimate's own position: on its module's plane as well */
     if (!orc_update(q, Cq, &h[0], &V[0], 1, pu, Cu, NULL)) return 0;
     for (int j = 1; j < 3; ++j) {
         if (orc_propagate(g, layers[j], pu, Cu, material, pp, Cp, &s) != 1) return 0;
-        if (!orc_update(pp, Cp, &h[3 * j], &V[6 * j], 1, pu, Cu, NULL)) return 0;
+        if (ids) {
+            if (!at_hit_surface(g, ids[j], pp, Cp, ph, Ch, NULL)) return 0;
+        } else {
+            memcpy(ph, pp, sizeof(pp));
+            memcpy(Ch, Cp, sizeof(Cp));
+        }
+        if (!orc_update(ph, Ch, &h[3 * j], &V[6 * j], 1, pu, Cu, NULL)) return 0;
     }
     memcpy(p, pu, sizeof(pu));
     memcpy(C, Cu, sizeof(Cu));
     return 1;
+}
+
+int orc_seed(const orc_geom* g, int material, const double h[9], const double V[18],
+             const int layers[3], double p[6], double C[21], double pinit[6]) {
+    return seed_fit(g, material, h, V, layers, NULL, p, C, pinit);
 }
 
 static int plan_start(const orc_geom* g, int region, int layer3) {
@@ -724,12 +738,14 @@ void orc_seed_batch(const orc_geom* g, int material, int n, const int* seed_hits
                     double* p, double* C, double* pinit, int* region, int* start, int* status) {
     for (int i = 0; i < n; ++i) {
         double h[9], V[18];
+        long long ids[3];
         for (int j = 0; j < 3; ++j) {
             long long id = seed_hits[3 * i + j];
+            ids[j] = id;
             memcpy(&h[3 * j], &xyz[3 * id], 3 * sizeof(double));
             memcpy(&V[6 * j], &cov[6 * id], 6 * sizeof(double));
         }
-        int ok = orc_seed(g, material, h, V, &seed_layers[3 * i], &p[6 * i], &C[21 * i], &pinit[6 * i]);
+        int ok = seed_fit(g, material, h, V, &seed_layers[3 * i], ids, &p[6 * i], &C[21 * i], &pinit[6 * i]);
         region[i] = ok ? orc_select_region(g, &p[6 * i]) : -1;
         start[i] = ok ? plan_start(g, region[i], seed_layers[3 * i + 2]) : -1;
         status[i] = (ok && start[i] >= 0) ? 0 : 1;
@@ -1334,11 +1350,9 @@ int orc_build_event(const orc_geom* g, const orc_params* P, const orc_tie* T,
         }
         out->region[si] = -1;
         out->start[si] = -1;
-        /* the seed fit takes hits on the layers' own surfaces: a seed with a module hit fails */
-        if (hit_module(g, seed_hits[3 * si]) >= 0 || hit_module(g, seed_hits[3 * si + 1]) >= 0 ||
-            hit_module(g, seed_hits[3 * si + 2]) >= 0)
-            continue;
-        if (!orc_seed(g, P->material, h, V, &seed_layers[3 * si], w.cur[0].p, w.cur[0].C, pinit)) continue;
+        /* a seed hit measured on a module is used on its module's plane (Sec. 3.1) */
+        const long long ids[3] = {seed_hits[3 * si], seed_hits[3 * si + 1], seed_hits[3 * si + 2]};
+        if (!seed_fit(g, P->material, h, V, &seed_layers[3 * si], ids, w.cur[0].p, w.cur[0].C, pinit)) continue;
         int region = orc_select_region(g, w.cur[0].p);
         int start = plan_start(g, region, seed_layers[3 * si + 2]);
         out->region[si] = region;

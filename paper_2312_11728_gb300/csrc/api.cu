@@ -622,7 +622,7 @@ int mkgb_seed(mkgb_ctx* ctx, int n_seeds, const int32_t* seed_hits, int on_devic
     const bool fp64 = ctx->params.precision == MKGB_FP64;
     CK(launch_seed_fit(st, (const DevGeom*)ctx->geom_d.p, ctx->params, hit_store(ctx), n, (const int*)sh,
                        (float*)ctx->seed_state.p, fp64 ? (double*)ctx->seed_state64.p : nullptr,
-                       (int4*)ctx->seed_info.p, (float*)s6, (float*)c21, (int*)i3, SeedRange()));
+                       (int4*)ctx->seed_info.p, (float*)s6, (float*)c21, (int*)i3, SeedRange(), ctx->mod_hits));
     rc = seed_order(ctx, st, n);
     if (rc != MKGB_OK) return rc;
     CK(copy_back(ctx, state_out, s6, 24 * (size_t)n, on_device));
@@ -1122,7 +1122,7 @@ int run_host_impl(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const flo
         range.which = which;
         CK(launch_seed_fit(main_st, (const DevGeom*)ctx->geom_d.p, ctx->params, H, n_seeds, d_seeds,
                            (float*)ctx->seed_state.p, fp64 ? (double*)ctx->seed_state64.p : nullptr,
-                           (int4*)ctx->seed_info.p, nullptr, nullptr, nullptr, range));
+                           (int4*)ctx->seed_info.p, nullptr, nullptr, nullptr, range, false));
         return MKGB_OK;
     };
     CK(cudaStreamWaitEvent(main_st, ctx->ev_seedin, 0));

@@ -104,9 +104,10 @@ struct SeedRange {
 cudaError_t launch_seed(cudaStream_t st, const DevGeom* g, DevParams P, HitStore H, int n, const int* seed_hits,
                         float* state, double* state64, int4* info, int* key_of, int* key_counts, float* state6,
                         float* cov21, int* info3);
+// modular: module hits loaded (a seed hit on a module is used on its module's plane)
 cudaError_t launch_seed_fit(cudaStream_t st, const DevGeom* g, DevParams P, HitStore H, int n, const int* seed_hits,
                             float* state, double* state64, int4* info, float* state6, float* cov21, int* info3,
-                            const SeedRange& range);
+                            const SeedRange& range, bool modular);
 cudaError_t launch_seed_keys(cudaStream_t st, int n, const float* state, const int4* info, int* key_of,
                              int* key_counts);
 

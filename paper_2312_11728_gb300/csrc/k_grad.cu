@@ -29,7 +29,7 @@ namespace mk {
 namespace {
 
 constexpr int kThreads = 64;
-constexpr int KD = 4;   // derivative directions per pass
+constexpr int KD = 2;   // derivative directions per pass (at 4 the dual state spilled 1.4 KB of stack per thread)
 using D = Dual<float, KD>;
 
 __device__ __forceinline__ void load_geom(const DevGeom* __restrict__ gp, DevGeom& g) {

@@ -56,7 +56,9 @@ __device__ __forceinline__ int chunk_of(const SeedRange& r, int h) {
     return -1;
 }
 
-template <bool FAST>
+// MOD: module hits loaded (seed hits on modules are used on their planes); the plain
+// instantiation keeps the layers-only registers.
+template <bool FAST, bool MOD>
 __global__ void __launch_bounds__(kThreads) k_seed(const DevGeom* __restrict__ gp, DevParams P, HitStore H, int n,
                                                    const int* __restrict__ seed_hits, float* __restrict__ state,
                                                    double* __restrict__ state64, int4* __restrict__ info,
@@ -73,7 +75,7 @@ __global__ void __launch_bounds__(kThreads) k_seed(const DevGeom* __restrict__ g
     }
     StateT<double> td;
     int lay[3], event, region, start;
-    const bool ok = seed_fit<double, FAST>(g, P, H, seed_hits, i, td, lay, event);
+    const bool ok = seed_fit<double, FAST, MOD>(g, P, H, seed_hits, i, td, lay, event);
     State t;
     narrow_state(td, t);
     seed_region(g, P, t.th, lay[2], ok, region, start);
@@ -109,16 +111,13 @@ __global__ void __launch_bounds__(kThreads) k_seed_key(int n, const float* __res
 
 cudaError_t launch_seed_fit(cudaStream_t st, const DevGeom* g, DevParams P, HitStore H, int n, const int* seed_hits,
                             float* state, double* state64, int4* info, float* state6, float* cov21, int* info3,
-                            const SeedRange& range) {
+                            const SeedRange& range, bool modular) {
     if (n == 0) return cudaSuccess;
     const int blocks = (n + kThreads - 1) / kThreads;
     // the FP32 path's seed fits take the FP32-assisted FP64 steps; the plain all-FP64 path does not
-    if (P.precision == MKGB_FP64)
-        k_seed<false><<<blocks, kThreads, 0, st>>>(g, P, H, n, seed_hits, state, state64, info, state6, cov21, info3,
-                                                   range);
-    else
-        k_seed<true><<<blocks, kThreads, 0, st>>>(g, P, H, n, seed_hits, state, state64, info, state6, cov21, info3,
-                                                  range);
+    auto kern = P.precision == MKGB_FP64 ? (modular ? k_seed<false, true> : k_seed<false, false>)
+                                         : (modular ? k_seed<true, true> : k_seed<true, false>);
+    kern<<<blocks, kThreads, 0, st>>>(g, P, H, n, seed_hits, state, state64, info, state6, cov21, info3, range);
     return cudaGetLastError();
 }
 
@@ -133,7 +132,7 @@ cudaError_t launch_seed(cudaStream_t st, const DevGeom* g, DevParams P, HitStore
                         float* state, double* state64, int4* info, int* key_of, int* key_counts, float* state6,
                         float* cov21, int* info3) {
     const cudaError_t e = launch_seed_fit(st, g, P, H, n, seed_hits, state, state64, info, state6, cov21, info3,
-                                          SeedRange());
+                                          SeedRange(), false);
     if (e != cudaSuccess) return e;
     return launch_seed_keys(st, n, state, info, key_of, key_counts);
 }

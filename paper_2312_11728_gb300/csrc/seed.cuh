@@ -10,7 +10,8 @@ namespace mk {
 // cot(theta); the covariance is diagonal and diffuse.  Returns ok (valid hits of one event).
 template <class F>
 __device__ __forceinline__ bool seed_prior(const DevGeom& g, const HitStore& H, const int* __restrict__ seed_hits,
-                                           int i, F m[3][3], F v[3][6], int lay[3], int& event, StateT<F>& t) {
+                                           int i, F m[3][3], F v[3][6], int lay[3], int& event, StateT<F>& t,
+                                           int mod[3]) {
     int id[3], ev[3];
     bool ok = true;
 #pragma unroll
@@ -23,9 +24,8 @@ __device__ __forceinline__ bool seed_prior(const DevGeom& g, const HitStore& H, 
         const int seg = H.hit_seg[id[j]];
         ev[j] = seg / H.n_layers;
         lay[j] = seg - ev[j] * H.n_layers;
-        int md;
-        load_hit(H.pay, id[j], m[j], v[j], nullptr, &md);
-        ok = ok && md < 0;   // the seed fit takes hits on the layers' own surfaces
+        load_hit(H.pay, id[j], m[j], v[j], nullptr, &mod[j]);   // mod: the hit's module, -1 none
+        if (!g.mods) mod[j] = -1;
     }
     event = ev[0];
     ok = ok && ev[0] == ev[1] && ev[1] == ev[2];
@@ -64,16 +64,19 @@ __device__ __forceinline__ bool seed_prior(const DevGeom& g, const HitStore& H, 
 }
 
 // Seed fit of seed i in precision F: update with hit 1, then propagate to and update with hits
-// 2 and 3.  FAST (FP64 fits of the FP32 path): the first update in closed form (zero residual,
+// 2 and 3 (MOD: a hit measured on a module is used on its module's plane, reached from its
+// layer's surface; hit 1 needs no step, the estimate sits on it).  FAST (FP64 fits of the FP32 path): the first update in closed form (zero residual,
 // diagonal prior), FP32 crossings refined in FP64 (propagate_refined), the update's frame from
 // the propagation's direction and the short covariance update (I - K H) C; the plain all-FP64
 // path takes the general steps.  Returns ok.
-template <class F, bool FAST = false>
+template <class F, bool FAST = false, bool MOD = false>
 __device__ __forceinline__ bool seed_fit(const DevGeom& g, const DevParams& P, const HitStore& H,
                                          const int* __restrict__ seed_hits, int i, StateT<F>& t, int lay[3],
                                          int& event) {
     F m[3][3], v[3][6];
-    bool ok = seed_prior(g, H, seed_hits, i, m, v, lay, event, t);
+    int mod[3];
+    bool ok = seed_prior(g, H, seed_hits, i, m, v, lay, event, t, mod);
+    if constexpr (!MOD) ok = ok && mod[0] < 0 && mod[1] < 0 && mod[2] < 0;
     int newton = 0;
     constexpr bool fast = FAST && sizeof(F) == 8;
     if constexpr (fast)
@@ -86,6 +89,14 @@ __device__ __forceinline__ bool seed_fit(const DevGeom& g, const DevParams& P, c
         const DevLayer& L = g.layers[lay[j]];
         F dir[4];
         ok = ok && propagate_refined(L, g.cB, P.material, t, q, newton, fast, dir) == 1;
+        if constexpr (MOD) {
+            if (ok && mod[j] >= 0) {   // a module hit: the update on its module's plane (Sec. 3.1)
+                F x2u;
+                float kap;
+                ok = module_update(L.kind, q, g.mods, mod[j], g.cB, m[j], v[j], 0.0f, t, x2u, kap) == 0;
+                continue;
+            }
+        }
         if constexpr (fast)
             ok = ok && kalman_update_f<F, false>(frame_of(L.kind, q.xh, q.yh, dir[0], dir[1], dir[2], dir[3]), q,
                                                  m[j][0], m[j][1], m[j][2], v[j], t);

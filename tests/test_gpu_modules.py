@@ -149,12 +149,16 @@ def test_modular_edge_cases(lib, work):
     with pytest.raises(mkgb.MkgbError):
         plain.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov, hit_module=hm)
     ctx.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov, hit_module=hm)
-    # a seed with a module hit fails, as in the oracle
+    # a seed given a module hit of another track: its hits are taken on their planes as the
+    # oracle takes them, and the result is the oracle's
     sh = batch.seed_hits[:6].copy()
     sh[0, 2] = i
     ctx.seed(sh)
     out = ctx.build(mkgb.alloc_tracks(6, g.max_plan, ovl=True))
-    assert out["score"][0] == -np.inf and np.all(out["ovl"][0] == -1)
+    b6 = S.Batch(batch.n_events, batch.n_layers, batch.hit_xyz, batch.hit_cov, batch.hit_off, batch.hit_track,
+                 sh, batch.seed_event[:6], batch.seed_track[:6], batch.events, batch.hit_mod)
+    rep6 = PR.compare_build(out, PR.oracle_build(_oracle(g, batch, params), b6))
+    assert len(rep6["hit_mismatch"]) == 0 and rep6["failed_mismatch"] == 0 and rep6["param_bad"] == 0, rep6
     # no overlap array requested: the search runs the same
     ctx.seed(batch.seed_hits[:200])
     a = ctx.build(mkgb.alloc_tracks(200, g.max_plan, ovl=True))
@@ -340,3 +344,34 @@ def test_modular_one_call_pass_equals_separate_calls(lib, work):
     for x, y in zip(fa, fb):
         assert np.array_equal(x, y)
     assert (a["ovl"] >= 0).sum() > 0
+
+
+def test_seeds_on_modular_layers_match_oracle(lib):
+    """Seeding layers built from modules (cylinders 0-2 of flat and tilted modules): every seed hit
+    is taken on its module's plane in the seed fit (Sec. 3.1), on the GPU as in the oracle; seed
+    states and the search from them against the oracle."""
+    g = S.geometry_phase2_modular(layers=(0, 1, 2))
+    evs = [S.simulate_event(g, 800, 43, e, pt_sampler=S.sample_pt_phase2, eta_max=2.5, noise_total=2000)
+           for e in range(2)]
+    batch = S.concat_events(evs, g.n_layers)
+    params = S.default_params()
+    assert (batch.hit_mod[batch.seed_hits] >= 0).any(1).mean() > 0.5   # most seeds carry module hits
+    ctx = _ctx(g, batch, params)
+    n = batch.seed_hits.shape[0]
+    state, cov, info = np.zeros((n, 6), np.float32), np.zeros((n, 21), np.float32), np.zeros((n, 3), np.int32)
+    ctx.seed(batch.seed_hits, state, cov, info)
+    orc = _oracle(g, batch, params)
+    lo = batch.hit_off
+    sl = np.concatenate([oracle.hit_layers(lo[e * g.n_layers:(e + 1) * g.n_layers + 1],
+                                           batch.seed_hits[batch.seed_event == e]) for e in range(batch.n_events)])
+    r = orc.seed_batch(batch.seed_hits, sl, batch.hit_xyz.astype(np.float64), batch.hit_cov.astype(np.float64))
+    assert np.array_equal(info[:, 2], r["status"]) and np.array_equal(info[:, 0], r["region"])
+    ok = r["status"] == 0
+    assert ok.mean() > 0.95
+    pok, prat = PR.param_close(state[ok], r["p"][ok])
+    cok, crat = PR.cov_close_surface(cov[ok], r["c"][ok], r["p"][ok], r["surf"])
+    assert pok.all() and cok.all(), (prat.max(), crat.max())
+    out = ctx.build(mkgb.alloc_tracks(n, g.max_plan, ovl=True))
+    rep = PR.compare_build(out, PR.oracle_build(orc, batch))
+    assert len(rep["hit_mismatch"]) == 0 and rep["failed_mismatch"] == 0, rep
+    assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0, rep

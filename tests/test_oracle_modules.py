@@ -217,18 +217,51 @@ def test_overlap_bonus_raises_score_only(geo):
     assert np.all(o0["chi2"][same] == o1["chi2"][same])
 
 
-def test_modular_seeds_fail_and_no_modules_is_plain_search(geo):
-    """A seed with a module hit fails; with the module table cleared, hits are taken on the
-    reference cylinder and no overlap hit is ever picked up."""
+def test_seed_on_module_planes_recovers_truth():
+    """Seeding cylinders built from modules, noise-free hits, no material: the seed fit takes each
+    hit on its module's plane and ends on the third hit with the helix's own parameters (three
+    exact points of a helix fix it); the same seeds with the hits taken on the cylinders miss it."""
+    g = S.geometry_phase2_modular(layers=(0, 1, 2))
+    ev = S.simulate_event(g, 200, 27, 0, pt_sampler=S.sample_pt_phase2, eta_max=1.0, noise_total=0,
+                          material=False, smear=False)
+    b = S.concat_events([ev], g.n_layers)
+    params = dict(S.default_params(), material=0)
+    sl = oracle.hit_layers(b.hit_off, b.seed_hits)
+    X, V = b.hit_xyz.astype(np.float64), b.hit_cov.astype(np.float64)
+    mod_seed = (b.hit_mod[b.seed_hits] >= 0).all(1)
+    assert mod_seed.mean() > 0.8
+    orc = _oracle_with_modules(g, b, params)
+    r = orc.seed_batch(b.seed_hits, sl, X, V)
+    ok = (r["status"] == 0) & mod_seed
+    assert ok.sum() > 0.8 * mod_seed.sum()
+    # truth: the hit itself for the position; q/pT and theta are constants of the helix without
+    # material; the direction at the hit from the truth at the cylinder crossing: the chord between
+    # two points of a circle runs along the mean of the tangent angles at its ends
+    x3 = b.hit_xyz[b.seed_hits[ok, 2]].astype(np.float64)
+    t3 = ev.track_truth[b.seed_track[ok], 2]
+    alpha = np.arctan2(x3[:, 1] - t3[:, 1], x3[:, 0] - t3[:, 0])
+    alpha = np.where(np.cos(alpha - t3[:, 4]) < 0, alpha + np.pi, alpha)
+    phi3 = 2 * alpha - t3[:, 4]
+    p = r["p"][ok]
+    dpos = np.abs(p[:, :3] - x3).max(1)
+    assert dpos.max() < 1e-4                                   # hits stored in float32
+    assert np.abs(p[:, 3] / t3[:, 3] - 1).max() < 1e-3
+    assert np.abs(p[:, 5] - t3[:, 5]).max() < 1e-5
+    # the chord's angle carries the float32 rounding of the hit (~1e-6 cm) over the chord length
+    chord = np.hypot(x3[:, 0] - t3[:, 0], x3[:, 1] - t3[:, 1])
+    assert np.all(np.abs(np.angle(np.exp(1j * (p[:, 4] - phi3)))) < 1e-5 + 1e-5 / chord)
+    orc.set_modules(None, None, None)
+    r0 = orc.seed_batch(b.seed_hits, sl, X, V)
+    ok0 = r0["status"][ok] == 0
+    d0 = np.abs(r0["p"][ok][ok0, :3] - x3[ok0]).max(1)
+    assert np.median(d0) > 100 * max(np.median(dpos), 1e-6)
+
+
+def test_no_modules_is_plain_search(geo):
+    """With the module table cleared, hits are taken on the reference cylinder and no overlap hit
+    is ever picked up."""
     batch = _modular_batch(geo, n_events=1, n_tracks=200, seed=29)
     orc = _oracle_with_modules(geo, batch)
-    sh = batch.seed_hits.copy()
-    bad = np.nonzero(batch.hit_mod >= 0)[0][:1]
-    sh[0, 2] = bad[0]
-    b2 = S.Batch(batch.n_events, batch.n_layers, batch.hit_xyz, batch.hit_cov, batch.hit_off, batch.hit_track,
-                 sh[:5], batch.seed_event[:5], batch.seed_track[:5], batch.events, batch.hit_mod)
-    o = PR.oracle_build(orc, b2)
-    assert o["score"][0] == -np.inf and o["region"][0] == -1
     orc.set_modules(None, None, None)
     o = PR.oracle_build(orc, batch)
     assert np.all(o["ovl"] == -1)
