@@ -65,10 +65,11 @@ __device__ __forceinline__ bool seed_prior(const DevGeom& g, const HitStore& H, 
 
 // Seed fit of seed i in precision F: update with hit 1, then propagate to and update with hits
 // 2 and 3 (MOD: a hit measured on a module is used on its module's plane, reached from its
-// layer's surface; hit 1 needs no step, the estimate sits on it).  FAST (FP64 fits of the FP32 path): the first update in closed form (zero residual,
-// diagonal prior), FP32 crossings refined in FP64 (propagate_refined), the update's frame from
-// the propagation's direction and the short covariance update (I - K H) C; the plain all-FP64
-// path takes the general steps.  Returns ok.
+// layer's surface; hit 1 needs no step, the estimate sits on it).  FAST (the seed fits of the
+// FP32 path): the first update in closed form (zero residual, diagonal prior), the trajectory and
+// Jacobian of each step in FP32 with the covariance transport and the update in FP64, the
+// update's frame from the propagation's direction and the short covariance update (I - K H) C;
+// the plain all-FP64 path takes the general steps.  Returns ok.
 template <class F, bool FAST = false, bool MOD = false>
 __device__ __forceinline__ bool seed_fit(const DevGeom& g, const DevParams& P, const HitStore& H,
                                          const int* __restrict__ seed_hits, int i, StateT<F>& t, int lay[3],
@@ -88,7 +89,24 @@ __device__ __forceinline__ bool seed_fit(const DevGeom& g, const DevParams& P, c
         PredT<F> q;
         const DevLayer& L = g.layers[lay[j]];
         F dir[4];
-        ok = ok && propagate_refined(L, g.cB, P.material, t, q, newton, fast, dir) == 1;
+        if constexpr (fast) {
+            // the trajectory (float-float positions and angles), its Jacobian and the material
+            // in FP32, the covariance transported from the FP64 state in FP64: the ill-conditioned
+            // part of the seed fit, the update's cancellation, stays in FP64, while a Jacobian
+            // rounded to FP32 only perturbs the problem by ~1e-7 relative
+            State t32;
+            narrow_to_fp32(t, t32);
+            Pred q32;
+            float d32[4];
+            ok = ok && propagate_core<float, F>(L, g.cB, P.material, t32, t.c, q32, q.c, newton, d32) == 1;
+            q.xh = F(q32.xh); q.yh = F(q32.yh); q.zh = F(q32.zh);
+            q.xl = F(q32.xl); q.yl = F(q32.yl); q.zl = F(q32.zl);
+            q.k = F(q32.k); q.phi = F(q32.phi); q.pl = F(q32.pl); q.th = F(q32.th); q.tl = F(q32.tl);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) dir[c] = F(d32[c]);
+        } else {
+            ok = ok && propagate_refined(L, g.cB, P.material, t, q, newton, fast, dir) == 1;
+        }
         if constexpr (MOD) {
             if (ok && mod[j] >= 0) {   // a module hit: the update on its module's plane (Sec. 3.1)
                 F x2u;

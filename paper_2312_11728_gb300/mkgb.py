@@ -96,6 +96,16 @@ def load_library(path: str = LIB_PATH):
     lib.mkgb_propagate.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, i32]
     lib.mkgb_update.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32]
     lib.mkgb_counters.argtypes = [vp, i32, vp]
+    lib.mkgb_load_modules.argtypes = [vp, i32, vp, vp, vp]
+    lib.mkgb_load_hits_modular.argtypes = [vp, i32, vp, vp, vp, vp, i32]
+    lib.mkgb_run_modular.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp, C.POINTER(Tracks), i32, i32, vp, vp, vp, vp,
+                                     vp, vp, vp, vp]
+    lib.mkgb_version.argtypes = []
+    # every entry point is declared: an undeclared one would pass a host pointer given as a Python
+    # int as a 32-bit C int, truncating any address above 2 GB
+    missing = [n for n in EXPORTS if getattr(lib, n).argtypes is None]
+    if missing:
+        raise MkgbError(f"entry points without argument types: {missing}")
     _lib = lib
     return lib
 

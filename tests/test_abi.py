@@ -38,6 +38,20 @@ def test_every_declared_entry_point_is_exported(lib):
         assert hasattr(lib, n)
 
 
+def test_every_entry_point_has_its_argument_types(lib):
+    """The binding declares each entry point's parameters, as many as the header gives it: an
+    undeclared pointer parameter would go through ctypes as a 32-bit int and lose the high bits of
+    any host address above 2 GB."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    for n in mkgb.EXPORTS:
+        m = re.search(r"\b" + n + r"\s*\(([^)]*)\)", text)
+        assert m, n
+        params = m.group(1).strip()
+        count = 0 if params in ("", "void") else params.count(",") + 1
+        assert getattr(lib, n).argtypes is not None, n
+        assert len(getattr(lib, n).argtypes) == count, (n, count)
+
+
 def test_library_is_built_for_sm_103a_only(lib):
     assert B.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
     assert B.up_to_date()
