@@ -793,6 +793,19 @@ def main():
         fp64 = measure_fp64_plain(args, g, params, evs, stream, local, rank, dist)
         fp64["factor"] = value / fp64["value"]
 
+    # the seed fits redone in FP64: the seeds whose mixed-precision fit gives |q/pT| below 0.05
+    s_state = torch.zeros((n_seeds, 6), dtype=torch.float32, device=f"cuda:{local}")
+    s_cov = torch.zeros((n_seeds, 21), dtype=torch.float32, device=f"cuda:{local}")
+    s_info = torch.zeros((n_seeds, 3), dtype=torch.int32, device=f"cuda:{local}")
+    ctx.seed(db.seeds, s_state, s_cov, s_info)
+    torch.cuda.synchronize()
+    ok_seed = s_info[:, 2] == 0
+    seed_precision = {
+        "mode": "FP32 trajectory and Jacobian, FP64 covariance transport and update; the seeds with "
+                "|q/pT| < 0.05 /GeV fitted again entirely in FP64",
+        "fp64_redo_fraction": float(((s_state[:, 3].abs() < 0.05) & ok_seed).sum().item() / max(1, n_seeds))}
+    del s_state, s_cov, s_info
+
     bkfit = measure_fit_backward(ctx, db, fit, stream, dist, local)
     cleaning = measure_cleaning(ctx, db, g, stream, local)
     modular = None if mod is None else measure_modular(mod, params, shapes, stream, local, dist)
@@ -873,6 +886,7 @@ def main():
                             "fit": rf_fit},
         "e2e": e2e,
         "fp64_plain": fp64,
+        "seed_precision": seed_precision,
         "fit_grad": grad,
         "configs": configs,
         "fit_backward": bkfit,

@@ -76,7 +76,9 @@ typedef struct {
     float score_hole;
     float barrel_eta_max;  /* region choice with >1 plan: |eta_seed| < this -> plan 0, else 1 (eta>0) / 2 */
     int32_t material;      /* 1: multiple scattering and energy loss at every crossed layer */
-    int32_t precision;     /* MKGB_FP32: Kalman steps of the search and the fit in FP32 (seed fits in FP64);
+    int32_t precision;     /* MKGB_FP32: Kalman steps of the search and the fit in FP32 (seed fits with
+                              FP32 trajectories and FP64 covariance transport and updates, and all in
+                              FP64 for seeds with |q/pT| < 0.05 /GeV);
                               MKGB_FP64: every step in FP64 (the plain comparison path) */
     float kappa_fp64;      /* an update whose innovation covariance S has a condition estimate above this
                               is redone in FP64: the search redoes that update, the fit refits the whole

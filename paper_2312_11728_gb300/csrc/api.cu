@@ -83,6 +83,7 @@ struct mkgb_ctx {
     DevBuf seg_off, in_xyz, in_cov, pay, ep_tmp, bin_of_hit, hit_seg, bins, hb_ep, hb_pay, cursor, scan_tmp;
     int n_seeds = 0;
     DevBuf seed_hits, seed_state, seed_state64, seed_info, seed_key, key_counts, key_cursor, seed_order, seed_scan_tmp;
+    DevBuf seed_redo;   // the seeds whose mixed-precision fit is redone in FP64: count, then indices
     DevBuf counters_build, counters_fit, queue, rescue_list, rescue_count, build_work, probe_sink, grad_ck;
     // backward search: the geometry with reversed plans and the tracks' start records
     DevBuf geom_bwd_d, bw_state, bw_info, bw_order;
@@ -177,6 +178,7 @@ int seed_buffers(mkgb_ctx* ctx, int n) {
     CK(ensure(ctx->key_counts, 4 * (nkeys + 1)));
     CK(ensure(ctx->key_cursor, 4 * (nkeys + 1)));
     CK(ensure(ctx->seed_scan_tmp, 4 * scan_tmp_ints(nkeys + 1)));
+    CK(ensure(ctx->seed_redo, 4 * ((size_t)n + 1)));
     return MKGB_OK;
 }
 
@@ -308,7 +310,7 @@ void mkgb_destroy(mkgb_ctx* ctx) {
         DevBuf* all[] = {&ctx->host_run, &ctx->geom_d, &ctx->seg_off, &ctx->in_xyz, &ctx->in_cov, &ctx->pay, &ctx->ep_tmp,
                          &ctx->bin_of_hit, &ctx->hit_seg, &ctx->bins, &ctx->hb_ep, &ctx->hb_pay, &ctx->cursor,
                          &ctx->scan_tmp, &ctx->seed_hits, &ctx->seed_state, &ctx->seed_state64, &ctx->seed_info, &ctx->seed_key,
-                         &ctx->key_counts, &ctx->key_cursor, &ctx->seed_order, &ctx->seed_scan_tmp,
+                         &ctx->key_counts, &ctx->key_cursor, &ctx->seed_order, &ctx->seed_scan_tmp, &ctx->seed_redo,
                          &ctx->counters_build, &ctx->counters_fit, &ctx->queue, &ctx->rescue_list,
                          &ctx->rescue_count, &ctx->build_work, &ctx->probe_sink, &ctx->grad_ck,
                          &ctx->geom_bwd_d, &ctx->bw_state, &ctx->bw_info, &ctx->bw_order,
@@ -620,9 +622,14 @@ int mkgb_seed(mkgb_ctx* ctx, int n_seeds, const int32_t* seed_hits, int on_devic
     CK(stage_out(ctx, S_C, cov_out, 84 * (size_t)n, on_device, &c21));
     CK(stage_out(ctx, S_D, info_out, 12 * (size_t)n, on_device, &i3));
     const bool fp64 = ctx->params.precision == MKGB_FP64;
+    CK(cudaMemsetAsync(ctx->seed_redo.p, 0, 4, st));
     CK(launch_seed_fit(st, (const DevGeom*)ctx->geom_d.p, ctx->params, hit_store(ctx), n, (const int*)sh,
                        (float*)ctx->seed_state.p, fp64 ? (double*)ctx->seed_state64.p : nullptr,
-                       (int4*)ctx->seed_info.p, (float*)s6, (float*)c21, (int*)i3, SeedRange(), ctx->mod_hits));
+                       (int4*)ctx->seed_info.p, (float*)s6, (float*)c21, (int*)i3, SeedRange(), ctx->mod_hits,
+                       (int*)ctx->seed_redo.p));
+    CK(launch_seed_redo(st, (const DevGeom*)ctx->geom_d.p, ctx->params, hit_store(ctx), n, (const int*)sh,
+                        (float*)ctx->seed_state.p, (int4*)ctx->seed_info.p, (float*)s6, (float*)c21, (int*)i3,
+                        ctx->mod_hits, (const int*)ctx->seed_redo.p, ctx->n_sms));
     rc = seed_order(ctx, st, n);
     if (rc != MKGB_OK) return rc;
     CK(copy_back(ctx, state_out, s6, 24 * (size_t)n, on_device));
@@ -1122,9 +1129,14 @@ int run_host_impl(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const flo
         range.which = which;
         CK(launch_seed_fit(main_st, (const DevGeom*)ctx->geom_d.p, ctx->params, H, n_seeds, d_seeds,
                            (float*)ctx->seed_state.p, fp64 ? (double*)ctx->seed_state64.p : nullptr,
-                           (int4*)ctx->seed_info.p, nullptr, nullptr, nullptr, range, false));
+                           (int4*)ctx->seed_info.p, nullptr, nullptr, nullptr, range, false, (int*)ctx->seed_redo.p));
+        if (which == K)   // every chunk's seeds are fitted: the FP64 redo of the listed ones
+            CK(launch_seed_redo(main_st, (const DevGeom*)ctx->geom_d.p, ctx->params, H, n_seeds, d_seeds,
+                                (float*)ctx->seed_state.p, (int4*)ctx->seed_info.p, nullptr, nullptr, nullptr, false,
+                                (const int*)ctx->seed_redo.p, ctx->n_sms));
         return MKGB_OK;
     };
+    CK(cudaMemsetAsync(ctx->seed_redo.p, 0, 4, main_st));
     CK(cudaStreamWaitEvent(main_st, ctx->ev_seedin, 0));
     HitChunks hc;
     hc.n = K;

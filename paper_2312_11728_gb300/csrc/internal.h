@@ -101,13 +101,17 @@ struct SeedRange {
     int n_chunks = 0;
     int off[kMaxSeedChunks + 1] = {};
 };
-cudaError_t launch_seed(cudaStream_t st, const DevGeom* g, DevParams P, HitStore H, int n, const int* seed_hits,
-                        float* state, double* state64, int4* info, int* key_of, int* key_counts, float* state6,
-                        float* cov21, int* info3);
-// modular: module hits loaded (a seed hit on a module is used on its module's plane)
+// modular: module hits loaded (a seed hit on a module is used on its module's plane).  The FP32
+// path's seed fits are mixed-precision; those with |q/pT| below a limit are left to
+// launch_seed_redo through redo (n + 1 ints: the count, zeroed before the batch's first launch,
+// then the seed indices).  The all-FP64 path fits every seed in FP64 and ignores redo.
 cudaError_t launch_seed_fit(cudaStream_t st, const DevGeom* g, DevParams P, HitStore H, int n, const int* seed_hits,
                             float* state, double* state64, int4* info, float* state6, float* cov21, int* info3,
-                            const SeedRange& range, bool modular);
+                            const SeedRange& range, bool modular, int* redo);
+// The FP64 (FP32-assisted) fits of the seeds listed in redo, after every launch_seed_fit of the batch.
+cudaError_t launch_seed_redo(cudaStream_t st, const DevGeom* g, DevParams P, HitStore H, int n, const int* seed_hits,
+                             float* state, int4* info, float* state6, float* cov21, int* info3, bool modular,
+                             const int* redo, int n_sms);
 cudaError_t launch_seed_keys(cudaStream_t st, int n, const float* state, const int4* info, int* key_of,
                              int* key_counts);
 

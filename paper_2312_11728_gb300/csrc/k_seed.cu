@@ -57,36 +57,46 @@ __device__ __forceinline__ int chunk_of(const SeedRange& r, int h) {
 }
 
 // MOD: module hits loaded (seed hits on modules are used on their planes); the plain
-// instantiation keeps the layers-only registers.
-template <bool FAST, bool MOD>
+// instantiation keeps the layers-only registers.  MODE: the seed fit's precision mode (seed.cuh).
+// redo_in (may be nullptr): the seeds to fit, a list of redo_in[0] seed indices at redo_in + 1
+// (grid-stride); else seed i = the thread.  redo_out (kSeedMixed only, may be nullptr): seeds whose
+// |q/pT| falls below kSeedKappaRedo are appended there in the same layout, to be fitted again.
+template <int MODE, bool MOD>
 __global__ void __launch_bounds__(kThreads) k_seed(const DevGeom* __restrict__ gp, DevParams P, HitStore H, int n,
                                                    const int* __restrict__ seed_hits, float* __restrict__ state,
                                                    double* __restrict__ state64, int4* __restrict__ info,
-                                                   float* state6, float* cov21, int* info3, SeedRange range) {
+                                                   float* state6, float* cov21, int* info3, SeedRange range,
+                                                   const int* __restrict__ redo_in, int* __restrict__ redo_out) {
     __shared__ DevGeom g;
     load_geom(gp, g);
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (range.which >= 0) {   // hits arriving in chunks: the seeds of one chunk, or the rest
-        const int c0 = chunk_of(range, seed_hits[3 * i]), c1 = chunk_of(range, seed_hits[3 * i + 1]),
-                  c2 = chunk_of(range, seed_hits[3 * i + 2]);
-        const bool in_one = c0 >= 0 && c0 == c1 && c1 == c2;
-        if (range.which < range.n_chunks ? !(in_one && c0 == range.which) : in_one) return;
-    }
-    StateT<double> td;
-    int lay[3], event, region, start;
-    const bool ok = seed_fit<double, FAST, MOD>(g, P, H, seed_hits, i, td, lay, event);
-    State t;
-    narrow_state(td, t);
-    seed_region(g, P, t.th, lay[2], ok, region, start);
-    write_seed(t, i, region, start, event, state, info, state6, cov21, info3);
-    if (state64) {   // the FP64 state for the all-FP64 search
-        double* o = state64 + (int64_t)i * kSeedStateStride;
-        o[0] = td.xh; o[1] = td.yh; o[2] = td.zh; o[3] = td.xl; o[4] = td.yl; o[5] = td.zl;
-        o[6] = td.k; o[7] = td.phi; o[8] = td.th;
+    const int n_items = redo_in ? redo_in[0] : n;
+    for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < n_items; item += gridDim.x * blockDim.x) {
+        const int i = redo_in ? redo_in[1 + item] : item;
+        if (range.which >= 0) {   // hits arriving in chunks: the seeds of one chunk, or the rest
+            const int c0 = chunk_of(range, seed_hits[3 * i]), c1 = chunk_of(range, seed_hits[3 * i + 1]),
+                      c2 = chunk_of(range, seed_hits[3 * i + 2]);
+            const bool in_one = c0 >= 0 && c0 == c1 && c1 == c2;
+            if (range.which < range.n_chunks ? !(in_one && c0 == range.which) : in_one) continue;
+        }
+        StateT<double> td;
+        int lay[3], event, region, start;
+        const bool ok = seed_fit<double, MODE, MOD>(g, P, H, seed_hits, i, td, lay, event);
+        if (MODE == kSeedMixed && redo_out && ok && fabs(td.k) < kSeedKappaRedo) {
+            redo_out[1 + atomicAdd(redo_out, 1)] = i;
+            continue;   // written by the redo
+        }
+        State t;
+        narrow_state(td, t);
+        seed_region(g, P, t.th, lay[2], ok, region, start);
+        write_seed(t, i, region, start, event, state, info, state6, cov21, info3);
+        if (state64) {   // the FP64 state for the all-FP64 search
+            double* o = state64 + (int64_t)i * kSeedStateStride;
+            o[0] = td.xh; o[1] = td.yh; o[2] = td.zh; o[3] = td.xl; o[4] = td.yl; o[5] = td.zl;
+            o[6] = td.k; o[7] = td.phi; o[8] = td.th;
 #pragma unroll
-        for (int q = 0; q < 21; ++q) o[9 + q] = td.c[q];
-        o[30] = td.tl; o[31] = td.pl;
+            for (int q = 0; q < 21; ++q) o[9 + q] = td.c[q];
+            o[30] = td.tl; o[31] = td.pl;
+        }
     }
 }
 
@@ -111,13 +121,32 @@ __global__ void __launch_bounds__(kThreads) k_seed_key(int n, const float* __res
 
 cudaError_t launch_seed_fit(cudaStream_t st, const DevGeom* g, DevParams P, HitStore H, int n, const int* seed_hits,
                             float* state, double* state64, int4* info, float* state6, float* cov21, int* info3,
-                            const SeedRange& range, bool modular) {
+                            const SeedRange& range, bool modular, int* redo) {
     if (n == 0) return cudaSuccess;
     const int blocks = (n + kThreads - 1) / kThreads;
-    // the FP32 path's seed fits take the FP32-assisted FP64 steps; the plain all-FP64 path does not
-    auto kern = P.precision == MKGB_FP64 ? (modular ? k_seed<false, true> : k_seed<false, false>)
-                                         : (modular ? k_seed<true, true> : k_seed<true, false>);
-    kern<<<blocks, kThreads, 0, st>>>(g, P, H, n, seed_hits, state, state64, info, state6, cov21, info3, range);
+    if (P.precision == MKGB_FP64) {   // the plain all-FP64 path
+        auto kern = modular ? k_seed<kSeedPlain, true> : k_seed<kSeedPlain, false>;
+        kern<<<blocks, kThreads, 0, st>>>(g, P, H, n, seed_hits, state, state64, info, state6, cov21, info3, range,
+                                          nullptr, nullptr);
+        return cudaGetLastError();
+    }
+    // the FP32 path: mixed-precision seed fits, the low-|q/pT| ones redone FP32-assisted in FP64
+    // when a redo list is given (redo[0] must be zero before the first launch of a batch)
+    auto kern = modular ? k_seed<kSeedMixed, true> : k_seed<kSeedMixed, false>;
+    kern<<<blocks, kThreads, 0, st>>>(g, P, H, n, seed_hits, state, state64, info, state6, cov21, info3, range,
+                                      nullptr, redo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seed_redo(cudaStream_t st, const DevGeom* g, DevParams P, HitStore H, int n, const int* seed_hits,
+                             float* state, int4* info, float* state6, float* cov21, int* info3, bool modular,
+                             const int* redo, int n_sms) {
+    if (n == 0 || P.precision == MKGB_FP64) return cudaSuccess;
+    const int need = (n + kThreads - 1) / kThreads, cap = 8 * n_sms;
+    const int blocks = need < cap ? need : cap;   // grid-stride over the list, whose length the device holds
+    auto kern = modular ? k_seed<kSeedAssisted, true> : k_seed<kSeedAssisted, false>;
+    kern<<<blocks, kThreads, 0, st>>>(g, P, H, n, seed_hits, state, nullptr, info, state6, cov21, info3, SeedRange(),
+                                      redo, nullptr);
     return cudaGetLastError();
 }
 
@@ -126,15 +155,6 @@ cudaError_t launch_seed_keys(cudaStream_t st, int n, const float* state, const i
     if (n == 0) return cudaSuccess;
     k_seed_key<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(n, state, info, key_of, key_counts);
     return cudaGetLastError();
-}
-
-cudaError_t launch_seed(cudaStream_t st, const DevGeom* g, DevParams P, HitStore H, int n, const int* seed_hits,
-                        float* state, double* state64, int4* info, int* key_of, int* key_counts, float* state6,
-                        float* cov21, int* info3) {
-    const cudaError_t e = launch_seed_fit(st, g, P, H, n, seed_hits, state, state64, info, state6, cov21, info3,
-                                          SeedRange(), false);
-    if (e != cudaSuccess) return e;
-    return launch_seed_keys(st, n, state, info, key_of, key_counts);
 }
 
 }  // namespace mk

@@ -35,7 +35,7 @@ __device__ __forceinline__ bool seed_prior(const DevGeom& g, const HitStore& H, 
     const F cross = ax * by - ay * bx;
     const F chord2 = bx * bx + by * by;
     F k, phi1, arc;
-    if (fabs(cross) < F(1e-7) * chord2) {
+    if (fabs(cross) < F(1e-12) * chord2) {   // three points on a line: no curvature
         k = F(0);
         phi1 = atan2(by, bx);
         arc = sqrt(chord2);
@@ -63,14 +63,24 @@ __device__ __forceinline__ bool seed_prior(const DevGeom& g, const HitStore& H, 
     return ok;
 }
 
+// The seed fit's precision modes.  kSeedPlain: every step in F (the all-FP64 path).
+// kSeedAssisted (FP64 with FP32 help): the first update in closed form (zero residual, diagonal
+// prior), FP32 crossings refined by FP64 Newton iterations (propagate_refined), the update's frame
+// from the propagation's direction and the short covariance update (I - K H) C.  kSeedMixed (the
+// seeds of the FP32 path): as kSeedAssisted, but each step's trajectory (float-float positions and
+// angles), Jacobian and material in FP32, with the FP64 covariance transported in FP64 by that
+// Jacobian: the update's cancellation, the ill-conditioned part of the seed fit, stays in FP64,
+// and an FP32 Jacobian only perturbs the problem by ~1e-7 relative.  The FP32 trajectory leaves
+// ~2e-6 cm in a 30 cm step's transverse position, ~1e-6 of q/pT on a short lever arm: seeds with
+// |q/pT| below kSeedKappaRedo, whose q/pT tolerance is that small, are fitted again in
+// kSeedAssisted.
+enum : int { kSeedPlain = 0, kSeedAssisted = 1, kSeedMixed = 2 };
+constexpr double kSeedKappaRedo = 0.05;   // 1/GeV: |q/pT| below which a mixed seed fit is redone
+
 // Seed fit of seed i in precision F: update with hit 1, then propagate to and update with hits
 // 2 and 3 (MOD: a hit measured on a module is used on its module's plane, reached from its
-// layer's surface; hit 1 needs no step, the estimate sits on it).  FAST (the seed fits of the
-// FP32 path): the first update in closed form (zero residual, diagonal prior), the trajectory and
-// Jacobian of each step in FP32 with the covariance transport and the update in FP64, the
-// update's frame from the propagation's direction and the short covariance update (I - K H) C;
-// the plain all-FP64 path takes the general steps.  Returns ok.
-template <class F, bool FAST = false, bool MOD = false>
+// layer's surface; hit 1 needs no step, the estimate sits on it).  Returns ok.
+template <class F, int MODE = kSeedPlain, bool MOD = false>
 __device__ __forceinline__ bool seed_fit(const DevGeom& g, const DevParams& P, const HitStore& H,
                                          const int* __restrict__ seed_hits, int i, StateT<F>& t, int lay[3],
                                          int& event) {
@@ -79,7 +89,7 @@ __device__ __forceinline__ bool seed_fit(const DevGeom& g, const DevParams& P, c
     bool ok = seed_prior(g, H, seed_hits, i, m, v, lay, event, t, mod);
     if constexpr (!MOD) ok = ok && mod[0] < 0 && mod[1] < 0 && mod[2] < 0;
     int newton = 0;
-    constexpr bool fast = FAST && sizeof(F) == 8;
+    constexpr bool fast = MODE != kSeedPlain && sizeof(F) == 8;
     if constexpr (fast)
         ok = ok && prior_update_at_hit(t, v[0]);
     else
@@ -89,11 +99,7 @@ __device__ __forceinline__ bool seed_fit(const DevGeom& g, const DevParams& P, c
         PredT<F> q;
         const DevLayer& L = g.layers[lay[j]];
         F dir[4];
-        if constexpr (fast) {
-            // the trajectory (float-float positions and angles), its Jacobian and the material
-            // in FP32, the covariance transported from the FP64 state in FP64: the ill-conditioned
-            // part of the seed fit, the update's cancellation, stays in FP64, while a Jacobian
-            // rounded to FP32 only perturbs the problem by ~1e-7 relative
+        if constexpr (fast && MODE == kSeedMixed) {
             State t32;
             narrow_to_fp32(t, t32);
             Pred q32;

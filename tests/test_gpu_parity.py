@@ -396,6 +396,46 @@ def test_full_size_phase2_sampled_against_oracle(lib, phase2_full):
     assert rep["cov_bad"] == 0, rep
 
 
+def test_full_size_seeds_against_oracle(lib, phase2_full):
+    """Every one of the 1.28M seeds of the 64-event batch (FP32 trajectory and Jacobian, FP64
+    covariance transport and update) against the oracle's FP64 seed fit: region, start step and
+    status equal, parameters and covariance within the tolerances."""
+    g, batch, params = phase2_full
+    ctx = _ctx(g, params)
+    ctx.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov)
+    n = batch.seed_hits.shape[0]
+    state, cov, info = np.zeros((n, 6), np.float32), np.zeros((n, 21), np.float32), np.zeros((n, 3), np.int32)
+    ctx.seed(batch.seed_hits, state, cov, info)
+    L = g.n_layers
+    sl = np.concatenate([oracle.hit_layers(batch.hit_off[e * L:(e + 1) * L + 1],
+                                           batch.seed_hits[batch.seed_event == e]) for e in range(batch.n_events)])
+    r = oracle.Oracle(g, params).seed_batch(batch.seed_hits, sl, batch.hit_xyz.astype(np.float64),
+                                            batch.hit_cov.astype(np.float64))
+    # the region follows from the seed's eta against the barrel's eta limit, decided in FP32 on the
+    # GPU and in FP64 by the oracle: a seed whose eta lies within 1e-5 of the limit may take either
+    # region (a near-tie, as for hit selection); it must take one of the two
+    eta = -np.log(np.tan(0.5 * r["p"][:, 5]))
+    near = (r["status"] == 0) & (np.abs(np.abs(eta) - g.barrel_eta_max) < 1e-5)
+    side = np.where(eta > 0, 1, 2)
+    assert np.all((info[near, 0] == 0) | (info[near, 0] == side[near]))
+    far = ~near
+    bad_region = np.nonzero(far & (info[:, 0] != r["region"]))[0]
+    ok = far & (r["status"] == 0)
+    pok, prat = PR.param_close(state[ok], r["p"][ok])
+    cok, crat = PR.cov_close_surface(cov[ok], r["c"][ok], r["p"][ok], r["surf"])
+    okidx = np.nonzero(ok)[0]
+    bad = okidx[~(pok.all(1) & cok.all(1))]
+    _report("seed_full_size", dict(seeds=int(n), near_ties=int(near.sum()), bad_region=bad_region[:20],
+                                   n_bad=int(bad.size), bad=bad[:50], bad_param_ratio=prat.max(1)[~(pok.all(1) & cok.all(1))][:50],
+                                   bad_cov_ratio=crat.max(1)[~(pok.all(1) & cok.all(1))][:50],
+                                   worst_param=float(prat.max()), worst_cov=float(crat.max())))
+    assert bad_region.size == 0, (bad_region[:10], eta[bad_region[:10]])
+    assert np.array_equal(info[far, 1], r["start"][far]) and np.array_equal(info[far, 2], r["status"][far])
+    assert near.sum() < 20
+    assert pok.all(), (int((~pok.all(1)).sum()), float(prat.max()))
+    assert cok.all(), (int((~cok.all(1)).sum()), float(crat.max()))
+
+
 # ------------------------------------------------------------------ uneven events, loopers at scale
 
 def test_uneven_events_match_oracle(lib):
