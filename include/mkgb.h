@@ -78,7 +78,7 @@ typedef struct {
     int32_t material;      /* 1: multiple scattering and energy loss at every crossed layer */
     int32_t precision;     /* MKGB_FP32: Kalman steps of the search and the fit in FP32 (seed fits with
                               FP32 trajectories and FP64 covariance transport and updates, and all in
-                              FP64 for seeds with |q/pT| < 0.05 /GeV);
+                              FP64 for seeds with |q/pT| < 0.03 /GeV);
                               MKGB_FP64: every step in FP64 (the plain comparison path) */
     float kappa_fp64;      /* an update whose innovation covariance S has a condition estimate above this
                               is redone in FP64: the search redoes that update, the fit refits the whole

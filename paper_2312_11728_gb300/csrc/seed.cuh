@@ -75,7 +75,7 @@ __device__ __forceinline__ bool seed_prior(const DevGeom& g, const HitStore& H, 
 // |q/pT| below kSeedKappaRedo, whose q/pT tolerance is that small, are fitted again in
 // kSeedAssisted.
 enum : int { kSeedPlain = 0, kSeedAssisted = 1, kSeedMixed = 2 };
-constexpr double kSeedKappaRedo = 0.05;   // 1/GeV: |q/pT| below which a mixed seed fit is redone
+constexpr double kSeedKappaRedo = 0.03;   // 1/GeV: |q/pT| below which a mixed seed fit is redone
 
 // Seed fit of seed i in precision F: update with hit 1, then propagate to and update with hits
 // 2 and 3 (MOD: a hit measured on a module is used on its module's plane, reached from its
