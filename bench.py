@@ -771,7 +771,8 @@ def main():
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    total_ms = sum(e[0].elapsed_time(e[1]) for e in ev_step)
+    step_ms = [e[0].elapsed_time(e[1]) for e in ev_step]
+    total_ms = sum(step_ms)
 
     # stage times from passes through the separate calls (no overlap between stages)
     n_stage = max(1, min(args.steps, 3))
@@ -881,6 +882,8 @@ def main():
                    "parallelism": f"replicas{world}",
                    "search_launch": {"find_shape": shapes[0], "select_shape": shapes[1],
                                      "autotune_ms_per_search": shapes[2], "cuda_graph": not args.no_graph}},
+        "step_ms_spread": {"median": float(np.median(step_ms)), "min": float(np.min(step_ms)),
+                           "max": float(np.max(step_ms))},
         "stages_ms": {k: round(float(v), 4) for k, v in stage.items()},
         "roofline": rf_search,
         "roofline_stages": {"seed": rf_seed, "search": {k: rf_search[k] for k in rf_search
