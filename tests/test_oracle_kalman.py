@@ -114,6 +114,41 @@ def test_seed_recovers_truth_on_noise_free_hits():
     assert n_ok == len(ev.seed_track)
 
 
+def test_seed_of_a_straight_track_and_of_a_very_stiff_one():
+    """Three hits on a straight line (q/pT = 0): the prior takes the line (no circle through three
+    collinear points) and the fit ends on hit 3 with q/pT 0 and the line's angles.  A 500 TeV track,
+    whose three points bend by ~1e-8 of the chord squared (the range where a coarser straight-line
+    threshold would take the line instead), gets the circle's q/pT as its prior and keeps it."""
+    g = S.geometry_barrel()
+    o = oracle.Oracle(g, dict(material=0))
+    r = np.asarray(g.pos[:3], np.float64)
+    v = np.tile(np.array([1e-6, 0.0, 1e-6, 0.0, 0.0, 1e-5]), 3)
+    for phi0, cot in ((0.3, 0.2), (-2.5, -0.7), (1.9, 0.0)):
+        h = np.stack([r * np.cos(phi0), r * np.sin(phi0), 1.5 + r * cot], 1).ravel()
+        ok, p, c, pinit = o.seed(h, v, [0, 1, 2])
+        assert ok
+        assert pinit[3] == 0.0
+        assert abs(p[3]) < 1e-9
+        assert abs(np.angle(np.exp(1j * (p[4] - phi0)))) < 1e-9
+        assert abs(p[5] - np.arctan2(1.0, cot)) < 1e-9
+        assert np.allclose(p[:3], h[6:9], atol=1e-9)
+    # a stiff helix: q/pT = 2e-6 /GeV, starting at the origin towards phi0, crossing the cylinders
+    cB = 0.299792458e-2 * g.bz
+    k, phi0, cot = 2e-6, 0.7, 0.3
+    om = -cB * k                     # signed curvature in 1/cm (the oracle's convention)
+    pts = []
+    for R in r:
+        # on a circle through the origin the chord to the point at radius R is R itself and runs
+        # at half the turning angle, arcsin(R om / 2), from the start direction
+        half = np.arcsin(R * om / 2.0)
+        pts.append((R * np.cos(phi0 + half), R * np.sin(phi0 + half), 2.0 * half / om * cot))
+    h = np.asarray(pts).ravel()
+    ax, ay, bx, by = h[3] - h[0], h[4] - h[1], h[6] - h[0], h[7] - h[1]
+    assert 1e-12 < abs(ax * by - ay * bx) / (bx * bx + by * by) < 1e-7
+    ok, p, c, pinit = o.seed(h, v, [0, 1, 2])
+    assert ok and abs(pinit[3] / k - 1) < 1e-6 and abs(p[3] / k - 1) < 1e-3
+
+
 @pytest.fixture(scope="module")
 def smeared_fit():
     g = S.geometry_barrel()

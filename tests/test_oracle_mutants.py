@@ -27,6 +27,9 @@ MUTANTS = {
                    "double y2 = (r[2] - Lc[4] * y0 - Lc[3] * y1) / Lc[5];"),
     "helix_cot": ("out[2] = p[2] + s * cos(p[5]) / sin(p[5]);", "out[2] = p[2] + s * sin(p[5]) / cos(p[5]);"),
     "seed_charge": ("k = -om / cB;", "k = om / cB;"),
+    "seed_straight_threshold": ("if (fabs(cross) < 1e-12 * chord2) {", "if (fabs(cross) < 1e-7 * chord2) {"),
+    "seed_module_plane_ignored": ("if (ids) {\n            if (!at_hit_surface(g, ids[j]",
+                                  "if (0) {\n            if (!at_hit_surface(g, ids[j]"),
     "window_index": ("ve += ge[i] * M[i][j] * ge[j];", "ve += ge[i] * M[i][i] * ge[j];"),
     "miss_penalty_sign": ("ch.score = cd->score - P->score_hole;", "ch.score = cd->score + P->score_hole;"),
     "child_order": ("if (x->score != y->score) return x->score > y->score ? -1 : 1;",
