@@ -791,14 +791,28 @@ def uneven_counts(n_events=256, mean=8000, lo=200, hi=25000, seed=0):
     return np.clip(rng.poisson(mean, n_events), lo, hi)
 
 
-def workload_uneven(n_events=256, mean=8000, lo=200, hi=25000, seed=0, noise_per_track=2.5, counts=None):
+def _uneven_event(args):
+    n, seed, e, noise_per_track = args
+    return simulate_event(geometry_phase2(), int(n), seed, e, pt_sampler=sample_pt_phase2, eta_max=3.0,
+                          noise_total=int(noise_per_track * n))
+
+
+def workload_uneven(n_events=256, mean=8000, lo=200, hi=25000, seed=0, noise_per_track=2.5, counts=None,
+                    processes=None):
     """Events with Poisson track counts (clipped to [lo, hi]; or the given counts) on the
-    Phase-2-like geometry, noise in proportion to the tracks (50,000 per 20,000 tracks)."""
+    Phase-2-like geometry, noise in proportion to the tracks (50,000 per 20,000 tracks).
+    processes > 1: the events are simulated in a spawn pool of that many processes (the same
+    events: each depends only on (seed, event))."""
     g = geometry_phase2()
     if counts is None:
         counts = uneven_counts(n_events, mean, lo, hi, seed)
-    evs = [simulate_event(g, int(n), seed, e, pt_sampler=sample_pt_phase2, eta_max=3.0,
-                          noise_total=int(noise_per_track * n)) for e, n in enumerate(counts)]
+    jobs = [(int(n), seed, e, noise_per_track) for e, n in enumerate(counts)]
+    if processes and processes > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(processes) as pool:
+            evs = pool.map(_uneven_event, jobs)
+    else:
+        evs = [_uneven_event(j) for j in jobs]
     return g, evs
 
 

@@ -438,6 +438,41 @@ def test_full_size_seeds_against_oracle(lib, phase2_full):
 
 # ------------------------------------------------------------------ uneven events, loopers at scale
 
+def test_uneven_256_events_at_size_sampled_against_oracle(lib):
+    """The uneven-batch workload at its size, as the benchmark runs it: 256 events of Poisson(8,000)
+    tracks clipped to [200, 25,000], ~2.05M seeds searched in one call with the search kernels'
+    shapes autotuned on the batch; the oracle recomputes a random sample of seeds and fit tracks
+    (searches are independent per seed)."""
+    import os
+    import torch
+    g, evs = S.workload_uneven(processes=min(16, os.cpu_count() or 1))
+    batch = S.concat_events(evs, g.n_layers)
+    assert batch.n_events == 256 and batch.seed_hits.shape[0] > 2_000_000
+    params = S.default_params()
+    ctx = _ctx(g, params)
+    fi = pipeline.fit_inputs(batch)
+    db = pipeline.DeviceBatch(batch, fi, g.max_plan, "cuda")
+    pipeline.run_step(ctx, db)
+    torch.cuda.synchronize()
+    ctx.autotune(reps=1)   # keeps the fastest shapes, as the benchmark's pass does
+    pipeline.run_step_fused(ctx, db)
+    torch.cuda.synchronize()
+    gpu = {k: v.cpu().numpy() for k, v in db.out.items()}
+    rng = np.random.default_rng(17)
+    sample = np.sort(rng.choice(batch.seed_hits.shape[0], 400, replace=False))
+    orc = oracle.Oracle(g, params)
+    rep = _report("build_uneven_256", PR.compare_build(gpu, PR.oracle_build(orc, batch, sample)))
+    assert len(rep["hit_mismatch"]) == 0 and rep["failed_mismatch"] == 0, rep
+    assert rep["param_bad"] == 0 and rep["cov_bad"] == 0 and rep["chi2_bad"] == 0, rep
+    tsample = np.sort(rng.choice(fi.layers.shape[0], 2000, replace=False))
+    r = orc.fit_batch(fi.layers[tsample], fi.hits[tsample], batch.hit_xyz.astype(np.float64),
+                      batch.hit_cov.astype(np.float64), fi.p0[tsample].astype(np.float64),
+                      fi.c0[tsample].astype(np.float64))
+    gf = {k: db.fit[k].cpu().numpy()[tsample] for k in ("p", "c", "chi2", "status")}
+    rep = _report("fit_uneven_256", PR.compare_fit(gf, r))
+    assert rep["status_bad"] == 0 and rep["param_bad"] == 0 and rep["chi2_bad"] == 0 and rep["cov_bad"] == 0, rep
+
+
 def test_uneven_events_match_oracle(lib):
     """Events of very different sizes in one call (Poisson track counts as in the uneven-batch
     workload, plus a 20-track, a 1,500-track and a track-less event with noise only): every
