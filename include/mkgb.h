@@ -170,8 +170,8 @@ int mkgb_load_hits_modular(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, 
 
 /* Seeds (Sec. 2.2): n_seeds x 3 hit indices on three consecutive crossed layers of one event,
  * innermost first.  Computes each seed's state at its third hit (circle estimate + 3-hit
- * Kalman fit), its region and first search step, and orders seeds by (event, eta, phi) for
- * hit-access coherency.  Optional outputs (NULL to skip): state n x 6, cov n x 21, info n x 3
+ * Kalman fit; precision as params.precision states), its region and first search step, and
+ * orders seeds by (event, eta, phi) for hit-access coherency.  Optional outputs (NULL to skip): state n x 6, cov n x 21, info n x 3
  * (region, first plan step, status 0 = ok).  Errors: MKGB_ESTATE without hits, MKGB_EINVAL. */
 int mkgb_seed(mkgb_ctx* ctx, int n_seeds, const int32_t* seed_hits, int on_device,
               float* state_out, float* cov_out, int32_t* info_out);
