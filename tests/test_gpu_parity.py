@@ -150,6 +150,37 @@ def test_seed_states_match_oracle(lib, which, request):
     assert cok.all(), crat.max()
 
 
+@pytest.mark.parametrize("pt", [(60.0, 500.0), (0.5, 0.6)])
+def test_seeds_all_or_none_refitted_in_fp64_match_oracle(lib, pt):
+    """Stiff tracks only (pT 60-500 GeV: >90% of the seeds fit |q/pT| < 0.03 and go through the
+    FP64 refit list; the rest are short forward seeds whose q/pT the three hits fix only loosely)
+    and soft tracks only (0.5-0.6 GeV: the list stays empty): seed states against the oracle, as
+    for the mixed workloads."""
+    g = S.geometry_phase2()
+    ev = S.simulate_event(g, 1500, 5, 0, pt_sampler=lambda rng, n: S.sample_pt_loguniform(rng, n, *pt), eta_max=3.0,
+                          noise_total=1000)
+    batch = S.concat_events([ev], g.n_layers)
+    params = S.default_params()
+    ctx = _ctx(g, params)
+    ctx.load_hits(batch.n_events, batch.hit_off, batch.hit_xyz, batch.hit_cov)
+    n = batch.seed_hits.shape[0]
+    state, cov, info = np.zeros((n, 6), np.float32), np.zeros((n, 21), np.float32), np.zeros((n, 3), np.int32)
+    ctx.seed(batch.seed_hits, state, cov, info)
+    r = oracle.Oracle(g, params).seed_batch(batch.seed_hits, oracle.hit_layers(batch.hit_off, batch.seed_hits),
+                                            batch.hit_xyz.astype(np.float64), batch.hit_cov.astype(np.float64))
+    ok = r["status"] == 0
+    refit = np.abs(r["p"][ok, 3]) < 0.03
+    assert refit.mean() > 0.9 if pt[0] > 1 else not refit.any()
+    assert np.array_equal(info[:, 2], r["status"])
+    eta = -np.log(np.tan(0.5 * r["p"][:, 5]))
+    far = ~(ok & (np.abs(np.abs(eta) - g.barrel_eta_max) < 1e-5))
+    assert np.array_equal(info[far, 0], r["region"][far])
+    pok, prat = PR.param_close(state[ok], r["p"][ok])
+    cok, crat = PR.cov_close_surface(cov[ok], r["c"][ok], r["p"][ok], r["surf"])
+    assert pok.all(), prat.max()
+    assert cok.all(), crat.max()
+
+
 @pytest.mark.parametrize("which", ["small_barrel", "phase2_small"])
 def test_fit_over_known_assignment_matches_oracle(lib, which, request):
     g, batch, params = request.getfixturevalue(which)
