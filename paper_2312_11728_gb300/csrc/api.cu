@@ -986,6 +986,16 @@ int mkgb_fit_static(mkgb_ctx* ctx, int n, int max_steps, const int32_t* layers, 
 
 namespace {
 
+// The fit's stream in a one-call pass: the highest priority, so that its blocks are scheduled
+// as soon as SM resources free up beside the FP64-bound seed fit and the latency-bound search
+// (28.03 against 28.13 ms per 64-event pass at the default priority).
+cudaError_t create_fit_stream(cudaStream_t* st) {
+    int least = 0, greatest = 0;
+    const cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e != cudaSuccess) return e;
+    return cudaStreamCreateWithPriority(st, cudaStreamNonBlocking, greatest);
+}
+
 int run_impl(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* xyz, const float* cov6,
              const int32_t* hit_module, int n_seeds, const int32_t* seed_hits, const mkgb_tracks* out, int n_fit,
              int max_steps, const int32_t* layers, const int32_t* hits, const float* p0, const float* c0,
@@ -993,7 +1003,7 @@ int run_impl(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const float* x
     DevGuard guard(ctx->device);
     const cudaStream_t main_st = ctx->stream;
     if (!ctx->fit_st) {
-        CK(cudaStreamCreateWithFlags(&ctx->fit_st, cudaStreamNonBlocking));
+        CK(create_fit_stream(&ctx->fit_st));
         CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&ctx->ev_fit, cudaEventDisableTiming));
     }
@@ -1042,7 +1052,7 @@ int run_host_impl(mkgb_ctx* ctx, int n_events, const int64_t* seg_off, const flo
     DevGuard guard(ctx->device);
     const cudaStream_t main_st = ctx->stream;
     if (!ctx->fit_st) {
-        CK(cudaStreamCreateWithFlags(&ctx->fit_st, cudaStreamNonBlocking));
+        CK(create_fit_stream(&ctx->fit_st));
         CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&ctx->ev_fit, cudaEventDisableTiming));
     }
