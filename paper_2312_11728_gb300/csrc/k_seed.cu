@@ -9,12 +9,13 @@
 // state at hit 3.  The seed's region (layer plan) follows from its eta, and the search
 // starts at the plan step after hit 3's layer.
 //
-// Precision: the seed fit runs in FP64 (the same code instantiated for double).  Its diffuse
-// prior makes every update badly conditioned (the innovation covariance S has a condition
-// number of ~1e6 at the median seed): the posterior variance along a precisely measured
-// direction is a small difference of numbers that FP32 rounding has already perturbed.  It is
-// done once per seed, against ~60 FP32 Kalman steps per seed in the search.  A second kernel
-// computes the (event, eta, phi) ordering keys.
+// Precision: the seed fit's covariance arithmetic runs in FP64.  Its diffuse prior makes every
+// update badly conditioned (the innovation covariance S has a condition number of ~1e6 at the
+// median seed): the posterior variance along a precisely measured direction is a small
+// difference of numbers that FP32 rounding has already perturbed.  The trajectory and Jacobian
+// of each step are FP32 in the FP32 path (seed.cuh, kSeedMixed); seeds whose q/pT is too small
+// for the FP32 trajectory's accuracy are fitted again in FP64 from a device list.  Another
+// kernel computes the (event, eta, phi) ordering keys.
 #include "seed.cuh"
 
 namespace mk {

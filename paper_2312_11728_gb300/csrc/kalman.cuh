@@ -79,7 +79,7 @@ struct DevParams {
     int max_cands, max_holes, material;
     float nsig, deta_min, deta_max, dphi_min, dphi_max;
     float score_hit, score_hole, barrel_eta_max;
-    int precision;      // MKGB_FP32: FP32 Kalman steps (FP64 seed fit); MKGB_FP64: every step in FP64
+    int precision;      // MKGB_FP32: FP32 Kalman steps (mixed-precision seed fit); MKGB_FP64: every step in FP64
     float kappa_fp64;   // fit: tracks with an update whose S condition estimate exceeds this are refit in FP64
     float fit_outlier_chi2;   // fits: a listed hit with a predicted chi2 above this is not used (0: off)
     float score_overlap;      // search: score of a picked-up overlap hit (Sec. 2.2)
